@@ -1,0 +1,228 @@
+"""ctypes binding of the FP64 CPU oracle (vl2_oracle.cpp).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the benchmark's
+CPU-baseline / reference leg.  The product path never imports this module.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "vl2_oracle.cpp")
+BUILD_DIR = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD_DIR, "liborc.so")
+
+HLLE, HLLD = 0, 1
+DC, PLM = 0, 1
+VL2, RK1, RK2, RK3 = 0, 1, 2, 3
+
+_lib = None
+
+
+def build(force=False):
+    """Compile the oracle with value-safe flags (no FMA contraction, no reassociation)."""
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+        return LIB
+    tmp = LIB + ".tmp%d" % os.getpid()
+    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+           "-o", tmp, SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.orc_mesh_new.restype = ctypes.c_void_p
+        L.orc_mesh_new.argtypes = [ip, ip, dp, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_int]
+        L.orc_mesh_free.argtypes = [ctypes.c_void_p]
+        L.orc_set_prims.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
+        L.orc_get_cons.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
+        L.orc_get_prims.argtypes = [ctypes.c_void_p, dp]
+        L.orc_fill_ghosts.argtypes = [ctypes.c_void_p]
+        L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_double]
+        L.orc_new_dt.argtypes = [ctypes.c_void_p, ctypes.c_double]
+        L.orc_new_dt.restype = ctypes.c_double
+        L.orc_floor_count.argtypes = [ctypes.c_void_p]
+        L.orc_floor_count.restype = ctypes.c_long
+        L.orc_emf_mismatch_count.argtypes = [ctypes.c_void_p]
+        L.orc_emf_mismatch_count.restype = ctypes.c_long
+        L.orc_debug_fluxes.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, dp, dp]
+        L.orc_debug_emfs.argtypes = [ctypes.c_void_p, ctypes.c_int, dp, dp, dp]
+        L.orc_divb_norm.argtypes = [ctypes.c_void_p]
+        L.orc_divb_norm.restype = ctypes.c_double
+        L.orc_totals.argtypes = [ctypes.c_void_p, dp]
+        L.orc_riemann.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double, dp]
+        L.orc_physical_flux.argtypes = [dp, ctypes.c_double, ctypes.c_double, dp, dp]
+        L.orc_fast_speed.argtypes = [ctypes.c_double] * 6
+        L.orc_fast_speed.restype = ctypes.c_double
+        L.orc_vanleer_slope.argtypes = [ctypes.c_double] * 3
+        L.orc_vanleer_slope.restype = ctypes.c_double
+        L.orc_ct_corner.argtypes = [dp, dp, dp, dp, dp]
+        L.orc_ct_corner.restype = ctypes.c_double
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ------------------------------------------------------------------------------------------------
+# pointwise functions
+# ------------------------------------------------------------------------------------------------
+
+def riemann(solver, wl, wr, bn, gamma):
+    f = np.zeros(7)
+    wl, wr = _c64(wl), _c64(wr)
+    lib().orc_riemann(solver, _dp(wl), _dp(wr), float(bn), float(gamma), _dp(f))
+    return f
+
+
+def physical_flux(w, bn, gamma):
+    w = _c64(w)
+    u, f = np.zeros(7), np.zeros(7)
+    lib().orc_physical_flux(_dp(w), float(bn), float(gamma), _dp(u), _dp(f))
+    return u, f
+
+
+def fast_speed(d, p, bn, bt1, bt2, gamma):
+    return lib().orc_fast_speed(d, p, bn, bt1, bt2, gamma)
+
+
+def vanleer_slope(qm, q0, qp):
+    return lib().orc_vanleer_slope(qm, q0, qp)
+
+
+def ct_corner(ea, eb, ec, ma, mb):
+    arrs = [_c64(a) for a in (ea, eb, ec, ma, mb)]
+    return lib().orc_ct_corner(*[_dp(a) for a in arrs])
+
+
+# ------------------------------------------------------------------------------------------------
+# mesh
+# ------------------------------------------------------------------------------------------------
+
+class Mesh:
+    """Oracle mesh of equal-size MeshBlocks holding one VL2 state."""
+
+    def __init__(self, nx, mb, xmin=(0.0, 0.0, 0.0), xmax=(1.0, 1.0, 1.0), gamma=5.0 / 3.0,
+                 riemann=HLLD, bc=(0,) * 6, dfloor=1e-12, pfloor=1e-12, integrator=VL2):
+        self.nx = tuple(int(v) for v in nx)
+        self.mb = tuple(int(v) for v in mb)
+        self.xmin, self.xmax = tuple(xmin), tuple(xmax)
+        self.gamma = gamma
+        L = lib()
+        ia = (ctypes.c_int * 3)(*self.nx)
+        ib = (ctypes.c_int * 3)(*self.mb)
+        da = (ctypes.c_double * 3)(*self.xmin)
+        db = (ctypes.c_double * 3)(*self.xmax)
+        bcs = (ctypes.c_int * 6)(*bc)
+        self._h = L.orc_mesh_new(ia, ib, da, db, gamma, riemann, bcs, dfloor, pfloor, integrator)
+        if not self._h:
+            raise ValueError("invalid oracle mesh parameters")
+
+    @classmethod
+    def from_problem(cls, prob, **kw):
+        m = cls(prob.nx, kw.pop("mb", prob.mb), prob.xmin, prob.xmax, prob.gamma, bc=prob.bc, **kw)
+        m.set_prims(prob.w, prob.b1, prob.b2, prob.b3)
+        return m
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().orc_mesh_free(h)
+            self._h = None
+
+    @property
+    def shape(self):
+        return (self.nx[2], self.nx[1], self.nx[0])
+
+    @property
+    def dx(self):
+        return tuple((self.xmax[d] - self.xmin[d]) / self.nx[d] for d in range(3))
+
+    def face_shapes(self):
+        NX, NY, NZ = self.nx
+        return (NZ, NY, NX + 1), (NZ, NY + 1, NX), (NZ + 1, NY, NX)
+
+    def set_prims(self, w, b1, b2, b3):
+        arrs = [_c64(a) for a in (w, b1, b2, b3)]
+        lib().orc_set_prims(self._h, *[_dp(a) for a in arrs])
+
+    def get_cons(self):
+        u = np.zeros((5,) + self.shape)
+        b = [np.zeros(s) for s in self.face_shapes()]
+        lib().orc_get_cons(self._h, _dp(u), *[_dp(x) for x in b])
+        return u, b[0], b[1], b[2]
+
+    def get_prims(self):
+        w = np.zeros((8,) + self.shape)
+        lib().orc_get_prims(self._h, _dp(w))
+        return w
+
+    def fill_ghosts(self):
+        lib().orc_fill_ghosts(self._h)
+
+    def step(self, dt):
+        lib().orc_step(self._h, float(dt))
+
+    def new_dt(self, cfl):
+        return lib().orc_new_dt(self._h, float(cfl))
+
+    def floor_count(self):
+        return lib().orc_floor_count(self._h)
+
+    def emf_mismatch_count(self):
+        return lib().orc_emf_mismatch_count(self._h)
+
+    def debug_fluxes(self, recon):
+        NX, NY, NZ = self.nx
+        fx = np.zeros((7, NZ, NY, NX + 1))
+        fy = np.zeros((7, NZ, NY + 1, NX))
+        fz = np.zeros((7, NZ + 1, NY, NX))
+        lib().orc_debug_fluxes(self._h, recon, _dp(fx), _dp(fy), _dp(fz))
+        return fx, fy, fz
+
+    def debug_emfs(self, recon):
+        NX, NY, NZ = self.nx
+        e1 = np.zeros((NZ + 1, NY + 1, NX))
+        e2 = np.zeros((NZ + 1, NY, NX + 1))
+        e3 = np.zeros((NZ, NY + 1, NX + 1))
+        lib().orc_debug_emfs(self._h, recon, _dp(e1), _dp(e2), _dp(e3))
+        return e1, e2, e3
+
+    def divb_norm(self):
+        return lib().orc_divb_norm(self._h)
+
+    def totals(self):
+        out = np.zeros(8)
+        lib().orc_totals(self._h, _dp(out))
+        return out
+
+    def run(self, t_end, cfl=0.3, max_steps=100000):
+        """Advance to t_end with the CFL step, the last step clipped to land on t_end."""
+        t, nsteps = 0.0, 0
+        while t < t_end and nsteps < max_steps:
+            dt = self.new_dt(cfl)
+            if t + dt > t_end:
+                dt = t_end - t
+            self.step(dt)
+            t += dt
+            nsteps += 1
+        return nsteps

@@ -1,0 +1,1075 @@
+/*
+ * vl2_oracle.cpp -- plain, slow, FP64 CPU oracle of one VL2 cycle of adiabatic ideal MHD on a
+ * uniform mesh of equal-size MeshBlocks (Stone, Tomida, White & Felker 2020, "The Athena++
+ * Adaptive Mesh Refinement Framework", arXiv:2005.06651).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library exists to check the CUDA path.  Only the tests, the
+ * smoke check and the benchmark's CPU-baseline / reference leg may load it; the product path never
+ * calls it, and it shares no code, header or table with the CUDA sources.
+ *
+ * What it follows, step by step (sections / equations of the paper):
+ *   - equations of ideal MHD, mu = 1, total energy E = e + rho v^2/2 + B^2/2     (Sec. 3.1, eq. cons,
+ *     eq. total_energy), ideal-gas EOS P = (gamma-1) e                          (Sec. 3.1)
+ *   - finite volumes: cell-averaged U, face-area-averaged B, edge EMFs (upwind CT) (Sec. 3.1, Sec. 2.1.1)
+ *   - MeshBlocks of equal size with N_G = 2 ghost layers, filled from the 26 neighbours
+ *     (periodic wrap, or outflow = copy of the nearest active cell)              (Sec. 2.1, 2.1.1)
+ *   - EMFs on edges shared by several MeshBlocks are averaged over the copies   (Sec. 2.1.1)
+ *   - donor-cell and PLM reconstruction of primitives, original van Leer limiter (Sec. 3.2.1)
+ *   - HLLE and HLLD approximate Riemann solvers                                 (Sec. 3.2.2)
+ *   - 2S low-storage register scheme (eq. rk-2s) with the VL2 coefficients; the
+ *     predictor uses donor-cell fluxes                                           (Sec. 3.2.3)
+ *   - one global time step from |v| + C_f                                      (Sec. 2.1.7, 3.2.3)
+ *
+ * The paper names HLLE / HLLD / upwind CT / VL2 but prints no formulas for them; the formulas here
+ * are written from the published methods (HLLD: Miyoshi & Kusano 2005; upwind CT: Gardiner &
+ * Stone 2005; VL2: Stone & Gardiner 2009).  Every point where the paper is silent is marked
+ * [reading] below; the CUDA path takes the same reading.
+ *
+ * Every expression that combines a left and a right quantity is written so that it is exactly
+ * (bitwise) mirror symmetric: swapping L and R and negating the normal components gives the
+ * negated result in IEEE arithmetic.  Build with -ffp-contract=off (no FMA contraction), as the
+ * paper requires for value-safe symmetric results (Sec. 3.3.5).
+ *
+ * Parity pins: every function here is pinned by a CPU test (consistency, exact contact / rotational
+ * discontinuity, exact Sod solution, linear-wave convergence slope, CT identities, conservation,
+ * mirror / axis symmetry).  The choice of the upwind cell in the CT corner EMF (gs05) is pinned only
+ * through the convergence slope and the symmetry tests ("parity partially pinned").
+ */
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+namespace orc {
+
+using std::fabs;
+using std::sqrt;
+
+enum { RS_HLLE = 0, RS_HLLD = 1 };
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
+enum { REC_DC = 0, REC_PLM = 1 };
+enum { INT_VL2 = 0, INT_RK1 = 1, INT_RK2 = 2, INT_RK3 = 3 };
+
+/* Interface-state layout (normal n, transverse t1, t2 taken cyclically: x->(y,z), y->(z,x),
+ * z->(x,y)), and flux layout (mass, normal momentum, two transverse momenta, energy, two transverse
+ * field components). */
+enum { IDN = 0, IVN = 1, IVT1 = 2, IVT2 = 3, IPR = 4, IBT1 = 5, IBT2 = 6, NW7 = 7 };
+
+template <class T> static inline T vmin(T a, T b) { return (a < b) ? a : b; }
+template <class T> static inline T vmax(T a, T b) { return (a > b) ? a : b; }
+
+/* ---------------------------------------------------------------------------------------------
+ * Pointwise physics
+ * ------------------------------------------------------------------------------------------- */
+
+/* Conserved state and physical flux of one 1D interface state (eq. cons with P* = P + B^2/2,
+ * eq. total_energy, ideal EOS). */
+template <class T>
+static void physical_flux(const T w[NW7], T bn, double gamma, T u[NW7], T f[NW7]) {
+  const T d = w[IDN], vn = w[IVN], vt1 = w[IVT1], vt2 = w[IVT2], p = w[IPR];
+  const T bt1 = w[IBT1], bt2 = w[IBT2];
+  const T b2 = (bn * bn + bt1 * bt1) + bt2 * bt2;
+  const T v2 = (vn * vn + vt1 * vt1) + vt2 * vt2;
+  const T e = p / (gamma - 1.0) + 0.5 * d * v2 + 0.5 * b2;
+  const T pt = p + 0.5 * b2;
+  const T vb = (vn * bn + vt1 * bt1) + vt2 * bt2;
+  u[IDN] = d;
+  u[IVN] = d * vn;
+  u[IVT1] = d * vt1;
+  u[IVT2] = d * vt2;
+  u[IPR] = e;
+  u[IBT1] = bt1;
+  u[IBT2] = bt2;
+  f[IDN] = d * vn;
+  f[IVN] = d * vn * vn + pt - bn * bn;
+  f[IVT1] = d * vn * vt1 - bn * bt1;
+  f[IVT2] = d * vn * vt2 - bn * bt2;
+  f[IPR] = (e + pt) * vn - bn * vb;
+  f[IBT1] = bt1 * vn - bn * vt1;
+  f[IBT2] = bt2 * vn - bn * vt2;
+}
+
+/* Fast magnetosonic speed along the normal, C_f^2 = (a^2 + b^2/rho + sqrt((a^2 + b^2/rho)^2 -
+ * 4 a^2 b_n^2/rho)) / 2, with the radicand rewritten as (a^2 - c_n^2)^2 + c_t^2 (c_t^2 + 2 a^2 + 2 c_n^2)
+ * (algebraically identical, never negative). */
+template <class T>
+static T fast_speed(T d, T p, T bn, T bt1, T bt2, double gamma) {
+  const T asq = gamma * p / d;
+  const T cnsq = bn * bn / d;
+  const T ctsq = (bt1 * bt1 + bt2 * bt2) / d;
+  const T diff = asq - cnsq;
+  const T rad = diff * diff + ctsq * (ctsq + 2.0 * (asq + cnsq));
+  const T cf2 = 0.5 * ((asq + cnsq + ctsq) + sqrt(rad));
+  return sqrt(cf2);
+}
+
+/* HLLE flux [reading: the paper prints no formula; outer speeds are the extreme fast-wave speeds of
+ * the two states, S_L = min(u_L - c_L, u_R - c_R), S_R = max(u_L + c_L, u_R + c_R)]. */
+template <class T>
+static void flux_hlle(const T wl[NW7], const T wr[NW7], T bn, double gamma, T f[NW7]) {
+  T ul[NW7], ur[NW7], fl[NW7], fr[NW7];
+  physical_flux(wl, bn, gamma, ul, fl);
+  physical_flux(wr, bn, gamma, ur, fr);
+  const T cl = fast_speed(wl[IDN], wl[IPR], bn, wl[IBT1], wl[IBT2], gamma);
+  const T cr = fast_speed(wr[IDN], wr[IPR], bn, wr[IBT1], wr[IBT2], gamma);
+  const T sl = vmin(wl[IVN] - cl, wr[IVN] - cr);
+  const T sr = vmax(wl[IVN] + cl, wr[IVN] + cr);
+  const T bm = vmin(sl, T(0.0));
+  const T bp = vmax(sr, T(0.0));
+  for (int n = 0; n < NW7; ++n)
+    f[n] = ((bp * fl[n] - bm * fr[n]) + (bp * bm) * (ur[n] - ul[n])) / (bp - bm);
+}
+
+/* HLLD flux (Miyoshi & Kusano 2005), written out in the order of that method:
+ * outer speeds, contact speed S_M, total pressure p_T*, single-star states, Alfven speeds S*_L/R,
+ * double-star states, flux selection.
+ * [reading] S_L = min(u_L,u_R) - max(c_L,c_R), S_R = max(u_L,u_R) + max(c_L,c_R);
+ * [reading] p_T* in its symmetric two-sided form;
+ * [reading] degenerate single-star case when |rho(S-u)(S-S_M) - b_n^2| <= 1e-8 p_T*: transverse
+ *           velocity and field unchanged;
+ * [reading] sign(b_n) = +1 for b_n = 0 (the double-star fans then have zero width);
+ * [reading] selection: the sign of S_M picks the side; on a side, ties at a wave speed of exactly 0
+ *           go to the outer state (the added jump is multiplied by 0); at S_M == 0 exactly the two
+ *           sides' double-star (or star) fluxes are averaged, which keeps the scheme exactly mirror
+ *           symmetric. */
+template <class T>
+static void flux_hlld(const T wl[NW7], const T wr[NW7], T bn, double gamma, T f[NW7]) {
+  T ul[NW7], ur[NW7], fl[NW7], fr[NW7];
+  physical_flux(wl, bn, gamma, ul, fl);
+  physical_flux(wr, bn, gamma, ur, fr);
+  const T cl = fast_speed(wl[IDN], wl[IPR], bn, wl[IBT1], wl[IBT2], gamma);
+  const T cr = fast_speed(wr[IDN], wr[IPR], bn, wr[IBT1], wr[IBT2], gamma);
+  const T cmax = vmax(cl, cr);
+  const T sl = vmin(wl[IVN], wr[IVN]) - cmax;
+  const T sr = vmax(wl[IVN], wr[IVN]) + cmax;
+
+  const T ptl = wl[IPR] + 0.5 * ((bn * bn + wl[IBT1] * wl[IBT1]) + wl[IBT2] * wl[IBT2]);
+  const T ptr = wr[IPR] + 0.5 * ((bn * bn + wr[IBT1] * wr[IBT1]) + wr[IBT2] * wr[IBT2]);
+  const T al = (sl - wl[IVN]) * wl[IDN];  // rho_L (S_L - u_L) < 0
+  const T ar = (sr - wr[IVN]) * wr[IDN];  // rho_R (S_R - u_R) > 0
+  const T den = ar - al;
+  const T sm = ((ar * wr[IVN] - al * wl[IVN]) + (ptl - ptr)) / den;
+  const T ptst = ((ar * ptl - al * ptr) + (ar * al) * (wr[IVN] - wl[IVN])) / den;
+
+  /* single-star states */
+  T us[2][NW7];
+  T dst[2];
+  const T* w[2] = {wl, wr};
+  const T* uu[2] = {ul, ur};
+  const T s[2] = {sl, sr};
+  const T a[2] = {al, ar};
+  const T pt[2] = {ptl, ptr};
+  T vbst[2];
+  T vtst[2][2], btst[2][2];
+  for (int side = 0; side < 2; ++side) {
+    const T* ws = w[side];
+    const T sms = s[side] - sm;
+    dst[side] = a[side] / sms;
+    const T dd = a[side] * sms - bn * bn;
+    if (fabs(dd) > 1.0e-8 * ptst) {
+      const T tv = bn * (sm - ws[IVN]) / dd;
+      const T tb = (a[side] * (s[side] - ws[IVN]) - bn * bn) / dd;
+      vtst[side][0] = ws[IVT1] - ws[IBT1] * tv;
+      vtst[side][1] = ws[IVT2] - ws[IBT2] * tv;
+      btst[side][0] = ws[IBT1] * tb;
+      btst[side][1] = ws[IBT2] * tb;
+    } else {
+      vtst[side][0] = ws[IVT1];
+      vtst[side][1] = ws[IVT2];
+      btst[side][0] = ws[IBT1];
+      btst[side][1] = ws[IBT2];
+    }
+    const T vb = (ws[IVN] * bn + ws[IVT1] * ws[IBT1]) + ws[IVT2] * ws[IBT2];
+    vbst[side] = (sm * bn + vtst[side][0] * btst[side][0]) + vtst[side][1] * btst[side][1];
+    const T est = ((((s[side] - ws[IVN]) * uu[side][IPR] - pt[side] * ws[IVN]) + ptst * sm) +
+                   bn * (vb - vbst[side])) /
+                  sms;
+    us[side][IDN] = dst[side];
+    us[side][IVN] = dst[side] * sm;
+    us[side][IVT1] = dst[side] * vtst[side][0];
+    us[side][IVT2] = dst[side] * vtst[side][1];
+    us[side][IPR] = est;
+    us[side][IBT1] = btst[side][0];
+    us[side][IBT2] = btst[side][1];
+  }
+
+  /* double-star states */
+  const T sqdl = sqrt(dst[0]);
+  const T sqdr = sqrt(dst[1]);
+  const T abn = fabs(bn);
+  const T sls = sm - abn / sqdl;
+  const T srs = sm + abn / sqdr;
+  const T sgn = (bn >= 0.0) ? T(1.0) : T(-1.0);
+  const T sqsum = sqdl + sqdr;
+  const T vt1ss = ((sqdl * vtst[0][0] + sqdr * vtst[1][0]) + (btst[1][0] - btst[0][0]) * sgn) / sqsum;
+  const T vt2ss = ((sqdl * vtst[0][1] + sqdr * vtst[1][1]) + (btst[1][1] - btst[0][1]) * sgn) / sqsum;
+  const T bt1ss =
+      ((sqdl * btst[1][0] + sqdr * btst[0][0]) + (sqdl * sqdr) * (vtst[1][0] - vtst[0][0]) * sgn) / sqsum;
+  const T bt2ss =
+      ((sqdl * btst[1][1] + sqdr * btst[0][1]) + (sqdl * sqdr) * (vtst[1][1] - vtst[0][1]) * sgn) / sqsum;
+  const T vbss = (sm * bn + vt1ss * bt1ss) + vt2ss * bt2ss;
+  T uss[2][NW7];
+  for (int side = 0; side < 2; ++side) {
+    uss[side][IDN] = dst[side];
+    uss[side][IVN] = dst[side] * sm;
+    uss[side][IVT1] = dst[side] * vt1ss;
+    uss[side][IVT2] = dst[side] * vt2ss;
+    uss[side][IBT1] = bt1ss;
+    uss[side][IBT2] = bt2ss;
+  }
+  uss[0][IPR] = us[0][IPR] - sqdl * (vbst[0] - vbss) * sgn;
+  uss[1][IPR] = us[1][IPR] + sqdr * (vbst[1] - vbss) * sgn;
+
+  /* flux selection: left-side pick and right-side pick */
+  T fpl[NW7], fpr[NW7];
+  for (int n = 0; n < NW7; ++n) {
+    if (sl >= 0.0) {
+      fpl[n] = fl[n];
+    } else if (sls >= 0.0) {
+      fpl[n] = fl[n] + sl * (us[0][n] - ul[n]);
+    } else {
+      fpl[n] = (fl[n] + sl * (us[0][n] - ul[n])) + sls * (uss[0][n] - us[0][n]);
+    }
+    if (sr <= 0.0) {
+      fpr[n] = fr[n];
+    } else if (srs <= 0.0) {
+      fpr[n] = fr[n] + sr * (us[1][n] - ur[n]);
+    } else {
+      fpr[n] = (fr[n] + sr * (us[1][n] - ur[n])) + srs * (uss[1][n] - us[1][n]);
+    }
+  }
+  for (int n = 0; n < NW7; ++n) {
+    if (sm > 0.0)
+      f[n] = fpl[n];
+    else if (sm < 0.0)
+      f[n] = fpr[n];
+    else
+      f[n] = 0.5 * (fpl[n] + fpr[n]);
+  }
+}
+
+template <class T>
+static void riemann(int solver, const T wl[NW7], const T wr[NW7], T bn, double gamma, T f[NW7]) {
+  if (solver == RS_HLLE)
+    flux_hlle(wl, wr, bn, gamma, f);
+  else
+    flux_hlld(wl, wr, bn, gamma, f);
+}
+
+/* Piecewise-linear slope with the original van Leer (harmonic-mean) limiter on a uniform grid
+ * (Sec. 3.2.1): delta = 2 dl dr / (dl + dr) if dl dr > 0, else 0. */
+template <class T>
+static T vanleer_slope(T qm, T q0, T qp) {
+  const T dl = q0 - qm;
+  const T dr = qp - q0;
+  const T prod = dl * dr;
+  if (prod > 0.0) return (2.0 * dl * dr) / (dl + dr);
+  return T(0.0);
+}
+
+/* Upwind constrained-transport corner EMF (Gardiner & Stone 2005), for an edge whose two
+ * transverse directions are "a" (first) and "b" (second), e.g. E_z at (i-1/2, j-1/2) with a = x,
+ * b = y.  The corner value is the mean of the four face values plus one quarter of each of the two
+ * upwinded second-difference corrections, obtained by integrating from each face centre to the
+ * corner with the gradient taken in the upwind cell (sign of the face mass flux; mean of both cells
+ * when the mass flux is exactly zero).
+ *   ea[0], ea[1]: a-face EMFs at b-index j-1, j         (x-faces (i-1/2, j-1), (i-1/2, j))
+ *   eb[0], eb[1]: b-face EMFs at a-index i-1, i         (y-faces (i-1, j-1/2), (i, j-1/2))
+ *   ec[0..3]: cell-centre EMFs at (i-1,j-1), (i,j-1), (i-1,j), (i,j)
+ *   ma[0], ma[1]: a-face mass fluxes at j-1, j;  mb[0], mb[1]: b-face mass fluxes at i-1, i. */
+template <class T>
+static T ct_corner(const T ea[2], const T eb[2], const T ec[4], const T ma[2], const T mb[2]) {
+  const T sum4 = (ea[0] + ea[1]) + (eb[0] + eb[1]);
+  /* gradient along b between the corner and the a-face below it, in the cell chosen by ma[0] */
+  const T dlo_m = eb[0] - ec[0];  // cell i-1
+  const T dlo_p = eb[1] - ec[1];  // cell i
+  T tlo;
+  if (ma[0] > 0.0)
+    tlo = dlo_m;
+  else if (ma[0] < 0.0)
+    tlo = dlo_p;
+  else
+    tlo = 0.5 * (dlo_m + dlo_p);
+  const T dhi_m = ec[2] - eb[0];
+  const T dhi_p = ec[3] - eb[1];
+  T thi;
+  if (ma[1] > 0.0)
+    thi = dhi_m;
+  else if (ma[1] < 0.0)
+    thi = dhi_p;
+  else
+    thi = 0.5 * (dhi_m + dhi_p);
+  /* gradient along a between the corner and the b-face, in the cell chosen by the b-face mass flux */
+  const T slo_m = ea[0] - ec[0];  // row j-1
+  const T slo_p = ea[1] - ec[2];  // row j
+  T slo;
+  if (mb[0] > 0.0)
+    slo = slo_m;
+  else if (mb[0] < 0.0)
+    slo = slo_p;
+  else
+    slo = 0.5 * (slo_m + slo_p);
+  const T shi_m = ec[1] - ea[0];
+  const T shi_p = ec[3] - ea[1];
+  T shi;
+  if (mb[1] > 0.0)
+    shi = shi_m;
+  else if (mb[1] < 0.0)
+    shi = shi_p;
+  else
+    shi = 0.5 * (shi_m + shi_p);
+  return (0.25 * sum4 + 0.25 * (tlo - thi)) + 0.25 * (slo - shi);
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Mesh of equal-size MeshBlocks (Sec. 2.1)
+ * ------------------------------------------------------------------------------------------- */
+
+struct Params {
+  int nx[3];  // global active cells
+  int mb[3];  // MeshBlock active cells
+  double xmin[3], xmax[3];
+  double gamma;
+  int riemann;
+  int bc[6];  // x-, x+, y-, y+, z-, z+
+  double dfloor, pfloor;
+  int integrator;
+};
+
+/* dense 3D array (k, j, i), i fastest */
+template <class T> struct Arr3 {
+  int n0 = 0, n1 = 0, n2 = 0;  // sizes in i, j, k
+  std::vector<T> v;
+  void init(int ni, int nj, int nk) {
+    n0 = ni;
+    n1 = nj;
+    n2 = nk;
+    v.assign((size_t)ni * nj * nk, T(0.0));
+  }
+  T& operator()(int k, int j, int i) { return v[((size_t)k * n1 + j) * n0 + i]; }
+  const T& operator()(int k, int j, int i) const { return v[((size_t)k * n1 + j) * n0 + i]; }
+};
+
+static const int NG = 2;  // ghost layers for second order MHD (Sec. 2.1.1)
+
+template <class T> struct Block {
+  int loc[3];
+  Arr3<T> u[2][5];  // two registers of the cell-centred conserved variables (eq. rk-2s)
+  Arr3<T> b[2][3];  // two registers of the face-centred field: b[.][0] on x-faces, ...
+  Arr3<T> w[8];     // rho, vx, vy, vz, p, bcx, bcy, bcz
+  Arr3<T> flx[3][NW7];  // fluxes on faces of direction d (component layout of the sweep)
+  Arr3<T> emf[3];   // E1 on (j-1/2,k-1/2), E2 on (k-1/2,i-1/2), E3 on (i-1/2,j-1/2)
+};
+
+template <class T> struct Mesh {
+  Params P;
+  int n[3];      // block active cells
+  int nb[3];     // blocks per dim
+  int c[3];      // cells with ghosts per dim
+  double dx[3];
+  std::vector<Block<T>> blk;
+  long floor_events = 0;
+  long emf_mismatch = 0;
+
+  int bid(int bx, int by, int bz) const { return (bz * nb[1] + by) * nb[0] + bx; }
+
+  void init(const Params& p) {
+    P = p;
+    for (int d = 0; d < 3; ++d) {
+      n[d] = p.mb[d];
+      nb[d] = p.nx[d] / p.mb[d];
+      c[d] = n[d] + 2 * NG;
+      dx[d] = (p.xmax[d] - p.xmin[d]) / p.nx[d];
+    }
+    blk.resize((size_t)nb[0] * nb[1] * nb[2]);
+    for (int bz = 0; bz < nb[2]; ++bz)
+      for (int by = 0; by < nb[1]; ++by)
+        for (int bx = 0; bx < nb[0]; ++bx) {
+          Block<T>& B = blk[bid(bx, by, bz)];
+          B.loc[0] = bx;
+          B.loc[1] = by;
+          B.loc[2] = bz;
+          for (int r = 0; r < 2; ++r) {
+            for (int v = 0; v < 5; ++v) B.u[r][v].init(c[0], c[1], c[2]);
+            B.b[r][0].init(c[0] + 1, c[1], c[2]);
+            B.b[r][1].init(c[0], c[1] + 1, c[2]);
+            B.b[r][2].init(c[0], c[1], c[2] + 1);
+          }
+          for (int v = 0; v < 8; ++v) B.w[v].init(c[0], c[1], c[2]);
+          for (int v = 0; v < NW7; ++v) {
+            B.flx[0][v].init(c[0] + 1, c[1], c[2]);
+            B.flx[1][v].init(c[0], c[1] + 1, c[2]);
+            B.flx[2][v].init(c[0], c[1], c[2] + 1);
+          }
+          B.emf[0].init(c[0], c[1] + 1, c[2] + 1);
+          B.emf[1].init(c[0] + 1, c[1], c[2] + 1);
+          B.emf[2].init(c[0] + 1, c[1] + 1, c[2]);
+        }
+  }
+
+  /* Map a global index along dimension d that may lie outside [0, N) onto the cell (or face, when
+   * `face` is set: valid range [0, N]) whose data fills it (Sec. 2.1.1): periodic wrap, or outflow =
+   * nearest active cell / the boundary face. */
+  int map_index(int d, int g, bool face) const {
+    const int N = P.nx[d];
+    if (g >= 0 && g < N) return g;
+    if (face && g == N) return N;  // upper boundary face is an active face of the last block
+    const bool lo = g < 0;
+    const int bc = P.bc[2 * d + (lo ? 0 : 1)];
+    if (bc == BC_PERIODIC) {
+      int r = g % N;
+      if (r < 0) r += N;
+      return r;
+    }
+    if (face) return lo ? 0 : N;
+    return lo ? 0 : N - 1;
+  }
+
+  /* Block and local index holding global cell (or face) index g along dimension d.  A face on the
+   * boundary between two blocks is read from the block where it is the lower face; face N from the
+   * last block's upper face. */
+  void owner(int d, int g, bool face, int& b, int& l) const {
+    if (face && g == P.nx[d]) {
+      b = nb[d] - 1;
+      l = n[d] + NG;
+      return;
+    }
+    b = g / n[d];
+    l = g - b * n[d] + NG;
+  }
+
+  /* Ghost exchange for one register (Sec. 2.1.1): cell-centred U and face-centred B, depth N_G,
+   * 26 neighbours.  Faces on a block's own surface are active and are not overwritten. */
+  void fill_ghosts(int r) {
+#pragma omp parallel for schedule(static)
+    for (size_t ib = 0; ib < blk.size(); ++ib) {
+      Block<T>& B = blk[ib];
+      for (int k = 0; k < c[2]; ++k)
+        for (int j = 0; j < c[1]; ++j)
+          for (int i = 0; i < c[0]; ++i) {
+            const int li[3] = {i, j, k};
+            bool ghost = false;
+            for (int d = 0; d < 3; ++d)
+              if (li[d] < NG || li[d] >= n[d] + NG) ghost = true;
+            if (!ghost) continue;
+            int sb[3], sl[3];
+            for (int d = 0; d < 3; ++d) {
+              const int g = map_index(d, B.loc[d] * n[d] + li[d] - NG, false);
+              owner(d, g, false, sb[d], sl[d]);
+            }
+            const Block<T>& S = blk[bid(sb[0], sb[1], sb[2])];
+            for (int v = 0; v < 5; ++v) B.u[r][v](k, j, i) = S.u[r][v](sl[2], sl[1], sl[0]);
+          }
+      for (int fd = 0; fd < 3; ++fd) {
+        Arr3<T>& A = B.b[r][fd];
+        for (int k = 0; k < A.n2; ++k)
+          for (int j = 0; j < A.n1; ++j)
+            for (int i = 0; i < A.n0; ++i) {
+              const int li[3] = {i, j, k};
+              bool ghost = false;
+              for (int d = 0; d < 3; ++d) {
+                const int hi = (d == fd) ? n[d] + NG : n[d] + NG - 1;
+                if (li[d] < NG || li[d] > hi) ghost = true;
+              }
+              if (!ghost) continue;
+              int sb[3], sl[3];
+              for (int d = 0; d < 3; ++d) {
+                const bool face = (d == fd);
+                const int g = map_index(d, B.loc[d] * n[d] + li[d] - NG, face);
+                owner(d, g, face, sb[d], sl[d]);
+              }
+              A(k, j, i) = blk[bid(sb[0], sb[1], sb[2])].b[r][fd](sl[2], sl[1], sl[0]);
+            }
+      }
+    }
+  }
+
+  /* cons -> prim for every cell of every block, ghosts included (Sec. 3.1):
+   * b_c = mean of the two face values [reading: uniform-grid face average], v = M / rho,
+   * p = (gamma-1)(E - |M|^2/(2 rho) - |b_c|^2/2).  [reading] Floors: rho < dfloor -> dfloor and
+   * p < pfloor -> pfloor; an active cell whose floor fires has U rewritten to match, and the
+   * event is counted. */
+  void cons_to_prim(int r) {
+    const double gm1 = P.gamma - 1.0;
+    long fired_total = 0;
+#pragma omp parallel for schedule(static) reduction(+ : fired_total)
+    for (size_t ib = 0; ib < blk.size(); ++ib) {
+      Block<T>& B = blk[ib];
+      for (int k = 0; k < c[2]; ++k)
+        for (int j = 0; j < c[1]; ++j)
+          for (int i = 0; i < c[0]; ++i) {
+            const T bcx = 0.5 * (B.b[r][0](k, j, i) + B.b[r][0](k, j, i + 1));
+            const T bcy = 0.5 * (B.b[r][1](k, j, i) + B.b[r][1](k, j + 1, i));
+            const T bcz = 0.5 * (B.b[r][2](k, j, i) + B.b[r][2](k + 1, j, i));
+            T d = B.u[r][0](k, j, i);
+            const T m1 = B.u[r][1](k, j, i), m2 = B.u[r][2](k, j, i), m3 = B.u[r][3](k, j, i);
+            T e = B.u[r][4](k, j, i);
+            const bool active = i >= NG && i < n[0] + NG && j >= NG && j < n[1] + NG && k >= NG &&
+                                k < n[2] + NG;
+            bool fired = false;
+            if (d < P.dfloor) {
+              d = T(P.dfloor);
+              fired = true;
+            }
+            const T vx = m1 / d, vy = m2 / d, vz = m3 / d;
+            const T ke = 0.5 * ((m1 * m1 + m2 * m2) + m3 * m3) / d;
+            const T me = 0.5 * ((bcx * bcx + bcy * bcy) + bcz * bcz);
+            T p = gm1 * (e - ke - me);
+            if (p < P.pfloor) {
+              p = T(P.pfloor);
+              e = p / gm1 + ke + me;
+              fired = true;
+            }
+            if (fired && active) {
+              ++fired_total;
+              B.u[r][0](k, j, i) = d;
+              B.u[r][4](k, j, i) = e;
+            }
+            B.w[0](k, j, i) = d;
+            B.w[1](k, j, i) = vx;
+            B.w[2](k, j, i) = vy;
+            B.w[3](k, j, i) = vz;
+            B.w[4](k, j, i) = p;
+            B.w[5](k, j, i) = bcx;
+            B.w[6](k, j, i) = bcy;
+            B.w[7](k, j, i) = bcz;
+          }
+    }
+    floor_events += fired_total;
+  }
+
+  /* 7-component interface state of cell (k,j,i) for a sweep in direction d: (rho, v_n, v_t1, v_t2,
+   * p, b_t1, b_t2) with (n, t1, t2) = (d, d+1, d+2) mod 3. */
+  void cell_state(const Block<T>& B, int d, int k, int j, int i, T q[NW7]) const {
+    const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    q[IDN] = B.w[0](k, j, i);
+    q[IVN] = B.w[1 + d](k, j, i);
+    q[IVT1] = B.w[1 + t1](k, j, i);
+    q[IVT2] = B.w[1 + t2](k, j, i);
+    q[IPR] = B.w[4](k, j, i);
+    q[IBT1] = B.w[5 + t1](k, j, i);
+    q[IBT2] = B.w[5 + t2](k, j, i);
+  }
+
+  /* Fluxes on every face a block needs: faces of direction d from the block's lower to its upper
+   * surface, over the active cells plus one ghost layer in the two transverse directions (these
+   * feed the corner EMFs on the block surface).  Donor cell: W_L = W_{i-1}, W_R = W_i; PLM: face
+   * values of the van Leer limited linear profiles (Sec. 3.2.1). */
+  void compute_fluxes(Block<T>& B, int recon) {
+    for (int d = 0; d < 3; ++d) {
+      int lo[3], hi[3];
+      for (int e = 0; e < 3; ++e) {
+        lo[e] = (e == d) ? NG : NG - 1;
+        hi[e] = (e == d) ? n[e] + NG : n[e] + NG;  // inclusive
+      }
+      const int sh[3] = {d == 0, d == 1, d == 2};
+      for (int k = lo[2]; k <= hi[2]; ++k)
+        for (int j = lo[1]; j <= hi[1]; ++j)
+          for (int i = lo[0]; i <= hi[0]; ++i) {
+            T qm2[NW7], qm1[NW7], q0[NW7], qp1[NW7];
+            cell_state(B, d, k - sh[2], j - sh[1], i - sh[0], qm1);
+            cell_state(B, d, k, j, i, q0);
+            T wl[NW7], wr[NW7];
+            if (recon == REC_DC) {
+              for (int v = 0; v < NW7; ++v) {
+                wl[v] = qm1[v];
+                wr[v] = q0[v];
+              }
+            } else {
+              cell_state(B, d, k - 2 * sh[2], j - 2 * sh[1], i - 2 * sh[0], qm2);
+              cell_state(B, d, k + sh[2], j + sh[1], i + sh[0], qp1);
+              for (int v = 0; v < NW7; ++v) {
+                const T dlm = vanleer_slope(qm2[v], qm1[v], q0[v]);
+                const T dl0 = vanleer_slope(qm1[v], q0[v], qp1[v]);
+                wl[v] = qm1[v] + 0.5 * dlm;
+                wr[v] = q0[v] - 0.5 * dl0;
+              }
+            }
+            T f[NW7];
+            riemann(P.riemann, wl, wr, B.b[0][d](k, j, i), P.gamma, f);
+            for (int v = 0; v < NW7; ++v) B.flx[d][v](k, j, i) = f[v];
+          }
+    }
+  }
+
+  /* cell-centre EMF component e (0: E1, 1: E2, 2: E3) from E = -v x b_c */
+  T cell_emf(const Block<T>& B, int e, int k, int j, int i) const {
+    const T vx = B.w[1](k, j, i), vy = B.w[2](k, j, i), vz = B.w[3](k, j, i);
+    const T bx = B.w[5](k, j, i), by = B.w[6](k, j, i), bz = B.w[7](k, j, i);
+    if (e == 0) return vz * by - vy * bz;
+    if (e == 1) return vx * bz - vz * bx;
+    return vy * bx - vx * by;
+  }
+
+  /* Corner EMFs on every edge of the block's active region (Sec. 2.1.1 / upwind CT).  Edge
+   * direction e, first transverse direction a = e+1, second b = e+2.  The face EMF of the same
+   * component is -F_a[b_t1] on a-faces and +F_b[b_t2] on b-faces (E = -v x B). */
+  void compute_emfs(Block<T>& B) {
+    for (int e = 0; e < 3; ++e) {
+      const int a = (e + 1) % 3, b = (e + 2) % 3;
+      int lo[3], hi[3];
+      for (int q = 0; q < 3; ++q) {
+        lo[q] = NG;
+        hi[q] = (q == e) ? n[q] + NG - 1 : n[q] + NG;
+      }
+      int sa[3] = {0, 0, 0}, sb[3] = {0, 0, 0};
+      sa[a] = 1;
+      sb[b] = 1;
+      for (int k = lo[2]; k <= hi[2]; ++k)
+        for (int j = lo[1]; j <= hi[1]; ++j)
+          for (int i = lo[0]; i <= hi[0]; ++i) {
+            /* edge at (a-1/2, b-1/2) of cell (k,j,i) */
+            const int km_b = k - sb[2], jm_b = j - sb[1], im_b = i - sb[0];  // one step down in b
+            const int km_a = k - sa[2], jm_a = j - sa[1], im_a = i - sa[0];  // one step down in a
+            const int kmm = k - sa[2] - sb[2], jmm = j - sa[1] - sb[1], imm = i - sa[0] - sb[0];
+            T ea[2], eb[2], ec[4], ma[2], mb[2];
+            ea[0] = -B.flx[a][IBT1](km_b, jm_b, im_b);
+            ea[1] = -B.flx[a][IBT1](k, j, i);
+            eb[0] = B.flx[b][IBT2](km_a, jm_a, im_a);
+            eb[1] = B.flx[b][IBT2](k, j, i);
+            ma[0] = B.flx[a][IDN](km_b, jm_b, im_b);
+            ma[1] = B.flx[a][IDN](k, j, i);
+            mb[0] = B.flx[b][IDN](km_a, jm_a, im_a);
+            mb[1] = B.flx[b][IDN](k, j, i);
+            ec[0] = cell_emf(B, e, kmm, jmm, imm);    // (a-1, b-1)
+            ec[1] = cell_emf(B, e, km_b, jm_b, im_b); // (a,   b-1)
+            ec[2] = cell_emf(B, e, km_a, jm_a, im_a); // (a-1, b)
+            ec[3] = cell_emf(B, e, k, j, i);          // (a,   b)
+            B.emf[e](k, j, i) = ct_corner(ea, eb, ec, ma, mb);
+          }
+    }
+  }
+
+  /* Fluxes then corner EMFs of every block; blocks are independent (each owns its arrays). */
+  void all_fluxes_and_emfs(int recon) {
+#pragma omp parallel for schedule(static)
+    for (size_t ib = 0; ib < blk.size(); ++ib) {
+      compute_fluxes(blk[ib], recon);
+      compute_emfs(blk[ib]);
+    }
+  }
+
+  /* Shared-edge EMF averaging (Sec. 2.1.1): every edge held by more than one MeshBlock (or twice by
+   * one block through periodic wrap) gets the mean of all its copies, formed as
+   * first + sum(copy - first) / count so that equal copies average to themselves exactly.  Copies
+   * that differ from the first are counted. */
+  void average_shared_emfs() {
+    for (int e = 0; e < 3; ++e) {
+      int gdim[3];
+      for (int q = 0; q < 3; ++q) gdim[q] = (q == e) ? P.nx[q] : P.nx[q] + 1;
+      const size_t ng = (size_t)gdim[0] * gdim[1] * gdim[2];
+      std::vector<T> ref(ng, T(0.0)), acc(ng, T(0.0));
+      std::vector<int> cnt(ng, 0);
+      for (int pass = 0; pass < 2; ++pass)
+        for (auto& B : blk) {
+          Arr3<T>& A = B.emf[e];
+          for (int k = NG; k <= ((e == 2) ? n[2] + NG - 1 : n[2] + NG); ++k)
+            for (int j = NG; j <= ((e == 1) ? n[1] + NG - 1 : n[1] + NG); ++j)
+              for (int i = NG; i <= ((e == 0) ? n[0] + NG - 1 : n[0] + NG); ++i) {
+                const int li[3] = {i, j, k};
+                int g[3];
+                for (int q = 0; q < 3; ++q) {
+                  g[q] = B.loc[q] * n[q] + li[q] - NG;
+                  if (q != e && g[q] == P.nx[q] && P.bc[2 * q + 1] == BC_PERIODIC) g[q] = 0;
+                }
+                const size_t gi = ((size_t)g[2] * gdim[1] + g[1]) * gdim[0] + g[0];
+                if (pass == 0) {
+                  if (cnt[gi] == 0) {
+                    ref[gi] = A(k, j, i);
+                  } else {
+                    if (!(A(k, j, i) == ref[gi])) ++emf_mismatch;
+                    acc[gi] = acc[gi] + (A(k, j, i) - ref[gi]);
+                  }
+                  ++cnt[gi];
+                } else if (cnt[gi] > 1) {
+                  A(k, j, i) = ref[gi] + acc[gi] / (double)cnt[gi];
+                }
+              }
+        }
+    }
+  }
+
+  /* 2S register update of one stage (eq. rk-2s):
+   *   u1 <- u1 + delta_s u0 ;  u0 <- g0 u0 + g1 u1 + beta dt L(u0)
+   * with L = -div F for the cell-centred variables and L = -curl E for the face field. */
+  void register_update(double delta, double g0, double g1, double beta, double dt) {
+#pragma omp parallel for schedule(static)
+    for (size_t ib = 0; ib < blk.size(); ++ib) {
+      Block<T>& B = blk[ib];
+      for (int v = 0; v < 5; ++v)
+        for (int k = NG; k < n[2] + NG; ++k)
+          for (int j = NG; j < n[1] + NG; ++j)
+            for (int i = NG; i < n[0] + NG; ++i) B.u[1][v](k, j, i) = B.u[1][v](k, j, i) + delta * B.u[0][v](k, j, i);
+      for (int fd = 0; fd < 3; ++fd) {
+        Arr3<T>& A1 = B.b[1][fd];
+        Arr3<T>& A0 = B.b[0][fd];
+        for (int k = NG; k <= n[2] + NG - (fd == 2 ? 0 : 1); ++k)
+          for (int j = NG; j <= n[1] + NG - (fd == 1 ? 0 : 1); ++j)
+            for (int i = NG; i <= n[0] + NG - (fd == 0 ? 0 : 1); ++i) A1(k, j, i) = A1(k, j, i) + delta * A0(k, j, i);
+      }
+      const double h = beta * dt;
+      /* cell-centred: conserved variable v <- flux component (rho, M_n..., E) */
+      for (int k = NG; k < n[2] + NG; ++k)
+        for (int j = NG; j < n[1] + NG; ++j)
+          for (int i = NG; i < n[0] + NG; ++i)
+            for (int v = 0; v < 5; ++v) {
+              T dfl[3];
+              for (int d = 0; d < 3; ++d) {
+                /* flux component carrying conserved variable v in a sweep along d */
+                int comp;
+                if (v == 0)
+                  comp = IDN;
+                else if (v == 4)
+                  comp = IPR;
+                else {
+                  const int mdir = v - 1;  // momentum component x/y/z
+                  if (mdir == d)
+                    comp = IVN;
+                  else if (mdir == (d + 1) % 3)
+                    comp = IVT1;
+                  else
+                    comp = IVT2;
+                }
+                const int ip = i + (d == 0), jp = j + (d == 1), kp = k + (d == 2);
+                dfl[d] = (B.flx[d][comp](kp, jp, ip) - B.flx[d][comp](k, j, i)) / dx[d];
+              }
+              const T L = -((dfl[0] + dfl[1]) + dfl[2]);
+              B.u[0][v](k, j, i) = (g0 * B.u[0][v](k, j, i) + g1 * B.u[1][v](k, j, i)) + h * L;
+            }
+      /* face field: B1 on x-faces uses E3 (along y) and E2 (along z), cyclically */
+      for (int fd = 0; fd < 3; ++fd) {
+        const int a = (fd + 1) % 3, b = (fd + 2) % 3;  // B_fd: -[(dE_b/d a) - (dE_a/d b)]
+        Arr3<T>& A0 = B.b[0][fd];
+        Arr3<T>& A1 = B.b[1][fd];
+        for (int k = NG; k <= n[2] + NG - (fd == 2 ? 0 : 1); ++k)
+          for (int j = NG; j <= n[1] + NG - (fd == 1 ? 0 : 1); ++j)
+            for (int i = NG; i <= n[0] + NG - (fd == 0 ? 0 : 1); ++i) {
+              const int ia = i + (a == 0), ja = j + (a == 1), ka = k + (a == 2);
+              const int ib = i + (b == 0), jb = j + (b == 1), kb = k + (b == 2);
+              const T curl = (B.emf[b](ka, ja, ia) - B.emf[b](k, j, i)) / dx[a] -
+                             (B.emf[a](kb, jb, ib) - B.emf[a](k, j, i)) / dx[b];
+              const T L = -curl;
+              A0(k, j, i) = (g0 * A0(k, j, i) + g1 * A1(k, j, i)) + h * L;
+            }
+      }
+    }
+  }
+
+  /* One cycle of a 2S integrator (eq. rk-2s, Sec. 3.2.3).  VL2: gamma_0 = {0,1}, beta_0 = 1/2 with
+   * donor-cell fluxes in the predictor; gamma_1 = {0,1}, beta_1 = 1 with PLM fluxes. */
+  void step(double dt) {
+    struct Stage { double delta, g0, g1, beta; int recon; };
+    std::vector<Stage> st;
+    switch (P.integrator) {
+      case INT_RK1: st = {{1.0, 0.0, 1.0, 1.0, REC_DC}}; break;
+      case INT_RK2: st = {{1.0, 0.0, 1.0, 1.0, REC_PLM}, {0.0, 0.5, 0.5, 0.5, REC_PLM}}; break;
+      case INT_RK3:
+        st = {{1.0, 0.0, 1.0, 1.0, REC_PLM}, {0.0, 0.25, 0.75, 0.25, REC_PLM}, {0.0, 2.0 / 3.0, 1.0 / 3.0, 2.0 / 3.0, REC_PLM}};
+        break;
+      default: st = {{1.0, 0.0, 1.0, 0.5, REC_DC}, {0.0, 0.0, 1.0, 1.0, REC_PLM}}; break;
+    }
+    /* u1 <- 0 at the start of every cycle */
+    for (auto& B : blk) {
+      for (int v = 0; v < 5; ++v) std::fill(B.u[1][v].v.begin(), B.u[1][v].v.end(), T(0.0));
+      for (int fd = 0; fd < 3; ++fd) std::fill(B.b[1][fd].v.begin(), B.b[1][fd].v.end(), T(0.0));
+    }
+    for (const Stage& s : st) {
+      cons_to_prim(0);
+      all_fluxes_and_emfs(s.recon);
+      average_shared_emfs();
+      register_update(s.delta, s.g0, s.g1, s.beta, dt);
+      fill_ghosts(0);
+    }
+  }
+
+  /* Fluxes and EMFs of the current state for one reconstruction, without updating (debug view). */
+  void stage_terms(int recon) {
+    cons_to_prim(0);
+    all_fluxes_and_emfs(recon);
+    average_shared_emfs();
+  }
+
+  /* Time step (Sec. 2.1.7, Sec. 3.2.3): dt = C0 min over active cells and directions of
+   * dx_d / (|v_d| + C_f,d).  [reading] per-direction fast speed with b_c,d as the normal field. */
+  double new_dt(double cfl) {
+    cons_to_prim(0);
+    double best = 1e300;
+    for (auto& B : blk)
+      for (int k = NG; k < n[2] + NG; ++k)
+        for (int j = NG; j < n[1] + NG; ++j)
+          for (int i = NG; i < n[0] + NG; ++i)
+            for (int d = 0; d < 3; ++d) {
+              const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+              const T cf = fast_speed(B.w[0](k, j, i), B.w[4](k, j, i), B.w[5 + d](k, j, i), B.w[5 + t1](k, j, i),
+                                      B.w[5 + t2](k, j, i), P.gamma);
+              const T dtd = dx[d] / (fabs(B.w[1 + d](k, j, i)) + cf);
+              const double v = value_of(dtd);
+              if (v < best) best = v;
+            }
+    return cfl * best;
+  }
+
+  static double value_of(double x) { return x; }
+};
+
+/* ---------------------------------------------------------------------------------------------
+ * Global-array I/O (active region, [var][k][j][i])
+ * ------------------------------------------------------------------------------------------- */
+
+template <class T>
+static void set_prims(Mesh<T>& M, const double* w, const double* b1, const double* b2, const double* b3) {
+  const int NX = M.P.nx[0], NY = M.P.nx[1], NZ = M.P.nx[2];
+  const size_t ncell = (size_t)NX * NY * NZ;
+  for (auto& B : M.blk) {
+    const int o[3] = {B.loc[0] * M.n[0], B.loc[1] * M.n[1], B.loc[2] * M.n[2]};
+    for (int k = 0; k <= M.n[2]; ++k)
+      for (int j = 0; j <= M.n[1]; ++j)
+        for (int i = 0; i <= M.n[0]; ++i) {
+          const int gi = o[0] + i, gj = o[1] + j, gk = o[2] + k;
+          if (j < M.n[1] && k < M.n[2])
+            B.b[0][0](k + NG, j + NG, i + NG) = b1[((size_t)gk * NY + gj) * (NX + 1) + gi];
+          if (i < M.n[0] && k < M.n[2])
+            B.b[0][1](k + NG, j + NG, i + NG) = b2[((size_t)gk * (NY + 1) + gj) * NX + gi];
+          if (i < M.n[0] && j < M.n[1])
+            B.b[0][2](k + NG, j + NG, i + NG) = b3[((size_t)gk * NY + gj) * NX + gi];
+        }
+  }
+  const double gm1 = M.P.gamma - 1.0;
+  for (auto& B : M.blk) {
+    const int o[3] = {B.loc[0] * M.n[0], B.loc[1] * M.n[1], B.loc[2] * M.n[2]};
+    for (int k = 0; k < M.n[2]; ++k)
+      for (int j = 0; j < M.n[1]; ++j)
+        for (int i = 0; i < M.n[0]; ++i) {
+          const size_t g = ((size_t)(o[2] + k) * NY + (o[1] + j)) * NX + (o[0] + i);
+          const T d = w[0 * ncell + g], vx = w[1 * ncell + g], vy = w[2 * ncell + g], vz = w[3 * ncell + g];
+          const T p = w[4 * ncell + g];
+          const int K = k + NG, J = j + NG, I = i + NG;
+          const T bcx = 0.5 * (B.b[0][0](K, J, I) + B.b[0][0](K, J, I + 1));
+          const T bcy = 0.5 * (B.b[0][1](K, J, I) + B.b[0][1](K, J + 1, I));
+          const T bcz = 0.5 * (B.b[0][2](K, J, I) + B.b[0][2](K + 1, J, I));
+          B.u[0][0](K, J, I) = d;
+          B.u[0][1](K, J, I) = d * vx;
+          B.u[0][2](K, J, I) = d * vy;
+          B.u[0][3](K, J, I) = d * vz;
+          B.u[0][4](K, J, I) = p / gm1 + 0.5 * d * ((vx * vx + vy * vy) + vz * vz) + 0.5 * ((bcx * bcx + bcy * bcy) + bcz * bcz);
+        }
+  }
+  M.fill_ghosts(0);
+}
+
+template <class T>
+static void get_cons(const Mesh<T>& M, double* u, double* b1, double* b2, double* b3) {
+  const int NX = M.P.nx[0], NY = M.P.nx[1], NZ = M.P.nx[2];
+  const size_t ncell = (size_t)NX * NY * NZ;
+  for (const auto& B : M.blk) {
+    const int o[3] = {B.loc[0] * M.n[0], B.loc[1] * M.n[1], B.loc[2] * M.n[2]};
+    for (int k = 0; k <= M.n[2]; ++k)
+      for (int j = 0; j <= M.n[1]; ++j)
+        for (int i = 0; i <= M.n[0]; ++i) {
+          const int gi = o[0] + i, gj = o[1] + j, gk = o[2] + k;
+          const int K = k + NG, J = j + NG, I = i + NG;
+          const bool own_i = (i < M.n[0]) || (gi == NX);
+          const bool own_j = (j < M.n[1]) || (gj == NY);
+          const bool own_k = (k < M.n[2]) || (gk == NZ);
+          if (u && i < M.n[0] && j < M.n[1] && k < M.n[2]) {
+            const size_t g = ((size_t)gk * NY + gj) * NX + gi;
+            for (int v = 0; v < 5; ++v) u[v * ncell + g] = Mesh<T>::value_of(B.u[0][v](K, J, I));
+          }
+          if (b1 && own_i && j < M.n[1] && k < M.n[2])
+            b1[((size_t)gk * NY + gj) * (NX + 1) + gi] = Mesh<T>::value_of(B.b[0][0](K, J, I));
+          if (b2 && own_j && i < M.n[0] && k < M.n[2])
+            b2[((size_t)gk * (NY + 1) + gj) * NX + gi] = Mesh<T>::value_of(B.b[0][1](K, J, I));
+          if (b3 && own_k && i < M.n[0] && j < M.n[1])
+            b3[((size_t)gk * NY + gj) * NX + gi] = Mesh<T>::value_of(B.b[0][2](K, J, I));
+        }
+  }
+}
+
+}  // namespace orc
+
+/* =============================================================================================
+ * C interface (ctypes)
+ * =========================================================================================== */
+using orc::Mesh;
+
+extern "C" {
+
+void* orc_mesh_new(const int* nx, const int* mb, const double* xmin, const double* xmax, double gamma,
+                   int riemann, const int* bc, double dfloor, double pfloor, int integrator) {
+  orc::Params p;
+  for (int d = 0; d < 3; ++d) {
+    if (nx[d] <= 0 || mb[d] <= 0 || nx[d] % mb[d] != 0) return nullptr;
+    p.nx[d] = nx[d];
+    p.mb[d] = mb[d];
+    p.xmin[d] = xmin[d];
+    p.xmax[d] = xmax[d];
+  }
+  for (int f = 0; f < 6; ++f) p.bc[f] = bc[f];
+  p.gamma = gamma;
+  p.riemann = riemann;
+  p.dfloor = dfloor;
+  p.pfloor = pfloor;
+  p.integrator = integrator;
+  Mesh<double>* M = new Mesh<double>();
+  M->init(p);
+  return M;
+}
+
+void orc_mesh_free(void* m) { delete static_cast<Mesh<double>*>(m); }
+
+void orc_set_prims(void* m, const double* w, const double* b1, const double* b2, const double* b3) {
+  orc::set_prims(*static_cast<Mesh<double>*>(m), w, b1, b2, b3);
+}
+
+void orc_get_cons(void* m, double* u, double* b1, double* b2, double* b3) {
+  orc::get_cons(*static_cast<Mesh<double>*>(m), u, b1, b2, b3);
+}
+
+/* cons -> prim of the current state on the active region: w[8][nz][ny][nx] (rho, v, p, b_c) */
+void orc_get_prims(void* m, double* w) {
+  Mesh<double>& M = *static_cast<Mesh<double>*>(m);
+  M.cons_to_prim(0);
+  const int NX = M.P.nx[0], NY = M.P.nx[1], NZ = M.P.nx[2];
+  const size_t ncell = (size_t)NX * NY * NZ;
+  for (const auto& B : M.blk)
+    for (int k = 0; k < M.n[2]; ++k)
+      for (int j = 0; j < M.n[1]; ++j)
+        for (int i = 0; i < M.n[0]; ++i) {
+          const size_t g = ((size_t)(B.loc[2] * M.n[2] + k) * NY + (B.loc[1] * M.n[1] + j)) * NX + (B.loc[0] * M.n[0] + i);
+          for (int v = 0; v < 8; ++v) w[v * ncell + g] = B.w[v](k + orc::NG, j + orc::NG, i + orc::NG);
+        }
+}
+
+void orc_fill_ghosts(void* m) { static_cast<Mesh<double>*>(m)->fill_ghosts(0); }
+
+void orc_step(void* m, double dt) { static_cast<Mesh<double>*>(m)->step(dt); }
+
+double orc_new_dt(void* m, double cfl) { return static_cast<Mesh<double>*>(m)->new_dt(cfl); }
+
+long orc_floor_count(void* m) { return static_cast<Mesh<double>*>(m)->floor_events; }
+
+long orc_emf_mismatch_count(void* m) { return static_cast<Mesh<double>*>(m)->emf_mismatch; }
+
+/* Fluxes of the current state on the global face grids: fx[7][NZ][NY][NX+1], fy[7][NZ][NY+1][NX],
+ * fz[7][NZ+1][NY][NX]; component layout of each sweep (mass, M_n, M_t1, M_t2, E, B_t1, B_t2). */
+void orc_debug_fluxes(void* m, int recon, double* fx, double* fy, double* fz) {
+  Mesh<double>& M = *static_cast<Mesh<double>*>(m);
+  M.stage_terms(recon);
+  const int N[3] = {M.P.nx[0], M.P.nx[1], M.P.nx[2]};
+  double* out[3] = {fx, fy, fz};
+  for (int d = 0; d < 3; ++d) {
+    int gd[3] = {N[0], N[1], N[2]};
+    gd[d] += 1;
+    const size_t nf = (size_t)gd[0] * gd[1] * gd[2];
+    for (const auto& B : M.blk)
+      for (int k = 0; k < M.n[2] + (d == 2); ++k)
+        for (int j = 0; j < M.n[1] + (d == 1); ++j)
+          for (int i = 0; i < M.n[0] + (d == 0); ++i) {
+            const int g[3] = {B.loc[0] * M.n[0] + i, B.loc[1] * M.n[1] + j, B.loc[2] * M.n[2] + k};
+            const int li[3] = {i, j, k};
+            if (li[d] == M.n[d] && g[d] != N[d]) continue;  // taken from the upper neighbour
+            const size_t gi = ((size_t)g[2] * gd[1] + g[1]) * gd[0] + g[0];
+            for (int v = 0; v < orc::NW7; ++v) out[d][v * nf + gi] = B.flx[d][v](k + orc::NG, j + orc::NG, i + orc::NG);
+          }
+  }
+}
+
+/* Corner EMFs of the current state: e1[NZ+1][NY+1][NX], e2[NZ+1][NY][NX+1], e3[NZ][NY+1][NX+1]. */
+void orc_debug_emfs(void* m, int recon, double* e1, double* e2, double* e3) {
+  Mesh<double>& M = *static_cast<Mesh<double>*>(m);
+  M.stage_terms(recon);
+  const int N[3] = {M.P.nx[0], M.P.nx[1], M.P.nx[2]};
+  double* out[3] = {e1, e2, e3};
+  for (int e = 0; e < 3; ++e) {
+    int gd[3] = {N[0] + 1, N[1] + 1, N[2] + 1};
+    gd[e] -= 1;
+    for (const auto& B : M.blk)
+      for (int k = 0; k < M.n[2] + (e != 2); ++k)
+        for (int j = 0; j < M.n[1] + (e != 1); ++j)
+          for (int i = 0; i < M.n[0] + (e != 0); ++i) {
+            const int g[3] = {B.loc[0] * M.n[0] + i, B.loc[1] * M.n[1] + j, B.loc[2] * M.n[2] + k};
+            const int li[3] = {i, j, k};
+            bool skip = false;
+            for (int q = 0; q < 3; ++q)
+              if (q != e && li[q] == M.n[q] && g[q] != N[q]) skip = true;
+            if (skip) continue;
+            const size_t gi = ((size_t)g[2] * gd[1] + g[1]) * gd[0] + g[0];
+            out[e][gi] = B.emf[e](k + orc::NG, j + orc::NG, i + orc::NG);
+          }
+  }
+}
+
+/* max over active cells of |div_h B| * min(dx) / max(rms |b_c|, 1e-300)  [reading] */
+double orc_divb_norm(void* m) {
+  Mesh<double>& M = *static_cast<Mesh<double>*>(m);
+  double mx = 0.0, s2 = 0.0;
+  size_t cnt = 0;
+  const int G = orc::NG;
+  for (const auto& B : M.blk)
+    for (int k = G; k < M.n[2] + G; ++k)
+      for (int j = G; j < M.n[1] + G; ++j)
+        for (int i = G; i < M.n[0] + G; ++i) {
+          const double dv = (B.b[0][0](k, j, i + 1) - B.b[0][0](k, j, i)) / M.dx[0] +
+                            (B.b[0][1](k, j + 1, i) - B.b[0][1](k, j, i)) / M.dx[1] +
+                            (B.b[0][2](k + 1, j, i) - B.b[0][2](k, j, i)) / M.dx[2];
+          mx = std::fmax(mx, std::fabs(dv));
+          const double bx = 0.5 * (B.b[0][0](k, j, i) + B.b[0][0](k, j, i + 1));
+          const double by = 0.5 * (B.b[0][1](k, j, i) + B.b[0][1](k, j + 1, i));
+          const double bz = 0.5 * (B.b[0][2](k, j, i) + B.b[0][2](k + 1, j, i));
+          s2 += bx * bx + by * by + bz * bz;
+          ++cnt;
+        }
+  const double hmin = std::fmin(M.dx[0], std::fmin(M.dx[1], M.dx[2]));
+  const double rms = std::sqrt(s2 / (double)cnt);
+  return mx * hmin / std::fmax(rms, 1e-300);
+}
+
+/* Volume integrals of rho, M1..3, E, b_c1..3 over the active region, Neumaier-compensated. */
+void orc_totals(void* m, double* out) {
+  Mesh<double>& M = *static_cast<Mesh<double>*>(m);
+  const double dv = M.dx[0] * M.dx[1] * M.dx[2];
+  double s[8] = {0}, cmp[8] = {0};
+  const int G = orc::NG;
+  for (const auto& B : M.blk)
+    for (int k = G; k < M.n[2] + G; ++k)
+      for (int j = G; j < M.n[1] + G; ++j)
+        for (int i = G; i < M.n[0] + G; ++i) {
+          double x[8];
+          for (int v = 0; v < 5; ++v) x[v] = B.u[0][v](k, j, i);
+          x[5] = 0.5 * (B.b[0][0](k, j, i) + B.b[0][0](k, j, i + 1));
+          x[6] = 0.5 * (B.b[0][1](k, j, i) + B.b[0][1](k, j + 1, i));
+          x[7] = 0.5 * (B.b[0][2](k, j, i) + B.b[0][2](k + 1, j, i));
+          for (int v = 0; v < 8; ++v) {
+            const double y = x[v] * dv;
+            const double t = s[v] + y;
+            if (std::fabs(s[v]) >= std::fabs(y))
+              cmp[v] += (s[v] - t) + y;
+            else
+              cmp[v] += (y - t) + s[v];
+            s[v] = t;
+          }
+        }
+  for (int v = 0; v < 8; ++v) out[v] = s[v] + cmp[v];
+}
+
+/* ---- pointwise entry points for the unit pins ---- */
+void orc_riemann(int solver, const double* wl, const double* wr, double bn, double gamma, double* f) {
+  orc::riemann<double>(solver, wl, wr, bn, gamma, f);
+}
+
+void orc_physical_flux(const double* w, double bn, double gamma, double* u, double* f) {
+  orc::physical_flux<double>(w, bn, gamma, u, f);
+}
+
+double orc_fast_speed(double d, double p, double bn, double bt1, double bt2, double gamma) {
+  return orc::fast_speed<double>(d, p, bn, bt1, bt2, gamma);
+}
+
+double orc_vanleer_slope(double qm, double q0, double qp) { return orc::vanleer_slope<double>(qm, q0, qp); }
+
+double orc_ct_corner(const double* ea, const double* eb, const double* ec, const double* ma, const double* mb) {
+  return orc::ct_corner<double>(ea, eb, ec, ma, mb);
+}
+
+}  // extern "C"
