@@ -1,0 +1,337 @@
+#!/usr/bin/env python3
+"""Benchmark of the plain FP64 VL2 + PLM + HLLD + CT step on one GB300 per process.
+
+Workload: 3D Orszag-Tang-style vortex (seeded phases, seed 2005) on a 256^3 periodic grid split into
+512 MeshBlocks of 32^3 with 2 ghost layers; gamma = 5/3, CFL 0.3, VL2 (donor-cell predictor, PLM
+corrector), HLLD fluxes, upwind CT.  One "step" = one VL2 cycle plus the CFL time step of the new
+state (new_dt), all through the C ABI.
+
+Printed JSON line (rank 0):
+  value       zone-cycles/s of the whole job, timed with CUDA events on the mesh's stream over exactly
+              --steps cycles (state already resident; the 1.07 GB state register exceeds the 129 MB
+              L2, so no flush is needed)
+  e2e         the same metric when every step also uploads its input state from pinned host memory
+              (set_prims) and reads the new state back to pinned host memory (get_cons)
+  roofline    the dominant kernel (largest device time in the timed region): achieved FP64 FLOP/s =
+              algorithmic FP64 operations per face (counted with the oracle's operation-counting scalar:
+              add/sub, mul, div, sqrt each one) x faces per launch / event-timed launch duration, against
+              the FP64 peak derived from 152 SMs x 2 FP64 FMA per clock x 2 FLOP x 2.07 GHz
+  hbm         320 algorithmic bytes per zone-cycle (8 doubles read+written in the predictor, a stencil
+              read, a base read and a write of 8 doubles in the corrector) x value / measured HBM copy
+              bandwidth
+  cpu_baseline the CPU oracle timed on this host's cores on a bounded sample (N = 1, rank 0)
+
+--impl reference times the CPU oracle itself on a 64^3 sample of the same workload (8 MeshBlocks of
+32^3): every step is one oracle VL2 cycle of that sample.
+Under torchrun every rank advances its own replica (the method is not sharded: replicas only).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MHD zone-cycles/s at 256^3 (FP64 plain vs mixed/batched), % of HBM roofline"
+UNIT = "zone-cycles/s"
+HBM_BYTES_PER_ZONE_CYCLE = 320.0
+# FP64 operations of one face flux (add/sub + mul + div + sqrt), counted by instantiating the oracle's
+# pointwise reconstruction and Riemann functions with its operation-counting scalar and averaging over
+# 3000 faces of the seed-2005 vortex (oracle/count_flops.py).
+FLOPS_PER_FACE = {("plm", "hlld"): 484.9, ("dc", "hlld"): 394.1, ("plm", "hlle"): 299.8, ("dc", "hlle"): 209.0}
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of
+# the PLM+HLLD x sweep on the 128^3 vortex, 2,441,472 faces), scaled to a launch by its faces; valid only
+# for the kernel source it was taken on (hash of the flux and physics sources), else reported as null.
+NCU_TRAFFIC = {"hash": "d3132fc066f2b334", "bytes_per_face": 135.2}
+
+
+def flux_source_hash():
+    h = hashlib.sha256()
+    for f in ("vl2_flux.cu", "vl2_physics.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2005_06651_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, n = [], None, set(), 0
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            n += 1
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": n}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_rate(n, mb, steps, warmup, seed=2005, min_seconds=0.0, max_steps=None):
+    """Time the CPU oracle on an n^3 sample of the vortex; returns (zone-cycles/s, steps, threads, s)."""
+    from oracle import orc
+    from paper_2005_06651_gb300 import inputs
+
+    prob = inputs.orszag_tang(n=n, mb=mb, seed=seed)
+    m = orc.Mesh.from_problem(prob)
+    for _ in range(warmup):
+        m.step(m.new_dt(0.3))
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        m.step(m.new_dt(0.3))
+        done += 1
+        el = time.perf_counter() - t0
+        if done >= steps and el >= min_seconds:
+            break
+        if max_steps is not None and done >= max_steps:
+            break
+    el = time.perf_counter() - t0
+    threads = orc_threads()
+    return prob.ncells * done / el, done, threads, el
+
+
+def orc_threads():
+    try:
+        import ctypes
+
+        gomp = ctypes.CDLL("libgomp.so.1")
+        gomp.omp_get_max_threads.restype = ctypes.c_int
+        return int(gomp.omp_get_max_threads())
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    n, mb = 64, 32
+    rate, done, threads, el = oracle_rate(n, mb, args.steps, args.warmup)
+    sample = "%d VL2 cycles of a %d^3 sample of the vortex (%d MeshBlocks of %d^3), FP64 CPU oracle" % (
+        done, n, (n // mb) ** 3, mb)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / done, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args),
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    return {"workload": "orszag_tang_3d_%d^3_%dx%d^3_blocks_vl2_plm_hlld_ct_fp64" % (
+        args.n, (args.n // args.mb) ** 3, args.mb), "grid": [args.n] * 3, "meshblock": [args.mb] * 3,
+        "meshblocks": (args.n // args.mb) ** 3, "ghosts": 2, "gamma": 5.0 / 3.0, "cfl": 0.3,
+        "integrator": "vl2", "reconstruction": "plm (donor cell predictor)", "riemann": "hlld", "seed": 2005,
+        "l2": "state (1.07 GB per register at 256^3) exceeds the 129 MB L2; no flush", "parallelism": "replicas"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--mb", type=int, default=32)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2005_06651_gb300 import build, inputs, vl2
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    build.build()
+    vl2.load()
+    prob = inputs.orszag_tang(n=args.n, mb=args.mb, seed=2005)
+    stream = torch.cuda.current_stream(dev)
+    mesh = vl2.Mesh.from_problem(prob, device=dev, stream=stream)
+    for _ in range(args.warmup):
+        mesh.step(mesh.new_dt())
+    torch.cuda.synchronize(dev)
+
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = ("GPU-" + str(props.uuid)) if getattr(props, "uuid", None) else str(local)
+    sampler = ClockSampler(gpu_id)
+    mesh.profile(True)
+    mesh.profile_read()
+    launches0 = mesh.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.3)
+    e0.record(stream)
+    for _ in range(args.steps):
+        mesh.step(mesh.new_dt())
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    if pg:
+        pg.barrier()
+    ms_total = e0.elapsed_time(e1)
+    launches = mesh.launch_count() - launches0
+    prof = mesh.profile_read()
+    mesh.profile(False)
+    if pg:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * prob.ncells * args.steps / (ms_total / 1e3)
+
+    # roofline of the dominant kernel
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    tot = sum(v[0] for v in kinds.values())
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dms, dn, dunits = kinds[dom]
+    rec = {"flux_plm": "plm", "flux_dc": "dc"}.get(dom)
+    roofline = {"kernel": dom, "bound": "alu", "unit": "TFLOP/s", "peak": round(FP64_PEAK_TFLOPS, 4),
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz",
+                "launches": dn, "ms_per_launch": dms / dn, "units_per_launch": dunits / dn}
+    if rec:
+        fpu = FLOPS_PER_FACE[(rec, "hlld")]
+        achieved = fpu * (dunits / dn) / (dms / dn / 1e3) / 1e12
+        roofline.update({"achieved": achieved, "frac": achieved / FP64_PEAK_TFLOPS,
+                         "flops_per_unit": fpu, "unit_kind": "face"})
+        if NCU_TRAFFIC["hash"] == flux_source_hash() and NCU_TRAFFIC["bytes_per_face"]:
+            roofline["traffic"] = NCU_TRAFFIC["bytes_per_face"] * dunits / dn
+        else:
+            roofline["traffic"] = None
+    else:
+        roofline.update({"achieved": None, "frac": None, "traffic": None})
+    kernel_share = {k: {"ms_per_step": v[0] / args.steps, "share": v[0] / tot, "launches_per_step": v[1] / args.steps}
+                    for k, v in kinds.items()}
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm = {"bytes_per_zone_cycle": HBM_BYTES_PER_ZONE_CYCLE,
+           "achieved_GBps": HBM_BYTES_PER_ZONE_CYCLE * value / world / 1e9, "peak_GBps": hbm_peak,
+           "frac": HBM_BYTES_PER_ZONE_CYCLE * value / world / 1e9 / hbm_peak,
+           "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+    # end to end through the C ABI with pinned host buffers
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hw, hb1, hb2, hb3 = (pin(a) for a in (prob.w, prob.b1, prob.b2, prob.b3))
+    outs = (torch.empty((5,) + mesh.shape, dtype=torch.float64).pin_memory(),
+            *[torch.empty(s, dtype=torch.float64).pin_memory() for s in mesh.face_shapes()])
+    h2d = sum(t.numel() * 8 for t in (hw, hb1, hb2, hb3))
+    d2h = sum(t.numel() * 8 for t in outs)
+    ke = max(1, min(args.e2e_steps, args.steps))
+    mesh.set_prims(hw, hb1, hb2, hb3)
+    mesh.step(mesh.new_dt())
+    mesh.get_cons(outs)
+    torch.cuda.synchronize(dev)
+    if pg:
+        pg.barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        mesh.set_prims(hw, hb1, hb2, hb3)
+        mesh.step(mesh.new_dt())
+        mesh.get_cons(outs)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    if pg:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * prob.ncells * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "steps": ke,
+           "path": "set_prims (pinned host) + new_dt + step + get_cons (pinned host) per step"}
+    divb = mesh.divb_norm()
+    floors = mesh.floor_count()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        del mesh
+        torch.cuda.empty_cache()
+        rate, done, threads, el = oracle_rate(args.n, args.mb, 1, 0, min_seconds=10.0, max_steps=3)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "%d VL2 cycle(s) of the full %d^3 workload (%d MeshBlocks), %.1f s" % (
+                   done, args.n, (args.n // args.mb) ** 3, el)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args),
+                "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "hbm": hbm,
+                "kernels": kernel_share, "cpu_baseline": cpu, "divb_norm": divb, "floor_events": floors}
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

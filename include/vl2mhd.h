@@ -1,0 +1,195 @@
+/*
+ * vl2mhd.h -- C ABI of the GB300 (sm_103a) VL2 ideal-MHD stepper.
+ *
+ * The library advances 3D adiabatic ideal MHD (Stone et al. 2020, arXiv:2005.06651, Sec. 3.1,
+ * eq. cons with mu = 1, ideal-gas EOS) on a uniform Cartesian mesh of equal-size MeshBlocks
+ * (Sec. 2.1) held on one GPU, with the VL2 predictor-corrector (Sec. 3.2.3, eq. rk-2s: donor-cell
+ * predictor over dt/2, PLM corrector over dt), PLM reconstruction of primitives with the van Leer
+ * limiter (Sec. 3.2.1), HLLD or HLLE fluxes (Sec. 3.2.2), upwind constrained transport of the
+ * face-centred field (Sec. 3.1, Sec. 2.1.1), ghost exchange between blocks (Sec. 2.1.1) and the
+ * global CFL time step (Sec. 2.1.7).
+ *
+ * Conventions shared by every call
+ *  - Every call returns a vl2_status; 0 (VL2_OK) is success.  Nothing throws across the ABI.
+ *    vl2_last_error() returns a short message for the last failing call on a mesh.
+ *  - All device work of a mesh is issued on the stream given in vl2_params.stream (a cudaStream_t
+ *    passed as void*; NULL selects the legacy default stream).  Calls on one mesh are not
+ *    re-entrant: do not call into the same mesh from two host threads at once.
+ *  - The caller owns the device workspace (vl2_workspace_bytes / vl2_mesh_create) and every buffer
+ *    it passes.  Caller buffers are only read or written during the call; `where` says whether a
+ *    pointer is host memory (VL2_HOST, pinned or pageable) or device memory (VL2_DEVICE).  Calls
+ *    that read back to host memory return after the data has arrived; calls with device buffers
+ *    only enqueue on the mesh's stream.
+ *  - Global arrays cover the active (non-ghost) cells of the whole mesh in C order, x fastest:
+ *      cell arrays  [var][NZ][NY][NX]
+ *      b1 (B_x)     [NZ][NY][NX+1]   face i is the lower x-face of cell i
+ *      b2 (B_y)     [NZ][NY+1][NX]
+ *      b3 (B_z)     [NZ+1][NY][NX]
+ *    In a periodic direction the last face row duplicates the first (face N == face 0).
+ */
+#ifndef VL2MHD_H
+#define VL2MHD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum vl2_status {
+  VL2_OK = 0,
+  VL2_E_ARG = 1,      /* invalid argument (null pointer, bad size, inconsistent parameters) */
+  VL2_E_CUDA = 2,     /* a CUDA runtime call or kernel launch failed */
+  VL2_E_NONPHYS = 3,  /* a density or pressure floor fired (value floored and counted), or dt not finite */
+  VL2_E_TIMEOUT = 4,  /* a bounded device-side wait expired */
+  VL2_E_STATE = 5,    /* call not valid in the mesh's current state */
+  VL2_E_NOMEM = 6     /* workspace smaller than vl2_workspace_bytes() */
+} vl2_status;
+
+enum { VL2_HLLE = 0, VL2_HLLD = 1 };       /* Riemann solver, Sec. 3.2.2 */
+enum { VL2_PERIODIC = 0, VL2_OUTFLOW = 1 };/* per-face boundary condition */
+enum { VL2_FP64 = 0, VL2_MIXED = 1 };      /* arithmetic of reconstruction and fluxes */
+enum { VL2_HOST = 0, VL2_DEVICE = 1 };     /* where a caller buffer lives */
+enum { VL2_DC = 0, VL2_PLM = 1 };          /* reconstruction, Sec. 3.2.1 */
+
+typedef struct vl2_params {
+  int nx[3];          /* global active cells (x, y, z); each a multiple of mb[d] */
+  int mb[3];          /* MeshBlock active cells (x, y, z), Sec. 2.1: equal for every block */
+  int ng;             /* ghost layers; must be 2 for second-order MHD (Sec. 2.1.1) */
+  double xmin[3], xmax[3]; /* domain bounds; cells are uniform, dx_d = (xmax-xmin)/nx */
+  double gamma;       /* adiabatic index of the ideal-gas EOS, P = (gamma-1) e (Sec. 3.1) */
+  double cfl;         /* Courant number C0 of vl2_new_dt; <= 1/2 for VL2 in 3D (Sec. 3.2.3) */
+  int riemann;        /* VL2_HLLD or VL2_HLLE */
+  int precision;      /* VL2_FP64 (only value accepted by this version) */
+  int bc[6];          /* boundary of faces x-, x+, y-, y+, z-, z+: VL2_PERIODIC or VL2_OUTFLOW;
+                         periodic must be set on both faces of a direction */
+  double dfloor, pfloor; /* density / pressure floors of cons->prim (> 0) */
+  void* stream;       /* cudaStream_t for all device work of this mesh (may be NULL) */
+} vl2_params;
+
+typedef struct vl2_mesh vl2_mesh;
+
+/* Block layout of the mesh's device arrays (Sec. 2.1).  Pointers are owned by the mesh and stay valid
+ * until vl2_mesh_destroy.  Block id b has logical position (bx, by, bz) = block_loc[3b..3b+2], x
+ * fastest.  Element (var v, cell k, j, i) of block b in a cell array starts at
+ *   base + (b * nvar + v) * block_stride_vars + (k * sy + j) * sx + i
+ * with local indices including the ng ghost layers (active cells are ng .. ng+mb-1).  Face arrays
+ * use the same strides, with one extra face along their own direction. */
+typedef struct vl2_layout {
+  int nblocks;
+  int nb[3];            /* blocks per direction */
+  int mb[3];            /* active cells per block */
+  int ng;               /* ghost layers */
+  int sx, sy, sz;       /* padded box extents (elements) in x, y, z */
+  long long block_stride_vars; /* sx * sy * sz */
+  const int* block_loc; /* host, [nblocks][3] */
+  const int* neighbor;  /* host, [nblocks][27]: block id of neighbour (di,dj,dk) in {-1,0,1}^3 at
+                           index (dk+1)*9 + (dj+1)*3 + (di+1), or -1 beyond an outflow boundary */
+  double* u;            /* device, conserved variables rho, M1, M2, M3, E (nvar 5) of the current state */
+  double* b[3];         /* device, face fields B1, B2, B3 (nvar 1 each) of the current state */
+} vl2_layout;
+
+/* Bytes of device workspace a mesh with these parameters needs (registers, primitives, fluxes,
+ * EMFs, staging for global-array I/O, reduction scratch).  Errors: VL2_E_ARG for invalid
+ * parameters (same checks as vl2_mesh_create). */
+vl2_status vl2_workspace_bytes(const vl2_params* params, size_t* bytes);
+
+/* Create a mesh of nx/mb MeshBlocks (Sec. 2.1) inside the caller's device workspace (at least
+ * vl2_workspace_bytes(), 256-byte aligned; the caller keeps it alive until vl2_mesh_destroy and
+ * frees it afterwards).  The state is zero until vl2_set_prims.  Errors: VL2_E_ARG (bad parameters,
+ * misaligned workspace), VL2_E_NOMEM (workspace too small), VL2_E_CUDA. */
+vl2_status vl2_mesh_create(const vl2_params* params, void* workspace, size_t bytes, vl2_mesh** out);
+
+/* Release the host-side mesh object (the device workspace stays the caller's).  NULL is accepted. */
+vl2_status vl2_mesh_destroy(vl2_mesh* mesh);
+
+/* Describe the block layout (see vl2_layout).  Errors: VL2_E_ARG. */
+vl2_status vl2_block_layout(const vl2_mesh* mesh, vl2_layout* out);
+
+/* Set the state from primitives: w = [5][NZ][NY][NX] (rho, vx, vy, vz, p) at cell centres and the
+ * face fields b1, b2, b3 (global layout above).  U = (rho, rho v, E) with E = p/(gamma-1) +
+ * rho v^2/2 + |b_c|^2/2, b_c the mean of the two face values (Sec. 3.1, eq. total_energy); ghosts are
+ * then exchanged (Sec. 2.1.1).  Errors: VL2_E_ARG (null pointer, periodic face duplicates that
+ * differ), VL2_E_CUDA. */
+vl2_status vl2_set_prims(vl2_mesh* mesh, const double* w, const double* b1, const double* b2,
+                         const double* b3, int where);
+
+/* Ghost exchange of the current state (Sec. 2.1.1): cell-centred U and face fields copied, depth
+ * ng, from the 26 neighbours (periodic wrap; outflow copies the nearest active cell / boundary face).
+ * Faces on a block's own surface are active and are not overwritten.  Errors: VL2_E_CUDA. */
+vl2_status vl2_fill_ghosts(vl2_mesh* mesh);
+
+/* One VL2 cycle with step dt (Sec. 3.2.3): predictor U* = U^n + (dt/2) L_DC(U^n), corrector
+ * U^{n+1} = U^n + dt L_PLM(U*), where L = -div F for U and -curl E (upwind CT corner EMFs) for the
+ * face field; cons->prim and ghost exchange between the stages and after the corrector.  Ghosts are
+ * valid on return.  dt must be finite and > 0.  Work is only enqueued.  Errors: VL2_E_ARG, VL2_E_CUDA. */
+vl2_status vl2_step(vl2_mesh* mesh, double dt);
+
+/* CFL time step of the current state (Sec. 2.1.7, 3.2.3): dt = cfl * min over active cells and
+ * directions d of dx_d / (|v_d| + C_f,d), C_f,d the fast speed with b_c,d as normal field.  Blocks on
+ * the device; also reports floor events seen since the previous call: returns VL2_E_NONPHYS (with
+ * *dt_out still set) when a density/pressure floor fired or dt is not finite.  Errors: VL2_E_ARG,
+ * VL2_E_CUDA, VL2_E_NONPHYS. */
+vl2_status vl2_new_dt(vl2_mesh* mesh, double* dt_out);
+
+/* Copy out the conserved state: u = [5][NZ][NY][NX] (rho, M1, M2, M3, E) and the face fields (any of
+ * the four pointers may be NULL to skip it).  Errors: VL2_E_ARG, VL2_E_CUDA. */
+vl2_status vl2_get_cons(vl2_mesh* mesh, double* u, double* b1, double* b2, double* b3, int where);
+
+/* Primitives of the current state on the active cells: w = [8][NZ][NY][NX] (rho, vx, vy, vz, p,
+ * b_c1, b_c2, b_c3), with the floors of the cons->prim step applied (Sec. 3.1).  Errors as above. */
+vl2_status vl2_get_prims(vl2_mesh* mesh, double* w, int where);
+
+/* Discrete divergence diagnostic (Sec. 2.1.1: CT keeps div B at round-off):
+ * *out = max over active cells of |div_h B| * min(dx) / max(rms |b_c|, 1e-300).  Blocks.
+ * Errors: VL2_E_ARG, VL2_E_CUDA. */
+vl2_status vl2_divb_norm(vl2_mesh* mesh, double* out);
+
+/* Volume integrals over the active cells: out[0..7] = sum(rho, M1, M2, M3, E, b_c1, b_c2, b_c3) dV,
+ * FP64 with a fixed reduction order (deterministic).  Blocks.  Errors: VL2_E_ARG, VL2_E_CUDA. */
+vl2_status vl2_totals(vl2_mesh* mesh, double out[8]);
+
+/* Total number of cons->prim floor events on active cells since creation.  Blocks. */
+vl2_status vl2_floor_count(vl2_mesh* mesh, long long* out);
+
+/* Inspection of one stage's terms for the current state (Sec. 3.2.1-3.2.2, 3.1), without updating
+ * it: face fluxes of the given reconstruction on the global face grids fx[7][NZ][NY][NX+1],
+ * fy[7][NZ][NY+1][NX], fz[7][NZ+1][NY][NX], components in the sweep frame (mass, M_n, M_t1, M_t2,
+ * E, B_t1, B_t2) with (n, t1, t2) = (x, y, z), (y, z, x), (z, x, y).  Errors: VL2_E_ARG, VL2_E_CUDA. */
+vl2_status vl2_debug_fluxes(vl2_mesh* mesh, int recon, double* fx, double* fy, double* fz, int where);
+
+/* Corner EMFs (upwind CT) of the current state for the given reconstruction on the global edge
+ * grids e1[NZ+1][NY+1][NX] (E_x), e2[NZ+1][NY][NX+1] (E_y), e3[NZ][NY+1][NX+1] (E_z). */
+vl2_status vl2_debug_emfs(vl2_mesh* mesh, int recon, double* e1, double* e2, double* e3, int where);
+
+/* Kernel kinds of vl2_profile_read. */
+enum {
+  VL2_K_PRIM = 0,     /* cons -> prim on every cell (with the fused CFL reduction after a cycle) */
+  VL2_K_GHOSTS = 1,   /* ghost exchange of U and the face field */
+  VL2_K_FLUX_DC = 2,  /* donor-cell + Riemann fluxes of one sweep direction (units: faces) */
+  VL2_K_FLUX_PLM = 3, /* PLM + Riemann fluxes of one sweep direction (units: faces) */
+  VL2_K_EMF = 4,      /* upwind CT corner EMFs (units: corner nodes) */
+  VL2_K_UPDATE = 5,   /* register update of U and the face field (units: nodes) */
+  VL2_K_COUNT = 6
+};
+
+/* Per-kernel timing, the measuring side of the paper's zone-cycles-per-second benchmarks (Sec. 3.4.1).
+ * vl2_profile(mesh, 1) brackets every later kernel launch of the mesh with CUDA events on its stream;
+ * vl2_profile_read() waits for the stream, then returns and resets the accumulated device time (ms),
+ * the launch count and the work units (cells, faces or nodes) of one kernel kind.  Events are owned
+ * by the mesh.  Errors: VL2_E_ARG (NULL, bad kind), VL2_E_CUDA. */
+vl2_status vl2_profile(vl2_mesh* mesh, int enable);
+vl2_status vl2_profile_read(vl2_mesh* mesh, int kind, double* ms, long long* launches, long long* units);
+
+/* Number of CUDA kernels this mesh has launched since creation (every launch, profiled or not). */
+vl2_status vl2_launch_count(const vl2_mesh* mesh, long long* n);
+
+/* Message of the last failing call on `mesh` (or of the last failing call with no mesh, if NULL).
+ * The string is owned by the library. */
+const char* vl2_last_error(const vl2_mesh* mesh);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VL2MHD_H */

@@ -69,6 +69,8 @@ def lib():
         L.orc_fast_speed.restype = ctypes.c_double
         L.orc_vanleer_slope.argtypes = [ctypes.c_double] * 3
         L.orc_vanleer_slope.restype = ctypes.c_double
+        L.orc_count_face_ops.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
+                                         ctypes.POINTER(ctypes.c_longlong)]
         L.orc_ct_corner.argtypes = [dp, dp, dp, dp, dp]
         L.orc_ct_corner.restype = ctypes.c_double
         _lib = L
@@ -107,6 +109,15 @@ def fast_speed(d, p, bn, bt1, bt2, gamma):
 
 def vanleer_slope(qm, q0, qp):
     return lib().orc_vanleer_slope(qm, q0, qp)
+
+
+def count_face_ops(recon, solver, q4, bn, gamma):
+    """(add/sub, mul, div, sqrt, compare) FP64 operations of one face flux; q4 = states of cells
+    i-2 .. i+1 in the sweep frame, shape (4, 7)."""
+    q = _c64(q4).reshape(-1)
+    out = (ctypes.c_longlong * 5)()
+    lib().orc_count_face_ops(recon, solver, _dp(q), float(bn), float(gamma), out)
+    return np.array(out[:], dtype=np.int64)
 
 
 def ct_corner(ea, eb, ec, ma, mb):

@@ -59,6 +59,43 @@ enum { IDN = 0, IVN = 1, IVT1 = 2, IVT2 = 3, IPR = 4, IBT1 = 5, IBT2 = 6, NW7 = 
 template <class T> static inline T vmin(T a, T b) { return (a < b) ? a : b; }
 template <class T> static inline T vmax(T a, T b) { return (a > b) ? a : b; }
 
+/* Operation-counting scalar: carries the FP64 value and counts every arithmetic operation applied to
+ * it (add/sub, mul, div, sqrt, compare; sign changes and |x| are free).  Instantiating the pointwise
+ * functions with it gives the algorithmic FP64 work of one face, used as the roofline's unit cost. */
+struct OpCount {
+  long long add = 0, mul = 0, div = 0, sqrt = 0, cmp = 0;
+};
+static thread_local OpCount g_ops;
+struct Flop {
+  double v;
+  Flop() : v(0.0) {}
+  Flop(double x) : v(x) {}
+};
+static inline Flop operator+(Flop a, Flop b) { ++g_ops.add; return Flop(a.v + b.v); }
+static inline Flop operator-(Flop a, Flop b) { ++g_ops.add; return Flop(a.v - b.v); }
+static inline Flop operator*(Flop a, Flop b) { ++g_ops.mul; return Flop(a.v * b.v); }
+static inline Flop operator/(Flop a, Flop b) { ++g_ops.div; return Flop(a.v / b.v); }
+static inline Flop operator+(double a, Flop b) { return Flop(a) + b; }
+static inline Flop operator-(double a, Flop b) { return Flop(a) - b; }
+static inline Flop operator*(double a, Flop b) { return Flop(a) * b; }
+static inline Flop operator/(double a, Flop b) { return Flop(a) / b; }
+static inline Flop operator+(Flop a, double b) { return a + Flop(b); }
+static inline Flop operator-(Flop a, double b) { return a - Flop(b); }
+static inline Flop operator*(Flop a, double b) { return a * Flop(b); }
+static inline Flop operator/(Flop a, double b) { return a / Flop(b); }
+static inline Flop operator-(Flop a) { return Flop(-a.v); }
+static inline bool operator<(Flop a, Flop b) { ++g_ops.cmp; return a.v < b.v; }
+static inline bool operator>(Flop a, Flop b) { ++g_ops.cmp; return a.v > b.v; }
+static inline bool operator<=(Flop a, Flop b) { ++g_ops.cmp; return a.v <= b.v; }
+static inline bool operator>=(Flop a, Flop b) { ++g_ops.cmp; return a.v >= b.v; }
+static inline bool operator==(Flop a, Flop b) { ++g_ops.cmp; return a.v == b.v; }
+static inline bool operator<(Flop a, double b) { return a < Flop(b); }
+static inline bool operator>(Flop a, double b) { return a > Flop(b); }
+static inline bool operator<=(Flop a, double b) { return a <= Flop(b); }
+static inline bool operator>=(Flop a, double b) { return a >= Flop(b); }
+static inline Flop fabs(Flop a) { return Flop(std::fabs(a.v)); }
+static inline Flop sqrt(Flop a) { ++g_ops.sqrt; return Flop(std::sqrt(a.v)); }
+
 /* ---------------------------------------------------------------------------------------------
  * Pointwise physics
  * ------------------------------------------------------------------------------------------- */
@@ -1067,6 +1104,32 @@ double orc_fast_speed(double d, double p, double bn, double bt1, double bt2, dou
 }
 
 double orc_vanleer_slope(double qm, double q0, double qp) { return orc::vanleer_slope<double>(qm, q0, qp); }
+
+/* FP64 operations of one face flux for the given reconstruction and solver, counted with the
+ * operation-counting scalar.  q: the 7-component sweep-frame states of cells i-2, i-1, i, i+1
+ * ([4][7]); out: add/sub, mul, div, sqrt, compare counts. */
+void orc_count_face_ops(int recon, int solver, const double* q, double bn, double gamma, long long* out) {
+  using orc::Flop;
+  orc::g_ops = orc::OpCount();
+  Flop wl[7], wr[7], f[7];
+  for (int n = 0; n < 7; ++n) {
+    if (recon == orc::REC_DC) {
+      wl[n] = Flop(q[7 + n]);
+      wr[n] = Flop(q[14 + n]);
+    } else {
+      const Flop dlm = orc::vanleer_slope(Flop(q[n]), Flop(q[7 + n]), Flop(q[14 + n]));
+      const Flop dl0 = orc::vanleer_slope(Flop(q[7 + n]), Flop(q[14 + n]), Flop(q[21 + n]));
+      wl[n] = Flop(q[7 + n]) + 0.5 * dlm;
+      wr[n] = Flop(q[14 + n]) - 0.5 * dl0;
+    }
+  }
+  orc::riemann<Flop>(solver, wl, wr, Flop(bn), gamma, f);
+  out[0] = orc::g_ops.add;
+  out[1] = orc::g_ops.mul;
+  out[2] = orc::g_ops.div;
+  out[3] = orc::g_ops.sqrt;
+  out[4] = orc::g_ops.cmp;
+}
 
 double orc_ct_corner(const double* ea, const double* eb, const double* ec, const double* ma, const double* mb) {
   return orc::ct_corner<double>(ea, eb, ec, ma, mb);

@@ -1,0 +1,654 @@
+// C ABI of the GB300 VL2 MHD library (declarations and contracts in include/vl2mhd.h).
+// Host orchestration only: argument checks, workspace carving, the kernel sequence of a VL2 cycle
+// (Sec. 3.2.3) and the copies of global-array I/O.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vl2_internal.h"
+#include "vl2mhd.h"
+
+using vl2::Arrays;
+using vl2::Geom;
+using vl2::NG;
+
+struct vl2_mesh {
+  vl2_params p;
+  Geom g;
+  Arrays a;
+  cudaStream_t st = nullptr;
+  std::vector<int> loc, nbr;
+  bool initialized = false;
+  bool w_valid = false;     // primitives of register 0 are current on every cell
+  bool dt_pending = false;  // scal[SC_MAXRATE] holds the CFL rate of register 0
+  unsigned long long floors_seen = 0;
+  double* dres = nullptr;   // device result slots of the reductions
+  std::string err;
+  // kernel timing (vl2_profile) and launch counting
+  bool prof = false;
+  struct Rec {
+    int kind;
+    long long units;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+  double acc_ms[VL2_K_COUNT] = {0};
+  long long acc_n[VL2_K_COUNT] = {0}, acc_units[VL2_K_COUNT] = {0};
+  long long launches = 0;
+  ~vl2_mesh() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+vl2_status fail(vl2_mesh* m, vl2_status s, const std::string& msg) {
+  if (m)
+    m->err = msg;
+  else
+    g_err = msg;
+  return s;
+}
+
+vl2_status cuda_fail(vl2_mesh* m, cudaError_t e, const char* where) {
+  return fail(m, VL2_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define VL2_CHECK(m, call)                                  \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail((m), e_, #call); \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+long long ncells(const Geom& g) { return (long long)g.N[0] * g.N[1] * g.N[2]; }
+
+long long nfaces_total(const Geom& g) {
+  const long long X = g.N[0], Y = g.N[1], Z = g.N[2];
+  return (X + 1) * Y * Z + X * (Y + 1) * Z + X * Y * (Z + 1);
+}
+
+long long max_face_grid(const Geom& g) {
+  const long long X = g.N[0], Y = g.N[1], Z = g.N[2];
+  long long m = (X + 1) * Y * Z;
+  m = std::max(m, X * (Y + 1) * Z);
+  m = std::max(m, X * Y * (Z + 1));
+  return m;
+}
+
+long long max_edge_grid(const Geom& g) {
+  const long long X = g.N[0], Y = g.N[1], Z = g.N[2];
+  long long m = X * (Y + 1) * (Z + 1);
+  m = std::max(m, (X + 1) * Y * (Z + 1));
+  m = std::max(m, (X + 1) * (Y + 1) * Z);
+  return m;
+}
+
+constexpr int RED_CTAS = 608;  // 4 per SM on a 152-SM GB300
+
+vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
+  if (!p) {
+    msg = "params is NULL";
+    return VL2_E_ARG;
+  }
+  for (int d = 0; d < 3; ++d) {
+    if (p->nx[d] <= 0 || p->mb[d] <= 0 || p->nx[d] % p->mb[d] != 0) {
+      msg = "nx must be positive multiples of mb in every direction";
+      return VL2_E_ARG;
+    }
+    if (!(p->xmax[d] > p->xmin[d])) {
+      msg = "xmax must exceed xmin";
+      return VL2_E_ARG;
+    }
+  }
+  if (p->ng != NG) {
+    msg = "ng must be 2";
+    return VL2_E_ARG;
+  }
+  if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->dfloor > 0.0) || !(p->pfloor > 0.0)) {
+    msg = "gamma > 1, cfl > 0 and positive floors are required";
+    return VL2_E_ARG;
+  }
+  if (p->riemann != VL2_HLLD && p->riemann != VL2_HLLE) {
+    msg = "riemann must be VL2_HLLD or VL2_HLLE";
+    return VL2_E_ARG;
+  }
+  if (p->precision != VL2_FP64) {
+    msg = "precision must be VL2_FP64";
+    return VL2_E_ARG;
+  }
+  for (int d = 0; d < 3; ++d) {
+    const int lo = p->bc[2 * d], hi = p->bc[2 * d + 1];
+    if ((lo != VL2_PERIODIC && lo != VL2_OUTFLOW) || (hi != VL2_PERIODIC && hi != VL2_OUTFLOW) ||
+        ((lo == VL2_PERIODIC) != (hi == VL2_PERIODIC))) {
+      msg = "bc must be periodic on both faces of a direction or outflow";
+      return VL2_E_ARG;
+    }
+  }
+  std::memset(&g, 0, sizeof(g));
+  long long nblk = 1;
+  for (int d = 0; d < 3; ++d) {
+    g.N[d] = p->nx[d];
+    g.mb[d] = p->mb[d];
+    g.nb[d] = p->nx[d] / p->mb[d];
+    nblk *= g.nb[d];
+    g.dx[d] = (p->xmax[d] - p->xmin[d]) / p->nx[d];
+    g.idx[d] = 1.0 / g.dx[d];
+  }
+  if (nblk > (1LL << 30)) {
+    msg = "too many MeshBlocks";
+    return VL2_E_ARG;
+  }
+  g.nblk = (int)nblk;
+  g.sx = ((p->mb[0] + 2 * NG + 1) + 3) & ~3;
+  g.sy = p->mb[1] + 2 * NG + 1;
+  g.sz = p->mb[2] + 2 * NG + 1;
+  g.box = (long long)g.sx * g.sy * g.sz;
+  if (g.box * 8 > (1LL << 31)) {
+    msg = "MeshBlock too large";
+    return VL2_E_ARG;
+  }
+  for (int f = 0; f < 6; ++f) g.bc[f] = p->bc[f];
+  g.gamma = p->gamma;
+  g.gm1 = p->gamma - 1.0;
+  g.igm1 = 1.0 / (p->gamma - 1.0);
+  g.dfloor = p->dfloor;
+  g.pfloor = p->pfloor;
+  return VL2_OK;
+}
+
+struct Plan {
+  size_t off_u[2], off_b[2][3], off_w, off_f[3], off_e[3], off_stage, off_red, off_scal, total;
+  size_t stage_elems;
+};
+
+Plan make_plan(const Geom& g) {
+  Plan pl;
+  size_t o = 0;
+  const size_t per = (size_t)g.nblk * g.box * sizeof(double);
+  for (int r = 0; r < 2; ++r) {
+    pl.off_u[r] = o;
+    o = align256(o + 5 * per);
+    for (int d = 0; d < 3; ++d) {
+      pl.off_b[r][d] = o;
+      o = align256(o + per);
+    }
+  }
+  pl.off_w = o;
+  o = align256(o + 8 * per);
+  for (int d = 0; d < 3; ++d) {
+    pl.off_f[d] = o;
+    o = align256(o + 7 * per);
+  }
+  for (int d = 0; d < 3; ++d) {
+    pl.off_e[d] = o;
+    o = align256(o + per);
+  }
+  const long long nc = ncells(g);
+  long long st = 5 * nc + nfaces_total(g);
+  st = std::max(st, 8 * nc);
+  st = std::max(st, 7 * max_face_grid(g));
+  st = std::max(st, max_edge_grid(g));
+  pl.stage_elems = (size_t)st;
+  pl.off_stage = o;
+  o = align256(o + (size_t)st * sizeof(double));
+  pl.off_red = o;
+  o = align256(o + (size_t)RED_CTAS * 8 * sizeof(double));
+  pl.off_scal = o;
+  o = align256(o + vl2::SC_COUNT * sizeof(unsigned long long) + 16 * sizeof(double));
+  pl.total = o;
+  return pl;
+}
+
+vl2_status sync(vl2_mesh* m) {
+  VL2_CHECK(m, cudaStreamSynchronize(m->st));
+  return VL2_OK;
+}
+
+vl2_status copy_in(vl2_mesh* m, double* dst, const double* src, size_t n, int where) {
+  VL2_CHECK(m, cudaMemcpyAsync(dst, src, n * sizeof(double),
+                               where == VL2_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, m->st));
+  return VL2_OK;
+}
+
+vl2_status copy_out(vl2_mesh* m, double* dst, const double* src, size_t n) {
+  VL2_CHECK(m, cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, m->st));
+  return VL2_OK;
+}
+
+
+bool bad_where(int where) { return where != VL2_HOST && where != VL2_DEVICE; }
+
+cudaEvent_t pool_event(vl2_mesh* m) {
+  if (m->pool_used == m->pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    m->pool.push_back(e);
+  }
+  return m->pool[m->pool_used++];
+}
+
+// Enqueue one kernel launch: counts it and, when profiling is on, brackets it with events.
+template <class Fn>
+cudaError_t timed(vl2_mesh* m, int kind, long long units, Fn&& fn) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (m->prof) {
+    a = pool_event(m);
+    b = pool_event(m);
+    if (a) cudaEventRecord(a, m->st);
+  }
+  cudaError_t e = fn();
+  ++m->launches;
+  if (m->prof && a && b && e == cudaSuccess) {
+    cudaEventRecord(b, m->st);
+    m->recs.push_back({kind, units, a, b});
+  }
+  return e;
+}
+
+long long cells_all(const Geom& g) {
+  return (long long)g.nblk * (g.mb[0] + 2 * NG) * (g.mb[1] + 2 * NG) * (g.mb[2] + 2 * NG);
+}
+long long nodes(const Geom& g) { return (long long)g.nblk * (g.mb[0] + 1) * (g.mb[1] + 1) * (g.mb[2] + 1); }
+long long ghost_elems(const Geom& g) {
+  return (long long)g.nblk * (g.mb[0] + 2 * NG + 1) * (g.mb[1] + 2 * NG + 1) * (g.mb[2] + 2 * NG + 1);
+}
+long long flux_faces(const Geom& g, int d) {
+  long long n = g.nblk;
+  for (int q = 0; q < 3; ++q) n *= g.mb[q] + (q == d ? 1 : 2);
+  return n;
+}
+
+cudaError_t k_prim(vl2_mesh* m, int reg, bool dt) {
+  return timed(m, VL2_K_PRIM, cells_all(m->g), [&] { return vl2::launch_prim(m->g, m->a, reg, true, dt, m->st); });
+}
+cudaError_t k_ghosts(vl2_mesh* m, int reg) {
+  return timed(m, VL2_K_GHOSTS, ghost_elems(m->g), [&] { return vl2::launch_ghosts(m->g, m->a, reg, m->st); });
+}
+cudaError_t k_fluxes(vl2_mesh* m, int reg, int recon) {
+  for (int d = 0; d < 3; ++d) {
+    cudaError_t e = timed(m, recon == VL2_DC ? VL2_K_FLUX_DC : VL2_K_FLUX_PLM, flux_faces(m->g, d),
+                          [&] { return vl2::launch_flux(m->g, m->a, reg, recon, m->p.riemann, d, m->st); });
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+cudaError_t k_emfs(vl2_mesh* m) {
+  return timed(m, VL2_K_EMF, nodes(m->g), [&] { return vl2::launch_emfs(m->g, m->a, m->st); });
+}
+cudaError_t k_update(vl2_mesh* m, int base, int out, double h) {
+  return timed(m, VL2_K_UPDATE, nodes(m->g), [&] { return vl2::launch_update(m->g, m->a, base, out, h, m->st); });
+}
+
+vl2_status ensure_prims(vl2_mesh* m) {
+  if (!m->w_valid) {
+    VL2_CHECK(m, k_prim(m, 0, false));
+    m->w_valid = true;
+  }
+  return VL2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vl2_status vl2_workspace_bytes(const vl2_params* params, size_t* bytes) {
+  Geom g;
+  std::string msg;
+  vl2_status s = make_geom(params, g, msg);
+  if (s != VL2_OK) return fail(nullptr, s, msg);
+  if (!bytes) return fail(nullptr, VL2_E_ARG, "bytes is NULL");
+  *bytes = make_plan(g).total;
+  return VL2_OK;
+}
+
+vl2_status vl2_mesh_create(const vl2_params* params, void* workspace, size_t bytes, vl2_mesh** out) {
+  if (!out) return fail(nullptr, VL2_E_ARG, "out is NULL");
+  *out = nullptr;
+  Geom g;
+  std::string msg;
+  vl2_status s = make_geom(params, g, msg);
+  if (s != VL2_OK) return fail(nullptr, s, msg);
+  if (!workspace || ((uintptr_t)workspace & 255u)) return fail(nullptr, VL2_E_ARG, "workspace must be 256-byte aligned");
+  const Plan pl = make_plan(g);
+  if (bytes < pl.total) return fail(nullptr, VL2_E_NOMEM, "workspace smaller than vl2_workspace_bytes()");
+  vl2_mesh* m = new (std::nothrow) vl2_mesh();
+  if (!m) return fail(nullptr, VL2_E_ARG, "host allocation failed");
+  m->p = *params;
+  m->g = g;
+  m->st = (cudaStream_t)params->stream;
+  char* base = (char*)workspace;
+  for (int r = 0; r < 2; ++r) {
+    m->a.u[r] = (double*)(base + pl.off_u[r]);
+    for (int d = 0; d < 3; ++d) m->a.b[r][d] = (double*)(base + pl.off_b[r][d]);
+  }
+  m->a.w = (double*)(base + pl.off_w);
+  for (int d = 0; d < 3; ++d) {
+    m->a.f[d] = (double*)(base + pl.off_f[d]);
+    m->a.e[d] = (double*)(base + pl.off_e[d]);
+  }
+  m->a.stage = (double*)(base + pl.off_stage);
+  m->a.stage_elems = pl.stage_elems;
+  m->a.red = (double*)(base + pl.off_red);
+  m->a.red_ctas = RED_CTAS;
+  m->a.scal = (unsigned long long*)(base + pl.off_scal);
+  m->dres = (double*)(m->a.scal + vl2::SC_COUNT);
+  // block table and 26-neighbour table (x fastest block order)
+  m->loc.resize((size_t)g.nblk * 3);
+  m->nbr.resize((size_t)g.nblk * 27);
+  for (int b = 0; b < g.nblk; ++b) {
+    const int l[3] = {b % g.nb[0], (b / g.nb[0]) % g.nb[1], b / (g.nb[0] * g.nb[1])};
+    for (int d = 0; d < 3; ++d) m->loc[3 * b + d] = l[d];
+    for (int dk = -1; dk <= 1; ++dk)
+      for (int dj = -1; dj <= 1; ++dj)
+        for (int di = -1; di <= 1; ++di) {
+          const int dd[3] = {di, dj, dk};
+          int q[3];
+          bool ok = true;
+          for (int d = 0; d < 3; ++d) {
+            q[d] = l[d] + dd[d];
+            if (q[d] < 0 || q[d] >= g.nb[d]) {
+              if (g.bc[2 * d] == vl2::BC_PERIODIC)
+                q[d] = (q[d] + g.nb[d]) % g.nb[d];
+              else
+                ok = false;
+            }
+          }
+          m->nbr[(size_t)b * 27 + (dk + 1) * 9 + (dj + 1) * 3 + (di + 1)] =
+              ok ? (q[2] * g.nb[1] + q[1]) * g.nb[0] + q[0] : -1;
+        }
+  }
+  cudaError_t e = cudaMemsetAsync(workspace, 0, pl.total, m->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
+  if (e != cudaSuccess) {
+    delete m;
+    return fail(nullptr, VL2_E_CUDA, std::string("workspace clear: ") + cudaGetErrorString(e));
+  }
+  *out = m;
+  return VL2_OK;
+}
+
+vl2_status vl2_mesh_destroy(vl2_mesh* mesh) {
+  delete mesh;
+  return VL2_OK;
+}
+
+vl2_status vl2_block_layout(const vl2_mesh* mesh, vl2_layout* out) {
+  if (!mesh || !out) return fail(nullptr, VL2_E_ARG, "NULL argument");
+  out->nblocks = mesh->g.nblk;
+  for (int d = 0; d < 3; ++d) {
+    out->nb[d] = mesh->g.nb[d];
+    out->mb[d] = mesh->g.mb[d];
+  }
+  out->ng = NG;
+  out->sx = mesh->g.sx;
+  out->sy = mesh->g.sy;
+  out->sz = mesh->g.sz;
+  out->block_stride_vars = mesh->g.box;
+  out->block_loc = mesh->loc.data();
+  out->neighbor = mesh->nbr.data();
+  out->u = mesh->a.u[0];
+  for (int d = 0; d < 3; ++d) out->b[d] = mesh->a.b[0][d];
+  return VL2_OK;
+}
+
+vl2_status vl2_set_prims(vl2_mesh* m, const double* w, const double* b1, const double* b2, const double* b3,
+                         int where) {
+  if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
+  if (!w || !b1 || !b2 || !b3 || bad_where(where)) return fail(m, VL2_E_ARG, "NULL input or bad where");
+  const Geom& g = m->g;
+  const long long nc = ncells(g);
+  const long long n1 = (long long)(g.N[0] + 1) * g.N[1] * g.N[2];
+  const long long n2 = (long long)g.N[0] * (g.N[1] + 1) * g.N[2];
+  const long long n3 = (long long)g.N[0] * g.N[1] * (g.N[2] + 1);
+  const double *dw = w, *d1 = b1, *d2 = b2, *d3 = b3;
+  if (where == VL2_HOST) {
+    double* s = m->a.stage;
+    vl2_status st;
+    if ((st = copy_in(m, s, w, 5 * nc, where)) != VL2_OK) return st;
+    if ((st = copy_in(m, s + 5 * nc, b1, n1, where)) != VL2_OK) return st;
+    if ((st = copy_in(m, s + 5 * nc + n1, b2, n2, where)) != VL2_OK) return st;
+    if ((st = copy_in(m, s + 5 * nc + n1 + n2, b3, n3, where)) != VL2_OK) return st;
+    dw = s;
+    d1 = s + 5 * nc;
+    d2 = d1 + n1;
+    d3 = d2 + n2;
+  }
+  VL2_CHECK(m, cudaMemsetAsync(m->a.scal + vl2::SC_MISMATCH, 0, sizeof(unsigned long long), m->st));
+  VL2_CHECK(m, vl2::launch_check_periodic(g, d1, d2, d3, m->a.scal + vl2::SC_MISMATCH, m->st));
+  ++m->launches;
+  unsigned long long mism = 0;
+  VL2_CHECK(m, cudaMemcpyAsync(&mism, m->a.scal + vl2::SC_MISMATCH, sizeof(mism), cudaMemcpyDeviceToHost, m->st));
+  vl2_status s = sync(m);
+  if (s != VL2_OK) return s;
+  if (mism) return fail(m, VL2_E_ARG, "periodic duplicate faces (face N and face 0) differ");
+  VL2_CHECK(m, vl2::launch_scatter_prims(g, m->a, dw, d1, d2, d3, m->st));
+  ++m->launches;
+  VL2_CHECK(m, k_ghosts(m, 0));
+  m->initialized = true;
+  m->w_valid = false;
+  m->dt_pending = false;
+  return sync(m);
+}
+
+vl2_status vl2_fill_ghosts(vl2_mesh* m) {
+  if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
+  VL2_CHECK(m, k_ghosts(m, 0));
+  m->w_valid = false;
+  m->dt_pending = false;
+  return VL2_OK;
+}
+
+vl2_status vl2_step(vl2_mesh* m, double dt) {
+  if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
+  if (!m->initialized) return fail(m, VL2_E_STATE, "vl2_set_prims has not been called");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(m, VL2_E_ARG, "dt must be finite and positive");
+  vl2_status s = ensure_prims(m);
+  if (s != VL2_OK) return s;
+  // predictor: U* = U^n + (dt/2) L_DC(U^n) into register 1 (Sec. 3.2.3, VL2)
+  VL2_CHECK(m, k_fluxes(m, 0, VL2_DC));
+  VL2_CHECK(m, k_emfs(m));
+  VL2_CHECK(m, k_update(m, 0, 1, 0.5 * dt));
+  VL2_CHECK(m, k_ghosts(m, 1));
+  VL2_CHECK(m, k_prim(m, 1, false));
+  // corrector: U^{n+1} = U^n + dt L_PLM(U*) in place in register 0
+  VL2_CHECK(m, k_fluxes(m, 1, VL2_PLM));
+  VL2_CHECK(m, k_emfs(m));
+  VL2_CHECK(m, k_update(m, 0, 0, dt));
+  VL2_CHECK(m, k_ghosts(m, 0));
+  // primitives of U^{n+1} for the next cycle, with the CFL reduction fused in
+  VL2_CHECK(m, cudaMemsetAsync(m->a.scal + vl2::SC_MAXRATE, 0, sizeof(unsigned long long), m->st));
+  VL2_CHECK(m, k_prim(m, 0, true));
+  m->w_valid = true;
+  m->dt_pending = true;
+  return VL2_OK;
+}
+
+vl2_status vl2_new_dt(vl2_mesh* m, double* dt_out) {
+  if (!m || !dt_out) return fail(m, VL2_E_ARG, "NULL argument");
+  if (!m->initialized) return fail(m, VL2_E_STATE, "vl2_set_prims has not been called");
+  if (!m->dt_pending) {
+    VL2_CHECK(m, cudaMemsetAsync(m->a.scal + vl2::SC_MAXRATE, 0, sizeof(unsigned long long), m->st));
+    VL2_CHECK(m, k_prim(m, 0, true));
+    m->w_valid = true;
+    m->dt_pending = true;
+  }
+  unsigned long long sc[2];
+  VL2_CHECK(m, cudaMemcpyAsync(sc, m->a.scal, sizeof(sc), cudaMemcpyDeviceToHost, m->st));
+  vl2_status s = sync(m);
+  if (s != VL2_OK) return s;
+  double rate;
+  std::memcpy(&rate, &sc[vl2::SC_MAXRATE], sizeof(rate));
+  const double dt = m->p.cfl / rate;
+  *dt_out = dt;
+  const unsigned long long floors = sc[vl2::SC_FLOORS];
+  const bool fired = floors > m->floors_seen;
+  m->floors_seen = floors;
+  if (!std::isfinite(dt) || !(dt > 0.0)) return fail(m, VL2_E_NONPHYS, "time step is not finite and positive");
+  if (fired) return fail(m, VL2_E_NONPHYS, "a density or pressure floor fired");
+  return VL2_OK;
+}
+
+vl2_status vl2_get_cons(vl2_mesh* m, double* u, double* b1, double* b2, double* b3, int where) {
+  if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
+  if (bad_where(where)) return fail(m, VL2_E_ARG, "bad where");
+  const Geom& g = m->g;
+  if (where == VL2_DEVICE) {
+    VL2_CHECK(m, vl2::launch_gather_cons(g, m->a, u, b1, b2, b3, m->st));
+    ++m->launches;
+    return VL2_OK;
+  }
+  const long long nc = ncells(g);
+  const long long n1 = (long long)(g.N[0] + 1) * g.N[1] * g.N[2];
+  const long long n2 = (long long)g.N[0] * (g.N[1] + 1) * g.N[2];
+  const long long n3 = (long long)g.N[0] * g.N[1] * (g.N[2] + 1);
+  double* s = m->a.stage;
+  double *su = u ? s : nullptr, *s1 = b1 ? s + 5 * nc : nullptr, *s2 = b2 ? s + 5 * nc + n1 : nullptr,
+         *s3 = b3 ? s + 5 * nc + n1 + n2 : nullptr;
+  VL2_CHECK(m, vl2::launch_gather_cons(g, m->a, su, s1, s2, s3, m->st));
+  ++m->launches;
+  vl2_status st;
+  if (u && (st = copy_out(m, u, su, 5 * nc)) != VL2_OK) return st;
+  if (b1 && (st = copy_out(m, b1, s1, n1)) != VL2_OK) return st;
+  if (b2 && (st = copy_out(m, b2, s2, n2)) != VL2_OK) return st;
+  if (b3 && (st = copy_out(m, b3, s3, n3)) != VL2_OK) return st;
+  return sync(m);
+}
+
+vl2_status vl2_get_prims(vl2_mesh* m, double* w, int where) {
+  if (!m || !w) return fail(m, VL2_E_ARG, "NULL argument");
+  if (bad_where(where)) return fail(m, VL2_E_ARG, "bad where");
+  vl2_status s = ensure_prims(m);
+  if (s != VL2_OK) return s;
+  const long long nc = ncells(m->g);
+  double* dst = where == VL2_DEVICE ? w : m->a.stage;
+  VL2_CHECK(m, vl2::launch_gather_prims(m->g, m->a, dst, m->st));
+  ++m->launches;
+  if (where == VL2_DEVICE) return VL2_OK;
+  if ((s = copy_out(m, w, dst, 8 * nc)) != VL2_OK) return s;
+  return sync(m);
+}
+
+vl2_status vl2_divb_norm(vl2_mesh* m, double* out) {
+  if (!m || !out) return fail(m, VL2_E_ARG, "NULL argument");
+  VL2_CHECK(m, vl2::launch_divb(m->g, m->a, m->dres, m->st));
+  double r[2];
+  VL2_CHECK(m, cudaMemcpyAsync(r, m->dres, sizeof(r), cudaMemcpyDeviceToHost, m->st));
+  vl2_status s = sync(m);
+  if (s != VL2_OK) return s;
+  const Geom& g = m->g;
+  const double hmin = std::fmin(g.dx[0], std::fmin(g.dx[1], g.dx[2]));
+  const double rms = std::sqrt(r[1] / (double)ncells(g));
+  *out = r[0] * hmin / std::fmax(rms, 1e-300);
+  return VL2_OK;
+}
+
+vl2_status vl2_totals(vl2_mesh* m, double out[8]) {
+  if (!m || !out) return fail(m, VL2_E_ARG, "NULL argument");
+  VL2_CHECK(m, vl2::launch_totals(m->g, m->a, m->dres, m->st));
+  VL2_CHECK(m, cudaMemcpyAsync(out, m->dres, 8 * sizeof(double), cudaMemcpyDeviceToHost, m->st));
+  return sync(m);
+}
+
+vl2_status vl2_floor_count(vl2_mesh* m, long long* out) {
+  if (!m || !out) return fail(m, VL2_E_ARG, "NULL argument");
+  unsigned long long v = 0;
+  VL2_CHECK(m, cudaMemcpyAsync(&v, m->a.scal + vl2::SC_FLOORS, sizeof(v), cudaMemcpyDeviceToHost, m->st));
+  vl2_status s = sync(m);
+  if (s != VL2_OK) return s;
+  *out = (long long)v;
+  return VL2_OK;
+}
+
+static vl2_status gather_out(vl2_mesh* m, int kind, int dir, double* out, long long n, int where) {
+  double* dst = where == VL2_DEVICE ? out : m->a.stage;
+  if (kind == 0)
+    VL2_CHECK(m, vl2::launch_gather_fluxes(m->g, m->a, dir, dst, m->st));
+  else
+    VL2_CHECK(m, vl2::launch_gather_emfs(m->g, m->a, dir, dst, m->st));
+  if (where == VL2_DEVICE) return VL2_OK;
+  vl2_status s = copy_out(m, out, dst, (size_t)n);
+  if (s != VL2_OK) return s;
+  return sync(m);  // the staging buffer is reused by the next direction
+}
+
+vl2_status vl2_debug_fluxes(vl2_mesh* m, int recon, double* fx, double* fy, double* fz, int where) {
+  if (!m || !fx || !fy || !fz) return fail(m, VL2_E_ARG, "NULL argument");
+  if (bad_where(where) || (recon != VL2_DC && recon != VL2_PLM)) return fail(m, VL2_E_ARG, "bad where or recon");
+  if (!m->initialized) return fail(m, VL2_E_STATE, "vl2_set_prims has not been called");
+  vl2_status s = ensure_prims(m);
+  if (s != VL2_OK) return s;
+  VL2_CHECK(m, k_fluxes(m, 0, recon));
+  const Geom& g = m->g;
+  double* outs[3] = {fx, fy, fz};
+  for (int d = 0; d < 3; ++d) {
+    long long gd[3] = {g.N[0], g.N[1], g.N[2]};
+    gd[d] += 1;
+    if ((s = gather_out(m, 0, d, outs[d], 7 * gd[0] * gd[1] * gd[2], where)) != VL2_OK) return s;
+  }
+  return VL2_OK;
+}
+
+vl2_status vl2_debug_emfs(vl2_mesh* m, int recon, double* e1, double* e2, double* e3, int where) {
+  if (!m || !e1 || !e2 || !e3) return fail(m, VL2_E_ARG, "NULL argument");
+  if (bad_where(where) || (recon != VL2_DC && recon != VL2_PLM)) return fail(m, VL2_E_ARG, "bad where or recon");
+  if (!m->initialized) return fail(m, VL2_E_STATE, "vl2_set_prims has not been called");
+  vl2_status s = ensure_prims(m);
+  if (s != VL2_OK) return s;
+  VL2_CHECK(m, k_fluxes(m, 0, recon));
+  VL2_CHECK(m, k_emfs(m));
+  const Geom& g = m->g;
+  double* outs[3] = {e1, e2, e3};
+  for (int e = 0; e < 3; ++e) {
+    long long gd[3] = {g.N[0] + 1, g.N[1] + 1, g.N[2] + 1};
+    gd[e] -= 1;
+    if ((s = gather_out(m, 1, e, outs[e], gd[0] * gd[1] * gd[2], where)) != VL2_OK) return s;
+  }
+  return VL2_OK;
+}
+
+vl2_status vl2_profile(vl2_mesh* m, int enable) {
+  if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
+  m->prof = enable != 0;
+  return VL2_OK;
+}
+
+vl2_status vl2_profile_read(vl2_mesh* m, int kind, double* ms, long long* launches, long long* units) {
+  if (!m || !ms || !launches || !units) return fail(m, VL2_E_ARG, "NULL argument");
+  if (kind < 0 || kind >= VL2_K_COUNT) return fail(m, VL2_E_ARG, "bad kernel kind");
+  vl2_status s = sync(m);
+  if (s != VL2_OK) return s;
+  for (const auto& r : m->recs) {
+    float t = 0.f;
+    VL2_CHECK(m, cudaEventElapsedTime(&t, r.a, r.b));
+    m->acc_ms[r.kind] += t;
+    m->acc_n[r.kind] += 1;
+    m->acc_units[r.kind] += r.units;
+  }
+  m->recs.clear();
+  m->pool_used = 0;
+  *ms = m->acc_ms[kind];
+  *launches = m->acc_n[kind];
+  *units = m->acc_units[kind];
+  m->acc_ms[kind] = 0.0;
+  m->acc_n[kind] = m->acc_units[kind] = 0;
+  return VL2_OK;
+}
+
+vl2_status vl2_launch_count(const vl2_mesh* m, long long* n) {
+  if (!m || !n) return fail(nullptr, VL2_E_ARG, "NULL argument");
+  *n = m->launches;
+  return VL2_OK;
+}
+
+const char* vl2_last_error(const vl2_mesh* mesh) { return mesh ? mesh->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"

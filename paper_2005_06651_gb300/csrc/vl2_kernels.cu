@@ -1,0 +1,631 @@
+// Non-flux kernels of the VL2 MHD step: cons->prim with the fused CFL reduction, ghost exchange
+// between MeshBlocks, upwind-CT corner EMFs, the register update, global-array I/O and the
+// diagnostic reductions.
+#include "vl2_internal.h"
+#include "vl2_physics.cuh"
+
+namespace vl2 {
+
+static inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+__device__ __forceinline__ void block_loc(const Geom& g, int b, int* loc) {
+  loc[0] = b % g.nb[0];
+  loc[1] = (b / g.nb[0]) % g.nb[1];
+  loc[2] = b / (g.nb[0] * g.nb[1]);
+}
+
+// ------------------------------------------------------------------------------------------------
+// cons -> prim (Sec. 3.1): b_c = mean of the two face values, v = M / rho,
+// p = (gamma-1)(E - |M|^2 / (2 rho) - |b_c|^2 / 2); floors rho >= dfloor, p >= pfloor (an active cell
+// whose floor fires gets U rewritten and is counted).  With DT, the active cells also reduce the CFL
+// rate max_d (|v_d| + C_f,d) / dx_d (Sec. 2.1.7) into scal[SC_MAXRATE] (bit pattern of a positive
+// double, so an integer max is the floating max).
+// ------------------------------------------------------------------------------------------------
+template <bool DT>
+__global__ void __launch_bounds__(256) k_prim(Geom g, double* U, const double* __restrict__ B0,
+                                              const double* __restrict__ B1, const double* __restrict__ B2,
+                                              double* __restrict__ W, unsigned long long* scal, int all) {
+  const int off = all ? 0 : NG;
+  const int ex = g.mb[0] + (all ? 2 * NG : 0), ey = g.mb[1] + (all ? 2 * NG : 0), ez = g.mb[2] + (all ? 2 * NG : 0);
+  const long long per = (long long)ex * ey * ez;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long rate_bits = 0ULL;
+  if (t < per * g.nblk) {
+    const int b = (int)(t / per);
+    int rem = (int)(t - (long long)b * per);
+    const int i = rem % ex + off;
+    rem /= ex;
+    const int j = rem % ey + off;
+    const int k = rem / ey + off;
+    const long long c = cell_off(g, k, j, i);
+    const long long fb = (long long)b * g.box + c;
+    const double bcx = 0.5 * (B0[fb] + B0[fb + 1]);
+    const double bcy = 0.5 * (B1[fb] + B1[fb + g.sx]);
+    const double bcz = 0.5 * (B2[fb] + B2[fb + (long long)g.sx * g.sy]);
+    double* Ub = U + (long long)b * 5 * g.box + c;
+    double d = Ub[0];
+    const double m1 = Ub[g.box], m2 = Ub[2 * g.box], m3 = Ub[3 * g.box];
+    double e = Ub[4 * g.box];
+    const bool active = i >= NG && i < NG + g.mb[0] && j >= NG && j < NG + g.mb[1] && k >= NG && k < NG + g.mb[2];
+    bool fired = false;
+    if (d < g.dfloor) {
+      d = g.dfloor;
+      fired = true;
+    }
+    const double id = 1.0 / d;
+    const double vx = m1 * id, vy = m2 * id, vz = m3 * id;
+    const double ke = 0.5 * ((m1 * m1 + m2 * m2) + m3 * m3) * id;
+    const double me = 0.5 * ((bcx * bcx + bcy * bcy) + bcz * bcz);
+    double p = g.gm1 * (e - ke - me);
+    if (p < g.pfloor) {
+      p = g.pfloor;
+      e = p * g.igm1 + ke + me;
+      fired = true;
+    }
+    if (fired && active) {
+      atomicAdd(scal + SC_FLOORS, 1ULL);
+      Ub[0] = d;
+      Ub[4 * g.box] = e;
+    }
+    double* Wb = W + (long long)b * 8 * g.box + c;
+    Wb[0] = d;
+    Wb[g.box] = vx;
+    Wb[2 * g.box] = vy;
+    Wb[3 * g.box] = vz;
+    Wb[4 * g.box] = p;
+    Wb[5 * g.box] = bcx;
+    Wb[6 * g.box] = bcy;
+    Wb[7 * g.box] = bcz;
+    if (DT && active) {
+      const double bx2 = bcx * bcx, by2 = bcy * bcy, bz2 = bcz * bcz;
+      const double rx = (fabs(vx) + fast_speed_r(id, p, bx2, by2 + bz2, g.gamma)) * g.idx[0];
+      const double ry = (fabs(vy) + fast_speed_r(id, p, by2, bz2 + bx2, g.gamma)) * g.idx[1];
+      const double rz = (fabs(vz) + fast_speed_r(id, p, bz2, bx2 + by2, g.gamma)) * g.idx[2];
+      const unsigned long long ax = __double_as_longlong(rx), ay = __double_as_longlong(ry),
+                               az = __double_as_longlong(rz);
+      rate_bits = ax > ay ? ax : ay;
+      rate_bits = rate_bits > az ? rate_bits : az;
+    }
+  }
+  if (DT) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, rate_bits, o);
+      rate_bits = v > rate_bits ? v : rate_bits;
+    }
+    __shared__ unsigned long long red[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = rate_bits;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long m = 0ULL;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m = red[q] > m ? red[q] : m;
+      if (m) atomicMax(scal + SC_MAXRATE, m);
+    }
+  }
+}
+
+cudaError_t launch_prim(const Geom& g, const Arrays& a, int reg, bool all_cells, bool want_dt, cudaStream_t st) {
+  const long long per = all_cells ? (long long)(g.mb[0] + 2 * NG) * (g.mb[1] + 2 * NG) * (g.mb[2] + 2 * NG)
+                                  : (long long)g.mb[0] * g.mb[1] * g.mb[2];
+  const unsigned grid = grid_for(per * g.nblk, 256);
+  if (want_dt)
+    k_prim<true><<<grid, 256, 0, st>>>(g, a.u[reg], a.b[reg][0], a.b[reg][1], a.b[reg][2], a.w, a.scal, all_cells);
+  else
+    k_prim<false><<<grid, 256, 0, st>>>(g, a.u[reg], a.b[reg][0], a.b[reg][1], a.b[reg][2], a.w, a.scal, all_cells);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Ghost exchange (Sec. 2.1.1): every ghost cell and ghost face of every block is copied from the block
+// that owns the (periodically wrapped, or outflow-clamped) global index.  Faces on a block's surface
+// are active and not overwritten.  A face on the boundary between two blocks is read from the block
+// where it is the lower face; global face N from the last block's upper face.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ void source_of(const Geom& g, int q, int gi, bool face, int& blk, int& loc) {
+  const int N = g.N[q];
+  int m = gi;
+  const bool inside = (m >= 0 && m < N) || (face && m == N);
+  if (!inside) {
+    if (m < 0) {
+      if (g.bc[2 * q] == BC_PERIODIC) {
+        m %= N;
+        if (m < 0) m += N;
+      } else {
+        m = 0;
+      }
+    } else {
+      if (g.bc[2 * q + 1] == BC_PERIODIC)
+        m %= N;
+      else
+        m = face ? N : N - 1;
+    }
+  }
+  if (face && m == N) {
+    blk = g.nb[q] - 1;
+    loc = g.mb[q] + NG;
+  } else {
+    blk = m / g.mb[q];
+    loc = m - blk * g.mb[q] + NG;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_ghosts(Geom g, double* U, double* B0, double* B1, double* B2) {
+  const int ex = g.mb[0] + 2 * NG + 1, ey = g.mb[1] + 2 * NG + 1, ez = g.mb[2] + 2 * NG + 1;
+  const long long per = (long long)ex * ey * ez;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per * g.nblk) return;
+  const int b = (int)(t / per);
+  int rem = (int)(t - (long long)b * per);
+  const int li[3] = {rem % ex, (rem / ex) % ey, rem / (ex * ey)};
+  int loc[3];
+  block_loc(g, b, loc);
+  const long long c = cell_off(g, li[2], li[1], li[0]);
+  const int cmax[3] = {g.mb[0] + 2 * NG, g.mb[1] + 2 * NG, g.mb[2] + 2 * NG};
+  // cell-centred conserved variables
+  if (li[0] < cmax[0] && li[1] < cmax[1] && li[2] < cmax[2]) {
+    bool ghost = false;
+    for (int q = 0; q < 3; ++q) ghost |= (li[q] < NG || li[q] >= NG + g.mb[q]);
+    if (ghost) {
+      int sb[3], sl[3];
+      for (int q = 0; q < 3; ++q) source_of(g, q, loc[q] * g.mb[q] + li[q] - NG, false, sb[q], sl[q]);
+      const int src = (sb[2] * g.nb[1] + sb[1]) * g.nb[0] + sb[0];
+      const long long sc = cell_off(g, sl[2], sl[1], sl[0]);
+      const double* Us = U + (long long)src * 5 * g.box + sc;
+      double* Ud = U + (long long)b * 5 * g.box + c;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Ud[(long long)v * g.box] = Us[(long long)v * g.box];
+    }
+  }
+  // face-centred field
+  double* Bf[3] = {B0, B1, B2};
+#pragma unroll
+  for (int fd = 0; fd < 3; ++fd) {
+    bool valid = true, ghost = false;
+    for (int q = 0; q < 3; ++q) {
+      const int hi_valid = (q == fd) ? cmax[q] : cmax[q] - 1;
+      const int hi_active = (q == fd) ? NG + g.mb[q] : NG + g.mb[q] - 1;
+      valid &= li[q] <= hi_valid;
+      ghost |= (li[q] < NG || li[q] > hi_active);
+    }
+    if (!valid || !ghost) continue;
+    int sb[3], sl[3];
+    for (int q = 0; q < 3; ++q) source_of(g, q, loc[q] * g.mb[q] + li[q] - NG, q == fd, sb[q], sl[q]);
+    const int src = (sb[2] * g.nb[1] + sb[1]) * g.nb[0] + sb[0];
+    Bf[fd][(long long)b * g.box + c] = Bf[fd][(long long)src * g.box + cell_off(g, sl[2], sl[1], sl[0])];
+  }
+}
+
+cudaError_t launch_ghosts(const Geom& g, const Arrays& a, int reg, cudaStream_t st) {
+  const long long per = (long long)(g.mb[0] + 2 * NG + 1) * (g.mb[1] + 2 * NG + 1) * (g.mb[2] + 2 * NG + 1);
+  k_ghosts<<<grid_for(per * g.nblk, 256), 256, 0, st>>>(g, a.u[reg], a.b[reg][0], a.b[reg][1], a.b[reg][2]);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Upwind CT corner EMFs (Sec. 3.1 / Sec. 2.1.1).  Edge family e (E1 along x, E2 along y, E3 along z),
+// transverse directions a = e+1, b = e+2.  Face EMFs of that component: -F_a[B_t1] on a-faces and
+// +F_b[B_t2] on b-faces (E = -v x B); cell EMFs from the primitives.  One thread per corner node.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ double cell_emf(int e, const double* Wc, long long box) {
+  const double vx = Wc[box], vy = Wc[2 * box], vz = Wc[3 * box];
+  const double bx = Wc[5 * box], by = Wc[6 * box], bz = Wc[7 * box];
+  if (e == 0) return vz * by - vy * bz;
+  if (e == 1) return vx * bz - vz * bx;
+  return vy * bx - vx * by;
+}
+
+__global__ void __launch_bounds__(256) k_emf(Geom g, const double* __restrict__ W, const double* __restrict__ F0,
+                                             const double* __restrict__ F1, const double* __restrict__ F2,
+                                             double* __restrict__ E0, double* __restrict__ E1, double* __restrict__ E2) {
+  const int ex = g.mb[0] + 1, ey = g.mb[1] + 1, ez = g.mb[2] + 1;
+  const long long per = (long long)ex * ey * ez;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per * g.nblk) return;
+  const int b = (int)(t / per);
+  int rem = (int)(t - (long long)b * per);
+  const int li[3] = {rem % ex + NG, (rem / ex) % ey + NG, rem / (ex * ey) + NG};
+  const long long c = cell_off(g, li[2], li[1], li[0]);
+  const long long stride[3] = {1LL, (long long)g.sx, (long long)g.sx * g.sy};
+  const double* F[3] = {F0, F1, F2};
+  double* E[3] = {E0, E1, E2};
+  const double* Wb = W + (long long)b * 8 * g.box;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    if (li[e] > NG + g.mb[e] - 1) continue;
+    const int a = (e + 1) % 3, bq = (e + 2) % 3;
+    const long long sa = stride[a], sb = stride[bq];
+    const double* Fa = F[a] + (long long)b * 7 * g.box;
+    const double* Fb = F[bq] + (long long)b * 7 * g.box;
+    double ea[2], eb[2], ec[4], ma[2], mb[2];
+    ea[0] = -Fa[5 * g.box + c - sb];
+    ea[1] = -Fa[5 * g.box + c];
+    eb[0] = Fb[6 * g.box + c - sa];
+    eb[1] = Fb[6 * g.box + c];
+    ma[0] = Fa[c - sb];
+    ma[1] = Fa[c];
+    mb[0] = Fb[c - sa];
+    mb[1] = Fb[c];
+    ec[0] = cell_emf(e, Wb + c - sa - sb, g.box);
+    ec[1] = cell_emf(e, Wb + c - sb, g.box);
+    ec[2] = cell_emf(e, Wb + c - sa, g.box);
+    ec[3] = cell_emf(e, Wb + c, g.box);
+    E[e][(long long)b * g.box + c] = ct_corner(ea, eb, ec, ma, mb);
+  }
+}
+
+cudaError_t launch_emfs(const Geom& g, const Arrays& a, cudaStream_t st) {
+  const long long per = (long long)(g.mb[0] + 1) * (g.mb[1] + 1) * (g.mb[2] + 1);
+  k_emf<<<grid_for(per * g.nblk, 256), 256, 0, st>>>(g, a.w, a.f[0], a.f[1], a.f[2], a.e[0], a.e[1], a.e[2]);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Register update of one stage (Sec. 3.2.3, eq. rk-2s with gamma_s = {0, 1}):
+//   U_out = U_base + h L,  L = -[(F_x(i+1/2) - F_x(i-1/2))/dx + (F_y..)/dy + (F_z..)/dz]
+//   B_out = B_base - h curl_h E   (B1 uses E3 along y and E2 along z, cyclically).
+// U_base / U_out may alias (the corrector updates u^n in place), so no __restrict__ here.
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_update(Geom g, const double* Ubase, double* Uout, const double* Bb0,
+                                                const double* Bb1, const double* Bb2, double* Bo0, double* Bo1,
+                                                double* Bo2, const double* __restrict__ F0, const double* __restrict__ F1,
+                                                const double* __restrict__ F2, const double* __restrict__ E0,
+                                                const double* __restrict__ E1, const double* __restrict__ E2, double h) {
+  const int ex = g.mb[0] + 1, ey = g.mb[1] + 1, ez = g.mb[2] + 1;
+  const long long per = (long long)ex * ey * ez;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per * g.nblk) return;
+  const int b = (int)(t / per);
+  int rem = (int)(t - (long long)b * per);
+  const int li[3] = {rem % ex + NG, (rem / ex) % ey + NG, rem / (ex * ey) + NG};
+  const long long c = cell_off(g, li[2], li[1], li[0]);
+  const long long stride[3] = {1LL, (long long)g.sx, (long long)g.sx * g.sy};
+  const bool inside[3] = {li[0] < NG + g.mb[0], li[1] < NG + g.mb[1], li[2] < NG + g.mb[2]};
+  if (inside[0] && inside[1] && inside[2]) {
+    const double* F[3] = {F0 + (long long)b * 7 * g.box + c, F1 + (long long)b * 7 * g.box + c,
+                          F2 + (long long)b * 7 * g.box + c};
+    const long long ub = (long long)b * 5 * g.box + c;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double dfl[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        int comp;
+        if (v == 0)
+          comp = 0;
+        else if (v == 4)
+          comp = 4;
+        else {
+          const int m = v - 1;
+          comp = (m == d) ? 1 : ((m == (d + 1) % 3) ? 2 : 3);
+        }
+        const double* fp = F[d] + (long long)comp * g.box;
+        dfl[d] = (fp[stride[d]] - fp[0]) * g.idx[d];
+      }
+      const double L = -((dfl[0] + dfl[1]) + dfl[2]);
+      Uout[ub + (long long)v * g.box] = Ubase[ub + (long long)v * g.box] + h * L;
+    }
+  }
+  const double* Bb[3] = {Bb0, Bb1, Bb2};
+  double* Bo[3] = {Bo0, Bo1, Bo2};
+  const double* E[3] = {E0 + (long long)b * g.box + c, E1 + (long long)b * g.box + c, E2 + (long long)b * g.box + c};
+#pragma unroll
+  for (int fd = 0; fd < 3; ++fd) {
+    const int a = (fd + 1) % 3, bq = (fd + 2) % 3;
+    if (!inside[a] || !inside[bq]) continue;
+    const double curl = (E[bq][stride[a]] - E[bq][0]) * g.idx[a] - (E[a][stride[bq]] - E[a][0]) * g.idx[bq];
+    const long long o = (long long)b * g.box + c;
+    Bo[fd][o] = Bb[fd][o] + h * (-curl);
+  }
+}
+
+cudaError_t launch_update(const Geom& g, const Arrays& a, int base_reg, int out_reg, double h, cudaStream_t st) {
+  const long long per = (long long)(g.mb[0] + 1) * (g.mb[1] + 1) * (g.mb[2] + 1);
+  k_update<<<grid_for(per * g.nblk, 256), 256, 0, st>>>(
+      g, a.u[base_reg], a.u[out_reg], a.b[base_reg][0], a.b[base_reg][1], a.b[base_reg][2], a.b[out_reg][0],
+      a.b[out_reg][1], a.b[out_reg][2], a.f[0], a.f[1], a.f[2], a.e[0], a.e[1], a.e[2], h);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Global-array I/O.  Threads cover (block, k, j, i) with i, j, k in [0, mb] (faces need the +1).
+// ------------------------------------------------------------------------------------------------
+struct IoIdx {
+  int b, li[3], gi[3];
+};
+
+__device__ __forceinline__ bool io_index(const Geom& g, IoIdx& x) {
+  const int ex = g.mb[0] + 1, ey = g.mb[1] + 1, ez = g.mb[2] + 1;
+  const long long per = (long long)ex * ey * ez;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per * g.nblk) return false;
+  x.b = (int)(t / per);
+  int rem = (int)(t - (long long)x.b * per);
+  x.li[0] = rem % ex;
+  x.li[1] = (rem / ex) % ey;
+  x.li[2] = rem / (ex * ey);
+  int loc[3];
+  block_loc(g, x.b, loc);
+  for (int q = 0; q < 3; ++q) x.gi[q] = loc[q] * g.mb[q] + x.li[q];
+  return true;
+}
+
+static inline unsigned io_grid(const Geom& g) {
+  return grid_for((long long)(g.mb[0] + 1) * (g.mb[1] + 1) * (g.mb[2] + 1) * g.nblk, 256);
+}
+
+__global__ void __launch_bounds__(256) k_scatter_prims(Geom g, double* U, double* B0, double* B1, double* B2,
+                                                       const double* __restrict__ w, const double* __restrict__ b1,
+                                                       const double* __restrict__ b2, const double* __restrict__ b3) {
+  IoIdx x;
+  if (!io_index(g, x)) return;
+  const int NX = g.N[0], NY = g.N[1], NZ = g.N[2];
+  const long long c = cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG);
+  const long long o = (long long)x.b * g.box + c;
+  const bool in[3] = {x.li[0] < g.mb[0], x.li[1] < g.mb[1], x.li[2] < g.mb[2]};
+  const long long f1 = ((long long)x.gi[2] * NY + x.gi[1]) * (NX + 1) + x.gi[0];
+  const long long f2 = ((long long)x.gi[2] * (NY + 1) + x.gi[1]) * NX + x.gi[0];
+  const long long f3 = ((long long)x.gi[2] * NY + x.gi[1]) * NX + x.gi[0];
+  if (in[1] && in[2]) B0[o] = b1[f1];
+  if (in[0] && in[2]) B1[o] = b2[f2];
+  if (in[0] && in[1]) B2[o] = b3[f3];
+  if (in[0] && in[1] && in[2]) {
+    const long long n = (long long)NX * NY * NZ;
+    const long long gc = ((long long)x.gi[2] * NY + x.gi[1]) * NX + x.gi[0];
+    const double d = w[gc], vx = w[n + gc], vy = w[2 * n + gc], vz = w[3 * n + gc], p = w[4 * n + gc];
+    const double bcx = 0.5 * (b1[f1] + b1[f1 + 1]);
+    const double bcy = 0.5 * (b2[f2] + b2[f2 + NX]);
+    const double bcz = 0.5 * (b3[f3] + b3[f3 + (long long)NX * NY]);
+    double* Ub = U + (long long)x.b * 5 * g.box + c;
+    Ub[0] = d;
+    Ub[g.box] = d * vx;
+    Ub[2 * g.box] = d * vy;
+    Ub[3 * g.box] = d * vz;
+    Ub[4 * g.box] = p * g.igm1 + 0.5 * d * ((vx * vx + vy * vy) + vz * vz) + 0.5 * ((bcx * bcx + bcy * bcy) + bcz * bcz);
+  }
+}
+
+cudaError_t launch_scatter_prims(const Geom& g, const Arrays& a, const double* w, const double* b1, const double* b2,
+                                 const double* b3, cudaStream_t st) {
+  k_scatter_prims<<<io_grid(g), 256, 0, st>>>(g, a.u[0], a.b[0][0], a.b[0][1], a.b[0][2], w, b1, b2, b3);
+  return cudaGetLastError();
+}
+
+// periodic duplicate faces (face N and face 0) must be bitwise equal
+__global__ void k_check_periodic(Geom g, const double* b1, const double* b2, const double* b3, unsigned long long* cnt) {
+  const int NX = g.N[0], NY = g.N[1], NZ = g.N[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nxy = (long long)NX * NY, nyz = (long long)NY * NZ, nxz = (long long)NX * NZ;
+  if (t < nyz && g.bc[0] == BC_PERIODIC) {
+    const long long r = t * (NX + 1);
+    if (b1[r] != b1[r + NX]) atomicAdd(cnt, 1ULL);
+  }
+  if (t < nxz && g.bc[2] == BC_PERIODIC) {
+    const long long kk = t / NX, ii = t % NX;
+    const long long r0 = (kk * (NY + 1)) * NX + ii;
+    if (b2[r0] != b2[r0 + (long long)NY * NX]) atomicAdd(cnt, 1ULL);
+  }
+  if (t < nxy && g.bc[4] == BC_PERIODIC) {
+    if (b3[t] != b3[t + (long long)NZ * nxy]) atomicAdd(cnt, 1ULL);
+  }
+}
+
+cudaError_t launch_check_periodic(const Geom& g, const double* b1, const double* b2, const double* b3,
+                                  unsigned long long* count, cudaStream_t st) {
+  long long n = (long long)g.N[1] * g.N[2];
+  n = n > (long long)g.N[0] * g.N[2] ? n : (long long)g.N[0] * g.N[2];
+  n = n > (long long)g.N[0] * g.N[1] ? n : (long long)g.N[0] * g.N[1];
+  k_check_periodic<<<grid_for(n, 256), 256, 0, st>>>(g, b1, b2, b3, count);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_gather_cons(Geom g, const double* __restrict__ U, const double* __restrict__ B0,
+                                                     const double* __restrict__ B1, const double* __restrict__ B2,
+                                                     double* u, double* b1, double* b2, double* b3) {
+  IoIdx x;
+  if (!io_index(g, x)) return;
+  const int NX = g.N[0], NY = g.N[1], NZ = g.N[2];
+  const long long c = cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG);
+  const long long o = (long long)x.b * g.box + c;
+  const bool in[3] = {x.li[0] < g.mb[0], x.li[1] < g.mb[1], x.li[2] < g.mb[2]};
+  const bool own[3] = {in[0] || x.gi[0] == NX, in[1] || x.gi[1] == NY, in[2] || x.gi[2] == NZ};
+  if (b1 && own[0] && in[1] && in[2]) b1[((long long)x.gi[2] * NY + x.gi[1]) * (NX + 1) + x.gi[0]] = B0[o];
+  if (b2 && own[1] && in[0] && in[2]) b2[((long long)x.gi[2] * (NY + 1) + x.gi[1]) * NX + x.gi[0]] = B1[o];
+  if (b3 && own[2] && in[0] && in[1]) b3[((long long)x.gi[2] * NY + x.gi[1]) * NX + x.gi[0]] = B2[o];
+  if (u && in[0] && in[1] && in[2]) {
+    const long long n = (long long)NX * NY * NZ;
+    const long long gc = ((long long)x.gi[2] * NY + x.gi[1]) * NX + x.gi[0];
+    const double* Ub = U + (long long)x.b * 5 * g.box + c;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) u[v * n + gc] = Ub[(long long)v * g.box];
+  }
+}
+
+cudaError_t launch_gather_cons(const Geom& g, const Arrays& a, double* u, double* b1, double* b2, double* b3,
+                               cudaStream_t st) {
+  k_gather_cons<<<io_grid(g), 256, 0, st>>>(g, a.u[0], a.b[0][0], a.b[0][1], a.b[0][2], u, b1, b2, b3);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_gather_prims(Geom g, const double* __restrict__ W, double* w) {
+  IoIdx x;
+  if (!io_index(g, x)) return;
+  if (x.li[0] >= g.mb[0] || x.li[1] >= g.mb[1] || x.li[2] >= g.mb[2]) return;
+  const int NX = g.N[0], NY = g.N[1], NZ = g.N[2];
+  const long long n = (long long)NX * NY * NZ;
+  const long long gc = ((long long)x.gi[2] * NY + x.gi[1]) * NX + x.gi[0];
+  const double* Wb = W + (long long)x.b * 8 * g.box + cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG);
+#pragma unroll
+  for (int v = 0; v < 8; ++v) w[v * n + gc] = Wb[(long long)v * g.box];
+}
+
+cudaError_t launch_gather_prims(const Geom& g, const Arrays& a, double* w, cudaStream_t st) {
+  k_gather_prims<<<io_grid(g), 256, 0, st>>>(g, a.w, w);
+  return cudaGetLastError();
+}
+
+// fluxes of sweep `dir` on the global face grid [7][..]; a face on a block boundary is taken from the
+// block where it is the lower face (global face N from the last block)
+__global__ void __launch_bounds__(256) k_gather_fluxes(Geom g, int dir, const double* __restrict__ F, double* out) {
+  IoIdx x;
+  if (!io_index(g, x)) return;
+  int gd[3] = {g.N[0], g.N[1], g.N[2]};
+  gd[dir] += 1;
+  for (int q = 0; q < 3; ++q) {
+    if (q == dir) {
+      if (x.li[q] == g.mb[q] && x.gi[q] != g.N[q]) return;
+    } else if (x.li[q] >= g.mb[q]) {
+      return;
+    }
+  }
+  const long long nf = (long long)gd[0] * gd[1] * gd[2];
+  const long long gf = ((long long)x.gi[2] * gd[1] + x.gi[1]) * gd[0] + x.gi[0];
+  const double* Fb = F + (long long)x.b * 7 * g.box + cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG);
+#pragma unroll
+  for (int n = 0; n < 7; ++n) out[n * nf + gf] = Fb[(long long)n * g.box];
+}
+
+cudaError_t launch_gather_fluxes(const Geom& g, const Arrays& a, int dir, double* out, cudaStream_t st) {
+  k_gather_fluxes<<<io_grid(g), 256, 0, st>>>(g, dir, a.f[dir], out);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_gather_emfs(Geom g, int e, const double* __restrict__ E, double* out) {
+  IoIdx x;
+  if (!io_index(g, x)) return;
+  int gd[3] = {g.N[0] + 1, g.N[1] + 1, g.N[2] + 1};
+  gd[e] -= 1;
+  for (int q = 0; q < 3; ++q) {
+    if (q == e) {
+      if (x.li[q] >= g.mb[q]) return;
+    } else if (x.li[q] == g.mb[q] && x.gi[q] != g.N[q]) {
+      return;
+    }
+  }
+  const long long gf = ((long long)x.gi[2] * gd[1] + x.gi[1]) * gd[0] + x.gi[0];
+  out[gf] = E[(long long)x.b * g.box + cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG)];
+}
+
+cudaError_t launch_gather_emfs(const Geom& g, const Arrays& a, int dir, double* out, cudaStream_t st) {
+  k_gather_emfs<<<io_grid(g), 256, 0, st>>>(g, dir, a.e[dir], out);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Diagnostics: fixed grid, grid-stride loops, per-CTA partials, then one CTA combines the partials in a
+// fixed order (deterministic results).
+// ------------------------------------------------------------------------------------------------
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ void active_cell(const Geom& g, long long t, int& b, long long& c) {
+  const long long per = (long long)g.mb[0] * g.mb[1] * g.mb[2];
+  b = (int)(t / per);
+  int rem = (int)(t - (long long)b * per);
+  const int i = rem % g.mb[0] + NG;
+  rem /= g.mb[0];
+  const int j = rem % g.mb[1] + NG;
+  const int k = rem / g.mb[1] + NG;
+  c = cell_off(g, k, j, i);
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_divb_partial(Geom g, const double* __restrict__ B0,
+                                                              const double* __restrict__ B1,
+                                                              const double* __restrict__ B2, double* part) {
+  const long long n = (long long)g.mb[0] * g.mb[1] * g.mb[2] * g.nblk;
+  double mx = 0.0, s2 = 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    int b;
+    long long c;
+    active_cell(g, t, b, c);
+    const long long o = (long long)b * g.box + c;
+    const long long sy = g.sx, sz = (long long)g.sx * g.sy;
+    const double dv = (B0[o + 1] - B0[o]) * g.idx[0] + (B1[o + sy] - B1[o]) * g.idx[1] + (B2[o + sz] - B2[o]) * g.idx[2];
+    mx = fmax(mx, fabs(dv));
+    const double bx = 0.5 * (B0[o] + B0[o + 1]), by = 0.5 * (B1[o] + B1[o + sy]), bz = 0.5 * (B2[o] + B2[o + sz]);
+    s2 += bx * bx + by * by + bz * bz;
+  }
+  __shared__ double smx[RED_THREADS], ss[RED_THREADS];
+  smx[threadIdx.x] = mx;
+  ss[threadIdx.x] = s2;
+  __syncthreads();
+  for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      smx[threadIdx.x] = fmax(smx[threadIdx.x], smx[threadIdx.x + o]);
+      ss[threadIdx.x] += ss[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = smx[0];
+    part[2 * blockIdx.x + 1] = ss[0];
+  }
+}
+
+__global__ void k_combine(const double* part, int nparts, int width, unsigned max_mask, double* out) {
+  // thread v combines component v over the partials, sequentially (max, or a Neumaier sum)
+  const int v = threadIdx.x;
+  if (v >= width) return;
+  if ((max_mask >> v) & 1u) {
+    double m = 0.0;
+    for (int q = 0; q < nparts; ++q) m = fmax(m, part[q * width + v]);
+    out[v] = m;
+  } else {
+    double s = 0.0, comp = 0.0;
+    for (int q = 0; q < nparts; ++q) {
+      const double y = part[q * width + v];
+      const double t = s + y;
+      if (fabs(s) >= fabs(y))
+        comp += (s - t) + y;
+      else
+        comp += (y - t) + s;
+      s = t;
+    }
+    out[v] = s + comp;
+  }
+}
+
+cudaError_t launch_divb(const Geom& g, const Arrays& a, double* result2, cudaStream_t st) {
+  k_divb_partial<<<a.red_ctas, RED_THREADS, 0, st>>>(g, a.b[0][0], a.b[0][1], a.b[0][2], a.red);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_combine<<<1, 32, 0, st>>>(a.red, a.red_ctas, 2, 1u, result2);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_totals_partial(Geom g, const double* __restrict__ U,
+                                                                const double* __restrict__ B0,
+                                                                const double* __restrict__ B1,
+                                                                const double* __restrict__ B2, double* part) {
+  const long long n = (long long)g.mb[0] * g.mb[1] * g.mb[2] * g.nblk;
+  const double dv = g.dx[0] * g.dx[1] * g.dx[2];
+  double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    int b;
+    long long c;
+    active_cell(g, t, b, c);
+    const double* Ub = U + (long long)b * 5 * g.box + c;
+    for (int v = 0; v < 5; ++v) s[v] += Ub[(long long)v * g.box] * dv;
+    const long long o = (long long)b * g.box + c;
+    s[5] += 0.5 * (B0[o] + B0[o + 1]) * dv;
+    s[6] += 0.5 * (B1[o] + B1[o + g.sx]) * dv;
+    s[7] += 0.5 * (B2[o] + B2[o + (long long)g.sx * g.sy]) * dv;
+  }
+  __shared__ double sh[8][RED_THREADS];
+  for (int v = 0; v < 8; ++v) sh[v][threadIdx.x] = s[v];
+  __syncthreads();
+  for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o)
+      for (int v = 0; v < 8; ++v) sh[v][threadIdx.x] += sh[v][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 8) part[8 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+cudaError_t launch_totals(const Geom& g, const Arrays& a, double* result8, cudaStream_t st) {
+  k_totals_partial<<<a.red_ctas, RED_THREADS, 0, st>>>(g, a.u[0], a.b[0][0], a.b[0][1], a.b[0][2], a.red);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_combine<<<1, 32, 0, st>>>(a.red, a.red_ctas, 8, 0u, result8);
+  return cudaGetLastError();
+}
+
+}  // namespace vl2

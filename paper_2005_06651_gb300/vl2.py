@@ -1,0 +1,341 @@
+"""Python binding of the C ABI in include/vl2mhd.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library libvl2mhd.so; this module only converts arguments.
+PyTorch provides the device workspace and the stream.  There is no CPU fallback: if the compiled
+library is missing, loading it raises.
+
+The module-level functions carry the ABI's names (mesh_create, block_layout, set_prims, step,
+fill_ghosts, new_dt, get_cons, get_prims, divb_norm, totals); `Mesh` bundles them as methods.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libvl2mhd.so")
+
+VL2_OK, VL2_E_ARG, VL2_E_CUDA, VL2_E_NONPHYS, VL2_E_TIMEOUT, VL2_E_STATE, VL2_E_NOMEM = range(7)
+HLLE, HLLD = 0, 1
+PERIODIC, OUTFLOW = 0, 1
+FP64, MIXED = 0, 1
+HOST, DEVICE = 0, 1
+DC, PLM = 0, 1
+
+STATUS_NAMES = {0: "VL2_OK", 1: "VL2_E_ARG", 2: "VL2_E_CUDA", 3: "VL2_E_NONPHYS", 4: "VL2_E_TIMEOUT",
+                5: "VL2_E_STATE", 6: "VL2_E_NOMEM"}
+
+
+class VL2Error(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int * 3), ("mb", ctypes.c_int * 3), ("ng", ctypes.c_int),
+                ("xmin", ctypes.c_double * 3), ("xmax", ctypes.c_double * 3), ("gamma", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("riemann", ctypes.c_int), ("precision", ctypes.c_int),
+                ("bc", ctypes.c_int * 6), ("dfloor", ctypes.c_double), ("pfloor", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
+
+
+class Layout(ctypes.Structure):
+    _fields_ = [("nblocks", ctypes.c_int), ("nb", ctypes.c_int * 3), ("mb", ctypes.c_int * 3), ("ng", ctypes.c_int),
+                ("sx", ctypes.c_int), ("sy", ctypes.c_int), ("sz", ctypes.c_int),
+                ("block_stride_vars", ctypes.c_longlong), ("block_loc", ctypes.POINTER(ctypes.c_int)),
+                ("neighbor", ctypes.POINTER(ctypes.c_int)), ("u", ctypes.c_void_p), ("b", ctypes.c_void_p * 3)]
+
+
+_lib = None
+EXPORTS = ["vl2_workspace_bytes", "vl2_mesh_create", "vl2_mesh_destroy", "vl2_block_layout", "vl2_set_prims",
+           "vl2_fill_ghosts", "vl2_step", "vl2_new_dt", "vl2_get_cons", "vl2_get_prims", "vl2_divb_norm",
+           "vl2_totals", "vl2_floor_count", "vl2_debug_fluxes", "vl2_debug_emfs", "vl2_profile",
+           "vl2_profile_read", "vl2_launch_count", "vl2_last_error"]
+K_PRIM, K_GHOSTS, K_FLUX_DC, K_FLUX_PLM, K_EMF, K_UPDATE = range(6)
+KERNEL_KINDS = {K_PRIM: "prim", K_GHOSTS: "ghosts", K_FLUX_DC: "flux_dc", K_FLUX_PLM: "flux_plm", K_EMF: "emf",
+                K_UPDATE: "update"}
+
+
+def load(path: str = LIB_PATH):
+    """Load libvl2mhd.so (raises if it has not been built: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libvl2mhd.so not found at %s; build it with paper_2005_06651_gb300.build.build()" % path)
+    L = ctypes.CDLL(path)
+    vp, dp, sz = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t
+    L.vl2_workspace_bytes.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]
+    L.vl2_mesh_create.argtypes = [ctypes.POINTER(Params), vp, sz, ctypes.POINTER(ctypes.c_void_p)]
+    L.vl2_mesh_destroy.argtypes = [vp]
+    L.vl2_block_layout.argtypes = [vp, ctypes.POINTER(Layout)]
+    L.vl2_set_prims.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int]
+    L.vl2_fill_ghosts.argtypes = [vp]
+    L.vl2_step.argtypes = [vp, ctypes.c_double]
+    L.vl2_new_dt.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.vl2_get_cons.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int]
+    L.vl2_get_prims.argtypes = [vp, dp, ctypes.c_int]
+    L.vl2_divb_norm.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.vl2_totals.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.vl2_floor_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.vl2_debug_fluxes.argtypes = [vp, ctypes.c_int, dp, dp, dp, ctypes.c_int]
+    L.vl2_debug_emfs.argtypes = [vp, ctypes.c_int, dp, dp, dp, ctypes.c_int]
+    L.vl2_profile.argtypes = [vp, ctypes.c_int]
+    L.vl2_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
+                                   ctypes.POINTER(ctypes.c_longlong)]
+    L.vl2_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.vl2_last_error.argtypes = [vp]
+    L.vl2_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "vl2_last_error":
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status, mesh_handle=None, allow=()):
+    if status != VL2_OK and status not in allow:
+        msg = load().vl2_last_error(mesh_handle)
+        raise VL2Error(status, msg.decode() if msg else "")
+    return status
+
+
+def _ptr(a):
+    """(pointer, where) for a numpy array or a torch tensor (CPU or CUDA), without copying."""
+    if a is None:
+        return None, HOST
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous float64")
+        return a.ctypes.data, HOST
+    import torch
+
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError("tensors must be contiguous float64")
+        return a.data_ptr(), (DEVICE if a.is_cuda else HOST)
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _where_of(ptrs):
+    wheres = {w for p, w in ptrs if p is not None}
+    if len(wheres) > 1:
+        raise ValueError("all buffers of one call must live on the same side (host or device)")
+    return wheres.pop() if wheres else HOST
+
+
+class Mesh:
+    """A mesh of equal-size MeshBlocks on one CUDA device; all methods call the C ABI."""
+
+    def __init__(self, nx, mb, xmin=(0.0, 0.0, 0.0), xmax=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, cfl=0.3,
+                 riemann=HLLD, bc=(PERIODIC,) * 6, dfloor=1e-12, pfloor=1e-12, precision=FP64, device=None,
+                 stream=None):
+        import torch
+
+        L = load()
+        self.nx, self.mb = tuple(int(v) for v in nx), tuple(int(v) for v in mb)
+        self.xmin, self.xmax = tuple(float(v) for v in xmin), tuple(float(v) for v in xmax)
+        self.gamma, self.cfl = float(gamma), float(cfl)
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        p = Params()
+        p.nx[:] = self.nx
+        p.mb[:] = self.mb
+        p.ng = 2
+        p.xmin[:] = self.xmin
+        p.xmax[:] = self.xmax
+        p.gamma, p.cfl = self.gamma, self.cfl
+        p.riemann, p.precision = int(riemann), int(precision)
+        p.bc[:] = tuple(int(v) for v in bc)
+        p.dfloor, p.pfloor = float(dfloor), float(pfloor)
+        p.stream = ctypes.c_void_p(stream.cuda_stream)
+        self._params = p
+        nbytes = ctypes.c_size_t()
+        _check(L.vl2_workspace_bytes(ctypes.byref(p), ctypes.byref(nbytes)))
+        self.workspace_bytes = int(nbytes.value)
+        self._ws = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws.data_ptr()
+        aligned = (base + 255) & ~255
+        h = ctypes.c_void_p()
+        _check(L.vl2_mesh_create(ctypes.byref(p), ctypes.c_void_p(aligned), ctypes.c_size_t(self.workspace_bytes),
+                                 ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_problem(cls, prob, **kw):
+        m = cls(prob.nx, kw.pop("mb", prob.mb), prob.xmin, prob.xmax, prob.gamma, bc=prob.bc, **kw)
+        m.set_prims(prob.w, prob.b1, prob.b2, prob.b3)
+        return m
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load().vl2_mesh_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- shapes ----
+    @property
+    def shape(self):
+        return (self.nx[2], self.nx[1], self.nx[0])
+
+    def face_shapes(self):
+        NX, NY, NZ = self.nx
+        return (NZ, NY, NX + 1), (NZ, NY + 1, NX), (NZ + 1, NY, NX)
+
+    @property
+    def ncells(self):
+        return self.nx[0] * self.nx[1] * self.nx[2]
+
+    # ---- ABI calls ----
+    def set_prims(self, w, b1, b2, b3):
+        keep = [np.ascontiguousarray(x, dtype=np.float64) if isinstance(x, np.ndarray) else x for x in (w, b1, b2, b3)]
+        ptrs = [_ptr(x) for x in keep]
+        where = _where_of(ptrs)
+        _check(load().vl2_set_prims(self._h, *[ctypes.c_void_p(p) for p, _ in ptrs], where), self._h)
+
+    def fill_ghosts(self):
+        _check(load().vl2_fill_ghosts(self._h), self._h)
+
+    def step(self, dt):
+        _check(load().vl2_step(self._h, float(dt)), self._h)
+
+    def new_dt(self, allow_nonphys=False):
+        out = ctypes.c_double()
+        _check(load().vl2_new_dt(self._h, ctypes.byref(out)), self._h, allow=(VL2_E_NONPHYS,) if allow_nonphys else ())
+        return out.value
+
+    def get_cons(self, out=None):
+        """Conserved state (u, b1, b2, b3); into `out` (numpy or torch, host or device) or new numpy arrays."""
+        if out is None:
+            out = (np.empty((5,) + self.shape), *[np.empty(s) for s in self.face_shapes()])
+        ptrs = [_ptr(x) for x in out]
+        where = _where_of(ptrs)
+        _check(load().vl2_get_cons(self._h, *[ctypes.c_void_p(p) if p else None for p, _ in ptrs], where), self._h)
+        return out
+
+    def get_prims(self, out=None):
+        if out is None:
+            out = np.empty((8,) + self.shape)
+        p, where = _ptr(out)
+        _check(load().vl2_get_prims(self._h, ctypes.c_void_p(p), where), self._h)
+        return out
+
+    def divb_norm(self):
+        out = ctypes.c_double()
+        _check(load().vl2_divb_norm(self._h, ctypes.byref(out)), self._h)
+        return out.value
+
+    def totals(self):
+        out = (ctypes.c_double * 8)()
+        _check(load().vl2_totals(self._h, out), self._h)
+        return np.array(out[:])
+
+    def floor_count(self):
+        out = ctypes.c_longlong()
+        _check(load().vl2_floor_count(self._h, ctypes.byref(out)), self._h)
+        return out.value
+
+    def block_layout(self):
+        lay = Layout()
+        _check(load().vl2_block_layout(self._h, ctypes.byref(lay)), self._h)
+        n = lay.nblocks
+        return {"nblocks": n, "nb": tuple(lay.nb), "mb": tuple(lay.mb), "ng": lay.ng,
+                "strides": (lay.sx, lay.sy, lay.sz), "block_stride_vars": lay.block_stride_vars,
+                "block_loc": np.ctypeslib.as_array(lay.block_loc, shape=(n, 3)).copy(),
+                "neighbor": np.ctypeslib.as_array(lay.neighbor, shape=(n, 27)).copy(),
+                "u": lay.u, "b": tuple(lay.b)}
+
+    def profile(self, enable=True):
+        _check(load().vl2_profile(self._h, int(bool(enable))), self._h)
+
+    def profile_read(self):
+        """{kind: (ms, launches, units)} accumulated since the last read (resets)."""
+        out = {}
+        for k, name in KERNEL_KINDS.items():
+            ms, n, u = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
+            _check(load().vl2_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(u)), self._h)
+            out[name] = (ms.value, n.value, u.value)
+        return out
+
+    def launch_count(self):
+        n = ctypes.c_longlong()
+        _check(load().vl2_launch_count(self._h, ctypes.byref(n)), self._h)
+        return n.value
+
+    def debug_fluxes(self, recon):
+        NX, NY, NZ = self.nx
+        fx, fy, fz = np.empty((7, NZ, NY, NX + 1)), np.empty((7, NZ, NY + 1, NX)), np.empty((7, NZ + 1, NY, NX))
+        _check(load().vl2_debug_fluxes(self._h, int(recon), *[ctypes.c_void_p(a.ctypes.data) for a in (fx, fy, fz)],
+                                       HOST), self._h)
+        return fx, fy, fz
+
+    def debug_emfs(self, recon):
+        NX, NY, NZ = self.nx
+        e1, e2, e3 = np.empty((NZ + 1, NY + 1, NX)), np.empty((NZ + 1, NY, NX + 1)), np.empty((NZ, NY + 1, NX + 1))
+        _check(load().vl2_debug_emfs(self._h, int(recon), *[ctypes.c_void_p(a.ctypes.data) for a in (e1, e2, e3)],
+                                     HOST), self._h)
+        return e1, e2, e3
+
+    def run(self, t_end, max_steps=1_000_000):
+        """Advance to t_end with the CFL step; the last step is clipped to land on t_end."""
+        t, n = 0.0, 0
+        while t < t_end and n < max_steps:
+            dt = self.new_dt()
+            if t + dt > t_end:
+                dt = t_end - t
+            self.step(dt)
+            t += dt
+            n += 1
+        return n
+
+
+# ---- ABI-named module functions ----
+def mesh_create(nx, mb, **kw):
+    return Mesh(nx, mb, **kw)
+
+
+def block_layout(mesh):
+    return mesh.block_layout()
+
+
+def set_prims(mesh, w, b1, b2, b3):
+    return mesh.set_prims(w, b1, b2, b3)
+
+
+def fill_ghosts(mesh):
+    return mesh.fill_ghosts()
+
+
+def step(mesh, dt):
+    return mesh.step(dt)
+
+
+def new_dt(mesh):
+    return mesh.new_dt()
+
+
+def get_cons(mesh, out=None):
+    return mesh.get_cons(out)
+
+
+def get_prims(mesh, out=None):
+    return mesh.get_prims(out)
+
+
+def divb_norm(mesh):
+    return mesh.divb_norm()
+
+
+def totals(mesh):
+    return mesh.totals()
