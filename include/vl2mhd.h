@@ -184,6 +184,30 @@ vl2_status vl2_profile_read(vl2_mesh* mesh, int kind, double* ms, long long* lau
 /* Number of CUDA kernels this mesh has launched since creation (every launch, profiled or not). */
 vl2_status vl2_launch_count(const vl2_mesh* mesh, long long* n);
 
+/* Largest nz that vl2_totals_noalloc accepts: its fixed scratch holds one row of partial sums per
+ * z-plane (VL2_NOALLOC_MAX_NZ x 8 doubles = 256 KiB per device). */
+#define VL2_NOALLOC_MAX_NZ 4096
+
+/* vl2_totals without any device allocation, for callers that cannot call cudaMalloc (a host that has
+ * given all device memory to its own pool and forbids further allocations, or a pipeline that must not
+ * take the device-wide synchronisation an allocation or free can cause).  The paper has no
+ * counterpart: it is a deployment aid.
+ * Inputs: a state in the global layout as device arrays u [5][NZ][NY][NX] (rho, M1, M2, M3, E) and the
+ * face fields b1, b2, b3; nx = (NX, NY, NZ); dx = cell widths.  Output: out, a device array of 8 doubles,
+ * receives the volume integrals of rho, M1, M2, M3, E, b_c1, b_c2, b_c3 (b_c the mean of the two face
+ * values), with a fixed summation order.  Work is enqueued on `stream` (a cudaStream_t; NULL = legacy
+ * default stream) and the call returns without waiting.
+ * Memory: the partial sums go to a file-scope device array that this library reserves on every GPU that
+ * loads it, until the process exits; nothing is allocated or freed.  The first call on a device looks up
+ * that array's device address with the device current, so make that first call before any stream
+ * capture begins.  All calls share the array: calls whose work overlaps on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller.  Every slot a call reads it first writes, so
+ * no clearing is needed between calls.
+ * Errors: VL2_E_ARG (NULL pointer, non-positive size, nz > VL2_NOALLOC_MAX_NZ), VL2_E_CUDA; the message
+ * is available from vl2_last_error(NULL). */
+vl2_status vl2_totals_noalloc(const double* u, const double* b1, const double* b2, const double* b3,
+                              const int nx[3], const double dx[3], double* out, void* stream);
+
 /* Message of the last failing call on `mesh` (or of the last failing call with no mesh, if NULL).
  * The string is owned by the library. */
 const char* vl2_last_error(const vl2_mesh* mesh);

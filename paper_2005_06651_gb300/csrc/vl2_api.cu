@@ -298,6 +298,10 @@ vl2_status ensure_prims(vl2_mesh* m) {
 
 }  // namespace
 
+namespace vl2 {
+void record_error(const char* msg) { g_err = msg; }
+}  // namespace vl2
+
 extern "C" {
 
 vl2_status vl2_workspace_bytes(const vl2_params* params, size_t* bytes) {

@@ -65,4 +65,7 @@ cudaError_t launch_gather_emfs(const Geom& g, const Arrays& a, int dir, double* 
 cudaError_t launch_divb(const Geom& g, const Arrays& a, double* result2, cudaStream_t st);
 cudaError_t launch_totals(const Geom& g, const Arrays& a, double* result8, cudaStream_t st);
 
+// Sets the message vl2_last_error(NULL) returns (entry points that have no mesh).
+void record_error(const char* msg);
+
 }  // namespace vl2

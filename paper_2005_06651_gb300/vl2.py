@@ -53,7 +53,8 @@ _lib = None
 EXPORTS = ["vl2_workspace_bytes", "vl2_mesh_create", "vl2_mesh_destroy", "vl2_block_layout", "vl2_set_prims",
            "vl2_fill_ghosts", "vl2_step", "vl2_new_dt", "vl2_get_cons", "vl2_get_prims", "vl2_divb_norm",
            "vl2_totals", "vl2_floor_count", "vl2_debug_fluxes", "vl2_debug_emfs", "vl2_profile",
-           "vl2_profile_read", "vl2_launch_count", "vl2_last_error"]
+           "vl2_profile_read", "vl2_launch_count", "vl2_totals_noalloc", "vl2_last_error"]
+NOALLOC_MAX_NZ = 4096
 K_PRIM, K_GHOSTS, K_FLUX_DC, K_FLUX_PLM, K_EMF, K_UPDATE = range(6)
 KERNEL_KINDS = {K_PRIM: "prim", K_GHOSTS: "ghosts", K_FLUX_DC: "flux_dc", K_FLUX_PLM: "flux_plm", K_EMF: "emf",
                 K_UPDATE: "update"}
@@ -87,6 +88,8 @@ def load(path: str = LIB_PATH):
     L.vl2_profile_read.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong),
                                    ctypes.POINTER(ctypes.c_longlong)]
     L.vl2_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.vl2_totals_noalloc.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                     vp, vp]
     L.vl2_last_error.argtypes = [vp]
     L.vl2_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -298,6 +301,23 @@ class Mesh:
             t += dt
             n += 1
         return n
+
+
+def totals_noalloc(u, b1, b2, b3, dx, out, stream=None):
+    """vl2_totals_noalloc on device tensors u [5][NZ][NY][NX], b1, b2, b3 (global layout) into the device
+    tensor out (8 doubles), enqueued on `stream` (default: the current torch stream).  Allocates nothing."""
+    import torch
+
+    for t in (u, b1, b2, b3, out):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError("totals_noalloc takes contiguous float64 CUDA tensors")
+    nz, ny, nx = u.shape[1:]
+    dims = (ctypes.c_int * 3)(nx, ny, nz)
+    h = (ctypes.c_double * 3)(*dx)
+    st = (stream or torch.cuda.current_stream(u.device)).cuda_stream
+    _check(load().vl2_totals_noalloc(*[ctypes.c_void_p(t.data_ptr()) for t in (u, b1, b2, b3)], dims, h,
+                                     ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st)))
+    return out
 
 
 # ---- ABI-named module functions ----
