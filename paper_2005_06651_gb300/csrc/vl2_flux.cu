@@ -52,6 +52,141 @@ __global__ void __launch_bounds__(128) k_flux(Geom g, const double* __restrict__
   for (int n = 0; n < 7; ++n) Fb[(long long)n * g.box] = f[n];
 }
 
+// Corrector fluxes with each cell's PLM reconstruction formed once (Sec. 3.2.1).  A CTA takes P lines
+// of faces along DIR: phase A reconstructs the mb+2 cells of each line (ng-1 .. ng+mb) into shared
+// memory (face values q -+ delta/2 of 7 variables), phase B solves the mb+1 Riemann problems of each line
+// from shared memory.  The 7 limiter denominators of a cell share one division (simultaneous inversion:
+// reciprocals of a product and of its prefix products); a product outside the normal range falls back
+// to one division per variable.
+template <int DIR>
+struct LineMap {
+  // transverse directions ordered so that the fastest-varying memory index comes first
+  static constexpr int TA = (DIR == 0) ? 1 : 0;
+  static constexpr int TB = (DIR == 2) ? 1 : 2;
+};
+
+__device__ __forceinline__ bool normal_pos(double x) {
+  const long long e = (__double_as_longlong(x) >> 52) & 0x7ff;
+  return e != 0 && e != 0x7ff;
+}
+
+template <int DIR, int RS>
+__global__ void __launch_bounds__(256, 2) k_flux_plm(Geom g, const double* __restrict__ W,
+                                                     const double* __restrict__ Bn, double* __restrict__ F, int P) {
+  extern __shared__ double smem[];
+  constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
+  constexpr int TA = LineMap<DIR>::TA, TB = LineMap<DIR>::TB;
+  const int L = g.mb[DIR] + 2;   // reconstructed cells per line
+  const int NF = g.mb[DIR] + 1;  // faces per line
+  const int na = g.mb[TA] + 2, nb = g.mb[TB] + 2;
+  const int nlines = na * nb;
+  const int tiles = (nlines + P - 1) / P;
+  const int b = blockIdx.x / tiles;
+  const int tile = blockIdx.x - b * tiles;
+  const long long stride[3] = {1LL, (long long)g.sx, (long long)g.sx * g.sy};
+  const long long sd = stride[DIR];
+  const double* Wb = W + (long long)b * 8 * g.box;
+  const int var[7] = {0, 1 + DIR, 1 + T1, 1 + T2, 4, 5 + T1, 5 + T2};
+  // shared layout: the fastest thread index is contiguous
+  auto sidx = [&](int v, int side, int p, int c) -> int {
+    return (DIR == 0) ? (((v * 2 + side) * P + p) * L + c) : (((v * 2 + side) * L + c) * P + p);
+  };
+  // phase A: reconstruct cells
+  for (int t = threadIdx.x; t < P * L; t += blockDim.x) {
+    const int p = (DIR == 0) ? t / L : t % P;
+    const int c = (DIR == 0) ? t % L : t / P;
+    const int line = tile * P + p;
+    if (line >= nlines) continue;
+    int li[3];
+    li[DIR] = NG - 1 + c;
+    li[TA] = NG - 1 + line % na;
+    li[TB] = NG - 1 + line / na;
+    const long long o = cell_off(g, li[2], li[1], li[0]);
+    double q0[7], dl[7], dr[7], den[7];
+    bool pos[7];
+#pragma unroll
+    for (int n = 0; n < 7; ++n) {
+      const double* q = Wb + (long long)var[n] * g.box + o;
+      const double qm = q[-sd], qc = q[0], qp = q[sd];
+      q0[n] = qc;
+      dl[n] = qc - qm;
+      dr[n] = qp - qc;
+      pos[n] = gt0(dl[n] * dr[n]);
+      den[n] = pos[n] ? dl[n] + dr[n] : 1.0;
+    }
+    double pre[7];
+    pre[0] = den[0];
+#pragma unroll
+    for (int n = 1; n < 7; ++n) pre[n] = pre[n - 1] * den[n];
+    double rec[7];
+    if (normal_pos(fabs(pre[6]))) {
+      double inv = 1.0 / pre[6];
+#pragma unroll
+      for (int n = 6; n > 0; --n) {
+        rec[n] = inv * pre[n - 1];
+        inv = inv * den[n];
+      }
+      rec[0] = inv;
+    } else {
+#pragma unroll
+      for (int n = 0; n < 7; ++n) rec[n] = 1.0 / den[n];
+    }
+#pragma unroll
+    for (int n = 0; n < 7; ++n) {
+      const double delta = pos[n] ? (2.0 * (dl[n] * dr[n])) * rec[n] : 0.0;
+      smem[sidx(n, 0, p, c)] = q0[n] - 0.5 * delta;  // value at the cell's lower face
+      smem[sidx(n, 1, p, c)] = q0[n] + 0.5 * delta;  // value at the cell's upper face
+    }
+  }
+  __syncthreads();
+  // phase B: Riemann problems of the faces ng .. ng+mb of every line
+  for (int t = threadIdx.x; t < P * NF; t += blockDim.x) {
+    const int p = (DIR == 0) ? t / NF : t % P;
+    const int f = (DIR == 0) ? t % NF : t / P;
+    const int line = tile * P + p;
+    if (line >= nlines) continue;
+    int li[3];
+    li[DIR] = NG + f;
+    li[TA] = NG - 1 + line % na;
+    li[TB] = NG - 1 + line / na;
+    const long long o = cell_off(g, li[2], li[1], li[0]);
+    double wl[7], wr[7];
+#pragma unroll
+    for (int n = 0; n < 7; ++n) {
+      wl[n] = smem[sidx(n, 1, p, f)];      // upper-face value of cell ng-1+f
+      wr[n] = smem[sidx(n, 0, p, f + 1)];  // lower-face value of cell ng+f
+    }
+    const double bn = Bn[(long long)b * g.box + o];
+    double fl[7];
+    if (RS == RS_HLLD)
+      flux_hlld<double>(wl, wr, bn, g.gamma, g.igm1, fl);
+    else
+      flux_hlle<double>(wl, wr, bn, g.gamma, g.igm1, fl);
+    double* Fb = F + (long long)b * 7 * g.box + o;
+#pragma unroll
+    for (int n = 0; n < 7; ++n) Fb[(long long)n * g.box] = fl[n];
+  }
+}
+
+constexpr size_t PLM_SMEM_MAX = 64 * 1024;  // shared bytes per CTA (two CTAs per SM)
+
+template <int DIR, int RS>
+static cudaError_t launch_plm(const Geom& g, const double* w, const double* bn, double* f, cudaStream_t st) {
+  constexpr int TA = LineMap<DIR>::TA, TB = LineMap<DIR>::TB;
+  const size_t per_line = (size_t)(g.mb[DIR] + 2) * 14 * sizeof(double);
+  int P = (int)(PLM_SMEM_MAX / per_line);
+  P = P < 1 ? 1 : (P > 16 ? 16 : P);
+  const int nlines = (g.mb[TA] + 2) * (g.mb[TB] + 2);
+  const int tiles = (nlines + P - 1) / P;
+  const size_t shmem = (size_t)P * per_line;
+  if (shmem > PLM_SMEM_MAX) return cudaErrorInvalidValue;  // a line longer than the shared budget
+  cudaError_t e = cudaFuncSetAttribute(k_flux_plm<DIR, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)PLM_SMEM_MAX);
+  if (e != cudaSuccess) return e;
+  k_flux_plm<DIR, RS><<<(unsigned)((long long)tiles * g.nblk), 256, shmem, st>>>(g, w, bn, f, P);
+  return cudaGetLastError();
+}
+
 template <int DIR, int REC, int RS>
 static cudaError_t launch_one(const Geom& g, const double* w, const double* bn, double* f, cudaStream_t st) {
   const long long per = (long long)(g.mb[0] + (DIR == 0 ? 1 : 2)) * (g.mb[1] + (DIR == 1 ? 1 : 2)) *
@@ -70,7 +205,16 @@ static cudaError_t launch_dir(const Geom& g, const Arrays& a, int reg, int dir, 
   return launch_one<2, REC, RS>(g, a.w, a.b[reg][2], a.f[2], st);
 }
 
+template <int RS>
+static cudaError_t launch_plm_dir(const Geom& g, const Arrays& a, int reg, int dir, cudaStream_t st) {
+  if (dir == 0) return launch_plm<0, RS>(g, a.w, a.b[reg][0], a.f[0], st);
+  if (dir == 1) return launch_plm<1, RS>(g, a.w, a.b[reg][1], a.f[1], st);
+  return launch_plm<2, RS>(g, a.w, a.b[reg][2], a.f[2], st);
+}
+
 cudaError_t launch_flux(const Geom& g, const Arrays& a, int reg, int recon, int riemann, int dir, cudaStream_t st) {
+  if (recon == REC_PLM)
+    return riemann == RS_HLLD ? launch_plm_dir<RS_HLLD>(g, a, reg, dir, st) : launch_plm_dir<RS_HLLE>(g, a, reg, dir, st);
   if (recon == REC_DC)
     return riemann == RS_HLLD ? launch_dir<REC_DC, RS_HLLD>(g, a, reg, dir, st) : launch_dir<REC_DC, RS_HLLE>(g, a, reg, dir, st);
   return riemann == RS_HLLD ? launch_dir<REC_PLM, RS_HLLD>(g, a, reg, dir, st) : launch_dir<REC_PLM, RS_HLLE>(g, a, reg, dir, st);

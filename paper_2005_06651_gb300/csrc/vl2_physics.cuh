@@ -59,110 +59,180 @@ __device__ __forceinline__ void flux_hlle(const R* wl, const R* wr, R bn, R gamm
   for (int n = 0; n < 7; ++n) f[n] = ((bp * fl[n] - bm * fr[n]) + bpm * (ur[n] - ul[n])) * iden;
 }
 
+// ---- sign tests and orderings on the integer pipe --------------------------------------------
+// The FP64 pipe is the bottleneck of the plain kernels, so comparisons of doubles are done on the IEEE
+// bit patterns (integer compares) rather than with FP64 compare instructions.  They return exactly what
+// the corresponding IEEE comparison returns (NaN aside).
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ int dbits(float x) { return __float_as_int(x); }
+// x > 0 (false for +0 and -0)
+template <class R> __device__ __forceinline__ bool gt0(R x) { return dbits(x) > 0; }
+// x >= 0 (true for -0)
+template <class R> __device__ __forceinline__ bool ge0(R x) {
+  const auto b = dbits(x);
+  return b >= 0 || (b << 1) == 0;
+}
+// x < 0 (false for -0)
+template <class R> __device__ __forceinline__ bool lt0(R x) { return !ge0(x); }
+template <class R> __device__ __forceinline__ bool is0(R x) { return (dbits(x) << 1) == 0; }
+// total-order key: a < b  <=>  key(a) < key(b) for all non-NaN a, b (-0 and +0 map to 0 and -1)
+__device__ __forceinline__ long long okey(double x) {
+  const long long b = dbits(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ int okey(float x) {
+  const int b = dbits(x);
+  return b ^ ((b >> 31) & 0x7fffffff);
+}
+template <class R> __device__ __forceinline__ R imin(R a, R b) { return okey(b) < okey(a) ? b : a; }
+template <class R> __device__ __forceinline__ R imax(R a, R b) { return okey(b) > okey(a) ? b : a; }
+template <class R> __device__ __forceinline__ bool igt(R a, R b) { return okey(a) > okey(b); }
+
+// One side (L or R) of the HLLD fan: the state, its conserved vector and physical flux, and its
+// single-star state.
+template <class R>
+struct HlldSide {
+  R w[7];   // rho, v_n, v_t1, v_t2, p, b_t1, b_t2
+  R u[7];   // conserved
+  R f[7];   // physical flux
+  R s;      // outer speed S_L or S_R
+  R pt;     // total pressure
+  R a;      // rho (S - v_n)
+  R dst;    // rho*
+  R vt[2];  // v_t*
+  R bt[2];  // b_t*
+  R est;    // E*
+  R vbst;   // v* . B*
+};
+
+// Transverse velocity and field of the single-star state (degenerate case: unchanged).
+template <class R>
+__device__ __forceinline__ void hlld_star_vb(const R* w, R a, R s, R sm, R bn, R bn2, R ptst, R* vt, R* bt) {
+  const R dd = a * (s - sm) - bn2;
+  vt[0] = w[2];
+  vt[1] = w[3];
+  bt[0] = w[5];
+  bt[1] = w[6];
+  if (igt(fabs(dd), R(1e-8) * ptst)) {
+    const R idd = R(1) / dd;
+    const R tv = bn * (sm - w[1]) * idd;
+    const R tb = (a * (s - w[1]) - bn2) * idd;
+    vt[0] = w[2] - w[5] * tv;
+    vt[1] = w[3] - w[6] * tv;
+    bt[0] = w[5] * tb;
+    bt[1] = w[6] * tb;
+  }
+}
+
+// Flux of one side of the fan: outer state, single-star or double-star region.  `o` is the other
+// side's raw state (used only in the double-star region).
+template <class R>
+__device__ __forceinline__ void hlld_side_flux(HlldSide<R>& S, const R* o_w, R o_s, R o_a, bool left, R sm,
+                                               R bn, R bn2, R ptst, R* f) {
+  const R isms = R(1) / (S.s - sm);
+  S.dst = S.a * isms;
+  hlld_star_vb(S.w, S.a, S.s, sm, bn, bn2, ptst, S.vt, S.bt);
+  const R vb = (S.w[1] * bn + S.w[2] * S.w[5]) + S.w[3] * S.w[6];
+  S.vbst = (sm * bn + S.vt[0] * S.bt[0]) + S.vt[1] * S.bt[1];
+  S.est = ((((S.s - S.w[1]) * S.u[4] - S.pt * S.w[1]) + ptst * sm) + bn * (vb - S.vbst)) * isms;
+  const R rs = rsqrt(S.dst);
+  const R abn = fabs(bn);
+  const R sst = left ? sm - abn * rs : sm + abn * rs;
+  // region: outer if the outer wave has not reached the interface, single star if the Alfven wave has not
+  const bool outer = left ? ge0(S.s) : !gt0(S.s);
+  const bool single = left ? ge0(sst) : !gt0(sst);
+  R us[7];
+  us[0] = S.dst;
+  us[1] = S.dst * sm;
+  us[2] = S.dst * S.vt[0];
+  us[3] = S.dst * S.vt[1];
+  us[4] = S.est;
+  us[5] = S.bt[0];
+  us[6] = S.bt[1];
+#pragma unroll
+  for (int n = 0; n < 7; ++n) f[n] = S.f[n];
+  if (!outer) {
+#pragma unroll
+    for (int n = 0; n < 7; ++n) f[n] = f[n] + S.s * (us[n] - S.u[n]);
+  }
+  if (!outer && !single) {
+    // double star: needs the other side's single-star density, velocity and field
+    const R o_dst = o_a / (o_s - sm);
+    R o_vt[2], o_bt[2];
+    hlld_star_vb(o_w, o_a, o_s, sm, bn, bn2, ptst, o_vt, o_bt);
+    const R sq = S.dst * rs;  // sqrt(rho*) of this side
+    const R o_sq = sqrt(o_dst);
+    const R sql = left ? sq : o_sq, sqr = left ? o_sq : sq;
+    const R* vtl = left ? S.vt : o_vt;
+    const R* vtr = left ? o_vt : S.vt;
+    const R* btl = left ? S.bt : o_bt;
+    const R* btr = left ? o_bt : S.bt;
+    const R sgn = ge0(bn) ? R(1) : R(-1);
+    const R isq = R(1) / (sql + sqr);
+    const R vss1 = ((sql * vtl[0] + sqr * vtr[0]) + (btr[0] - btl[0]) * sgn) * isq;
+    const R vss2 = ((sql * vtl[1] + sqr * vtr[1]) + (btr[1] - btl[1]) * sgn) * isq;
+    const R bss1 = ((sql * btr[0] + sqr * btl[0]) + (sql * sqr) * (vtr[0] - vtl[0]) * sgn) * isq;
+    const R bss2 = ((sql * btr[1] + sqr * btl[1]) + (sql * sqr) * (vtr[1] - vtl[1]) * sgn) * isq;
+    const R vbss = (sm * bn + vss1 * bss1) + vss2 * bss2;
+    R uss[7];
+    uss[0] = S.dst;
+    uss[1] = S.dst * sm;
+    uss[2] = S.dst * vss1;
+    uss[3] = S.dst * vss2;
+    uss[4] = left ? S.est - sq * (S.vbst - vbss) * sgn : S.est + sq * (S.vbst - vbss) * sgn;
+    uss[5] = bss1;
+    uss[6] = bss2;
+#pragma unroll
+    for (int n = 0; n < 7; ++n) f[n] = f[n] + sst * (uss[n] - us[n]);
+  }
+}
+
 // HLLD flux (Miyoshi & Kusano 2005; the paper names the solver in Sec. 3.2.2):
 // outer speeds S_L = min(u_L,u_R) - max(c_L,c_R), S_R = max(u_L,u_R) + max(c_L,c_R); contact speed
 // S_M and total pressure p_T* from the two-sided forms; single-star states (degenerate when
 // |rho (S-u)(S-S_M) - b_n^2| <= 1e-8 p_T*); Alfven speeds S*_{L,R} = S_M -+ |b_n| / sqrt(rho*);
 // double-star states with sign(0) = +1.  Selection: the sign of S_M picks the side, ties at an outer
-// or Alfven speed of exactly zero take the outer state, S_M == 0 averages both sides.
+// or Alfven speed of exactly zero take the outer state, S_M == 0 averages both sides.  Only the
+// picked side's star state is formed (the other side's only in the double-star region).
 template <class R>
 __device__ __forceinline__ void flux_hlld(const R* wl, const R* wr, R bn, R gamma, R igm1, R* f) {
-  R uo[2][7], fo[2][7];
-  phys_flux(wl, bn, igm1, uo[0], fo[0]);
-  phys_flux(wr, bn, igm1, uo[1], fo[1]);
   const R bn2 = bn * bn;
-  const R idl = R(1) / wl[0], idr = R(1) / wr[0];
   const R btl2 = wl[5] * wl[5] + wl[6] * wl[6];
   const R btr2 = wr[5] * wr[5] + wr[6] * wr[6];
-  const R cl = fast_speed_r(idl, wl[4], bn2, btl2, gamma);
-  const R cr = fast_speed_r(idr, wr[4], bn2, btr2, gamma);
-  const R cmax = fmax(cl, cr);
-  const R s[2] = {fmin(wl[1], wr[1]) - cmax, fmax(wl[1], wr[1]) + cmax};
-  const R pt[2] = {wl[4] + R(0.5) * (bn2 + btl2), wr[4] + R(0.5) * (bn2 + btr2)};
-  const R a[2] = {(s[0] - wl[1]) * wl[0], (s[1] - wr[1]) * wr[0]};
-  const R iden = R(1) / (a[1] - a[0]);
-  const R sm = ((a[1] * wr[1] - a[0] * wl[1]) + (pt[0] - pt[1])) * iden;
-  const R ptst = ((a[1] * pt[0] - a[0] * pt[1]) + (a[1] * a[0]) * (wr[1] - wl[1])) * iden;
-
-  R us[2][7], vbst[2], dst[2], vst[2][2];
+  const R ilr = R(1) / (wl[0] * wr[0]);  // 1/rho_L and 1/rho_R from one division
+  const R cl = fast_speed_r(wr[0] * ilr, wl[4], bn2, btl2, gamma);
+  const R cr = fast_speed_r(wl[0] * ilr, wr[4], bn2, btr2, gamma);
+  const R cmax = imax(cl, cr);
+  const R sl = imin(wl[1], wr[1]) - cmax;
+  const R sr = imax(wl[1], wr[1]) + cmax;
+  const R ptl = wl[4] + R(0.5) * (bn2 + btl2), ptr = wr[4] + R(0.5) * (bn2 + btr2);
+  const R al = (sl - wl[1]) * wl[0], ar = (sr - wr[1]) * wr[0];
+  const R iden = R(1) / (ar - al);
+  const R sm = ((ar * wr[1] - al * wl[1]) + (ptl - ptr)) * iden;
+  const R ptst = ((ar * ptl - al * ptr) + (ar * al) * (wr[1] - wl[1])) * iden;
+  const bool left = ge0(sm);
+  HlldSide<R> S;
 #pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    const R* w = side ? wr : wl;
-    const R sms = s[side] - sm;
-    const R isms = R(1) / sms;
-    const R dd = a[side] * sms - bn2;
-    R vt1 = w[2], vt2 = w[3], bt1 = w[5], bt2 = w[6];
-    if (fabs(dd) > R(1e-8) * ptst) {
-      const R idd = R(1) / dd;
-      const R tv = bn * (sm - w[1]) * idd;
-      const R tb = (a[side] * (s[side] - w[1]) - bn2) * idd;
-      vt1 = w[2] - w[5] * tv;
-      vt2 = w[3] - w[6] * tv;
-      bt1 = w[5] * tb;
-      bt2 = w[6] * tb;
-    }
-    dst[side] = a[side] * isms;
-    vst[side][0] = vt1;
-    vst[side][1] = vt2;
-    const R vb = (w[1] * bn + w[2] * w[5]) + w[3] * w[6];
-    vbst[side] = (sm * bn + vt1 * bt1) + vt2 * bt2;
-    us[side][0] = dst[side];
-    us[side][1] = dst[side] * sm;
-    us[side][2] = dst[side] * vt1;
-    us[side][3] = dst[side] * vt2;
-    us[side][4] = ((((s[side] - w[1]) * uo[side][4] - pt[side] * w[1]) + ptst * sm) + bn * (vb - vbst[side])) * isms;
-    us[side][5] = bt1;
-    us[side][6] = bt2;
+  for (int n = 0; n < 7; ++n) S.w[n] = left ? wl[n] : wr[n];
+  S.s = left ? sl : sr;
+  S.pt = left ? ptl : ptr;
+  S.a = left ? al : ar;
+  phys_flux(S.w, bn, igm1, S.u, S.f);
+  const R* o_w = left ? wr : wl;
+  hlld_side_flux(S, o_w, left ? sr : sl, left ? ar : al, left, sm, bn, bn2, ptst, f);
+  if (is0(sm)) {  // both sides are valid at S_M == 0: average them (exact mirror symmetry)
+    HlldSide<R> T;
+#pragma unroll
+    for (int n = 0; n < 7; ++n) T.w[n] = wr[n];
+    T.s = sr;
+    T.pt = ptr;
+    T.a = ar;
+    phys_flux(T.w, bn, igm1, T.u, T.f);
+    R g[7];
+    hlld_side_flux(T, wl, sl, al, false, sm, bn, bn2, ptst, g);
+#pragma unroll
+    for (int n = 0; n < 7; ++n) f[n] = R(0.5) * (f[n] + g[n]);
   }
-  const R rsl = rsqrt(dst[0]), rsr = rsqrt(dst[1]);
-  const R sql = dst[0] * rsl, sqr = dst[1] * rsr;  // sqrt(rho*_L), sqrt(rho*_R)
-  const R abn = fabs(bn);
-  const R sst[2] = {sm - abn * rsl, sm + abn * rsr};
-  const R sgn = (bn >= R(0)) ? R(1) : R(-1);
-  const R isq = R(1) / (sql + sqr);
-  const R vss1 = ((sql * vst[0][0] + sqr * vst[1][0]) + (us[1][5] - us[0][5]) * sgn) * isq;
-  const R vss2 = ((sql * vst[0][1] + sqr * vst[1][1]) + (us[1][6] - us[0][6]) * sgn) * isq;
-  const R bss1 = ((sql * us[1][5] + sqr * us[0][5]) + (sql * sqr) * (vst[1][0] - vst[0][0]) * sgn) * isq;
-  const R bss2 = ((sql * us[1][6] + sqr * us[0][6]) + (sql * sqr) * (vst[1][1] - vst[0][1]) * sgn) * isq;
-  const R vbss = (sm * bn + vss1 * bss1) + vss2 * bss2;
-
-  // region on each side: 0 outer, 1 single star, 2 double star
-  const int regl = (s[0] >= R(0)) ? 0 : ((sst[0] >= R(0)) ? 1 : 2);
-  const int regr = (s[1] <= R(0)) ? 0 : ((sst[1] <= R(0)) ? 1 : 2);
-  const bool use_l = sm >= R(0);
-  const bool use_r = sm <= R(0);
-  R fsum[7];
-#pragma unroll
-  for (int n = 0; n < 7; ++n) fsum[n] = R(0);
-#pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    if (side == 0 ? !use_l : !use_r) continue;
-    const int reg = side ? regr : regl;
-    R fl[7];
-#pragma unroll
-    for (int n = 0; n < 7; ++n) fl[n] = fo[side][n];
-    if (reg >= 1) {
-#pragma unroll
-      for (int n = 0; n < 7; ++n) fl[n] = fl[n] + s[side] * (us[side][n] - uo[side][n]);
-    }
-    if (reg == 2) {
-      R uss[7];
-      uss[0] = dst[side];
-      uss[1] = dst[side] * sm;
-      uss[2] = dst[side] * vss1;
-      uss[3] = dst[side] * vss2;
-      uss[4] = side ? us[1][4] + sqr * (vbst[1] - vbss) * sgn : us[0][4] - sql * (vbst[0] - vbss) * sgn;
-      uss[5] = bss1;
-      uss[6] = bss2;
-#pragma unroll
-      for (int n = 0; n < 7; ++n) fl[n] = fl[n] + sst[side] * (uss[n] - us[side][n]);
-    }
-#pragma unroll
-    for (int n = 0; n < 7; ++n) fsum[n] = fsum[n] + fl[n];
-  }
-  const R scale = (use_l && use_r) ? R(0.5) : R(1);
-#pragma unroll
-  for (int n = 0; n < 7; ++n) f[n] = fsum[n] * scale;
 }
 
 // Original van Leer limited slope on a uniform grid (Sec. 3.2.1).
@@ -170,7 +240,7 @@ template <class R>
 __device__ __forceinline__ R vl_slope(R qm, R q0, R qp) {
   const R dl = q0 - qm, dr = qp - q0;
   const R pr = dl * dr;
-  return (pr > R(0)) ? (R(2) * pr) / (dl + dr) : R(0);
+  return gt0(pr) ? (R(2) * pr) / (dl + dr) : R(0);
 }
 
 // Upwind CT corner EMF (Gardiner & Stone 2005) for an edge with transverse directions a, b:
@@ -178,7 +248,7 @@ __device__ __forceinline__ R vl_slope(R qm, R q0, R qp) {
 // ea[0..1]: a-face EMFs at b-index -1, 0; eb[0..1]: b-face EMFs at a-index -1, 0;
 // ec[0..3]: cell EMFs at (a-1,b-1), (a,b-1), (a-1,b), (a,b); ma, mb: the matching face mass fluxes.
 __device__ __forceinline__ double ct_pick(double m, double lo, double hi) {
-  return (m > 0.0) ? lo : ((m < 0.0) ? hi : 0.5 * (lo + hi));
+  return gt0(m) ? lo : (lt0(m) ? hi : 0.5 * (lo + hi));
 }
 
 __device__ __forceinline__ double ct_corner(const double* ea, const double* eb, const double* ec,
