@@ -47,9 +47,9 @@ HBM_BYTES_PER_ZONE_CYCLE = 320.0
 FLOPS_PER_FACE = {("plm", "hlld"): 484.9, ("dc", "hlld"): 394.1, ("plm", "hlle"): 299.8, ("dc", "hlle"): 209.0}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of
-# the PLM+HLLD x sweep on the 128^3 vortex, 2,441,472 faces), scaled to a launch by its faces; valid only
+# the k_flux_plm x sweep on the 128^3 vortex, 2,441,472 faces), scaled to a launch by its faces; valid only
 # for the kernel source it was taken on (hash of the flux and physics sources), else reported as null.
-NCU_TRAFFIC = {"hash": "d3132fc066f2b334", "bytes_per_face": 135.2}
+NCU_TRAFFIC = {"hash": "7f607692b43ac1e9", "bytes_per_face": 134.3}
 
 
 def flux_source_hash():
@@ -183,6 +183,85 @@ def workload_config(args):
         "l2": "state (1.07 GB per register at 256^3) exceeds the 129 MB L2; no flush", "parallelism": "replicas"}
 
 
+def timed_steps(mesh, steps, stream, dts=None):
+    """Device time (ms) of `steps` cycles (new_dt + step, or the given dt sequence); returns (ms, dts)."""
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    e0.record(stream)
+    for s in range(steps):
+        dt = mesh.new_dt() if dts is None else dts[s]
+        mesh.step(dt)
+        out.append(dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def mixed_form(args, dev, stream, vl2, inputs):
+    """Mixed-precision form on decaying turbulence (Mach 2, beta 10) at forms_n^3 in 32^3 MeshBlocks, next
+    to plain FP64 on the same state and the same dt sequence; plus the 64^3 linear-wave L1 error of both."""
+    import torch
+
+    n, mb, K = args.forms_n, args.mb, args.forms_steps
+    prob = inputs.turbulence(n=n, mb=mb, seed=3003, mach=2.0, beta=10.0)
+    res = {"config": {"workload": "decaying_turbulence_%d^3_%dx%d^3_blocks_mach2_beta10" % (n, (n // mb) ** 3, mb),
+                      "seed": 3003, "steps": K, "dtype": "f32 reconstruction/fluxes/CT, f64 state/cons->prim/accumulation"}}
+    states, times = {}, {}
+    dts = None
+    for name, prec in (("fp64", vl2.FP64), ("mixed", vl2.MIXED)):
+        m = vl2.Mesh.from_problem(prob, device=dev, stream=stream, precision=prec)
+        for _ in range(3):
+            m.step(m.new_dt())
+        m.set_prims(prob.w, prob.b1, prob.b2, prob.b3)
+        torch.cuda.synchronize(dev)
+        ms, used = timed_steps(m, K, stream, dts)
+        if dts is None:
+            dts = used
+        times[name] = ms
+        u = torch.empty((5,) + m.shape, dtype=torch.float64, device=dev)
+        m.get_cons((u, None, None, None))
+        c = n // 2
+        sl = slice(c - 64, c + 64) if n >= 128 else slice(0, n)
+        states[name] = (u[0, sl, sl, sl].clone(), u[4, sl, sl, sl].clone())
+        del m, u
+        torch.cuda.empty_cache()
+    rho_err = float(((states["mixed"][0] - states["fp64"][0]).abs() / states["fp64"][0].abs()).max())
+    e_err = float(((states["mixed"][1] - states["fp64"][1]).abs() / states["fp64"][1].abs()).max())
+    ncell = prob.ncells
+    res.update({"value": ncell * K / (times["mixed"] / 1e3), "unit": UNIT, "ms_per_step": times["mixed"] / K,
+                "fp64_value": ncell * K / (times["fp64"] / 1e3), "fp64_ms_per_step": times["fp64"] / K,
+                "speedup_vs_fp64": times["fp64"] / times["mixed"],
+                "hbm_frac": HBM_BYTES_PER_ZONE_CYCLE * ncell * K / (times["mixed"] / 1e3) / 1e9 /
+                float(measured_peaks().get("hbm_gbs", 6800.0)),
+                "max_rel_err_vs_fp64_central_128": {"rho": rho_err, "E": e_err,
+                                                    "after_steps": K, "same_dt_sequence": True}})
+    # linear-wave L1 error (eq. RMS-error) at 64^3, one period, both precisions
+    wave = inputs.linear_wave(64, mb=32, kind="alfven", amp=1e-6)
+    l1 = {}
+    for name, prec in (("fp64", vl2.FP64), ("mixed", vl2.MIXED)):
+        m = vl2.Mesh.from_problem(wave, device=dev, stream=stream, precision=prec)
+        ref = m.get_cons()
+        m.run(wave.meta["period"])
+        l1[name] = rms_l1(m.get_cons(), ref)
+        del m
+    res["linear_wave_l1_64"] = {"amplitude": 1e-6, "fp64": l1["fp64"], "mixed": l1["mixed"]}
+    return res
+
+
+def rms_l1(state, ref):
+    import numpy as np
+
+    def cb(b1, b2, b3):
+        return (0.5 * (b1[:, :, 1:] + b1[:, :, :-1]), 0.5 * (b2[:, 1:, :] + b2[:, :-1, :]), 0.5 * (b3[1:] + b3[:-1]))
+
+    u, b = state[0], cb(*state[1:])
+    u0, b0 = ref[0], cb(*ref[1:])
+    e = [np.mean(np.abs(u[v] - u0[v])) for v in range(5)] + [np.mean(np.abs(b[d] - b0[d])) for d in range(3)]
+    return float(np.sqrt(np.sum(np.square(e))))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -193,6 +272,9 @@ def main():
     ap.add_argument("--mb", type=int, default=32)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the mixed-precision and batched forms")
+    ap.add_argument("--forms-n", type=int, default=512, help="grid of the mixed-precision form")
+    ap.add_argument("--forms-steps", type=int, default=20)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -312,11 +394,15 @@ def main():
            "path": "set_prims (pinned host) + new_dt + step + get_cons (pinned host) per step"}
     divb = mesh.divb_norm()
     floors = mesh.floor_count()
+    mesh.close()
+    mesh = None
+    torch.cuda.empty_cache()
+    forms = None
+    if not args.no_forms:
+        forms = {"mixed": mixed_form(args, dev, stream, vl2, inputs)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        del mesh
-        torch.cuda.empty_cache()
         rate, done, threads, el = oracle_rate(args.n, args.mb, 1, 0, min_seconds=10.0, max_steps=3)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": "%d VL2 cycle(s) of the full %d^3 workload (%d MeshBlocks), %.1f s" % (
@@ -326,7 +412,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args),
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "hbm": hbm,
-                "kernels": kernel_share, "cpu_baseline": cpu, "divb_norm": divb, "floor_events": floors}
+                "kernels": kernel_share, "cpu_baseline": cpu, "divb_norm": divb, "floor_events": floors,
+                "forms": forms}
         print(json.dumps(line), flush=True)
     if pg:
         pg.barrier()

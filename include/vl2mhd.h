@@ -48,7 +48,7 @@ typedef enum vl2_status {
 
 enum { VL2_HLLE = 0, VL2_HLLD = 1 };       /* Riemann solver, Sec. 3.2.2 */
 enum { VL2_PERIODIC = 0, VL2_OUTFLOW = 1 };/* per-face boundary condition */
-enum { VL2_FP64 = 0, VL2_MIXED = 1 };      /* arithmetic of reconstruction and fluxes */
+enum { VL2_FP64 = 0, VL2_MIXED = 1 };      /* arithmetic of reconstruction, fluxes and EMFs */
 enum { VL2_HOST = 0, VL2_DEVICE = 1 };     /* where a caller buffer lives */
 enum { VL2_DC = 0, VL2_PLM = 1 };          /* reconstruction, Sec. 3.2.1 */
 
@@ -60,7 +60,9 @@ typedef struct vl2_params {
   double gamma;       /* adiabatic index of the ideal-gas EOS, P = (gamma-1) e (Sec. 3.1) */
   double cfl;         /* Courant number C0 of vl2_new_dt; <= 1/2 for VL2 in 3D (Sec. 3.2.3) */
   int riemann;        /* VL2_HLLD or VL2_HLLE */
-  int precision;      /* VL2_FP64 (only value accepted by this version) */
+  int precision;      /* VL2_FP64: all arithmetic in FP64.  VL2_MIXED: reconstruction, Riemann fluxes and
+                         CT EMFs in FP32 (FP32 scratch), while U and B stay FP64, cons->prim (pressure
+                         recovery) is FP64, and the flux divergence / EMF curl are accumulated in FP64 */
   int bc[6];          /* boundary of faces x-, x+, y-, y+, z-, z+: VL2_PERIODIC or VL2_OUTFLOW;
                          periodic must be set on both faces of a direction */
   double dfloor, pfloor; /* density / pressure floors of cons->prim (> 0) */

@@ -121,8 +121,8 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
     msg = "riemann must be VL2_HLLD or VL2_HLLE";
     return VL2_E_ARG;
   }
-  if (p->precision != VL2_FP64) {
-    msg = "precision must be VL2_FP64";
+  if (p->precision != VL2_FP64 && p->precision != VL2_MIXED) {
+    msg = "precision must be VL2_FP64 or VL2_MIXED";
     return VL2_E_ARG;
   }
   for (int d = 0; d < 3; ++d) {
@@ -170,10 +170,11 @@ struct Plan {
   size_t stage_elems;
 };
 
-Plan make_plan(const Geom& g) {
+Plan make_plan(const Geom& g, int precision) {
   Plan pl;
   size_t o = 0;
   const size_t per = (size_t)g.nblk * g.box * sizeof(double);
+  const size_t sper = (size_t)g.nblk * g.box * (precision == VL2_MIXED ? sizeof(float) : sizeof(double));
   for (int r = 0; r < 2; ++r) {
     pl.off_u[r] = o;
     o = align256(o + 5 * per);
@@ -183,14 +184,14 @@ Plan make_plan(const Geom& g) {
     }
   }
   pl.off_w = o;
-  o = align256(o + 8 * per);
+  o = align256(o + 8 * sper);
   for (int d = 0; d < 3; ++d) {
     pl.off_f[d] = o;
-    o = align256(o + 7 * per);
+    o = align256(o + 7 * sper);
   }
   for (int d = 0; d < 3; ++d) {
     pl.off_e[d] = o;
-    o = align256(o + per);
+    o = align256(o + sper);
   }
   const long long nc = ncells(g);
   long long st = 5 * nc + nfaces_total(g);
@@ -310,7 +311,7 @@ vl2_status vl2_workspace_bytes(const vl2_params* params, size_t* bytes) {
   vl2_status s = make_geom(params, g, msg);
   if (s != VL2_OK) return fail(nullptr, s, msg);
   if (!bytes) return fail(nullptr, VL2_E_ARG, "bytes is NULL");
-  *bytes = make_plan(g).total;
+  *bytes = make_plan(g, params->precision).total;
   return VL2_OK;
 }
 
@@ -322,7 +323,7 @@ vl2_status vl2_mesh_create(const vl2_params* params, void* workspace, size_t byt
   vl2_status s = make_geom(params, g, msg);
   if (s != VL2_OK) return fail(nullptr, s, msg);
   if (!workspace || ((uintptr_t)workspace & 255u)) return fail(nullptr, VL2_E_ARG, "workspace must be 256-byte aligned");
-  const Plan pl = make_plan(g);
+  const Plan pl = make_plan(g, params->precision);
   if (bytes < pl.total) return fail(nullptr, VL2_E_NOMEM, "workspace smaller than vl2_workspace_bytes()");
   vl2_mesh* m = new (std::nothrow) vl2_mesh();
   if (!m) return fail(nullptr, VL2_E_ARG, "host allocation failed");
@@ -334,11 +335,12 @@ vl2_status vl2_mesh_create(const vl2_params* params, void* workspace, size_t byt
     m->a.u[r] = (double*)(base + pl.off_u[r]);
     for (int d = 0; d < 3; ++d) m->a.b[r][d] = (double*)(base + pl.off_b[r][d]);
   }
-  m->a.w = (double*)(base + pl.off_w);
+  m->a.w = base + pl.off_w;
   for (int d = 0; d < 3; ++d) {
-    m->a.f[d] = (double*)(base + pl.off_f[d]);
-    m->a.e[d] = (double*)(base + pl.off_e[d]);
+    m->a.f[d] = base + pl.off_f[d];
+    m->a.e[d] = base + pl.off_e[d];
   }
+  m->a.mixed = params->precision == VL2_MIXED ? 1 : 0;
   m->a.stage = (double*)(base + pl.off_stage);
   m->a.stage_elems = pl.stage_elems;
   m->a.red = (double*)(base + pl.off_red);

@@ -33,11 +33,13 @@ __host__ __device__ inline long long cell_off(const Geom& g, int k, int j, int i
 
 // Device arrays of one mesh (all inside the caller's workspace).
 struct Arrays {
-  double* u[2];      // conserved registers: [nblk][5][box]
-  double* b[2][3];   // face-field registers: [nblk][box] per direction
-  double* w;         // primitives rho, vx, vy, vz, p, bcx, bcy, bcz: [nblk][8][box]
-  double* f[3];      // fluxes per sweep direction: [nblk][7][box]
-  double* e[3];      // corner EMFs E1, E2, E3: [nblk][box]
+  double* u[2];      // conserved registers: [nblk][5][box] (FP64 in every precision)
+  double* b[2][3];   // face-field registers: [nblk][box] per direction (FP64)
+  // Stage scratch; element type double (FP64 form) or float (mixed form: FP32 reconstruction, fluxes, EMFs)
+  void* w;           // primitives rho, vx, vy, vz, p, bcx, bcy, bcz: [nblk][8][box]
+  void* f[3];        // fluxes per sweep direction: [nblk][7][box]
+  void* e[3];        // corner EMFs E1, E2, E3: [nblk][box]
+  int mixed;         // 1: scratch is float
   double* stage;     // staging for global-array I/O
   size_t stage_elems;
   double* red;       // reduction partials

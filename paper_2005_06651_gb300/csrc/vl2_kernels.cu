@@ -21,10 +21,10 @@ __device__ __forceinline__ void block_loc(const Geom& g, int b, int* loc) {
 // rate max_d (|v_d| + C_f,d) / dx_d (Sec. 2.1.7) into scal[SC_MAXRATE] (bit pattern of a positive
 // double, so an integer max is the floating max).
 // ------------------------------------------------------------------------------------------------
-template <bool DT>
+template <bool DT, class TW>
 __global__ void __launch_bounds__(256) k_prim(Geom g, double* U, const double* __restrict__ B0,
                                               const double* __restrict__ B1, const double* __restrict__ B2,
-                                              double* __restrict__ W, unsigned long long* scal, int all) {
+                                              TW* __restrict__ W, unsigned long long* scal, int all) {
   const int off = all ? 0 : NG;
   const int ex = g.mb[0] + (all ? 2 * NG : 0), ey = g.mb[1] + (all ? 2 * NG : 0), ez = g.mb[2] + (all ? 2 * NG : 0);
   const long long per = (long long)ex * ey * ez;
@@ -67,15 +67,15 @@ __global__ void __launch_bounds__(256) k_prim(Geom g, double* U, const double* _
       Ub[0] = d;
       Ub[4 * g.box] = e;
     }
-    double* Wb = W + (long long)b * 8 * g.box + c;
-    Wb[0] = d;
-    Wb[g.box] = vx;
-    Wb[2 * g.box] = vy;
-    Wb[3 * g.box] = vz;
-    Wb[4 * g.box] = p;
-    Wb[5 * g.box] = bcx;
-    Wb[6 * g.box] = bcy;
-    Wb[7 * g.box] = bcz;
+    TW* Wb = W + (long long)b * 8 * g.box + c;
+    Wb[0] = (TW)d;
+    Wb[g.box] = (TW)vx;
+    Wb[2 * g.box] = (TW)vy;
+    Wb[3 * g.box] = (TW)vz;
+    Wb[4 * g.box] = (TW)p;
+    Wb[5 * g.box] = (TW)bcx;
+    Wb[6 * g.box] = (TW)bcy;
+    Wb[7 * g.box] = (TW)bcz;
     if (DT && active) {
       const double bx2 = bcx * bcx, by2 = bcy * bcy, bz2 = bcz * bcz;
       const double rx = (fabs(vx) + fast_speed_r(id, p, bx2, by2 + bz2, g.gamma)) * g.idx[0];
@@ -108,10 +108,22 @@ cudaError_t launch_prim(const Geom& g, const Arrays& a, int reg, bool all_cells,
   const long long per = all_cells ? (long long)(g.mb[0] + 2 * NG) * (g.mb[1] + 2 * NG) * (g.mb[2] + 2 * NG)
                                   : (long long)g.mb[0] * g.mb[1] * g.mb[2];
   const unsigned grid = grid_for(per * g.nblk, 256);
-  if (want_dt)
-    k_prim<true><<<grid, 256, 0, st>>>(g, a.u[reg], a.b[reg][0], a.b[reg][1], a.b[reg][2], a.w, a.scal, all_cells);
-  else
-    k_prim<false><<<grid, 256, 0, st>>>(g, a.u[reg], a.b[reg][0], a.b[reg][1], a.b[reg][2], a.w, a.scal, all_cells);
+  const double* B0 = a.b[reg][0];
+  const double* B1 = a.b[reg][1];
+  const double* B2 = a.b[reg][2];
+  if (a.mixed) {
+    float* w = static_cast<float*>(a.w);
+    if (want_dt)
+      k_prim<true, float><<<grid, 256, 0, st>>>(g, a.u[reg], B0, B1, B2, w, a.scal, all_cells);
+    else
+      k_prim<false, float><<<grid, 256, 0, st>>>(g, a.u[reg], B0, B1, B2, w, a.scal, all_cells);
+  } else {
+    double* w = static_cast<double*>(a.w);
+    if (want_dt)
+      k_prim<true, double><<<grid, 256, 0, st>>>(g, a.u[reg], B0, B1, B2, w, a.scal, all_cells);
+    else
+      k_prim<false, double><<<grid, 256, 0, st>>>(g, a.u[reg], B0, B1, B2, w, a.scal, all_cells);
+  }
   return cudaGetLastError();
 }
 
@@ -206,17 +218,19 @@ cudaError_t launch_ghosts(const Geom& g, const Arrays& a, int reg, cudaStream_t 
 // transverse directions a = e+1, b = e+2.  Face EMFs of that component: -F_a[B_t1] on a-faces and
 // +F_b[B_t2] on b-faces (E = -v x B); cell EMFs from the primitives.  One thread per corner node.
 // ------------------------------------------------------------------------------------------------
-__device__ __forceinline__ double cell_emf(int e, const double* Wc, long long box) {
-  const double vx = Wc[box], vy = Wc[2 * box], vz = Wc[3 * box];
-  const double bx = Wc[5 * box], by = Wc[6 * box], bz = Wc[7 * box];
+template <class T>
+__device__ __forceinline__ T cell_emf(int e, const T* Wc, long long box) {
+  const T vx = Wc[box], vy = Wc[2 * box], vz = Wc[3 * box];
+  const T bx = Wc[5 * box], by = Wc[6 * box], bz = Wc[7 * box];
   if (e == 0) return vz * by - vy * bz;
   if (e == 1) return vx * bz - vz * bx;
   return vy * bx - vx * by;
 }
 
-__global__ void __launch_bounds__(256) k_emf(Geom g, const double* __restrict__ W, const double* __restrict__ F0,
-                                             const double* __restrict__ F1, const double* __restrict__ F2,
-                                             double* __restrict__ E0, double* __restrict__ E1, double* __restrict__ E2) {
+template <class T>
+__global__ void __launch_bounds__(256) k_emf(Geom g, const T* __restrict__ W, const T* __restrict__ F0,
+                                             const T* __restrict__ F1, const T* __restrict__ F2, T* __restrict__ E0,
+                                             T* __restrict__ E1, T* __restrict__ E2) {
   const int ex = g.mb[0] + 1, ey = g.mb[1] + 1, ez = g.mb[2] + 1;
   const long long per = (long long)ex * ey * ez;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -226,17 +240,17 @@ __global__ void __launch_bounds__(256) k_emf(Geom g, const double* __restrict__ 
   const int li[3] = {rem % ex + NG, (rem / ex) % ey + NG, rem / (ex * ey) + NG};
   const long long c = cell_off(g, li[2], li[1], li[0]);
   const long long stride[3] = {1LL, (long long)g.sx, (long long)g.sx * g.sy};
-  const double* F[3] = {F0, F1, F2};
-  double* E[3] = {E0, E1, E2};
-  const double* Wb = W + (long long)b * 8 * g.box;
+  const T* F[3] = {F0, F1, F2};
+  T* E[3] = {E0, E1, E2};
+  const T* Wb = W + (long long)b * 8 * g.box;
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     if (li[e] > NG + g.mb[e] - 1) continue;
     const int a = (e + 1) % 3, bq = (e + 2) % 3;
     const long long sa = stride[a], sb = stride[bq];
-    const double* Fa = F[a] + (long long)b * 7 * g.box;
-    const double* Fb = F[bq] + (long long)b * 7 * g.box;
-    double ea[2], eb[2], ec[4], ma[2], mb[2];
+    const T* Fa = F[a] + (long long)b * 7 * g.box;
+    const T* Fb = F[bq] + (long long)b * 7 * g.box;
+    T ea[2], eb[2], ec[4], ma[2], mb[2];
     ea[0] = -Fa[5 * g.box + c - sb];
     ea[1] = -Fa[5 * g.box + c];
     eb[0] = Fb[6 * g.box + c - sa];
@@ -253,9 +267,20 @@ __global__ void __launch_bounds__(256) k_emf(Geom g, const double* __restrict__ 
   }
 }
 
+template <class T>
+static void emf_typed(const Geom& g, const Arrays& a, unsigned grid, cudaStream_t st) {
+  k_emf<T><<<grid, 256, 0, st>>>(g, static_cast<const T*>(a.w), static_cast<const T*>(a.f[0]),
+                                 static_cast<const T*>(a.f[1]), static_cast<const T*>(a.f[2]),
+                                 static_cast<T*>(a.e[0]), static_cast<T*>(a.e[1]), static_cast<T*>(a.e[2]));
+}
+
 cudaError_t launch_emfs(const Geom& g, const Arrays& a, cudaStream_t st) {
   const long long per = (long long)(g.mb[0] + 1) * (g.mb[1] + 1) * (g.mb[2] + 1);
-  k_emf<<<grid_for(per * g.nblk, 256), 256, 0, st>>>(g, a.w, a.f[0], a.f[1], a.f[2], a.e[0], a.e[1], a.e[2]);
+  const unsigned grid = grid_for(per * g.nblk, 256);
+  if (a.mixed)
+    emf_typed<float>(g, a, grid, st);
+  else
+    emf_typed<double>(g, a, grid, st);
   return cudaGetLastError();
 }
 
@@ -265,11 +290,12 @@ cudaError_t launch_emfs(const Geom& g, const Arrays& a, cudaStream_t st) {
 //   B_out = B_base - h curl_h E   (B1 uses E3 along y and E2 along z, cyclically).
 // U_base / U_out may alias (the corrector updates u^n in place), so no __restrict__ here.
 // ------------------------------------------------------------------------------------------------
+template <class T>
 __global__ void __launch_bounds__(256) k_update(Geom g, const double* Ubase, double* Uout, const double* Bb0,
                                                 const double* Bb1, const double* Bb2, double* Bo0, double* Bo1,
-                                                double* Bo2, const double* __restrict__ F0, const double* __restrict__ F1,
-                                                const double* __restrict__ F2, const double* __restrict__ E0,
-                                                const double* __restrict__ E1, const double* __restrict__ E2, double h) {
+                                                double* Bo2, const T* __restrict__ F0, const T* __restrict__ F1,
+                                                const T* __restrict__ F2, const T* __restrict__ E0,
+                                                const T* __restrict__ E1, const T* __restrict__ E2, double h) {
   const int ex = g.mb[0] + 1, ey = g.mb[1] + 1, ez = g.mb[2] + 1;
   const long long per = (long long)ex * ey * ez;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -281,8 +307,8 @@ __global__ void __launch_bounds__(256) k_update(Geom g, const double* Ubase, dou
   const long long stride[3] = {1LL, (long long)g.sx, (long long)g.sx * g.sy};
   const bool inside[3] = {li[0] < NG + g.mb[0], li[1] < NG + g.mb[1], li[2] < NG + g.mb[2]};
   if (inside[0] && inside[1] && inside[2]) {
-    const double* F[3] = {F0 + (long long)b * 7 * g.box + c, F1 + (long long)b * 7 * g.box + c,
-                          F2 + (long long)b * 7 * g.box + c};
+    const T* F[3] = {F0 + (long long)b * 7 * g.box + c, F1 + (long long)b * 7 * g.box + c,
+                     F2 + (long long)b * 7 * g.box + c};
     const long long ub = (long long)b * 5 * g.box + c;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -298,8 +324,8 @@ __global__ void __launch_bounds__(256) k_update(Geom g, const double* Ubase, dou
           const int m = v - 1;
           comp = (m == d) ? 1 : ((m == (d + 1) % 3) ? 2 : 3);
         }
-        const double* fp = F[d] + (long long)comp * g.box;
-        dfl[d] = (fp[stride[d]] - fp[0]) * g.idx[d];
+        const T* fp = F[d] + (long long)comp * g.box;
+        dfl[d] = ((double)fp[stride[d]] - (double)fp[0]) * g.idx[d];  // FP64 accumulation
       }
       const double L = -((dfl[0] + dfl[1]) + dfl[2]);
       Uout[ub + (long long)v * g.box] = Ubase[ub + (long long)v * g.box] + h * L;
@@ -307,22 +333,35 @@ __global__ void __launch_bounds__(256) k_update(Geom g, const double* Ubase, dou
   }
   const double* Bb[3] = {Bb0, Bb1, Bb2};
   double* Bo[3] = {Bo0, Bo1, Bo2};
-  const double* E[3] = {E0 + (long long)b * g.box + c, E1 + (long long)b * g.box + c, E2 + (long long)b * g.box + c};
+  const T* E[3] = {E0 + (long long)b * g.box + c, E1 + (long long)b * g.box + c, E2 + (long long)b * g.box + c};
 #pragma unroll
   for (int fd = 0; fd < 3; ++fd) {
     const int a = (fd + 1) % 3, bq = (fd + 2) % 3;
     if (!inside[a] || !inside[bq]) continue;
-    const double curl = (E[bq][stride[a]] - E[bq][0]) * g.idx[a] - (E[a][stride[bq]] - E[a][0]) * g.idx[bq];
+    const double curl = ((double)E[bq][stride[a]] - (double)E[bq][0]) * g.idx[a] -
+                        ((double)E[a][stride[bq]] - (double)E[a][0]) * g.idx[bq];
     const long long o = (long long)b * g.box + c;
     Bo[fd][o] = Bb[fd][o] + h * (-curl);
   }
 }
 
+template <class T>
+static void update_typed(const Geom& g, const Arrays& a, int base_reg, int out_reg, double h, unsigned grid,
+                         cudaStream_t st) {
+  k_update<T><<<grid, 256, 0, st>>>(g, a.u[base_reg], a.u[out_reg], a.b[base_reg][0], a.b[base_reg][1],
+                                    a.b[base_reg][2], a.b[out_reg][0], a.b[out_reg][1], a.b[out_reg][2],
+                                    static_cast<const T*>(a.f[0]), static_cast<const T*>(a.f[1]),
+                                    static_cast<const T*>(a.f[2]), static_cast<const T*>(a.e[0]),
+                                    static_cast<const T*>(a.e[1]), static_cast<const T*>(a.e[2]), h);
+}
+
 cudaError_t launch_update(const Geom& g, const Arrays& a, int base_reg, int out_reg, double h, cudaStream_t st) {
   const long long per = (long long)(g.mb[0] + 1) * (g.mb[1] + 1) * (g.mb[2] + 1);
-  k_update<<<grid_for(per * g.nblk, 256), 256, 0, st>>>(
-      g, a.u[base_reg], a.u[out_reg], a.b[base_reg][0], a.b[base_reg][1], a.b[base_reg][2], a.b[out_reg][0],
-      a.b[out_reg][1], a.b[out_reg][2], a.f[0], a.f[1], a.f[2], a.e[0], a.e[1], a.e[2], h);
+  const unsigned grid = grid_for(per * g.nblk, 256);
+  if (a.mixed)
+    update_typed<float>(g, a, base_reg, out_reg, h, grid, st);
+  else
+    update_typed<double>(g, a, base_reg, out_reg, h, grid, st);
   return cudaGetLastError();
 }
 
@@ -446,26 +485,31 @@ cudaError_t launch_gather_cons(const Geom& g, const Arrays& a, double* u, double
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256) k_gather_prims(Geom g, const double* __restrict__ W, double* w) {
+template <class T>
+__global__ void __launch_bounds__(256) k_gather_prims(Geom g, const T* __restrict__ W, double* w) {
   IoIdx x;
   if (!io_index(g, x)) return;
   if (x.li[0] >= g.mb[0] || x.li[1] >= g.mb[1] || x.li[2] >= g.mb[2]) return;
   const int NX = g.N[0], NY = g.N[1], NZ = g.N[2];
   const long long n = (long long)NX * NY * NZ;
   const long long gc = ((long long)x.gi[2] * NY + x.gi[1]) * NX + x.gi[0];
-  const double* Wb = W + (long long)x.b * 8 * g.box + cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG);
+  const T* Wb = W + (long long)x.b * 8 * g.box + cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG);
 #pragma unroll
-  for (int v = 0; v < 8; ++v) w[v * n + gc] = Wb[(long long)v * g.box];
+  for (int v = 0; v < 8; ++v) w[v * n + gc] = (double)Wb[(long long)v * g.box];
 }
 
 cudaError_t launch_gather_prims(const Geom& g, const Arrays& a, double* w, cudaStream_t st) {
-  k_gather_prims<<<io_grid(g), 256, 0, st>>>(g, a.w, w);
+  if (a.mixed)
+    k_gather_prims<float><<<io_grid(g), 256, 0, st>>>(g, static_cast<const float*>(a.w), w);
+  else
+    k_gather_prims<double><<<io_grid(g), 256, 0, st>>>(g, static_cast<const double*>(a.w), w);
   return cudaGetLastError();
 }
 
 // fluxes of sweep `dir` on the global face grid [7][..]; a face on a block boundary is taken from the
 // block where it is the lower face (global face N from the last block)
-__global__ void __launch_bounds__(256) k_gather_fluxes(Geom g, int dir, const double* __restrict__ F, double* out) {
+template <class T>
+__global__ void __launch_bounds__(256) k_gather_fluxes(Geom g, int dir, const T* __restrict__ F, double* out) {
   IoIdx x;
   if (!io_index(g, x)) return;
   int gd[3] = {g.N[0], g.N[1], g.N[2]};
@@ -479,17 +523,21 @@ __global__ void __launch_bounds__(256) k_gather_fluxes(Geom g, int dir, const do
   }
   const long long nf = (long long)gd[0] * gd[1] * gd[2];
   const long long gf = ((long long)x.gi[2] * gd[1] + x.gi[1]) * gd[0] + x.gi[0];
-  const double* Fb = F + (long long)x.b * 7 * g.box + cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG);
+  const T* Fb = F + (long long)x.b * 7 * g.box + cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG);
 #pragma unroll
-  for (int n = 0; n < 7; ++n) out[n * nf + gf] = Fb[(long long)n * g.box];
+  for (int n = 0; n < 7; ++n) out[n * nf + gf] = (double)Fb[(long long)n * g.box];
 }
 
 cudaError_t launch_gather_fluxes(const Geom& g, const Arrays& a, int dir, double* out, cudaStream_t st) {
-  k_gather_fluxes<<<io_grid(g), 256, 0, st>>>(g, dir, a.f[dir], out);
+  if (a.mixed)
+    k_gather_fluxes<float><<<io_grid(g), 256, 0, st>>>(g, dir, static_cast<const float*>(a.f[dir]), out);
+  else
+    k_gather_fluxes<double><<<io_grid(g), 256, 0, st>>>(g, dir, static_cast<const double*>(a.f[dir]), out);
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256) k_gather_emfs(Geom g, int e, const double* __restrict__ E, double* out) {
+template <class T>
+__global__ void __launch_bounds__(256) k_gather_emfs(Geom g, int e, const T* __restrict__ E, double* out) {
   IoIdx x;
   if (!io_index(g, x)) return;
   int gd[3] = {g.N[0] + 1, g.N[1] + 1, g.N[2] + 1};
@@ -502,11 +550,14 @@ __global__ void __launch_bounds__(256) k_gather_emfs(Geom g, int e, const double
     }
   }
   const long long gf = ((long long)x.gi[2] * gd[1] + x.gi[1]) * gd[0] + x.gi[0];
-  out[gf] = E[(long long)x.b * g.box + cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG)];
+  out[gf] = (double)E[(long long)x.b * g.box + cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG)];
 }
 
 cudaError_t launch_gather_emfs(const Geom& g, const Arrays& a, int dir, double* out, cudaStream_t st) {
-  k_gather_emfs<<<io_grid(g), 256, 0, st>>>(g, dir, a.e[dir], out);
+  if (a.mixed)
+    k_gather_emfs<float><<<io_grid(g), 256, 0, st>>>(g, dir, static_cast<const float*>(a.e[dir]), out);
+  else
+    k_gather_emfs<double><<<io_grid(g), 256, 0, st>>>(g, dir, static_cast<const double*>(a.e[dir]), out);
   return cudaGetLastError();
 }
 

@@ -247,18 +247,19 @@ __device__ __forceinline__ R vl_slope(R qm, R q0, R qp) {
 // mean of the four face EMFs plus one quarter of the upwinded face-to-corner corrections.
 // ea[0..1]: a-face EMFs at b-index -1, 0; eb[0..1]: b-face EMFs at a-index -1, 0;
 // ec[0..3]: cell EMFs at (a-1,b-1), (a,b-1), (a-1,b), (a,b); ma, mb: the matching face mass fluxes.
-__device__ __forceinline__ double ct_pick(double m, double lo, double hi) {
-  return gt0(m) ? lo : (lt0(m) ? hi : 0.5 * (lo + hi));
+template <class R>
+__device__ __forceinline__ R ct_pick(R m, R lo, R hi) {
+  return gt0(m) ? lo : (lt0(m) ? hi : R(0.5) * (lo + hi));
 }
 
-__device__ __forceinline__ double ct_corner(const double* ea, const double* eb, const double* ec,
-                                            const double* ma, const double* mb) {
-  const double sum4 = (ea[0] + ea[1]) + (eb[0] + eb[1]);
-  const double tlo = ct_pick(ma[0], eb[0] - ec[0], eb[1] - ec[1]);
-  const double thi = ct_pick(ma[1], ec[2] - eb[0], ec[3] - eb[1]);
-  const double slo = ct_pick(mb[0], ea[0] - ec[0], ea[1] - ec[2]);
-  const double shi = ct_pick(mb[1], ec[1] - ea[0], ec[3] - ea[1]);
-  return (0.25 * sum4 + 0.25 * (tlo - thi)) + 0.25 * (slo - shi);
+template <class R>
+__device__ __forceinline__ R ct_corner(const R* ea, const R* eb, const R* ec, const R* ma, const R* mb) {
+  const R sum4 = (ea[0] + ea[1]) + (eb[0] + eb[1]);
+  const R tlo = ct_pick(ma[0], eb[0] - ec[0], eb[1] - ec[1]);
+  const R thi = ct_pick(ma[1], ec[2] - eb[0], ec[3] - eb[1]);
+  const R slo = ct_pick(mb[0], ea[0] - ec[0], ea[1] - ec[2]);
+  const R shi = ct_pick(mb[1], ec[1] - ea[0], ec[3] - ea[1]);
+  return (R(0.25) * sum4 + R(0.25) * (tlo - thi)) + R(0.25) * (slo - shi);
 }
 
 }  // namespace vl2

@@ -250,6 +250,15 @@ def linear_wave(n=32, mb=None, kind="alfven", amp=1.0e-6, geometry="cube", b_uni
 # Random-phase turbulence (Gaussian velocity field, k^-2 amplitude spectrum)
 # ------------------------------------------------------------------------------------------------
 
+def _irfftn(a, shape):
+    try:  # multithreaded when scipy is present; same transform either way
+        import scipy.fft
+
+        return scipy.fft.irfftn(a, s=shape, axes=(0, 1, 2), workers=-1)
+    except ImportError:
+        return np.fft.irfftn(a, s=shape, axes=(0, 1, 2))
+
+
 def turbulence(n=64, mb=None, seed=3003, mach=1.0, beta=1.0, gamma=5.0 / 3.0):
     """Gaussian random velocity field on the unit periodic cube.
 
@@ -274,7 +283,7 @@ def turbulence(n=64, mb=None, seed=3003, mach=1.0, beta=1.0, gamma=5.0 / 3.0):
     for _ in range(3):
         re = rng.standard_normal(kk.shape)
         im = rng.standard_normal(kk.shape)
-        field = np.fft.irfftn(amp * (re + 1j * im), s=(NX, NY, NZ))  # Hermitian by construction
+        field = _irfftn(amp * (re + 1j * im), (NX, NY, NZ))  # Hermitian by construction
         field -= field.mean()
         vel.append(np.transpose(field, (2, 1, 0)))  # (x, y, z) -> (z, y, x)
     vrms = math.sqrt(sum(float(np.mean(v ** 2)) for v in vel))
