@@ -250,6 +250,74 @@ def mixed_form(args, dev, stream, vl2, inputs):
     return res
 
 
+def batched_form(args, dev, stream, vl2, inputs):
+    """Batched form: boxes of sizes drawn from {16, 32, 48, 64}^3 (seed 3003), one MeshBlock each, periodic
+    turbulence (Mach 1, beta 1), FP64.  The same meshes are timed through the per-box launch path (new_dt +
+    step per box) and through the batch (autotuned flux shapes, K cycles as one CUDA-graph launch with
+    per-box CFL steps on the device); both start from the same state and must end bitwise equal."""
+    import numpy as np
+    import torch
+
+    nbox, K = args.batch_boxes, args.batch_steps
+    rng = np.random.Generator(np.random.PCG64(3003))
+    sizes = rng.choice([16, 32, 48, 64], size=nbox)
+    probs = [inputs.turbulence(n=int(n), mb=int(n), seed=3003 + q, mach=1.0, beta=1.0) for q, n in enumerate(sizes)]
+    meshes = [vl2.Mesh(p.nx, p.mb, p.xmin, p.xmax, p.gamma, device=dev, stream=stream) for p in probs]
+    ncell = sum(p.ncells for p in probs)
+    for m, p in zip(meshes, probs):
+        m.set_prims(p.w, p.b1, p.b2, p.b3)
+    for m in meshes:  # warm-up
+        m.step(m.new_dt())
+    for m, p in zip(meshes, probs):
+        m.set_prims(p.w, p.b1, p.b2, p.b3)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = sum(m.launch_count() for m in meshes)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for _ in range(K):
+        for m in meshes:
+            m.step(m.new_dt())
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    per_box_s = time.perf_counter() - t0
+    per_box_launches = sum(m.launch_count() for m in meshes) - launches0
+    check = [q for q in range(0, nbox, max(1, nbox // 8))]
+    ref = {q: meshes[q].get_cons() for q in check}
+    for m, p in zip(meshes, probs):
+        m.set_prims(p.w, p.b1, p.b2, p.b3)
+    batch = vl2.Batch(meshes)
+    dc, pl = batch.autotune()
+    batch.run(1, want_dt=False)  # capture-free warm-up of a one-cycle graph
+    for m, p in zip(meshes, probs):
+        m.set_prims(p.w, p.b1, p.b2, p.b3)
+    batch.run(K, want_dt=False)  # capture the K-cycle graph (untimed), then reset and time it
+    for m, p in zip(meshes, probs):
+        m.set_prims(p.w, p.b1, p.b2, p.b3)
+    torch.cuda.synchronize(dev)
+    l0 = batch.launch_count()
+    t0 = time.perf_counter()
+    e0.record(stream)
+    batch.run(K, want_dt=False)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    batched_s = time.perf_counter() - t0
+    batched_ms = e0.elapsed_time(e1)
+    batched_launches = batch.launch_count() - l0
+    same = all(all(np.array_equal(a, b) for a, b in zip(meshes[q].get_cons(), ref[q])) for q in check)
+    del batch
+    counts = {int(v): int((sizes == v).sum()) for v in (16, 32, 48, 64)}
+    return {"config": {"workload": "%d_turbulence_boxes_sizes_16_32_48_64_cubed_one_block_each" % nbox,
+                       "box_counts": counts, "cells": ncell, "steps": K, "seed": 3003, "mach": 1.0, "beta": 1.0,
+                       "dtype": "f64"},
+            "value": ncell * K / batched_s, "unit": UNIT, "ms_per_step": 1e3 * batched_s / K,
+            "device_ms_per_step": batched_ms / K, "gpu_launches_per_step": batched_launches / K,
+            "per_box_value": ncell * K / per_box_s, "per_box_ms_per_step": 1e3 * per_box_s / K,
+            "per_box_launches_per_step": per_box_launches / K, "speedup_vs_per_box": per_box_s / batched_s,
+            "autotuned": {"dc_threads": dc, "plm_lines": pl},
+            "bitwise_equal_to_per_box_path": bool(same), "checked_boxes": len(check)}
+
+
 def rms_l1(state, ref):
     import numpy as np
 
@@ -275,6 +343,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the mixed-precision and batched forms")
     ap.add_argument("--forms-n", type=int, default=512, help="grid of the mixed-precision form")
     ap.add_argument("--forms-steps", type=int, default=20)
+    ap.add_argument("--batch-boxes", type=int, default=1024)
+    ap.add_argument("--batch-steps", type=int, default=10)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -400,6 +470,8 @@ def main():
     forms = None
     if not args.no_forms:
         forms = {"mixed": mixed_form(args, dev, stream, vl2, inputs)}
+        torch.cuda.empty_cache()
+        forms["batched"] = batched_form(args, dev, stream, vl2, inputs)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

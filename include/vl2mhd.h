@@ -186,6 +186,49 @@ vl2_status vl2_profile_read(vl2_mesh* mesh, int kind, double* ms, long long* lau
 /* Number of CUDA kernels this mesh has launched since creation (every launch, profiled or not). */
 vl2_status vl2_launch_count(const vl2_mesh* mesh, long long* n);
 
+/* ---- Batched form ----------------------------------------------------------------------------
+ * Many independent meshes ("boxes", any sizes; the paper advances each MeshBlock independently between
+ * exchanges, Sec. 2.1, 2.6) advanced together: each kernel of the VL2 cycle is one launch over a
+ * (box, tile) work list that covers every box; each box keeps its own CFL time step (Sec. 2.1.7) on the
+ * device; vl2_batch_run captures K cycles in one CUDA graph and launches it once.
+ * The batch refers to the meshes' own device arrays (no copy): results are read back with the mesh calls
+ * (vl2_get_cons, vl2_new_dt, ...).  All meshes need the same Riemann solver and precision and must not
+ * be stepped through their own calls while a batch call runs; the batch uses the first mesh's stream.
+ * The caller owns the batch workspace (vl2_batch_workspace_bytes, 256-byte aligned) and the meshes; the
+ * batch must be destroyed before its meshes. */
+typedef struct vl2_batch vl2_batch;
+
+/* Bytes of device workspace for a batch of these meshes (mesh views, per-box dt, work lists).
+ * Errors: VL2_E_ARG (NULL, n <= 0, mixed solvers or precisions). */
+vl2_status vl2_batch_workspace_bytes(vl2_mesh* const* meshes, int n, size_t* bytes);
+
+/* Create the batch (builds and uploads its work lists).  Errors: VL2_E_ARG, VL2_E_NOMEM, VL2_E_CUDA. */
+vl2_status vl2_batch_create(vl2_mesh* const* meshes, int n, void* workspace, size_t bytes, vl2_batch** out);
+
+vl2_status vl2_batch_destroy(vl2_batch* batch);
+
+/* Pick the launch shapes of the flux kernels by timing them on the batch's current state (donor-cell CTA
+ * size in {64, 128, 256}, PLM lines per CTA in {4, 8, 16}); the state is not changed.  Outputs may be
+ * NULL.  Blocks.  Errors: VL2_E_STATE, VL2_E_CUDA. */
+vl2_status vl2_batch_autotune(vl2_batch* batch, int* dc_threads, int* plm_lines);
+
+/* One VL2 cycle of every box with the given per-box steps dt[n] (host or device, see `where`); the same
+ * arithmetic as vl2_step on each mesh.  Errors: VL2_E_ARG (dt not finite and positive), VL2_E_STATE,
+ * VL2_E_CUDA. */
+vl2_status vl2_batch_step(vl2_batch* batch, const double* dt, int where);
+
+/* nsteps VL2 cycles of every box, each with the box's own CFL step dt = cfl * (min over its active cells
+ * of dx_d / (|v_d| + C_f,d)) formed on the device, as one CUDA-graph launch (captured on the first call
+ * with this nsteps, then reused).  dt_last (host, n doubles, may be NULL) receives the last steps used;
+ * with dt_last NULL the call only enqueues.  Errors: VL2_E_ARG, VL2_E_STATE, VL2_E_CUDA. */
+vl2_status vl2_batch_run(vl2_batch* batch, int nsteps, double* dt_last);
+
+/* Kernels launched by this batch since creation (a graph launch counts its kernels). */
+vl2_status vl2_batch_launch_count(const vl2_batch* batch, long long* n);
+
+/* Message of the last failing batch call (or of the last failing call with no batch, if NULL). */
+const char* vl2_batch_last_error(const vl2_batch* batch);
+
 /* Largest nz that vl2_totals_noalloc accepts: its fixed scratch holds one row of partial sums per
  * z-plane (VL2_NOALLOC_MAX_NZ x 8 doubles = 256 KiB per device). */
 #define VL2_NOALLOC_MAX_NZ 4096

@@ -40,6 +40,9 @@ struct vl2_mesh {
   double acc_ms[VL2_K_COUNT] = {0};
   long long acc_n[VL2_K_COUNT] = {0}, acc_units[VL2_K_COUNT] = {0};
   long long launches = 0;
+  vl2::FluxShape fs;
+  vl2::MeshView view() const { return vl2::MeshView{g, a}; }
+  int max_mb() const { return std::max(g.mb[0], std::max(g.mb[1], g.mb[2])); }
   ~vl2_mesh() {
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
   }
@@ -269,24 +272,27 @@ long long flux_faces(const Geom& g, int d) {
 }
 
 cudaError_t k_prim(vl2_mesh* m, int reg, bool dt) {
-  return timed(m, VL2_K_PRIM, cells_all(m->g), [&] { return vl2::launch_prim(m->g, m->a, reg, true, dt, m->st); });
+  return timed(m, VL2_K_PRIM, cells_all(m->g),
+               [&] { return vl2::launch_prim(m->view(), nullptr, reg, true, dt, m->st); });
 }
 cudaError_t k_ghosts(vl2_mesh* m, int reg) {
-  return timed(m, VL2_K_GHOSTS, ghost_elems(m->g), [&] { return vl2::launch_ghosts(m->g, m->a, reg, m->st); });
+  return timed(m, VL2_K_GHOSTS, ghost_elems(m->g), [&] { return vl2::launch_ghosts(m->view(), nullptr, reg, m->st); });
 }
 cudaError_t k_fluxes(vl2_mesh* m, int reg, int recon) {
   for (int d = 0; d < 3; ++d) {
-    cudaError_t e = timed(m, recon == VL2_DC ? VL2_K_FLUX_DC : VL2_K_FLUX_PLM, flux_faces(m->g, d),
-                          [&] { return vl2::launch_flux(m->g, m->a, reg, recon, m->p.riemann, d, m->st); });
+    cudaError_t e = timed(m, recon == VL2_DC ? VL2_K_FLUX_DC : VL2_K_FLUX_PLM, flux_faces(m->g, d), [&] {
+      return vl2::launch_flux(m->view(), nullptr, reg, recon, m->p.riemann, d, m->fs, m->max_mb(), m->st);
+    });
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 cudaError_t k_emfs(vl2_mesh* m) {
-  return timed(m, VL2_K_EMF, nodes(m->g), [&] { return vl2::launch_emfs(m->g, m->a, m->st); });
+  return timed(m, VL2_K_EMF, nodes(m->g), [&] { return vl2::launch_emfs(m->view(), nullptr, m->st); });
 }
 cudaError_t k_update(vl2_mesh* m, int base, int out, double h) {
-  return timed(m, VL2_K_UPDATE, nodes(m->g), [&] { return vl2::launch_update(m->g, m->a, base, out, h, m->st); });
+  return timed(m, VL2_K_UPDATE, nodes(m->g),
+               [&] { return vl2::launch_update(m->view(), nullptr, base, out, h, nullptr, 0.0, m->st); });
 }
 
 vl2_status ensure_prims(vl2_mesh* m) {
@@ -372,7 +378,8 @@ vl2_status vl2_mesh_create(const vl2_params* params, void* workspace, size_t byt
               ok ? (q[2] * g.nb[1] + q[1]) * g.nb[0] + q[0] : -1;
         }
   }
-  cudaError_t e = cudaMemsetAsync(workspace, 0, pl.total, m->st);
+  cudaError_t e = vl2::prepare_kernel_attributes();
+  if (e == cudaSuccess) e = cudaMemsetAsync(workspace, 0, pl.total, m->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
   if (e != cudaSuccess) {
     delete m;
@@ -656,5 +663,406 @@ vl2_status vl2_launch_count(const vl2_mesh* m, long long* n) {
 }
 
 const char* vl2_last_error(const vl2_mesh* mesh) { return mesh ? mesh->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"
+
+/* =============================================================================================
+ * Batched form: many independent meshes (boxes) advanced by one launch per kernel over a (box, tile)
+ * work list; per-box CFL time steps stay on the device; K cycles are captured in one CUDA graph.
+ * =========================================================================================== */
+struct vl2_batch {
+  enum { W_PRIM, W_GHOSTS, W_NODES, W_DC, W_PLM = W_DC + 3, W_COUNT = W_PLM + 3 };
+  std::vector<vl2_mesh*> meshes;
+  int n = 0;
+  cudaStream_t st = nullptr;
+  vl2::MeshView* dviews = nullptr;
+  double* ddt = nullptr;
+  double* dcfl = nullptr;
+  vl2::WorkItem* dwork[W_COUNT] = {nullptr};
+  size_t cap[W_COUNT] = {0};
+  int nwork[W_COUNT] = {0};
+  vl2::FluxShape fs;
+  int max_mb = 1;
+  int riemann = VL2_HLLD;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int graph_steps = 0;
+  long long launches = 0;
+  // Graphs are captured and launched on a stream of the batch's own (the meshes' stream may be the legacy
+  // default stream, which cannot be captured), ordered against the meshes' stream with two events.
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaStream_t cur = nullptr;  // stream the kernels of the current call go to
+  std::string err;
+  ~vl2_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
+};
+
+namespace {
+
+const int kDcCandidates[3] = {64, 128, 256};
+const int kPlmCandidates[3] = {4, 8, 16};
+
+vl2_status bfail(vl2_batch* b, vl2_status s, const std::string& msg) {
+  if (b)
+    b->err = msg;
+  else
+    g_err = msg;
+  return s;
+}
+
+#define VL2_BCHECK(b, call)                                                                              \
+  do {                                                                                                  \
+    cudaError_t e_ = (call);                                                                            \
+    if (e_ != cudaSuccess) return bfail((b), VL2_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// tiles of kernel type w for one mesh under flux shape fs
+long long batch_tiles(const vl2_mesh* m, int w, const vl2::FluxShape& fs, int max_mb) {
+  const vl2::Geom& g = m->g;
+  if (w == vl2_batch::W_PRIM) return vl2::tiles_prim(g);
+  if (w == vl2_batch::W_GHOSTS) return vl2::tiles_ghosts(g);
+  if (w == vl2_batch::W_NODES) return vl2::tiles_nodes(g);
+  if (w < vl2_batch::W_PLM) return vl2::tiles_flux_dc(g, w - vl2_batch::W_DC, fs);
+  const int d = w - vl2_batch::W_PLM;
+  vl2::FluxShape f2 = fs;
+  f2.plm_lines = vl2::plm_lines_for(g, d, fs, max_mb);
+  return vl2::tiles_flux_plm(g, d, f2);
+}
+
+// capacity of each work list: the most tiles any candidate launch shape produces
+size_t batch_capacity(const std::vector<vl2_mesh*>& ms, int w, int max_mb) {
+  size_t best = 0;
+  for (int dc : kDcCandidates)
+    for (int pl : kPlmCandidates) {
+      vl2::FluxShape fs;
+      fs.dc_threads = dc;
+      fs.plm_lines = pl;
+      size_t tot = 0;
+      for (const vl2_mesh* m : ms) tot += (size_t)batch_tiles(m, w, fs, max_mb);
+      best = std::max(best, tot);
+    }
+  return best;
+}
+
+vl2_status batch_check(vl2_mesh* const* meshes, int n, std::string& msg) {
+  if (!meshes || n <= 0) {
+    msg = "meshes is NULL or n <= 0";
+    return VL2_E_ARG;
+  }
+  for (int q = 0; q < n; ++q) {
+    if (!meshes[q]) {
+      msg = "NULL mesh in the batch";
+      return VL2_E_ARG;
+    }
+    if (meshes[q]->p.riemann != meshes[0]->p.riemann || meshes[q]->p.precision != meshes[0]->p.precision) {
+      msg = "all meshes of a batch need the same Riemann solver and precision";
+      return VL2_E_ARG;
+    }
+  }
+  return VL2_OK;
+}
+
+struct BatchPlan {
+  size_t off_views, off_dt, off_cfl, off_work[vl2_batch::W_COUNT], total;
+  size_t cap[vl2_batch::W_COUNT];
+};
+
+BatchPlan batch_plan(const std::vector<vl2_mesh*>& ms, int max_mb) {
+  BatchPlan pl;
+  size_t o = 0;
+  pl.off_views = o;
+  o = align256(o + ms.size() * sizeof(vl2::MeshView));
+  pl.off_dt = o;
+  o = align256(o + ms.size() * sizeof(double));
+  pl.off_cfl = o;
+  o = align256(o + ms.size() * sizeof(double));
+  for (int w = 0; w < vl2_batch::W_COUNT; ++w) {
+    pl.cap[w] = batch_capacity(ms, w, max_mb);
+    pl.off_work[w] = o;
+    o = align256(o + pl.cap[w] * sizeof(vl2::WorkItem));
+  }
+  pl.total = o;
+  return pl;
+}
+
+// (re)build the work lists for the batch's flux shape and upload them
+vl2_status batch_lists(vl2_batch* B) {
+  for (int w = 0; w < vl2_batch::W_COUNT; ++w) {
+    std::vector<vl2::WorkItem> list;
+    for (int q = 0; q < B->n; ++q) {
+      const long long t = batch_tiles(B->meshes[q], w, B->fs, B->max_mb);
+      for (long long i = 0; i < t; ++i) list.push_back(vl2::WorkItem{q, (int)i});
+    }
+    if (list.size() > B->cap[w] || list.size() > (size_t)INT32_MAX) return bfail(B, VL2_E_ARG, "work list overflow");
+    B->nwork[w] = (int)list.size();
+    VL2_BCHECK(B, cudaMemcpyAsync(B->dwork[w], list.data(), list.size() * sizeof(vl2::WorkItem),
+                                  cudaMemcpyHostToDevice, B->st));
+  }
+  VL2_BCHECK(B, cudaStreamSynchronize(B->st));
+  return VL2_OK;
+}
+
+vl2::Dispatch disp(const vl2_batch* B, int w) {
+  vl2::Dispatch d;
+  d.views = B->dviews;
+  d.work = B->dwork[w];
+  d.nwork = B->nwork[w];
+  return d;
+}
+
+// enqueue the flux launches of one reconstruction for every box
+cudaError_t batch_fluxes(vl2_batch* B, int reg, int recon) {
+  const vl2::MeshView v0 = B->meshes[0]->view();
+  for (int d = 0; d < 3; ++d) {
+    const vl2::Dispatch dd = disp(B, (recon == VL2_DC ? vl2_batch::W_DC : vl2_batch::W_PLM) + d);
+    cudaError_t e = vl2::launch_flux(v0, &dd, reg, recon, B->riemann, d, B->fs, B->max_mb, B->cur);
+    ++B->launches;
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// one VL2 cycle of every box; h = beta * dt[box] with dt in device memory.  With device_dt the cycle
+// first turns each box's reduced CFL rate into its dt (Sec. 2.1.7 per box), else it only resets the rates.
+cudaError_t batch_cycle(vl2_batch* B, bool device_dt) {
+  const vl2::MeshView v0 = B->meshes[0]->view();
+  cudaError_t e;
+  const vl2::Dispatch dp = disp(B, vl2_batch::W_PRIM), dg = disp(B, vl2_batch::W_GHOSTS),
+                      dn = disp(B, vl2_batch::W_NODES);
+  if ((e = vl2::launch_batch_dt(B->dviews, B->n, device_dt ? B->dcfl : nullptr, B->ddt, B->cur)) != cudaSuccess) return e;
+  if ((e = batch_fluxes(B, 0, VL2_DC)) != cudaSuccess) return e;
+  if ((e = vl2::launch_emfs(v0, &dn, B->cur)) != cudaSuccess) return e;
+  if ((e = vl2::launch_update(v0, &dn, 0, 1, 0.0, B->ddt, 0.5, B->cur)) != cudaSuccess) return e;
+  if ((e = vl2::launch_ghosts(v0, &dg, 1, B->cur)) != cudaSuccess) return e;
+  if ((e = vl2::launch_prim(v0, &dp, 1, true, false, B->cur)) != cudaSuccess) return e;
+  if ((e = batch_fluxes(B, 1, VL2_PLM)) != cudaSuccess) return e;
+  if ((e = vl2::launch_emfs(v0, &dn, B->cur)) != cudaSuccess) return e;
+  if ((e = vl2::launch_update(v0, &dn, 0, 0, 0.0, B->ddt, 1.0, B->cur)) != cudaSuccess) return e;
+  if ((e = vl2::launch_ghosts(v0, &dg, 0, B->cur)) != cudaSuccess) return e;
+  if ((e = vl2::launch_prim(v0, &dp, 0, true, true, B->cur)) != cudaSuccess) return e;
+  B->launches += 11;  // plus the 6 flux launches counted in batch_fluxes
+  return cudaSuccess;
+}
+
+// make sure every box has current primitives and a reduced CFL rate
+vl2_status batch_ready(vl2_batch* B) {
+  bool all = true;
+  for (vl2_mesh* m : B->meshes) {
+    if (!m->initialized) return bfail(B, VL2_E_STATE, "a mesh of the batch has no state (vl2_set_prims)");
+    all = all && m->w_valid && m->dt_pending;
+  }
+  if (!all) {
+    const vl2::MeshView v0 = B->meshes[0]->view();
+    const vl2::Dispatch dp = disp(B, vl2_batch::W_PRIM);
+    VL2_BCHECK(B, vl2::launch_batch_dt(B->dviews, B->n, nullptr, B->ddt, B->cur));
+    VL2_BCHECK(B, vl2::launch_prim(v0, &dp, 0, true, true, B->cur));
+    B->launches += 2;
+    for (vl2_mesh* m : B->meshes) m->w_valid = m->dt_pending = true;
+  }
+  return VL2_OK;
+}
+
+void batch_mark(vl2_batch* B) {
+  for (vl2_mesh* m : B->meshes) m->w_valid = m->dt_pending = true;
+}
+
+}  // namespace
+
+extern "C" {
+
+vl2_status vl2_batch_workspace_bytes(vl2_mesh* const* meshes, int n, size_t* bytes) {
+  std::string msg;
+  vl2_status s = batch_check(meshes, n, msg);
+  if (s != VL2_OK) return bfail(nullptr, s, msg);
+  if (!bytes) return bfail(nullptr, VL2_E_ARG, "bytes is NULL");
+  std::vector<vl2_mesh*> ms(meshes, meshes + n);
+  int max_mb = 1;
+  for (vl2_mesh* m : ms) max_mb = std::max(max_mb, m->max_mb());
+  *bytes = batch_plan(ms, max_mb).total;
+  return VL2_OK;
+}
+
+vl2_status vl2_batch_create(vl2_mesh* const* meshes, int n, void* workspace, size_t bytes, vl2_batch** out) {
+  if (!out) return bfail(nullptr, VL2_E_ARG, "out is NULL");
+  *out = nullptr;
+  std::string msg;
+  vl2_status s = batch_check(meshes, n, msg);
+  if (s != VL2_OK) return bfail(nullptr, s, msg);
+  if (!workspace || ((uintptr_t)workspace & 255u)) return bfail(nullptr, VL2_E_ARG, "workspace must be 256-byte aligned");
+  vl2_batch* B = new (std::nothrow) vl2_batch();
+  if (!B) return bfail(nullptr, VL2_E_ARG, "host allocation failed");
+  B->meshes.assign(meshes, meshes + n);
+  B->n = n;
+  B->st = meshes[0]->st;
+  B->cur = B->st;
+  if (cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    delete B;
+    return bfail(nullptr, VL2_E_CUDA, "batch stream/event creation failed");
+  }
+  B->riemann = meshes[0]->p.riemann;
+  for (vl2_mesh* m : B->meshes) B->max_mb = std::max(B->max_mb, m->max_mb());
+  const BatchPlan pl = batch_plan(B->meshes, B->max_mb);
+  if (bytes < pl.total) {
+    delete B;
+    return bfail(nullptr, VL2_E_NOMEM, "workspace smaller than vl2_batch_workspace_bytes()");
+  }
+  char* base = (char*)workspace;
+  B->dviews = (vl2::MeshView*)(base + pl.off_views);
+  B->ddt = (double*)(base + pl.off_dt);
+  B->dcfl = (double*)(base + pl.off_cfl);
+  for (int w = 0; w < vl2_batch::W_COUNT; ++w) {
+    B->dwork[w] = (vl2::WorkItem*)(base + pl.off_work[w]);
+    B->cap[w] = pl.cap[w];
+  }
+  std::vector<vl2::MeshView> views;
+  std::vector<double> cfl;
+  for (vl2_mesh* m : B->meshes) {
+    views.push_back(m->view());
+    cfl.push_back(m->p.cfl);
+  }
+  cudaError_t e = cudaMemcpyAsync(B->dviews, views.data(), views.size() * sizeof(vl2::MeshView),
+                                  cudaMemcpyHostToDevice, B->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(B->dcfl, cfl.data(), cfl.size() * sizeof(double), cudaMemcpyHostToDevice, B->st);
+  if (e != cudaSuccess) {
+    delete B;
+    return bfail(nullptr, VL2_E_CUDA, std::string("batch upload: ") + cudaGetErrorString(e));
+  }
+  if ((s = batch_lists(B)) != VL2_OK) {
+    g_err = B->err;
+    delete B;
+    return s;
+  }
+  *out = B;
+  return VL2_OK;
+}
+
+vl2_status vl2_batch_destroy(vl2_batch* batch) {
+  delete batch;
+  return VL2_OK;
+}
+
+vl2_status vl2_batch_autotune(vl2_batch* B, int* dc_threads, int* plm_lines) {
+  if (!B) return bfail(nullptr, VL2_E_ARG, "batch is NULL");
+  B->cur = B->st;
+  vl2_status s = batch_ready(B);
+  if (s != VL2_OK) return s;
+  cudaEvent_t e0, e1;
+  VL2_BCHECK(B, cudaEventCreate(&e0));
+  VL2_BCHECK(B, cudaEventCreate(&e1));
+  float best = 1e30f;
+  vl2::FluxShape best_fs = B->fs;
+  for (int dc : kDcCandidates)
+    for (int pl : kPlmCandidates) {
+      B->fs.dc_threads = dc;
+      B->fs.plm_lines = pl;
+      if ((s = batch_lists(B)) != VL2_OK) break;
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {  // the flux launches only write flux scratch: the state is untouched
+        VL2_BCHECK(B, cudaEventRecord(e0, B->st));
+        VL2_BCHECK(B, batch_fluxes(B, 0, VL2_DC));
+        VL2_BCHECK(B, batch_fluxes(B, 0, VL2_PLM));
+        VL2_BCHECK(B, cudaEventRecord(e1, B->st));
+        VL2_BCHECK(B, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        VL2_BCHECK(B, cudaEventElapsedTime(&ms, e0, e1));
+        tmin = std::min(tmin, ms);
+      }
+      if (tmin < best) {
+        best = tmin;
+        best_fs = B->fs;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != VL2_OK) return s;
+  B->fs = best_fs;
+  if ((s = batch_lists(B)) != VL2_OK) return s;
+  if (B->exec) {  // the captured graph used the old launch shapes
+    cudaGraphExecDestroy(B->exec);
+    cudaGraphDestroy(B->graph);
+    B->exec = nullptr;
+    B->graph = nullptr;
+    B->graph_steps = 0;
+  }
+  if (dc_threads) *dc_threads = B->fs.dc_threads;
+  if (plm_lines) *plm_lines = B->fs.plm_lines;
+  return VL2_OK;
+}
+
+vl2_status vl2_batch_step(vl2_batch* B, const double* dt, int where) {
+  if (!B || !dt || bad_where(where)) return bfail(B, VL2_E_ARG, "NULL argument or bad where");
+  B->cur = B->st;
+  if (where == VL2_HOST)
+    for (int q = 0; q < B->n; ++q)
+      if (!(dt[q] > 0.0) || !std::isfinite(dt[q])) return bfail(B, VL2_E_ARG, "dt must be finite and positive");
+  vl2_status s = batch_ready(B);
+  if (s != VL2_OK) return s;
+  VL2_BCHECK(B, cudaMemcpyAsync(B->ddt, dt, B->n * sizeof(double),
+                                where == VL2_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, B->st));
+  VL2_BCHECK(B, batch_cycle(B, false));
+  batch_mark(B);
+  if (where == VL2_HOST) VL2_BCHECK(B, cudaStreamSynchronize(B->st));  // the caller may reuse dt
+  return VL2_OK;
+}
+
+vl2_status vl2_batch_run(vl2_batch* B, int nsteps, double* dt_last) {
+  if (!B || nsteps <= 0) return bfail(B, VL2_E_ARG, "NULL batch or nsteps <= 0");
+  B->cur = B->st;
+  vl2_status s = batch_ready(B);
+  if (s != VL2_OK) return s;
+  VL2_BCHECK(B, cudaEventRecord(B->ev_in, B->st));
+  VL2_BCHECK(B, cudaStreamWaitEvent(B->cap_stream, B->ev_in, 0));
+  if (!B->exec || B->graph_steps != nsteps) {
+    if (B->exec) {
+      cudaGraphExecDestroy(B->exec);
+      cudaGraphDestroy(B->graph);
+      B->exec = nullptr;
+      B->graph = nullptr;
+    }
+    B->cur = B->cap_stream;
+    VL2_BCHECK(B, cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    const long long l0 = B->launches;
+    for (int k = 0; k < nsteps && e == cudaSuccess; ++k) e = batch_cycle(B, true);
+    B->launches = l0;  // counted when the graph runs
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(B->cap_stream, &graph);
+    B->cur = B->st;
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return bfail(B, VL2_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    B->graph = graph;
+    VL2_BCHECK(B, cudaGraphInstantiate(&B->exec, B->graph, 0));
+    B->graph_steps = nsteps;
+  }
+  VL2_BCHECK(B, cudaGraphLaunch(B->exec, B->cap_stream));
+  VL2_BCHECK(B, cudaEventRecord(B->ev_out, B->cap_stream));
+  VL2_BCHECK(B, cudaStreamWaitEvent(B->st, B->ev_out, 0));
+  B->launches += 17LL * nsteps;
+  batch_mark(B);
+  if (dt_last) {
+    VL2_BCHECK(B, cudaMemcpyAsync(dt_last, B->ddt, B->n * sizeof(double), cudaMemcpyDeviceToHost, B->st));
+    VL2_BCHECK(B, cudaStreamSynchronize(B->st));
+  }
+  return VL2_OK;
+}
+
+vl2_status vl2_batch_launch_count(const vl2_batch* B, long long* n) {
+  if (!B || !n) return bfail(nullptr, VL2_E_ARG, "NULL argument");
+  *n = B->launches;
+  return VL2_OK;
+}
+
+const char* vl2_batch_last_error(const vl2_batch* B) { return B ? B->err.c_str() : g_err.c_str(); }
 
 }  // extern "C"

@@ -1,22 +1,29 @@
-// Face-flux kernels of the VL2 MHD step: reconstruction (donor cell or PLM with the van Leer limiter,
-// Sec. 3.2.1) and the HLLD / HLLE Riemann fluxes (Sec. 3.2.2) on every face a MeshBlock needs.
+// Face-flux kernels of the VL2 MHD step: reconstruction (donor cell, or PLM with the van Leer limiter,
+// Sec. 3.2.1) and the HLLD / HLLE Riemann fluxes (Sec. 3.2.2) on every face a MeshBlock needs.  Each
+// kernel runs either on one mesh (tile = blockIdx.x) or on a batch of meshes through a (box, tile)
+// work list; the mesh view is staged in shared memory once per CTA.
 #include "vl2_internal.h"
 #include "vl2_physics.cuh"
 
 namespace vl2 {
 
-// One thread per face.  Faces of direction DIR cover the block's active faces along DIR (ng .. ng+mb)
-// and the active cells plus one ghost layer transversally (ng-1 .. ng+mb), which feed the corner EMFs
-// on the block surface.  W: [nblk][8][box] primitives incl. ghosts; Bn: face field of direction DIR.
+// ------------------------------------------------------------------------------------------------
+// Predictor fluxes, one thread per face.  Faces of direction DIR cover the block's active faces along
+// DIR (ng .. ng+mb) and the active cells plus one ghost layer transversally (ng-1 .. ng+mb), which feed
+// the corner EMFs on the block surface.
+// ------------------------------------------------------------------------------------------------
 template <int DIR, int REC, int RS, class T>
-__global__ void __launch_bounds__(128) k_flux(Geom g, const T* __restrict__ W, const double* __restrict__ Bn,
-                                              T* __restrict__ F) {
+__global__ void __launch_bounds__(256) k_flux(MeshView single, const MeshView* views, const WorkItem* work, int reg) {
+  __shared__ MeshView sv;
+  int tile;
+  const MeshView& V = stage_view(sv, single, views, work, tile);
+  const Geom& g = V.g;
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   const int rx = g.mb[0] + (DIR == 0 ? 1 : 2);
   const int ry = g.mb[1] + (DIR == 1 ? 1 : 2);
   const int rz = g.mb[2] + (DIR == 2 ? 1 : 2);
   const long long per = (long long)rx * ry * rz;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long t = (long long)tile * blockDim.x + threadIdx.x;
   if (t >= per * g.nblk) return;
   const int b = (int)(t / per);
   int rem = (int)(t - (long long)b * per);
@@ -26,7 +33,7 @@ __global__ void __launch_bounds__(128) k_flux(Geom g, const T* __restrict__ W, c
   const int k = rem / ry + (DIR == 2 ? NG : NG - 1);
   const long long c = cell_off(g, k, j, i);
   const long long sd = (DIR == 0) ? 1LL : ((DIR == 1) ? (long long)g.sx : (long long)g.sx * g.sy);
-  const T* Wb = W + (long long)b * 8 * g.box;
+  const T* Wb = static_cast<const T*>(V.a.w) + (long long)b * 8 * g.box;
   const int var[7] = {0, 1 + DIR, 1 + T1, 1 + T2, 4, 5 + T1, 5 + T2};
   T wl[7], wr[7];
 #pragma unroll
@@ -41,23 +48,25 @@ __global__ void __launch_bounds__(128) k_flux(Geom g, const T* __restrict__ W, c
       wr[n] = q0 - T(0.5) * vl_slope(qm1, q0, qp1);
     }
   }
-  const T bn = (T)Bn[(long long)b * g.box + c];
+  const T bn = (T)V.a.b[reg][DIR][(long long)b * g.box + c];
   T f[7];
   if (RS == RS_HLLD)
     flux_hlld<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, f);
   else
     flux_hlle<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, f);
-  T* Fb = F + (long long)b * 7 * g.box + c;
+  T* Fb = static_cast<T*>(V.a.f[DIR]) + (long long)b * 7 * g.box + c;
 #pragma unroll
   for (int n = 0; n < 7; ++n) Fb[(long long)n * g.box] = f[n];
 }
 
+// ------------------------------------------------------------------------------------------------
 // Corrector fluxes with each cell's PLM reconstruction formed once (Sec. 3.2.1).  A CTA takes P lines
 // of faces along DIR: phase A reconstructs the mb+2 cells of each line (ng-1 .. ng+mb) into shared
 // memory (face values q -+ delta/2 of 7 variables), phase B solves the mb+1 Riemann problems of each line
-// from shared memory.  The 7 limiter denominators of a cell share one division (simultaneous inversion:
-// reciprocals of a product and of its prefix products); a product outside the normal range falls back
-// to one division per variable.
+// from shared memory.  In FP64 the 7 limiter denominators of a cell share one division (simultaneous
+// inversion: the reciprocal of their product and of its prefix products); a product outside the normal
+// range falls back to one division per variable.
+// ------------------------------------------------------------------------------------------------
 template <int DIR>
 struct LineMap {
   // transverse directions ordered so that the fastest-varying memory index comes first
@@ -71,10 +80,14 @@ __device__ __forceinline__ bool normal_pos(double x) {
 }
 
 template <int DIR, int RS, class T>
-__global__ void __launch_bounds__(256, 2) k_flux_plm(Geom g, const T* __restrict__ W,
-                                                     const double* __restrict__ Bn, T* __restrict__ F, int P) {
+__global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const MeshView* views, const WorkItem* work,
+                                                     int reg, int P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
+  __shared__ MeshView sv;
+  int tile_all;
+  const MeshView& V = stage_view(sv, single, views, work, tile_all);
+  const Geom& g = V.g;
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   constexpr int TA = LineMap<DIR>::TA, TB = LineMap<DIR>::TB;
   const int L = g.mb[DIR] + 2;   // reconstructed cells per line
@@ -82,11 +95,11 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(Geom g, const T* __restrict
   const int na = g.mb[TA] + 2, nb = g.mb[TB] + 2;
   const int nlines = na * nb;
   const int tiles = (nlines + P - 1) / P;
-  const int b = blockIdx.x / tiles;
-  const int tile = blockIdx.x - b * tiles;
+  const int b = tile_all / tiles;
+  const int tile = tile_all - b * tiles;
   const long long stride[3] = {1LL, (long long)g.sx, (long long)g.sx * g.sy};
   const long long sd = stride[DIR];
-  const T* Wb = W + (long long)b * 8 * g.box;
+  const T* Wb = static_cast<const T*>(V.a.w) + (long long)b * 8 * g.box;
   const int var[7] = {0, 1 + DIR, 1 + T1, 1 + T2, 4, 5 + T1, 5 + T2};
   // shared layout: the fastest thread index is contiguous
   auto sidx = [&](int v, int side, int p, int c) -> int {
@@ -146,6 +159,7 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(Geom g, const T* __restrict
   }
   __syncthreads();
   // phase B: Riemann problems of the faces ng .. ng+mb of every line
+  const double* Bn = V.a.b[reg][DIR];
   for (int t = threadIdx.x; t < P * NF; t += blockDim.x) {
     const int p = (DIR == 0) ? t / NF : t % P;
     const int f = (DIR == 0) ? t % NF : t / P;
@@ -168,63 +182,98 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(Geom g, const T* __restrict
       flux_hlld<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, fl);
     else
       flux_hlle<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, fl);
-    T* Fb = F + (long long)b * 7 * g.box + o;
+    T* Fb = static_cast<T*>(V.a.f[DIR]) + (long long)b * 7 * g.box + o;
 #pragma unroll
     for (int n = 0; n < 7; ++n) Fb[(long long)n * g.box] = fl[n];
   }
 }
 
-constexpr size_t PLM_SMEM_MAX = 64 * 1024;  // shared bytes per CTA (two CTAs per SM)
+// ------------------------------------------------------------------------------------------------
+// launch shapes and launchers
+// ------------------------------------------------------------------------------------------------
+constexpr size_t PLM_SMEM_MAX = 112 * 1024;  // shared bytes one CTA may take (two fit in an SM)
 
-template <int DIR, int RS, class T>
-static cudaError_t launch_plm(const Geom& g, const T* w, const double* bn, T* f, cudaStream_t st) {
-  constexpr int TA = LineMap<DIR>::TA, TB = LineMap<DIR>::TB;
-  const size_t per_line = (size_t)(g.mb[DIR] + 2) * 14 * sizeof(T);
-  int P = (int)(PLM_SMEM_MAX / per_line);
-  P = P < 1 ? 1 : (P > 16 ? 16 : P);
-  const int nlines = (g.mb[TA] + 2) * (g.mb[TB] + 2);
-  const int tiles = (nlines + P - 1) / P;
-  const size_t shmem = (size_t)P * per_line;
-  if (shmem > PLM_SMEM_MAX) return cudaErrorInvalidValue;  // a line longer than the shared budget
-  cudaError_t e = cudaFuncSetAttribute(k_flux_plm<DIR, RS, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)PLM_SMEM_MAX);
-  if (e != cudaSuccess) return e;
-  k_flux_plm<DIR, RS, T><<<(unsigned)((long long)tiles * g.nblk), 256, shmem, st>>>(g, w, bn, f, P);
-  return cudaGetLastError();
+static int lines_ta(const Geom& g, int dir) { return g.mb[dir == 0 ? 1 : 0] + 2; }
+static int lines_tb(const Geom& g, int dir) { return g.mb[dir == 2 ? 1 : 2] + 2; }
+
+// Lines per CTA: the requested count, reduced until a CTA's shared memory fits (max_mb = the longest
+// line of any mesh sharing the launch).
+int plm_lines_for(const Geom& g, int dir, const FluxShape& fs, int max_mb) {
+  (void)g;
+  (void)dir;
+  const size_t per_line = (size_t)(max_mb + 2) * 14 * sizeof(double);
+  int P = fs.plm_lines > 0 ? fs.plm_lines : 16;
+  while (P > 1 && (size_t)P * per_line > PLM_SMEM_MAX) --P;
+  return P;
 }
 
-template <int DIR, int REC, int RS, class T>
-static cudaError_t launch_one(const Geom& g, const T* w, const double* bn, T* f, cudaStream_t st) {
-  const long long per = (long long)(g.mb[0] + (DIR == 0 ? 1 : 2)) * (g.mb[1] + (DIR == 1 ? 1 : 2)) *
-                        (g.mb[2] + (DIR == 2 ? 1 : 2));
-  const long long n = per * g.nblk;
-  const int threads = 128;
-  const long long blocks = (n + threads - 1) / threads;
-  k_flux<DIR, REC, RS, T><<<(unsigned)blocks, threads, 0, st>>>(g, w, bn, f);
-  return cudaGetLastError();
+long long tiles_flux_dc(const Geom& g, int dir, const FluxShape& fs) {
+  long long n = g.nblk;
+  for (int q = 0; q < 3; ++q) n *= g.mb[q] + (q == dir ? 1 : 2);
+  return (n + fs.dc_threads - 1) / fs.dc_threads;
+}
+
+long long tiles_flux_plm(const Geom& g, int dir, const FluxShape& fs) {
+  const int P = fs.plm_lines;
+  const long long nlines = (long long)lines_ta(g, dir) * lines_tb(g, dir);
+  return (long long)g.nblk * ((nlines + P - 1) / P);
+}
+
+template <class K>
+static cudaError_t set_smem_attr(K kern) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PLM_SMEM_MAX);
 }
 
 template <int DIR, int RS, class T>
-static cudaError_t launch_typed(const Geom& g, const Arrays& a, int reg, int recon, cudaStream_t st) {
-  const T* w = static_cast<const T*>(a.w);
-  T* f = static_cast<T*>(a.f[DIR]);
-  if (recon == REC_PLM) return launch_plm<DIR, RS, T>(g, w, a.b[reg][DIR], f, st);
-  return launch_one<DIR, REC_DC, RS, T>(g, w, a.b[reg][DIR], f, st);
+static cudaError_t launch_typed(const MeshView& v, const Dispatch* d, int reg, int recon, const FluxShape& fs,
+                                int max_mb, cudaStream_t st) {
+  const Geom& g = v.g;
+  if (recon == REC_PLM) {
+    FluxShape f2 = fs;
+    f2.plm_lines = plm_lines_for(g, DIR, fs, max_mb);
+    const size_t shmem = (size_t)f2.plm_lines * (max_mb + 2) * 14 * sizeof(T);
+    const long long grid = d ? d->nwork : tiles_flux_plm(g, DIR, f2);
+    if (grid <= 0) return cudaSuccess;
+    k_flux_plm<DIR, RS, T><<<(unsigned)grid, 256, shmem, st>>>(v, d ? d->views : nullptr, d ? d->work : nullptr, reg,
+                                                              f2.plm_lines);
+    return cudaGetLastError();
+  }
+  const long long grid = d ? d->nwork : tiles_flux_dc(g, DIR, fs);
+  if (grid <= 0) return cudaSuccess;
+  k_flux<DIR, REC_DC, RS, T><<<(unsigned)grid, fs.dc_threads, 0, st>>>(v, d ? d->views : nullptr,
+                                                                        d ? d->work : nullptr, reg);
+  return cudaGetLastError();
 }
 
 template <int DIR>
-static cudaError_t launch_dir(const Geom& g, const Arrays& a, int reg, int recon, int riemann, cudaStream_t st) {
-  if (a.mixed)
-    return riemann == RS_HLLD ? launch_typed<DIR, RS_HLLD, float>(g, a, reg, recon, st)
-                              : launch_typed<DIR, RS_HLLE, float>(g, a, reg, recon, st);
-  return riemann == RS_HLLD ? launch_typed<DIR, RS_HLLD, double>(g, a, reg, recon, st)
-                            : launch_typed<DIR, RS_HLLE, double>(g, a, reg, recon, st);
+static cudaError_t launch_dir(const MeshView& v, const Dispatch* d, int reg, int recon, int riemann,
+                              const FluxShape& fs, int max_mb, cudaStream_t st) {
+  if (v.a.mixed)
+    return riemann == RS_HLLD ? launch_typed<DIR, RS_HLLD, float>(v, d, reg, recon, fs, max_mb, st)
+                              : launch_typed<DIR, RS_HLLE, float>(v, d, reg, recon, fs, max_mb, st);
+  return riemann == RS_HLLD ? launch_typed<DIR, RS_HLLD, double>(v, d, reg, recon, fs, max_mb, st)
+                            : launch_typed<DIR, RS_HLLE, double>(v, d, reg, recon, fs, max_mb, st);
 }
 
-cudaError_t launch_flux(const Geom& g, const Arrays& a, int reg, int recon, int riemann, int dir, cudaStream_t st) {
-  if (dir == 0) return launch_dir<0>(g, a, reg, recon, riemann, st);
-  if (dir == 1) return launch_dir<1>(g, a, reg, recon, riemann, st);
-  return launch_dir<2>(g, a, reg, recon, riemann, st);
+cudaError_t launch_flux(const MeshView& v, const Dispatch* d, int reg, int recon, int riemann, int dir,
+                        const FluxShape& fs, int max_mb, cudaStream_t st) {
+  if (dir == 0) return launch_dir<0>(v, d, reg, recon, riemann, fs, max_mb, st);
+  if (dir == 1) return launch_dir<1>(v, d, reg, recon, riemann, fs, max_mb, st);
+  return launch_dir<2>(v, d, reg, recon, riemann, fs, max_mb, st);
+}
+
+// The PLM kernels need more than the default 48 KB of dynamic shared memory; the attribute is set on the
+// current device before any launch (and so before any stream capture).
+cudaError_t prepare_kernel_attributes() {
+  cudaError_t e = cudaSuccess;
+#define VL2_ATTR(DIR, RS, T) \
+  if (e == cudaSuccess) e = set_smem_attr(k_flux_plm<DIR, RS, T>);
+  VL2_ATTR(0, RS_HLLD, double) VL2_ATTR(1, RS_HLLD, double) VL2_ATTR(2, RS_HLLD, double)
+  VL2_ATTR(0, RS_HLLE, double) VL2_ATTR(1, RS_HLLE, double) VL2_ATTR(2, RS_HLLE, double)
+  VL2_ATTR(0, RS_HLLD, float) VL2_ATTR(1, RS_HLLD, float) VL2_ATTR(2, RS_HLLD, float)
+  VL2_ATTR(0, RS_HLLE, float) VL2_ATTR(1, RS_HLLE, float) VL2_ATTR(2, RS_HLLE, float)
+#undef VL2_ATTR
+  return e;
 }
 
 }  // namespace vl2

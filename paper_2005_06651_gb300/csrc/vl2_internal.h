@@ -49,12 +49,73 @@ struct Arrays {
 
 enum { SC_MAXRATE = 0, SC_FLOORS = 1, SC_MISMATCH = 2, SC_COUNT = 8 };
 
-// ---- launchers (vl2_kernels.cu / vl2_flux.cu); all enqueue on `st` ----
-cudaError_t launch_prim(const Geom& g, const Arrays& a, int reg, bool all_cells, bool want_dt, cudaStream_t st);
-cudaError_t launch_ghosts(const Geom& g, const Arrays& a, int reg, cudaStream_t st);
-cudaError_t launch_flux(const Geom& g, const Arrays& a, int reg, int recon, int riemann, int dir, cudaStream_t st);
-cudaError_t launch_emfs(const Geom& g, const Arrays& a, cudaStream_t st);
-cudaError_t launch_update(const Geom& g, const Arrays& a, int base_reg, int out_reg, double h, cudaStream_t st);
+// A mesh as the kernels see it (copied to device memory for batched launches).
+struct MeshView {
+  Geom g;
+  Arrays a;
+};
+
+// One CTA of a batched launch: which mesh (box) and which tile of that mesh's work.
+struct WorkItem {
+  int box;
+  int tile;
+};
+
+// How a launch is scheduled: one mesh (views == nullptr: tile = blockIdx.x), or many meshes through a
+// work list of (box, tile) entries, one per CTA.
+struct Dispatch {
+  const MeshView* views = nullptr;  // device array, one per box
+  const WorkItem* work = nullptr;   // device array, nwork entries
+  int nwork = 0;
+};
+
+#ifdef __CUDACC__
+// Resolve the mesh and tile of this CTA (single mesh: the launch argument and blockIdx.x; batch: the
+// CTA's work item) and stage the mesh view in shared memory.  Every thread of the CTA must call it.
+__device__ __forceinline__ const MeshView& stage_view(MeshView& sv, const MeshView& single, const MeshView* views,
+                                                      const WorkItem* work, int& tile, int* box = nullptr) {
+  if (work) {
+    const WorkItem w = work[blockIdx.x];
+    tile = w.tile;
+    if (box) *box = w.box;
+    if (threadIdx.x == 0) sv = views[w.box];
+  } else {
+    tile = blockIdx.x;
+    if (box) *box = 0;
+    if (threadIdx.x == 0) sv = single;
+  }
+  __syncthreads();
+  return sv;
+}
+#endif
+
+// Threads per CTA of the per-element kernels, and the tunable flux launch shapes.
+constexpr int THREADS = 256;
+struct FluxShape {
+  int dc_threads = 128;  // CTA size of the donor-cell flux kernel
+  int plm_lines = 16;    // lines of faces per CTA of the PLM flux kernel (0: largest that fits)
+};
+
+// Work units of each kernel for one mesh (used to size single launches and to build work lists).
+long long tiles_prim(const Geom& g);
+long long tiles_ghosts(const Geom& g);
+long long tiles_nodes(const Geom& g);  // EMF and update
+long long tiles_flux_dc(const Geom& g, int dir, const FluxShape& fs);
+long long tiles_flux_plm(const Geom& g, int dir, const FluxShape& fs);
+int plm_lines_for(const Geom& g, int dir, const FluxShape& fs, int max_mb);
+
+// ---- launchers (vl2_kernels.cu / vl2_flux.cu); all enqueue on `st`.  d == nullptr: the single mesh v.
+// For batched launches v only selects the precision; dtbox (per-box dt, device) and beta give h. ----
+cudaError_t launch_prim(const MeshView& v, const Dispatch* d, int reg, bool all_cells, bool want_dt, cudaStream_t st);
+cudaError_t launch_ghosts(const MeshView& v, const Dispatch* d, int reg, cudaStream_t st);
+cudaError_t launch_flux(const MeshView& v, const Dispatch* d, int reg, int recon, int riemann, int dir,
+                        const FluxShape& fs, int max_mb, cudaStream_t st);
+cudaError_t launch_emfs(const MeshView& v, const Dispatch* d, cudaStream_t st);
+cudaError_t launch_update(const MeshView& v, const Dispatch* d, int base_reg, int out_reg, double h,
+                          const double* dtbox, double beta, cudaStream_t st);
+// per-box dt from the CFL rates the last prim reduced: dt[box] = cfl / rate, rate reset to 0
+cudaError_t launch_batch_dt(const MeshView* views, int nbox, const double* cfl, double* dt, cudaStream_t st);
+cudaError_t prepare_kernel_attributes();
 cudaError_t launch_scatter_prims(const Geom& g, const Arrays& a, const double* w, const double* b1,
                                  const double* b2, const double* b3, cudaStream_t st);
 cudaError_t launch_check_periodic(const Geom& g, const double* b1, const double* b2, const double* b3,

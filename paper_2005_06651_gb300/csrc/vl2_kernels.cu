@@ -22,13 +22,16 @@ __device__ __forceinline__ void block_loc(const Geom& g, int b, int* loc) {
 // double, so an integer max is the floating max).
 // ------------------------------------------------------------------------------------------------
 template <bool DT, class TW>
-__global__ void __launch_bounds__(256) k_prim(Geom g, double* U, const double* __restrict__ B0,
-                                              const double* __restrict__ B1, const double* __restrict__ B2,
-                                              TW* __restrict__ W, unsigned long long* scal, int all) {
+__global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* views, const WorkItem* work, int reg,
+                                              int all) {
+  __shared__ MeshView sv;
+  int tile;
+  const MeshView& V = stage_view(sv, single, views, work, tile);
+  const Geom& g = V.g;
   const int off = all ? 0 : NG;
   const int ex = g.mb[0] + (all ? 2 * NG : 0), ey = g.mb[1] + (all ? 2 * NG : 0), ez = g.mb[2] + (all ? 2 * NG : 0);
   const long long per = (long long)ex * ey * ez;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long t = (long long)tile * blockDim.x + threadIdx.x;
   unsigned long long rate_bits = 0ULL;
   if (t < per * g.nblk) {
     const int b = (int)(t / per);
@@ -39,10 +42,13 @@ __global__ void __launch_bounds__(256) k_prim(Geom g, double* U, const double* _
     const int k = rem / ey + off;
     const long long c = cell_off(g, k, j, i);
     const long long fb = (long long)b * g.box + c;
+    const double* B0 = V.a.b[reg][0];
+    const double* B1 = V.a.b[reg][1];
+    const double* B2 = V.a.b[reg][2];
     const double bcx = 0.5 * (B0[fb] + B0[fb + 1]);
     const double bcy = 0.5 * (B1[fb] + B1[fb + g.sx]);
     const double bcz = 0.5 * (B2[fb] + B2[fb + (long long)g.sx * g.sy]);
-    double* Ub = U + (long long)b * 5 * g.box + c;
+    double* Ub = V.a.u[reg] + (long long)b * 5 * g.box + c;
     double d = Ub[0];
     const double m1 = Ub[g.box], m2 = Ub[2 * g.box], m3 = Ub[3 * g.box];
     double e = Ub[4 * g.box];
@@ -63,11 +69,11 @@ __global__ void __launch_bounds__(256) k_prim(Geom g, double* U, const double* _
       fired = true;
     }
     if (fired && active) {
-      atomicAdd(scal + SC_FLOORS, 1ULL);
+      atomicAdd(V.a.scal + SC_FLOORS, 1ULL);
       Ub[0] = d;
       Ub[4 * g.box] = e;
     }
-    TW* Wb = W + (long long)b * 8 * g.box + c;
+    TW* Wb = static_cast<TW*>(V.a.w) + (long long)b * 8 * g.box + c;
     Wb[0] = (TW)d;
     Wb[g.box] = (TW)vx;
     Wb[2 * g.box] = (TW)vy;
@@ -99,31 +105,56 @@ __global__ void __launch_bounds__(256) k_prim(Geom g, double* U, const double* _
     if (threadIdx.x == 0) {
       unsigned long long m = 0ULL;
       for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m = red[q] > m ? red[q] : m;
-      if (m) atomicMax(scal + SC_MAXRATE, m);
+      if (m) atomicMax(V.a.scal + SC_MAXRATE, m);
     }
   }
 }
 
-cudaError_t launch_prim(const Geom& g, const Arrays& a, int reg, bool all_cells, bool want_dt, cudaStream_t st) {
-  const long long per = all_cells ? (long long)(g.mb[0] + 2 * NG) * (g.mb[1] + 2 * NG) * (g.mb[2] + 2 * NG)
-                                  : (long long)g.mb[0] * g.mb[1] * g.mb[2];
-  const unsigned grid = grid_for(per * g.nblk, 256);
-  const double* B0 = a.b[reg][0];
-  const double* B1 = a.b[reg][1];
-  const double* B2 = a.b[reg][2];
-  if (a.mixed) {
-    float* w = static_cast<float*>(a.w);
+long long tiles_prim(const Geom& g) {
+  return ((long long)(g.mb[0] + 2 * NG) * (g.mb[1] + 2 * NG) * (g.mb[2] + 2 * NG) * g.nblk + THREADS - 1) / THREADS;
+}
+
+cudaError_t launch_prim(const MeshView& v, const Dispatch* d, int reg, bool all_cells, bool want_dt, cudaStream_t st) {
+  const Geom& g = v.g;
+  long long grid;
+  if (d)
+    grid = d->nwork;  // batched launches always cover every cell
+  else if (all_cells)
+    grid = tiles_prim(g);
+  else
+    grid = ((long long)g.mb[0] * g.mb[1] * g.mb[2] * g.nblk + THREADS - 1) / THREADS;
+  if (grid <= 0) return cudaSuccess;
+  const MeshView* vs = d ? d->views : nullptr;
+  const WorkItem* wk = d ? d->work : nullptr;
+  const int all = (d || all_cells) ? 1 : 0;
+  if (v.a.mixed) {
     if (want_dt)
-      k_prim<true, float><<<grid, 256, 0, st>>>(g, a.u[reg], B0, B1, B2, w, a.scal, all_cells);
+      k_prim<true, float><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk, reg, all);
     else
-      k_prim<false, float><<<grid, 256, 0, st>>>(g, a.u[reg], B0, B1, B2, w, a.scal, all_cells);
+      k_prim<false, float><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk, reg, all);
   } else {
-    double* w = static_cast<double*>(a.w);
     if (want_dt)
-      k_prim<true, double><<<grid, 256, 0, st>>>(g, a.u[reg], B0, B1, B2, w, a.scal, all_cells);
+      k_prim<true, double><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk, reg, all);
     else
-      k_prim<false, double><<<grid, 256, 0, st>>>(g, a.u[reg], B0, B1, B2, w, a.scal, all_cells);
+      k_prim<false, double><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk, reg, all);
   }
+  return cudaGetLastError();
+}
+
+// per-box time step from the CFL rate each box's last prim pass reduced; the rate is reset for the next pass
+__global__ void k_batch_dt(const MeshView* views, int nbox, const double* cfl, double* dt) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nbox) return;
+  unsigned long long* rp = views[q].a.scal + SC_MAXRATE;
+  if (cfl) {
+    const double rate = __longlong_as_double((long long)*rp);
+    dt[q] = cfl[q] / rate;
+  }
+  *rp = 0ULL;
+}
+
+cudaError_t launch_batch_dt(const MeshView* views, int nbox, const double* cfl, double* dt, cudaStream_t st) {
+  k_batch_dt<<<(nbox + 127) / 128, 128, 0, st>>>(views, nbox, cfl, dt);
   return cudaGetLastError();
 }
 
@@ -161,10 +192,18 @@ __device__ __forceinline__ void source_of(const Geom& g, int q, int gi, bool fac
   }
 }
 
-__global__ void __launch_bounds__(256) k_ghosts(Geom g, double* U, double* B0, double* B1, double* B2) {
+__global__ void __launch_bounds__(256) k_ghosts(MeshView single, const MeshView* views, const WorkItem* work, int reg) {
+  __shared__ MeshView sv;
+  int tile;
+  const MeshView& V = stage_view(sv, single, views, work, tile);
+  const Geom& g = V.g;
+  double* U = V.a.u[reg];
+  double* B0 = V.a.b[reg][0];
+  double* B1 = V.a.b[reg][1];
+  double* B2 = V.a.b[reg][2];
   const int ex = g.mb[0] + 2 * NG + 1, ey = g.mb[1] + 2 * NG + 1, ez = g.mb[2] + 2 * NG + 1;
   const long long per = (long long)ex * ey * ez;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long t = (long long)tile * blockDim.x + threadIdx.x;
   if (t >= per * g.nblk) return;
   const int b = (int)(t / per);
   int rem = (int)(t - (long long)b * per);
@@ -207,9 +246,15 @@ __global__ void __launch_bounds__(256) k_ghosts(Geom g, double* U, double* B0, d
   }
 }
 
-cudaError_t launch_ghosts(const Geom& g, const Arrays& a, int reg, cudaStream_t st) {
+long long tiles_ghosts(const Geom& g) {
   const long long per = (long long)(g.mb[0] + 2 * NG + 1) * (g.mb[1] + 2 * NG + 1) * (g.mb[2] + 2 * NG + 1);
-  k_ghosts<<<grid_for(per * g.nblk, 256), 256, 0, st>>>(g, a.u[reg], a.b[reg][0], a.b[reg][1], a.b[reg][2]);
+  return (per * g.nblk + THREADS - 1) / THREADS;
+}
+
+cudaError_t launch_ghosts(const MeshView& v, const Dispatch* d, int reg, cudaStream_t st) {
+  const long long grid = d ? d->nwork : tiles_ghosts(v.g);
+  if (grid <= 0) return cudaSuccess;
+  k_ghosts<<<(unsigned)grid, THREADS, 0, st>>>(v, d ? d->views : nullptr, d ? d->work : nullptr, reg);
   return cudaGetLastError();
 }
 
@@ -228,12 +273,21 @@ __device__ __forceinline__ T cell_emf(int e, const T* Wc, long long box) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(256) k_emf(Geom g, const T* __restrict__ W, const T* __restrict__ F0,
-                                             const T* __restrict__ F1, const T* __restrict__ F2, T* __restrict__ E0,
-                                             T* __restrict__ E1, T* __restrict__ E2) {
+__global__ void __launch_bounds__(256) k_emf(MeshView single, const MeshView* views, const WorkItem* work) {
+  __shared__ MeshView sv;
+  int tile;
+  const MeshView& V = stage_view(sv, single, views, work, tile);
+  const Geom& g = V.g;
+  const T* W = static_cast<const T*>(V.a.w);
+  const T* F0 = static_cast<const T*>(V.a.f[0]);
+  const T* F1 = static_cast<const T*>(V.a.f[1]);
+  const T* F2 = static_cast<const T*>(V.a.f[2]);
+  T* E0 = static_cast<T*>(V.a.e[0]);
+  T* E1 = static_cast<T*>(V.a.e[1]);
+  T* E2 = static_cast<T*>(V.a.e[2]);
   const int ex = g.mb[0] + 1, ey = g.mb[1] + 1, ez = g.mb[2] + 1;
   const long long per = (long long)ex * ey * ez;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long t = (long long)tile * blockDim.x + threadIdx.x;
   if (t >= per * g.nblk) return;
   const int b = (int)(t / per);
   int rem = (int)(t - (long long)b * per);
@@ -267,20 +321,19 @@ __global__ void __launch_bounds__(256) k_emf(Geom g, const T* __restrict__ W, co
   }
 }
 
-template <class T>
-static void emf_typed(const Geom& g, const Arrays& a, unsigned grid, cudaStream_t st) {
-  k_emf<T><<<grid, 256, 0, st>>>(g, static_cast<const T*>(a.w), static_cast<const T*>(a.f[0]),
-                                 static_cast<const T*>(a.f[1]), static_cast<const T*>(a.f[2]),
-                                 static_cast<T*>(a.e[0]), static_cast<T*>(a.e[1]), static_cast<T*>(a.e[2]));
+long long tiles_nodes(const Geom& g) {
+  return ((long long)(g.mb[0] + 1) * (g.mb[1] + 1) * (g.mb[2] + 1) * g.nblk + THREADS - 1) / THREADS;
 }
 
-cudaError_t launch_emfs(const Geom& g, const Arrays& a, cudaStream_t st) {
-  const long long per = (long long)(g.mb[0] + 1) * (g.mb[1] + 1) * (g.mb[2] + 1);
-  const unsigned grid = grid_for(per * g.nblk, 256);
-  if (a.mixed)
-    emf_typed<float>(g, a, grid, st);
+cudaError_t launch_emfs(const MeshView& v, const Dispatch* d, cudaStream_t st) {
+  const long long grid = d ? d->nwork : tiles_nodes(v.g);
+  if (grid <= 0) return cudaSuccess;
+  const MeshView* vs = d ? d->views : nullptr;
+  const WorkItem* wk = d ? d->work : nullptr;
+  if (v.a.mixed)
+    k_emf<float><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk);
   else
-    emf_typed<double>(g, a, grid, st);
+    k_emf<double><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk);
   return cudaGetLastError();
 }
 
@@ -291,14 +344,30 @@ cudaError_t launch_emfs(const Geom& g, const Arrays& a, cudaStream_t st) {
 // U_base / U_out may alias (the corrector updates u^n in place), so no __restrict__ here.
 // ------------------------------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(256) k_update(Geom g, const double* Ubase, double* Uout, const double* Bb0,
-                                                const double* Bb1, const double* Bb2, double* Bo0, double* Bo1,
-                                                double* Bo2, const T* __restrict__ F0, const T* __restrict__ F1,
-                                                const T* __restrict__ F2, const T* __restrict__ E0,
-                                                const T* __restrict__ E1, const T* __restrict__ E2, double h) {
+__global__ void __launch_bounds__(256) k_update(MeshView single, const MeshView* views, const WorkItem* work,
+                                                int base_reg, int out_reg, double h, const double* dtbox, double beta) {
+  __shared__ MeshView sv;
+  int tile, box;
+  const MeshView& V = stage_view(sv, single, views, work, tile, &box);
+  const Geom& g = V.g;
+  if (dtbox) h = beta * dtbox[box];
+  const double* Ubase = V.a.u[base_reg];
+  double* Uout = V.a.u[out_reg];
+  const double* Bb0 = V.a.b[base_reg][0];
+  const double* Bb1 = V.a.b[base_reg][1];
+  const double* Bb2 = V.a.b[base_reg][2];
+  double* Bo0 = V.a.b[out_reg][0];
+  double* Bo1 = V.a.b[out_reg][1];
+  double* Bo2 = V.a.b[out_reg][2];
+  const T* F0 = static_cast<const T*>(V.a.f[0]);
+  const T* F1 = static_cast<const T*>(V.a.f[1]);
+  const T* F2 = static_cast<const T*>(V.a.f[2]);
+  const T* E0 = static_cast<const T*>(V.a.e[0]);
+  const T* E1 = static_cast<const T*>(V.a.e[1]);
+  const T* E2 = static_cast<const T*>(V.a.e[2]);
   const int ex = g.mb[0] + 1, ey = g.mb[1] + 1, ez = g.mb[2] + 1;
   const long long per = (long long)ex * ey * ez;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long t = (long long)tile * blockDim.x + threadIdx.x;
   if (t >= per * g.nblk) return;
   const int b = (int)(t / per);
   int rem = (int)(t - (long long)b * per);
@@ -345,23 +414,16 @@ __global__ void __launch_bounds__(256) k_update(Geom g, const double* Ubase, dou
   }
 }
 
-template <class T>
-static void update_typed(const Geom& g, const Arrays& a, int base_reg, int out_reg, double h, unsigned grid,
-                         cudaStream_t st) {
-  k_update<T><<<grid, 256, 0, st>>>(g, a.u[base_reg], a.u[out_reg], a.b[base_reg][0], a.b[base_reg][1],
-                                    a.b[base_reg][2], a.b[out_reg][0], a.b[out_reg][1], a.b[out_reg][2],
-                                    static_cast<const T*>(a.f[0]), static_cast<const T*>(a.f[1]),
-                                    static_cast<const T*>(a.f[2]), static_cast<const T*>(a.e[0]),
-                                    static_cast<const T*>(a.e[1]), static_cast<const T*>(a.e[2]), h);
-}
-
-cudaError_t launch_update(const Geom& g, const Arrays& a, int base_reg, int out_reg, double h, cudaStream_t st) {
-  const long long per = (long long)(g.mb[0] + 1) * (g.mb[1] + 1) * (g.mb[2] + 1);
-  const unsigned grid = grid_for(per * g.nblk, 256);
-  if (a.mixed)
-    update_typed<float>(g, a, base_reg, out_reg, h, grid, st);
+cudaError_t launch_update(const MeshView& v, const Dispatch* d, int base_reg, int out_reg, double h,
+                          const double* dtbox, double beta, cudaStream_t st) {
+  const long long grid = d ? d->nwork : tiles_nodes(v.g);
+  if (grid <= 0) return cudaSuccess;
+  const MeshView* vs = d ? d->views : nullptr;
+  const WorkItem* wk = d ? d->work : nullptr;
+  if (v.a.mixed)
+    k_update<float><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk, base_reg, out_reg, h, dtbox, beta);
   else
-    update_typed<double>(g, a, base_reg, out_reg, h, grid, st);
+    k_update<double><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk, base_reg, out_reg, h, dtbox, beta);
   return cudaGetLastError();
 }
 

@@ -53,7 +53,9 @@ _lib = None
 EXPORTS = ["vl2_workspace_bytes", "vl2_mesh_create", "vl2_mesh_destroy", "vl2_block_layout", "vl2_set_prims",
            "vl2_fill_ghosts", "vl2_step", "vl2_new_dt", "vl2_get_cons", "vl2_get_prims", "vl2_divb_norm",
            "vl2_totals", "vl2_floor_count", "vl2_debug_fluxes", "vl2_debug_emfs", "vl2_profile",
-           "vl2_profile_read", "vl2_launch_count", "vl2_totals_noalloc", "vl2_last_error"]
+           "vl2_profile_read", "vl2_launch_count", "vl2_totals_noalloc", "vl2_batch_workspace_bytes",
+           "vl2_batch_create", "vl2_batch_destroy", "vl2_batch_autotune", "vl2_batch_step", "vl2_batch_run",
+           "vl2_batch_launch_count", "vl2_batch_last_error", "vl2_last_error"]
 NOALLOC_MAX_NZ = 4096
 K_PRIM, K_GHOSTS, K_FLUX_DC, K_FLUX_PLM, K_EMF, K_UPDATE = range(6)
 KERNEL_KINDS = {K_PRIM: "prim", K_GHOSTS: "ghosts", K_FLUX_DC: "flux_dc", K_FLUX_PLM: "flux_plm", K_EMF: "emf",
@@ -90,10 +92,19 @@ def load(path: str = LIB_PATH):
     L.vl2_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.vl2_totals_noalloc.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                      vp, vp]
+    L.vl2_batch_workspace_bytes.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+    L.vl2_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, vp, sz, ctypes.POINTER(ctypes.c_void_p)]
+    L.vl2_batch_destroy.argtypes = [vp]
+    L.vl2_batch_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.vl2_batch_step.argtypes = [vp, vp, ctypes.c_int]
+    L.vl2_batch_run.argtypes = [vp, ctypes.c_int, vp]
+    L.vl2_batch_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    L.vl2_batch_last_error.argtypes = [vp]
+    L.vl2_batch_last_error.restype = ctypes.c_char_p
     L.vl2_last_error.argtypes = [vp]
     L.vl2_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name != "vl2_last_error":
+        if name not in ("vl2_last_error", "vl2_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -320,6 +331,75 @@ def totals_noalloc(u, b1, b2, b3, dx, out, stream=None):
     return out
 
 
+def _bcheck(status, handle=None):
+    if status != VL2_OK:
+        msg = load().vl2_batch_last_error(handle)
+        raise VL2Error(status, msg.decode() if msg else "")
+    return status
+
+
+class Batch:
+    """Many independent meshes advanced together (vl2_batch_*).  Keeps the meshes alive."""
+
+    def __init__(self, meshes):
+        import torch
+
+        L = load()
+        self.meshes = list(meshes)
+        arr = (ctypes.c_void_p * len(self.meshes))(*[m._h.value for m in self.meshes])
+        self._arr = arr
+        nbytes = ctypes.c_size_t()
+        _bcheck(L.vl2_batch_workspace_bytes(arr, len(self.meshes), ctypes.byref(nbytes)))
+        dev = self.meshes[0].device
+        self._ws = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=dev)
+        aligned = (self._ws.data_ptr() + 255) & ~255
+        h = ctypes.c_void_p()
+        _bcheck(L.vl2_batch_create(arr, len(self.meshes), ctypes.c_void_p(aligned), nbytes, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load().vl2_batch_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def ncells(self):
+        return sum(m.ncells for m in self.meshes)
+
+    def autotune(self):
+        dc, pl = ctypes.c_int(), ctypes.c_int()
+        _bcheck(load().vl2_batch_autotune(self._h, ctypes.byref(dc), ctypes.byref(pl)), self._h)
+        return dc.value, pl.value
+
+    def step(self, dt):
+        """One cycle with per-box steps dt (sequence of floats, or a CUDA float64 tensor)."""
+        if isinstance(dt, np.ndarray) or isinstance(dt, (list, tuple)):
+            a = np.ascontiguousarray(dt, dtype=np.float64)
+            _bcheck(load().vl2_batch_step(self._h, ctypes.c_void_p(a.ctypes.data), HOST), self._h)
+        else:
+            p, where = _ptr(dt)
+            _bcheck(load().vl2_batch_step(self._h, ctypes.c_void_p(p), where), self._h)
+
+    def run(self, nsteps, want_dt=True):
+        """nsteps cycles with per-box CFL steps formed on the device, as one graph launch."""
+        out = np.empty(len(self.meshes)) if want_dt else None
+        _bcheck(load().vl2_batch_run(self._h, int(nsteps), ctypes.c_void_p(out.ctypes.data) if want_dt else None),
+                self._h)
+        return out
+
+    def launch_count(self):
+        n = ctypes.c_longlong()
+        _bcheck(load().vl2_batch_launch_count(self._h, ctypes.byref(n)), self._h)
+        return n.value
+
+
 # ---- ABI-named module functions ----
 def mesh_create(nx, mb, **kw):
     return Mesh(nx, mb, **kw)
@@ -359,3 +439,7 @@ def divb_norm(mesh):
 
 def totals(mesh):
     return mesh.totals()
+
+
+def batch_create(meshes):
+    return Batch(meshes)
