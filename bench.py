@@ -267,7 +267,7 @@ def batched_form(args, dev, stream, vl2, inputs):
     for m, p in zip(meshes, probs):
         m.set_prims(p.w, p.b1, p.b2, p.b3)
     for m in meshes:  # warm-up
-        m.step(m.new_dt())
+        m.step(m.new_dt(allow_nonphys=True))
     for m, p in zip(meshes, probs):
         m.set_prims(p.w, p.b1, p.b2, p.b3)
     torch.cuda.synchronize(dev)
@@ -275,9 +275,10 @@ def batched_form(args, dev, stream, vl2, inputs):
     launches0 = sum(m.launch_count() for m in meshes)
     t0 = time.perf_counter()
     e0.record(stream)
+    floors0 = [m.floor_count() for m in meshes]
     for _ in range(K):
         for m in meshes:
-            m.step(m.new_dt())
+            m.step(m.new_dt(allow_nonphys=True))  # a floor is part of the method: counted, not fatal
     e1.record(stream)
     torch.cuda.synchronize(dev)
     per_box_s = time.perf_counter() - t0
@@ -305,6 +306,7 @@ def batched_form(args, dev, stream, vl2, inputs):
     batched_ms = e0.elapsed_time(e1)
     batched_launches = batch.launch_count() - l0
     same = all(all(np.array_equal(a, b) for a, b in zip(meshes[q].get_cons(), ref[q])) for q in check)
+    floor_boxes = [q for q, m in enumerate(meshes) if m.floor_count() > floors0[q]]
     del batch
     counts = {int(v): int((sizes == v).sum()) for v in (16, 32, 48, 64)}
     return {"config": {"workload": "%d_turbulence_boxes_sizes_16_32_48_64_cubed_one_block_each" % nbox,
@@ -315,7 +317,85 @@ def batched_form(args, dev, stream, vl2, inputs):
             "per_box_value": ncell * K / per_box_s, "per_box_ms_per_step": 1e3 * per_box_s / K,
             "per_box_launches_per_step": per_box_launches / K, "speedup_vs_per_box": per_box_s / batched_s,
             "autotuned": {"dc_threads": dc, "plm_lines": pl},
-            "bitwise_equal_to_per_box_path": bool(same), "checked_boxes": len(check)}
+            "bitwise_equal_to_per_box_path": bool(same), "checked_boxes": len(check),
+            "boxes_with_floor_events": floor_boxes}
+
+
+def adjoint_form(args, dev, stream, vl2, inputs):
+    """Differentiation form, FP64: a 64^3 periodic box (8 MeshBlocks of 32^3) holding a fast magnetosonic
+    wave (amplitude 1e-2) carried by a uniform flow, adv_steps VL2 cycles behind torch.autograd with a
+    checkpoint every ~sqrt(N) cycles.  Loss = sum over cells of (rho_final - target)^2 dV, target = initial
+    density + 0.01 N(0,1) (seed 5005); gradient with respect to the initial velocity (3 x 64^3).  Reports
+    forward and backward device time, their ratio, the peak device memory of forward + backward, and a
+    central finite-difference check of the gradient along smooth directions (same time steps)."""
+    import numpy as np
+    import torch
+
+    from paper_2005_06651_gb300 import adjoint
+
+    n, K = args.adj_n, args.adj_steps
+    prob = inputs.linear_wave(n, mb=min(32, n), kind="fast", amp=1e-2, v0=(0.7, 0.4, 0.2))
+    k = max(1, int(round(K ** 0.5)))
+    torch.cuda.synchronize(dev)
+    torch.cuda.empty_cache()
+    base_mem = torch.cuda.memory_allocated(dev)
+    torch.cuda.reset_peak_memory_stats(dev)
+    runner = adjoint.Rollout(prob, nsteps=K, checkpoint_every=k, device=dev)
+    rng = np.random.Generator(np.random.PCG64(5005))
+    target = torch.from_numpy(prob.w[0] + 0.01 * rng.standard_normal(prob.w[0].shape)).to(dev)
+    dv = float(np.prod(prob.dx))
+    v_init = torch.from_numpy(np.ascontiguousarray(prob.w[1:4])).to(dev)
+
+    def loss_of(u):
+        return ((u[0] - target) ** 2).sum() * dv
+
+    times = {"forward": [], "backward": []}
+    grad = None
+    for rep in range(3):  # the first repetition is the warm-up
+        v = v_init.clone().requires_grad_(True)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        loss = loss_of(adjoint.rollout(v, runner))
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize(dev)
+        t2 = time.perf_counter()
+        if rep:
+            times["forward"].append(t1 - t0)
+            times["backward"].append(t2 - t1)
+        grad = v.grad.detach().clone()
+    peak = torch.cuda.max_memory_allocated(dev) - base_mem
+    state_bytes = 8 * (5 * prob.ncells + sum(int(np.prod(b.shape)) for b in (prob.b1, prob.b2, prob.b3)))
+    runner.fixed_dts = list(runner.dts)
+    x, y, z = inputs._cell_coords(prob.nx, prob.xmin, prob.xmax)
+    fd_checks = []
+    for trial in range(2):
+        ph = rng.uniform(0, 2 * np.pi, size=(3, 3))
+        d = np.stack([np.sin(2 * np.pi * x + ph[c, 0]) * np.cos(2 * np.pi * y + ph[c, 1]) *
+                      np.sin(2 * np.pi * z + ph[c, 2]) for c in range(3)])
+        d = torch.from_numpy(np.ascontiguousarray(d)).to(dev)
+        h = 1e-8  # small enough that the step crosses almost no limiter switch at this size
+        with torch.no_grad():
+            lp = float(loss_of(runner.run_forward(v_init + h * d)))
+            lm = float(loss_of(runner.run_forward(v_init - h * d)))
+        fd = (lp - lm) / (2 * h)
+        ad = float((grad * d).sum())
+        fd_checks.append({"fd": fd, "adjoint": ad, "rel_err": abs(fd - ad) / abs(ad)})
+    runner.mesh.close()
+    fwd, bwd = float(np.median(times["forward"])), float(np.median(times["backward"]))
+    return {"config": {"workload": "fast_wave_%d^3_%dx%d^3_blocks_amp1e-2_flow_0.7_0.4_0.2" % (
+                           n, (n // min(32, n)) ** 3, min(32, n)),
+                       "steps": K, "checkpoint_every": k, "checkpoints": (K + k - 1) // k,
+                       "loss": "sum (rho_final - target)^2 dV, target = rho_0 + 0.01 N(0,1), seed 5005",
+                       "wrt": "initial velocity (3 x %d^3)" % n, "dtype": "f64", "riemann": "hlld",
+                       "reconstruction": "plm"},
+            "forward_s": fwd, "backward_s": bwd, "backward_over_forward": bwd / fwd,
+            "forward_value": prob.ncells * K / fwd, "unit": UNIT,
+            "peak_mem_bytes": int(peak), "state_bytes": state_bytes,
+            "peak_mem_over_state": peak / state_bytes,
+            "fd_check": {"h": 1e-8, "directions": "smooth sin/cos products, random phases", "checks": fd_checks,
+                         "max_rel_err": max(c["rel_err"] for c in fd_checks)}}
 
 
 def rms_l1(state, ref):
@@ -340,11 +420,13 @@ def main():
     ap.add_argument("--mb", type=int, default=32)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-forms", action="store_true", help="skip the mixed-precision and batched forms")
+    ap.add_argument("--no-forms", action="store_true", help="skip the mixed-precision, batched and differentiation forms")
     ap.add_argument("--forms-n", type=int, default=512, help="grid of the mixed-precision form")
     ap.add_argument("--forms-steps", type=int, default=20)
     ap.add_argument("--batch-boxes", type=int, default=1024)
     ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--adj-n", type=int, default=64, help="grid of the differentiation form")
+    ap.add_argument("--adj-steps", type=int, default=100)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -472,6 +554,8 @@ def main():
         forms = {"mixed": mixed_form(args, dev, stream, vl2, inputs)}
         torch.cuda.empty_cache()
         forms["batched"] = batched_form(args, dev, stream, vl2, inputs)
+        torch.cuda.empty_cache()
+        forms["adjoint"] = adjoint_form(args, dev, stream, vl2, inputs)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

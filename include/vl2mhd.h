@@ -67,6 +67,7 @@ typedef struct vl2_params {
                          periodic must be set on both faces of a direction */
   double dfloor, pfloor; /* density / pressure floors of cons->prim (> 0) */
   void* stream;       /* cudaStream_t for all device work of this mesh (may be NULL) */
+  int adjoint;        /* 1: also reserve the arrays of vl2_step_vjp (VL2_FP64 only); 0: forward only */
 } vl2_params;
 
 typedef struct vl2_mesh vl2_mesh;
@@ -116,6 +117,12 @@ vl2_status vl2_block_layout(const vl2_mesh* mesh, vl2_layout* out);
 vl2_status vl2_set_prims(vl2_mesh* mesh, const double* w, const double* b1, const double* b2,
                          const double* b3, int where);
 
+/* Set the state from conserved variables directly: u = [5][NZ][NY][NX] (rho, M1, M2, M3, E) and the face
+ * fields (global layout); ghosts are then exchanged.  Used to restore checkpoints.  Errors: VL2_E_ARG,
+ * VL2_E_CUDA. */
+vl2_status vl2_set_cons(vl2_mesh* mesh, const double* u, const double* b1, const double* b2, const double* b3,
+                        int where);
+
 /* Ghost exchange of the current state (Sec. 2.1.1): cell-centred U and face fields copied, depth
  * ng, from the 26 neighbours (periodic wrap; outflow copies the nearest active cell / boundary face).
  * Faces on a block's own surface are active and are not overwritten.  Errors: VL2_E_CUDA. */
@@ -163,6 +170,24 @@ vl2_status vl2_debug_fluxes(vl2_mesh* mesh, int recon, double* fx, double* fy, d
 /* Corner EMFs (upwind CT) of the current state for the given reconstruction on the global edge
  * grids e1[NZ+1][NY+1][NX] (E_x), e2[NZ+1][NY][NX+1] (E_y), e3[NZ][NY+1][NX+1] (E_z). */
 vl2_status vl2_debug_emfs(vl2_mesh* mesh, int recon, double* e1, double* e2, double* e3, int where);
+
+/* Adjoint of one VL2 cycle (Sec. 3.2.3) with dt held fixed: for the mesh's current state x and the
+ * adjoint lam_out of the cycle's output (u [5][NZ][NY][NX] and face fields b1..b3, global layout, device),
+ * writes lam_in = J(x)^T lam_out (same layout, device) where J is the Jacobian of the cycle.  The
+ * cycle's forward intermediates are recomputed from x, which is left unchanged.  Reverse order: update,
+ * upwind-CT EMFs (upwind choices frozen at x), Riemann fluxes (local Jacobians by forward-mode dual
+ * numbers through the forward flux function), PLM (limiter switch frozen), cons->prim, ghost exchange;
+ * corrector first, then the predictor.  Face entries follow the global layout: the adjoint of face N of a
+ * periodic direction is kept apart from face 0 (they are separate array entries).  Needs a mesh created
+ * with params.adjoint = 1 and VL2_FP64, and no active floors.  Errors: VL2_E_ARG, VL2_E_STATE,
+ * VL2_E_CUDA. */
+vl2_status vl2_step_vjp(vl2_mesh* mesh, double dt, const double* lam_u, const double* lam_b1, const double* lam_b2,
+                        const double* lam_b3, double* out_u, double* out_b1, double* out_b2, double* out_b3);
+
+/* Adjoint of the set-up map prims -> conserved (eq. total_energy) with the field held fixed: from the
+ * primitives w = [5][N] (rho, v, p; device, global layout) and lam_u = [5][N] (device), writes
+ * lam_w = [5][N] (device).  Errors: VL2_E_ARG, VL2_E_CUDA. */
+vl2_status vl2_prims_vjp(vl2_mesh* mesh, const double* w, const double* lam_u, double* lam_w);
 
 /* Kernel kinds of vl2_profile_read. */
 enum {

@@ -72,6 +72,8 @@ def lib():
         L.orc_count_face_ops.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
                                          ctypes.POINTER(ctypes.c_longlong)]
         L.orc_ct_corner.argtypes = [dp, dp, dp, dp, dp]
+        L.orc_tl_step.argtypes = [ip, ip, dp, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.c_double] + [dp] * 16
+        L.orc_step_cons.argtypes = [ip, ip, dp, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.c_double] + [dp] * 8
         L.orc_ct_corner.restype = ctypes.c_double
         _lib = L
     return _lib
@@ -123,6 +125,35 @@ def count_face_ops(recon, solver, q4, bn, gamma):
 def ct_corner(ea, eb, ec, ma, mb):
     arrs = [_c64(a) for a in (ea, eb, ec, ma, mb)]
     return lib().orc_ct_corner(*[_dp(a) for a in arrs])
+
+
+def _geom_args(nx, mb, xmin, xmax, bc):
+    return ((ctypes.c_int * 3)(*nx), (ctypes.c_int * 3)(*mb), (ctypes.c_double * 3)(*xmin),
+            (ctypes.c_double * 3)(*xmax), (ctypes.c_int * 6)(*bc))
+
+
+def tl_step(prob_geom, dt, state, tangent, gamma=5.0 / 3.0, riemann=HLLD):
+    """Tangent-linear of one VL2 cycle (dual numbers): state/tangent = (u, b1, b2, b3) global arrays.
+    prob_geom = (nx, mb, xmin, xmax, bc).  Returns (new state, J @ tangent)."""
+    nx, mb, xmin, xmax, bc = prob_geom
+    ins = [_c64(a) for a in state] + [_c64(a) for a in tangent]
+    outs = [np.zeros_like(a) for a in ins]
+    g = _geom_args(nx, mb, xmin, xmax, bc)
+    lib().orc_tl_step(g[0], g[1], g[2], g[3], float(gamma), riemann, g[4], float(dt),
+                      *[_dp(a) for a in ins[:4]], *[_dp(a) for a in ins[4:]], *[_dp(a) for a in outs[:4]],
+                      *[_dp(a) for a in outs[4:]])
+    return tuple(outs[:4]), tuple(outs[4:])
+
+
+def step_cons(prob_geom, dt, state, gamma=5.0 / 3.0, riemann=HLLD):
+    """One VL2 cycle from a conserved state (global arrays); returns the new state."""
+    nx, mb, xmin, xmax, bc = prob_geom
+    ins = [_c64(a) for a in state]
+    outs = [np.zeros_like(a) for a in ins]
+    g = _geom_args(nx, mb, xmin, xmax, bc)
+    lib().orc_step_cons(g[0], g[1], g[2], g[3], float(gamma), riemann, g[4], float(dt), *[_dp(a) for a in ins],
+                        *[_dp(a) for a in outs])
+    return tuple(outs)
 
 
 # ------------------------------------------------------------------------------------------------

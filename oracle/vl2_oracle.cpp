@@ -96,6 +96,46 @@ static inline bool operator>=(Flop a, double b) { return a >= Flop(b); }
 static inline Flop fabs(Flop a) { return Flop(std::fabs(a.v)); }
 static inline Flop sqrt(Flop a) { ++g_ops.sqrt; return Flop(std::sqrt(a.v)); }
 
+/* Dual number (value, tangent) for the tangent-linear of a cycle: every operation carries its exact
+ * first-order derivative along one input direction (forward-mode differentiation).  Comparisons look at
+ * the value only, so a branch (limiter, Riemann fan region, upwind choice) is frozen at the point. */
+struct Dual {
+  double v, d;
+  Dual() : v(0.0), d(0.0) {}
+  Dual(double x) : v(x), d(0.0) {}
+  Dual(double x, double t) : v(x), d(t) {}
+};
+static inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+static inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+static inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+static inline Dual operator/(Dual a, Dual b) { return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)); }
+static inline Dual operator+(double a, Dual b) { return Dual(a) + b; }
+static inline Dual operator-(double a, Dual b) { return Dual(a) - b; }
+static inline Dual operator*(double a, Dual b) { return Dual(a * b.v, a * b.d); }
+static inline Dual operator/(double a, Dual b) { return Dual(a) / b; }
+static inline Dual operator+(Dual a, double b) { return a + Dual(b); }
+static inline Dual operator-(Dual a, double b) { return a - Dual(b); }
+static inline Dual operator*(Dual a, double b) { return Dual(a.v * b, a.d * b); }
+static inline Dual operator/(Dual a, double b) { return Dual(a.v / b, a.d / b); }
+static inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+static inline bool operator<(Dual a, Dual b) { return a.v < b.v; }
+static inline bool operator>(Dual a, Dual b) { return a.v > b.v; }
+static inline bool operator<=(Dual a, Dual b) { return a.v <= b.v; }
+static inline bool operator>=(Dual a, Dual b) { return a.v >= b.v; }
+static inline bool operator==(Dual a, Dual b) { return a.v == b.v; }
+static inline bool operator<(Dual a, double b) { return a.v < b; }
+static inline bool operator>(Dual a, double b) { return a.v > b; }
+static inline bool operator<=(Dual a, double b) { return a.v <= b; }
+static inline bool operator>=(Dual a, double b) { return a.v >= b; }
+static inline Dual fabs(Dual a) { return a.v < 0.0 ? -a : a; }
+static inline Dual sqrt(Dual a) {
+  const double r = std::sqrt(a.v);
+  return Dual(r, a.d / (2.0 * r));
+}
+template <class T> static inline T make_scalar(double v, double t);
+template <> inline double make_scalar<double>(double v, double) { return v; }
+template <> inline Dual make_scalar<Dual>(double v, double t) { return Dual(v, t); }
+
 /* ---------------------------------------------------------------------------------------------
  * Pointwise physics
  * ------------------------------------------------------------------------------------------- */
@@ -848,6 +888,7 @@ template <class T> struct Mesh {
   }
 
   static double value_of(double x) { return x; }
+  static double value_of(Dual x) { return x.v; }
 };
 
 /* ---------------------------------------------------------------------------------------------
@@ -919,6 +960,66 @@ static void get_cons(const Mesh<T>& M, double* u, double* b1, double* b2, double
             b2[((size_t)gk * (NY + 1) + gj) * NX + gi] = Mesh<T>::value_of(B.b[0][1](K, J, I));
           if (b3 && own_k && i < M.n[0] && j < M.n[1])
             b3[((size_t)gk * NY + gj) * NX + gi] = Mesh<T>::value_of(B.b[0][2](K, J, I));
+        }
+  }
+}
+
+/* Set the conserved state directly from global arrays (active region), then exchange ghosts. */
+template <class T>
+static void set_cons(Mesh<T>& M, const double* u, const double* du, const double* b1, const double* db1,
+                     const double* b2, const double* db2, const double* b3, const double* db3) {
+  const int NX = M.P.nx[0], NY = M.P.nx[1], NZ = M.P.nx[2];
+  const size_t ncell = (size_t)NX * NY * NZ;
+  for (auto& B : M.blk) {
+    const int o[3] = {B.loc[0] * M.n[0], B.loc[1] * M.n[1], B.loc[2] * M.n[2]};
+    for (int k = 0; k <= M.n[2]; ++k)
+      for (int j = 0; j <= M.n[1]; ++j)
+        for (int i = 0; i <= M.n[0]; ++i) {
+          const int gi = o[0] + i, gj = o[1] + j, gk = o[2] + k;
+          const int K = k + NG, J = j + NG, I = i + NG;
+          if (j < M.n[1] && k < M.n[2]) {
+            const size_t f = ((size_t)gk * NY + gj) * (NX + 1) + gi;
+            B.b[0][0](K, J, I) = make_scalar<T>(b1[f], db1 ? db1[f] : 0.0);
+          }
+          if (i < M.n[0] && k < M.n[2]) {
+            const size_t f = ((size_t)gk * (NY + 1) + gj) * NX + gi;
+            B.b[0][1](K, J, I) = make_scalar<T>(b2[f], db2 ? db2[f] : 0.0);
+          }
+          if (i < M.n[0] && j < M.n[1]) {
+            const size_t f = ((size_t)gk * NY + gj) * NX + gi;
+            B.b[0][2](K, J, I) = make_scalar<T>(b3[f], db3 ? db3[f] : 0.0);
+          }
+          if (i < M.n[0] && j < M.n[1] && k < M.n[2]) {
+            const size_t g = ((size_t)gk * NY + gj) * NX + gi;
+            for (int v = 0; v < 5; ++v)
+              B.u[0][v](K, J, I) = make_scalar<T>(u[v * ncell + g], du ? du[v * ncell + g] : 0.0);
+          }
+        }
+  }
+  M.fill_ghosts(0);
+}
+
+/* Tangent parts of the conserved state (global layout), the counterpart of get_cons. */
+static void get_tangent(const Mesh<Dual>& M, double* du, double* db1, double* db2, double* db3) {
+  const int NX = M.P.nx[0], NY = M.P.nx[1], NZ = M.P.nx[2];
+  const size_t ncell = (size_t)NX * NY * NZ;
+  for (const auto& B : M.blk) {
+    const int o[3] = {B.loc[0] * M.n[0], B.loc[1] * M.n[1], B.loc[2] * M.n[2]};
+    for (int k = 0; k <= M.n[2]; ++k)
+      for (int j = 0; j <= M.n[1]; ++j)
+        for (int i = 0; i <= M.n[0]; ++i) {
+          const int gi = o[0] + i, gj = o[1] + j, gk = o[2] + k;
+          const int K = k + NG, J = j + NG, I = i + NG;
+          const bool own_i = (i < M.n[0]) || (gi == NX);
+          const bool own_j = (j < M.n[1]) || (gj == NY);
+          const bool own_k = (k < M.n[2]) || (gk == NZ);
+          if (i < M.n[0] && j < M.n[1] && k < M.n[2]) {
+            const size_t g = ((size_t)gk * NY + gj) * NX + gi;
+            for (int v = 0; v < 5; ++v) du[v * ncell + g] = B.u[0][v](K, J, I).d;
+          }
+          if (own_i && j < M.n[1] && k < M.n[2]) db1[((size_t)gk * NY + gj) * (NX + 1) + gi] = B.b[0][0](K, J, I).d;
+          if (own_j && i < M.n[0] && k < M.n[2]) db2[((size_t)gk * (NY + 1) + gj) * NX + gi] = B.b[0][1](K, J, I).d;
+          if (own_k && i < M.n[0] && j < M.n[1]) db3[((size_t)gk * NY + gj) * NX + gi] = B.b[0][2](K, J, I).d;
         }
   }
 }
@@ -1088,6 +1189,58 @@ void orc_totals(void* m, double* out) {
           }
         }
   for (int v = 0; v < 8; ++v) out[v] = s[v] + cmp[v];
+}
+
+/* Tangent-linear of one VL2 cycle with a fixed dt, by dual numbers: from the conserved state (u, b1..3)
+ * and a direction (du, db1..3), all in the global layout, return the new state and J*direction. */
+void orc_tl_step(const int* nx, const int* mb, const double* xmin, const double* xmax, double gamma, int riemann,
+                 const int* bc, double dt, const double* u, const double* b1, const double* b2, const double* b3,
+                 const double* du, const double* db1, const double* db2, const double* db3, double* u_out,
+                 double* b1_out, double* b2_out, double* b3_out, double* du_out, double* db1_out, double* db2_out,
+                 double* db3_out) {
+  orc::Params p;
+  for (int d = 0; d < 3; ++d) {
+    p.nx[d] = nx[d];
+    p.mb[d] = mb[d];
+    p.xmin[d] = xmin[d];
+    p.xmax[d] = xmax[d];
+  }
+  for (int f = 0; f < 6; ++f) p.bc[f] = bc[f];
+  p.gamma = gamma;
+  p.riemann = riemann;
+  p.dfloor = 1e-12;
+  p.pfloor = 1e-12;
+  p.integrator = orc::INT_VL2;
+  orc::Mesh<orc::Dual> M;
+  M.init(p);
+  orc::set_cons(M, u, du, b1, db1, b2, db2, b3, db3);
+  M.step(dt);
+  orc::get_cons(M, u_out, b1_out, b2_out, b3_out);
+  orc::get_tangent(M, du_out, db1_out, db2_out, db3_out);
+}
+
+/* Plain (value) cycle from a conserved state, same entry form as orc_tl_step (no tangent). */
+void orc_step_cons(const int* nx, const int* mb, const double* xmin, const double* xmax, double gamma, int riemann,
+                   const int* bc, double dt, const double* u, const double* b1, const double* b2, const double* b3,
+                   double* u_out, double* b1_out, double* b2_out, double* b3_out) {
+  orc::Params p;
+  for (int d = 0; d < 3; ++d) {
+    p.nx[d] = nx[d];
+    p.mb[d] = mb[d];
+    p.xmin[d] = xmin[d];
+    p.xmax[d] = xmax[d];
+  }
+  for (int f = 0; f < 6; ++f) p.bc[f] = bc[f];
+  p.gamma = gamma;
+  p.riemann = riemann;
+  p.dfloor = 1e-12;
+  p.pfloor = 1e-12;
+  p.integrator = orc::INT_VL2;
+  orc::Mesh<double> M;
+  M.init(p);
+  orc::set_cons(M, u, nullptr, b1, nullptr, b2, nullptr, b3, nullptr);
+  M.step(dt);
+  orc::get_cons(M, u_out, b1_out, b2_out, b3_out);
 }
 
 /* ---- pointwise entry points for the unit pins ---- */

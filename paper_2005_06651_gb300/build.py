@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libvl2mhd.so")
-SOURCES = ["vl2_api.cu", "vl2_kernels.cu", "vl2_flux.cu", "vl2_noalloc.cu"]
+SOURCES = ["vl2_api.cu", "vl2_kernels.cu", "vl2_flux.cu", "vl2_adjoint.cu", "vl2_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

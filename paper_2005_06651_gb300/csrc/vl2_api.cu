@@ -41,6 +41,8 @@ struct vl2_mesh {
   long long acc_n[VL2_K_COUNT] = {0}, acc_units[VL2_K_COUNT] = {0};
   long long launches = 0;
   vl2::FluxShape fs;
+  vl2::AdjArrays adj{};
+  bool has_adj = false;
   vl2::MeshView view() const { return vl2::MeshView{g, a}; }
   int max_mb() const { return std::max(g.mb[0], std::max(g.mb[1], g.mb[2])); }
   ~vl2_mesh() {
@@ -128,6 +130,10 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
     msg = "precision must be VL2_FP64 or VL2_MIXED";
     return VL2_E_ARG;
   }
+  if (p->adjoint != 0 && (p->adjoint != 1 || p->precision != VL2_FP64)) {
+    msg = "adjoint must be 0 or 1, and 1 needs VL2_FP64";
+    return VL2_E_ARG;
+  }
   for (int d = 0; d < 3; ++d) {
     const int lo = p->bc[2 * d], hi = p->bc[2 * d + 1];
     if ((lo != VL2_PERIODIC && lo != VL2_OUTFLOW) || (hi != VL2_PERIODIC && hi != VL2_OUTFLOW) ||
@@ -171,9 +177,11 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
 struct Plan {
   size_t off_u[2], off_b[2][3], off_w, off_f[3], off_e[3], off_stage, off_red, off_scal, total;
   size_t stage_elems;
+  size_t off_adj;  // start of the adjoint arrays (59 FP64 arrays per block) when requested
 };
+constexpr int ADJ_ARRAYS = 10 + 6 + 8 + 21 + 3 + 8 + 3;
 
-Plan make_plan(const Geom& g, int precision) {
+Plan make_plan(const Geom& g, int precision, int adjoint) {
   Plan pl;
   size_t o = 0;
   const size_t per = (size_t)g.nblk * g.box * sizeof(double);
@@ -208,6 +216,8 @@ Plan make_plan(const Geom& g, int precision) {
   o = align256(o + (size_t)RED_CTAS * 8 * sizeof(double));
   pl.off_scal = o;
   o = align256(o + vl2::SC_COUNT * sizeof(unsigned long long) + 16 * sizeof(double));
+  pl.off_adj = o;
+  if (adjoint) o = align256(o + (size_t)ADJ_ARRAYS * per);
   pl.total = o;
   return pl;
 }
@@ -317,7 +327,7 @@ vl2_status vl2_workspace_bytes(const vl2_params* params, size_t* bytes) {
   vl2_status s = make_geom(params, g, msg);
   if (s != VL2_OK) return fail(nullptr, s, msg);
   if (!bytes) return fail(nullptr, VL2_E_ARG, "bytes is NULL");
-  *bytes = make_plan(g, params->precision).total;
+  *bytes = make_plan(g, params->precision, params->adjoint).total;
   return VL2_OK;
 }
 
@@ -329,7 +339,7 @@ vl2_status vl2_mesh_create(const vl2_params* params, void* workspace, size_t byt
   vl2_status s = make_geom(params, g, msg);
   if (s != VL2_OK) return fail(nullptr, s, msg);
   if (!workspace || ((uintptr_t)workspace & 255u)) return fail(nullptr, VL2_E_ARG, "workspace must be 256-byte aligned");
-  const Plan pl = make_plan(g, params->precision);
+  const Plan pl = make_plan(g, params->precision, params->adjoint);
   if (bytes < pl.total) return fail(nullptr, VL2_E_NOMEM, "workspace smaller than vl2_workspace_bytes()");
   vl2_mesh* m = new (std::nothrow) vl2_mesh();
   if (!m) return fail(nullptr, VL2_E_ARG, "host allocation failed");
@@ -347,6 +357,25 @@ vl2_status vl2_mesh_create(const vl2_params* params, void* workspace, size_t byt
     m->a.e[d] = base + pl.off_e[d];
   }
   m->a.mixed = params->precision == VL2_MIXED ? 1 : 0;
+  if (params->adjoint) {
+    const size_t per = (size_t)g.nblk * g.box;
+    double* q = (double*)(base + pl.off_adj);
+    auto take = [&](size_t nvar) {
+      double* r = q;
+      q += nvar * per;
+      return r;
+    };
+    for (int r = 0; r < 2; ++r) {
+      m->adj.lu[r] = take(5);
+      for (int d = 0; d < 3; ++d) m->adj.lb[r][d] = take(1);
+    }
+    m->adj.lw = take(8);
+    for (int d = 0; d < 3; ++d) m->adj.lf[d] = take(7);
+    for (int d = 0; d < 3; ++d) m->adj.le[d] = take(1);
+    m->adj.w0 = take(8);
+    for (int d = 0; d < 3; ++d) m->adj.m1[d] = take(1);
+    m->has_adj = true;
+  }
   m->a.stage = (double*)(base + pl.off_stage);
   m->a.stage_elems = pl.stage_elems;
   m->a.red = (double*)(base + pl.off_red);
@@ -450,6 +479,106 @@ vl2_status vl2_set_prims(vl2_mesh* m, const double* w, const double* b1, const d
   m->w_valid = false;
   m->dt_pending = false;
   return sync(m);
+}
+
+vl2_status vl2_set_cons(vl2_mesh* m, const double* u, const double* b1, const double* b2, const double* b3, int where) {
+  if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
+  if (!u || !b1 || !b2 || !b3 || bad_where(where)) return fail(m, VL2_E_ARG, "NULL input or bad where");
+  const Geom& g = m->g;
+  const long long nc = ncells(g);
+  const long long n1 = (long long)(g.N[0] + 1) * g.N[1] * g.N[2];
+  const long long n2 = (long long)g.N[0] * (g.N[1] + 1) * g.N[2];
+  const long long n3 = (long long)g.N[0] * g.N[1] * (g.N[2] + 1);
+  const double *du = u, *d1 = b1, *d2 = b2, *d3 = b3;
+  if (where == VL2_HOST) {
+    double* s = m->a.stage;
+    vl2_status st;
+    if ((st = copy_in(m, s, u, 5 * nc, where)) != VL2_OK) return st;
+    if ((st = copy_in(m, s + 5 * nc, b1, n1, where)) != VL2_OK) return st;
+    if ((st = copy_in(m, s + 5 * nc + n1, b2, n2, where)) != VL2_OK) return st;
+    if ((st = copy_in(m, s + 5 * nc + n1 + n2, b3, n3, where)) != VL2_OK) return st;
+    du = s;
+    d1 = s + 5 * nc;
+    d2 = d1 + n1;
+    d3 = d2 + n2;
+  }
+  VL2_CHECK(m, vl2::launch_scatter_cons(g, m->a, du, d1, d2, d3, m->st));
+  ++m->launches;
+  VL2_CHECK(m, k_ghosts(m, 0));
+  m->initialized = true;
+  m->w_valid = false;
+  m->dt_pending = false;
+  if (where == VL2_HOST) return sync(m);
+  return VL2_OK;
+}
+
+vl2_status vl2_step_vjp(vl2_mesh* m, double dt, const double* lam_u, const double* lam_b1, const double* lam_b2,
+                        const double* lam_b3, double* out_u, double* out_b1, double* out_b2, double* out_b3) {
+  if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
+  if (!lam_u || !lam_b1 || !lam_b2 || !lam_b3 || !out_u || !out_b1 || !out_b2 || !out_b3)
+    return fail(m, VL2_E_ARG, "NULL argument");
+  if (!m->has_adj) return fail(m, VL2_E_STATE, "mesh was created without params.adjoint");
+  if (!m->initialized) return fail(m, VL2_E_STATE, "vl2_set_prims/vl2_set_cons has not been called");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(m, VL2_E_ARG, "dt must be finite and positive");
+  const Geom& g = m->g;
+  const vl2::AdjArrays& j = m->adj;
+  cudaStream_t st = m->st;
+  const size_t per = (size_t)g.nblk * g.box * sizeof(double);
+  // forward recompute of the cycle's intermediates from x (register 0 is not written)
+  VL2_CHECK(m, k_prim(m, 0, false));
+  VL2_CHECK(m, cudaMemcpyAsync(j.w0, m->a.w, 8 * per, cudaMemcpyDeviceToDevice, st));
+  VL2_CHECK(m, k_fluxes(m, 0, VL2_DC));
+  for (int d = 0; d < 3; ++d)
+    VL2_CHECK(m, cudaMemcpy2DAsync(j.m1[d], g.box * sizeof(double), m->a.f[d], 7 * g.box * sizeof(double),
+                                   g.box * sizeof(double), g.nblk, cudaMemcpyDeviceToDevice, st));
+  VL2_CHECK(m, k_emfs(m));
+  VL2_CHECK(m, k_update(m, 0, 1, 0.5 * dt));
+  VL2_CHECK(m, k_ghosts(m, 1));
+  VL2_CHECK(m, k_prim(m, 1, false));
+  VL2_CHECK(m, k_fluxes(m, 1, VL2_PLM));
+  m->w_valid = false;
+  m->dt_pending = false;
+  // reverse sweep
+  for (int r = 0; r < 2; ++r) {
+    VL2_CHECK(m, cudaMemsetAsync(j.lu[r], 0, 5 * per, st));
+    for (int d = 0; d < 3; ++d) VL2_CHECK(m, cudaMemsetAsync(j.lb[r][d], 0, per, st));
+  }
+  VL2_CHECK(m, cudaMemsetAsync(j.lw, 0, 8 * per, st));
+  VL2_CHECK(m, vl2::adj_scatter_out(g, j, lam_u, lam_b1, lam_b2, lam_b3, st));
+  const double* W1 = static_cast<const double*>(m->a.w);
+  const double* mf2[3] = {static_cast<const double*>(m->a.f[0]), static_cast<const double*>(m->a.f[1]),
+                          static_cast<const double*>(m->a.f[2])};
+  const double* bn1[3] = {m->a.b[1][0], m->a.b[1][1], m->a.b[1][2]};
+  const double* bn0[3] = {m->a.b[0][0], m->a.b[0][1], m->a.b[0][2]};
+  const double* mf1[3] = {j.m1[0], j.m1[1], j.m1[2]};
+  // corrector: U0 <- U0 + dt L_PLM(U1)
+  VL2_CHECK(m, vl2::adj_update(g, j, 0, 0, dt, st));
+  VL2_CHECK(m, vl2::adj_ct(g, j, W1, mf2, 7 * g.box, st));
+  VL2_CHECK(m, vl2::adj_fluxes(g, j, vl2::REC_PLM, m->p.riemann, W1, bn1, 1, st));
+  VL2_CHECK(m, vl2::adj_prim(g, j, W1, 1, st));
+  VL2_CHECK(m, vl2::adj_ghosts(g, j, 1, st));
+  // predictor: U1 = U0 + dt/2 L_DC(U0)
+  VL2_CHECK(m, cudaMemsetAsync(j.lw, 0, 8 * per, st));
+  VL2_CHECK(m, vl2::adj_update(g, j, 1, 0, 0.5 * dt, st));
+  VL2_CHECK(m, vl2::adj_ct(g, j, j.w0, mf1, g.box, st));
+  VL2_CHECK(m, vl2::adj_fluxes(g, j, vl2::REC_DC, m->p.riemann, j.w0, bn0, 0, st));
+  VL2_CHECK(m, vl2::adj_prim(g, j, j.w0, 0, st));
+  VL2_CHECK(m, vl2::adj_ghosts(g, j, 0, st));
+  const long long nc = ncells(g);
+  VL2_CHECK(m, cudaMemsetAsync(out_b1, 0, (size_t)(g.N[0] + 1) * g.N[1] * g.N[2] * sizeof(double), st));
+  VL2_CHECK(m, cudaMemsetAsync(out_b2, 0, (size_t)g.N[0] * (g.N[1] + 1) * g.N[2] * sizeof(double), st));
+  VL2_CHECK(m, cudaMemsetAsync(out_b3, 0, (size_t)g.N[0] * g.N[1] * (g.N[2] + 1) * sizeof(double), st));
+  (void)nc;
+  VL2_CHECK(m, vl2::adj_gather_in(g, j, out_u, out_b1, out_b2, out_b3, st));
+  m->launches += 20;
+  return VL2_OK;
+}
+
+vl2_status vl2_prims_vjp(vl2_mesh* m, const double* w, const double* lam_u, double* lam_w) {
+  if (!m || !w || !lam_u || !lam_w) return fail(m, VL2_E_ARG, "NULL argument");
+  VL2_CHECK(m, vl2::prims_vjp(ncells(m->g), m->g.igm1, w, lam_u, lam_w, m->st));
+  ++m->launches;
+  return VL2_OK;
 }
 
 vl2_status vl2_fill_ghosts(vl2_mesh* m) {

@@ -128,6 +128,32 @@ cudaError_t launch_gather_emfs(const Geom& g, const Arrays& a, int dir, double* 
 cudaError_t launch_divb(const Geom& g, const Arrays& a, double* result2, cudaStream_t st);
 cudaError_t launch_totals(const Geom& g, const Arrays& a, double* result8, cudaStream_t st);
 
+// Adjoint (reverse) arrays of one mesh, FP64, block layout like the forward arrays.
+struct AdjArrays {
+  double* lu[2];     // adjoints of the two conserved registers: [nblk][5][box]
+  double* lb[2][3];  // adjoints of the two face-field registers
+  double* lw;        // adjoint of the primitives: [nblk][8][box]
+  double* lf[3];     // adjoints of the face fluxes: [nblk][7][box]
+  double* le[3];     // adjoints of the corner EMFs
+  double* w0;        // predictor primitives kept from the forward recompute: [nblk][8][box]
+  double* m1[3];     // predictor face mass fluxes (upwind choices of its CT): [nblk][box]
+};
+
+cudaError_t adj_scatter_out(const Geom& g, const AdjArrays& j, const double* gu, const double* gb1, const double* gb2,
+                            const double* gb3, cudaStream_t st);
+cudaError_t adj_update(const Geom& g, const AdjArrays& j, int out_reg, int base_reg, double h, cudaStream_t st);
+cudaError_t adj_ct(const Geom& g, const AdjArrays& j, const double* W, const double* const* mflux, long long mstride,
+                   cudaStream_t st);
+cudaError_t adj_fluxes(const Geom& g, const AdjArrays& j, int recon, int riemann, const double* W,
+                       const double* const* Bn, int lam_reg, cudaStream_t st);
+cudaError_t adj_prim(const Geom& g, const AdjArrays& j, const double* W, int lam_reg, cudaStream_t st);
+cudaError_t adj_ghosts(const Geom& g, const AdjArrays& j, int lam_reg, cudaStream_t st);
+cudaError_t adj_gather_in(const Geom& g, const AdjArrays& j, double* gu, double* gb1, double* gb2, double* gb3,
+                          cudaStream_t st);
+cudaError_t prims_vjp(long long ncell, double igm1, const double* w, const double* lam_u, double* lam_w, cudaStream_t st);
+cudaError_t launch_scatter_cons(const Geom& g, const Arrays& a, const double* u, const double* b1, const double* b2,
+                                const double* b3, cudaStream_t st);
+
 // Sets the message vl2_last_error(NULL) returns (entry points that have no mesh).
 void record_error(const char* msg);
 

@@ -491,6 +491,32 @@ cudaError_t launch_scatter_prims(const Geom& g, const Arrays& a, const double* w
   return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(256) k_scatter_cons(Geom g, double* U, double* B0, double* B1, double* B2,
+                                                      const double* __restrict__ u, const double* __restrict__ b1,
+                                                      const double* __restrict__ b2, const double* __restrict__ b3) {
+  IoIdx x;
+  if (!io_index(g, x)) return;
+  const int NX = g.N[0], NY = g.N[1], NZ = g.N[2];
+  const long long c = cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG);
+  const long long o = (long long)x.b * g.box + c;
+  const bool in[3] = {x.li[0] < g.mb[0], x.li[1] < g.mb[1], x.li[2] < g.mb[2]};
+  if (in[1] && in[2]) B0[o] = b1[((long long)x.gi[2] * NY + x.gi[1]) * (NX + 1) + x.gi[0]];
+  if (in[0] && in[2]) B1[o] = b2[((long long)x.gi[2] * (NY + 1) + x.gi[1]) * NX + x.gi[0]];
+  if (in[0] && in[1]) B2[o] = b3[((long long)x.gi[2] * NY + x.gi[1]) * NX + x.gi[0]];
+  if (in[0] && in[1] && in[2]) {
+    const long long n = (long long)NX * NY * NZ;
+    const long long gc = ((long long)x.gi[2] * NY + x.gi[1]) * NX + x.gi[0];
+    double* Ub = U + (long long)x.b * 5 * g.box + c;
+    for (int v = 0; v < 5; ++v) Ub[(long long)v * g.box] = u[v * n + gc];
+  }
+}
+
+cudaError_t launch_scatter_cons(const Geom& g, const Arrays& a, const double* u, const double* b1, const double* b2,
+                                const double* b3, cudaStream_t st) {
+  k_scatter_cons<<<io_grid(g), 256, 0, st>>>(g, a.u[0], a.b[0][0], a.b[0][1], a.b[0][2], u, b1, b2, b3);
+  return cudaGetLastError();
+}
+
 // periodic duplicate faces (face N and face 0) must be bitwise equal
 __global__ void k_check_periodic(Geom g, const double* b1, const double* b2, const double* b3, unsigned long long* cnt) {
   const int NX = g.N[0], NY = g.N[1], NZ = g.N[2];

@@ -39,26 +39,6 @@ __device__ __forceinline__ void phys_flux(const R* w, R bn, R igm1, R* u, R* f) 
   f[6] = b2 * vn - bn * v2;
 }
 
-// HLLE flux; outer speeds are the extreme fast-wave speeds of the two states (Sec. 3.2.2 names the
-// solver; the speed estimate is this library's reading).
-template <class R>
-__device__ __forceinline__ void flux_hlle(const R* wl, const R* wr, R bn, R gamma, R igm1, R* f) {
-  R ul[7], fl[7], ur[7], fr[7];
-  phys_flux(wl, bn, igm1, ul, fl);
-  phys_flux(wr, bn, igm1, ur, fr);
-  const R bn2 = bn * bn;
-  const R cl = fast_speed_r(R(1) / wl[0], wl[4], bn2, wl[5] * wl[5] + wl[6] * wl[6], gamma);
-  const R cr = fast_speed_r(R(1) / wr[0], wr[4], bn2, wr[5] * wr[5] + wr[6] * wr[6], gamma);
-  const R sl = fmin(wl[1] - cl, wr[1] - cr);
-  const R sr = fmax(wl[1] + cl, wr[1] + cr);
-  const R bm = fmin(sl, R(0));
-  const R bp = fmax(sr, R(0));
-  const R iden = R(1) / (bp - bm);
-  const R bpm = bp * bm;
-#pragma unroll
-  for (int n = 0; n < 7; ++n) f[n] = ((bp * fl[n] - bm * fr[n]) + bpm * (ur[n] - ul[n])) * iden;
-}
-
 // ---- sign tests and orderings on the integer pipe --------------------------------------------
 // The FP64 pipe is the bottleneck of the plain kernels, so comparisons of doubles are done on the IEEE
 // bit patterns (integer compares) rather than with FP64 compare instructions.  They return exactly what
@@ -87,6 +67,26 @@ __device__ __forceinline__ int okey(float x) {
 template <class R> __device__ __forceinline__ R imin(R a, R b) { return okey(b) < okey(a) ? b : a; }
 template <class R> __device__ __forceinline__ R imax(R a, R b) { return okey(b) > okey(a) ? b : a; }
 template <class R> __device__ __forceinline__ bool igt(R a, R b) { return okey(a) > okey(b); }
+
+// HLLE flux; outer speeds are the extreme fast-wave speeds of the two states (Sec. 3.2.2 names the
+// solver; the speed estimate is this library's reading).
+template <class R>
+__device__ __forceinline__ void flux_hlle(const R* wl, const R* wr, R bn, R gamma, R igm1, R* f) {
+  R ul[7], fl[7], ur[7], fr[7];
+  phys_flux(wl, bn, igm1, ul, fl);
+  phys_flux(wr, bn, igm1, ur, fr);
+  const R bn2 = bn * bn;
+  const R cl = fast_speed_r(R(1) / wl[0], wl[4], bn2, wl[5] * wl[5] + wl[6] * wl[6], gamma);
+  const R cr = fast_speed_r(R(1) / wr[0], wr[4], bn2, wr[5] * wr[5] + wr[6] * wr[6], gamma);
+  const R sl = imin(wl[1] - cl, wr[1] - cr);
+  const R sr = imax(wl[1] + cl, wr[1] + cr);
+  const R bm = ge0(sl) ? R(0) : sl;
+  const R bp = gt0(sr) ? sr : R(0);
+  const R iden = R(1) / (bp - bm);
+  const R bpm = bp * bm;
+#pragma unroll
+  for (int n = 0; n < 7; ++n) f[n] = ((bp * fl[n] - bm * fr[n]) + bpm * (ur[n] - ul[n])) * iden;
+}
 
 // One side (L or R) of the HLLD fan: the state, its conserved vector and physical flux, and its
 // single-star state.

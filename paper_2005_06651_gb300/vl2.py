@@ -39,7 +39,7 @@ class Params(ctypes.Structure):
                 ("xmin", ctypes.c_double * 3), ("xmax", ctypes.c_double * 3), ("gamma", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("riemann", ctypes.c_int), ("precision", ctypes.c_int),
                 ("bc", ctypes.c_int * 6), ("dfloor", ctypes.c_double), ("pfloor", ctypes.c_double),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("adjoint", ctypes.c_int)]
 
 
 class Layout(ctypes.Structure):
@@ -55,7 +55,8 @@ EXPORTS = ["vl2_workspace_bytes", "vl2_mesh_create", "vl2_mesh_destroy", "vl2_bl
            "vl2_totals", "vl2_floor_count", "vl2_debug_fluxes", "vl2_debug_emfs", "vl2_profile",
            "vl2_profile_read", "vl2_launch_count", "vl2_totals_noalloc", "vl2_batch_workspace_bytes",
            "vl2_batch_create", "vl2_batch_destroy", "vl2_batch_autotune", "vl2_batch_step", "vl2_batch_run",
-           "vl2_batch_launch_count", "vl2_batch_last_error", "vl2_last_error"]
+           "vl2_batch_launch_count", "vl2_batch_last_error", "vl2_set_cons", "vl2_step_vjp", "vl2_prims_vjp",
+           "vl2_last_error"]
 NOALLOC_MAX_NZ = 4096
 K_PRIM, K_GHOSTS, K_FLUX_DC, K_FLUX_PLM, K_EMF, K_UPDATE = range(6)
 KERNEL_KINDS = {K_PRIM: "prim", K_GHOSTS: "ghosts", K_FLUX_DC: "flux_dc", K_FLUX_PLM: "flux_plm", K_EMF: "emf",
@@ -92,6 +93,9 @@ def load(path: str = LIB_PATH):
     L.vl2_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.vl2_totals_noalloc.argtypes = [vp, vp, vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                      vp, vp]
+    L.vl2_set_cons.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int]
+    L.vl2_step_vjp.argtypes = [vp, ctypes.c_double] + [dp] * 8
+    L.vl2_prims_vjp.argtypes = [vp, dp, dp, dp]
     L.vl2_batch_workspace_bytes.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.vl2_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, vp, sz, ctypes.POINTER(ctypes.c_void_p)]
     L.vl2_batch_destroy.argtypes = [vp]
@@ -146,7 +150,7 @@ class Mesh:
 
     def __init__(self, nx, mb, xmin=(0.0, 0.0, 0.0), xmax=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, cfl=0.3,
                  riemann=HLLD, bc=(PERIODIC,) * 6, dfloor=1e-12, pfloor=1e-12, precision=FP64, device=None,
-                 stream=None):
+                 stream=None, adjoint=False):
         import torch
 
         L = load()
@@ -168,6 +172,7 @@ class Mesh:
         p.bc[:] = tuple(int(v) for v in bc)
         p.dfloor, p.pfloor = float(dfloor), float(pfloor)
         p.stream = ctypes.c_void_p(stream.cuda_stream)
+        p.adjoint = 1 if adjoint else 0
         self._params = p
         nbytes = ctypes.c_size_t()
         _check(L.vl2_workspace_bytes(ctypes.byref(p), ctypes.byref(nbytes)))
@@ -217,6 +222,34 @@ class Mesh:
         ptrs = [_ptr(x) for x in keep]
         where = _where_of(ptrs)
         _check(load().vl2_set_prims(self._h, *[ctypes.c_void_p(p) for p, _ in ptrs], where), self._h)
+
+    def set_cons(self, u, b1, b2, b3):
+        keep = [np.ascontiguousarray(x, dtype=np.float64) if isinstance(x, np.ndarray) else x for x in (u, b1, b2, b3)]
+        ptrs = [_ptr(x) for x in keep]
+        where = _where_of(ptrs)
+        _check(load().vl2_set_cons(self._h, *[ctypes.c_void_p(p) for p, _ in ptrs], where), self._h)
+
+    def step_vjp(self, dt, lam, out=None):
+        """J^T lam for one cycle of step dt at the current state; lam/out = (u, b1, b2, b3) CUDA tensors."""
+        import torch
+
+        if out is None:
+            out = tuple(torch.empty_like(t) for t in lam)
+        for t in tuple(lam) + tuple(out):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError("step_vjp takes contiguous float64 CUDA tensors")
+        _check(load().vl2_step_vjp(self._h, float(dt), *[ctypes.c_void_p(t.data_ptr()) for t in lam],
+                                   *[ctypes.c_void_p(t.data_ptr()) for t in out]), self._h)
+        return out
+
+    def prims_vjp(self, w, lam_u, out=None):
+        import torch
+
+        if out is None:
+            out = torch.empty_like(lam_u)
+        _check(load().vl2_prims_vjp(self._h, ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(lam_u.data_ptr()),
+                                    ctypes.c_void_p(out.data_ptr())), self._h)
+        return out
 
     def fill_ghosts(self):
         _check(load().vl2_fill_ghosts(self._h), self._h)
