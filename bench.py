@@ -49,7 +49,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of
 # the k_flux_plm x sweep on the 128^3 vortex, 2,441,472 faces), scaled to a launch by its faces; valid only
 # for the kernel source it was taken on (hash of the flux and physics sources), else reported as null.
-NCU_TRAFFIC = {"hash": "7f607692b43ac1e9", "bytes_per_face": 134.3}
+NCU_TRAFFIC = {"hash": "d06840d23810bb88", "bytes_per_face": 134.6}
 
 
 def flux_source_hash():
@@ -398,6 +398,19 @@ def adjoint_form(args, dev, stream, vl2, inputs):
                          "max_rel_err": max(c["rel_err"] for c in fd_checks)}}
 
 
+def run_forms(args, dev, stream, vl2, inputs):
+    import torch
+
+    fns = {"mixed": mixed_form, "batched": batched_form, "adjoint": adjoint_form}
+    forms = {}
+    for name in [f for f in args.forms.split(",") if f]:
+        if name not in fns:
+            raise SystemExit("unknown form %r (choose from %s)" % (name, ", ".join(fns)))
+        forms[name] = fns[name](args, dev, stream, vl2, inputs)
+        torch.cuda.empty_cache()
+    return forms
+
+
 def rms_l1(state, ref):
     import numpy as np
 
@@ -422,11 +435,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the mixed-precision, batched and differentiation forms")
     ap.add_argument("--forms-n", type=int, default=512, help="grid of the mixed-precision form")
-    ap.add_argument("--forms-steps", type=int, default=20)
+    ap.add_argument("--forms-steps", type=int, default=50)
     ap.add_argument("--batch-boxes", type=int, default=1024)
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--adj-n", type=int, default=64, help="grid of the differentiation form")
     ap.add_argument("--adj-steps", type=int, default=100)
+    ap.add_argument("--forms", default="mixed,batched,adjoint", help="comma list of the forms to run")
+    ap.add_argument("--forms-only", action="store_true",
+                    help="run only the forms (a profiling aid: prints {'forms': ...}, not the bench line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -449,6 +465,10 @@ def main():
         pg = dist
     build.build()
     vl2.load()
+    if args.forms_only:
+        stream = torch.cuda.current_stream(dev)
+        print(json.dumps({"forms": run_forms(args, dev, stream, vl2, inputs)}), flush=True)
+        return
     prob = inputs.orszag_tang(n=args.n, mb=args.mb, seed=2005)
     stream = torch.cuda.current_stream(dev)
     mesh = vl2.Mesh.from_problem(prob, device=dev, stream=stream)
@@ -551,11 +571,7 @@ def main():
     torch.cuda.empty_cache()
     forms = None
     if not args.no_forms:
-        forms = {"mixed": mixed_form(args, dev, stream, vl2, inputs)}
-        torch.cuda.empty_cache()
-        forms["batched"] = batched_form(args, dev, stream, vl2, inputs)
-        torch.cuda.empty_cache()
-        forms["adjoint"] = adjoint_form(args, dev, stream, vl2, inputs)
+        forms = run_forms(args, dev, stream, vl2, inputs)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
