@@ -65,7 +65,7 @@ typedef struct vl2_params {
                          recovery) is FP64, and the flux divergence / EMF curl are accumulated in FP64 */
   int bc[6];          /* boundary of faces x-, x+, y-, y+, z-, z+: VL2_PERIODIC or VL2_OUTFLOW;
                          periodic must be set on both faces of a direction */
-  double dfloor, pfloor; /* density / pressure floors of cons->prim (> 0) */
+  double dfloor, pfloor; /* density / pressure floors of cons->prim (positive normal numbers, >= DBL_MIN) */
   void* stream;       /* cudaStream_t for all device work of this mesh (may be NULL) */
   int adjoint;        /* 1: also reserve the arrays of vl2_step_vjp (VL2_FP64 only); 0: forward only */
 } vl2_params;

@@ -2,6 +2,7 @@
 // Host orchestration only: argument checks, workspace carving, the kernel sequence of a VL2 cycle
 // (Sec. 3.2.3) and the copies of global-array I/O.
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -118,8 +119,9 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
     msg = "ng must be 2";
     return VL2_E_ARG;
   }
-  if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->dfloor > 0.0) || !(p->pfloor > 0.0)) {
-    msg = "gamma > 1, cfl > 0 and positive floors are required";
+  if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->dfloor >= DBL_MIN) || !(p->pfloor >= DBL_MIN) ||
+      !std::isfinite(p->dfloor) || !std::isfinite(p->pfloor)) {
+    msg = "gamma > 1, cfl > 0 and floors that are positive normal numbers are required";
     return VL2_E_ARG;
   }
   if (p->riemann != VL2_HLLD && p->riemann != VL2_HLLE) {

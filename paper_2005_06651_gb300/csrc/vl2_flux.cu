@@ -135,13 +135,13 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
 #pragma unroll
       for (int n = 1; n < 7; ++n) pre[n] = pre[n - 1] * den[n];
       if (normal_pos((double)fabs(pre[6]))) {
-        T inv = T(1) / pre[6];
+        T acc = inv(pre[6]);  // pre[6] is a positive normal number here
 #pragma unroll
         for (int n = 6; n > 0; --n) {
-          rec[n] = inv * pre[n - 1];
-          inv = inv * den[n];
+          rec[n] = acc * pre[n - 1];
+          acc = acc * den[n];
         }
-        rec[0] = inv;
+        rec[0] = acc;
       } else {
 #pragma unroll
         for (int n = 0; n < 7; ++n) rec[n] = T(1) / den[n];

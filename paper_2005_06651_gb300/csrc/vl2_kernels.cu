@@ -21,6 +21,10 @@ __device__ __forceinline__ void block_loc(const Geom& g, int b, int* loc) {
 // rate max_d (|v_d| + C_f,d) / dx_d (Sec. 2.1.7) into scal[SC_MAXRATE] (bit pattern of a positive
 // double, so an integer max is the floating max).
 // ------------------------------------------------------------------------------------------------
+template <class TW> __device__ __forceinline__ TW to_wtype(double x);
+template <> __device__ __forceinline__ double to_wtype<double>(double x) { return x; }
+template <> __device__ __forceinline__ float to_wtype<float>(double x) { return to_f32(x); }
+
 template <bool DT, class TW>
 __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* views, const WorkItem* work, int reg,
                                               int all) {
@@ -32,7 +36,10 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
   const int ex = g.mb[0] + (all ? 2 * NG : 0), ey = g.mb[1] + (all ? 2 * NG : 0), ez = g.mb[2] + (all ? 2 * NG : 0);
   const long long per = (long long)ex * ey * ez;
   const long long t = (long long)tile * blockDim.x + threadIdx.x;
-  unsigned long long rate_bits = 0ULL;
+  // kept for the CFL rate: the cell's FP64 primitives and a single-precision estimate of its rate
+  bool active = false;
+  double id = 0.0, p = 0.0, vx = 0.0, vy = 0.0, vz = 0.0, bcx = 0.0, bcy = 0.0, bcz = 0.0;
+  float r32 = 0.0f;
   if (t < per * g.nblk) {
     const int b = (int)(t / per);
     int rem = (int)(t - (long long)b * per);
@@ -45,24 +52,26 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
     const double* B0 = V.a.b[reg][0];
     const double* B1 = V.a.b[reg][1];
     const double* B2 = V.a.b[reg][2];
-    const double bcx = 0.5 * (B0[fb] + B0[fb + 1]);
-    const double bcy = 0.5 * (B1[fb] + B1[fb + g.sx]);
-    const double bcz = 0.5 * (B2[fb] + B2[fb + (long long)g.sx * g.sy]);
+    bcx = 0.5 * (B0[fb] + B0[fb + 1]);
+    bcy = 0.5 * (B1[fb] + B1[fb + g.sx]);
+    bcz = 0.5 * (B2[fb] + B2[fb + (long long)g.sx * g.sy]);
     double* Ub = V.a.u[reg] + (long long)b * 5 * g.box + c;
     double d = Ub[0];
     const double m1 = Ub[g.box], m2 = Ub[2 * g.box], m3 = Ub[3 * g.box];
     double e = Ub[4 * g.box];
-    const bool active = i >= NG && i < NG + g.mb[0] && j >= NG && j < NG + g.mb[1] && k >= NG && k < NG + g.mb[2];
+    active = i >= NG && i < NG + g.mb[0] && j >= NG && j < NG + g.mb[1] && k >= NG && k < NG + g.mb[2];
     bool fired = false;
     if (d < g.dfloor) {
       d = g.dfloor;
       fired = true;
     }
-    const double id = 1.0 / d;
-    const double vx = m1 * id, vy = m2 * id, vz = m3 * id;
+    id = rcp_nr(d);  // d >= dfloor, a positive normal number
+    vx = m1 * id;
+    vy = m2 * id;
+    vz = m3 * id;
     const double ke = 0.5 * ((m1 * m1 + m2 * m2) + m3 * m3) * id;
     const double me = 0.5 * ((bcx * bcx + bcy * bcy) + bcz * bcz);
-    double p = g.gm1 * (e - ke - me);
+    p = g.gm1 * (e - ke - me);
     if (p < g.pfloor) {
       p = g.pfloor;
       e = p * g.igm1 + ke + me;
@@ -74,15 +83,41 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
       Ub[4 * g.box] = e;
     }
     TW* Wb = static_cast<TW*>(V.a.w) + (long long)b * 8 * g.box + c;
-    Wb[0] = (TW)d;
-    Wb[g.box] = (TW)vx;
-    Wb[2 * g.box] = (TW)vy;
-    Wb[3 * g.box] = (TW)vz;
-    Wb[4 * g.box] = (TW)p;
-    Wb[5 * g.box] = (TW)bcx;
-    Wb[6 * g.box] = (TW)bcy;
-    Wb[7 * g.box] = (TW)bcz;
+    Wb[0] = to_wtype<TW>(d);
+    Wb[g.box] = to_wtype<TW>(vx);
+    Wb[2 * g.box] = to_wtype<TW>(vy);
+    Wb[3 * g.box] = to_wtype<TW>(vz);
+    Wb[4 * g.box] = to_wtype<TW>(p);
+    Wb[5 * g.box] = to_wtype<TW>(bcx);
+    Wb[6 * g.box] = to_wtype<TW>(bcy);
+    Wb[7 * g.box] = to_wtype<TW>(bcz);
     if (DT && active) {
+      // single-precision estimate of the rate (relative error well below 1e-5)
+      const float fid = to_f32(id), fp = to_f32(p), fg = (float)g.gamma;
+      const float fx = to_f32(bcx), fy = to_f32(bcy), fz = to_f32(bcz);
+      const float x2 = fx * fx, y2 = fy * fy, z2 = fz * fz;
+      const float sx = (fabsf(to_f32(vx)) + fast_speed_r(fid, fp, x2, y2 + z2, fg)) * (float)g.idx[0];
+      const float sy = (fabsf(to_f32(vy)) + fast_speed_r(fid, fp, y2, z2 + x2, fg)) * (float)g.idx[1];
+      const float sz = (fabsf(to_f32(vz)) + fast_speed_r(fid, fp, z2, x2 + y2, fg)) * (float)g.idx[2];
+      r32 = fmaxf(fmaxf(sx, sy), sz);
+      if (sx != sx || sy != sy || sz != sz) r32 = __int_as_float(0x7fc00000);  // keep a NaN visible
+    }
+  }
+  if (DT) {
+    // The CFL rate max_d (|v_d| + C_f,d) / dx_d of the CTA's cells, in FP64.  Only cells whose
+    // single-precision rate is within 1e-4 of the CTA's single-precision maximum (or is not a number) can
+    // hold the FP64 maximum, so only they evaluate it; the result equals the FP64 maximum over all cells.
+    __shared__ float redf[8];
+    __shared__ unsigned long long red[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    float m32 = r32;
+    for (int o = 16; o > 0; o >>= 1) m32 = fmaxf(m32, __shfl_xor_sync(0xffffffffu, m32, o));
+    if (lane == 0) redf[wid] = m32;
+    __syncthreads();
+    m32 = 0.0f;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m32 = fmaxf(m32, redf[q]);
+    unsigned long long rate_bits = 0ULL;
+    if (active && (!(r32 < m32 * 0.9999f) || isinf(m32))) {  // an overflowed estimate: evaluate every cell
       const double bx2 = bcx * bcx, by2 = bcy * bcy, bz2 = bcz * bcz;
       const double rx = (fabs(vx) + fast_speed_r(id, p, bx2, by2 + bz2, g.gamma)) * g.idx[0];
       const double ry = (fabs(vy) + fast_speed_r(id, p, by2, bz2 + bx2, g.gamma)) * g.idx[1];
@@ -92,14 +127,10 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
       rate_bits = ax > ay ? ax : ay;
       rate_bits = rate_bits > az ? rate_bits : az;
     }
-  }
-  if (DT) {
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned long long v = __shfl_xor_sync(0xffffffffu, rate_bits, o);
       rate_bits = v > rate_bits ? v : rate_bits;
     }
-    __shared__ unsigned long long red[8];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) red[wid] = rate_bits;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -394,7 +425,7 @@ __global__ void __launch_bounds__(256) k_update(MeshView single, const MeshView*
           comp = (m == d) ? 1 : ((m == (d + 1) % 3) ? 2 : 3);
         }
         const T* fp = F[d] + (long long)comp * g.box;
-        dfl[d] = ((double)fp[stride[d]] - (double)fp[0]) * g.idx[d];  // FP64 accumulation
+        dfl[d] = (to_f64(fp[stride[d]]) - to_f64(fp[0])) * g.idx[d];  // FP64 accumulation
       }
       const double L = -((dfl[0] + dfl[1]) + dfl[2]);
       Uout[ub + (long long)v * g.box] = Ubase[ub + (long long)v * g.box] + h * L;
@@ -407,8 +438,8 @@ __global__ void __launch_bounds__(256) k_update(MeshView single, const MeshView*
   for (int fd = 0; fd < 3; ++fd) {
     const int a = (fd + 1) % 3, bq = (fd + 2) % 3;
     if (!inside[a] || !inside[bq]) continue;
-    const double curl = ((double)E[bq][stride[a]] - (double)E[bq][0]) * g.idx[a] -
-                        ((double)E[a][stride[bq]] - (double)E[a][0]) * g.idx[bq];
+    const double curl = (to_f64(E[bq][stride[a]]) - to_f64(E[bq][0])) * g.idx[a] -
+                        (to_f64(E[a][stride[bq]]) - to_f64(E[a][0])) * g.idx[bq];
     const long long o = (long long)b * g.box + c;
     Bo[fd][o] = Bb[fd][o] + h * (-curl);
   }

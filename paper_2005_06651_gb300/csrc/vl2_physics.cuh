@@ -1,11 +1,74 @@
 // Device physics of the VL2 MHD step (Stone et al. 2020, arXiv:2005.06651, Sec. 3.1-3.2).
 // Interface states are 7-vectors in the sweep frame (rho, v_n, v_t1, v_t2, p, b_t1, b_t2) with
 // (n, t1, t2) = (x, y, z), (y, z, x), (z, x, y); fluxes use the same slots (mass, M_n, M_t1, M_t2,
-// E, B_t1, B_t2).  Reciprocals are formed once and reused; FMA contraction is allowed.
+// E, B_t1, B_t2).  Reciprocals are formed once and reused (FP64 ones by rcp_nr below, within about one
+// ulp); FMA contraction is allowed.
 #pragma once
 #include <cuda_runtime.h>
 
 namespace vl2 {
+
+// ---- FP64 reciprocal and square root ------------------------------------------------------------
+// The FP64 divide and square root are the costliest steps of the flux arithmetic on this part.  Here the
+// PTX approximations rcp.approx.ftz.f64 and rsqrt.approx.ftz.f64 (relative error about 1e-6, measured)
+// are refined by one cubically convergent Newton step (Newton's method on 1/r - b and on 1/y^2 - x, in the
+// series form given by Markstein and in Muller et al., Handbook of Floating-Point Arithmetic):
+//   r ~ 1/b,       e = 1 - b r:        1/b      = r (1 + e + e^2 + ...)
+//   y ~ x^(-1/2),  h = 1 - x y^2:      x^(-1/2) = y (1 + h/2 + 3 h^2/8 + ...)
+// The remaining relative error is O(1e-18) plus the rounding of the last steps: within about one ulp of
+// the correctly rounded result, not always equal to it.  Inputs are finite normal numbers (no denormals);
+// sqrt_nr also takes +0 and returns +0.  Other scalar types (float, dual numbers) use their own / and sqrt.
+__device__ __forceinline__ double rcp_nr(double b) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
+  const double e = fma(-b, r, 1.0);
+  return fma(r, fma(e, e, e), r);
+}
+__device__ __forceinline__ double sqrt_nr(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double h = fma(-(x * y), y, 1.0);
+  const double s = x * fma(y * h, fma(0.375, h, 0.5), y);
+  return (__double_as_longlong(x) << 1) == 0 ? x : s;
+}
+template <class R> __device__ __forceinline__ R inv(R x) { return R(1) / x; }
+template <> __device__ __forceinline__ double inv<double>(double x) { return rcp_nr(x); }
+template <class R> __device__ __forceinline__ R root(R x) { return sqrt(x); }
+template <> __device__ __forceinline__ double root<double>(double x) { return sqrt_nr(x); }
+
+// ---- float <-> double on the integer pipe ----------------------------------------------------------
+// On this part a hardware conversion between float and double occupies the FP64 pipe like an FP64
+// operation.  Both directions are written here on the IEEE 754 bit layouts (binary32: 8-bit exponent,
+// bias 127; binary64: 11-bit exponent, bias 1023), which moves the work to the integer pipe.  Results
+// equal the hardware conversion (round to nearest even for double -> float); zeros are handled here, and
+// the rare cases outside the normal float range (denormal float inputs or results, overflow, inf, nan)
+// fall back to the hardware conversion.
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int mag = u & 0x7fffffffu;
+  const unsigned int e = mag >> 23;
+  if (e - 1u >= 254u) {  // exponent field 0 or 255
+    if (mag == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));  // signed zero
+    return (double)f;
+  }
+  const unsigned long long bits =
+      ((unsigned long long)(u >> 31) << 63) | (((unsigned long long)mag << 29) + (896ULL << 52));
+  return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ float to_f32(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long mag = u & 0x7fffffffffffffffULL;
+  const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
+  // double exponent field 897..1150 maps to the float exponents 1..254 (the rounding carry may reach 255 = inf)
+  if (mag - (897ULL << 52) < (254ULL << 52)) {
+    const unsigned long long r = mag + 0x0fffffffULL + ((mag >> 29) & 1ULL);  // nearest, ties to even
+    return __uint_as_float(sign | (unsigned int)((r >> 29) - (896ULL << 23)));
+  }
+  if (mag == 0ULL) return __uint_as_float(sign);
+  return (float)x;
+}
+__device__ __forceinline__ float to_f32(float x) { return x; }
 
 // Fast magnetosonic speed along the normal (Sec. 2.1.7 uses |v| + C_f):
 // C_f^2 = (a^2 + c_n^2 + c_t^2 + sqrt((a^2 - c_n^2)^2 + c_t^2 (c_t^2 + 2 a^2 + 2 c_n^2))) / 2,
@@ -17,7 +80,7 @@ __device__ __forceinline__ R fast_speed_r(R id, R p, R bn2, R bt2, R gamma) {
   const R ct = bt2 * id;
   const R df = asq - cn;
   const R rad = df * df + ct * (ct + R(2) * (asq + cn));
-  return sqrt(R(0.5) * ((asq + cn + ct) + sqrt(rad)));
+  return root(R(0.5) * ((asq + cn + ct) + root(rad)));
 }
 
 // Conserved 7-vector and physical flux of one sweep-frame state (eq. cons, eq. total_energy).
@@ -76,13 +139,14 @@ __device__ __forceinline__ void flux_hlle(const R* wl, const R* wr, R bn, R gamm
   phys_flux(wl, bn, igm1, ul, fl);
   phys_flux(wr, bn, igm1, ur, fr);
   const R bn2 = bn * bn;
-  const R cl = fast_speed_r(R(1) / wl[0], wl[4], bn2, wl[5] * wl[5] + wl[6] * wl[6], gamma);
-  const R cr = fast_speed_r(R(1) / wr[0], wr[4], bn2, wr[5] * wr[5] + wr[6] * wr[6], gamma);
+  const R ilr = inv(wl[0] * wr[0]);  // 1/rho_L and 1/rho_R from one reciprocal
+  const R cl = fast_speed_r(wr[0] * ilr, wl[4], bn2, wl[5] * wl[5] + wl[6] * wl[6], gamma);
+  const R cr = fast_speed_r(wl[0] * ilr, wr[4], bn2, wr[5] * wr[5] + wr[6] * wr[6], gamma);
   const R sl = imin(wl[1] - cl, wr[1] - cr);
   const R sr = imax(wl[1] + cl, wr[1] + cr);
   const R bm = ge0(sl) ? R(0) : sl;
   const R bp = gt0(sr) ? sr : R(0);
-  const R iden = R(1) / (bp - bm);
+  const R iden = inv(bp - bm);
   const R bpm = bp * bm;
 #pragma unroll
   for (int n = 0; n < 7; ++n) f[n] = ((bp * fl[n] - bm * fr[n]) + bpm * (ur[n] - ul[n])) * iden;
@@ -114,7 +178,7 @@ __device__ __forceinline__ void hlld_star_vb(const R* w, R a, R s, R sm, R bn, R
   bt[0] = w[5];
   bt[1] = w[6];
   if (igt(fabs(dd), R(1e-8) * ptst)) {
-    const R idd = R(1) / dd;
+    const R idd = inv(dd);
     const R tv = bn * (sm - w[1]) * idd;
     const R tb = (a * (s - w[1]) - bn2) * idd;
     vt[0] = w[2] - w[5] * tv;
@@ -129,7 +193,7 @@ __device__ __forceinline__ void hlld_star_vb(const R* w, R a, R s, R sm, R bn, R
 template <class R>
 __device__ __forceinline__ void hlld_side_flux(HlldSide<R>& S, const R* o_w, R o_s, R o_a, bool left, R sm,
                                                R bn, R bn2, R ptst, R* f) {
-  const R isms = R(1) / (S.s - sm);
+  const R isms = inv(S.s - sm);
   S.dst = S.a * isms;
   hlld_star_vb(S.w, S.a, S.s, sm, bn, bn2, ptst, S.vt, S.bt);
   const R vb = (S.w[1] * bn + S.w[2] * S.w[5]) + S.w[3] * S.w[6];
@@ -157,18 +221,18 @@ __device__ __forceinline__ void hlld_side_flux(HlldSide<R>& S, const R* o_w, R o
   }
   if (!outer && !single) {
     // double star: needs the other side's single-star density, velocity and field
-    const R o_dst = o_a / (o_s - sm);
+    const R o_dst = o_a * inv(o_s - sm);
     R o_vt[2], o_bt[2];
     hlld_star_vb(o_w, o_a, o_s, sm, bn, bn2, ptst, o_vt, o_bt);
     const R sq = S.dst * rs;  // sqrt(rho*) of this side
-    const R o_sq = sqrt(o_dst);
+    const R o_sq = root(o_dst);
     const R sql = left ? sq : o_sq, sqr = left ? o_sq : sq;
     const R* vtl = left ? S.vt : o_vt;
     const R* vtr = left ? o_vt : S.vt;
     const R* btl = left ? S.bt : o_bt;
     const R* btr = left ? o_bt : S.bt;
     const R sgn = ge0(bn) ? R(1) : R(-1);
-    const R isq = R(1) / (sql + sqr);
+    const R isq = inv(sql + sqr);
     const R vss1 = ((sql * vtl[0] + sqr * vtr[0]) + (btr[0] - btl[0]) * sgn) * isq;
     const R vss2 = ((sql * vtl[1] + sqr * vtr[1]) + (btr[1] - btl[1]) * sgn) * isq;
     const R bss1 = ((sql * btr[0] + sqr * btl[0]) + (sql * sqr) * (vtr[0] - vtl[0]) * sgn) * isq;
@@ -199,7 +263,7 @@ __device__ __forceinline__ void flux_hlld(const R* wl, const R* wr, R bn, R gamm
   const R bn2 = bn * bn;
   const R btl2 = wl[5] * wl[5] + wl[6] * wl[6];
   const R btr2 = wr[5] * wr[5] + wr[6] * wr[6];
-  const R ilr = R(1) / (wl[0] * wr[0]);  // 1/rho_L and 1/rho_R from one division
+  const R ilr = inv(wl[0] * wr[0]);  // 1/rho_L and 1/rho_R from one reciprocal
   const R cl = fast_speed_r(wr[0] * ilr, wl[4], bn2, btl2, gamma);
   const R cr = fast_speed_r(wl[0] * ilr, wr[4], bn2, btr2, gamma);
   const R cmax = imax(cl, cr);
@@ -207,7 +271,7 @@ __device__ __forceinline__ void flux_hlld(const R* wl, const R* wr, R bn, R gamm
   const R sr = imax(wl[1], wr[1]) + cmax;
   const R ptl = wl[4] + R(0.5) * (bn2 + btl2), ptr = wr[4] + R(0.5) * (bn2 + btr2);
   const R al = (sl - wl[1]) * wl[0], ar = (sr - wr[1]) * wr[0];
-  const R iden = R(1) / (ar - al);
+  const R iden = inv(ar - al);
   const R sm = ((ar * wr[1] - al * wl[1]) + (ptl - ptr)) * iden;
   const R ptst = ((ar * ptl - al * ptr) + (ar * al) * (wr[1] - wl[1])) * iden;
   const bool left = ge0(sm);

@@ -101,6 +101,7 @@ def test_one_step(vl2, oracle, case, riemann):
     g.step(dto)
     o.step(dto)
     d = state_diff(g.get_cons(), o.get_cons())
+    print("one cycle, %s, riemann %d: max normalised difference %.2e" % (case, riemann, np.max(d)))
     assert np.max(d) <= 1e-12, d
     assert g.new_dt() == pytest.approx(o.new_dt(0.3), rel=1e-12)
     assert g.floor_count() == 0
@@ -115,6 +116,7 @@ def test_hundred_steps_smooth(vl2, oracle):
         g.step(dt)
         o.step(dt)
     d = state_diff(g.get_cons(), o.get_cons())
+    print("100 cycles, smooth wave: max normalised difference %.2e" % np.max(d))
     assert np.max(d) <= 1e-9, d
 
 
@@ -128,6 +130,7 @@ def test_hundred_steps_orszag_tang_small(vl2, oracle):
         g.step(g.new_dt())
         o.step(o.new_dt(0.3))
     d = state_diff(g.get_cons(), o.get_cons())
+    print("100 cycles, vortex 24^3: max normalised difference %.2e" % np.max(d))
     assert np.max(d) <= 1e-9, d
 
 
