@@ -175,14 +175,24 @@ vl2_status vl2_debug_emfs(vl2_mesh* mesh, int recon, double* e1, double* e2, dou
  * adjoint lam_out of the cycle's output (u [5][NZ][NY][NX] and face fields b1..b3, global layout, device),
  * writes lam_in = J(x)^T lam_out (same layout, device) where J is the Jacobian of the cycle.  The
  * cycle's forward intermediates are recomputed from x, which is left unchanged.  Reverse order: update,
- * upwind-CT EMFs (upwind choices frozen at x), Riemann fluxes (local Jacobians by forward-mode dual
- * numbers through the forward flux function), PLM (limiter switch frozen), cons->prim, ghost exchange;
+ * upwind-CT EMFs (upwind choices frozen at x), Riemann fluxes (reverse-mode derivative replaying the
+ * forward flux's arithmetic and branches), PLM (limiter switch frozen), cons->prim, ghost exchange;
  * corrector first, then the predictor.  Face entries follow the global layout: the adjoint of face N of a
  * periodic direction is kept apart from face 0 (they are separate array entries).  Needs a mesh created
  * with params.adjoint = 1 and VL2_FP64, and no active floors.  Errors: VL2_E_ARG, VL2_E_STATE,
  * VL2_E_CUDA. */
 vl2_status vl2_step_vjp(vl2_mesh* mesh, double dt, const double* lam_u, const double* lam_b1, const double* lam_b2,
                         const double* lam_b3, double* out_u, double* out_b1, double* out_b2, double* out_b3);
+
+/* Pointwise reverse-mode derivative of the Riemann flux (Sec. 3.2.2) used by vl2_step_vjp, for checking it
+ * against an independent Jacobian: for n interfaces q with sweep-frame states wl[q][7], wr[q][7]
+ * (rho, v_n, v_t1, v_t2, p, b_t1, b_t2), normal field bn[q] and flux adjoint lf[q][7] (mass, M_n, M_t1,
+ * M_t2, E, B_t1, B_t2), writes out[q][k] = sum_m lf[q][m] dF_m/dx_k with x = (wl[0..6], wr[0..6], bn).
+ * riemann: VL2_HLLD or VL2_HLLE; gamma > 1.  All arrays are device memory owned by the caller, row-major
+ * as shown; the work is enqueued on `stream` (cudaStream_t, may be NULL) and the call does not wait.
+ * Errors: VL2_E_ARG (NULL pointer, n < 0, bad riemann or gamma), VL2_E_CUDA. */
+vl2_status vl2_debug_riemann_vjp(int riemann, long long n, const double* wl, const double* wr, const double* bn,
+                                 const double* lf, double gamma, double* out, void* stream);
 
 /* Adjoint of the set-up map prims -> conserved (eq. total_energy) with the field held fixed: from the
  * primitives w = [5][N] (rho, v, p; device, global layout) and lam_u = [5][N] (device), writes

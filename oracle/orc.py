@@ -64,6 +64,7 @@ def lib():
         L.orc_divb_norm.restype = ctypes.c_double
         L.orc_totals.argtypes = [ctypes.c_void_p, dp]
         L.orc_riemann.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double, dp]
+        L.orc_riemann_jacobian.argtypes = [ctypes.c_int, ctypes.c_longlong, dp, dp, dp, ctypes.c_double, dp]
         L.orc_physical_flux.argtypes = [dp, ctypes.c_double, ctypes.c_double, dp, dp]
         L.orc_fast_speed.argtypes = [ctypes.c_double] * 6
         L.orc_fast_speed.restype = ctypes.c_double
@@ -96,6 +97,16 @@ def riemann(solver, wl, wr, bn, gamma):
     wl, wr = _c64(wl), _c64(wr)
     lib().orc_riemann(solver, _dp(wl), _dp(wr), float(bn), float(gamma), _dp(f))
     return f
+
+
+def riemann_jacobian(solver, wl, wr, bn, gamma):
+    """dF/d(w_L, w_R, b_n) for n interfaces: wl, wr (n, 7), bn (n,) -> (n, 7, 15), by dual numbers."""
+    wl, wr = _c64(np.atleast_2d(wl)), _c64(np.atleast_2d(wr))
+    bn = _c64(np.atleast_1d(bn))
+    n = wl.shape[0]
+    jac = np.zeros((n, 7, 15))
+    lib().orc_riemann_jacobian(solver, n, _dp(wl), _dp(wr), _dp(bn), float(gamma), _dp(jac))
+    return jac
 
 
 def physical_flux(w, bn, gamma):

@@ -1248,6 +1248,24 @@ void orc_riemann(int solver, const double* wl, const double* wr, double bn, doub
   orc::riemann<double>(solver, wl, wr, bn, gamma, f);
 }
 
+/* Jacobians of the Riemann flux for n interfaces: jac[q][n][k] = dF_n / dx_k with x = (w_L[0..6], w_R[0..6],
+   b_n), one dual-number evaluation per column (test infrastructure for the adjoint). */
+void orc_riemann_jacobian(int solver, long long n, const double* wl, const double* wr, const double* bn, double gamma,
+                          double* jac) {
+  for (long long q = 0; q < n; ++q) {
+    for (int k = 0; k < 15; ++k) {
+      orc::Dual dl[orc::NW7], dr[orc::NW7], f[orc::NW7];
+      for (int m = 0; m < orc::NW7; ++m) {
+        dl[m] = orc::Dual(wl[7 * q + m], k == m ? 1.0 : 0.0);
+        dr[m] = orc::Dual(wr[7 * q + m], k == 7 + m ? 1.0 : 0.0);
+      }
+      const orc::Dual b(bn[q], k == 14 ? 1.0 : 0.0);
+      orc::riemann<orc::Dual>(solver, dl, dr, b, gamma, f);
+      for (int m = 0; m < orc::NW7; ++m) jac[(q * 7 + m) * 15 + k] = f[m].d;
+    }
+  }
+}
+
 void orc_physical_flux(const double* w, double bn, double gamma, double* u, double* f) {
   orc::physical_flux<double>(w, bn, gamma, u, f);
 }

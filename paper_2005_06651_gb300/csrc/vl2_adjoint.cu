@@ -3,11 +3,11 @@
 // (Sec. 3.2.3): update -> CT corner EMFs -> fluxes (PLM / donor cell + Riemann solver) -> cons->prim ->
 // ghost exchange, for the corrector and then the predictor.  The linear steps (update, CT for the frozen
 // upwind choices, ghost exchange, PLM limiter away from its switch) have hand-derived transposes; the
-// Riemann solver's local Jacobian comes from forward-mode dual numbers through the same device flux
-// function the forward step uses.
-#include "vl2_dual.cuh"
+// Riemann solvers have hand-written reverse-mode derivatives (vl2_riemann_vjp.cuh) that replay the
+// forward flux's arithmetic and branch decisions.
 #include "vl2_internal.h"
 #include "vl2_physics.cuh"
+#include "vl2_riemann_vjp.cuh"
 
 namespace vl2 {
 
@@ -212,8 +212,8 @@ __global__ void k_adj_ct(Geom g, const double* W, const double* m0, const double
 }
 
 // ------------------------------------------------------------------------------------------------
-// Transpose of the face fluxes: lam_F . dF/d(w_L, w_R, b_n) by forward-mode dual numbers (NT tangent
-// directions per pass), then through the reconstruction to the cells (PLM: van Leer slope derivatives;
+// Transpose of the face fluxes: lam_F . dF/d(w_L, w_R, b_n) by reverse mode (one value pass and one
+// reverse pass per face), then through the reconstruction to the cells (PLM: van Leer slope derivatives;
 // its switch at dl*dr = 0 is frozen).
 // ------------------------------------------------------------------------------------------------
 __device__ __forceinline__ void vl_slope_grad(double qm, double q0, double qp, double& dqm, double& dq0, double& dqp) {
@@ -231,7 +231,7 @@ __device__ __forceinline__ void vl_slope_grad(double qm, double q0, double qp, d
   }
 }
 
-template <int DIR, int REC, int RS, int NT>
+template <int DIR, int REC, int RS>
 __global__ void __launch_bounds__(128) k_adj_flux(Geom g, const double* __restrict__ W, const double* __restrict__ Bn,
                                                   const double* __restrict__ LF, double* lw, double* lbn) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
@@ -279,40 +279,14 @@ __global__ void __launch_bounds__(128) k_adj_flux(Geom g, const double* __restri
     }
   }
   const double bn = Bn[(long long)b * g.box + c];
-  // adjoints of the 15 Riemann inputs: lam_x[k] = sum_n lf[n] dF_n/dx_k
+  // adjoints of the 15 Riemann inputs: lam_x[k] = sum_n lf[n] dF_n/dx_k, by reverse mode
   double lx[15];
-  for (int p0 = 0; p0 < 15; p0 += NT) {
-    DualN<NT> dl[7], dr[7], dbn(bn);
 #pragma unroll
-    for (int n = 0; n < 7; ++n) {
-      dl[n] = DualN<NT>(wl[n]);
-      dr[n] = DualN<NT>(wr[n]);
-    }
-#pragma unroll
-    for (int q2 = 0; q2 < NT; ++q2) {
-      const int kx = p0 + q2;
-      if (kx < 7)
-        dl[kx].d[q2] = 1.0;
-      else if (kx < 14)
-        dr[kx - 7].d[q2] = 1.0;
-      else if (kx == 14)
-        dbn.d[q2] = 1.0;
-    }
-    DualN<NT> f[7];
-    if (RS == RS_HLLD)
-      flux_hlld<DualN<NT>>(dl, dr, dbn, DualN<NT>(g.gamma), DualN<NT>(g.igm1), f);
-    else
-      flux_hlle<DualN<NT>>(dl, dr, dbn, DualN<NT>(g.gamma), DualN<NT>(g.igm1), f);
-#pragma unroll
-    for (int q2 = 0; q2 < NT; ++q2) {
-      const int kx = p0 + q2;
-      if (kx >= 15) break;
-      double s = 0.0;
-#pragma unroll
-      for (int n = 0; n < 7; ++n) s += lf[n] * f[n].d[q2];
-      lx[kx] = s;
-    }
-  }
+  for (int k = 0; k < 15; ++k) lx[k] = 0.0;
+  if (RS == RS_HLLD)
+    flux_hlld_vjp(wl, wr, bn, g.gamma, g.igm1, lf, lx, lx + 7, lx[14]);
+  else
+    flux_hlle_vjp(wl, wr, bn, g.gamma, g.igm1, lf, lx, lx + 7, lx[14]);
   lbn[(long long)b * g.box + c] += lx[14];
   double* LWb = lw + (long long)b * 8 * g.box + c;
 #pragma unroll
@@ -501,11 +475,33 @@ __global__ void k_prims_vjp(long long n, double igm1, const double* w, const dou
   lam_w[4 * n + t] = l4 * igm1;
 }
 
+// Pointwise Riemann VJP for n interfaces (rows of 7 / 15), for checking the adjoint's flux derivative.
+__global__ void k_riemann_vjp_points(int rs, long long n, const double* wl, const double* wr, const double* bn,
+                                     const double* lf, double gamma, double* out) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  double a[7], b[7], l[7], x[15];
+#pragma unroll
+  for (int m = 0; m < 7; ++m) {
+    a[m] = wl[7 * q + m];
+    b[m] = wr[7 * q + m];
+    l[m] = lf[7 * q + m];
+  }
+#pragma unroll
+  for (int k = 0; k < 15; ++k) x[k] = 0.0;
+  const double igm1 = 1.0 / (gamma - 1.0);
+  if (rs == RS_HLLD)
+    flux_hlld_vjp(a, b, bn[q], gamma, igm1, l, x, x + 7, x[14]);
+  else
+    flux_hlle_vjp(a, b, bn[q], gamma, igm1, l, x, x + 7, x[14]);
+#pragma unroll
+  for (int k = 0; k < 15; ++k) out[15 * q + k] = x[k];
+}
+
 // ------------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------------
 constexpr int AT = 256;
-constexpr int DUAL_TANGENTS = 3;
 
 static long long nodes_ext(const Geom& g) {
   return (long long)(g.mb[0] + 2) * (g.mb[1] + 2) * (g.mb[2] + 2) * g.nblk;
@@ -541,7 +537,7 @@ static cudaError_t adj_flux_one(const Geom& g, const AdjArrays& j, const double*
                                 cudaStream_t st) {
   long long n = g.nblk;
   for (int q = 0; q < 3; ++q) n *= g.mb[q] + (q == DIR ? 1 : 2);
-  k_adj_flux<DIR, REC, RS, DUAL_TANGENTS><<<grid_of(n, 128), 128, 0, st>>>(g, W, Bn, j.lf[DIR], j.lw, lbn);
+  k_adj_flux<DIR, REC, RS><<<grid_of(n, 128), 128, 0, st>>>(g, W, Bn, j.lf[DIR], j.lw, lbn);
   return cudaGetLastError();
 }
 
@@ -586,6 +582,13 @@ cudaError_t adj_gather_in(const Geom& g, const AdjArrays& j, double* gu, double*
 
 cudaError_t prims_vjp(long long ncell, double igm1, const double* w, const double* lam_u, double* lam_w, cudaStream_t st) {
   k_prims_vjp<<<grid_of(ncell, AT), AT, 0, st>>>(ncell, igm1, w, lam_u, lam_w);
+  return cudaGetLastError();
+}
+
+cudaError_t riemann_vjp_points(int rs, long long n, const double* wl, const double* wr, const double* bn,
+                               const double* lf, double gamma, double* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_riemann_vjp_points<<<grid_of(n, 128), 128, 0, st>>>(rs, n, wl, wr, bn, lf, gamma, out);
   return cudaGetLastError();
 }
 

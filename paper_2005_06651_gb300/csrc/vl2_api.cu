@@ -576,6 +576,17 @@ vl2_status vl2_step_vjp(vl2_mesh* m, double dt, const double* lam_u, const doubl
   return VL2_OK;
 }
 
+vl2_status vl2_debug_riemann_vjp(int riemann, long long n, const double* wl, const double* wr, const double* bn,
+                                 const double* lf, double gamma, double* out, void* stream) {
+  if (n < 0 || (n > 0 && (!wl || !wr || !bn || !lf || !out))) return fail(nullptr, VL2_E_ARG, "bad pointer or n < 0");
+  if (riemann != VL2_HLLD && riemann != VL2_HLLE) return fail(nullptr, VL2_E_ARG, "riemann must be VL2_HLLD or VL2_HLLE");
+  if (!(gamma > 1.0) || !std::isfinite(gamma)) return fail(nullptr, VL2_E_ARG, "gamma must be > 1");
+  const cudaError_t e = vl2::riemann_vjp_points(riemann == VL2_HLLD ? vl2::RS_HLLD : vl2::RS_HLLE, n, wl, wr, bn, lf,
+                                                gamma, out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(nullptr, VL2_E_CUDA, cudaGetErrorString(e));
+  return VL2_OK;
+}
+
 vl2_status vl2_prims_vjp(vl2_mesh* m, const double* w, const double* lam_u, double* lam_w) {
   if (!m || !w || !lam_u || !lam_w) return fail(m, VL2_E_ARG, "NULL argument");
   VL2_CHECK(m, vl2::prims_vjp(ncells(m->g), m->g.igm1, w, lam_u, lam_w, m->st));

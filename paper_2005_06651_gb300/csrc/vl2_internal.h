@@ -151,6 +151,8 @@ cudaError_t adj_ghosts(const Geom& g, const AdjArrays& j, int lam_reg, cudaStrea
 cudaError_t adj_gather_in(const Geom& g, const AdjArrays& j, double* gu, double* gb1, double* gb2, double* gb3,
                           cudaStream_t st);
 cudaError_t prims_vjp(long long ncell, double igm1, const double* w, const double* lam_u, double* lam_w, cudaStream_t st);
+cudaError_t riemann_vjp_points(int rs, long long n, const double* wl, const double* wr, const double* bn,
+                               const double* lf, double gamma, double* out, cudaStream_t st);
 cudaError_t launch_scatter_cons(const Geom& g, const Arrays& a, const double* u, const double* b1, const double* b2,
                                 const double* b3, cudaStream_t st);
 

@@ -127,8 +127,10 @@ __device__ __forceinline__ int okey(float x) {
   const int b = dbits(x);
   return b ^ ((b >> 31) & 0x7fffffff);
 }
-template <class R> __device__ __forceinline__ R imin(R a, R b) { return okey(b) < okey(a) ? b : a; }
-template <class R> __device__ __forceinline__ R imax(R a, R b) { return okey(b) > okey(a) ? b : a; }
+// min / max with ties going to b (the values agree at a tie; the rule fixes which argument a derivative
+// follows there)
+template <class R> __device__ __forceinline__ R imin(R a, R b) { return okey(a) < okey(b) ? a : b; }
+template <class R> __device__ __forceinline__ R imax(R a, R b) { return okey(a) > okey(b) ? a : b; }
 template <class R> __device__ __forceinline__ bool igt(R a, R b) { return okey(a) > okey(b); }
 
 // HLLE flux; outer speeds are the extreme fast-wave speeds of the two states (Sec. 3.2.2 names the

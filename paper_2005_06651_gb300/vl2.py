@@ -56,7 +56,7 @@ EXPORTS = ["vl2_workspace_bytes", "vl2_mesh_create", "vl2_mesh_destroy", "vl2_bl
            "vl2_profile_read", "vl2_launch_count", "vl2_totals_noalloc", "vl2_batch_workspace_bytes",
            "vl2_batch_create", "vl2_batch_destroy", "vl2_batch_autotune", "vl2_batch_step", "vl2_batch_run",
            "vl2_batch_launch_count", "vl2_batch_last_error", "vl2_set_cons", "vl2_step_vjp", "vl2_prims_vjp",
-           "vl2_last_error"]
+           "vl2_debug_riemann_vjp", "vl2_last_error"]
 NOALLOC_MAX_NZ = 4096
 K_PRIM, K_GHOSTS, K_FLUX_DC, K_FLUX_PLM, K_EMF, K_UPDATE = range(6)
 KERNEL_KINDS = {K_PRIM: "prim", K_GHOSTS: "ghosts", K_FLUX_DC: "flux_dc", K_FLUX_PLM: "flux_plm", K_EMF: "emf",
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
     L.vl2_set_cons.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int]
     L.vl2_step_vjp.argtypes = [vp, ctypes.c_double] + [dp] * 8
     L.vl2_prims_vjp.argtypes = [vp, dp, dp, dp]
+    L.vl2_debug_riemann_vjp.argtypes = [ctypes.c_int, ctypes.c_longlong, dp, dp, dp, dp, ctypes.c_double, dp, vp]
     L.vl2_batch_workspace_bytes.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.vl2_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, vp, sz, ctypes.POINTER(ctypes.c_void_p)]
     L.vl2_batch_destroy.argtypes = [vp]
@@ -361,6 +362,22 @@ def totals_noalloc(u, b1, b2, b3, dx, out, stream=None):
     st = (stream or torch.cuda.current_stream(u.device)).cuda_stream
     _check(load().vl2_totals_noalloc(*[ctypes.c_void_p(t.data_ptr()) for t in (u, b1, b2, b3)], dims, h,
                                      ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st)))
+    return out
+
+
+def debug_riemann_vjp(riemann, wl, wr, bn, lf, gamma, stream=None):
+    """vl2_debug_riemann_vjp on contiguous float64 CUDA tensors wl, wr, lf [n][7] and bn [n]: returns the
+    [n][15] tensor lf . dF/d(w_L, w_R, b_n)."""
+    import torch
+
+    for t in (wl, wr, bn, lf):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError("debug_riemann_vjp takes contiguous float64 CUDA tensors")
+    n = bn.shape[0]
+    out = torch.empty((n, 15), dtype=torch.float64, device=bn.device)
+    st = (stream or torch.cuda.current_stream(bn.device)).cuda_stream
+    _check(load().vl2_debug_riemann_vjp(int(riemann), n, *[ctypes.c_void_p(t.data_ptr()) for t in (wl, wr, bn, lf)],
+                                        float(gamma), ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st)))
     return out
 
 
