@@ -49,7 +49,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of
 # the k_flux_plm x sweep on the 128^3 vortex, 2,441,472 faces), scaled to a launch by its faces; valid only
 # for the kernel source it was taken on (hash of the flux and physics sources), else reported as null.
-NCU_TRAFFIC = {"hash": "d06840d23810bb88", "bytes_per_face": 134.6}
+NCU_TRAFFIC = {"hash": "d214e7738f806cef", "bytes_per_face": 134.8}
 
 
 def flux_source_hash():
@@ -124,6 +124,24 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(x, pg, device):
+    """The largest value of x over all ranks (the job's time is its slowest rank's); x itself when there is
+    no process group."""
+    if not pg:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(cells_per_rank, steps, seconds, world):
+    """Zone-cycles/s of the whole job: every rank advances its own replica of `cells_per_rank` cells for
+    `steps` cycles, and the job takes `seconds` (the max over ranks)."""
+    return world * cells_per_rank * steps / seconds
+
+
 def oracle_rate(n, mb, steps, warmup, seed=2005, min_seconds=0.0, max_steps=None):
     """Time the CPU oracle on an n^3 sample of the vortex; returns (zone-cycles/s, steps, threads, s)."""
     from oracle import orc
@@ -148,6 +166,26 @@ def oracle_rate(n, mb, steps, warmup, seed=2005, min_seconds=0.0, max_steps=None
     return prob.ncells * done / el, done, threads, el
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the CPU baseline's record."""
+    import subprocess
+
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def orc_threads():
     try:
         import ctypes
@@ -170,7 +208,8 @@ def run_reference(args, world, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / done, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args),
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                             "cpu": cpu_model()},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -322,35 +361,37 @@ def batched_form(args, dev, stream, vl2, inputs):
 
 
 def adjoint_form(args, dev, stream, vl2, inputs):
-    """Differentiation form, FP64: a 64^3 periodic box (8 MeshBlocks of 32^3) holding a fast magnetosonic
-    wave (amplitude 1e-2) carried by a uniform flow, adv_steps VL2 cycles behind torch.autograd with a
-    checkpoint every ~sqrt(N) cycles.  Loss = sum over cells of (rho_final - target)^2 dV, target = initial
-    density + 0.01 N(0,1) (seed 5005); gradient with respect to the initial velocity (3 x 64^3).  Reports
-    forward and backward device time, their ratio, the peak device memory of forward + backward, and a
-    central finite-difference check of the gradient along smooth directions (same time steps)."""
+    """Differentiation form, FP64, 64^3 periodic box in 8 MeshBlocks of 32^3, adj_steps VL2 cycles behind
+    torch.autograd with a checkpoint every ~sqrt(N) cycles.  Loss = sum over cells of (rho_final - target)^2
+    dV with target = 1 + 0.01 N(0,1) (seed 5005); gradient with respect to the initial velocity (3 x 64^3).
+    Timing and peak memory: seeded decaying turbulence (Mach 1, beta 10, seed 3003), forward and backward
+    device time and their ratio.  Gradient check: a fast magnetosonic wave (amplitude 1e-2) carried by a
+    uniform flow, central finite differences along smooth directions with the same time steps."""
     import numpy as np
     import torch
 
     from paper_2005_06651_gb300 import adjoint
 
     n, K = args.adj_n, args.adj_steps
-    prob = inputs.linear_wave(n, mb=min(32, n), kind="fast", amp=1e-2, v0=(0.7, 0.4, 0.2))
+    mb = min(32, n)
     k = max(1, int(round(K ** 0.5)))
+    target = torch.from_numpy(1.0 + 0.01 * np.random.Generator(np.random.PCG64(5005)).standard_normal((n, n, n)))
+    target = target.to(dev)
+
+    def setup(prob):
+        runner = adjoint.Rollout(prob, nsteps=K, checkpoint_every=k, device=dev)
+        dv = float(np.prod(prob.dx))
+        v_init = torch.from_numpy(np.ascontiguousarray(prob.w[1:4])).to(dev)
+        return runner, v_init, (lambda u: ((u[0] - target) ** 2).sum() * dv)
+
+    # timing and memory on the turbulence state
+    turb = inputs.turbulence(n=n, mb=mb, seed=3003, mach=1.0, beta=10.0)
     torch.cuda.synchronize(dev)
     torch.cuda.empty_cache()
     base_mem = torch.cuda.memory_allocated(dev)
     torch.cuda.reset_peak_memory_stats(dev)
-    runner = adjoint.Rollout(prob, nsteps=K, checkpoint_every=k, device=dev)
-    rng = np.random.Generator(np.random.PCG64(5005))
-    target = torch.from_numpy(prob.w[0] + 0.01 * rng.standard_normal(prob.w[0].shape)).to(dev)
-    dv = float(np.prod(prob.dx))
-    v_init = torch.from_numpy(np.ascontiguousarray(prob.w[1:4])).to(dev)
-
-    def loss_of(u):
-        return ((u[0] - target) ** 2).sum() * dv
-
+    runner, v_init, loss_of = setup(turb)
     times = {"forward": [], "backward": []}
-    grad = None
     for rep in range(3):  # the first repetition is the warm-up
         v = v_init.clone().requires_grad_(True)
         torch.cuda.synchronize(dev)
@@ -364,11 +405,20 @@ def adjoint_form(args, dev, stream, vl2, inputs):
         if rep:
             times["forward"].append(t1 - t0)
             times["backward"].append(t2 - t1)
-        grad = v.grad.detach().clone()
     peak = torch.cuda.max_memory_allocated(dev) - base_mem
-    state_bytes = 8 * (5 * prob.ncells + sum(int(np.prod(b.shape)) for b in (prob.b1, prob.b2, prob.b3)))
+    floors = runner.mesh.floor_count()
+    runner.mesh.close()
+    state_bytes = 8 * (5 * turb.ncells + sum(int(np.prod(b.shape)) for b in (turb.b1, turb.b2, turb.b3)))
+
+    # gradient check on the advected wave
+    wave = inputs.linear_wave(n, mb=mb, kind="fast", amp=1e-2, v0=(0.7, 0.4, 0.2))
+    runner, v_init, loss_of = setup(wave)
+    v = v_init.clone().requires_grad_(True)
+    loss_of(adjoint.rollout(v, runner)).backward()
+    grad = v.grad.detach().clone()
     runner.fixed_dts = list(runner.dts)
-    x, y, z = inputs._cell_coords(prob.nx, prob.xmin, prob.xmax)
+    x, y, z = inputs._cell_coords(wave.nx, wave.xmin, wave.xmax)
+    rng = np.random.Generator(np.random.PCG64(5006))
     fd_checks = []
     for trial in range(2):
         ph = rng.uniform(0, 2 * np.pi, size=(3, 3))
@@ -384,18 +434,17 @@ def adjoint_form(args, dev, stream, vl2, inputs):
         fd_checks.append({"fd": fd, "adjoint": ad, "rel_err": abs(fd - ad) / abs(ad)})
     runner.mesh.close()
     fwd, bwd = float(np.median(times["forward"])), float(np.median(times["backward"]))
-    return {"config": {"workload": "fast_wave_%d^3_%dx%d^3_blocks_amp1e-2_flow_0.7_0.4_0.2" % (
-                           n, (n // min(32, n)) ** 3, min(32, n)),
-                       "steps": K, "checkpoint_every": k, "checkpoints": (K + k - 1) // k,
-                       "loss": "sum (rho_final - target)^2 dV, target = rho_0 + 0.01 N(0,1), seed 5005",
+    return {"config": {"workload": "decaying_turbulence_%d^3_%dx%d^3_blocks_mach1_beta10" % (n, (n // mb) ** 3, mb),
+                       "seed": 3003, "steps": K, "checkpoint_every": k, "checkpoints": (K + k - 1) // k,
+                       "loss": "sum (rho_final - target)^2 dV, target = 1 + 0.01 N(0,1), seed 5005",
                        "wrt": "initial velocity (3 x %d^3)" % n, "dtype": "f64", "riemann": "hlld",
-                       "reconstruction": "plm"},
+                       "reconstruction": "plm", "fd_check_workload": "fast_wave_%d^3_amp1e-2_flow_0.7_0.4_0.2" % n},
             "forward_s": fwd, "backward_s": bwd, "backward_over_forward": bwd / fwd,
-            "forward_value": prob.ncells * K / fwd, "unit": UNIT,
+            "forward_value": turb.ncells * K / fwd, "unit": UNIT, "floor_events": floors,
             "peak_mem_bytes": int(peak), "state_bytes": state_bytes,
             "peak_mem_over_state": peak / state_bytes,
-            "fd_check": {"h": 1e-8, "directions": "smooth sin/cos products, random phases", "checks": fd_checks,
-                         "max_rel_err": max(c["rel_err"] for c in fd_checks)}}
+            "fd_check": {"h": 1e-8, "directions": "smooth sin/cos products, random phases (seed 5006)",
+                         "checks": fd_checks, "max_rel_err": max(c["rel_err"] for c in fd_checks)}}
 
 
 def run_forms(args, dev, stream, vl2, inputs):
@@ -500,12 +549,9 @@ def main():
     launches = mesh.launch_count() - launches0
     prof = mesh.profile_read()
     mesh.profile(False)
-    if pg:
-        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, pg, dev)
     ms_step = ms_total / args.steps
-    value = world * prob.ncells * args.steps / (ms_total / 1e3)
+    value = whole_job_rate(prob.ncells, args.steps, ms_total / 1e3, world)
 
     # roofline of the dominant kernel
     kinds = {k: v for k, v in prof.items() if v[1] > 0}
@@ -557,11 +603,8 @@ def main():
         mesh.get_cons(outs)
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
-    if pg:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * prob.ncells * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+    e2e_s = max_over_ranks(e2e_s, pg, dev)
+    e2e = {"value": whole_job_rate(prob.ncells, ke, e2e_s, world), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "steps": ke,
            "path": "set_prims (pinned host) + new_dt + step + get_cons (pinned host) per step"}
     divb = mesh.divb_norm()
@@ -576,7 +619,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, done, threads, el = oracle_rate(args.n, args.mb, 1, 0, min_seconds=10.0, max_steps=3)
-        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu": cpu_model(),
                "sample": "%d VL2 cycle(s) of the full %d^3 workload (%d MeshBlocks), %.1f s" % (
                    done, args.n, (args.n // args.mb) ** 3, el)}
     if rank == 0:

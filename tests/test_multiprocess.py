@@ -1,0 +1,74 @@
+"""The N>1 host path of bench.py on CPU: world size 2 over gloo (127.0.0.1).  Every rank runs its own
+replica; the only cross-rank steps are the barrier and the max-over-ranks time, and rank 0 alone prints
+the result line."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    mine = 1.5 + rank * 2.25  # each rank's own elapsed time
+    slowest = bench.max_over_ranks(mine, dist, "cpu")
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, slowest, bench.whole_job_rate(1000, 10, slowest, world)))
+
+
+def test_max_over_ranks_and_whole_job_rate_gloo_world_size_2():
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[1] for r in res] == [3.75, 3.75]  # both ranks see the slowest rank's time
+    assert all(r[2] == pytest.approx(2 * 1000 * 10 / 3.75) for r in res)
+
+
+def test_max_over_ranks_without_a_group_is_the_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert bench.max_over_ranks(2.5, None, "cpu") == 2.5
+    assert bench.whole_job_rate(100, 4, 2.0, 1) == 200.0
+
+
+def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
+    """bench.py --impl reference launched as 2 ranks: rank 0 times the oracle and prints the one JSON
+    line; the other rank exits 0 without work."""
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
+           "127.0.0.1", "--master-port", str(free_port()), "bench.py", "--impl", "reference", "--gpus", "2",
+           "--steps", "1", "--warmup", "0"]
+    out = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle"
