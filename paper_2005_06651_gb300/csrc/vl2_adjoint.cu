@@ -143,72 +143,111 @@ __device__ __forceinline__ void pick_w(double m, double& w0, double& w1) {
   }
 }
 
-__device__ __forceinline__ void cell_emf_adj(int e, const double* Wc, long long box, double lam, double* LWc) {
-  const double vx = Wc[box], vy = Wc[2 * box], vz = Wc[3 * box];
-  const double bx = Wc[5 * box], by = Wc[6 * box], bz = Wc[7 * box];
-  if (e == 0) {  // vz by - vy bz
-    atomicAdd(LWc + 3 * box, lam * by);
-    atomicAdd(LWc + 6 * box, lam * vz);
-    atomicAdd(LWc + 2 * box, -lam * bz);
-    atomicAdd(LWc + 7 * box, -lam * vy);
-  } else if (e == 1) {  // vx bz - vz bx
-    atomicAdd(LWc + 1 * box, lam * bz);
-    atomicAdd(LWc + 7 * box, lam * vx);
-    atomicAdd(LWc + 3 * box, -lam * bx);
-    atomicAdd(LWc + 5 * box, -lam * vz);
-  } else {  // vy bx - vx by
-    atomicAdd(LWc + 2 * box, lam * bx);
-    atomicAdd(LWc + 5 * box, lam * vy);
-    atomicAdd(LWc + 1 * box, -lam * by);
-    atomicAdd(LWc + 6 * box, -lam * vx);
-  }
+// Upwind weights and adjoint coefficients of one corner EMF (family e, node c): the corner EMF is
+//   E = cea0 ea(b-1) + cea1 ea(b) + ceb0 eb(a-1) + ceb1 eb(a) + cec0 ec(a-1,b-1) + cec1 ec(a,b-1)
+//     + cec2 ec(a-1,b) + cec3 ec(a,b)
+// with ea = -F_a[B_t1] and eb = +F_b[B_t2] (the face EMFs) and ec = -v x b (cell EMFs).
+struct EdgeCoef {
+  double cea0, cea1, ceb0, ceb1, cec0, cec1, cec2, cec3;
+};
+__device__ __forceinline__ EdgeCoef edge_coef(const double* Ma, const double* Mb, long long c, long long sa,
+                                              long long sb) {
+  double w0, w1, u0, u1, s0, s1, r0, r1;
+  pick_w(Ma[c - sb], w0, w1);  // tlo: gradient along b below the corner, by the a-face mass flux at b-1
+  pick_w(Ma[c], u0, u1);       // thi
+  pick_w(Mb[c - sa], s0, s1);  // slo: gradient along a, by the b-face mass flux at a-1
+  pick_w(Mb[c], r0, r1);       // shi
+  EdgeCoef k;
+  k.cea0 = 0.25 * (1.0 + s0 + r0);
+  k.cea1 = 0.25 * (1.0 + s1 + r1);
+  k.ceb0 = 0.25 * (1.0 + w0 + u0);
+  k.ceb1 = 0.25 * (1.0 + w1 + u1);
+  k.cec0 = -0.25 * (w0 + s0);
+  k.cec1 = -0.25 * (w1 + r0);
+  k.cec2 = -0.25 * (u0 + s1);
+  k.cec3 = -0.25 * (u1 + r1);
+  return k;
 }
 
+// corner EMFs of family e exist at nodes NG..NG+mb-1 along e and NG..NG+mb across
+__device__ __forceinline__ bool edge_valid(const Geom& g, int e, const int* n) {
+  bool ok = true;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) ok = ok && n[q] >= NG && n[q] <= NG + g.mb[q] - (q == e ? 1 : 0);
+  return ok;
+}
+
+// Transpose of the upwind CT (linear for the upwind choices the forward step made), as a gather: the
+// thread of node n collects, in a fixed order, what the corner EMFs around it give to (i) the face-EMF
+// components of the fluxes at n (F_d[B_t1] from family d+2 at n and n + s_(d+1); F_d[B_t2] from family
+// d+1 at n and n + s_(d+2)) and (ii) the primitives of cell n through its three cell EMFs (each from the
+// four edges of its family around the cell).
 __global__ void k_adj_ct(Geom g, const double* W, const double* m0, const double* m1, const double* m2, long long mstride,
                          const double* le0, const double* le1, const double* le2, double* lf0, double* lf1,
                          double* lf2, double* lw) {
-  const int ex = g.mb[0] + 1, ey = g.mb[1] + 1, ez = g.mb[2] + 1;
+  const int ex = g.mb[0] + 2, ey = g.mb[1] + 2, ez = g.mb[2] + 2;  // nodes NG-1 .. NG+mb
   const long long per = (long long)ex * ey * ez;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= per * g.nblk) return;
   const int b = (int)(t / per);
   int rem = (int)(t - (long long)b * per);
-  const int li[3] = {rem % ex + NG, (rem / ex) % ey + NG, rem / (ex * ey) + NG};
+  const int li[3] = {rem % ex + NG - 1, (rem / ex) % ey + NG - 1, rem / (ex * ey) + NG - 1};
   const long long c = cell_off(g, li[2], li[1], li[0]);
   const long long stride[3] = {1LL, (long long)g.sx, (long long)g.sx * g.sy};
-  const double* M[3] = {m0, m1, m2};
-  const double* LE[3] = {le0, le1, le2};
-  double* LF[3] = {lf0, lf1, lf2};
-  const double* Wb = W + (long long)b * 8 * g.box;
-  double* LWb = lw + (long long)b * 8 * g.box;
-  for (int e = 0; e < 3; ++e) {
-    if (li[e] > NG + g.mb[e] - 1) continue;
-    const double lam = LE[e][(long long)b * g.box + c];
-    if (lam == 0.0) continue;
+  const double* M[3] = {m0 + (long long)b * mstride, m1 + (long long)b * mstride, m2 + (long long)b * mstride};
+  const double* LE[3] = {le0 + (long long)b * g.box, le1 + (long long)b * g.box, le2 + (long long)b * g.box};
+  double* LF[3] = {lf0 + (long long)b * 7 * g.box, lf1 + (long long)b * 7 * g.box, lf2 + (long long)b * 7 * g.box};
+  // edge family e at node c + s_p + s_q (p, q in {a, b} offsets given as 0/1): value lam * coefficient
+  auto edge_term = [&](int e, int da, int db, int which) -> double {
     const int a = (e + 1) % 3, bq = (e + 2) % 3;
-    const long long sa = stride[a], sb = stride[bq];
-    const double* Ma = M[a] + (long long)b * mstride;
-    const double* Mb = M[bq] + (long long)b * mstride;
-    double w0, w1, u0, u1, s0, s1, r0, r1;
-    pick_w(Ma[c - sb], w0, w1);  // tlo: gradient along b below the corner, by the a-face mass flux at b-1
-    pick_w(Ma[c], u0, u1);       // thi
-    pick_w(Mb[c - sa], s0, s1);  // slo: gradient along a, by the b-face mass flux at a-1
-    pick_w(Mb[c], r0, r1);       // shi
-    const double cea0 = 0.25 * (1.0 + s0 + r0), cea1 = 0.25 * (1.0 + s1 + r1);
-    const double ceb0 = 0.25 * (1.0 + w0 + u0), ceb1 = 0.25 * (1.0 + w1 + u1);
-    const double cec0 = -0.25 * (w0 + s0), cec1 = -0.25 * (w1 + r0);
-    const double cec2 = -0.25 * (u0 + s1), cec3 = -0.25 * (u1 + r1);
-    double* Fa = LF[a] + (long long)b * 7 * g.box;
-    double* Fb = LF[bq] + (long long)b * 7 * g.box;
-    atomicAdd(Fa + 5 * g.box + c - sb, -cea0 * lam);  // ea = -F_a[B_t1]
-    atomicAdd(Fa + 5 * g.box + c, -cea1 * lam);
-    atomicAdd(Fb + 6 * g.box + c - sa, ceb0 * lam);  // eb = +F_b[B_t2]
-    atomicAdd(Fb + 6 * g.box + c, ceb1 * lam);
-    cell_emf_adj(e, Wb + c - sa - sb, g.box, cec0 * lam, LWb + c - sa - sb);
-    cell_emf_adj(e, Wb + c - sb, g.box, cec1 * lam, LWb + c - sb);
-    cell_emf_adj(e, Wb + c - sa, g.box, cec2 * lam, LWb + c - sa);
-    cell_emf_adj(e, Wb + c, g.box, cec3 * lam, LWb + c);
+    int n[3] = {li[0], li[1], li[2]};
+    n[a] += da;
+    n[bq] += db;
+    if (!edge_valid(g, e, n)) return 0.0;
+    const long long cn = c + da * stride[a] + db * stride[bq];
+    const double lam = LE[e][cn];
+    if (lam == 0.0) return 0.0;
+    const EdgeCoef k = edge_coef(M[a], M[bq], cn, stride[a], stride[bq]);
+    switch (which) {
+      case 0: return k.cea0 * lam;
+      case 1: return k.cea1 * lam;
+      case 2: return k.ceb0 * lam;
+      case 3: return k.ceb1 * lam;
+      case 4: return k.cec0 * lam;
+      case 5: return k.cec1 * lam;
+      case 6: return k.cec2 * lam;
+      default: return k.cec3 * lam;
+    }
+  };
+  // (i) face EMF components of the fluxes at node c, for faces in the flux region of each sweep
+  for (int d = 0; d < 3; ++d) {
+    bool face = li[d] >= NG;
+    for (int q = 0; q < 3; ++q) face = face && li[q] <= NG + g.mb[q];
+    if (!face) continue;
+    const int e5 = (d + 2) % 3;  // family whose a-faces are d-faces: ea = -F_d[B_t1]
+    const int e6 = (d + 1) % 3;  // family whose b-faces are d-faces: eb = +F_d[B_t2]
+    const double g5 = -(edge_term(e5, 0, 0, 1) + edge_term(e5, 0, 1, 0));
+    const double g6 = edge_term(e6, 0, 0, 3) + edge_term(e6, 1, 0, 2);
+    LF[d][5 * g.box + c] += g5;
+    LF[d][6 * g.box + c] += g6;
   }
+  // (ii) primitives of cell c through its cell EMFs (E = -v x b)
+  const double* Wc = W + (long long)b * 8 * g.box + c;
+  double* LW = lw + (long long)b * 8 * g.box + c;
+  const long long box = g.box;
+  double lam[3];
+  for (int e = 0; e < 3; ++e)
+    lam[e] = edge_term(e, 0, 0, 7) + edge_term(e, 1, 0, 6) + edge_term(e, 0, 1, 5) + edge_term(e, 1, 1, 4);
+  if (lam[0] == 0.0 && lam[1] == 0.0 && lam[2] == 0.0) return;
+  const double vx = Wc[box], vy = Wc[2 * box], vz = Wc[3 * box];
+  const double bx = Wc[5 * box], by = Wc[6 * box], bz = Wc[7 * box];
+  // E_x = vz by - vy bz, E_y = vx bz - vz bx, E_z = vy bx - vx by
+  LW[1 * box] += lam[1] * bz - lam[2] * by;
+  LW[2 * box] += lam[2] * bx - lam[0] * bz;
+  LW[3 * box] += lam[0] * by - lam[1] * bx;
+  LW[5 * box] += lam[2] * vy - lam[1] * vz;
+  LW[6 * box] += lam[0] * vz - lam[2] * vx;
+  LW[7 * box] += lam[1] * vx - lam[0] * vy;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -233,7 +272,7 @@ __device__ __forceinline__ void vl_slope_grad(double qm, double q0, double qp, d
 
 template <int DIR, int REC, int RS>
 __global__ void __launch_bounds__(128) k_adj_flux(Geom g, const double* __restrict__ W, const double* __restrict__ Bn,
-                                                  const double* __restrict__ LF, double* lw, double* lbn) {
+                                                  double* LF, double* LR, double* lbn) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   const int rx = g.mb[0] + (DIR == 0 ? 1 : 2);
   const int ry = g.mb[1] + (DIR == 1 ? 1 : 2);
@@ -249,7 +288,8 @@ __global__ void __launch_bounds__(128) k_adj_flux(Geom g, const double* __restri
   const int k = rem / ry + (DIR == 2 ? NG : NG - 1);
   const long long c = cell_off(g, k, j, i);
   const long long sd = (DIR == 0) ? 1LL : ((DIR == 1) ? (long long)g.sx : (long long)g.sx * g.sy);
-  const double* Fl = LF + (long long)b * 7 * g.box + c;
+  double* Fl = LF + (long long)b * 7 * g.box + c;
+  double* Fr = LR + (long long)b * 7 * g.box + c;
   double lf[7];
   bool any = false;
 #pragma unroll
@@ -257,99 +297,169 @@ __global__ void __launch_bounds__(128) k_adj_flux(Geom g, const double* __restri
     lf[n] = Fl[(long long)n * g.box];
     any = any || lf[n] != 0.0;
   }
-  if (!any) return;
+  if (!any) {  // this face passes nothing to its states
+#pragma unroll
+    for (int n = 0; n < 7; ++n) Fr[(long long)n * g.box] = 0.0;
+    return;
+  }
   const double* Wb = W + (long long)b * 8 * g.box;
   const int var[7] = {0, 1 + DIR, 1 + T1, 1 + T2, 4, 5 + T1, 5 + T2};
-  double wl[7], wr[7], q[4][7];
+  double wl[7], wr[7];
 #pragma unroll
   for (int n = 0; n < 7; ++n) {
     const double* p = Wb + (long long)var[n] * g.box + c;
     if (REC == REC_DC) {
-      q[1][n] = p[-sd];
-      q[2][n] = p[0];
-      wl[n] = q[1][n];
-      wr[n] = q[2][n];
+      wl[n] = p[-sd];
+      wr[n] = p[0];
     } else {
-      q[0][n] = p[-2 * sd];
-      q[1][n] = p[-sd];
-      q[2][n] = p[0];
-      q[3][n] = p[sd];
-      wl[n] = q[1][n] + 0.5 * vl_slope(q[0][n], q[1][n], q[2][n]);
-      wr[n] = q[2][n] - 0.5 * vl_slope(q[1][n], q[2][n], q[3][n]);
+      wl[n] = p[-sd] + 0.5 * vl_slope(p[-2 * sd], p[-sd], p[0]);
+      wr[n] = p[0] - 0.5 * vl_slope(p[-sd], p[0], p[sd]);
     }
   }
   const double bn = Bn[(long long)b * g.box + c];
   // adjoints of the 15 Riemann inputs: lam_x[k] = sum_n lf[n] dF_n/dx_k, by reverse mode
   double lx[15];
 #pragma unroll
-  for (int k = 0; k < 15; ++k) lx[k] = 0.0;
+  for (int q = 0; q < 15; ++q) lx[q] = 0.0;
   if (RS == RS_HLLD)
     flux_hlld_vjp(wl, wr, bn, g.gamma, g.igm1, lf, lx, lx + 7, lx[14]);
   else
     flux_hlle_vjp(wl, wr, bn, g.gamma, g.igm1, lf, lx, lx + 7, lx[14]);
   lbn[(long long)b * g.box + c] += lx[14];
+  // the face's left- and right-state adjoints, for the cells to collect (in place of the flux adjoint)
+#pragma unroll
+  for (int n = 0; n < 7; ++n) {
+    Fl[(long long)n * g.box] = lx[n];
+    Fr[(long long)n * g.box] = lx[7 + n];
+  }
+}
+
+// The cells' share of the face-state adjoints of one sweep, gathered per cell in a fixed order.  With
+// a(f), r(f) the adjoints of the left and right states of face f (between cells f-1 and f):
+//   donor cell:  lam q_i += a(i+1) + r(i)
+//   PLM:         w_L(f) = q_{f-1} + delta_{f-1}/2, w_R(f) = q_f - delta_f/2, so
+//                lam delta_j = a(j+1)/2 - r(j)/2 and
+//                lam q_i += a(i+1) + r(i) + sum_{j=i-1..i+1} lam delta_j d delta_j / d q_i.
+// Faces outside the sweep's flux region contribute nothing.
+template <int DIR, int REC>
+__global__ void __launch_bounds__(128) k_adj_flux_cells(Geom g, const double* __restrict__ W,
+                                                        const double* __restrict__ LA, const double* __restrict__ LR,
+                                                        double* lw) {
+  constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
+  constexpr int H = (REC == REC_DC) ? 1 : 2;  // cells NG-H .. NG+mb-1+H along the sweep
+  const int nx = g.mb[0] + (DIR == 0 ? 2 * H : 2), ny = g.mb[1] + (DIR == 1 ? 2 * H : 2),
+            nz = g.mb[2] + (DIR == 2 ? 2 * H : 2);
+  const long long per = (long long)nx * ny * nz;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per * g.nblk) return;
+  const int b = (int)(t / per);
+  int rem = (int)(t - (long long)b * per);
+  const int li[3] = {rem % nx + (DIR == 0 ? NG - H : NG - 1), (rem / nx) % ny + (DIR == 1 ? NG - H : NG - 1),
+                     rem / (nx * ny) + (DIR == 2 ? NG - H : NG - 1)};
+  const long long c = cell_off(g, li[2], li[1], li[0]);
+  const long long sd = (DIR == 0) ? 1LL : ((DIR == 1) ? (long long)g.sx : (long long)g.sx * g.sy);
+  const int id = li[DIR];
+  auto face_ok = [&](int f) { return f >= NG && f <= NG + g.mb[DIR]; };
+  const long long fb = (long long)b * 7 * g.box + c;
+  const int var[7] = {0, 1 + DIR, 1 + T1, 1 + T2, 4, 5 + T1, 5 + T2};
+  const double* Wb = W + (long long)b * 8 * g.box + c;
   double* LWb = lw + (long long)b * 8 * g.box + c;
 #pragma unroll
   for (int n = 0; n < 7; ++n) {
-    double* L = LWb + (long long)var[n] * g.box;
-    if (REC == REC_DC) {
-      atomicAdd(L - sd, lx[n]);
-      atomicAdd(L, lx[7 + n]);
-    } else {
-      double gm, g0, gp, hm, h0, hp;
-      vl_slope_grad(q[0][n], q[1][n], q[2][n], gm, g0, gp);  // w_L = q_{-1} + delta_{-1}/2
-      vl_slope_grad(q[1][n], q[2][n], q[3][n], hm, h0, hp);  // w_R = q_0 - delta_0/2
-      const double a = lx[n], r = lx[7 + n];
-      atomicAdd(L - 2 * sd, 0.5 * gm * a);
-      atomicAdd(L - sd, a * (1.0 + 0.5 * g0) - 0.5 * hm * r);
-      atomicAdd(L, 0.5 * gp * a + r * (1.0 - 0.5 * h0));
-      atomicAdd(L + sd, -0.5 * hp * r);
+    const long long o = fb + (long long)n * g.box;
+    const double a1 = face_ok(id + 1) ? LA[o + sd] : 0.0;  // a(i+1)
+    const double r0 = face_ok(id) ? LR[o] : 0.0;           // r(i)
+    double lam = a1 + r0;
+    if (REC == REC_PLM) {
+      const double a0 = face_ok(id) ? LA[o] : 0.0;                // a(i)
+      const double a2 = face_ok(id + 2) ? LA[o + 2 * sd] : 0.0;   // a(i+2)
+      const double rm = face_ok(id - 1) ? LR[o - sd] : 0.0;       // r(i-1)
+      const double r1 = face_ok(id + 1) ? LR[o + sd] : 0.0;       // r(i+1)
+      const double* q = Wb + (long long)var[n] * g.box;
+      double dm, d0, dp;
+      // A slope is evaluated only when one of its faces is in the flux region; its stencil then lies in
+      // cells NG-2 .. NG+mb+1 of the box.
+      if (face_ok(id) || face_ok(id - 1)) {  // slope of cell i-1 (q_{i-2}, q_{i-1}, q_i): d/dq_i = dp
+        vl_slope_grad(q[-2 * sd], q[-sd], q[0], dm, d0, dp);
+        lam += (0.5 * a0 - 0.5 * rm) * dp;
+      }
+      if (face_ok(id + 1) || face_ok(id)) {  // slope of cell i: d/dq_i = d0
+        vl_slope_grad(q[-sd], q[0], q[sd], dm, d0, dp);
+        lam += (0.5 * a1 - 0.5 * r0) * d0;
+      }
+      if (face_ok(id + 2) || face_ok(id + 1)) {  // slope of cell i+1 (q_i, q_{i+1}, q_{i+2}): d/dq_i = dm
+        vl_slope_grad(q[0], q[sd], q[2 * sd], dm, d0, dp);
+        lam += (0.5 * a2 - 0.5 * r1) * dm;
+      }
     }
+    LWb[(long long)var[n] * g.box] += lam;
   }
 }
 
 // ------------------------------------------------------------------------------------------------
 // Transpose of cons->prim on every cell (no floor active): lam_U from lam_W, and the cell-centred field's
-// adjoint split half and half onto the two faces of each direction.
+// adjoint split half and half onto the two faces of each direction, gathered per face (lower cell first).
+// One thread per node 0 .. mb+2 NG of the box: the cell at the node (if any) and the three faces there.
 // ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ double prim_field_adj(const Geom& g, const double* Wc, const double* Lc, int d) {
+  // d p / d b_c,d = -(gamma-1) b_c,d, and lam_W carries the cell-centred field directly
+  return Lc[(5 + d) * g.box] - g.gm1 * Lc[4 * g.box] * Wc[(5 + d) * g.box];
+}
+
 __global__ void k_adj_prim(Geom g, const double* W, const double* lw, double* lu, double* lb0, double* lb1, double* lb2) {
-  const int ex = g.mb[0] + 2 * NG, ey = g.mb[1] + 2 * NG, ez = g.mb[2] + 2 * NG;
+  const int ex = g.mb[0] + 2 * NG + 1, ey = g.mb[1] + 2 * NG + 1, ez = g.mb[2] + 2 * NG + 1;
   const long long per = (long long)ex * ey * ez;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= per * g.nblk) return;
   const int b = (int)(t / per);
   int rem = (int)(t - (long long)b * per);
-  const int i = rem % ex;
-  rem /= ex;
-  const int j = rem % ey;
-  const int k = rem / ey;
-  const long long c = cell_off(g, k, j, i);
-  const double* Wc = W + (long long)b * 8 * g.box + c;
-  const double* Lc = lw + (long long)b * 8 * g.box + c;
-  const double lrho = Lc[0], lvx = Lc[g.box], lvy = Lc[2 * g.box], lvz = Lc[3 * g.box], lp = Lc[4 * g.box];
-  const double d = Wc[0], vx = Wc[g.box], vy = Wc[2 * g.box], vz = Wc[3 * g.box];
-  const double bx = Wc[5 * g.box], by = Wc[6 * g.box], bz = Wc[7 * g.box];
-  const double id = 1.0 / d;
-  const double gp = g.gm1 * lp;
-  double* U = lu + (long long)b * 5 * g.box + c;
-  U[0] += lrho - (lvx * vx + lvy * vy + lvz * vz) * id + gp * 0.5 * (vx * vx + vy * vy + vz * vz);
-  U[g.box] += lvx * id - gp * vx;
-  U[2 * g.box] += lvy * id - gp * vy;
-  U[3 * g.box] += lvz * id - gp * vz;
-  U[4 * g.box] += gp;
-  const double lbx = Lc[5 * g.box] - gp * bx, lby = Lc[6 * g.box] - gp * by, lbz = Lc[7 * g.box] - gp * bz;
-  const long long fb = (long long)b * g.box + c;
-  atomicAdd(lb0 + fb, 0.5 * lbx);
-  atomicAdd(lb0 + fb + 1, 0.5 * lbx);
-  atomicAdd(lb1 + fb, 0.5 * lby);
-  atomicAdd(lb1 + fb + g.sx, 0.5 * lby);
-  atomicAdd(lb2 + fb, 0.5 * lbz);
-  atomicAdd(lb2 + fb + (long long)g.sx * g.sy, 0.5 * lbz);
+  const int li[3] = {rem % ex, (rem / ex) % ey, rem / (ex * ey)};
+  const int cmax[3] = {g.mb[0] + 2 * NG, g.mb[1] + 2 * NG, g.mb[2] + 2 * NG};
+  const long long c = cell_off(g, li[2], li[1], li[0]);
+  const long long stride[3] = {1LL, (long long)g.sx, (long long)g.sx * g.sy};
+  const double* Wb = W + (long long)b * 8 * g.box;
+  const double* Lb = lw + (long long)b * 8 * g.box;
+  const bool cell = li[0] < cmax[0] && li[1] < cmax[1] && li[2] < cmax[2];
+  if (cell) {
+    const double* Wc = Wb + c;
+    const double* Lc = Lb + c;
+    const double lrho = Lc[0], lvx = Lc[g.box], lvy = Lc[2 * g.box], lvz = Lc[3 * g.box], lp = Lc[4 * g.box];
+    const double d = Wc[0], vx = Wc[g.box], vy = Wc[2 * g.box], vz = Wc[3 * g.box];
+    const double id = 1.0 / d;
+    const double gp = g.gm1 * lp;
+    double* U = lu + (long long)b * 5 * g.box + c;
+    U[0] += lrho - (lvx * vx + lvy * vy + lvz * vz) * id + gp * 0.5 * (vx * vx + vy * vy + vz * vz);
+    U[g.box] += lvx * id - gp * vx;
+    U[2 * g.box] += lvy * id - gp * vy;
+    U[3 * g.box] += lvz * id - gp * vz;
+    U[4 * g.box] += gp;
+  }
+  double* LB[3] = {lb0, lb1, lb2};
+  for (int d = 0; d < 3; ++d) {
+    bool face = li[d] <= cmax[d];
+    for (int q = 0; q < 3; ++q)
+      if (q != d) face = face && li[q] < cmax[q];
+    if (!face) continue;
+    double x = 0.0;
+    if (li[d] >= 1) x += 0.5 * prim_field_adj(g, Wb + c - stride[d], Lb + c - stride[d], d);  // cell below
+    if (li[d] < cmax[d]) x += 0.5 * prim_field_adj(g, Wb + c, Lb + c, d);                    // cell above
+    LB[d][(long long)b * g.box + c] += x;
+  }
 }
 
 // ------------------------------------------------------------------------------------------------
-// Transpose of the ghost exchange: every ghost cell / ghost face adds its adjoint into the active element
-// it was copied from, then is cleared.
+// Transpose of the ghost exchange.  The exchange copies into each ghost element the element whose index
+// is given, direction by direction, by source_of (periodic wrap or outflow clamp).  For cells the copy map
+// is a product of one-dimensional maps, one per direction, and its transpose is applied one direction at a
+// time.  For the faces of direction fd the map along fd depends on the other two directions: a face on a
+// block's upper surface (index NG+mb along fd, below global face N) is kept when the element is active in
+// the other directions, but is copied from the next block's lower face when it is a ghost in one of them.
+// The map is then the product (map along fd, with that rule) x (the other two, plain), the former applied
+// last, so its transpose along fd comes first.  Pass p treats direction p for cells and direction fd + p
+// for faces of direction fd: every element that is active along that direction (for the rule above)
+// collects, in a fixed order, the adjoints of the elements that copy from it (same indices in the other
+// directions), then those elements are cleared.  After the three passes every ghost adjoint sits in the
+// active element it came from.
 // ------------------------------------------------------------------------------------------------
 __device__ __forceinline__ void source_of_adj(const Geom& g, int q, int gi, bool face, int& blk, int& loc) {
   const int N = g.N[q];
@@ -379,7 +489,97 @@ __device__ __forceinline__ void source_of_adj(const Geom& g, int q, int gi, bool
   }
 }
 
-__global__ void k_adj_ghosts(Geom g, double* lu, double* lb0, double* lb1, double* lb2) {
+// Element kinds: 0 = cell (5 conserved variables), 1 + fd = face of direction fd.
+__device__ __forceinline__ int hi_index(const Geom& g, int kind, int q) {  // largest index along q
+  return g.mb[q] + 2 * NG - ((kind == 1 + q) ? 0 : 1);
+}
+__device__ __forceinline__ int hi_active(const Geom& g, int kind, int q) {  // largest active index along q
+  return NG + g.mb[q] - ((kind == 1 + q) ? 0 : 1);
+}
+
+// Is the element (kind, li) a ghost in a direction other than q?
+__device__ __forceinline__ bool ghost_elsewhere(const Geom& g, int kind, const int* li, int q) {
+  bool gh = false;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    if (r != q) gh = gh || li[r] < NG || li[r] > hi_active(g, kind, r);
+  return gh;
+}
+// Is the element copied along q (a ghost along q, or an upper-surface face that the rule above moves)?
+__device__ __forceinline__ bool moved_along(const Geom& g, int kind, const int* li, int q, int locq) {
+  if (li[q] < NG || li[q] > hi_active(g, kind, q)) return true;
+  return kind == 1 + q && li[q] == NG + g.mb[q] && locq < g.nb[q] - 1 && ghost_elsewhere(g, kind, li, q);
+}
+
+__global__ void k_adj_ghost_gather(Geom g, int pass, double* lu, double* lb0, double* lb1, double* lb2) {
+  const int ex = g.mb[0] + 2 * NG + 1, ey = g.mb[1] + 2 * NG + 1, ez = g.mb[2] + 2 * NG + 1;
+  const long long per = (long long)ex * ey * ez;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per * g.nblk) return;
+  const int b = (int)(t / per);
+  int rem = (int)(t - (long long)b * per);
+  const int li[3] = {rem % ex, (rem / ex) % ey, rem / (ex * ey)};
+  int loc[3];
+  loc_of(g, b, loc);
+  const long long stride[3] = {1LL, (long long)g.sx, (long long)g.sx * g.sy};
+  const long long bstride[3] = {1LL, (long long)g.nb[0], (long long)g.nb[0] * g.nb[1]};
+  const long long c = cell_off(g, li[2], li[1], li[0]);
+  for (int kind = 0; kind < 4; ++kind) {
+    const int q = kind == 0 ? pass : (kind - 1 + pass) % 3;
+    bool ok = true;
+    for (int r = 0; r < 3; ++r) ok = ok && li[r] <= hi_index(g, kind, r);
+    if (!ok || moved_along(g, kind, li, q, loc[q])) continue;  // targets only
+    const bool face = (kind == 1 + q);
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    bool got = false;
+    auto take = [&](long long blk2, long long c2) {
+      if (kind == 0) {
+        const double* U2 = lu + blk2 * 5 * g.box + c2;
+        for (int v = 0; v < 5; ++v) acc[v] += U2[(long long)v * g.box];
+      } else {
+        acc[0] += (kind == 1 ? lb0 : (kind == 2 ? lb1 : lb2))[blk2 * g.box + c2];
+      }
+      got = true;
+    };
+    // an upper-surface face of the block below that is moved onto this lower face
+    if (face && li[q] == NG && loc[q] >= 1 && ghost_elsewhere(g, kind, li, q))
+      take((long long)b - bstride[q], c + (long long)g.mb[q] * stride[q]);
+    // ghosts along q in this block and the blocks within reach along q (distinct, existing) that copy from
+    // here: a ghost of block bq has global index up to bq mb + mb + NG, at most R = 1 + (NG + mb) / mb
+    // blocks away (R <= 4 for mb >= 1)
+    const int R = 1 + (NG + g.mb[q]) / g.mb[q];
+    int seen[9];
+    int nseen = 0;
+    for (int dl = -R; dl <= R; ++dl) {
+      int bq = loc[q] + dl;
+      if (bq < 0 || bq >= g.nb[q]) {
+        if (g.bc[dl < 0 ? 2 * q : 2 * q + 1] != BC_PERIODIC) continue;
+        bq = ((bq % g.nb[q]) + g.nb[q]) % g.nb[q];
+      }
+      bool dup = false;
+      for (int k = 0; k < nseen; ++k) dup = dup || seen[k] == bq;
+      if (dup) continue;
+      seen[nseen++] = bq;
+      const int hi = hi_index(g, kind, q), ha = hi_active(g, kind, q);
+      for (int gl = 0; gl <= hi; ++gl) {
+        if (gl >= NG && gl <= ha) continue;  // not a ghost along q
+        int sblk, sloc;
+        source_of_adj(g, q, bq * g.mb[q] + gl - NG, face, sblk, sloc);
+        if (sblk != loc[q] || sloc != li[q]) continue;
+        take((long long)b + (long long)(bq - loc[q]) * bstride[q], c + (long long)(gl - li[q]) * stride[q]);
+      }
+    }
+    if (!got) continue;
+    if (kind == 0) {
+      double* U = lu + (long long)b * 5 * g.box + c;
+      for (int v = 0; v < 5; ++v) U[(long long)v * g.box] += acc[v];
+    } else {
+      (kind == 1 ? lb0 : (kind == 2 ? lb1 : lb2))[(long long)b * g.box + c] += acc[0];
+    }
+  }
+}
+
+__global__ void k_adj_ghost_clear(Geom g, int pass, double* lu, double* lb0, double* lb1, double* lb2) {
   const int ex = g.mb[0] + 2 * NG + 1, ey = g.mb[1] + 2 * NG + 1, ez = g.mb[2] + 2 * NG + 1;
   const long long per = (long long)ex * ey * ez;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -390,71 +590,81 @@ __global__ void k_adj_ghosts(Geom g, double* lu, double* lb0, double* lb1, doubl
   int loc[3];
   loc_of(g, b, loc);
   const long long c = cell_off(g, li[2], li[1], li[0]);
-  const int cmax[3] = {g.mb[0] + 2 * NG, g.mb[1] + 2 * NG, g.mb[2] + 2 * NG};
-  if (li[0] < cmax[0] && li[1] < cmax[1] && li[2] < cmax[2]) {
-    bool ghost = false;
-    for (int q = 0; q < 3; ++q) ghost |= (li[q] < NG || li[q] >= NG + g.mb[q]);
-    if (ghost) {
-      int sb[3], sl[3];
-      for (int q = 0; q < 3; ++q) source_of_adj(g, q, loc[q] * g.mb[q] + li[q] - NG, false, sb[q], sl[q]);
-      const int src = (sb[2] * g.nb[1] + sb[1]) * g.nb[0] + sb[0];
-      double* Ud = lu + (long long)b * 5 * g.box + c;
-      double* Us = lu + (long long)src * 5 * g.box + cell_off(g, sl[2], sl[1], sl[0]);
-      for (int v = 0; v < 5; ++v) {
-        const double x = Ud[(long long)v * g.box];
-        if (x != 0.0) atomicAdd(Us + (long long)v * g.box, x);
-        Ud[(long long)v * g.box] = 0.0;
-      }
+  for (int kind = 0; kind < 4; ++kind) {
+    const int q = kind == 0 ? pass : (kind - 1 + pass) % 3;
+    bool ok = true;
+    for (int r = 0; r < 3; ++r) ok = ok && li[r] <= hi_index(g, kind, r);
+    if (!ok || !moved_along(g, kind, li, q, loc[q])) continue;
+    if (kind == 0) {
+      double* U = lu + (long long)b * 5 * g.box + c;
+      for (int v = 0; v < 5; ++v) U[(long long)v * g.box] = 0.0;
+    } else {
+      (kind == 1 ? lb0 : (kind == 2 ? lb1 : lb2))[(long long)b * g.box + c] = 0.0;
     }
-  }
-  double* Bf[3] = {lb0, lb1, lb2};
-  for (int fd = 0; fd < 3; ++fd) {
-    bool valid = true, ghost = false;
-    for (int q = 0; q < 3; ++q) {
-      const int hi_valid = (q == fd) ? cmax[q] : cmax[q] - 1;
-      const int hi_active = (q == fd) ? NG + g.mb[q] : NG + g.mb[q] - 1;
-      valid &= li[q] <= hi_valid;
-      ghost |= (li[q] < NG || li[q] > hi_active);
-    }
-    if (!valid || !ghost) continue;
-    int sb[3], sl[3];
-    for (int q = 0; q < 3; ++q) source_of_adj(g, q, loc[q] * g.mb[q] + li[q] - NG, q == fd, sb[q], sl[q]);
-    const int src = (sb[2] * g.nb[1] + sb[1]) * g.nb[0] + sb[0];
-    double* d = Bf[fd] + (long long)b * g.box + c;
-    const double x = *d;
-    if (x != 0.0) atomicAdd(Bf[fd] + (long long)src * g.box + cell_off(g, sl[2], sl[1], sl[0]), x);
-    *d = 0.0;
   }
 }
 
 // ------------------------------------------------------------------------------------------------
-// Block layout -> input adjoint (global layout): cells one to one; every active copy of a face adds into
-// its global entry (interior block boundaries have two copies).  The outputs must be zero on entry.
+// Block layout -> input adjoint (global layout), one thread per global element: cells one to one; a face
+// sums its block copies in a fixed order (a face on the boundary between blocks k-1 and k has two: the
+// upper face of block k-1, then the lower face of block k).  Writes every output element.
 // ------------------------------------------------------------------------------------------------
 __global__ void k_adj_gather_in(Geom g, const double* lu, const double* lb0, const double* lb1, const double* lb2,
                                 double* gu, double* gb1, double* gb2, double* gb3) {
-  const int ex = g.mb[0] + 1, ey = g.mb[1] + 1, ez = g.mb[2] + 1;
-  const long long per = (long long)ex * ey * ez;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= per * g.nblk) return;
-  const int b = (int)(t / per);
-  int rem = (int)(t - (long long)b * per);
-  const int li[3] = {rem % ex, (rem / ex) % ey, rem / (ex * ey)};
-  int loc[3];
-  loc_of(g, b, loc);
-  int gi[3];
-  for (int q = 0; q < 3; ++q) gi[q] = loc[q] * g.mb[q] + li[q];
   const int NX = g.N[0], NY = g.N[1], NZ = g.N[2];
-  const bool in[3] = {li[0] < g.mb[0], li[1] < g.mb[1], li[2] < g.mb[2]};
-  const long long o = (long long)b * g.box + cell_off(g, li[2] + NG, li[1] + NG, li[0] + NG);
-  if (in[1] && in[2]) atomicAdd(gb1 + ((long long)gi[2] * NY + gi[1]) * (NX + 1) + gi[0], lb0[o]);
-  if (in[0] && in[2]) atomicAdd(gb2 + ((long long)gi[2] * (NY + 1) + gi[1]) * NX + gi[0], lb1[o]);
-  if (in[0] && in[1]) atomicAdd(gb3 + ((long long)gi[2] * NY + gi[1]) * NX + gi[0], lb2[o]);
+  const long long ex = NX + 1, ey = NY + 1, ez = NZ + 1;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ex * ey * ez) return;
+  const int gi[3] = {(int)(t % ex), (int)((t / ex) % ey), (int)(t / (ex * ey))};
+  const int N[3] = {NX, NY, NZ};
+  // block coordinate and local index of a global cell index along q
+  auto cell_loc = [&](int q, int m, int& blk, int& l) {
+    blk = m / g.mb[q];
+    l = m - blk * g.mb[q] + NG;
+  };
+  const bool in[3] = {gi[0] < NX, gi[1] < NY, gi[2] < NZ};
   if (in[0] && in[1] && in[2]) {
+    int bb[3], l[3];
+    for (int q = 0; q < 3; ++q) cell_loc(q, gi[q], bb[q], l[q]);
+    const long long blk = ((long long)bb[2] * g.nb[1] + bb[1]) * g.nb[0] + bb[0];
+    const long long cu = blk * 5 * g.box + cell_off(g, l[2], l[1], l[0]);
     const long long n = (long long)NX * NY * NZ;
     const long long gc = ((long long)gi[2] * NY + gi[1]) * NX + gi[0];
-    const long long cu = (long long)b * 5 * g.box + cell_off(g, li[2] + NG, li[1] + NG, li[0] + NG);
     for (int v = 0; v < 5; ++v) gu[v * n + gc] = lu[cu + (long long)v * g.box];
+  }
+  const double* LB[3] = {lb0, lb1, lb2};
+  double* GB[3] = {gb1, gb2, gb3};
+  for (int fd = 0; fd < 3; ++fd) {
+    bool ok = true;
+    for (int q = 0; q < 3; ++q)
+      if (q != fd) ok = ok && in[q];
+    if (!ok) continue;
+    int bb[3], l[3];
+    for (int q = 0; q < 3; ++q)
+      if (q != fd) cell_loc(q, gi[q], bb[q], l[q]);
+    double x = 0.0;
+    const int m = gi[fd];
+    // upper face of the block below (faces k*mb, 0 < k <= nb)
+    if (m > 0 && m % g.mb[fd] == 0) {
+      bb[fd] = m / g.mb[fd] - 1;
+      l[fd] = NG + g.mb[fd];
+      const long long blk = ((long long)bb[2] * g.nb[1] + bb[1]) * g.nb[0] + bb[0];
+      x += LB[fd][blk * g.box + cell_off(g, l[2], l[1], l[0])];
+    }
+    // the face as a lower or interior face of its own block (all but global face N)
+    if (m < N[fd]) {
+      cell_loc(fd, m, bb[fd], l[fd]);
+      const long long blk = ((long long)bb[2] * g.nb[1] + bb[1]) * g.nb[0] + bb[0];
+      x += LB[fd][blk * g.box + cell_off(g, l[2], l[1], l[0])];
+    }
+    long long o;
+    if (fd == 0)
+      o = ((long long)gi[2] * NY + gi[1]) * (NX + 1) + gi[0];
+    else if (fd == 1)
+      o = ((long long)gi[2] * (NY + 1) + gi[1]) * NX + gi[0];
+    else
+      o = ((long long)gi[2] * NY + gi[1]) * NX + gi[0];
+    GB[fd][o] = x;
   }
 }
 
@@ -527,7 +737,7 @@ cudaError_t adj_update(const Geom& g, const AdjArrays& j, int out_reg, int base_
 
 cudaError_t adj_ct(const Geom& g, const AdjArrays& j, const double* W, const double* const* mflux, long long mstride,
                    cudaStream_t st) {
-  k_adj_ct<<<grid_of(nodes_act(g), AT), AT, 0, st>>>(g, W, mflux[0], mflux[1], mflux[2], mstride, j.le[0], j.le[1],
+  k_adj_ct<<<grid_of(nodes_ext(g), AT), AT, 0, st>>>(g, W, mflux[0], mflux[1], mflux[2], mstride, j.le[0], j.le[1],
                                                      j.le[2], j.lf[0], j.lf[1], j.lf[2], j.lw);
   return cudaGetLastError();
 }
@@ -537,7 +747,13 @@ static cudaError_t adj_flux_one(const Geom& g, const AdjArrays& j, const double*
                                 cudaStream_t st) {
   long long n = g.nblk;
   for (int q = 0; q < 3; ++q) n *= g.mb[q] + (q == DIR ? 1 : 2);
-  k_adj_flux<DIR, REC, RS><<<grid_of(n, 128), 128, 0, st>>>(g, W, Bn, j.lf[DIR], j.lw, lbn);
+  k_adj_flux<DIR, REC, RS><<<grid_of(n, 128), 128, 0, st>>>(g, W, Bn, j.lf[DIR], j.lr, lbn);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  constexpr int H = (REC == REC_DC) ? 1 : 2;
+  long long nc = g.nblk;
+  for (int q = 0; q < 3; ++q) nc *= g.mb[q] + (q == DIR ? 2 * H : 2);
+  k_adj_flux_cells<DIR, REC><<<grid_of(nc, 128), 128, 0, st>>>(g, W, j.lf[DIR], j.lr, j.lw);
   return cudaGetLastError();
 }
 
@@ -561,7 +777,8 @@ cudaError_t adj_fluxes(const Geom& g, const AdjArrays& j, int recon, int riemann
 }
 
 cudaError_t adj_prim(const Geom& g, const AdjArrays& j, const double* W, int lam_reg, cudaStream_t st) {
-  const long long n = (long long)(g.mb[0] + 2 * NG) * (g.mb[1] + 2 * NG) * (g.mb[2] + 2 * NG) * g.nblk;
+  // one thread per node 0 .. mb + 2 NG (cells and their faces)
+  const long long n = (long long)(g.mb[0] + 2 * NG + 1) * (g.mb[1] + 2 * NG + 1) * (g.mb[2] + 2 * NG + 1) * g.nblk;
   k_adj_prim<<<grid_of(n, AT), AT, 0, st>>>(g, W, j.lw, j.lu[lam_reg], j.lb[lam_reg][0], j.lb[lam_reg][1],
                                             j.lb[lam_reg][2]);
   return cudaGetLastError();
@@ -569,13 +786,23 @@ cudaError_t adj_prim(const Geom& g, const AdjArrays& j, const double* W, int lam
 
 cudaError_t adj_ghosts(const Geom& g, const AdjArrays& j, int lam_reg, cudaStream_t st) {
   const long long n = (long long)(g.mb[0] + 2 * NG + 1) * (g.mb[1] + 2 * NG + 1) * (g.mb[2] + 2 * NG + 1) * g.nblk;
-  k_adj_ghosts<<<grid_of(n, AT), AT, 0, st>>>(g, j.lu[lam_reg], j.lb[lam_reg][0], j.lb[lam_reg][1], j.lb[lam_reg][2]);
-  return cudaGetLastError();
+  for (int pass = 0; pass < 3; ++pass) {
+    k_adj_ghost_gather<<<grid_of(n, AT), AT, 0, st>>>(g, pass, j.lu[lam_reg], j.lb[lam_reg][0], j.lb[lam_reg][1],
+                                                      j.lb[lam_reg][2]);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_adj_ghost_clear<<<grid_of(n, AT), AT, 0, st>>>(g, pass, j.lu[lam_reg], j.lb[lam_reg][0], j.lb[lam_reg][1],
+                                                     j.lb[lam_reg][2]);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t adj_gather_in(const Geom& g, const AdjArrays& j, double* gu, double* gb1, double* gb2, double* gb3,
                           cudaStream_t st) {
-  k_adj_gather_in<<<grid_of(nodes_act(g), AT), AT, 0, st>>>(g, j.lu[0], j.lb[0][0], j.lb[0][1], j.lb[0][2], gu, gb1,
+  const long long n = (long long)(g.N[0] + 1) * (g.N[1] + 1) * (g.N[2] + 1);
+  k_adj_gather_in<<<grid_of(n, AT), AT, 0, st>>>(g, j.lu[0], j.lb[0][0], j.lb[0][1], j.lb[0][2], gu, gb1,
                                                             gb2, gb3);
   return cudaGetLastError();
 }

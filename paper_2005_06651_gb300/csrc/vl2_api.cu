@@ -181,7 +181,7 @@ struct Plan {
   size_t stage_elems;
   size_t off_adj;  // start of the adjoint arrays (59 FP64 arrays per block) when requested
 };
-constexpr int ADJ_ARRAYS = 10 + 6 + 8 + 21 + 3 + 8 + 3;
+constexpr int ADJ_ARRAYS = 10 + 6 + 8 + 21 + 7 + 3 + 8 + 3;
 
 Plan make_plan(const Geom& g, int precision, int adjoint) {
   Plan pl;
@@ -373,6 +373,7 @@ vl2_status vl2_mesh_create(const vl2_params* params, void* workspace, size_t byt
     }
     m->adj.lw = take(8);
     for (int d = 0; d < 3; ++d) m->adj.lf[d] = take(7);
+    m->adj.lr = take(7);
     for (int d = 0; d < 3; ++d) m->adj.le[d] = take(1);
     m->adj.w0 = take(8);
     for (int d = 0; d < 3; ++d) m->adj.m1[d] = take(1);
@@ -566,13 +567,8 @@ vl2_status vl2_step_vjp(vl2_mesh* m, double dt, const double* lam_u, const doubl
   VL2_CHECK(m, vl2::adj_fluxes(g, j, vl2::REC_DC, m->p.riemann, j.w0, bn0, 0, st));
   VL2_CHECK(m, vl2::adj_prim(g, j, j.w0, 0, st));
   VL2_CHECK(m, vl2::adj_ghosts(g, j, 0, st));
-  const long long nc = ncells(g);
-  VL2_CHECK(m, cudaMemsetAsync(out_b1, 0, (size_t)(g.N[0] + 1) * g.N[1] * g.N[2] * sizeof(double), st));
-  VL2_CHECK(m, cudaMemsetAsync(out_b2, 0, (size_t)g.N[0] * (g.N[1] + 1) * g.N[2] * sizeof(double), st));
-  VL2_CHECK(m, cudaMemsetAsync(out_b3, 0, (size_t)g.N[0] * g.N[1] * (g.N[2] + 1) * sizeof(double), st));
-  (void)nc;
   VL2_CHECK(m, vl2::adj_gather_in(g, j, out_u, out_b1, out_b2, out_b3, st));
-  m->launches += 20;
+  m->launches += 32;  // scatter, 2 x (update, CT, 3 x 2 flux, prim, 3 x 2 ghost passes), gather
   return VL2_OK;
 }
 

@@ -133,7 +133,8 @@ struct AdjArrays {
   double* lu[2];     // adjoints of the two conserved registers: [nblk][5][box]
   double* lb[2][3];  // adjoints of the two face-field registers
   double* lw;        // adjoint of the primitives: [nblk][8][box]
-  double* lf[3];     // adjoints of the face fluxes: [nblk][7][box]
+  double* lf[3];     // adjoints of the face fluxes: [nblk][7][box]; then the left-state adjoints of the faces
+  double* lr;        // right-state adjoints of the faces of the sweep being transposed: [nblk][7][box]
   double* le[3];     // adjoints of the corner EMFs
   double* w0;        // predictor primitives kept from the forward recompute: [nblk][8][box]
   double* m1[3];     // predictor face mass fluxes (upwind choices of its CT): [nblk][box]
