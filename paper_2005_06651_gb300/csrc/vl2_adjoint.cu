@@ -259,7 +259,8 @@ __device__ __forceinline__ void vl_slope_grad(double qm, double q0, double qp, d
   const double dl = q0 - qm, dr = qp - q0;
   if (gt0(dl * dr)) {
     const double s = dl + dr;
-    const double is2 = 1.0 / (s * s);
+    const double s2 = s * s;  // > 0 here (dl and dr have the same sign)
+    const double is2 = s2 >= 2.2250738585072014e-308 ? rcp_nr(s2) : 1.0 / s2;  // rcp_nr takes normal numbers
     const double gdl = 2.0 * dr * dr * is2;  // d delta / d dl
     const double gdr = 2.0 * dl * dl * is2;  // d delta / d dr
     dqm = -gdl;
@@ -530,6 +531,10 @@ __global__ void k_adj_ghost_gather(Geom g, int pass, double* lu, double* lb0, do
     for (int r = 0; r < 3; ++r) ok = ok && li[r] <= hi_index(g, kind, r);
     if (!ok || moved_along(g, kind, li, q, loc[q])) continue;  // targets only
     const bool face = (kind == 1 + q);
+    // only elements within NG + 1 of a block edge along q are the source of a ghost (a neighbour's ghost
+    // layer, a periodic wrap or an outflow clamp reaches no further; small blocks are near an edge
+    // everywhere)
+    if (li[q] - NG > NG + 1 && hi_active(g, kind, q) - li[q] > NG + 1) continue;
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     bool got = false;
     auto take = [&](long long blk2, long long c2) {
