@@ -447,10 +447,33 @@ def adjoint_form(args, dev, stream, vl2, inputs):
                          "checks": fd_checks, "max_rel_err": max(c["rel_err"] for c in fd_checks)}}
 
 
+def integrators_form(args, dev, stream, vl2, inputs):
+    """The other 2S integrators of Sec. 3.2.3 on the plain workload (256^3 vortex, 512 MeshBlocks of 32^3,
+    FP64, HLLD): RK2 (SSPRK(2,2)) and RK3 (SSPRK(3,3)) with PLM in every stage, zone-cycles/s next to VL2's
+    (the bench line).  A cycle has 2 or 3 PLM stages against VL2's donor-cell + PLM."""
+    import torch
+
+    prob = inputs.orszag_tang(n=args.n, mb=args.mb, seed=2005)
+    out = {"config": {"workload": "orszag_tang_3d_%d^3_%dx%d^3_blocks_plm_hlld_ct_fp64" % (
+        args.n, (args.n // args.mb) ** 3, args.mb), "steps": args.rk_steps, "dtype": "f64"}}
+    for name, integ in (("rk2", vl2.RK2), ("rk3", vl2.RK3)):
+        m = vl2.Mesh.from_problem(prob, device=dev, stream=stream, integrator=integ)
+        for _ in range(2):
+            m.step(m.new_dt())
+        torch.cuda.synchronize(dev)
+        ms, _ = timed_steps(m, args.rk_steps, stream)
+        out[name] = {"value": prob.ncells * args.rk_steps / (ms / 1e3), "unit": UNIT,
+                     "ms_per_step": ms / args.rk_steps, "floor_events": m.floor_count()}
+        m.close()
+        del m
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_forms(args, dev, stream, vl2, inputs):
     import torch
 
-    fns = {"mixed": mixed_form, "batched": batched_form, "adjoint": adjoint_form}
+    fns = {"mixed": mixed_form, "batched": batched_form, "adjoint": adjoint_form, "integrators": integrators_form}
     forms = {}
     for name in [f for f in args.forms.split(",") if f]:
         if name not in fns:
@@ -489,7 +512,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--adj-n", type=int, default=64, help="grid of the differentiation form")
     ap.add_argument("--adj-steps", type=int, default=100)
-    ap.add_argument("--forms", default="mixed,batched,adjoint", help="comma list of the forms to run")
+    ap.add_argument("--forms", default="mixed,batched,adjoint,integrators", help="comma list of the forms to run")
+    ap.add_argument("--rk-steps", type=int, default=10, help="timed cycles of each RK integrator")
     ap.add_argument("--forms-only", action="store_true",
                     help="run only the forms (a profiling aid: prints {'forms': ...}, not the bench line)")
     args = ap.parse_args()

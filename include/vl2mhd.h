@@ -51,6 +51,10 @@ enum { VL2_PERIODIC = 0, VL2_OUTFLOW = 1 };/* per-face boundary condition */
 enum { VL2_FP64 = 0, VL2_MIXED = 1 };      /* arithmetic of reconstruction, fluxes and EMFs */
 enum { VL2_HOST = 0, VL2_DEVICE = 1 };     /* where a caller buffer lives */
 enum { VL2_DC = 0, VL2_PLM = 1 };          /* reconstruction, Sec. 3.2.1 */
+/* time integrators of the 2S family (Sec. 3.2.3, eq. rk-2s and the coefficient list after it):
+ * VL2 (default): donor-cell predictor with beta = 1/2, PLM corrector with beta = 1;
+ * RK1: forward Euler with donor-cell fluxes; RK2 (SSPRK(2,2)) and RK3 (SSPRK(3,3)): PLM in every stage. */
+enum { VL2_INT_VL2 = 0, VL2_INT_RK1 = 1, VL2_INT_RK2 = 2, VL2_INT_RK3 = 3 };
 
 typedef struct vl2_params {
   int nx[3];          /* global active cells (x, y, z); each a multiple of mb[d] */
@@ -68,6 +72,7 @@ typedef struct vl2_params {
   double dfloor, pfloor; /* density / pressure floors of cons->prim (positive normal numbers, >= DBL_MIN) */
   void* stream;       /* cudaStream_t for all device work of this mesh (may be NULL) */
   int adjoint;        /* 1: also reserve the arrays of vl2_step_vjp (VL2_FP64 only); 0: forward only */
+  int integrator;     /* VL2_INT_VL2 (0, the default for a zero-initialised struct), VL2_INT_RK1, _RK2, _RK3 */
 } vl2_params;
 
 typedef struct vl2_mesh vl2_mesh;
@@ -128,10 +133,12 @@ vl2_status vl2_set_cons(vl2_mesh* mesh, const double* u, const double* b1, const
  * Faces on a block's own surface are active and are not overwritten.  Errors: VL2_E_CUDA. */
 vl2_status vl2_fill_ghosts(vl2_mesh* mesh);
 
-/* One VL2 cycle with step dt (Sec. 3.2.3): predictor U* = U^n + (dt/2) L_DC(U^n), corrector
- * U^{n+1} = U^n + dt L_PLM(U*), where L = -div F for U and -curl E (upwind CT corner EMFs) for the
- * face field; cons->prim and ghost exchange between the stages and after the corrector.  Ghosts are
- * valid on return.  dt must be finite and > 0.  Work is only enqueued.  Errors: VL2_E_ARG, VL2_E_CUDA. */
+/* One cycle with step dt (Sec. 3.2.3) of the mesh's integrator.  VL2: predictor U* = U^n + (dt/2) L_DC(U^n),
+ * corrector U^{n+1} = U^n + dt L_PLM(U*), where L = -div F for U and -curl E (upwind CT corner EMFs) for
+ * the face field.  RK1/RK2/RK3: eq. rk-2s with u^(0) = U^n, u^(1) = 0, then per stage s
+ * u^(1) += delta_s u^(0), u^(0) = gamma_s0 u^(0) + gamma_s1 u^(1) + beta_s dt L(u^(0)), with the
+ * coefficients the paper lists.  cons->prim and ghost exchange follow every stage.  Ghosts are valid on
+ * return.  dt must be finite and > 0.  Work is only enqueued.  Errors: VL2_E_ARG, VL2_E_CUDA. */
 vl2_status vl2_step(vl2_mesh* mesh, double dt);
 
 /* CFL time step of the current state (Sec. 2.1.7, 3.2.3): dt = cfl * min over active cells and

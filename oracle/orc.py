@@ -63,6 +63,7 @@ def lib():
         L.orc_divb_norm.argtypes = [ctypes.c_void_p]
         L.orc_divb_norm.restype = ctypes.c_double
         L.orc_totals.argtypes = [ctypes.c_void_p, dp]
+        L.orc_set_cons.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
         L.orc_riemann.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double, dp]
         L.orc_riemann_jacobian.argtypes = [ctypes.c_int, ctypes.c_longlong, dp, dp, dp, ctypes.c_double, dp]
         L.orc_physical_flux.argtypes = [dp, ctypes.c_double, ctypes.c_double, dp, dp]
@@ -217,6 +218,10 @@ class Mesh:
     def set_prims(self, w, b1, b2, b3):
         arrs = [_c64(a) for a in (w, b1, b2, b3)]
         lib().orc_set_prims(self._h, *[_dp(a) for a in arrs])
+
+    def set_cons(self, u, b1, b2, b3):
+        arrs = [_c64(a) for a in (u, b1, b2, b3)]
+        lib().orc_set_cons(self._h, *[_dp(a) for a in arrs])
 
     def get_cons(self):
         u = np.zeros((5,) + self.shape)

@@ -1064,6 +1064,11 @@ void orc_get_cons(void* m, double* u, double* b1, double* b2, double* b3) {
   orc::get_cons(*static_cast<Mesh<double>*>(m), u, b1, b2, b3);
 }
 
+/* Set the conserved state (global arrays, active region) and exchange ghosts. */
+void orc_set_cons(void* m, const double* u, const double* b1, const double* b2, const double* b3) {
+  orc::set_cons(*static_cast<Mesh<double>*>(m), u, nullptr, b1, nullptr, b2, nullptr, b3, nullptr);
+}
+
 /* cons -> prim of the current state on the active region: w[8][nz][ny][nx] (rho, v, p, b_c) */
 void orc_get_prims(void* m, double* w) {
   Mesh<double>& M = *static_cast<Mesh<double>*>(m);

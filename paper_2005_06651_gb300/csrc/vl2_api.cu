@@ -136,6 +136,14 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
     msg = "adjoint must be 0 or 1, and 1 needs VL2_FP64";
     return VL2_E_ARG;
   }
+  if (p->integrator < VL2_INT_VL2 || p->integrator > VL2_INT_RK3) {
+    msg = "integrator must be VL2_INT_VL2, VL2_INT_RK1, VL2_INT_RK2 or VL2_INT_RK3";
+    return VL2_E_ARG;
+  }
+  if (p->adjoint && p->integrator != VL2_INT_VL2) {
+    msg = "the adjoint (params.adjoint = 1) is written for the VL2 integrator";
+    return VL2_E_ARG;
+  }
   for (int d = 0; d < 3; ++d) {
     const int lo = p->bc[2 * d], hi = p->bc[2 * d + 1];
     if ((lo != VL2_PERIODIC && lo != VL2_OUTFLOW) || (hi != VL2_PERIODIC && hi != VL2_OUTFLOW) ||
@@ -302,9 +310,10 @@ cudaError_t k_fluxes(vl2_mesh* m, int reg, int recon) {
 cudaError_t k_emfs(vl2_mesh* m) {
   return timed(m, VL2_K_EMF, nodes(m->g), [&] { return vl2::launch_emfs(m->view(), nullptr, m->st); });
 }
-cudaError_t k_update(vl2_mesh* m, int base, int out, double h) {
-  return timed(m, VL2_K_UPDATE, nodes(m->g),
-               [&] { return vl2::launch_update(m->view(), nullptr, base, out, h, nullptr, 0.0, m->st); });
+cudaError_t k_update(vl2_mesh* m, int base, int out, double h, double g_base = 1.0, double g_other = 0.0) {
+  return timed(m, VL2_K_UPDATE, nodes(m->g), [&] {
+    return vl2::launch_update(m->view(), nullptr, base, out, h, nullptr, 0.0, m->st, g_base, g_other);
+  });
 }
 
 vl2_status ensure_prims(vl2_mesh* m) {
@@ -598,12 +607,50 @@ vl2_status vl2_fill_ghosts(vl2_mesh* m) {
   return VL2_OK;
 }
 
+namespace {
+// One cycle of RK1 / RK2 / RK3 in the 2S form (Sec. 3.2.3, eq. rk-2s): u^(0) = U^n in register 0,
+// u^(1) in register 1.  u^(1) = 0 + delta_0 u^(0) = U^n before the first stage (delta_s = 0 after it);
+// each stage s then forms the fluxes of u^(0) (donor cell for RK1, PLM otherwise) and updates
+// u^(0) = gamma_s0 u^(0) + gamma_s1 u^(1) + beta_s dt L(u^(0)) in place, followed by the ghost exchange and
+// cons->prim (the last one with the CFL reduction).
+struct RkStage {
+  double g0, g1, beta;
+};
+vl2_status step_rk(vl2_mesh* m, double dt) {
+  static const RkStage rk1[1] = {{0.0, 1.0, 1.0}};
+  static const RkStage rk2[2] = {{0.0, 1.0, 1.0}, {0.5, 0.5, 0.5}};
+  static const RkStage rk3[3] = {{0.0, 1.0, 1.0}, {0.25, 0.75, 0.25}, {2.0 / 3.0, 1.0 / 3.0, 2.0 / 3.0}};
+  const RkStage* st = m->p.integrator == VL2_INT_RK1 ? rk1 : (m->p.integrator == VL2_INT_RK2 ? rk2 : rk3);
+  const int ns = m->p.integrator == VL2_INT_RK1 ? 1 : (m->p.integrator == VL2_INT_RK2 ? 2 : 3);
+  const int recon = m->p.integrator == VL2_INT_RK1 ? VL2_DC : VL2_PLM;
+  const Geom& g = m->g;
+  const size_t per = (size_t)g.nblk * g.box * sizeof(double);
+  // u^(1) = U^n (every element, so that register 1 is a complete copy)
+  VL2_CHECK(m, cudaMemcpyAsync(m->a.u[1], m->a.u[0], 5 * per, cudaMemcpyDeviceToDevice, m->st));
+  for (int d = 0; d < 3; ++d)
+    VL2_CHECK(m, cudaMemcpyAsync(m->a.b[1][d], m->a.b[0][d], per, cudaMemcpyDeviceToDevice, m->st));
+  for (int k = 0; k < ns; ++k) {
+    if (k > 0) VL2_CHECK(m, k_prim(m, 0, false));
+    VL2_CHECK(m, k_fluxes(m, 0, recon));
+    VL2_CHECK(m, k_emfs(m));
+    VL2_CHECK(m, k_update(m, 0, 0, st[k].beta * dt, st[k].g0, st[k].g1));
+    VL2_CHECK(m, k_ghosts(m, 0));
+  }
+  VL2_CHECK(m, cudaMemsetAsync(m->a.scal + vl2::SC_MAXRATE, 0, sizeof(unsigned long long), m->st));
+  VL2_CHECK(m, k_prim(m, 0, true));
+  m->w_valid = true;
+  m->dt_pending = true;
+  return VL2_OK;
+}
+}  // namespace
+
 vl2_status vl2_step(vl2_mesh* m, double dt) {
   if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
   if (!m->initialized) return fail(m, VL2_E_STATE, "vl2_set_prims has not been called");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(m, VL2_E_ARG, "dt must be finite and positive");
   vl2_status s = ensure_prims(m);
   if (s != VL2_OK) return s;
+  if (m->p.integrator != VL2_INT_VL2) return step_rk(m, dt);
   // predictor: U* = U^n + (dt/2) L_DC(U^n) into register 1 (Sec. 3.2.3, VL2)
   VL2_CHECK(m, k_fluxes(m, 0, VL2_DC));
   VL2_CHECK(m, k_emfs(m));
@@ -896,6 +943,10 @@ vl2_status batch_check(vl2_mesh* const* meshes, int n, std::string& msg) {
   for (int q = 0; q < n; ++q) {
     if (!meshes[q]) {
       msg = "NULL mesh in the batch";
+      return VL2_E_ARG;
+    }
+    if (meshes[q]->p.integrator != VL2_INT_VL2) {
+      msg = "the batched form runs the VL2 integrator";
       return VL2_E_ARG;
     }
     if (meshes[q]->p.riemann != meshes[0]->p.riemann || meshes[q]->p.precision != meshes[0]->p.precision) {

@@ -112,7 +112,7 @@ cudaError_t launch_flux(const MeshView& v, const Dispatch* d, int reg, int recon
                         const FluxShape& fs, int max_mb, cudaStream_t st);
 cudaError_t launch_emfs(const MeshView& v, const Dispatch* d, cudaStream_t st);
 cudaError_t launch_update(const MeshView& v, const Dispatch* d, int base_reg, int out_reg, double h,
-                          const double* dtbox, double beta, cudaStream_t st);
+                          const double* dtbox, double beta, cudaStream_t st, double g_base = 1.0, double g_other = 0.0);
 // per-box dt from the CFL rates the last prim reduced: dt[box] = cfl / rate, rate reset to 0
 cudaError_t launch_batch_dt(const MeshView* views, int nbox, const double* cfl, double* dt, cudaStream_t st);
 cudaError_t prepare_kernel_attributes();

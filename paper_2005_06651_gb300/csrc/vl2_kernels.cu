@@ -369,20 +369,25 @@ cudaError_t launch_emfs(const MeshView& v, const Dispatch* d, cudaStream_t st) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Register update of one stage (Sec. 3.2.3, eq. rk-2s with gamma_s = {0, 1}):
-//   U_out = U_base + h L,  L = -[(F_x(i+1/2) - F_x(i-1/2))/dx + (F_y..)/dy + (F_z..)/dz]
-//   B_out = B_base - h curl_h E   (B1 uses E3 along y and E2 along z, cyclically).
-// U_base / U_out may alias (the corrector updates u^n in place), so no __restrict__ here.
+// Register update of one stage (Sec. 3.2.3, eq. rk-2s):
+//   U_out = (g_base U_base + g_other U_other) + h L,  L = -[(F_x(i+1/2) - F_x(i-1/2))/dx + (F_y..)/dy + ..]
+//   B_out = (g_base B_base + g_other B_other) - h curl_h E   (B1 uses E3 along y and E2 along z, cyclically)
+// with U_other the register that is not U_base.  g_base = 1, g_other = 0 is the plain U_base + h L (VL2's
+// stages, gamma_s = {0, 1}, written with the base register named directly).
+// U_base / U_out may alias (stages update a register in place), so no __restrict__ here.
 // ------------------------------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(256) k_update(MeshView single, const MeshView* views, const WorkItem* work,
-                                                int base_reg, int out_reg, double h, const double* dtbox, double beta) {
+                                                int base_reg, int out_reg, double h, const double* dtbox, double beta,
+                                                double g_base, double g_other) {
   __shared__ MeshView sv;
   int tile, box;
   const MeshView& V = stage_view(sv, single, views, work, tile, &box);
   const Geom& g = V.g;
   if (dtbox) h = beta * dtbox[box];
+  const bool plain = g_other == 0.0 && g_base == 1.0;  // uniform over the launch
   const double* Ubase = V.a.u[base_reg];
+  const double* Uoth = V.a.u[1 - base_reg];
   double* Uout = V.a.u[out_reg];
   const double* Bb0 = V.a.b[base_reg][0];
   const double* Bb1 = V.a.b[base_reg][1];
@@ -428,10 +433,12 @@ __global__ void __launch_bounds__(256) k_update(MeshView single, const MeshView*
         dfl[d] = (to_f64(fp[stride[d]]) - to_f64(fp[0])) * g.idx[d];  // FP64 accumulation
       }
       const double L = -((dfl[0] + dfl[1]) + dfl[2]);
-      Uout[ub + (long long)v * g.box] = Ubase[ub + (long long)v * g.box] + h * L;
+      const long long o = ub + (long long)v * g.box;
+      Uout[o] = (plain ? Ubase[o] : g_base * Ubase[o] + g_other * Uoth[o]) + h * L;
     }
   }
   const double* Bb[3] = {Bb0, Bb1, Bb2};
+  const double* Bx[3] = {V.a.b[1 - base_reg][0], V.a.b[1 - base_reg][1], V.a.b[1 - base_reg][2]};
   double* Bo[3] = {Bo0, Bo1, Bo2};
   const T* E[3] = {E0 + (long long)b * g.box + c, E1 + (long long)b * g.box + c, E2 + (long long)b * g.box + c};
 #pragma unroll
@@ -441,20 +448,22 @@ __global__ void __launch_bounds__(256) k_update(MeshView single, const MeshView*
     const double curl = (to_f64(E[bq][stride[a]]) - to_f64(E[bq][0])) * g.idx[a] -
                         (to_f64(E[a][stride[bq]]) - to_f64(E[a][0])) * g.idx[bq];
     const long long o = (long long)b * g.box + c;
-    Bo[fd][o] = Bb[fd][o] + h * (-curl);
+    Bo[fd][o] = (plain ? Bb[fd][o] : g_base * Bb[fd][o] + g_other * Bx[fd][o]) + h * (-curl);
   }
 }
 
 cudaError_t launch_update(const MeshView& v, const Dispatch* d, int base_reg, int out_reg, double h,
-                          const double* dtbox, double beta, cudaStream_t st) {
+                          const double* dtbox, double beta, cudaStream_t st, double g_base, double g_other) {
   const long long grid = d ? d->nwork : tiles_nodes(v.g);
   if (grid <= 0) return cudaSuccess;
   const MeshView* vs = d ? d->views : nullptr;
   const WorkItem* wk = d ? d->work : nullptr;
   if (v.a.mixed)
-    k_update<float><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk, base_reg, out_reg, h, dtbox, beta);
+    k_update<float><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk, base_reg, out_reg, h, dtbox, beta, g_base,
+                                                        g_other);
   else
-    k_update<double><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk, base_reg, out_reg, h, dtbox, beta);
+    k_update<double><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk, base_reg, out_reg, h, dtbox, beta, g_base,
+                                                         g_other);
   return cudaGetLastError();
 }
 

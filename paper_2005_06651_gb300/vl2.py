@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libvl2mhd.so")
 VL2_OK, VL2_E_ARG, VL2_E_CUDA, VL2_E_NONPHYS, VL2_E_TIMEOUT, VL2_E_STATE, VL2_E_NOMEM = range(7)
 HLLE, HLLD = 0, 1
 PERIODIC, OUTFLOW = 0, 1
+VL2, RK1, RK2, RK3 = 0, 1, 2, 3  # time integrators (vl2_params.integrator)
 FP64, MIXED = 0, 1
 HOST, DEVICE = 0, 1
 DC, PLM = 0, 1
@@ -39,7 +40,7 @@ class Params(ctypes.Structure):
                 ("xmin", ctypes.c_double * 3), ("xmax", ctypes.c_double * 3), ("gamma", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("riemann", ctypes.c_int), ("precision", ctypes.c_int),
                 ("bc", ctypes.c_int * 6), ("dfloor", ctypes.c_double), ("pfloor", ctypes.c_double),
-                ("stream", ctypes.c_void_p), ("adjoint", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("adjoint", ctypes.c_int), ("integrator", ctypes.c_int)]
 
 
 class Layout(ctypes.Structure):
@@ -151,7 +152,7 @@ class Mesh:
 
     def __init__(self, nx, mb, xmin=(0.0, 0.0, 0.0), xmax=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, cfl=0.3,
                  riemann=HLLD, bc=(PERIODIC,) * 6, dfloor=1e-12, pfloor=1e-12, precision=FP64, device=None,
-                 stream=None, adjoint=False):
+                 stream=None, adjoint=False, integrator=VL2):
         import torch
 
         L = load()
@@ -174,6 +175,7 @@ class Mesh:
         p.dfloor, p.pfloor = float(dfloor), float(pfloor)
         p.stream = ctypes.c_void_p(stream.cuda_stream)
         p.adjoint = 1 if adjoint else 0
+        p.integrator = int(integrator)
         self._params = p
         nbytes = ctypes.c_size_t()
         _check(L.vl2_workspace_bytes(ctypes.byref(p), ctypes.byref(nbytes)))
