@@ -186,6 +186,14 @@ def cpu_model():
     return "unknown"
 
 
+def set_orc_threads(n):
+    """Thread count of the oracle's OpenMP loops (libgomp, loaded by the oracle library)."""
+    import ctypes
+
+    gomp = ctypes.CDLL("libgomp.so.1")
+    gomp.omp_set_num_threads(int(n))
+
+
 def orc_threads():
     try:
         import ctypes
@@ -646,6 +654,12 @@ def main():
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu": cpu_model(),
                "sample": "%d VL2 cycle(s) of the full %d^3 workload (%d MeshBlocks), %.1f s" % (
                    done, args.n, (args.n // args.mb) ** 3, el)}
+        # one thread, on a 64^3 sample of the same vortex (one cycle)
+        set_orc_threads(1)
+        r1, d1, _, e1 = oracle_rate(64, 32, 1, 0, max_steps=1)
+        set_orc_threads(threads)
+        cpu["single_thread"] = {"value": r1, "unit": UNIT, "cores": 1,
+                                "sample": "%d VL2 cycle of a 64^3 sample of the vortex (8 MeshBlocks), %.1f s" % (d1, e1)}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

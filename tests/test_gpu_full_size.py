@@ -1,0 +1,63 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py times.
+
+- 256^3 vortex in 512 MeshBlocks of 32^3, FP64 VL2 + PLM + HLLD + CT: one cycle on the GPU against one
+  cycle of the oracle (FP64, all host cores), every output element compared (<= 1e-12, normalised as in
+  the other parity tests).
+- 512^3 decaying turbulence in 4096 MeshBlocks of 32^3, mixed precision: the oracle does not fit this
+  size in a test, so what holds at any size is checked: conservation of the totals and div B at FP64
+  round-off over two cycles.
+"""
+import numpy as np
+import pytest
+
+from paper_2005_06651_gb300 import inputs
+from test_gpu_parity import state_diff
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def vl2():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_06651_gb300 import build, vl2 as mod
+
+    build.build()
+    mod.load()
+    return mod
+
+
+def test_orszag_tang_256cubed_one_cycle_matches_oracle(vl2, oracle):
+    prob = inputs.orszag_tang(n=256, mb=32, seed=2005)
+    g = vl2.Mesh.from_problem(prob)
+    o = oracle.Mesh.from_problem(prob)
+    dt = o.new_dt(0.3)
+    assert g.new_dt() == pytest.approx(dt, rel=1e-13)
+    g.step(dt)
+    o.step(dt)
+    d = state_diff(g.get_cons(), o.get_cons())
+    print("256^3, 512 blocks, one cycle: max normalised difference %.2e" % np.max(d))
+    assert np.max(d) <= 1e-12, d
+    assert g.floor_count() == 0 and o.floor_count() == 0
+    assert g.divb_norm() <= 1e-13
+
+
+def test_mixed_512cubed_conserves_and_keeps_divb(vl2):
+    import torch
+
+    prob = inputs.turbulence(n=512, mb=32, seed=3003, mach=2.0, beta=10.0)
+    g = vl2.Mesh.from_problem(prob, precision=vl2.MIXED)
+    t0 = g.totals()
+    for _ in range(2):
+        g.step(g.new_dt())
+    t = g.totals()
+    print("512^3 mixed, 2 cycles: d(mass)/mass %.2e, div B %.2e" % (abs(t[0] - t0[0]) / t0[0], g.divb_norm()))
+    # the totals are FP64 sums over 1.3e8 cells: their own round-off (~1e-13 relative) sets the bound
+    assert abs(t[0] - t0[0]) <= 2e-12 * abs(t0[0])
+    assert np.all(np.abs(t[1:5] - t0[1:5]) <= 2e-12 * abs(t0[4]))
+    assert g.divb_norm() <= 1e-13
+    g.close()
+    del g
+    torch.cuda.empty_cache()
