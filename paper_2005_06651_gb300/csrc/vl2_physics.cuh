@@ -31,6 +31,14 @@ __device__ __forceinline__ double sqrt_nr(double x) {
   const double s = x * fma(y * h, fma(0.375, h, 0.5), y);
   return (__double_as_longlong(x) << 1) == 0 ? x : s;
 }
+// Products rounded on their own (never contracted into an FMA with a following add).  Used where two
+// products cancel exactly for mirror-image states, so that the difference is exactly zero there (an FMA
+// would leave the rounding error of one product): the contact speed S_M and the mass flux of a
+// symmetry plane, whose sign decides the HLLD side and the CT upwind cell.
+template <class R> __device__ __forceinline__ R mul_rn(R a, R b) { return a * b; }
+template <> __device__ __forceinline__ double mul_rn<double>(double a, double b) { return __dmul_rn(a, b); }
+template <> __device__ __forceinline__ float mul_rn<float>(float a, float b) { return __fmul_rn(a, b); }
+
 template <class R> __device__ __forceinline__ R inv(R x) { return R(1) / x; }
 template <> __device__ __forceinline__ double inv<double>(double x) { return rcp_nr(x); }
 template <class R> __device__ __forceinline__ R root(R x) { return sqrt(x); }
@@ -151,7 +159,7 @@ __device__ __forceinline__ void flux_hlle(const R* wl, const R* wr, R bn, R gamm
   const R iden = inv(bp - bm);
   const R bpm = bp * bm;
 #pragma unroll
-  for (int n = 0; n < 7; ++n) f[n] = ((bp * fl[n] - bm * fr[n]) + bpm * (ur[n] - ul[n])) * iden;
+  for (int n = 0; n < 7; ++n) f[n] = ((mul_rn(bp, fl[n]) - mul_rn(bm, fr[n])) + bpm * (ur[n] - ul[n])) * iden;
 }
 
 // One side (L or R) of the HLLD fan: the state, its conserved vector and physical flux, and its
@@ -274,7 +282,7 @@ __device__ __forceinline__ void flux_hlld(const R* wl, const R* wr, R bn, R gamm
   const R ptl = wl[4] + R(0.5) * (bn2 + btl2), ptr = wr[4] + R(0.5) * (bn2 + btr2);
   const R al = (sl - wl[1]) * wl[0], ar = (sr - wr[1]) * wr[0];
   const R iden = inv(ar - al);
-  const R sm = ((ar * wr[1] - al * wl[1]) + (ptl - ptr)) * iden;
+  const R sm = ((mul_rn(ar, wr[1]) - mul_rn(al, wl[1])) + (ptl - ptr)) * iden;
   const R ptst = ((ar * ptl - al * ptr) + (ar * al) * (wr[1] - wl[1])) * iden;
   const bool left = ge0(sm);
   HlldSide<R> S;

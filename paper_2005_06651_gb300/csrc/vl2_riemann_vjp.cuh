@@ -90,7 +90,7 @@ __device__ __forceinline__ void flux_hlle_vjp(const double* wl, const double* wr
   double gul[7], gfl[7], gur[7], gfr[7];
 #pragma unroll
   for (int n = 0; n < 7; ++n) {
-    const double N = (bp * fl[n] - bm * fr[n]) + bpm * (ur[n] - ul[n]);
+    const double N = (mul_rn(bp, fl[n]) - mul_rn(bm, fr[n])) + bpm * (ur[n] - ul[n]);
     giden += lf[n] * N;
     const double gN = lf[n] * iden;
     gfl[n] = gN * bp;
@@ -398,7 +398,7 @@ __device__ __forceinline__ void flux_hlld_vjp(const double* wl, const double* wr
   const double ptl = wl[4] + 0.5 * (bn2 + btl2), ptr = wr[4] + 0.5 * (bn2 + btr2);
   const double al = (sl - wl[1]) * wl[0], ar = (sr - wr[1]) * wr[0];
   const double iden = rcp_nr(ar - al);
-  const double NM = (ar * wr[1] - al * wl[1]) + (ptl - ptr);
+  const double NM = (mul_rn(ar, wr[1]) - mul_rn(al, wl[1])) + (ptl - ptr);
   const double sm = NM * iden;
   const double dv = wr[1] - wl[1];
   const double NP = (ar * ptl - al * ptr) + (ar * al) * dv;
