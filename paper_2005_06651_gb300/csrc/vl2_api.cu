@@ -185,7 +185,7 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
 }
 
 struct Plan {
-  size_t off_u[2], off_b[2][3], off_w, off_f[3], off_e[3], off_stage, off_red, off_scal, total;
+  size_t off_u[2], off_b[2][3], off_w, off_f[3], off_e[3], off_ec, off_stage, off_red, off_scal, total;
   size_t stage_elems;
   size_t off_adj;  // start of the adjoint arrays (59 FP64 arrays per block) when requested
 };
@@ -214,6 +214,8 @@ Plan make_plan(const Geom& g, int precision, int adjoint) {
     pl.off_e[d] = o;
     o = align256(o + sper);
   }
+  pl.off_ec = o;
+  o = align256(o + 3 * sper);
   const long long nc = ncells(g);
   long long st = 5 * nc + nfaces_total(g);
   st = std::max(st, 8 * nc);
@@ -367,6 +369,7 @@ vl2_status vl2_mesh_create(const vl2_params* params, void* workspace, size_t byt
     m->a.f[d] = base + pl.off_f[d];
     m->a.e[d] = base + pl.off_e[d];
   }
+  m->a.ec = base + pl.off_ec;
   m->a.mixed = params->precision == VL2_MIXED ? 1 : 0;
   if (params->adjoint) {
     const size_t per = (size_t)g.nblk * g.box;

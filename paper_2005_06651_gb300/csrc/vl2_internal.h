@@ -39,6 +39,7 @@ struct Arrays {
   void* w;           // primitives rho, vx, vy, vz, p, bcx, bcy, bcz: [nblk][8][box]
   void* f[3];        // fluxes per sweep direction: [nblk][7][box]
   void* e[3];        // corner EMFs E1, E2, E3: [nblk][box]
+  void* ec;          // cell EMFs -(v x b_c), components 1, 2, 3, written by cons->prim: [nblk][3][box]
   int mixed;         // 1: scratch is float
   double* stage;     // staging for global-array I/O
   size_t stage_elems;

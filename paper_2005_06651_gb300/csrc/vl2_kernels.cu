@@ -83,14 +83,22 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
       Ub[4 * g.box] = e;
     }
     TW* Wb = static_cast<TW*>(V.a.w) + (long long)b * 8 * g.box + c;
+    const TW wx = to_wtype<TW>(vx), wy = to_wtype<TW>(vy), wz = to_wtype<TW>(vz);
+    const TW ux = to_wtype<TW>(bcx), uy = to_wtype<TW>(bcy), uz = to_wtype<TW>(bcz);
     Wb[0] = to_wtype<TW>(d);
-    Wb[g.box] = to_wtype<TW>(vx);
-    Wb[2 * g.box] = to_wtype<TW>(vy);
-    Wb[3 * g.box] = to_wtype<TW>(vz);
+    Wb[g.box] = wx;
+    Wb[2 * g.box] = wy;
+    Wb[3 * g.box] = wz;
     Wb[4 * g.box] = to_wtype<TW>(p);
-    Wb[5 * g.box] = to_wtype<TW>(bcx);
-    Wb[6 * g.box] = to_wtype<TW>(bcy);
-    Wb[7 * g.box] = to_wtype<TW>(bcz);
+    Wb[5 * g.box] = ux;
+    Wb[6 * g.box] = uy;
+    Wb[7 * g.box] = uz;
+    // cell EMFs -(v x b_c) of the stored primitives, for the CT corners (each is used by four corners of
+    // its family): computed in the stage's precision, as the corners' face EMFs are
+    TW* Eb = static_cast<TW*>(V.a.ec) + (long long)b * 3 * g.box + c;
+    Eb[0] = wz * uy - wy * uz;
+    Eb[g.box] = wx * uz - wz * ux;
+    Eb[2 * g.box] = wy * ux - wx * uy;
     if (DT && active) {
       // single-precision estimate of the rate (relative error well below 1e-5)
       const float fid = to_f32(id), fp = to_f32(p), fg = (float)g.gamma;
@@ -223,6 +231,42 @@ __device__ __forceinline__ void source_of(const Geom& g, int q, int gi, bool fac
   }
 }
 
+// Ghost elements lie in the shell of the padded box: index triples 0 .. mb+2NG (one more than the cells,
+// for the faces) with at least one coordinate outside the interior NG .. NG+mb-1.  A thread per shell
+// element; the shell is decoded as z-slabs (k outside the interior), then y-slabs (k inside, j outside),
+// then x-slabs (k, j inside, i outside).
+__device__ __forceinline__ long long shell_size(const Geom& g) {
+  const long long ex = g.mb[0] + 2 * NG + 1, ey = g.mb[1] + 2 * NG + 1, ez = g.mb[2] + 2 * NG + 1;
+  return ex * ey * ez - (long long)g.mb[0] * g.mb[1] * g.mb[2];
+}
+__device__ __forceinline__ void shell_index(const Geom& g, int s, int* li) {
+  const int ex = g.mb[0] + 2 * NG + 1, ey = g.mb[1] + 2 * NG + 1, ez = g.mb[2] + 2 * NG + 1;
+  const int gx = ex - g.mb[0], gy = ey - g.mb[1], gz = ez - g.mb[2];  // ghost layers per direction
+  auto unfold = [&](int gidx, int q) { return gidx < NG ? gidx : gidx + g.mb[q]; };
+  const int nz = gz * ey * ex;
+  if (s < nz) {
+    li[2] = unfold(s / (ey * ex), 2);
+    const int r = s % (ey * ex);
+    li[1] = r / ex;
+    li[0] = r % ex;
+    return;
+  }
+  s -= nz;
+  const int ny = g.mb[2] * gy * ex;
+  if (s < ny) {
+    li[2] = s / (gy * ex) + NG;
+    const int r = s % (gy * ex);
+    li[1] = unfold(r / ex, 1);
+    li[0] = r % ex;
+    return;
+  }
+  s -= ny;
+  li[2] = s / (g.mb[1] * gx) + NG;
+  const int r = s % (g.mb[1] * gx);
+  li[1] = r / gx + NG;
+  li[0] = unfold(r % gx, 0);
+}
+
 __global__ void __launch_bounds__(256) k_ghosts(MeshView single, const MeshView* views, const WorkItem* work, int reg) {
   __shared__ MeshView sv;
   int tile;
@@ -232,24 +276,25 @@ __global__ void __launch_bounds__(256) k_ghosts(MeshView single, const MeshView*
   double* B0 = V.a.b[reg][0];
   double* B1 = V.a.b[reg][1];
   double* B2 = V.a.b[reg][2];
-  const int ex = g.mb[0] + 2 * NG + 1, ey = g.mb[1] + 2 * NG + 1, ez = g.mb[2] + 2 * NG + 1;
-  const long long per = (long long)ex * ey * ez;
+  const long long per = shell_size(g);
   const long long t = (long long)tile * blockDim.x + threadIdx.x;
   if (t >= per * g.nblk) return;
   const int b = (int)(t / per);
-  int rem = (int)(t - (long long)b * per);
-  const int li[3] = {rem % ex, (rem / ex) % ey, rem / (ex * ey)};
+  int li[3];
+  shell_index(g, (int)(t - (long long)b * per), li);
   int loc[3];
   block_loc(g, b, loc);
   const long long c = cell_off(g, li[2], li[1], li[0]);
   const int cmax[3] = {g.mb[0] + 2 * NG, g.mb[1] + 2 * NG, g.mb[2] + 2 * NG};
+  // source block and index of each coordinate as a cell index (faces re-map their own direction)
+  int sb[3], sl[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) source_of(g, q, loc[q] * g.mb[q] + li[q] - NG, false, sb[q], sl[q]);
   // cell-centred conserved variables
   if (li[0] < cmax[0] && li[1] < cmax[1] && li[2] < cmax[2]) {
     bool ghost = false;
     for (int q = 0; q < 3; ++q) ghost |= (li[q] < NG || li[q] >= NG + g.mb[q]);
     if (ghost) {
-      int sb[3], sl[3];
-      for (int q = 0; q < 3; ++q) source_of(g, q, loc[q] * g.mb[q] + li[q] - NG, false, sb[q], sl[q]);
       const int src = (sb[2] * g.nb[1] + sb[1]) * g.nb[0] + sb[0];
       const long long sc = cell_off(g, sl[2], sl[1], sl[0]);
       const double* Us = U + (long long)src * 5 * g.box + sc;
@@ -270,15 +315,16 @@ __global__ void __launch_bounds__(256) k_ghosts(MeshView single, const MeshView*
       ghost |= (li[q] < NG || li[q] > hi_active);
     }
     if (!valid || !ghost) continue;
-    int sb[3], sl[3];
-    for (int q = 0; q < 3; ++q) source_of(g, q, loc[q] * g.mb[q] + li[q] - NG, q == fd, sb[q], sl[q]);
-    const int src = (sb[2] * g.nb[1] + sb[1]) * g.nb[0] + sb[0];
-    Bf[fd][(long long)b * g.box + c] = Bf[fd][(long long)src * g.box + cell_off(g, sl[2], sl[1], sl[0])];
+    int fb[3] = {sb[0], sb[1], sb[2]}, fl[3] = {sl[0], sl[1], sl[2]};
+    source_of(g, fd, loc[fd] * g.mb[fd] + li[fd] - NG, true, fb[fd], fl[fd]);
+    const int src = (fb[2] * g.nb[1] + fb[1]) * g.nb[0] + fb[0];
+    Bf[fd][(long long)b * g.box + c] = Bf[fd][(long long)src * g.box + cell_off(g, fl[2], fl[1], fl[0])];
   }
 }
 
 long long tiles_ghosts(const Geom& g) {
-  const long long per = (long long)(g.mb[0] + 2 * NG + 1) * (g.mb[1] + 2 * NG + 1) * (g.mb[2] + 2 * NG + 1);
+  const long long per = (long long)(g.mb[0] + 2 * NG + 1) * (g.mb[1] + 2 * NG + 1) * (g.mb[2] + 2 * NG + 1) -
+                        (long long)g.mb[0] * g.mb[1] * g.mb[2];
   return (per * g.nblk + THREADS - 1) / THREADS;
 }
 
@@ -292,24 +338,14 @@ cudaError_t launch_ghosts(const MeshView& v, const Dispatch* d, int reg, cudaStr
 // ------------------------------------------------------------------------------------------------
 // Upwind CT corner EMFs (Sec. 3.1 / Sec. 2.1.1).  Edge family e (E1 along x, E2 along y, E3 along z),
 // transverse directions a = e+1, b = e+2.  Face EMFs of that component: -F_a[B_t1] on a-faces and
-// +F_b[B_t2] on b-faces (E = -v x B); cell EMFs from the primitives.  One thread per corner node.
+// +F_b[B_t2] on b-faces (E = -v x B); cell EMFs as cons->prim wrote them.  One thread per corner node.
 // ------------------------------------------------------------------------------------------------
-template <class T>
-__device__ __forceinline__ T cell_emf(int e, const T* Wc, long long box) {
-  const T vx = Wc[box], vy = Wc[2 * box], vz = Wc[3 * box];
-  const T bx = Wc[5 * box], by = Wc[6 * box], bz = Wc[7 * box];
-  if (e == 0) return vz * by - vy * bz;
-  if (e == 1) return vx * bz - vz * bx;
-  return vy * bx - vx * by;
-}
-
 template <class T>
 __global__ void __launch_bounds__(256) k_emf(MeshView single, const MeshView* views, const WorkItem* work) {
   __shared__ MeshView sv;
   int tile;
   const MeshView& V = stage_view(sv, single, views, work, tile);
   const Geom& g = V.g;
-  const T* W = static_cast<const T*>(V.a.w);
   const T* F0 = static_cast<const T*>(V.a.f[0]);
   const T* F1 = static_cast<const T*>(V.a.f[1]);
   const T* F2 = static_cast<const T*>(V.a.f[2]);
@@ -327,7 +363,7 @@ __global__ void __launch_bounds__(256) k_emf(MeshView single, const MeshView* vi
   const long long stride[3] = {1LL, (long long)g.sx, (long long)g.sx * g.sy};
   const T* F[3] = {F0, F1, F2};
   T* E[3] = {E0, E1, E2};
-  const T* Wb = W + (long long)b * 8 * g.box;
+  const T* Ecb = static_cast<const T*>(V.a.ec) + (long long)b * 3 * g.box;
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     if (li[e] > NG + g.mb[e] - 1) continue;
@@ -344,10 +380,11 @@ __global__ void __launch_bounds__(256) k_emf(MeshView single, const MeshView* vi
     ma[1] = Fa[c];
     mb[0] = Fb[c - sa];
     mb[1] = Fb[c];
-    ec[0] = cell_emf(e, Wb + c - sa - sb, g.box);
-    ec[1] = cell_emf(e, Wb + c - sb, g.box);
-    ec[2] = cell_emf(e, Wb + c - sa, g.box);
-    ec[3] = cell_emf(e, Wb + c, g.box);
+    const T* Ec = Ecb + (long long)e * g.box;
+    ec[0] = Ec[c - sa - sb];
+    ec[1] = Ec[c - sb];
+    ec[2] = Ec[c - sa];
+    ec[3] = Ec[c];
     E[e][(long long)b * g.box + c] = ct_corner(ea, eb, ec, ma, mb);
   }
 }
