@@ -478,10 +478,40 @@ def integrators_form(args, dev, stream, vl2, inputs):
     return out
 
 
+def blast_form(args, dev, stream, vl2, inputs):
+    """The paper's performance problem: the 3D MHD blast wave (rho = 1, p = 1e-3, total internal energy 1
+    within r = 0.01 of the centre, B = (sqrt 3, 1, 0)) on the 256^3 mesh of 512 MeshBlocks of 32^3, FP64
+    VL2 + PLM + HLLD + CT.  Ambient beta is 5e-4: floors fire (and are counted) as the pressure is
+    recovered from E - rho v^2/2 - B^2/2 around the blast."""
+    import torch
+
+    prob = inputs.blast(n=args.n, mb=args.mb, r0=0.01)
+    m = vl2.Mesh.from_problem(prob, device=dev, stream=stream)
+    for _ in range(2):
+        m.step(m.new_dt(allow_nonphys=True))
+    torch.cuda.synchronize(dev)
+    K = args.blast_steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(K):
+        m.step(m.new_dt(allow_nonphys=True))
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    out = {"config": {"workload": "mhd_blast_%d^3_%dx%d^3_blocks_r0.01_etot1_p1e-3_b_sqrt3_1_0" % (
+               args.n, (args.n // args.mb) ** 3, args.mb), "steps": K, "dtype": "f64",
+               "cells_inside": prob.meta["cells_inside"], "p_in": prob.meta["p_in"]},
+           "value": prob.ncells * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K,
+           "floor_events": m.floor_count(), "divb_norm": m.divb_norm()}
+    m.close()
+    return out
+
+
 def run_forms(args, dev, stream, vl2, inputs):
     import torch
 
-    fns = {"mixed": mixed_form, "batched": batched_form, "adjoint": adjoint_form, "integrators": integrators_form}
+    fns = {"mixed": mixed_form, "batched": batched_form, "adjoint": adjoint_form, "integrators": integrators_form,
+           "blast": blast_form}
     forms = {}
     for name in [f for f in args.forms.split(",") if f]:
         if name not in fns:
@@ -520,7 +550,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--adj-n", type=int, default=64, help="grid of the differentiation form")
     ap.add_argument("--adj-steps", type=int, default=100)
-    ap.add_argument("--forms", default="mixed,batched,adjoint,integrators", help="comma list of the forms to run")
+    ap.add_argument("--forms", default="mixed,batched,adjoint,integrators,blast", help="comma list of the forms to run")
+    ap.add_argument("--blast-steps", type=int, default=20, help="timed cycles of the blast-wave form")
     ap.add_argument("--rk-steps", type=int, default=10, help="timed cycles of each RK integrator")
     ap.add_argument("--forms-only", action="store_true",
                     help="run only the forms (a profiling aid: prints {'forms': ...}, not the bench line)")

@@ -301,6 +301,34 @@ def turbulence(n=64, mb=None, seed=3003, mach=1.0, beta=1.0, gamma=5.0 / 3.0):
 
 
 # ------------------------------------------------------------------------------------------------
+# Blast wave (Sec. 3.4, 3D blast wave tests; the paper's performance problem)
+# ------------------------------------------------------------------------------------------------
+
+def blast(n=256, mb=32, r0=0.01, e_tot=1.0, p_ambient=1e-3, magnetized=True, gamma=5.0 / 3.0):
+    """Periodic unit cube, rho = 1 and p = p_ambient everywhere, except the cells whose centres lie within
+    r0 of the centre.  Those hold the total internal energy e_tot = sum p/(gamma-1) dV exactly (the
+    discrete form of the paper's integral; for r0 = 0.01 and e_tot = 1 the sphere's pressure is 1.6e5).
+    The field is uniform, B = (sqrt 3, 1, 0) when magnetized.  Raises if no cell centre lies inside r0."""
+    nx = (n, n, n) if np.isscalar(n) else tuple(n)
+    mbt = (mb, mb, mb) if np.isscalar(mb) else tuple(mb)
+    xmin, xmax = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
+    x, y, z = _cell_coords(nx, xmin, xmax)
+    inside = (x - 0.5) ** 2 + (y - 0.5) ** 2 + (z - 0.5) ** 2 < r0 * r0
+    nin = int(inside.sum())
+    if nin == 0:
+        raise ValueError("no cell centre lies within r0 = %g at this resolution" % r0)
+    dv = 1.0 / (nx[0] * nx[1] * nx[2])
+    p_in = (gamma - 1.0) * e_tot / (nin * dv)
+    w = np.zeros((5,) + x.shape)
+    w[0] = 1.0
+    w[4] = np.where(inside, p_in, p_ambient)
+    b0 = (math.sqrt(3.0), 1.0, 0.0) if magnetized else (0.0, 0.0, 0.0)
+    b1, b2, b3 = uniform_faces(nx, b0)
+    return Problem("blast", nx, mbt, xmin, xmax, gamma, np.ascontiguousarray(w), b1, b2, b3,
+                   meta={"r0": r0, "p_in": p_in, "cells_inside": nin, "magnetized": magnetized})
+
+
+# ------------------------------------------------------------------------------------------------
 # Shock tubes (one-dimensional along a chosen axis, periodic double tube)
 # ------------------------------------------------------------------------------------------------
 

@@ -358,3 +358,31 @@ def test_rk_integrators_second_order_2d(oracle, integrator):
     slope = math.log2(errs[0] / errs[1])
     print("%s + PLM fast wave: L1 %.3e -> %.3e, slope %.3f" % (integrator, errs[0], errs[1], slope))
     assert 1.8 <= slope <= 2.2, (integrator, errs, slope)
+
+
+def test_blast_setup_and_pressure_floor(oracle):
+    """The blast holds the stated internal energy inside r0 on a uniform field; in its low-beta ambient the
+    pressure floor (reading 2) fires in the first donor-cell cycle, and each floored cell then holds
+    p = pfloor up to the rounding of E, with mass untouched and div B still at round-off."""
+    prob = inputs.blast(32, mb=16, r0=0.1, magnetized=True)
+    dv = 1.0 / 32 ** 3
+    inside = prob.w[4] > 1e-3
+    assert int(inside.sum()) == prob.meta["cells_inside"] > 0
+    assert np.sum(prob.w[4][inside]) / (G - 1.0) * dv == pytest.approx(1.0, rel=1e-13)
+    assert np.all(prob.w[4][~inside] == 1e-3) and np.all(prob.w[0] == 1.0)
+    assert np.all(prob.b1 == math.sqrt(3.0)) and np.all(prob.b2 == 1.0) and np.all(prob.b3 == 0.0)
+    o = oracle.Mesh.from_problem(prob, riemann=oracle.HLLD, integrator=oracle.RK1)
+    m0 = o.totals()[0]
+    o.step(o.new_dt(0.3))
+    assert o.floor_count() == 0
+    o.new_dt(0.3)
+    fired = o.floor_count()
+    assert fired > 0
+    u = o.get_cons()[0]
+    w = o.get_prims()  # recomputes p = (gamma-1)(E - ke - me) from the rewritten E
+    tol = 8 * np.finfo(float).eps * (G - 1.0) * u[4]  # a few ulps of E
+    floored = np.abs(w[4] - 1e-12) <= tol
+    assert int(floored.sum()) >= 1
+    assert np.all(w[4] >= 1e-12 - tol)
+    assert o.totals()[0] == pytest.approx(m0, rel=1e-14)
+    assert o.divb_norm() <= 1e-13
