@@ -140,6 +140,16 @@ __device__ __forceinline__ int okey(float x) {
 template <class R> __device__ __forceinline__ R imin(R a, R b) { return okey(a) < okey(b) ? a : b; }
 template <class R> __device__ __forceinline__ R imax(R a, R b) { return okey(a) > okey(b) ? a : b; }
 template <class R> __device__ __forceinline__ bool igt(R a, R b) { return okey(a) > okey(b); }
+// The two sweep-frame states are bitwise equal.  The flux of such a pair is the physical flux of the state
+// (consistency of every Riemann solver; HLLE's and HLLD's own arithmetic give it up to rounding, with the
+// same sign of the mass flux, exactly zero when v_n is), so both solvers form it directly: uniform regions
+// at rest would otherwise take HLLD's S_M == 0 branch and evaluate both sides of the fan.
+template <class R> __device__ __forceinline__ bool same_state(const R* a, const R* b) {
+  auto x = dbits(a[0]) ^ dbits(b[0]);
+#pragma unroll
+  for (int n = 1; n < 7; ++n) x |= dbits(a[n]) ^ dbits(b[n]);
+  return x == 0;
+}
 
 // HLLE flux; outer speeds are the extreme fast-wave speeds of the two states (Sec. 3.2.2 names the
 // solver; the speed estimate is this library's reading).
@@ -147,6 +157,11 @@ template <class R>
 __device__ __forceinline__ void flux_hlle(const R* wl, const R* wr, R bn, R gamma, R igm1, R* f) {
   R ul[7], fl[7], ur[7], fr[7];
   phys_flux(wl, bn, igm1, ul, fl);
+  if (same_state(wl, wr)) {
+#pragma unroll
+    for (int n = 0; n < 7; ++n) f[n] = fl[n];
+    return;
+  }
   phys_flux(wr, bn, igm1, ur, fr);
   const R bn2 = bn * bn;
   const R ilr = inv(wl[0] * wr[0]);  // 1/rho_L and 1/rho_R from one reciprocal
@@ -267,9 +282,15 @@ __device__ __forceinline__ void hlld_side_flux(HlldSide<R>& S, const R* o_w, R o
 // |rho (S-u)(S-S_M) - b_n^2| <= 1e-8 p_T*); Alfven speeds S*_{L,R} = S_M -+ |b_n| / sqrt(rho*);
 // double-star states with sign(0) = +1.  Selection: the sign of S_M picks the side, ties at an outer
 // or Alfven speed of exactly zero take the outer state, S_M == 0 averages both sides.  Only the
-// picked side's star state is formed (the other side's only in the double-star region).
+// picked side's star state is formed (the other side's only in the double-star region).  Bitwise-equal
+// states take the physical flux (same_state).
 template <class R>
 __device__ __forceinline__ void flux_hlld(const R* wl, const R* wr, R bn, R gamma, R igm1, R* f) {
+  if (same_state(wl, wr)) {
+    R u[7];
+    phys_flux(wl, bn, igm1, u, f);
+    return;
+  }
   const R bn2 = bn * bn;
   const R btl2 = wl[5] * wl[5] + wl[6] * wl[6];
   const R btr2 = wr[5] * wr[5] + wr[6] * wr[6];
