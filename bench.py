@@ -507,11 +507,79 @@ def blast_form(args, dev, stream, vl2, inputs):
     return out
 
 
+def _graph_ms_per_cycle(vl2, prob, mb, riemann, K, dev, stream):
+    """ms per VL2 cycle of prob on MeshBlocks of mb^3 cells: K cycles with device-side CFL steps as one
+    CUDA-graph launch (vl2_batch_run on a batch of this one mesh), so that no host call sits between the
+    cycles.  Returns (ms, floor events, div B norm)."""
+    import torch
+
+    m = vl2.Mesh.from_problem(prob, mb=(mb,) * 3, riemann=riemann, device=dev, stream=stream)
+    batch = vl2.Batch([m])
+    batch.run(K, want_dt=False)  # capture the K-cycle graph (untimed), then reset and time it
+    m.set_prims(prob.w, prob.b1, prob.b2, prob.b3)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    batch.run(K, want_dt=False)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / K
+    out = (ms, m.floor_count(), m.divb_norm())
+    batch.close()
+    m.close()
+    return out
+
+
+def meshblocks_form(args, dev, stream, vl2, inputs):
+    """MeshBlock size and cost, on the paper's blast wave (its Secs. on single-core performance and on the
+    size of MeshBlocks):
+    - sweep: the 128^3 MHD blast (HLLD) on MeshBlocks of x^3 cells, x = 4 ... 128, each cost normalised to
+      the single 128^3 MeshBlock and fitted by least squares to W(x) = A + b/x + c/x^3 (active-cell work,
+      a surface term, a per-MeshBlock term); the same on the 128^3 vortex, whose faces all carry distinct
+      states (most of the blast's faces are between equal states at rest, which the solvers short-cut);
+    - single 64^3 MeshBlock: the rate of each solver, MHD and hydro (HLLD at B = 0 is HLLC).
+    The energy goes to the cells whose centres lie within r0 = max(0.01, sqrt(3) dx / 2 (1 + 1e-6)) of the
+    centre: at 128^3 and at 64^3 these are the 8 cells around it (at 64^3 no centre lies within 0.01)."""
+    import numpy as np
+
+    K = args.mb_sweep_steps
+
+    def r0_of(n):
+        return max(0.01, 0.5 * np.sqrt(3.0) / n * (1.0 + 1e-6))
+
+    n = 128
+    sizes = [4, 8, 16, 32, 64, 128]
+    xs = np.array(sizes, dtype=float)
+    sweep = {}
+    blast128 = inputs.blast(n=n, mb=n, r0=r0_of(n))
+    for name, prob in (("mhd_blast_128^3_hlld_%d_cells_inside" % blast128.meta["cells_inside"], blast128),
+                       ("orszag_tang_128^3_hlld", inputs.orszag_tang(n=n, mb=n, seed=2005))):
+        ms = {x: _graph_ms_per_cycle(vl2, prob, x, vl2.HLLD, K, dev, stream)[0] for x in sizes}
+        w = np.array([ms[x] / ms[128] for x in sizes])
+        A, b, c = np.linalg.lstsq(np.stack([np.ones_like(xs), 1.0 / xs, xs ** -3], axis=1), w, rcond=None)[0]
+        sweep[name] = {"cycles": K, "ms_per_cycle": {str(x): ms[x] for x in sizes},
+                       "normalised_cost": {str(x): float(v) for x, v in zip(sizes, w)},
+                       "fit_W_A_b_c": [float(A), float(b), float(c)],
+                       "fit_max_abs_residual": float(np.max(np.abs(A + b / xs + c / xs ** 3 - w))),
+                       "surface_term_exceeds_A_below_x": float(b / A) if A > 0 else None}
+    n = 64
+    single = {}
+    for mhd in (True, False):
+        p64 = inputs.blast(n=n, mb=n, r0=r0_of(n), magnetized=mhd)
+        for name, riemann in (("hlld", vl2.HLLD), ("hlle", vl2.HLLE)):
+            t, floors, divb = _graph_ms_per_cycle(vl2, p64, n, riemann, K, dev, stream)
+            single["%s_plm_%s" % ("mhd" if mhd else "hydro", name)] = {
+                "value": p64.ncells / (t / 1e3), "unit": UNIT, "ms_per_cycle": t, "floor_events": floors}
+    return {"sweep": sweep, "single_64cubed_block": single,
+            "config": {"dtype": "f64", "integrator": "vl2", "recon": "plm",
+                       "timing": "K cycles with device-side dt as one CUDA graph (vl2_batch_run)"}}
+
+
 def run_forms(args, dev, stream, vl2, inputs):
     import torch
 
     fns = {"mixed": mixed_form, "batched": batched_form, "adjoint": adjoint_form, "integrators": integrators_form,
-           "blast": blast_form}
+           "blast": blast_form, "meshblocks": meshblocks_form}
     forms = {}
     for name in [f for f in args.forms.split(",") if f]:
         if name not in fns:
@@ -550,7 +618,9 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--adj-n", type=int, default=64, help="grid of the differentiation form")
     ap.add_argument("--adj-steps", type=int, default=100)
-    ap.add_argument("--forms", default="mixed,batched,adjoint,integrators,blast", help="comma list of the forms to run")
+    ap.add_argument("--forms", default="mixed,batched,adjoint,integrators,blast,meshblocks",
+                    help="comma list of the forms to run")
+    ap.add_argument("--mb-sweep-steps", type=int, default=20, help="timed cycles per MeshBlock size")
     ap.add_argument("--blast-steps", type=int, default=20, help="timed cycles of the blast-wave form")
     ap.add_argument("--rk-steps", type=int, default=10, help="timed cycles of each RK integrator")
     ap.add_argument("--forms-only", action="store_true",
