@@ -17,7 +17,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liborc.so")
 
 HLLE, HLLD = 0, 1
-DC, PLM = 0, 1
+DC, PLM, PPM = 0, 1, 2
 VL2, RK1, RK2, RK3 = 0, 1, 2, 3
 
 _lib = None
@@ -45,7 +45,7 @@ def lib():
         ip = ctypes.POINTER(ctypes.c_int)
         L.orc_mesh_new.restype = ctypes.c_void_p
         L.orc_mesh_new.argtypes = [ip, ip, dp, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.c_double,
-                                   ctypes.c_double, ctypes.c_int]
+                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.orc_mesh_free.argtypes = [ctypes.c_void_p]
         L.orc_set_prims.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
         L.orc_get_cons.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
@@ -71,6 +71,9 @@ def lib():
         L.orc_fast_speed.restype = ctypes.c_double
         L.orc_vanleer_slope.argtypes = [ctypes.c_double] * 3
         L.orc_vanleer_slope.restype = ctypes.c_double
+        L.orc_ppm_edges.argtypes = [dp, dp]
+        L.orc_ppm_face.argtypes = [dp]
+        L.orc_ppm_face.restype = ctypes.c_double
         L.orc_count_face_ops.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
                                          ctypes.POINTER(ctypes.c_longlong)]
         L.orc_ct_corner.argtypes = [dp, dp, dp, dp, dp]
@@ -125,6 +128,20 @@ def vanleer_slope(qm, q0, qp):
     return lib().orc_vanleer_slope(qm, q0, qp)
 
 
+def ppm_edges(q5):
+    """(left, right) PPM edge values of the middle cell of q5 = (q_{i-2}, ..., q_{i+2})."""
+    q = _c64(np.asarray(q5, dtype=np.float64))
+    out = np.zeros(2)
+    lib().orc_ppm_edges(_dp(q), _dp(out))
+    return float(out[0]), float(out[1])
+
+
+def ppm_face(q4):
+    """Limited fourth-order PPM face value between q4[1] and q4[2]."""
+    q = _c64(np.asarray(q4, dtype=np.float64))
+    return lib().orc_ppm_face(_dp(q))
+
+
 def count_face_ops(recon, solver, q4, bn, gamma):
     """(add/sub, mul, div, sqrt, compare) FP64 operations of one face flux; q4 = states of cells
     i-2 .. i+1 in the sweep frame, shape (4, 7)."""
@@ -173,10 +190,11 @@ def step_cons(prob_geom, dt, state, gamma=5.0 / 3.0, riemann=HLLD):
 # ------------------------------------------------------------------------------------------------
 
 class Mesh:
-    """Oracle mesh of equal-size MeshBlocks holding one VL2 state."""
+    """Oracle mesh of equal-size MeshBlocks holding one VL2 state.  recon is the reconstruction of the
+    higher-order stages (PLM or PPM); ng the ghost layers (default 2, or 3 with PPM)."""
 
     def __init__(self, nx, mb, xmin=(0.0, 0.0, 0.0), xmax=(1.0, 1.0, 1.0), gamma=5.0 / 3.0,
-                 riemann=HLLD, bc=(0,) * 6, dfloor=1e-12, pfloor=1e-12, integrator=VL2):
+                 riemann=HLLD, bc=(0,) * 6, dfloor=1e-12, pfloor=1e-12, integrator=VL2, recon=PLM, ng=None):
         self.nx = tuple(int(v) for v in nx)
         self.mb = tuple(int(v) for v in mb)
         self.xmin, self.xmax = tuple(xmin), tuple(xmax)
@@ -187,7 +205,8 @@ class Mesh:
         da = (ctypes.c_double * 3)(*self.xmin)
         db = (ctypes.c_double * 3)(*self.xmax)
         bcs = (ctypes.c_int * 6)(*bc)
-        self._h = L.orc_mesh_new(ia, ib, da, db, gamma, riemann, bcs, dfloor, pfloor, integrator)
+        self.ng = (3 if recon == PPM else 2) if ng is None else int(ng)
+        self._h = L.orc_mesh_new(ia, ib, da, db, gamma, riemann, bcs, dfloor, pfloor, integrator, recon, self.ng)
         if not self._h:
             raise ValueError("invalid oracle mesh parameters")
 

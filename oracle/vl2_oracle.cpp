@@ -15,6 +15,9 @@
  *     (periodic wrap, or outflow = copy of the nearest active cell)              (Sec. 2.1, 2.1.1)
  *   - EMFs on edges shared by several MeshBlocks are averaged over the copies   (Sec. 2.1.1)
  *   - donor-cell and PLM reconstruction of primitives, original van Leer limiter (Sec. 3.2.1)
+ *   - PPM reconstruction of primitives: fourth-order face values (eq. ppm-uniform-weights) and the
+ *     smooth-extremum-preserving limiter the paper names (Colella & Sekora 2008, as extended by
+ *     McCorquodale & Colella); N_G = 3                                          (Sec. 3.2.1, 2.1.1)
  *   - HLLE and HLLD approximate Riemann solvers                                 (Sec. 3.2.2)
  *   - 2S low-storage register scheme (eq. rk-2s) with the VL2 coefficients; the
  *     predictor uses donor-cell fluxes                                           (Sec. 3.2.3)
@@ -48,7 +51,7 @@ using std::sqrt;
 
 enum { RS_HLLE = 0, RS_HLLD = 1 };
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
-enum { REC_DC = 0, REC_PLM = 1 };
+enum { REC_DC = 0, REC_PLM = 1, REC_PPM = 2 };
 enum { INT_VL2 = 0, INT_RK1 = 1, INT_RK2 = 2, INT_RK3 = 3 };
 
 /* Interface-state layout (normal n, transverse t1, t2 taken cyclically: x->(y,z), y->(z,x),
@@ -345,6 +348,77 @@ static T vanleer_slope(T qm, T q0, T qp) {
   return T(0.0);
 }
 
+/* PPM edge values of one cell (Sec. 3.2.1) from the five cell values q[0..4] = q_{i-2} .. q_{i+2}:
+ *   1. fourth-order face values, eq. ppm-uniform-weights:
+ *        q_{i-1/2} = 7/12 (q_{i-1} + q_i) - 1/12 (q_{i-2} + q_{i+1});
+ *   2. a face value outside the range of its two cells is replaced by
+ *        (q_{i-1} + q_i)/2 - D2lim/6,   D2 = 3 (q_{i-1} - 2 q_{i-1/2} + q_i),
+ *      D2lim = sign(D2) min(|D2|, C |D2L|, C |D2R|) when D2 and the neighbouring second differences
+ *      D2L = q_{i-2} - 2 q_{i-1} + q_i, D2R = q_{i-1} - 2 q_i + q_{i+1} share its sign, else 0 (C = 1.25);
+ *      with D2lim = D2 this returns the face value unchanged;
+ *   3. the cell's parabola (edges qL, qR):
+ *      - at an extremum ((qR - q_i)(q_i - qL) <= 0 or (q_{i+1} - q_i)(q_i - q_{i-1}) <= 0) its second
+ *        derivative D2 = 6 (qL + qR - 2 q_i) is limited like step 2 against D2C = q_{i-1} - 2 q_i + q_{i+1},
+ *        D2L and D2R of the cells around, and both edges move towards q_i by the factor D2lim / D2
+ *        (to q_i when D2 = 0);
+ *      - otherwise an edge whose distance from q_i exceeds twice the other edge's is pulled in to
+ *        twice that distance on its side (the parabola stays monotone in the cell).
+ * [reading] The paper prints step 1 and names the limiter; steps 2 and 3 follow Colella & Sekora
+ * 2008.  McCorquodale & Colella's further test of third differences near smooth extrema is not
+ * applied. */
+// Second differences are written (outer sum) - 2 middle, so that mirrored inputs give bitwise mirrored
+// results (as everywhere in this file).
+template <class T> static inline T ppm_sign(T x) { return (x > 0.0) ? T(1.0) : ((x < 0.0) ? T(-1.0) : T(0.0)); }
+
+template <class T>
+static T ppm_face(T qm2, T qm1, T q0, T qp1) {
+  const double C = 1.25;
+  T f = (7.0 / 12.0) * (qm1 + q0) - (1.0 / 12.0) * (qm2 + qp1);
+  if ((f - qm1) * (q0 - f) < 0.0) {
+    const T d2 = 3.0 * ((qm1 + q0) - 2.0 * f);
+    const T d2l = (qm2 + q0) - 2.0 * qm1;
+    const T d2r = (qm1 + qp1) - 2.0 * q0;
+    T lim = T(0.0);
+    const T s = ppm_sign(d2);
+    if (ppm_sign(d2l) == s && ppm_sign(d2r) == s && !(s == 0.0))
+      lim = s * vmin(fabs(d2), vmin(C * fabs(d2l), C * fabs(d2r)));
+    f = 0.5 * (qm1 + q0) - lim / 6.0;
+  }
+  return f;
+}
+
+/* Edges (ql, qr) of cell i from q[0..4] = q_{i-2} .. q_{i+2}.  A face between cells i-1 and i therefore
+ * reads q_{i-3} .. q_{i+2}: three ghost layers. */
+template <class T>
+static void ppm_edges(const T q[5], T& ql, T& qr) {
+  const double C = 1.25;
+  const T qm2 = q[0], qm1 = q[1], q0 = q[2], qp1 = q[3], qp2 = q[4];
+  ql = ppm_face(qm2, qm1, q0, qp1);
+  qr = ppm_face(qm1, q0, qp1, qp2);
+  if ((qr - q0) * (q0 - ql) <= 0.0 || (qp1 - q0) * (q0 - qm1) <= 0.0) {
+    const T d2 = 6.0 * ((ql + qr) - 2.0 * q0);
+    const T d2c = (qm1 + qp1) - 2.0 * q0;
+    const T d2l = (qm2 + q0) - 2.0 * qm1;
+    const T d2r = (q0 + qp2) - 2.0 * qp1;
+    const T s = ppm_sign(d2);
+    T lim = T(0.0);
+    if (!(s == 0.0) && ppm_sign(d2c) == s && ppm_sign(d2l) == s && ppm_sign(d2r) == s)
+      lim = s * vmin(fabs(d2), vmin(C * fabs(d2c), vmin(C * fabs(d2l), C * fabs(d2r))));
+    if (s == 0.0) {
+      ql = q0;
+      qr = q0;
+    } else {
+      const T r = lim / d2;
+      ql = q0 + r * (ql - q0);
+      qr = q0 + r * (qr - q0);
+    }
+  } else {
+    const T dl = ql - q0, dr = qr - q0;
+    if (fabs(dl) >= 2.0 * fabs(dr)) ql = q0 - 2.0 * dr;
+    if (fabs(dr) >= 2.0 * fabs(dl)) qr = q0 - 2.0 * dl;
+  }
+}
+
 /* Upwind constrained-transport corner EMF (Gardiner & Stone 2005), for an edge whose two
  * transverse directions are "a" (first) and "b" (second), e.g. E_z at (i-1/2, j-1/2) with a = x,
  * b = y.  The corner value is the mean of the four face values plus one quarter of each of the two
@@ -412,6 +486,8 @@ struct Params {
   int bc[6];  // x-, x+, y-, y+, z-, z+
   double dfloor, pfloor;
   int integrator;
+  int recon;  // reconstruction of the PLM stages: REC_PLM or REC_PPM (VL2 corrector, RK2/RK3 stages)
+  int ng;     // ghost layers: 2 (DC, PLM) or 3 (PPM)
 };
 
 /* dense 3D array (k, j, i), i fastest */
@@ -428,7 +504,6 @@ template <class T> struct Arr3 {
   const T& operator()(int k, int j, int i) const { return v[((size_t)k * n1 + j) * n0 + i]; }
 };
 
-static const int NG = 2;  // ghost layers for second order MHD (Sec. 2.1.1)
 
 template <class T> struct Block {
   int loc[3];
@@ -441,6 +516,7 @@ template <class T> struct Block {
 
 template <class T> struct Mesh {
   Params P;
+  int NG = 2;    // ghost layers (Sec. 2.1.1): 2 for second order, 3 for PPM
   int n[3];      // block active cells
   int nb[3];     // blocks per dim
   int c[3];      // cells with ghosts per dim
@@ -453,6 +529,7 @@ template <class T> struct Mesh {
 
   void init(const Params& p) {
     P = p;
+    NG = p.ng;
     for (int d = 0; d < 3; ++d) {
       n[d] = p.mb[d];
       nb[d] = p.nx[d] / p.mb[d];
@@ -632,7 +709,8 @@ template <class T> struct Mesh {
   /* Fluxes on every face a block needs: faces of direction d from the block's lower to its upper
    * surface, over the active cells plus one ghost layer in the two transverse directions (these
    * feed the corner EMFs on the block surface).  Donor cell: W_L = W_{i-1}, W_R = W_i; PLM: face
-   * values of the van Leer limited linear profiles (Sec. 3.2.1). */
+   * values of the van Leer limited linear profiles; PPM: the right edge of cell i-1 and the left edge
+   * of cell i (Sec. 3.2.1). */
   void compute_fluxes(Block<T>& B, int recon) {
     for (int d = 0; d < 3; ++d) {
       int lo[3], hi[3];
@@ -652,6 +730,19 @@ template <class T> struct Mesh {
               for (int v = 0; v < NW7; ++v) {
                 wl[v] = qm1[v];
                 wr[v] = q0[v];
+              }
+            } else if (recon == REC_PPM) {
+              T qs[6][NW7];  // q_{i-3} .. q_{i+2} along d
+              for (int o = -3; o <= 2; ++o)
+                cell_state(B, d, k + o * sh[2], j + o * sh[1], i + o * sh[0], qs[o + 3]);
+              for (int v = 0; v < NW7; ++v) {
+                const T lo5[5] = {qs[0][v], qs[1][v], qs[2][v], qs[3][v], qs[4][v]};
+                const T hi5[5] = {qs[1][v], qs[2][v], qs[3][v], qs[4][v], qs[5][v]};
+                T ql, qr;
+                ppm_edges(lo5, ql, qr);  // cell i-1
+                wl[v] = qr;
+                ppm_edges(hi5, ql, qr);  // cell i
+                wr[v] = ql;
               }
             } else {
               cell_state(B, d, k - 2 * sh[2], j - 2 * sh[1], i - 2 * sh[0], qm2);
@@ -840,11 +931,11 @@ template <class T> struct Mesh {
     std::vector<Stage> st;
     switch (P.integrator) {
       case INT_RK1: st = {{1.0, 0.0, 1.0, 1.0, REC_DC}}; break;
-      case INT_RK2: st = {{1.0, 0.0, 1.0, 1.0, REC_PLM}, {0.0, 0.5, 0.5, 0.5, REC_PLM}}; break;
+      case INT_RK2: st = {{1.0, 0.0, 1.0, 1.0, P.recon}, {0.0, 0.5, 0.5, 0.5, P.recon}}; break;
       case INT_RK3:
-        st = {{1.0, 0.0, 1.0, 1.0, REC_PLM}, {0.0, 0.25, 0.75, 0.25, REC_PLM}, {0.0, 2.0 / 3.0, 1.0 / 3.0, 2.0 / 3.0, REC_PLM}};
+        st = {{1.0, 0.0, 1.0, 1.0, P.recon}, {0.0, 0.25, 0.75, 0.25, P.recon}, {0.0, 2.0 / 3.0, 1.0 / 3.0, 2.0 / 3.0, P.recon}};
         break;
-      default: st = {{1.0, 0.0, 1.0, 0.5, REC_DC}, {0.0, 0.0, 1.0, 1.0, REC_PLM}}; break;
+      default: st = {{1.0, 0.0, 1.0, 0.5, REC_DC}, {0.0, 0.0, 1.0, 1.0, P.recon}}; break;
     }
     /* u1 <- 0 at the start of every cycle */
     for (auto& B : blk) {
@@ -897,6 +988,7 @@ template <class T> struct Mesh {
 
 template <class T>
 static void set_prims(Mesh<T>& M, const double* w, const double* b1, const double* b2, const double* b3) {
+  const int NG = M.NG;
   const int NX = M.P.nx[0], NY = M.P.nx[1], NZ = M.P.nx[2];
   const size_t ncell = (size_t)NX * NY * NZ;
   for (auto& B : M.blk) {
@@ -938,6 +1030,7 @@ static void set_prims(Mesh<T>& M, const double* w, const double* b1, const doubl
 
 template <class T>
 static void get_cons(const Mesh<T>& M, double* u, double* b1, double* b2, double* b3) {
+  const int NG = M.NG;
   const int NX = M.P.nx[0], NY = M.P.nx[1], NZ = M.P.nx[2];
   const size_t ncell = (size_t)NX * NY * NZ;
   for (const auto& B : M.blk) {
@@ -968,6 +1061,7 @@ static void get_cons(const Mesh<T>& M, double* u, double* b1, double* b2, double
 template <class T>
 static void set_cons(Mesh<T>& M, const double* u, const double* du, const double* b1, const double* db1,
                      const double* b2, const double* db2, const double* b3, const double* db3) {
+  const int NG = M.NG;
   const int NX = M.P.nx[0], NY = M.P.nx[1], NZ = M.P.nx[2];
   const size_t ncell = (size_t)NX * NY * NZ;
   for (auto& B : M.blk) {
@@ -1001,6 +1095,7 @@ static void set_cons(Mesh<T>& M, const double* u, const double* du, const double
 
 /* Tangent parts of the conserved state (global layout), the counterpart of get_cons. */
 static void get_tangent(const Mesh<Dual>& M, double* du, double* db1, double* db2, double* db3) {
+  const int NG = M.NG;
   const int NX = M.P.nx[0], NY = M.P.nx[1], NZ = M.P.nx[2];
   const size_t ncell = (size_t)NX * NY * NZ;
   for (const auto& B : M.blk) {
@@ -1034,8 +1129,12 @@ using orc::Mesh;
 extern "C" {
 
 void* orc_mesh_new(const int* nx, const int* mb, const double* xmin, const double* xmax, double gamma,
-                   int riemann, const int* bc, double dfloor, double pfloor, int integrator) {
+                   int riemann, const int* bc, double dfloor, double pfloor, int integrator, int recon, int ng) {
   orc::Params p;
+  if (recon != orc::REC_PLM && recon != orc::REC_PPM) return nullptr;
+  if (ng < 2 || (recon == orc::REC_PPM && ng < 3)) return nullptr;
+  p.recon = recon;
+  p.ng = ng;
   for (int d = 0; d < 3; ++d) {
     if (nx[d] <= 0 || mb[d] <= 0 || nx[d] % mb[d] != 0) return nullptr;
     p.nx[d] = nx[d];
@@ -1080,7 +1179,7 @@ void orc_get_prims(void* m, double* w) {
       for (int j = 0; j < M.n[1]; ++j)
         for (int i = 0; i < M.n[0]; ++i) {
           const size_t g = ((size_t)(B.loc[2] * M.n[2] + k) * NY + (B.loc[1] * M.n[1] + j)) * NX + (B.loc[0] * M.n[0] + i);
-          for (int v = 0; v < 8; ++v) w[v * ncell + g] = B.w[v](k + orc::NG, j + orc::NG, i + orc::NG);
+          for (int v = 0; v < 8; ++v) w[v * ncell + g] = B.w[v](k + M.NG, j + M.NG, i + M.NG);
         }
 }
 
@@ -1113,7 +1212,7 @@ void orc_debug_fluxes(void* m, int recon, double* fx, double* fy, double* fz) {
             const int li[3] = {i, j, k};
             if (li[d] == M.n[d] && g[d] != N[d]) continue;  // taken from the upper neighbour
             const size_t gi = ((size_t)g[2] * gd[1] + g[1]) * gd[0] + g[0];
-            for (int v = 0; v < orc::NW7; ++v) out[d][v * nf + gi] = B.flx[d][v](k + orc::NG, j + orc::NG, i + orc::NG);
+            for (int v = 0; v < orc::NW7; ++v) out[d][v * nf + gi] = B.flx[d][v](k + M.NG, j + M.NG, i + M.NG);
           }
   }
 }
@@ -1138,7 +1237,7 @@ void orc_debug_emfs(void* m, int recon, double* e1, double* e2, double* e3) {
               if (q != e && li[q] == M.n[q] && g[q] != N[q]) skip = true;
             if (skip) continue;
             const size_t gi = ((size_t)g[2] * gd[1] + g[1]) * gd[0] + g[0];
-            out[e][gi] = B.emf[e](k + orc::NG, j + orc::NG, i + orc::NG);
+            out[e][gi] = B.emf[e](k + M.NG, j + M.NG, i + M.NG);
           }
   }
 }
@@ -1148,7 +1247,7 @@ double orc_divb_norm(void* m) {
   Mesh<double>& M = *static_cast<Mesh<double>*>(m);
   double mx = 0.0, s2 = 0.0;
   size_t cnt = 0;
-  const int G = orc::NG;
+  const int G = M.NG;
   for (const auto& B : M.blk)
     for (int k = G; k < M.n[2] + G; ++k)
       for (int j = G; j < M.n[1] + G; ++j)
@@ -1173,7 +1272,7 @@ void orc_totals(void* m, double* out) {
   Mesh<double>& M = *static_cast<Mesh<double>*>(m);
   const double dv = M.dx[0] * M.dx[1] * M.dx[2];
   double s[8] = {0}, cmp[8] = {0};
-  const int G = orc::NG;
+  const int G = M.NG;
   for (const auto& B : M.blk)
     for (int k = G; k < M.n[2] + G; ++k)
       for (int j = G; j < M.n[1] + G; ++j)
@@ -1216,6 +1315,8 @@ void orc_tl_step(const int* nx, const int* mb, const double* xmin, const double*
   p.dfloor = 1e-12;
   p.pfloor = 1e-12;
   p.integrator = orc::INT_VL2;
+  p.recon = orc::REC_PLM;
+  p.ng = 2;
   orc::Mesh<orc::Dual> M;
   M.init(p);
   orc::set_cons(M, u, du, b1, db1, b2, db2, b3, db3);
@@ -1241,6 +1342,8 @@ void orc_step_cons(const int* nx, const int* mb, const double* xmin, const doubl
   p.dfloor = 1e-12;
   p.pfloor = 1e-12;
   p.integrator = orc::INT_VL2;
+  p.recon = orc::REC_PLM;
+  p.ng = 2;
   orc::Mesh<double> M;
   M.init(p);
   orc::set_cons(M, u, nullptr, b1, nullptr, b2, nullptr, b3, nullptr);
@@ -1280,6 +1383,12 @@ double orc_fast_speed(double d, double p, double bn, double bt1, double bt2, dou
 }
 
 double orc_vanleer_slope(double qm, double q0, double qp) { return orc::vanleer_slope<double>(qm, q0, qp); }
+
+/* PPM edges of one cell from q[0..4] = q_{i-2} .. q_{i+2}: out[0] = left edge, out[1] = right edge. */
+void orc_ppm_edges(const double* q, double* out) { orc::ppm_edges<double>(q, out[0], out[1]); }
+
+/* PPM fourth-order face value between q[1] and q[2] from q[0..3], limited (step 2). */
+double orc_ppm_face(const double* q) { return orc::ppm_face<double>(q[0], q[1], q[2], q[3]); }
 
 /* FP64 operations of one face flux for the given reconstruction and solver, counted with the
  * operation-counting scalar.  q: the 7-component sweep-frame states of cells i-2, i-1, i, i+1
