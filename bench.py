@@ -456,22 +456,30 @@ def adjoint_form(args, dev, stream, vl2, inputs):
 
 
 def integrators_form(args, dev, stream, vl2, inputs):
-    """The other 2S integrators of Sec. 3.2.3 on the plain workload (256^3 vortex, 512 MeshBlocks of 32^3,
-    FP64, HLLD): RK2 (SSPRK(2,2)) and RK3 (SSPRK(3,3)) with PLM in every stage, zone-cycles/s next to VL2's
-    (the bench line).  A cycle has 2 or 3 PLM stages against VL2's donor-cell + PLM."""
+    """The other 2S integrators of Sec. 3.2.3 and PPM (Sec. 3.2.1) on the plain workload (256^3 vortex, 512
+    MeshBlocks of 32^3, FP64, HLLD): RK2 (SSPRK(2,2)) and RK3 (SSPRK(3,3)) with PLM in every stage, and VL2
+    and RK3 with PPM (three ghost layers), zone-cycles/s next to VL2 + PLM (the bench line).  A cycle has 2 or
+    3 PLM / PPM stages against VL2's donor-cell + PLM / PPM."""
     import torch
 
     prob = inputs.orszag_tang(n=args.n, mb=args.mb, seed=2005)
     out = {"config": {"workload": "orszag_tang_3d_%d^3_%dx%d^3_blocks_plm_hlld_ct_fp64" % (
         args.n, (args.n // args.mb) ** 3, args.mb), "steps": args.rk_steps, "dtype": "f64"}}
-    for name, integ in (("rk2", vl2.RK2), ("rk3", vl2.RK3)):
-        m = vl2.Mesh.from_problem(prob, device=dev, stream=stream, integrator=integ)
+    for name, integ, recon in (("rk2", vl2.RK2, vl2.PLM), ("rk3", vl2.RK3, vl2.PLM), ("vl2_ppm", vl2.VL2, vl2.PPM),
+                               ("rk3_ppm", vl2.RK3, vl2.PPM)):
+        m = vl2.Mesh.from_problem(prob, device=dev, stream=stream, integrator=integ, recon=recon)
         for _ in range(2):
             m.step(m.new_dt())
         torch.cuda.synchronize(dev)
         ms, _ = timed_steps(m, args.rk_steps, stream)
+        m.profile(True)
+        m.profile_read()
+        m.step(m.new_dt())
+        prof = {k: v[0] for k, v in m.profile_read().items() if v[1] > 0}
+        m.profile(False)
         out[name] = {"value": prob.ncells * args.rk_steps / (ms / 1e3), "unit": UNIT,
-                     "ms_per_step": ms / args.rk_steps, "floor_events": m.floor_count()}
+                     "ms_per_step": ms / args.rk_steps, "floor_events": m.floor_count(),
+                     "kernel_ms_one_cycle": prof}
         m.close()
         del m
         torch.cuda.empty_cache()

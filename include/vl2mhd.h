@@ -50,7 +50,7 @@ enum { VL2_HLLE = 0, VL2_HLLD = 1 };       /* Riemann solver, Sec. 3.2.2 */
 enum { VL2_PERIODIC = 0, VL2_OUTFLOW = 1 };/* per-face boundary condition */
 enum { VL2_FP64 = 0, VL2_MIXED = 1 };      /* arithmetic of reconstruction, fluxes and EMFs */
 enum { VL2_HOST = 0, VL2_DEVICE = 1 };     /* where a caller buffer lives */
-enum { VL2_DC = 0, VL2_PLM = 1 };          /* reconstruction, Sec. 3.2.1 */
+enum { VL2_DC = 0, VL2_PLM = 1, VL2_PPM = 2 }; /* reconstruction, Sec. 3.2.1 (PPM: eq. ppm-uniform-weights) */
 /* time integrators of the 2S family (Sec. 3.2.3, eq. rk-2s and the coefficient list after it):
  * VL2 (default): donor-cell predictor with beta = 1/2, PLM corrector with beta = 1;
  * RK1: forward Euler with donor-cell fluxes; RK2 (SSPRK(2,2)) and RK3 (SSPRK(3,3)): PLM in every stage. */
@@ -59,7 +59,8 @@ enum { VL2_INT_VL2 = 0, VL2_INT_RK1 = 1, VL2_INT_RK2 = 2, VL2_INT_RK3 = 3 };
 typedef struct vl2_params {
   int nx[3];          /* global active cells (x, y, z); each a multiple of mb[d] */
   int mb[3];          /* MeshBlock active cells (x, y, z), Sec. 2.1: equal for every block */
-  int ng;             /* ghost layers; must be 2 for second-order MHD (Sec. 2.1.1) */
+  int ng;             /* ghost layers (Sec. 2.1.1): 2 for DC / PLM, 3 for PPM (3 also allowed with PLM, same
+                         results); the adjoint needs 2 */
   double xmin[3], xmax[3]; /* domain bounds; cells are uniform, dx_d = (xmax-xmin)/nx */
   double gamma;       /* adiabatic index of the ideal-gas EOS, P = (gamma-1) e (Sec. 3.1) */
   double cfl;         /* Courant number C0 of vl2_new_dt; <= 1/2 for VL2 in 3D (Sec. 3.2.3) */
@@ -73,6 +74,9 @@ typedef struct vl2_params {
   void* stream;       /* cudaStream_t for all device work of this mesh (may be NULL) */
   int adjoint;        /* 1: also reserve the arrays of vl2_step_vjp (VL2_FP64 only); 0: forward only */
   int integrator;     /* VL2_INT_VL2 (0, the default for a zero-initialised struct), VL2_INT_RK1, _RK2, _RK3 */
+  int recon;          /* reconstruction of the higher-order stages (the VL2 corrector, every RK2 / RK3 stage):
+                         VL2_PLM (also 0) or VL2_PPM (needs ng = 3; not with adjoint).  The VL2 predictor and
+                         RK1 always use donor cell (Sec. 3.2.3). */
 } vl2_params;
 
 typedef struct vl2_mesh vl2_mesh;
@@ -169,7 +173,8 @@ vl2_status vl2_totals(vl2_mesh* mesh, double out[8]);
 vl2_status vl2_floor_count(vl2_mesh* mesh, long long* out);
 
 /* Inspection of one stage's terms for the current state (Sec. 3.2.1-3.2.2, 3.1), without updating
- * it: face fluxes of the given reconstruction on the global face grids fx[7][NZ][NY][NX+1],
+ * it: face fluxes of the given reconstruction (VL2_DC, VL2_PLM, or VL2_PPM on a mesh with ng = 3) on the
+ * global face grids fx[7][NZ][NY][NX+1],
  * fy[7][NZ][NY+1][NX], fz[7][NZ+1][NY][NX], components in the sweep frame (mass, M_n, M_t1, M_t2,
  * E, B_t1, B_t2) with (n, t1, t2) = (x, y, z), (y, z, x), (z, x, y).  Errors: VL2_E_ARG, VL2_E_CUDA. */
 vl2_status vl2_debug_fluxes(vl2_mesh* mesh, int recon, double* fx, double* fy, double* fz, int where);
@@ -214,7 +219,8 @@ enum {
   VL2_K_FLUX_PLM = 3, /* PLM + Riemann fluxes of one sweep direction (units: faces) */
   VL2_K_EMF = 4,      /* upwind CT corner EMFs (units: corner nodes) */
   VL2_K_UPDATE = 5,   /* register update of U and the face field (units: nodes) */
-  VL2_K_COUNT = 6
+  VL2_K_FLUX_PPM = 6, /* PPM + Riemann fluxes of one sweep direction (units: faces) */
+  VL2_K_COUNT = 7
 };
 
 /* Per-kernel timing, the measuring side of the paper's zone-cycles-per-second benchmarks (Sec. 3.4.1).

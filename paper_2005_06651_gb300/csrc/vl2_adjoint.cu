@@ -11,6 +11,9 @@
 
 namespace vl2 {
 
+// The adjoint is written for two ghost layers (the API refuses adjoint meshes with another ng).
+constexpr int NG = 2;
+
 static inline unsigned grid_of(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 __device__ __forceinline__ void loc_of(const Geom& g, int b, int* loc) {

@@ -14,7 +14,6 @@
 
 using vl2::Arrays;
 using vl2::Geom;
-using vl2::NG;
 
 struct vl2_mesh {
   vl2_params p;
@@ -46,6 +45,8 @@ struct vl2_mesh {
   bool has_adj = false;
   vl2::MeshView view() const { return vl2::MeshView{g, a}; }
   int max_mb() const { return std::max(g.mb[0], std::max(g.mb[1], g.mb[2])); }
+  // reconstruction of the higher-order stages (params.recon, 0 meaning PLM)
+  int rec() const { return p.recon == VL2_PPM ? VL2_PPM : VL2_PLM; }
   ~vl2_mesh() {
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
   }
@@ -115,8 +116,16 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
       return VL2_E_ARG;
     }
   }
-  if (p->ng != NG) {
-    msg = "ng must be 2";
+  if (p->ng != 2 && p->ng != 3) {
+    msg = "ng must be 2 or 3";
+    return VL2_E_ARG;
+  }
+  if (p->recon != 0 && p->recon != VL2_PLM && p->recon != VL2_PPM) {
+    msg = "recon must be VL2_PLM (or 0) or VL2_PPM";
+    return VL2_E_ARG;
+  }
+  if (p->recon == VL2_PPM && p->ng < 3) {
+    msg = "PPM needs ng = 3 (a face reads three cells on each side)";
     return VL2_E_ARG;
   }
   if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->dfloor >= DBL_MIN) || !(p->pfloor >= DBL_MIN) ||
@@ -144,6 +153,10 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
     msg = "the adjoint (params.adjoint = 1) is written for the VL2 integrator";
     return VL2_E_ARG;
   }
+  if (p->adjoint && (p->ng != 2 || p->recon == VL2_PPM)) {
+    msg = "the adjoint (params.adjoint = 1) is written for PLM with ng = 2";
+    return VL2_E_ARG;
+  }
   for (int d = 0; d < 3; ++d) {
     const int lo = p->bc[2 * d], hi = p->bc[2 * d + 1];
     if ((lo != VL2_PERIODIC && lo != VL2_OUTFLOW) || (hi != VL2_PERIODIC && hi != VL2_OUTFLOW) ||
@@ -167,9 +180,10 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
     return VL2_E_ARG;
   }
   g.nblk = (int)nblk;
-  g.sx = ((p->mb[0] + 2 * NG + 1) + 3) & ~3;
-  g.sy = p->mb[1] + 2 * NG + 1;
-  g.sz = p->mb[2] + 2 * NG + 1;
+  g.ng = p->ng;
+  g.sx = ((p->mb[0] + 2 * g.ng + 1) + 3) & ~3;
+  g.sy = p->mb[1] + 2 * g.ng + 1;
+  g.sz = p->mb[2] + 2 * g.ng + 1;
   g.box = (long long)g.sx * g.sy * g.sz;
   if (g.box * 8 > (1LL << 31)) {
     msg = "MeshBlock too large";
@@ -281,11 +295,11 @@ cudaError_t timed(vl2_mesh* m, int kind, long long units, Fn&& fn) {
 }
 
 long long cells_all(const Geom& g) {
-  return (long long)g.nblk * (g.mb[0] + 2 * NG) * (g.mb[1] + 2 * NG) * (g.mb[2] + 2 * NG);
+  return (long long)g.nblk * (g.mb[0] + 2 * g.ng) * (g.mb[1] + 2 * g.ng) * (g.mb[2] + 2 * g.ng);
 }
 long long nodes(const Geom& g) { return (long long)g.nblk * (g.mb[0] + 1) * (g.mb[1] + 1) * (g.mb[2] + 1); }
 long long ghost_elems(const Geom& g) {
-  return (long long)g.nblk * (g.mb[0] + 2 * NG + 1) * (g.mb[1] + 2 * NG + 1) * (g.mb[2] + 2 * NG + 1);
+  return (long long)g.nblk * (g.mb[0] + 2 * g.ng + 1) * (g.mb[1] + 2 * g.ng + 1) * (g.mb[2] + 2 * g.ng + 1);
 }
 long long flux_faces(const Geom& g, int d) {
   long long n = g.nblk;
@@ -302,7 +316,8 @@ cudaError_t k_ghosts(vl2_mesh* m, int reg) {
 }
 cudaError_t k_fluxes(vl2_mesh* m, int reg, int recon) {
   for (int d = 0; d < 3; ++d) {
-    cudaError_t e = timed(m, recon == VL2_DC ? VL2_K_FLUX_DC : VL2_K_FLUX_PLM, flux_faces(m->g, d), [&] {
+    const int kind = recon == VL2_DC ? VL2_K_FLUX_DC : (recon == VL2_PPM ? VL2_K_FLUX_PPM : VL2_K_FLUX_PLM);
+    cudaError_t e = timed(m, kind, flux_faces(m->g, d), [&] {
       return vl2::launch_flux(m->view(), nullptr, reg, recon, m->p.riemann, d, m->fs, m->max_mb(), m->st);
     });
     if (e != cudaSuccess) return e;
@@ -445,7 +460,7 @@ vl2_status vl2_block_layout(const vl2_mesh* mesh, vl2_layout* out) {
     out->nb[d] = mesh->g.nb[d];
     out->mb[d] = mesh->g.mb[d];
   }
-  out->ng = NG;
+  out->ng = mesh->g.ng;
   out->sx = mesh->g.sx;
   out->sy = mesh->g.sy;
   out->sz = mesh->g.sz;
@@ -625,7 +640,7 @@ vl2_status step_rk(vl2_mesh* m, double dt) {
   static const RkStage rk3[3] = {{0.0, 1.0, 1.0}, {0.25, 0.75, 0.25}, {2.0 / 3.0, 1.0 / 3.0, 2.0 / 3.0}};
   const RkStage* st = m->p.integrator == VL2_INT_RK1 ? rk1 : (m->p.integrator == VL2_INT_RK2 ? rk2 : rk3);
   const int ns = m->p.integrator == VL2_INT_RK1 ? 1 : (m->p.integrator == VL2_INT_RK2 ? 2 : 3);
-  const int recon = m->p.integrator == VL2_INT_RK1 ? VL2_DC : VL2_PLM;
+  const int recon = m->p.integrator == VL2_INT_RK1 ? VL2_DC : m->rec();
   const Geom& g = m->g;
   const size_t per = (size_t)g.nblk * g.box * sizeof(double);
   // u^(1) = U^n (every element, so that register 1 is a complete copy)
@@ -660,8 +675,8 @@ vl2_status vl2_step(vl2_mesh* m, double dt) {
   VL2_CHECK(m, k_update(m, 0, 1, 0.5 * dt));
   VL2_CHECK(m, k_ghosts(m, 1));
   VL2_CHECK(m, k_prim(m, 1, false));
-  // corrector: U^{n+1} = U^n + dt L_PLM(U*) in place in register 0
-  VL2_CHECK(m, k_fluxes(m, 1, VL2_PLM));
+  // corrector: U^{n+1} = U^n + dt L_PLM(U*) (or L_PPM) in place in register 0
+  VL2_CHECK(m, k_fluxes(m, 1, m->rec()));
   VL2_CHECK(m, k_emfs(m));
   VL2_CHECK(m, k_update(m, 0, 0, dt));
   VL2_CHECK(m, k_ghosts(m, 0));
@@ -783,7 +798,8 @@ static vl2_status gather_out(vl2_mesh* m, int kind, int dir, double* out, long l
 
 vl2_status vl2_debug_fluxes(vl2_mesh* m, int recon, double* fx, double* fy, double* fz, int where) {
   if (!m || !fx || !fy || !fz) return fail(m, VL2_E_ARG, "NULL argument");
-  if (bad_where(where) || (recon != VL2_DC && recon != VL2_PLM)) return fail(m, VL2_E_ARG, "bad where or recon");
+  if (bad_where(where) || (recon != VL2_DC && recon != VL2_PLM && !(recon == VL2_PPM && m->g.ng >= 3)))
+    return fail(m, VL2_E_ARG, "bad where or recon (PPM needs ng = 3)");
   if (!m->initialized) return fail(m, VL2_E_STATE, "vl2_set_prims has not been called");
   vl2_status s = ensure_prims(m);
   if (s != VL2_OK) return s;
@@ -800,7 +816,8 @@ vl2_status vl2_debug_fluxes(vl2_mesh* m, int recon, double* fx, double* fy, doub
 
 vl2_status vl2_debug_emfs(vl2_mesh* m, int recon, double* e1, double* e2, double* e3, int where) {
   if (!m || !e1 || !e2 || !e3) return fail(m, VL2_E_ARG, "NULL argument");
-  if (bad_where(where) || (recon != VL2_DC && recon != VL2_PLM)) return fail(m, VL2_E_ARG, "bad where or recon");
+  if (bad_where(where) || (recon != VL2_DC && recon != VL2_PLM && !(recon == VL2_PPM && m->g.ng >= 3)))
+    return fail(m, VL2_E_ARG, "bad where or recon (PPM needs ng = 3)");
   if (!m->initialized) return fail(m, VL2_E_STATE, "vl2_set_prims has not been called");
   vl2_status s = ensure_prims(m);
   if (s != VL2_OK) return s;
@@ -872,6 +889,7 @@ struct vl2_batch {
   vl2::FluxShape fs;
   int max_mb = 1;
   int riemann = VL2_HLLD;
+  int recon = VL2_PLM;  // reconstruction of the corrector
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_steps = 0;
@@ -952,8 +970,9 @@ vl2_status batch_check(vl2_mesh* const* meshes, int n, std::string& msg) {
       msg = "the batched form runs the VL2 integrator";
       return VL2_E_ARG;
     }
-    if (meshes[q]->p.riemann != meshes[0]->p.riemann || meshes[q]->p.precision != meshes[0]->p.precision) {
-      msg = "all meshes of a batch need the same Riemann solver and precision";
+    if (meshes[q]->p.riemann != meshes[0]->p.riemann || meshes[q]->p.precision != meshes[0]->p.precision ||
+        meshes[q]->rec() != meshes[0]->rec()) {
+      msg = "all meshes of a batch need the same Riemann solver, precision and reconstruction";
       return VL2_E_ARG;
     }
   }
@@ -1033,7 +1052,7 @@ cudaError_t batch_cycle(vl2_batch* B, bool device_dt) {
   if ((e = vl2::launch_update(v0, &dn, 0, 1, 0.0, B->ddt, 0.5, B->cur)) != cudaSuccess) return e;
   if ((e = vl2::launch_ghosts(v0, &dg, 1, B->cur)) != cudaSuccess) return e;
   if ((e = vl2::launch_prim(v0, &dp, 1, true, false, B->cur)) != cudaSuccess) return e;
-  if ((e = batch_fluxes(B, 1, VL2_PLM)) != cudaSuccess) return e;
+  if ((e = batch_fluxes(B, 1, B->recon)) != cudaSuccess) return e;
   if ((e = vl2::launch_emfs(v0, &dn, B->cur)) != cudaSuccess) return e;
   if ((e = vl2::launch_update(v0, &dn, 0, 0, 0.0, B->ddt, 1.0, B->cur)) != cudaSuccess) return e;
   if ((e = vl2::launch_ghosts(v0, &dg, 0, B->cur)) != cudaSuccess) return e;
@@ -1100,6 +1119,7 @@ vl2_status vl2_batch_create(vl2_mesh* const* meshes, int n, void* workspace, siz
     return bfail(nullptr, VL2_E_CUDA, "batch stream/event creation failed");
   }
   B->riemann = meshes[0]->p.riemann;
+  B->recon = meshes[0]->rec();
   for (vl2_mesh* m : B->meshes) B->max_mb = std::max(B->max_mb, m->max_mb());
   const BatchPlan pl = batch_plan(B->meshes, B->max_mb);
   if (bytes < pl.total) {
@@ -1161,7 +1181,7 @@ vl2_status vl2_batch_autotune(vl2_batch* B, int* dc_threads, int* plm_lines) {
       for (int rep = 0; rep < 3; ++rep) {  // the flux launches only write flux scratch: the state is untouched
         VL2_BCHECK(B, cudaEventRecord(e0, B->st));
         VL2_BCHECK(B, batch_fluxes(B, 0, VL2_DC));
-        VL2_BCHECK(B, batch_fluxes(B, 0, VL2_PLM));
+        VL2_BCHECK(B, batch_fluxes(B, 0, B->recon));
         VL2_BCHECK(B, cudaEventRecord(e1, B->st));
         VL2_BCHECK(B, cudaEventSynchronize(e1));
         float ms = 0.f;

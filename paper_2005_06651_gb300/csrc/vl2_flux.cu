@@ -27,10 +27,10 @@ __global__ void __launch_bounds__(256) k_flux(MeshView single, const MeshView* v
   if (t >= per * g.nblk) return;
   const int b = (int)(t / per);
   int rem = (int)(t - (long long)b * per);
-  const int i = rem % rx + (DIR == 0 ? NG : NG - 1);
+  const int i = rem % rx + (DIR == 0 ? g.ng : g.ng - 1);
   rem /= rx;
-  const int j = rem % ry + (DIR == 1 ? NG : NG - 1);
-  const int k = rem / ry + (DIR == 2 ? NG : NG - 1);
+  const int j = rem % ry + (DIR == 1 ? g.ng : g.ng - 1);
+  const int k = rem / ry + (DIR == 2 ? g.ng : g.ng - 1);
   const long long c = cell_off(g, k, j, i);
   const long long sd = (DIR == 0) ? 1LL : ((DIR == 1) ? (long long)g.sx : (long long)g.sx * g.sy);
   const T* Wb = static_cast<const T*>(V.a.w) + (long long)b * 8 * g.box;
@@ -60,12 +60,13 @@ __global__ void __launch_bounds__(256) k_flux(MeshView single, const MeshView* v
 }
 
 // ------------------------------------------------------------------------------------------------
-// Corrector fluxes with each cell's PLM reconstruction formed once (Sec. 3.2.1).  A CTA takes P lines
-// of faces along DIR: phase A reconstructs the mb+2 cells of each line (ng-1 .. ng+mb) into shared
-// memory (face values q -+ delta/2 of 7 variables), phase B solves the mb+1 Riemann problems of each line
-// from shared memory.  In FP64 the 7 limiter denominators of a cell share one division (simultaneous
-// inversion: the reciprocal of their product and of its prefix products); a product outside the normal
-// range falls back to one division per variable.
+// Corrector fluxes with each cell's reconstruction formed once (Sec. 3.2.1).  A CTA takes P lines of faces
+// along DIR: phase A reconstructs the mb+2 cells of each line (ng-1 .. ng+mb) into shared memory (the
+// cell's values at its lower and upper faces, 7 variables), phase B solves the mb+1 Riemann problems of each
+// line from shared memory.  PLM: q -+ delta/2; in FP64 the 7 limiter denominators of a cell share one
+// division (simultaneous inversion: the reciprocal of their product and of its prefix products), and a
+// product outside the normal range falls back to one division per variable.  PPM (ng = 3): the limited
+// parabola's edges from the cell and two neighbours on each side.
 // ------------------------------------------------------------------------------------------------
 template <int DIR>
 struct LineMap {
@@ -79,7 +80,7 @@ __device__ __forceinline__ bool normal_pos(double x) {
   return e != 0 && e != 0x7ff;
 }
 
-template <int DIR, int RS, class T>
+template <int DIR, int RS, class T, int REC>
 __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const MeshView* views, const WorkItem* work,
                                                      int reg, int P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -112,10 +113,21 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
     const int line = tile * P + p;
     if (line >= nlines) continue;
     int li[3];
-    li[DIR] = NG - 1 + c;
-    li[TA] = NG - 1 + line % na;
-    li[TB] = NG - 1 + line / na;
+    li[DIR] = g.ng - 1 + c;
+    li[TA] = g.ng - 1 + line % na;
+    li[TB] = g.ng - 1 + line / na;
     const long long o = cell_off(g, li[2], li[1], li[0]);
+    if (REC == REC_PPM) {
+#pragma unroll
+      for (int n = 0; n < 7; ++n) {
+        const T* q = Wb + (long long)var[n] * g.box + o;
+        T ql, qr;
+        ppm_edges(q[-2 * sd], q[-sd], q[0], q[sd], q[2 * sd], ql, qr);
+        smem[sidx(n, 0, p, c)] = ql;
+        smem[sidx(n, 1, p, c)] = qr;
+      }
+      continue;
+    }
     T q0[7], dl[7], dr[7], den[7];
     bool pos[7];
 #pragma unroll
@@ -166,9 +178,9 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
     const int line = tile * P + p;
     if (line >= nlines) continue;
     int li[3];
-    li[DIR] = NG + f;
-    li[TA] = NG - 1 + line % na;
-    li[TB] = NG - 1 + line / na;
+    li[DIR] = g.ng + f;
+    li[TA] = g.ng - 1 + line % na;
+    li[TB] = g.ng - 1 + line / na;
     const long long o = cell_off(g, li[2], li[1], li[0]);
     T wl[7], wr[7];
 #pragma unroll
@@ -228,14 +240,18 @@ template <int DIR, int RS, class T>
 static cudaError_t launch_typed(const MeshView& v, const Dispatch* d, int reg, int recon, const FluxShape& fs,
                                 int max_mb, cudaStream_t st) {
   const Geom& g = v.g;
-  if (recon == REC_PLM) {
+  if (recon == REC_PLM || recon == REC_PPM) {
     FluxShape f2 = fs;
     f2.plm_lines = plm_lines_for(g, DIR, fs, max_mb);
     const size_t shmem = (size_t)f2.plm_lines * (max_mb + 2) * 14 * sizeof(T);
     const long long grid = d ? d->nwork : tiles_flux_plm(g, DIR, f2);
     if (grid <= 0) return cudaSuccess;
-    k_flux_plm<DIR, RS, T><<<(unsigned)grid, 256, shmem, st>>>(v, d ? d->views : nullptr, d ? d->work : nullptr, reg,
-                                                              f2.plm_lines);
+    if (recon == REC_PPM)
+      k_flux_plm<DIR, RS, T, REC_PPM><<<(unsigned)grid, 256, shmem, st>>>(v, d ? d->views : nullptr,
+                                                                         d ? d->work : nullptr, reg, f2.plm_lines);
+    else
+      k_flux_plm<DIR, RS, T, REC_PLM><<<(unsigned)grid, 256, shmem, st>>>(v, d ? d->views : nullptr,
+                                                                         d ? d->work : nullptr, reg, f2.plm_lines);
     return cudaGetLastError();
   }
   const long long grid = d ? d->nwork : tiles_flux_dc(g, DIR, fs);
@@ -266,8 +282,9 @@ cudaError_t launch_flux(const MeshView& v, const Dispatch* d, int reg, int recon
 // current device before any launch (and so before any stream capture).
 cudaError_t prepare_kernel_attributes() {
   cudaError_t e = cudaSuccess;
-#define VL2_ATTR(DIR, RS, T) \
-  if (e == cudaSuccess) e = set_smem_attr(k_flux_plm<DIR, RS, T>);
+#define VL2_ATTR(DIR, RS, T)                                                      \
+  if (e == cudaSuccess) e = set_smem_attr(k_flux_plm<DIR, RS, T, REC_PLM>);     \
+  if (e == cudaSuccess) e = set_smem_attr(k_flux_plm<DIR, RS, T, REC_PPM>);
   VL2_ATTR(0, RS_HLLD, double) VL2_ATTR(1, RS_HLLD, double) VL2_ATTR(2, RS_HLLD, double)
   VL2_ATTR(0, RS_HLLE, double) VL2_ATTR(1, RS_HLLE, double) VL2_ATTR(2, RS_HLLE, double)
   VL2_ATTR(0, RS_HLLD, float) VL2_ATTR(1, RS_HLLD, float) VL2_ATTR(2, RS_HLLD, float)

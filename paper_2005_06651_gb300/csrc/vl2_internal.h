@@ -6,10 +6,9 @@
 
 namespace vl2 {
 
-constexpr int NG = 2;  // ghost layers for second-order MHD (Sec. 2.1.1)
 
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
-enum { REC_DC = 0, REC_PLM = 1 };
+enum { REC_DC = 0, REC_PLM = 1, REC_PPM = 2 };
 enum { RS_HLLE = 0, RS_HLLD = 1 };
 
 // Mesh geometry passed by value to every kernel.
@@ -17,6 +16,7 @@ struct Geom {
   int nblk;            // number of MeshBlocks
   int nb[3];           // blocks per direction
   int mb[3];           // active cells per block
+  int ng;              // ghost layers (Sec. 2.1.1): 2, or 3 for PPM
   int sx, sy, sz;      // padded per-block box extents (cells incl. ghosts + 1 face, x row padded)
   long long box;       // sx * sy * sz elements per block per variable
   int N[3];            // global active cells

@@ -32,8 +32,8 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
   int tile;
   const MeshView& V = stage_view(sv, single, views, work, tile);
   const Geom& g = V.g;
-  const int off = all ? 0 : NG;
-  const int ex = g.mb[0] + (all ? 2 * NG : 0), ey = g.mb[1] + (all ? 2 * NG : 0), ez = g.mb[2] + (all ? 2 * NG : 0);
+  const int off = all ? 0 : g.ng;
+  const int ex = g.mb[0] + (all ? 2 * g.ng : 0), ey = g.mb[1] + (all ? 2 * g.ng : 0), ez = g.mb[2] + (all ? 2 * g.ng : 0);
   const long long per = (long long)ex * ey * ez;
   const long long t = (long long)tile * blockDim.x + threadIdx.x;
   // kept for the CFL rate: the cell's FP64 primitives and a single-precision estimate of its rate
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
     double d = Ub[0];
     const double m1 = Ub[g.box], m2 = Ub[2 * g.box], m3 = Ub[3 * g.box];
     double e = Ub[4 * g.box];
-    active = i >= NG && i < NG + g.mb[0] && j >= NG && j < NG + g.mb[1] && k >= NG && k < NG + g.mb[2];
+    active = i >= g.ng && i < g.ng + g.mb[0] && j >= g.ng && j < g.ng + g.mb[1] && k >= g.ng && k < g.ng + g.mb[2];
     bool fired = false;
     if (d < g.dfloor) {
       d = g.dfloor;
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
 }
 
 long long tiles_prim(const Geom& g) {
-  return ((long long)(g.mb[0] + 2 * NG) * (g.mb[1] + 2 * NG) * (g.mb[2] + 2 * NG) * g.nblk + THREADS - 1) / THREADS;
+  return ((long long)(g.mb[0] + 2 * g.ng) * (g.mb[1] + 2 * g.ng) * (g.mb[2] + 2 * g.ng) * g.nblk + THREADS - 1) / THREADS;
 }
 
 cudaError_t launch_prim(const MeshView& v, const Dispatch* d, int reg, bool all_cells, bool want_dt, cudaStream_t st) {
@@ -224,25 +224,25 @@ __device__ __forceinline__ void source_of(const Geom& g, int q, int gi, bool fac
   }
   if (face && m == N) {
     blk = g.nb[q] - 1;
-    loc = g.mb[q] + NG;
+    loc = g.mb[q] + g.ng;
   } else {
     blk = m / g.mb[q];
-    loc = m - blk * g.mb[q] + NG;
+    loc = m - blk * g.mb[q] + g.ng;
   }
 }
 
 // Ghost elements lie in the shell of the padded box: index triples 0 .. mb+2NG (one more than the cells,
-// for the faces) with at least one coordinate outside the interior NG .. NG+mb-1.  A thread per shell
+// for the faces) with at least one coordinate outside the interior g.ng .. g.ng+mb-1.  A thread per shell
 // element; the shell is decoded as z-slabs (k outside the interior), then y-slabs (k inside, j outside),
 // then x-slabs (k, j inside, i outside).
 __device__ __forceinline__ long long shell_size(const Geom& g) {
-  const long long ex = g.mb[0] + 2 * NG + 1, ey = g.mb[1] + 2 * NG + 1, ez = g.mb[2] + 2 * NG + 1;
+  const long long ex = g.mb[0] + 2 * g.ng + 1, ey = g.mb[1] + 2 * g.ng + 1, ez = g.mb[2] + 2 * g.ng + 1;
   return ex * ey * ez - (long long)g.mb[0] * g.mb[1] * g.mb[2];
 }
 __device__ __forceinline__ void shell_index(const Geom& g, int s, int* li) {
-  const int ex = g.mb[0] + 2 * NG + 1, ey = g.mb[1] + 2 * NG + 1, ez = g.mb[2] + 2 * NG + 1;
+  const int ex = g.mb[0] + 2 * g.ng + 1, ey = g.mb[1] + 2 * g.ng + 1, ez = g.mb[2] + 2 * g.ng + 1;
   const int gx = ex - g.mb[0], gy = ey - g.mb[1], gz = ez - g.mb[2];  // ghost layers per direction
-  auto unfold = [&](int gidx, int q) { return gidx < NG ? gidx : gidx + g.mb[q]; };
+  auto unfold = [&](int gidx, int q) { return gidx < g.ng ? gidx : gidx + g.mb[q]; };
   const int nz = gz * ey * ex;
   if (s < nz) {
     li[2] = unfold(s / (ey * ex), 2);
@@ -254,16 +254,16 @@ __device__ __forceinline__ void shell_index(const Geom& g, int s, int* li) {
   s -= nz;
   const int ny = g.mb[2] * gy * ex;
   if (s < ny) {
-    li[2] = s / (gy * ex) + NG;
+    li[2] = s / (gy * ex) + g.ng;
     const int r = s % (gy * ex);
     li[1] = unfold(r / ex, 1);
     li[0] = r % ex;
     return;
   }
   s -= ny;
-  li[2] = s / (g.mb[1] * gx) + NG;
+  li[2] = s / (g.mb[1] * gx) + g.ng;
   const int r = s % (g.mb[1] * gx);
-  li[1] = r / gx + NG;
+  li[1] = r / gx + g.ng;
   li[0] = unfold(r % gx, 0);
 }
 
@@ -285,15 +285,15 @@ __global__ void __launch_bounds__(256) k_ghosts(MeshView single, const MeshView*
   int loc[3];
   block_loc(g, b, loc);
   const long long c = cell_off(g, li[2], li[1], li[0]);
-  const int cmax[3] = {g.mb[0] + 2 * NG, g.mb[1] + 2 * NG, g.mb[2] + 2 * NG};
+  const int cmax[3] = {g.mb[0] + 2 * g.ng, g.mb[1] + 2 * g.ng, g.mb[2] + 2 * g.ng};
   // source block and index of each coordinate as a cell index (faces re-map their own direction)
   int sb[3], sl[3];
 #pragma unroll
-  for (int q = 0; q < 3; ++q) source_of(g, q, loc[q] * g.mb[q] + li[q] - NG, false, sb[q], sl[q]);
+  for (int q = 0; q < 3; ++q) source_of(g, q, loc[q] * g.mb[q] + li[q] - g.ng, false, sb[q], sl[q]);
   // cell-centred conserved variables
   if (li[0] < cmax[0] && li[1] < cmax[1] && li[2] < cmax[2]) {
     bool ghost = false;
-    for (int q = 0; q < 3; ++q) ghost |= (li[q] < NG || li[q] >= NG + g.mb[q]);
+    for (int q = 0; q < 3; ++q) ghost |= (li[q] < g.ng || li[q] >= g.ng + g.mb[q]);
     if (ghost) {
       const int src = (sb[2] * g.nb[1] + sb[1]) * g.nb[0] + sb[0];
       const long long sc = cell_off(g, sl[2], sl[1], sl[0]);
@@ -310,20 +310,20 @@ __global__ void __launch_bounds__(256) k_ghosts(MeshView single, const MeshView*
     bool valid = true, ghost = false;
     for (int q = 0; q < 3; ++q) {
       const int hi_valid = (q == fd) ? cmax[q] : cmax[q] - 1;
-      const int hi_active = (q == fd) ? NG + g.mb[q] : NG + g.mb[q] - 1;
+      const int hi_active = (q == fd) ? g.ng + g.mb[q] : g.ng + g.mb[q] - 1;
       valid &= li[q] <= hi_valid;
-      ghost |= (li[q] < NG || li[q] > hi_active);
+      ghost |= (li[q] < g.ng || li[q] > hi_active);
     }
     if (!valid || !ghost) continue;
     int fb[3] = {sb[0], sb[1], sb[2]}, fl[3] = {sl[0], sl[1], sl[2]};
-    source_of(g, fd, loc[fd] * g.mb[fd] + li[fd] - NG, true, fb[fd], fl[fd]);
+    source_of(g, fd, loc[fd] * g.mb[fd] + li[fd] - g.ng, true, fb[fd], fl[fd]);
     const int src = (fb[2] * g.nb[1] + fb[1]) * g.nb[0] + fb[0];
     Bf[fd][(long long)b * g.box + c] = Bf[fd][(long long)src * g.box + cell_off(g, fl[2], fl[1], fl[0])];
   }
 }
 
 long long tiles_ghosts(const Geom& g) {
-  const long long per = (long long)(g.mb[0] + 2 * NG + 1) * (g.mb[1] + 2 * NG + 1) * (g.mb[2] + 2 * NG + 1) -
+  const long long per = (long long)(g.mb[0] + 2 * g.ng + 1) * (g.mb[1] + 2 * g.ng + 1) * (g.mb[2] + 2 * g.ng + 1) -
                         (long long)g.mb[0] * g.mb[1] * g.mb[2];
   return (per * g.nblk + THREADS - 1) / THREADS;
 }
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(256) k_emf(MeshView single, const MeshView* vi
   if (t >= per * g.nblk) return;
   const int b = (int)(t / per);
   int rem = (int)(t - (long long)b * per);
-  const int li[3] = {rem % ex + NG, (rem / ex) % ey + NG, rem / (ex * ey) + NG};
+  const int li[3] = {rem % ex + g.ng, (rem / ex) % ey + g.ng, rem / (ex * ey) + g.ng};
   const long long c = cell_off(g, li[2], li[1], li[0]);
   const long long stride[3] = {1LL, (long long)g.sx, (long long)g.sx * g.sy};
   const T* F[3] = {F0, F1, F2};
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(256) k_emf(MeshView single, const MeshView* vi
   const T* Ecb = static_cast<const T*>(V.a.ec) + (long long)b * 3 * g.box;
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
-    if (li[e] > NG + g.mb[e] - 1) continue;
+    if (li[e] > g.ng + g.mb[e] - 1) continue;
     const int a = (e + 1) % 3, bq = (e + 2) % 3;
     const long long sa = stride[a], sb = stride[bq];
     const T* Fa = F[a] + (long long)b * 7 * g.box;
@@ -443,10 +443,10 @@ __global__ void __launch_bounds__(256) k_update(MeshView single, const MeshView*
   if (t >= per * g.nblk) return;
   const int b = (int)(t / per);
   int rem = (int)(t - (long long)b * per);
-  const int li[3] = {rem % ex + NG, (rem / ex) % ey + NG, rem / (ex * ey) + NG};
+  const int li[3] = {rem % ex + g.ng, (rem / ex) % ey + g.ng, rem / (ex * ey) + g.ng};
   const long long c = cell_off(g, li[2], li[1], li[0]);
   const long long stride[3] = {1LL, (long long)g.sx, (long long)g.sx * g.sy};
-  const bool inside[3] = {li[0] < NG + g.mb[0], li[1] < NG + g.mb[1], li[2] < NG + g.mb[2]};
+  const bool inside[3] = {li[0] < g.ng + g.mb[0], li[1] < g.ng + g.mb[1], li[2] < g.ng + g.mb[2]};
   if (inside[0] && inside[1] && inside[2]) {
     const T* F[3] = {F0 + (long long)b * 7 * g.box + c, F1 + (long long)b * 7 * g.box + c,
                      F2 + (long long)b * 7 * g.box + c};
@@ -546,7 +546,7 @@ __global__ void __launch_bounds__(256) k_scatter_prims(Geom g, double* U, double
   IoIdx x;
   if (!io_index(g, x)) return;
   const int NX = g.N[0], NY = g.N[1], NZ = g.N[2];
-  const long long c = cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG);
+  const long long c = cell_off(g, x.li[2] + g.ng, x.li[1] + g.ng, x.li[0] + g.ng);
   const long long o = (long long)x.b * g.box + c;
   const bool in[3] = {x.li[0] < g.mb[0], x.li[1] < g.mb[1], x.li[2] < g.mb[2]};
   const long long f1 = ((long long)x.gi[2] * NY + x.gi[1]) * (NX + 1) + x.gi[0];
@@ -583,7 +583,7 @@ __global__ void __launch_bounds__(256) k_scatter_cons(Geom g, double* U, double*
   IoIdx x;
   if (!io_index(g, x)) return;
   const int NX = g.N[0], NY = g.N[1], NZ = g.N[2];
-  const long long c = cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG);
+  const long long c = cell_off(g, x.li[2] + g.ng, x.li[1] + g.ng, x.li[0] + g.ng);
   const long long o = (long long)x.b * g.box + c;
   const bool in[3] = {x.li[0] < g.mb[0], x.li[1] < g.mb[1], x.li[2] < g.mb[2]};
   if (in[1] && in[2]) B0[o] = b1[((long long)x.gi[2] * NY + x.gi[1]) * (NX + 1) + x.gi[0]];
@@ -637,7 +637,7 @@ __global__ void __launch_bounds__(256) k_gather_cons(Geom g, const double* __res
   IoIdx x;
   if (!io_index(g, x)) return;
   const int NX = g.N[0], NY = g.N[1], NZ = g.N[2];
-  const long long c = cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG);
+  const long long c = cell_off(g, x.li[2] + g.ng, x.li[1] + g.ng, x.li[0] + g.ng);
   const long long o = (long long)x.b * g.box + c;
   const bool in[3] = {x.li[0] < g.mb[0], x.li[1] < g.mb[1], x.li[2] < g.mb[2]};
   const bool own[3] = {in[0] || x.gi[0] == NX, in[1] || x.gi[1] == NY, in[2] || x.gi[2] == NZ};
@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(256) k_gather_prims(Geom g, const T* __restric
   const int NX = g.N[0], NY = g.N[1], NZ = g.N[2];
   const long long n = (long long)NX * NY * NZ;
   const long long gc = ((long long)x.gi[2] * NY + x.gi[1]) * NX + x.gi[0];
-  const T* Wb = W + (long long)x.b * 8 * g.box + cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG);
+  const T* Wb = W + (long long)x.b * 8 * g.box + cell_off(g, x.li[2] + g.ng, x.li[1] + g.ng, x.li[0] + g.ng);
 #pragma unroll
   for (int v = 0; v < 8; ++v) w[v * n + gc] = (double)Wb[(long long)v * g.box];
 }
@@ -697,7 +697,7 @@ __global__ void __launch_bounds__(256) k_gather_fluxes(Geom g, int dir, const T*
   }
   const long long nf = (long long)gd[0] * gd[1] * gd[2];
   const long long gf = ((long long)x.gi[2] * gd[1] + x.gi[1]) * gd[0] + x.gi[0];
-  const T* Fb = F + (long long)x.b * 7 * g.box + cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG);
+  const T* Fb = F + (long long)x.b * 7 * g.box + cell_off(g, x.li[2] + g.ng, x.li[1] + g.ng, x.li[0] + g.ng);
 #pragma unroll
   for (int n = 0; n < 7; ++n) out[n * nf + gf] = (double)Fb[(long long)n * g.box];
 }
@@ -724,7 +724,7 @@ __global__ void __launch_bounds__(256) k_gather_emfs(Geom g, int e, const T* __r
     }
   }
   const long long gf = ((long long)x.gi[2] * gd[1] + x.gi[1]) * gd[0] + x.gi[0];
-  out[gf] = (double)E[(long long)x.b * g.box + cell_off(g, x.li[2] + NG, x.li[1] + NG, x.li[0] + NG)];
+  out[gf] = (double)E[(long long)x.b * g.box + cell_off(g, x.li[2] + g.ng, x.li[1] + g.ng, x.li[0] + g.ng)];
 }
 
 cudaError_t launch_gather_emfs(const Geom& g, const Arrays& a, int dir, double* out, cudaStream_t st) {
@@ -745,10 +745,10 @@ __device__ __forceinline__ void active_cell(const Geom& g, long long t, int& b, 
   const long long per = (long long)g.mb[0] * g.mb[1] * g.mb[2];
   b = (int)(t / per);
   int rem = (int)(t - (long long)b * per);
-  const int i = rem % g.mb[0] + NG;
+  const int i = rem % g.mb[0] + g.ng;
   rem /= g.mb[0];
-  const int j = rem % g.mb[1] + NG;
-  const int k = rem / g.mb[1] + NG;
+  const int j = rem % g.mb[1] + g.ng;
+  const int k = rem / g.mb[1] + g.ng;
   c = cell_off(g, k, j, i);
 }
 

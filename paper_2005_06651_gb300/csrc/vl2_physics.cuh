@@ -338,6 +338,63 @@ __device__ __forceinline__ R vl_slope(R qm, R q0, R qp) {
   return gt0(pr) ? (R(2) * pr) / (dl + dr) : R(0);
 }
 
+// PPM (Sec. 3.2.1).  Face value: eq. ppm-uniform-weights, q_{i-1/2} = 7/12 (q_{i-1} + q_i) - 1/12 (q_{i-2} + q_{i+1});
+// a face value outside the range of its two cells becomes (q_{i-1} + q_i)/2 - D2lim/6 with
+// D2 = 3 (q_{i-1} + q_i - 2 q_{i-1/2}) limited by the neighbouring second differences (factor C = 1.25) when
+// all share its sign, else 0 (Colella & Sekora 2008).  Cell: at an extremum the parabola's second
+// derivative 6 (qL + qR - 2 q_i) is limited the same way against the second differences of the cells around
+// and both edges move towards q_i by D2lim / D2; elsewhere an edge more than twice as far from q_i as the
+// other is pulled in to twice that distance.  Second differences are (outer sum) - 2 middle, so mirrored
+// inputs give mirrored results; comparisons run on the integer pipe.
+template <class R> __device__ __forceinline__ int sgn3(R x) { return gt0(x) ? 1 : (lt0(x) ? -1 : 0); }
+template <class R> __device__ __forceinline__ bool ige(R a, R b) { return okey(a) >= okey(b); }
+
+template <class R>
+__device__ __forceinline__ R ppm_face(R qm2, R qm1, R q0, R qp1) {
+  const R C = R(1.25);
+  R f = R(7.0 / 12.0) * (qm1 + q0) - R(1.0 / 12.0) * (qm2 + qp1);
+  if (lt0((f - qm1) * (q0 - f))) {
+    const R d2 = R(3) * ((qm1 + q0) - R(2) * f);
+    const R d2l = (qm2 + q0) - R(2) * qm1;
+    const R d2r = (qm1 + qp1) - R(2) * q0;
+    const int s = sgn3(d2);
+    R lim = R(0);
+    if (s != 0 && sgn3(d2l) == s && sgn3(d2r) == s)
+      lim = R(s) * imin(fabs(d2), imin(C * fabs(d2l), C * fabs(d2r)));
+    f = R(0.5) * (qm1 + q0) - lim * R(1.0 / 6.0);
+  }
+  return f;
+}
+
+template <class R>
+__device__ __forceinline__ void ppm_edges(R qm2, R qm1, R q0, R qp1, R qp2, R& ql, R& qr) {
+  const R C = R(1.25);
+  ql = ppm_face(qm2, qm1, q0, qp1);
+  qr = ppm_face(qm1, q0, qp1, qp2);
+  if (!gt0((qr - q0) * (q0 - ql)) || !gt0((qp1 - q0) * (q0 - qm1))) {  // an extremum
+    const R d2 = R(6) * ((ql + qr) - R(2) * q0);
+    const R d2c = (qm1 + qp1) - R(2) * q0;
+    const R d2l = (qm2 + q0) - R(2) * qm1;
+    const R d2r = (q0 + qp2) - R(2) * qp1;
+    const int s = sgn3(d2);
+    if (s == 0) {
+      ql = q0;
+      qr = q0;
+    } else {
+      R lim = R(0);
+      if (sgn3(d2c) == s && sgn3(d2l) == s && sgn3(d2r) == s)
+        lim = R(s) * imin(fabs(d2), imin(C * fabs(d2c), imin(C * fabs(d2l), C * fabs(d2r))));
+      const R r = lim * inv(d2);
+      ql = q0 + r * (ql - q0);
+      qr = q0 + r * (qr - q0);
+    }
+  } else {
+    const R dl = ql - q0, dr = qr - q0;
+    if (ige(fabs(dl), R(2) * fabs(dr))) ql = q0 - R(2) * dr;
+    if (ige(fabs(dr), R(2) * fabs(dl))) qr = q0 - R(2) * dl;
+  }
+}
+
 // Upwind CT corner EMF (Gardiner & Stone 2005) for an edge with transverse directions a, b:
 // mean of the four face EMFs plus one quarter of the upwinded face-to-corner corrections.
 // ea[0..1]: a-face EMFs at b-index -1, 0; eb[0..1]: b-face EMFs at a-index -1, 0;

@@ -181,14 +181,15 @@ def wave_eigen(kind, rho, v, p, b, gamma):
 
 
 def linear_wave(n=32, mb=None, kind="alfven", amp=1.0e-6, geometry="cube", b_unit=True,
-                v0=(0.0, 0.0, 0.0), gamma=5.0 / 3.0):
+                v0=(0.0, 0.0, 0.0), gamma=5.0 / 3.0, phase=0.0):
     """Linear MHD wave on a periodic box, propagating along a grid diagonal.
 
     geometry "cube": unit cube, n^3 cells, k = 2 pi (1, 1, 1) (wavelength 1/sqrt(3)).
     geometry "paper": box (3, 1.5, 1.5) with 2n x n x n cells and wavelength 1; the periodic
     diagonal direction is k_hat = (1, 2, 2)/3, i.e. k = 2 pi (1/3, 2/3, 2/3).
     Background (wave frame): rho = 1, p = 1/gamma, b = (1, sqrt 2, 1/2) (c_f = 2, c_A = 1, c_s = 1/2),
-    scaled to |b| = 1 when b_unit.  `v0` is a uniform background flow in the grid frame.
+    scaled to |b| = 1 when b_unit.  `v0` is a uniform background flow in the grid frame; `phase` shifts the
+    profile sin(k.x + phase) (with phase 0 the extrema and zeros sit on cell symmetry points of the grid).
     Returns the Problem; meta holds the wave speed, the period and the exact (initial) state.
     """
     if geometry == "cube":
@@ -217,7 +218,7 @@ def linear_wave(n=32, mb=None, kind="alfven", amp=1.0e-6, geometry="cube", b_uni
     vw = np.array([v0 @ nhat, v0 @ t1, v0 @ t2])
     speed, r = wave_eigen(kind, rho0, vw, p0, bw, gamma)
     x, y, z = _cell_coords(nx, xmin, xmax)
-    ph = kvec[0] * x + kvec[1] * y + kvec[2] * z
+    ph = kvec[0] * x + kvec[1] * y + kvec[2] * z + phase
     s = amp * np.sin(ph)
     w = np.empty((5,) + x.shape)
     w[0] = rho0 + r[0] * s
@@ -230,9 +231,9 @@ def linear_wave(n=32, mb=None, kind="alfven", amp=1.0e-6, geometry="cube", b_uni
     beta = amp * r[5] / kmag
     avec = alpha * t1 + beta * t2
     (exx, exy, exz), (eyx, eyy, eyz), (ezx, ezy, ezz) = _edge_coords(nx, xmin, xmax)
-    ax = avec[0] * np.cos(kvec[0] * exx + kvec[1] * exy + kvec[2] * exz)
-    ay = avec[1] * np.cos(kvec[0] * eyx + kvec[1] * eyy + kvec[2] * eyz)
-    az = avec[2] * np.cos(kvec[0] * ezx + kvec[1] * ezy + kvec[2] * ezz)
+    ax = avec[0] * np.cos(kvec[0] * exx + kvec[1] * exy + kvec[2] * exz + phase)
+    ay = avec[1] * np.cos(kvec[0] * eyx + kvec[1] * eyy + kvec[2] * eyz + phase)
+    az = avec[2] * np.cos(kvec[0] * ezx + kvec[1] * ezy + kvec[2] * ezz + phase)
     b1, b2, b3 = faces_from_potential(nx, xmin, xmax, ax, ay, az)
     bg = bw[0] * nhat + bw[1] * t1 + bw[2] * t2
     b1 += bg[0]

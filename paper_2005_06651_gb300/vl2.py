@@ -23,7 +23,7 @@ PERIODIC, OUTFLOW = 0, 1
 VL2, RK1, RK2, RK3 = 0, 1, 2, 3  # time integrators (vl2_params.integrator)
 FP64, MIXED = 0, 1
 HOST, DEVICE = 0, 1
-DC, PLM = 0, 1
+DC, PLM, PPM = 0, 1, 2  # reconstructions (vl2_params.recon for the higher-order stages)
 
 STATUS_NAMES = {0: "VL2_OK", 1: "VL2_E_ARG", 2: "VL2_E_CUDA", 3: "VL2_E_NONPHYS", 4: "VL2_E_TIMEOUT",
                 5: "VL2_E_STATE", 6: "VL2_E_NOMEM"}
@@ -40,7 +40,8 @@ class Params(ctypes.Structure):
                 ("xmin", ctypes.c_double * 3), ("xmax", ctypes.c_double * 3), ("gamma", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("riemann", ctypes.c_int), ("precision", ctypes.c_int),
                 ("bc", ctypes.c_int * 6), ("dfloor", ctypes.c_double), ("pfloor", ctypes.c_double),
-                ("stream", ctypes.c_void_p), ("adjoint", ctypes.c_int), ("integrator", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("adjoint", ctypes.c_int), ("integrator", ctypes.c_int),
+                ("recon", ctypes.c_int)]
 
 
 class Layout(ctypes.Structure):
@@ -59,9 +60,9 @@ EXPORTS = ["vl2_workspace_bytes", "vl2_mesh_create", "vl2_mesh_destroy", "vl2_bl
            "vl2_batch_launch_count", "vl2_batch_last_error", "vl2_set_cons", "vl2_step_vjp", "vl2_prims_vjp",
            "vl2_debug_riemann_vjp", "vl2_last_error"]
 NOALLOC_MAX_NZ = 4096
-K_PRIM, K_GHOSTS, K_FLUX_DC, K_FLUX_PLM, K_EMF, K_UPDATE = range(6)
+K_PRIM, K_GHOSTS, K_FLUX_DC, K_FLUX_PLM, K_EMF, K_UPDATE, K_FLUX_PPM = range(7)
 KERNEL_KINDS = {K_PRIM: "prim", K_GHOSTS: "ghosts", K_FLUX_DC: "flux_dc", K_FLUX_PLM: "flux_plm", K_EMF: "emf",
-                K_UPDATE: "update"}
+                K_UPDATE: "update", K_FLUX_PPM: "flux_ppm"}
 
 
 def load(path: str = LIB_PATH):
@@ -152,7 +153,7 @@ class Mesh:
 
     def __init__(self, nx, mb, xmin=(0.0, 0.0, 0.0), xmax=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, cfl=0.3,
                  riemann=HLLD, bc=(PERIODIC,) * 6, dfloor=1e-12, pfloor=1e-12, precision=FP64, device=None,
-                 stream=None, adjoint=False, integrator=VL2):
+                 stream=None, adjoint=False, integrator=VL2, recon=PLM, ng=None):
         import torch
 
         L = load()
@@ -166,7 +167,8 @@ class Mesh:
         p = Params()
         p.nx[:] = self.nx
         p.mb[:] = self.mb
-        p.ng = 2
+        p.ng = (3 if recon == PPM else 2) if ng is None else int(ng)
+        p.recon = int(recon)
         p.xmin[:] = self.xmin
         p.xmax[:] = self.xmax
         p.gamma, p.cfl = self.gamma, self.cfl

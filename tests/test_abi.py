@@ -55,6 +55,8 @@ def _params(**kw):
     p.precision = kw.get("precision", 0)
     p.bc[:] = kw.get("bc", (0,) * 6)
     p.dfloor = p.pfloor = 1e-12
+    p.adjoint = kw.get("adjoint", 0)
+    p.recon = kw.get("recon", 0)
     return p
 
 
@@ -63,11 +65,17 @@ def test_workspace_bytes_and_argument_checks(lib):
     assert lib.vl2_workspace_bytes(ctypes.byref(_params()), ctypes.byref(n)) == 0
     # 8 blocks of (16+5 -> 24) x 21 x 21 padded cells, 48 double arrays, plus staging
     assert n.value >= 8 * 24 * 21 * 21 * 48 * 8
-    bad = [dict(nx=(30, 32, 32)), dict(ng=3), dict(gamma=1.0), dict(riemann=5), dict(precision=7),
-           dict(bc=(0, 1, 0, 0, 0, 0)), dict(nx=(0, 32, 32)), dict(xmax=(0.0, 1.0, 1.0))]
+    bad = [dict(nx=(30, 32, 32)), dict(ng=1), dict(ng=4), dict(gamma=1.0), dict(riemann=5), dict(precision=7),
+           dict(bc=(0, 1, 0, 0, 0, 0)), dict(nx=(0, 32, 32)), dict(xmax=(0.0, 1.0, 1.0)), dict(recon=7),
+           dict(recon=2, ng=2), dict(adjoint=1, ng=3), dict(adjoint=1, ng=3, recon=2)]
     for kw in bad:
         assert lib.vl2_workspace_bytes(ctypes.byref(_params(**kw)), ctypes.byref(n)) == 1, kw
         assert lib.vl2_last_error(None)
+    # three ghost layers (with PLM or PPM) enlarge the padded boxes
+    for kw in (dict(ng=3), dict(ng=3, recon=2)):
+        m = ctypes.c_size_t()
+        assert lib.vl2_workspace_bytes(ctypes.byref(_params(**kw)), ctypes.byref(m)) == 0, kw
+        assert m.value > n.value
     out = ctypes.c_void_p()
     # misaligned or null workspace is rejected before any CUDA call
     assert lib.vl2_mesh_create(ctypes.byref(_params()), ctypes.c_void_p(0), ctypes.c_size_t(1 << 30),
