@@ -231,8 +231,8 @@ __device__ __forceinline__ void source_of(const Geom& g, int q, int gi, bool fac
   }
 }
 
-// Ghost elements lie in the shell of the padded box: index triples 0 .. mb+2NG (one more than the cells,
-// for the faces) with at least one coordinate outside the interior g.ng .. g.ng+mb-1.  A thread per shell
+// Ghost elements lie in the shell of the padded box: index triples 0 .. mb+2ng (one more than the cells,
+// for the faces) with at least one coordinate outside the interior ng .. ng+mb-1.  A thread per shell
 // element; the shell is decoded as z-slabs (k outside the interior), then y-slabs (k inside, j outside),
 // then x-slabs (k, j inside, i outside).
 __device__ __forceinline__ long long shell_size(const Geom& g) {
