@@ -45,7 +45,9 @@ def lib():
         ip = ctypes.POINTER(ctypes.c_int)
         L.orc_mesh_new.restype = ctypes.c_void_p
         L.orc_mesh_new.argtypes = [ip, ip, dp, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.c_double,
-                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.orc_set_scalars.argtypes = [ctypes.c_void_p, dp]
+        L.orc_get_scalars.argtypes = [ctypes.c_void_p, dp]
         L.orc_mesh_free.argtypes = [ctypes.c_void_p]
         L.orc_set_prims.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
         L.orc_get_cons.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
@@ -191,10 +193,12 @@ def step_cons(prob_geom, dt, state, gamma=5.0 / 3.0, riemann=HLLD):
 
 class Mesh:
     """Oracle mesh of equal-size MeshBlocks holding one VL2 state.  recon is the reconstruction of the
-    higher-order stages (PLM or PPM); ng the ghost layers (default 2, or 3 with PPM)."""
+    higher-order stages (PLM or PPM); ng the ghost layers (default 2, or 3 with PPM); nscalars the passive
+    scalars (eq. passive_scalars)."""
 
     def __init__(self, nx, mb, xmin=(0.0, 0.0, 0.0), xmax=(1.0, 1.0, 1.0), gamma=5.0 / 3.0,
-                 riemann=HLLD, bc=(0,) * 6, dfloor=1e-12, pfloor=1e-12, integrator=VL2, recon=PLM, ng=None):
+                 riemann=HLLD, bc=(0,) * 6, dfloor=1e-12, pfloor=1e-12, integrator=VL2, recon=PLM, ng=None,
+                 nscalars=0):
         self.nx = tuple(int(v) for v in nx)
         self.mb = tuple(int(v) for v in mb)
         self.xmin, self.xmax = tuple(xmin), tuple(xmax)
@@ -206,7 +210,9 @@ class Mesh:
         db = (ctypes.c_double * 3)(*self.xmax)
         bcs = (ctypes.c_int * 6)(*bc)
         self.ng = (3 if recon == PPM else 2) if ng is None else int(ng)
-        self._h = L.orc_mesh_new(ia, ib, da, db, gamma, riemann, bcs, dfloor, pfloor, integrator, recon, self.ng)
+        self.nscalars = int(nscalars)
+        self._h = L.orc_mesh_new(ia, ib, da, db, gamma, riemann, bcs, dfloor, pfloor, integrator, recon, self.ng,
+                                 self.nscalars)
         if not self._h:
             raise ValueError("invalid oracle mesh parameters")
 
@@ -247,6 +253,17 @@ class Mesh:
         b = [np.zeros(s) for s in self.face_shapes()]
         lib().orc_get_cons(self._h, _dp(u), *[_dp(x) for x in b])
         return u, b[0], b[1], b[2]
+
+    def set_scalars(self, c):
+        """Concentrations c (nscalars, NZ, NY, NX); the state must be set first (rho C = rho c)."""
+        c = _c64(np.asarray(c, dtype=np.float64).reshape((self.nscalars,) + self.shape))
+        lib().orc_set_scalars(self._h, _dp(c))
+
+    def get_scalars(self):
+        """Scalar masses rho C, (nscalars, NZ, NY, NX)."""
+        out = np.zeros((self.nscalars,) + self.shape)
+        lib().orc_get_scalars(self._h, _dp(out))
+        return out
 
     def get_prims(self):
         w = np.zeros((8,) + self.shape)

@@ -22,6 +22,8 @@
  *   - 2S low-storage register scheme (eq. rk-2s) with the VL2 coefficients; the
  *     predictor uses donor-cell fluxes                                           (Sec. 3.2.3)
  *   - one global time step from |v| + C_f                                      (Sec. 2.1.7, 3.2.3)
+ *   - passive scalars rho C_i, d(rho C_i)/dt + div(rho v C_i) = 0 (eq. passive_scalars), C_i reconstructed
+ *     like the other primitives and carried by the Riemann mass flux from the upwind side   (Sec. 3.1)
  *
  * The paper names HLLE / HLLD / upwind CT / VL2 but prints no formulas for them; the formulas here
  * are written from the published methods (HLLD: Miyoshi & Kusano 2005; upwind CT: Gardiner &
@@ -488,6 +490,7 @@ struct Params {
   int integrator;
   int recon;  // reconstruction of the PLM stages: REC_PLM or REC_PPM (VL2 corrector, RK2/RK3 stages)
   int ng;     // ghost layers: 2 (DC, PLM) or 3 (PPM)
+  int nscal;  // passive scalars (eq. passive_scalars)
 };
 
 /* dense 3D array (k, j, i), i fastest */
@@ -512,6 +515,9 @@ template <class T> struct Block {
   Arr3<T> w[8];     // rho, vx, vy, vz, p, bcx, bcy, bcz
   Arr3<T> flx[3][NW7];  // fluxes on faces of direction d (component layout of the sweep)
   Arr3<T> emf[3];   // E1 on (j-1/2,k-1/2), E2 on (k-1/2,i-1/2), E3 on (i-1/2,j-1/2)
+  std::vector<Arr3<T>> s[2];   // two registers of the passive-scalar masses rho C_i
+  std::vector<Arr3<T>> cs;     // concentrations C_i (primitive)
+  std::vector<Arr3<T>> fs[3];  // scalar fluxes on faces of direction d
 };
 
 template <class T> struct Mesh {
@@ -559,6 +565,16 @@ template <class T> struct Mesh {
           B.emf[0].init(c[0], c[1] + 1, c[2] + 1);
           B.emf[1].init(c[0] + 1, c[1], c[2] + 1);
           B.emf[2].init(c[0] + 1, c[1] + 1, c[2]);
+          for (int r = 0; r < 2; ++r) {
+            B.s[r].resize(p.nscal);
+            for (auto& A : B.s[r]) A.init(c[0], c[1], c[2]);
+          }
+          B.cs.resize(p.nscal);
+          for (auto& A : B.cs) A.init(c[0], c[1], c[2]);
+          for (int d = 0; d < 3; ++d) {
+            B.fs[d].resize(p.nscal);
+            for (auto& A : B.fs[d]) A.init(c[0] + (d == 0), c[1] + (d == 1), c[2] + (d == 2));
+          }
         }
   }
 
@@ -614,6 +630,7 @@ template <class T> struct Mesh {
             }
             const Block<T>& S = blk[bid(sb[0], sb[1], sb[2])];
             for (int v = 0; v < 5; ++v) B.u[r][v](k, j, i) = S.u[r][v](sl[2], sl[1], sl[0]);
+            for (int q = 0; q < P.nscal; ++q) B.s[r][q](k, j, i) = S.s[r][q](sl[2], sl[1], sl[0]);
           }
       for (int fd = 0; fd < 3; ++fd) {
         Arr3<T>& A = B.b[r][fd];
@@ -688,6 +705,7 @@ template <class T> struct Mesh {
             B.w[5](k, j, i) = bcx;
             B.w[6](k, j, i) = bcy;
             B.w[7](k, j, i) = bcz;
+            for (int q = 0; q < P.nscal; ++q) B.cs[q](k, j, i) = B.s[r][q](k, j, i) / d;
           }
     }
     floor_events += fired_total;
@@ -757,6 +775,29 @@ template <class T> struct Mesh {
             T f[NW7];
             riemann(P.riemann, wl, wr, B.b[0][d](k, j, i), P.gamma, f);
             for (int v = 0; v < NW7; ++v) B.flx[d][v](k, j, i) = f[v];
+            /* passive scalars: C reconstructed like the primitives, carried by the mass flux from the
+             * upwind side, F = F_rho C_L if F_rho >= 0, else F_rho C_R  [reading] */
+            for (int q = 0; q < P.nscal; ++q) {
+              const Arr3<T>& C = B.cs[q];
+              auto at = [&](int o) { return C(k + o * sh[2], j + o * sh[1], i + o * sh[0]); };
+              T cl, cr;
+              if (recon == REC_DC) {
+                cl = at(-1);
+                cr = at(0);
+              } else if (recon == REC_PPM) {
+                const T lo5[5] = {at(-3), at(-2), at(-1), at(0), at(1)};
+                const T hi5[5] = {at(-2), at(-1), at(0), at(1), at(2)};
+                T a, b2;
+                ppm_edges(lo5, a, b2);
+                cl = b2;
+                ppm_edges(hi5, a, b2);
+                cr = a;
+              } else {
+                cl = at(-1) + 0.5 * vanleer_slope(at(-2), at(-1), at(0));
+                cr = at(0) - 0.5 * vanleer_slope(at(-1), at(0), at(1));
+              }
+              B.fs[d][q](k, j, i) = (f[IDN] >= 0.0) ? f[IDN] * cl : f[IDN] * cr;
+            }
           }
     }
   }
@@ -876,7 +917,24 @@ template <class T> struct Mesh {
           for (int j = NG; j <= n[1] + NG - (fd == 1 ? 0 : 1); ++j)
             for (int i = NG; i <= n[0] + NG - (fd == 0 ? 0 : 1); ++i) A1(k, j, i) = A1(k, j, i) + delta * A0(k, j, i);
       }
+      for (int q = 0; q < P.nscal; ++q)
+        for (int k = NG; k < n[2] + NG; ++k)
+          for (int j = NG; j < n[1] + NG; ++j)
+            for (int i = NG; i < n[0] + NG; ++i) B.s[1][q](k, j, i) = B.s[1][q](k, j, i) + delta * B.s[0][q](k, j, i);
       const double h = beta * dt;
+      /* passive scalars, with the association of the conserved variables below */
+      for (int q = 0; q < P.nscal; ++q)
+        for (int k = NG; k < n[2] + NG; ++k)
+          for (int j = NG; j < n[1] + NG; ++j)
+            for (int i = NG; i < n[0] + NG; ++i) {
+              T dfl[3];
+              for (int d = 0; d < 3; ++d) {
+                const int ip = i + (d == 0), jp = j + (d == 1), kp = k + (d == 2);
+                dfl[d] = (B.fs[d][q](kp, jp, ip) - B.fs[d][q](k, j, i)) / dx[d];
+              }
+              const T L = -((dfl[0] + dfl[1]) + dfl[2]);
+              B.s[0][q](k, j, i) = (g0 * B.s[0][q](k, j, i) + g1 * B.s[1][q](k, j, i)) + h * L;
+            }
       /* cell-centred: conserved variable v <- flux component (rho, M_n..., E) */
       for (int k = NG; k < n[2] + NG; ++k)
         for (int j = NG; j < n[1] + NG; ++j)
@@ -941,6 +999,7 @@ template <class T> struct Mesh {
     for (auto& B : blk) {
       for (int v = 0; v < 5; ++v) std::fill(B.u[1][v].v.begin(), B.u[1][v].v.end(), T(0.0));
       for (int fd = 0; fd < 3; ++fd) std::fill(B.b[1][fd].v.begin(), B.b[1][fd].v.end(), T(0.0));
+      for (auto& A : B.s[1]) std::fill(A.v.begin(), A.v.end(), T(0.0));
     }
     for (const Stage& s : st) {
       cons_to_prim(0);
@@ -1129,9 +1188,12 @@ using orc::Mesh;
 extern "C" {
 
 void* orc_mesh_new(const int* nx, const int* mb, const double* xmin, const double* xmax, double gamma,
-                   int riemann, const int* bc, double dfloor, double pfloor, int integrator, int recon, int ng) {
+                   int riemann, const int* bc, double dfloor, double pfloor, int integrator, int recon, int ng,
+                   int nscal) {
   orc::Params p;
   if (recon != orc::REC_PLM && recon != orc::REC_PPM) return nullptr;
+  if (nscal < 0 || nscal > 16) return nullptr;
+  p.nscal = nscal;
   if (ng < 2 || (recon == orc::REC_PPM && ng < 3)) return nullptr;
   p.recon = recon;
   p.ng = ng;
@@ -1169,6 +1231,39 @@ void orc_set_cons(void* m, const double* u, const double* b1, const double* b2, 
 }
 
 /* cons -> prim of the current state on the active region: w[8][nz][ny][nx] (rho, v, p, b_c) */
+/* Passive scalars from concentrations c[q][NZ][NY][NX]: rho C_q = rho c_q on the active cells (rho from the
+ * current state, so set the state first), then the ghost exchange. */
+void orc_set_scalars(void* m, const double* c) {
+  Mesh<double>& M = *static_cast<Mesh<double>*>(m);
+  const int NX = M.P.nx[0], NY = M.P.nx[1], NZ = M.P.nx[2];
+  const size_t ncell = (size_t)NX * NY * NZ;
+  for (auto& B : M.blk)
+    for (int q = 0; q < M.P.nscal; ++q)
+      for (int k = 0; k < M.n[2]; ++k)
+        for (int j = 0; j < M.n[1]; ++j)
+          for (int i = 0; i < M.n[0]; ++i) {
+            const size_t g = ((size_t)(B.loc[2] * M.n[2] + k) * NY + (B.loc[1] * M.n[1] + j)) * NX + (B.loc[0] * M.n[0] + i);
+            const int K = k + M.NG, J = j + M.NG, I = i + M.NG;
+            B.s[0][q](K, J, I) = B.u[0][0](K, J, I) * c[q * ncell + g];
+          }
+  M.fill_ghosts(0);
+}
+
+/* Scalar masses rho C_q of the active cells, out[q][NZ][NY][NX]. */
+void orc_get_scalars(void* m, double* out) {
+  Mesh<double>& M = *static_cast<Mesh<double>*>(m);
+  const int NX = M.P.nx[0], NY = M.P.nx[1], NZ = M.P.nx[2];
+  const size_t ncell = (size_t)NX * NY * NZ;
+  for (const auto& B : M.blk)
+    for (int q = 0; q < M.P.nscal; ++q)
+      for (int k = 0; k < M.n[2]; ++k)
+        for (int j = 0; j < M.n[1]; ++j)
+          for (int i = 0; i < M.n[0]; ++i) {
+            const size_t g = ((size_t)(B.loc[2] * M.n[2] + k) * NY + (B.loc[1] * M.n[1] + j)) * NX + (B.loc[0] * M.n[0] + i);
+            out[q * ncell + g] = B.s[0][q](k + M.NG, j + M.NG, i + M.NG);
+          }
+}
+
 void orc_get_prims(void* m, double* w) {
   Mesh<double>& M = *static_cast<Mesh<double>*>(m);
   M.cons_to_prim(0);
@@ -1317,6 +1412,7 @@ void orc_tl_step(const int* nx, const int* mb, const double* xmin, const double*
   p.integrator = orc::INT_VL2;
   p.recon = orc::REC_PLM;
   p.ng = 2;
+  p.nscal = 0;
   orc::Mesh<orc::Dual> M;
   M.init(p);
   orc::set_cons(M, u, du, b1, db1, b2, db2, b3, db3);
@@ -1344,6 +1440,7 @@ void orc_step_cons(const int* nx, const int* mb, const double* xmin, const doubl
   p.integrator = orc::INT_VL2;
   p.recon = orc::REC_PLM;
   p.ng = 2;
+  p.nscal = 0;
   orc::Mesh<double> M;
   M.init(p);
   orc::set_cons(M, u, nullptr, b1, nullptr, b2, nullptr, b3, nullptr);
