@@ -77,7 +77,11 @@ typedef struct vl2_params {
   int recon;          /* reconstruction of the higher-order stages (the VL2 corrector, every RK2 / RK3 stage):
                          VL2_PLM (also 0) or VL2_PPM (needs ng = 3; not with adjoint).  The VL2 predictor and
                          RK1 always use donor cell (Sec. 3.2.3). */
+  int nscalars;       /* passive scalars rho C_i, d(rho C_i)/dt + div(rho v C_i) = 0 (eq. passive_scalars):
+                         0 .. VL2_MAX_SCALARS; 0 with adjoint; not in a batch */
 } vl2_params;
+
+#define VL2_MAX_SCALARS 16
 
 typedef struct vl2_mesh vl2_mesh;
 
@@ -172,6 +176,15 @@ vl2_status vl2_totals(vl2_mesh* mesh, double out[8]);
 /* Total number of cons->prim floor events on active cells since creation.  Blocks. */
 vl2_status vl2_floor_count(vl2_mesh* mesh, long long* out);
 
+/* Passive scalars (eq. passive_scalars).  vl2_set_scalars takes concentrations c[nscalars][NZ][NY][NX]
+ * (C_i, the primitive form) and sets rho C_i = rho c_i on the active cells from the current density, so the
+ * state must be set first; ghosts are exchanged.  vl2_get_scalars returns the scalar masses rho C_i in the
+ * same layout.  Each scalar's flux is the Riemann mass flux times the upwind side's concentration,
+ * reconstructed like the primitives of the stage.  Errors: VL2_E_ARG (no scalars, NULL, bad where),
+ * VL2_E_STATE (state not set), VL2_E_CUDA. */
+vl2_status vl2_set_scalars(vl2_mesh* mesh, const double* c, int where);
+vl2_status vl2_get_scalars(vl2_mesh* mesh, double* out, int where);
+
 /* Inspection of one stage's terms for the current state (Sec. 3.2.1-3.2.2, 3.1), without updating
  * it: face fluxes of the given reconstruction (VL2_DC, VL2_PLM, or VL2_PPM on a mesh with ng = 3) on the
  * global face grids fx[7][NZ][NY][NX+1],
@@ -220,7 +233,8 @@ enum {
   VL2_K_EMF = 4,      /* upwind CT corner EMFs (units: corner nodes) */
   VL2_K_UPDATE = 5,   /* register update of U and the face field (units: nodes) */
   VL2_K_FLUX_PPM = 6, /* PPM + Riemann fluxes of one sweep direction (units: faces) */
-  VL2_K_COUNT = 7
+  VL2_K_SCALARS = 7,  /* passive-scalar fluxes and updates */
+  VL2_K_COUNT = 8
 };
 
 /* Per-kernel timing, the measuring side of the paper's zone-cycles-per-second benchmarks (Sec. 3.4.1).

@@ -157,6 +157,10 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
     msg = "the adjoint (params.adjoint = 1) is written for PLM with ng = 2";
     return VL2_E_ARG;
   }
+  if (p->nscalars < 0 || p->nscalars > VL2_MAX_SCALARS || (p->adjoint && p->nscalars)) {
+    msg = "nscalars must be 0 .. VL2_MAX_SCALARS (and 0 with the adjoint)";
+    return VL2_E_ARG;
+  }
   for (int d = 0; d < 3; ++d) {
     const int lo = p->bc[2 * d], hi = p->bc[2 * d + 1];
     if ((lo != VL2_PERIODIC && lo != VL2_OUTFLOW) || (hi != VL2_PERIODIC && hi != VL2_OUTFLOW) ||
@@ -181,6 +185,7 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
   }
   g.nblk = (int)nblk;
   g.ng = p->ng;
+  g.ns = p->nscalars;
   g.sx = ((p->mb[0] + 2 * g.ng + 1) + 3) & ~3;
   g.sy = p->mb[1] + 2 * g.ng + 1;
   g.sz = p->mb[2] + 2 * g.ng + 1;
@@ -200,6 +205,7 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
 
 struct Plan {
   size_t off_u[2], off_b[2][3], off_w, off_f[3], off_e[3], off_ec, off_stage, off_red, off_scal, total;
+  size_t off_s[2], off_cs, off_fsc[3];  // passive scalars (empty when ns = 0)
   size_t stage_elems;
   size_t off_adj;  // start of the adjoint arrays (59 FP64 arrays per block) when requested
 };
@@ -230,8 +236,20 @@ Plan make_plan(const Geom& g, int precision, int adjoint) {
   }
   pl.off_ec = o;
   o = align256(o + 3 * sper);
+  const size_t sc = (size_t)g.ns * per;
+  for (int r = 0; r < 2; ++r) {
+    pl.off_s[r] = o;
+    o = align256(o + sc);
+  }
+  pl.off_cs = o;
+  o = align256(o + sc);
+  for (int d = 0; d < 3; ++d) {
+    pl.off_fsc[d] = o;
+    o = align256(o + sc);
+  }
   const long long nc = ncells(g);
   long long st = 5 * nc + nfaces_total(g);
+  st = std::max(st, (long long)g.ns * nc);
   st = std::max(st, 8 * nc);
   st = std::max(st, 7 * max_face_grid(g));
   st = std::max(st, max_edge_grid(g));
@@ -324,6 +342,20 @@ cudaError_t k_fluxes(vl2_mesh* m, int reg, int recon) {
   }
   return cudaSuccess;
 }
+cudaError_t k_scalar_fluxes(vl2_mesh* m, int recon) {
+  if (!m->g.ns) return cudaSuccess;
+  for (int d = 0; d < 3; ++d) {
+    cudaError_t e = timed(m, VL2_K_SCALARS, flux_faces(m->g, d),
+                          [&] { return vl2::launch_scalar_fluxes(m->view(), recon, d, m->st); });
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+cudaError_t k_scalar_update(vl2_mesh* m, int base, int out, double h, double g_base = 1.0, double g_other = 0.0) {
+  if (!m->g.ns) return cudaSuccess;
+  return timed(m, VL2_K_SCALARS, nodes(m->g),
+               [&] { return vl2::launch_scalar_update(m->view(), base, out, h, g_base, g_other, m->st); });
+}
 cudaError_t k_emfs(vl2_mesh* m) {
   return timed(m, VL2_K_EMF, nodes(m->g), [&] { return vl2::launch_emfs(m->view(), nullptr, m->st); });
 }
@@ -386,6 +418,9 @@ vl2_status vl2_mesh_create(const vl2_params* params, void* workspace, size_t byt
   }
   m->a.ec = base + pl.off_ec;
   m->a.mixed = params->precision == VL2_MIXED ? 1 : 0;
+  for (int r = 0; r < 2; ++r) m->a.s[r] = g.ns ? (double*)(base + pl.off_s[r]) : nullptr;
+  m->a.cs = g.ns ? (double*)(base + pl.off_cs) : nullptr;
+  for (int d = 0; d < 3; ++d) m->a.fsc[d] = g.ns ? (double*)(base + pl.off_fsc[d]) : nullptr;
   if (params->adjoint) {
     const size_t per = (size_t)g.nblk * g.box;
     double* q = (double*)(base + pl.off_adj);
@@ -508,6 +543,43 @@ vl2_status vl2_set_prims(vl2_mesh* m, const double* w, const double* b1, const d
   m->initialized = true;
   m->w_valid = false;
   m->dt_pending = false;
+  return sync(m);
+}
+
+vl2_status vl2_set_scalars(vl2_mesh* m, const double* c, int where) {
+  if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
+  if (!c || bad_where(where)) return fail(m, VL2_E_ARG, "NULL input or bad where");
+  if (!m->initialized) return fail(m, VL2_E_STATE, "set the state (vl2_set_prims / vl2_set_cons) first");
+  if (!m->g.ns) return fail(m, VL2_E_ARG, "the mesh has no passive scalars");
+  const long long n = (long long)m->g.ns * ncells(m->g);
+  const double* dc = c;
+  if (where == VL2_HOST) {
+    vl2_status st;
+    if ((st = copy_in(m, m->a.stage, c, n, where)) != VL2_OK) return st;
+    dc = m->a.stage;
+  }
+  VL2_CHECK(m, vl2::launch_scatter_scalars(m->g, m->a, dc, m->st));
+  ++m->launches;
+  VL2_CHECK(m, k_ghosts(m, 0));
+  m->w_valid = false;
+  m->dt_pending = false;
+  return sync(m);
+}
+
+vl2_status vl2_get_scalars(vl2_mesh* m, double* out, int where) {
+  if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
+  if (!out || bad_where(where)) return fail(m, VL2_E_ARG, "NULL output or bad where");
+  if (!m->g.ns) return fail(m, VL2_E_ARG, "the mesh has no passive scalars");
+  const long long n = (long long)m->g.ns * ncells(m->g);
+  if (where == VL2_DEVICE) {
+    VL2_CHECK(m, vl2::launch_gather_scalars(m->g, m->a, out, m->st));
+    ++m->launches;
+    return VL2_OK;
+  }
+  VL2_CHECK(m, vl2::launch_gather_scalars(m->g, m->a, m->a.stage, m->st));
+  ++m->launches;
+  vl2_status st = copy_out(m, out, m->a.stage, n);
+  if (st != VL2_OK) return st;
   return sync(m);
 }
 
@@ -647,11 +719,15 @@ vl2_status step_rk(vl2_mesh* m, double dt) {
   VL2_CHECK(m, cudaMemcpyAsync(m->a.u[1], m->a.u[0], 5 * per, cudaMemcpyDeviceToDevice, m->st));
   for (int d = 0; d < 3; ++d)
     VL2_CHECK(m, cudaMemcpyAsync(m->a.b[1][d], m->a.b[0][d], per, cudaMemcpyDeviceToDevice, m->st));
+  if (g.ns)
+    VL2_CHECK(m, cudaMemcpyAsync(m->a.s[1], m->a.s[0], g.ns * per, cudaMemcpyDeviceToDevice, m->st));
   for (int k = 0; k < ns; ++k) {
     if (k > 0) VL2_CHECK(m, k_prim(m, 0, false));
     VL2_CHECK(m, k_fluxes(m, 0, recon));
+    VL2_CHECK(m, k_scalar_fluxes(m, recon));
     VL2_CHECK(m, k_emfs(m));
     VL2_CHECK(m, k_update(m, 0, 0, st[k].beta * dt, st[k].g0, st[k].g1));
+    VL2_CHECK(m, k_scalar_update(m, 0, 0, st[k].beta * dt, st[k].g0, st[k].g1));
     VL2_CHECK(m, k_ghosts(m, 0));
   }
   VL2_CHECK(m, cudaMemsetAsync(m->a.scal + vl2::SC_MAXRATE, 0, sizeof(unsigned long long), m->st));
@@ -671,14 +747,18 @@ vl2_status vl2_step(vl2_mesh* m, double dt) {
   if (m->p.integrator != VL2_INT_VL2) return step_rk(m, dt);
   // predictor: U* = U^n + (dt/2) L_DC(U^n) into register 1 (Sec. 3.2.3, VL2)
   VL2_CHECK(m, k_fluxes(m, 0, VL2_DC));
+  VL2_CHECK(m, k_scalar_fluxes(m, VL2_DC));
   VL2_CHECK(m, k_emfs(m));
   VL2_CHECK(m, k_update(m, 0, 1, 0.5 * dt));
+  VL2_CHECK(m, k_scalar_update(m, 0, 1, 0.5 * dt));
   VL2_CHECK(m, k_ghosts(m, 1));
   VL2_CHECK(m, k_prim(m, 1, false));
   // corrector: U^{n+1} = U^n + dt L_PLM(U*) (or L_PPM) in place in register 0
   VL2_CHECK(m, k_fluxes(m, 1, m->rec()));
+  VL2_CHECK(m, k_scalar_fluxes(m, m->rec()));
   VL2_CHECK(m, k_emfs(m));
   VL2_CHECK(m, k_update(m, 0, 0, dt));
+  VL2_CHECK(m, k_scalar_update(m, 0, 0, dt));
   VL2_CHECK(m, k_ghosts(m, 0));
   // primitives of U^{n+1} for the next cycle, with the CFL reduction fused in
   VL2_CHECK(m, cudaMemsetAsync(m->a.scal + vl2::SC_MAXRATE, 0, sizeof(unsigned long long), m->st));
@@ -966,8 +1046,8 @@ vl2_status batch_check(vl2_mesh* const* meshes, int n, std::string& msg) {
       msg = "NULL mesh in the batch";
       return VL2_E_ARG;
     }
-    if (meshes[q]->p.integrator != VL2_INT_VL2) {
-      msg = "the batched form runs the VL2 integrator";
+    if (meshes[q]->p.integrator != VL2_INT_VL2 || meshes[q]->g.ns != 0) {
+      msg = "the batched form runs the VL2 integrator without passive scalars";
       return VL2_E_ARG;
     }
     if (meshes[q]->p.riemann != meshes[0]->p.riemann || meshes[q]->p.precision != meshes[0]->p.precision ||

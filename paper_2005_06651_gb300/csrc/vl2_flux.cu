@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
     li[TA] = g.ng - 1 + line % na;
     li[TB] = g.ng - 1 + line / na;
     const long long o = cell_off(g, li[2], li[1], li[0]);
-    if (REC == REC_PPM) {
+    if constexpr (REC == REC_PPM) {
 #pragma unroll
       for (int n = 0; n < 7; ++n) {
         const T* q = Wb + (long long)var[n] * g.box + o;
@@ -126,47 +126,47 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
         smem[sidx(n, 0, p, c)] = ql;
         smem[sidx(n, 1, p, c)] = qr;
       }
-      continue;
-    }
-    T q0[7], dl[7], dr[7], den[7];
-    bool pos[7];
+    } else {
+      T q0[7], dl[7], dr[7], den[7];
+      bool pos[7];
 #pragma unroll
-    for (int n = 0; n < 7; ++n) {
-      const T* q = Wb + (long long)var[n] * g.box + o;
-      const T qm = q[-sd], qc = q[0], qp = q[sd];
-      q0[n] = qc;
-      dl[n] = qc - qm;
-      dr[n] = qp - qc;
-      pos[n] = gt0(dl[n] * dr[n]);
-      den[n] = pos[n] ? dl[n] + dr[n] : T(1);
-    }
-    T rec[7];
-    if (sizeof(T) == 8) {
-      T pre[7];
-      pre[0] = den[0];
+      for (int n = 0; n < 7; ++n) {
+        const T* q = Wb + (long long)var[n] * g.box + o;
+        const T qm = q[-sd], qc = q[0], qp = q[sd];
+        q0[n] = qc;
+        dl[n] = qc - qm;
+        dr[n] = qp - qc;
+        pos[n] = gt0(dl[n] * dr[n]);
+        den[n] = pos[n] ? dl[n] + dr[n] : T(1);
+      }
+      T rec[7];
+      if (sizeof(T) == 8) {
+        T pre[7];
+        pre[0] = den[0];
 #pragma unroll
-      for (int n = 1; n < 7; ++n) pre[n] = pre[n - 1] * den[n];
-      if (normal_pos((double)fabs(pre[6]))) {
-        T acc = inv(pre[6]);  // pre[6] is a positive normal number here
+        for (int n = 1; n < 7; ++n) pre[n] = pre[n - 1] * den[n];
+        if (normal_pos((double)fabs(pre[6]))) {
+          T acc = inv(pre[6]);  // pre[6] is a positive normal number here
 #pragma unroll
-        for (int n = 6; n > 0; --n) {
-          rec[n] = acc * pre[n - 1];
-          acc = acc * den[n];
+          for (int n = 6; n > 0; --n) {
+            rec[n] = acc * pre[n - 1];
+            acc = acc * den[n];
+          }
+          rec[0] = acc;
+        } else {
+#pragma unroll
+          for (int n = 0; n < 7; ++n) rec[n] = T(1) / den[n];
         }
-        rec[0] = acc;
-      } else {
+      } else {  // FP32: divisions are cheap, and a 7-fold product could leave the float range
 #pragma unroll
         for (int n = 0; n < 7; ++n) rec[n] = T(1) / den[n];
       }
-    } else {  // FP32: divisions are cheap, and a 7-fold product could leave the float range
 #pragma unroll
-      for (int n = 0; n < 7; ++n) rec[n] = T(1) / den[n];
-    }
-#pragma unroll
-    for (int n = 0; n < 7; ++n) {
-      const T delta = pos[n] ? (T(2) * (dl[n] * dr[n])) * rec[n] : T(0);
-      smem[sidx(n, 0, p, c)] = q0[n] - T(0.5) * delta;  // value at the cell's lower face
-      smem[sidx(n, 1, p, c)] = q0[n] + T(0.5) * delta;  // value at the cell's upper face
+      for (int n = 0; n < 7; ++n) {
+        const T delta = pos[n] ? (T(2) * (dl[n] * dr[n])) * rec[n] : T(0);
+        smem[sidx(n, 0, p, c)] = q0[n] - T(0.5) * delta;  // value at the cell's lower face
+        smem[sidx(n, 1, p, c)] = q0[n] + T(0.5) * delta;  // value at the cell's upper face
+      }
     }
   }
   __syncthreads();

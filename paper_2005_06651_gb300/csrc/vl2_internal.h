@@ -17,6 +17,7 @@ struct Geom {
   int nb[3];           // blocks per direction
   int mb[3];           // active cells per block
   int ng;              // ghost layers (Sec. 2.1.1): 2, or 3 for PPM
+  int ns;              // passive scalars (eq. passive_scalars)
   int sx, sy, sz;      // padded per-block box extents (cells incl. ghosts + 1 face, x row padded)
   long long box;       // sx * sy * sz elements per block per variable
   int N[3];            // global active cells
@@ -46,6 +47,10 @@ struct Arrays {
   double* red;       // reduction partials
   int red_ctas;
   unsigned long long* scal;  // device scalars (see SC_*)
+  // passive scalars (FP64 in every precision; null when ns = 0)
+  double* s[2];      // registers of the scalar masses rho C: [nblk][ns][box]
+  double* cs;        // concentrations C, written by cons->prim: [nblk][ns][box]
+  double* fsc[3];    // scalar fluxes per sweep direction: [nblk][ns][box]
 };
 
 enum { SC_MAXRATE = 0, SC_FLOORS = 1, SC_MISMATCH = 2, SC_COUNT = 8 };
@@ -124,6 +129,13 @@ cudaError_t launch_check_periodic(const Geom& g, const double* b1, const double*
 cudaError_t launch_gather_cons(const Geom& g, const Arrays& a, double* u, double* b1, double* b2, double* b3,
                                cudaStream_t st);
 cudaError_t launch_gather_prims(const Geom& g, const Arrays& a, double* w, cudaStream_t st);
+// passive scalars: fluxes of one sweep direction for one reconstruction (the stage's mass fluxes must be
+// in a.f[dir]), the register update, and the global-array I/O (concentrations in, masses out)
+cudaError_t launch_scalar_fluxes(const MeshView& v, int recon, int dir, cudaStream_t st);
+cudaError_t launch_scalar_update(const MeshView& v, int base_reg, int out_reg, double h, double g_base,
+                                 double g_other, cudaStream_t st);
+cudaError_t launch_scatter_scalars(const Geom& g, const Arrays& a, const double* c, cudaStream_t st);
+cudaError_t launch_gather_scalars(const Geom& g, const Arrays& a, double* out, cudaStream_t st);
 cudaError_t launch_gather_fluxes(const Geom& g, const Arrays& a, int dir, double* out, cudaStream_t st);
 cudaError_t launch_gather_emfs(const Geom& g, const Arrays& a, int dir, double* out, cudaStream_t st);
 cudaError_t launch_divb(const Geom& g, const Arrays& a, double* result2, cudaStream_t st);

@@ -82,6 +82,17 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
       Ub[0] = d;
       Ub[4 * g.box] = e;
     }
+    if (g.ns) {
+      // concentrations C = (rho C) / rho: the reciprocal's quotient with one correction step (exactly 1
+      // for C = 1, so that a unit scalar is carried exactly like the density)
+      const double* Sb = V.a.s[reg] + (long long)b * g.ns * g.box + c;
+      double* Cb = V.a.cs + (long long)b * g.ns * g.box + c;
+      for (int q = 0; q < g.ns; ++q) {
+        const double sq = Sb[(long long)q * g.box];
+        const double c0 = sq * id;
+        Cb[(long long)q * g.box] = fma(fma(-d, c0, sq), id, c0);
+      }
+    }
     TW* Wb = static_cast<TW*>(V.a.w) + (long long)b * 8 * g.box + c;
     const TW wx = to_wtype<TW>(vx), wy = to_wtype<TW>(vy), wz = to_wtype<TW>(vz);
     const TW ux = to_wtype<TW>(bcx), uy = to_wtype<TW>(bcy), uz = to_wtype<TW>(bcz);
@@ -301,6 +312,11 @@ __global__ void __launch_bounds__(256) k_ghosts(MeshView single, const MeshView*
       double* Ud = U + (long long)b * 5 * g.box + c;
 #pragma unroll
       for (int v = 0; v < 5; ++v) Ud[(long long)v * g.box] = Us[(long long)v * g.box];
+      if (g.ns) {  // passive scalars ride with the conserved variables
+        const double* Ss = V.a.s[reg] + (long long)src * g.ns * g.box + sc;
+        double* Sd = V.a.s[reg] + (long long)b * g.ns * g.box + c;
+        for (int q = 0; q < g.ns; ++q) Sd[(long long)q * g.box] = Ss[(long long)q * g.box];
+      }
     }
   }
   // face-centred field
@@ -332,6 +348,159 @@ cudaError_t launch_ghosts(const MeshView& v, const Dispatch* d, int reg, cudaStr
   const long long grid = d ? d->nwork : tiles_ghosts(v.g);
   if (grid <= 0) return cudaSuccess;
   k_ghosts<<<(unsigned)grid, THREADS, 0, st>>>(v, d ? d->views : nullptr, d ? d->work : nullptr, reg);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Passive scalars (eq. passive_scalars): d(rho C)/dt + div(rho v C) = 0.  C is reconstructed along the sweep
+// with the stage's reconstruction (donor cell, PLM or PPM, as for the primitives) and carried by the
+// Riemann mass flux from the upwind side: F = F_rho C_L if F_rho >= 0, else F_rho C_R.  One thread per face of
+// the block's active cells (the scalars feed no corner EMF).
+// ------------------------------------------------------------------------------------------------
+template <int DIR, int REC, class TF>
+__global__ void __launch_bounds__(256) k_scalar_flux(MeshView V) {
+  const Geom& g = V.g;
+  const int rx = g.mb[0] + (DIR == 0), ry = g.mb[1] + (DIR == 1), rz = g.mb[2] + (DIR == 2);
+  const long long per = (long long)rx * ry * rz;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per * g.nblk) return;
+  const int b = (int)(t / per);
+  int rem = (int)(t - (long long)b * per);
+  const int i = rem % rx + g.ng;
+  rem /= rx;
+  const int j = rem % ry + g.ng;
+  const int k = rem / ry + g.ng;
+  const long long c = cell_off(g, k, j, i);
+  const long long sd = (DIR == 0) ? 1LL : ((DIR == 1) ? (long long)g.sx : (long long)g.sx * g.sy);
+  const double m = to_f64(static_cast<const TF*>(V.a.f[DIR])[(long long)b * 7 * g.box + c]);
+  const bool up = ge0(m);
+  for (int q = 0; q < g.ns; ++q) {
+    const long long o = ((long long)b * g.ns + q) * g.box + c;
+    const double* C = V.a.cs + o;
+    double cl, cr;
+    if (REC == REC_DC) {
+      cl = C[-sd];
+      cr = C[0];
+    } else if (REC == REC_PPM) {
+      double e0, e1;
+      ppm_edges(C[-3 * sd], C[-2 * sd], C[-sd], C[0], C[sd], e0, e1);
+      cl = e1;
+      ppm_edges(C[-2 * sd], C[-sd], C[0], C[sd], C[2 * sd], e0, e1);
+      cr = e0;
+    } else {
+      cl = C[-sd] + 0.5 * vl_slope(C[-2 * sd], C[-sd], C[0]);
+      cr = C[0] - 0.5 * vl_slope(C[-sd], C[0], C[sd]);
+    }
+    V.a.fsc[DIR][o] = up ? m * cl : m * cr;
+  }
+}
+
+template <int DIR, class TF>
+static cudaError_t launch_scalar_dir(const MeshView& v, int recon, cudaStream_t st) {
+  const Geom& g = v.g;
+  const long long n = (long long)g.nblk * (g.mb[0] + (DIR == 0)) * (g.mb[1] + (DIR == 1)) * (g.mb[2] + (DIR == 2));
+  const unsigned grid = (unsigned)((n + THREADS - 1) / THREADS);
+  if (n <= 0) return cudaSuccess;
+  if (recon == REC_DC)
+    k_scalar_flux<DIR, REC_DC, TF><<<grid, THREADS, 0, st>>>(v);
+  else if (recon == REC_PPM)
+    k_scalar_flux<DIR, REC_PPM, TF><<<grid, THREADS, 0, st>>>(v);
+  else
+    k_scalar_flux<DIR, REC_PLM, TF><<<grid, THREADS, 0, st>>>(v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scalar_fluxes(const MeshView& v, int recon, int dir, cudaStream_t st) {
+  if (v.a.mixed) {
+    if (dir == 0) return launch_scalar_dir<0, float>(v, recon, st);
+    if (dir == 1) return launch_scalar_dir<1, float>(v, recon, st);
+    return launch_scalar_dir<2, float>(v, recon, st);
+  }
+  if (dir == 0) return launch_scalar_dir<0, double>(v, recon, st);
+  if (dir == 1) return launch_scalar_dir<1, double>(v, recon, st);
+  return launch_scalar_dir<2, double>(v, recon, st);
+}
+
+// Register update of the scalar masses, written as the conserved variables' update in k_update (same
+// association, same weights), so that a unit scalar stays bitwise equal to the density.
+template <bool PLAIN>
+__global__ void __launch_bounds__(256) k_scalar_update(MeshView V, int base_reg, int out_reg, double h, double g_base,
+                                                       double g_other) {
+  const Geom& g = V.g;
+  const long long per = (long long)g.mb[0] * g.mb[1] * g.mb[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per * g.nblk) return;
+  const int b = (int)(t / per);
+  int rem = (int)(t - (long long)b * per);
+  const int i = rem % g.mb[0] + g.ng;
+  rem /= g.mb[0];
+  const int j = rem % g.mb[1] + g.ng;
+  const int k = rem / g.mb[1] + g.ng;
+  const long long c = cell_off(g, k, j, i);
+  const long long stride[3] = {1LL, (long long)g.sx, (long long)g.sx * g.sy};
+  const double* Sbase = V.a.s[base_reg];
+  const double* Soth = V.a.s[1 - base_reg];
+  double* Sout = V.a.s[out_reg];
+  for (int q = 0; q < g.ns; ++q) {
+    const long long o = ((long long)b * g.ns + q) * g.box + c;
+    double dfl[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) dfl[d] = (V.a.fsc[d][o + stride[d]] - V.a.fsc[d][o]) * g.idx[d];
+    const double L = -((dfl[0] + dfl[1]) + dfl[2]);
+    Sout[o] = (PLAIN ? Sbase[o] : g_base * Sbase[o] + g_other * Soth[o]) + h * L;
+  }
+}
+
+cudaError_t launch_scalar_update(const MeshView& v, int base_reg, int out_reg, double h, double g_base,
+                                 double g_other, cudaStream_t st) {
+  const Geom& g = v.g;
+  const long long n = (long long)g.nblk * g.mb[0] * g.mb[1] * g.mb[2];
+  const unsigned grid = (unsigned)((n + THREADS - 1) / THREADS);
+  if (n <= 0 || g.ns == 0) return cudaSuccess;
+  if (g_base == 1.0 && g_other == 0.0)
+    k_scalar_update<true><<<grid, THREADS, 0, st>>>(v, base_reg, out_reg, h, g_base, g_other);
+  else
+    k_scalar_update<false><<<grid, THREADS, 0, st>>>(v, base_reg, out_reg, h, g_base, g_other);
+  return cudaGetLastError();
+}
+
+// Global-array I/O of the scalars: rho C = rho c on the active cells of register 0 (from concentrations
+// c[q][NZ][NY][NX]), and the masses out[q][NZ][NY][NX].
+__global__ void k_scalars_io(Geom g, Arrays a, const double* c, double* out) {
+  const long long per = (long long)g.mb[0] * g.mb[1] * g.mb[2];
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per * g.nblk) return;
+  const int b = (int)(t / per);
+  int rem = (int)(t - (long long)b * per);
+  const int i = rem % g.mb[0];
+  rem /= g.mb[0];
+  const int j = rem % g.mb[1];
+  const int k = rem / g.mb[1];
+  int loc[3];
+  block_loc(g, b, loc);
+  const long long gi = ((long long)(loc[2] * g.mb[2] + k) * g.N[1] + (loc[1] * g.mb[1] + j)) * g.N[0] +
+                       (loc[0] * g.mb[0] + i);
+  const long long nc = (long long)g.N[0] * g.N[1] * g.N[2];
+  const long long cc = cell_off(g, k + g.ng, j + g.ng, i + g.ng);
+  const double rho = a.u[0][(long long)b * 5 * g.box + cc];
+  for (int q = 0; q < g.ns; ++q) {
+    const long long o = ((long long)b * g.ns + q) * g.box + cc;
+    if (c)
+      a.s[0][o] = rho * c[q * nc + gi];
+    else
+      out[q * nc + gi] = a.s[0][o];
+  }
+}
+
+cudaError_t launch_scatter_scalars(const Geom& g, const Arrays& a, const double* c, cudaStream_t st) {
+  const long long n = (long long)g.nblk * g.mb[0] * g.mb[1] * g.mb[2];
+  k_scalars_io<<<(unsigned)((n + THREADS - 1) / THREADS), THREADS, 0, st>>>(g, a, c, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_scalars(const Geom& g, const Arrays& a, double* out, cudaStream_t st) {
+  const long long n = (long long)g.nblk * g.mb[0] * g.mb[1] * g.mb[2];
+  k_scalars_io<<<(unsigned)((n + THREADS - 1) / THREADS), THREADS, 0, st>>>(g, a, nullptr, out);
   return cudaGetLastError();
 }
 

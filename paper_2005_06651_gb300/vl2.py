@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("riemann", ctypes.c_int), ("precision", ctypes.c_int),
                 ("bc", ctypes.c_int * 6), ("dfloor", ctypes.c_double), ("pfloor", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("adjoint", ctypes.c_int), ("integrator", ctypes.c_int),
-                ("recon", ctypes.c_int)]
+                ("recon", ctypes.c_int), ("nscalars", ctypes.c_int)]
 
 
 class Layout(ctypes.Structure):
@@ -58,11 +58,11 @@ EXPORTS = ["vl2_workspace_bytes", "vl2_mesh_create", "vl2_mesh_destroy", "vl2_bl
            "vl2_profile_read", "vl2_launch_count", "vl2_totals_noalloc", "vl2_batch_workspace_bytes",
            "vl2_batch_create", "vl2_batch_destroy", "vl2_batch_autotune", "vl2_batch_step", "vl2_batch_run",
            "vl2_batch_launch_count", "vl2_batch_last_error", "vl2_set_cons", "vl2_step_vjp", "vl2_prims_vjp",
-           "vl2_debug_riemann_vjp", "vl2_last_error"]
+           "vl2_debug_riemann_vjp", "vl2_last_error", "vl2_set_scalars", "vl2_get_scalars"]
 NOALLOC_MAX_NZ = 4096
-K_PRIM, K_GHOSTS, K_FLUX_DC, K_FLUX_PLM, K_EMF, K_UPDATE, K_FLUX_PPM = range(7)
+K_PRIM, K_GHOSTS, K_FLUX_DC, K_FLUX_PLM, K_EMF, K_UPDATE, K_FLUX_PPM, K_SCALARS = range(8)
 KERNEL_KINDS = {K_PRIM: "prim", K_GHOSTS: "ghosts", K_FLUX_DC: "flux_dc", K_FLUX_PLM: "flux_plm", K_EMF: "emf",
-                K_UPDATE: "update", K_FLUX_PPM: "flux_ppm"}
+                K_UPDATE: "update", K_FLUX_PPM: "flux_ppm", K_SCALARS: "scalars"}
 
 
 def load(path: str = LIB_PATH):
@@ -153,7 +153,7 @@ class Mesh:
 
     def __init__(self, nx, mb, xmin=(0.0, 0.0, 0.0), xmax=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, cfl=0.3,
                  riemann=HLLD, bc=(PERIODIC,) * 6, dfloor=1e-12, pfloor=1e-12, precision=FP64, device=None,
-                 stream=None, adjoint=False, integrator=VL2, recon=PLM, ng=None):
+                 stream=None, adjoint=False, integrator=VL2, recon=PLM, ng=None, nscalars=0):
         import torch
 
         L = load()
@@ -169,6 +169,8 @@ class Mesh:
         p.mb[:] = self.mb
         p.ng = (3 if recon == PPM else 2) if ng is None else int(ng)
         p.recon = int(recon)
+        p.nscalars = int(nscalars)
+        self.nscalars = int(nscalars)
         p.xmin[:] = self.xmin
         p.xmax[:] = self.xmax
         p.gamma, p.cfl = self.gamma, self.cfl
@@ -227,6 +229,18 @@ class Mesh:
         ptrs = [_ptr(x) for x in keep]
         where = _where_of(ptrs)
         _check(load().vl2_set_prims(self._h, *[ctypes.c_void_p(p) for p, _ in ptrs], where), self._h)
+
+    def set_scalars(self, c):
+        """Concentrations c (nscalars, NZ, NY, NX), host array or CUDA tensor; set the state first."""
+        keep = np.ascontiguousarray(c, dtype=np.float64) if isinstance(c, np.ndarray) else c
+        ptr, where = _ptr(keep)
+        _check(load().vl2_set_scalars(self._h, ctypes.c_void_p(ptr), where), self._h)
+
+    def get_scalars(self):
+        """Scalar masses rho C, (nscalars, NZ, NY, NX)."""
+        out = np.empty((self.nscalars,) + self.shape)
+        _check(load().vl2_get_scalars(self._h, ctypes.c_void_p(out.ctypes.data), HOST), self._h)
+        return out
 
     def set_cons(self, u, b1, b2, b3):
         keep = [np.ascontiguousarray(x, dtype=np.float64) if isinstance(x, np.ndarray) else x for x in (u, b1, b2, b3)]
