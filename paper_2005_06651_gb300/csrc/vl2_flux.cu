@@ -163,9 +163,10 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
       }
 #pragma unroll
       for (int n = 0; n < 7; ++n) {
-        const T delta = pos[n] ? (T(2) * (dl[n] * dr[n])) * rec[n] : T(0);
-        smem[sidx(n, 0, p, c)] = q0[n] - T(0.5) * delta;  // value at the cell's lower face
-        smem[sidx(n, 1, p, c)] = q0[n] + T(0.5) * delta;  // value at the cell's upper face
+        // delta/2 = dl dr / (dl + dr): the factors 2 and 1/2 of the limited slope cancel exactly
+        const T half = pos[n] ? (dl[n] * dr[n]) * rec[n] : T(0);
+        smem[sidx(n, 0, p, c)] = q0[n] - half;  // value at the cell's lower face
+        smem[sidx(n, 1, p, c)] = q0[n] + half;  // value at the cell's upper face
       }
     }
   }

@@ -24,6 +24,12 @@ __device__ __forceinline__ double rcp_nr(double b) {
   const double e = fma(-b, r, 1.0);
   return fma(r, fma(e, e, e), r);
 }
+__device__ __forceinline__ double rsqrt_nr(double x) {  // x a positive normal number
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double h = fma(-(x * y), y, 1.0);
+  return fma(y * h, fma(0.375, h, 0.5), y);
+}
 __device__ __forceinline__ double sqrt_nr(double x) {
   double y;
   asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
@@ -43,6 +49,8 @@ template <class R> __device__ __forceinline__ R inv(R x) { return R(1) / x; }
 template <> __device__ __forceinline__ double inv<double>(double x) { return rcp_nr(x); }
 template <class R> __device__ __forceinline__ R root(R x) { return sqrt(x); }
 template <> __device__ __forceinline__ double root<double>(double x) { return sqrt_nr(x); }
+template <class R> __device__ __forceinline__ R rroot(R x) { return rsqrt(x); }
+template <> __device__ __forceinline__ double rroot<double>(double x) { return rsqrt_nr(x); }
 
 // ---- float <-> double on the integer pipe ----------------------------------------------------------
 // On this part a hardware conversion between float and double occupies the FP64 pipe like an FP64
@@ -82,13 +90,17 @@ __device__ __forceinline__ float to_f32(float x) { return x; }
 // C_f^2 = (a^2 + c_n^2 + c_t^2 + sqrt((a^2 - c_n^2)^2 + c_t^2 (c_t^2 + 2 a^2 + 2 c_n^2))) / 2,
 // a^2 = gamma p / rho, c_n^2 = b_n^2 / rho, c_t^2 = |b_t|^2 / rho.
 template <class R>
-__device__ __forceinline__ R fast_speed_r(R id, R p, R bn2, R bt2, R gamma) {
+__device__ __forceinline__ R fast_speed2_r(R id, R p, R bn2, R bt2, R gamma) {  // C_f^2
   const R asq = gamma * p * id;
   const R cn = bn2 * id;
   const R ct = bt2 * id;
   const R df = asq - cn;
   const R rad = df * df + ct * (ct + R(2) * (asq + cn));
-  return root(R(0.5) * ((asq + cn + ct) + root(rad)));
+  return R(0.5) * ((asq + cn + ct) + root(rad));
+}
+template <class R>
+__device__ __forceinline__ R fast_speed_r(R id, R p, R bn2, R bt2, R gamma) {
+  return root(fast_speed2_r(id, p, bn2, bt2, gamma));
 }
 
 // Conserved 7-vector and physical flux of one sweep-frame state (eq. cons, eq. total_energy).
@@ -224,7 +236,7 @@ __device__ __forceinline__ void hlld_side_flux(HlldSide<R>& S, const R* o_w, R o
   const R vb = (S.w[1] * bn + S.w[2] * S.w[5]) + S.w[3] * S.w[6];
   S.vbst = (sm * bn + S.vt[0] * S.bt[0]) + S.vt[1] * S.bt[1];
   S.est = ((((S.s - S.w[1]) * S.u[4] - S.pt * S.w[1]) + ptst * sm) + bn * (vb - S.vbst)) * isms;
-  const R rs = rsqrt(S.dst);
+  const R rs = rroot(S.dst);
   const R abn = fabs(bn);
   const R sst = left ? sm - abn * rs : sm + abn * rs;
   // region: outer if the outer wave has not reached the interface, single star if the Alfven wave has not
@@ -295,9 +307,9 @@ __device__ __forceinline__ void flux_hlld(const R* wl, const R* wr, R bn, R gamm
   const R btl2 = wl[5] * wl[5] + wl[6] * wl[6];
   const R btr2 = wr[5] * wr[5] + wr[6] * wr[6];
   const R ilr = inv(wl[0] * wr[0]);  // 1/rho_L and 1/rho_R from one reciprocal
-  const R cl = fast_speed_r(wr[0] * ilr, wl[4], bn2, btl2, gamma);
-  const R cr = fast_speed_r(wl[0] * ilr, wr[4], bn2, btr2, gamma);
-  const R cmax = imax(cl, cr);
+  // max(C_f,L, C_f,R) = sqrt(max(C_f,L^2, C_f,R^2)): one square root for both sides
+  const R cmax = root(imax(fast_speed2_r(wr[0] * ilr, wl[4], bn2, btl2, gamma),
+                           fast_speed2_r(wl[0] * ilr, wr[4], bn2, btr2, gamma)));
   const R sl = imin(wl[1], wr[1]) - cmax;
   const R sr = imax(wl[1], wr[1]) + cmax;
   const R ptl = wl[4] + R(0.5) * (bn2 + btl2), ptr = wr[4] + R(0.5) * (bn2 + btr2);
