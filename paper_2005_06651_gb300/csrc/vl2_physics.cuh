@@ -91,12 +91,12 @@ __device__ __forceinline__ float to_f32(float x) { return x; }
 // a^2 = gamma p / rho, c_n^2 = b_n^2 / rho, c_t^2 = |b_t|^2 / rho.
 template <class R>
 __device__ __forceinline__ R fast_speed2_r(R id, R p, R bn2, R bt2, R gamma) {  // C_f^2
-  const R asq = gamma * p * id;
-  const R cn = bn2 * id;
-  const R ct = bt2 * id;
-  const R df = asq - cn;
-  const R rad = df * df + ct * (ct + R(2) * (asq + cn));
-  return R(0.5) * ((asq + cn + ct) + root(rad));
+  // the same form scaled by rho^2 inside the root (rho C_f^2 with gamma p, b_n^2, |b_t|^2), one 1/rho at the end
+  const R gp = gamma * p;
+  const R df = gp - bn2;
+  const R sn = gp + bn2;
+  const R rad = df * df + bt2 * (bt2 + R(2) * sn);
+  return ((sn + bt2) + root(rad)) * (R(0.5) * id);
 }
 template <class R>
 __device__ __forceinline__ R fast_speed_r(R id, R p, R bn2, R bt2, R gamma) {
