@@ -103,13 +103,12 @@ __device__ __forceinline__ R fast_speed_r(R id, R p, R bn2, R bt2, R gamma) {
   return root(fast_speed2_r(id, p, bn2, bt2, gamma));
 }
 
-// Conserved 7-vector and physical flux of one sweep-frame state (eq. cons, eq. total_energy).
+// Conserved 7-vector and physical flux of one sweep-frame state (eq. cons, eq. total_energy), given
+// |B|^2 = bb and the total pressure pt = p + bb/2 of the state.
 template <class R>
-__device__ __forceinline__ void phys_flux(const R* w, R bn, R igm1, R* u, R* f) {
+__device__ __forceinline__ void phys_flux_bb(const R* w, R bn, R igm1, R bb, R pt, R* u, R* f) {
   const R d = w[0], vn = w[1], v1 = w[2], v2 = w[3], p = w[4], b1 = w[5], b2 = w[6];
-  const R bb = (bn * bn + b1 * b1) + b2 * b2;
   const R e = p * igm1 + R(0.5) * d * ((vn * vn + v1 * v1) + v2 * v2) + R(0.5) * bb;
-  const R pt = p + R(0.5) * bb;
   const R vb = (vn * bn + v1 * b1) + v2 * b2;
   const R m = d * vn;
   u[0] = d; u[1] = m; u[2] = d * v1; u[3] = d * v2; u[4] = e; u[5] = b1; u[6] = b2;
@@ -120,6 +119,11 @@ __device__ __forceinline__ void phys_flux(const R* w, R bn, R igm1, R* u, R* f) 
   f[4] = (e + pt) * vn - bn * vb;
   f[5] = b1 * vn - bn * v1;
   f[6] = b2 * vn - bn * v2;
+}
+template <class R>
+__device__ __forceinline__ void phys_flux(const R* w, R bn, R igm1, R* u, R* f) {
+  const R bb = (bn * bn + w[5] * w[5]) + w[6] * w[6];
+  phys_flux_bb(w, bn, igm1, bb, w[4] + R(0.5) * bb, u, f);
 }
 
 // ---- sign tests and orderings on the integer pipe --------------------------------------------
@@ -312,7 +316,8 @@ __device__ __forceinline__ void flux_hlld(const R* wl, const R* wr, R bn, R gamm
                            fast_speed2_r(wl[0] * ilr, wr[4], bn2, btr2, gamma)));
   const R sl = imin(wl[1], wr[1]) - cmax;
   const R sr = imax(wl[1], wr[1]) + cmax;
-  const R ptl = wl[4] + R(0.5) * (bn2 + btl2), ptr = wr[4] + R(0.5) * (bn2 + btr2);
+  const R bbl = bn2 + btl2, bbr = bn2 + btr2;
+  const R ptl = wl[4] + R(0.5) * bbl, ptr = wr[4] + R(0.5) * bbr;
   const R al = (sl - wl[1]) * wl[0], ar = (sr - wr[1]) * wr[0];
   const R iden = inv(ar - al);
   const R sm = ((mul_rn(ar, wr[1]) - mul_rn(al, wl[1])) + (ptl - ptr)) * iden;
@@ -324,7 +329,7 @@ __device__ __forceinline__ void flux_hlld(const R* wl, const R* wr, R bn, R gamm
   S.s = left ? sl : sr;
   S.pt = left ? ptl : ptr;
   S.a = left ? al : ar;
-  phys_flux(S.w, bn, igm1, S.u, S.f);
+  phys_flux_bb(S.w, bn, igm1, left ? bbl : bbr, S.pt, S.u, S.f);
   const R* o_w = left ? wr : wl;
   hlld_side_flux(S, o_w, left ? sr : sl, left ? ar : al, left, sm, bn, bn2, ptst, f);
   if (is0(sm)) {  // both sides are valid at S_M == 0: average them (exact mirror symmetry)
@@ -334,7 +339,7 @@ __device__ __forceinline__ void flux_hlld(const R* wl, const R* wr, R bn, R gamm
     T.s = sr;
     T.pt = ptr;
     T.a = ar;
-    phys_flux(T.w, bn, igm1, T.u, T.f);
+    phys_flux_bb(T.w, bn, igm1, bbr, ptr, T.u, T.f);
     R g[7];
     hlld_side_flux(T, wl, sl, al, false, sm, bn, bn2, ptst, g);
 #pragma unroll
