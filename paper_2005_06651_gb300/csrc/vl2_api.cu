@@ -1017,7 +1017,7 @@ long long batch_tiles(const vl2_mesh* m, int w, const vl2::FluxShape& fs, int ma
   if (w < vl2_batch::W_PLM) return vl2::tiles_flux_dc(g, w - vl2_batch::W_DC, fs);
   const int d = w - vl2_batch::W_PLM;
   vl2::FluxShape f2 = fs;
-  f2.plm_lines = vl2::plm_lines_for(g, d, fs, max_mb);
+  f2.plm_lines = vl2::plm_lines_for(g, d, fs, max_mb, m->rec());
   return vl2::tiles_flux_plm(g, d, f2);
 }
 

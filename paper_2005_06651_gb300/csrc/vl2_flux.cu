@@ -65,8 +65,9 @@ __global__ void __launch_bounds__(256) k_flux(MeshView single, const MeshView* v
 // cell's values at its lower and upper faces, 7 variables), phase B solves the mb+1 Riemann problems of each
 // line from shared memory.  PLM: q -+ delta/2; in FP64 the 7 limiter denominators of a cell share one
 // division (simultaneous inversion: the reciprocal of their product and of its prefix products), and a
-// product outside the normal range falls back to one division per variable.  PPM (ng = 3): the limited
-// parabola's edges from the cell and two neighbours on each side.
+// product outside the normal range falls back to one division per variable.  PPM (ng = 3): phase A first
+// forms the mb+3 limited face values of each line once (a face is shared by the cells on its two sides)
+// into shared memory behind the edge arrays, then limits each cell's parabola from its two faces.
 // ------------------------------------------------------------------------------------------------
 template <int DIR>
 struct LineMap {
@@ -106,8 +107,52 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
   auto sidx = [&](int v, int side, int p, int c) -> int {
     return (DIR == 0) ? (((v * 2 + side) * P + p) * L + c) : (((v * 2 + side) * L + c) * P + p);
   };
-  // phase A: reconstruct cells
-  for (int t = threadIdx.x; t < P * L; t += blockDim.x) {
+  if constexpr (REC == REC_PPM) {
+    // phase A1: the limited face values 0 .. L of every line; face f is the lower face of cell ng-1+f
+    T* fsm = smem + (size_t)14 * P * L;
+    auto fidx = [&](int v, int p, int f) -> int {
+      return (DIR == 0) ? ((v * P + p) * (L + 1) + f) : ((v * (L + 1) + f) * P + p);
+    };
+    for (int t = threadIdx.x; t < P * (L + 1); t += blockDim.x) {
+      const int p = (DIR == 0) ? t / (L + 1) : t % P;
+      const int f = (DIR == 0) ? t % (L + 1) : t / P;
+      const int line = tile * P + p;
+      if (line >= nlines) continue;
+      int li[3];
+      li[DIR] = g.ng - 1 + f;
+      li[TA] = g.ng - 1 + line % na;
+      li[TB] = g.ng - 1 + line / na;
+      const long long o = cell_off(g, li[2], li[1], li[0]);
+#pragma unroll
+      for (int n = 0; n < 7; ++n) {
+        const T* q = Wb + (long long)var[n] * g.box + o;
+        fsm[fidx(n, p, f)] = ppm_face(q[-2 * sd], q[-sd], q[0], q[sd]);
+      }
+    }
+    __syncthreads();
+    // phase A2: each cell's edges from its two faces
+    for (int t = threadIdx.x; t < P * L; t += blockDim.x) {
+      const int p = (DIR == 0) ? t / L : t % P;
+      const int c = (DIR == 0) ? t % L : t / P;
+      const int line = tile * P + p;
+      if (line >= nlines) continue;
+      int li[3];
+      li[DIR] = g.ng - 1 + c;
+      li[TA] = g.ng - 1 + line % na;
+      li[TB] = g.ng - 1 + line / na;
+      const long long o = cell_off(g, li[2], li[1], li[0]);
+#pragma unroll
+      for (int n = 0; n < 7; ++n) {
+        const T* q = Wb + (long long)var[n] * g.box + o;
+        T ql = fsm[fidx(n, p, c)], qr = fsm[fidx(n, p, c + 1)];
+        ppm_cell(q[-2 * sd], q[-sd], q[0], q[sd], q[2 * sd], ql, qr);
+        smem[sidx(n, 0, p, c)] = ql;
+        smem[sidx(n, 1, p, c)] = qr;
+      }
+    }
+  }
+  // phase A: reconstruct cells (PLM)
+  for (int t = threadIdx.x; REC == REC_PLM && t < P * L; t += blockDim.x) {
     const int p = (DIR == 0) ? t / L : t % P;
     const int c = (DIR == 0) ? t % L : t / P;
     const int line = tile * P + p;
@@ -117,16 +162,7 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
     li[TA] = g.ng - 1 + line % na;
     li[TB] = g.ng - 1 + line / na;
     const long long o = cell_off(g, li[2], li[1], li[0]);
-    if constexpr (REC == REC_PPM) {
-#pragma unroll
-      for (int n = 0; n < 7; ++n) {
-        const T* q = Wb + (long long)var[n] * g.box + o;
-        T ql, qr;
-        ppm_edges(q[-2 * sd], q[-sd], q[0], q[sd], q[2 * sd], ql, qr);
-        smem[sidx(n, 0, p, c)] = ql;
-        smem[sidx(n, 1, p, c)] = qr;
-      }
-    } else {
+    {
       T q0[7], dl[7], dr[7], den[7];
       bool pos[7];
 #pragma unroll
@@ -211,10 +247,15 @@ static int lines_tb(const Geom& g, int dir) { return g.mb[dir == 2 ? 1 : 2] + 2;
 
 // Lines per CTA: the requested count, reduced until a CTA's shared memory fits (max_mb = the longest
 // line of any mesh sharing the launch).
-int plm_lines_for(const Geom& g, int dir, const FluxShape& fs, int max_mb) {
+// PPM adds the line's mb+3 face values of 7 variables.
+static size_t line_bytes(int max_mb, int recon, size_t elem) {
+  return ((size_t)(max_mb + 2) * 14 + (recon == REC_PPM ? (size_t)(max_mb + 3) * 7 : 0)) * elem;
+}
+
+int plm_lines_for(const Geom& g, int dir, const FluxShape& fs, int max_mb, int recon) {
   (void)g;
   (void)dir;
-  const size_t per_line = (size_t)(max_mb + 2) * 14 * sizeof(double);
+  const size_t per_line = line_bytes(max_mb, recon, sizeof(double));
   int P = fs.plm_lines > 0 ? fs.plm_lines : 16;
   while (P > 1 && (size_t)P * per_line > PLM_SMEM_MAX) --P;
   return P;
@@ -243,8 +284,8 @@ static cudaError_t launch_typed(const MeshView& v, const Dispatch* d, int reg, i
   const Geom& g = v.g;
   if (recon == REC_PLM || recon == REC_PPM) {
     FluxShape f2 = fs;
-    f2.plm_lines = plm_lines_for(g, DIR, fs, max_mb);
-    const size_t shmem = (size_t)f2.plm_lines * (max_mb + 2) * 14 * sizeof(T);
+    f2.plm_lines = plm_lines_for(g, DIR, fs, max_mb, recon);
+    const size_t shmem = (size_t)f2.plm_lines * line_bytes(max_mb, recon, sizeof(T));
     const long long grid = d ? d->nwork : tiles_flux_plm(g, DIR, f2);
     if (grid <= 0) return cudaSuccess;
     if (recon == REC_PPM)

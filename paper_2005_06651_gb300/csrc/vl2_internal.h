@@ -108,7 +108,7 @@ long long tiles_ghosts(const Geom& g);
 long long tiles_nodes(const Geom& g);  // EMF and update
 long long tiles_flux_dc(const Geom& g, int dir, const FluxShape& fs);
 long long tiles_flux_plm(const Geom& g, int dir, const FluxShape& fs);
-int plm_lines_for(const Geom& g, int dir, const FluxShape& fs, int max_mb);
+int plm_lines_for(const Geom& g, int dir, const FluxShape& fs, int max_mb, int recon);
 
 // ---- launchers (vl2_kernels.cu / vl2_flux.cu); all enqueue on `st`.  d == nullptr: the single mesh v.
 // For batched launches v only selects the precision; dtbox (per-box dt, device) and beta give h. ----

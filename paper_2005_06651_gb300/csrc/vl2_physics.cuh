@@ -383,11 +383,10 @@ __device__ __forceinline__ R ppm_face(R qm2, R qm1, R q0, R qp1) {
   return f;
 }
 
+// The cell step: limits the edges (ql, qr) of cell i, given the face values, from q_{i-2} .. q_{i+2}.
 template <class R>
-__device__ __forceinline__ void ppm_edges(R qm2, R qm1, R q0, R qp1, R qp2, R& ql, R& qr) {
+__device__ __forceinline__ void ppm_cell(R qm2, R qm1, R q0, R qp1, R qp2, R& ql, R& qr) {
   const R C = R(1.25);
-  ql = ppm_face(qm2, qm1, q0, qp1);
-  qr = ppm_face(qm1, q0, qp1, qp2);
   if (!gt0((qr - q0) * (q0 - ql)) || !gt0((qp1 - q0) * (q0 - qm1))) {  // an extremum
     const R d2 = R(6) * ((ql + qr) - R(2) * q0);
     const R d2c = (qm1 + qp1) - R(2) * q0;
@@ -410,6 +409,13 @@ __device__ __forceinline__ void ppm_edges(R qm2, R qm1, R q0, R qp1, R qp2, R& q
     if (ige(fabs(dl), R(2) * fabs(dr))) ql = q0 - R(2) * dr;
     if (ige(fabs(dr), R(2) * fabs(dl))) qr = q0 - R(2) * dl;
   }
+}
+
+template <class R>
+__device__ __forceinline__ void ppm_edges(R qm2, R qm1, R q0, R qp1, R qp2, R& ql, R& qr) {
+  ql = ppm_face(qm2, qm1, q0, qp1);
+  qr = ppm_face(qm1, q0, qp1, qp2);
+  ppm_cell(qm2, qm1, q0, qp1, qp2, ql, qr);
 }
 
 // Upwind CT corner EMF (Gardiner & Stone 2005) for an edge with transverse directions a, b:
