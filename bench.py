@@ -20,6 +20,10 @@ Printed JSON line (rank 0):
               read, a base read and a write of 8 doubles in the corrector) x value / measured HBM copy
               bandwidth
   cpu_baseline the CPU oracle timed on this host's cores on a bounded sample (N = 1, rank 0)
+  forms       the other forms and workloads, each with its own config: mixed precision (512^3 decaying
+              turbulence), batched (1024 uneven boxes), adjoint (checkpointed rollout), integrators
+              (RK2, RK3, VL2 / RK3 with PPM, four passive scalars), blast (the paper's blast wave at 256^3)
+              and meshblocks (single 64^3 MeshBlock rates, MeshBlock-size sweep at 128^3)
 
 --impl reference times the CPU oracle itself on a 64^3 sample of the same workload (8 MeshBlocks of
 32^3): every step is one oracle VL2 cycle of that sample.

@@ -7,7 +7,10 @@
  * predictor over dt/2, PLM corrector over dt), PLM reconstruction of primitives with the van Leer
  * limiter (Sec. 3.2.1), HLLD or HLLE fluxes (Sec. 3.2.2), upwind constrained transport of the
  * face-centred field (Sec. 3.1, Sec. 2.1.1), ghost exchange between blocks (Sec. 2.1.1) and the
- * global CFL time step (Sec. 2.1.7).
+ * global CFL time step (Sec. 2.1.7).  Options: the RK1 / RK2 / RK3 integrators of the same 2S family
+ * (Sec. 3.2.3), PPM reconstruction with three ghost layers (Sec. 3.2.1), passive scalars (eq.
+ * passive_scalars), an FP32-flux mixed precision, a batched form for many independent meshes, and
+ * the adjoint of the VL2 cycle.
  *
  * Conventions shared by every call
  *  - Every call returns a vl2_status; 0 (VL2_OK) is success.  Nothing throws across the ABI.

@@ -11,7 +11,7 @@
  *   - equations of ideal MHD, mu = 1, total energy E = e + rho v^2/2 + B^2/2     (Sec. 3.1, eq. cons,
  *     eq. total_energy), ideal-gas EOS P = (gamma-1) e                          (Sec. 3.1)
  *   - finite volumes: cell-averaged U, face-area-averaged B, edge EMFs (upwind CT) (Sec. 3.1, Sec. 2.1.1)
- *   - MeshBlocks of equal size with N_G = 2 ghost layers, filled from the 26 neighbours
+ *   - MeshBlocks of equal size with N_G = 2 ghost layers (3 for PPM), filled from the 26 neighbours
  *     (periodic wrap, or outflow = copy of the nearest active cell)              (Sec. 2.1, 2.1.1)
  *   - EMFs on edges shared by several MeshBlocks are averaged over the copies   (Sec. 2.1.1)
  *   - donor-cell and PLM reconstruction of primitives, original van Leer limiter (Sec. 3.2.1)
