@@ -125,22 +125,61 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
   if (DT) {
     // The CFL rate max_d (|v_d| + C_f,d) / dx_d of the CTA's cells, in FP64.  Only cells whose
     // single-precision rate is within 1e-4 of the CTA's single-precision maximum (or is not a number) can
-    // hold the FP64 maximum, so only they evaluate it; the result equals the FP64 maximum over all cells.
+    // hold the FP64 maximum, so only they are candidates; the result equals the FP64 maximum over all cells.
+    // The rate is a function of (1/rho, p, v, b_c) alone: candidates of a warp whose eight inputs are
+    // bitwise equal (a region at rest makes whole warps of them) keep one representative, and the
+    // representatives of the CTA are gathered into shared memory and evaluated by its first threads, so
+    // the FP64 work runs in as few warps as there are distinct candidates.
     __shared__ float redf[8];
     __shared__ unsigned long long red[8];
+    __shared__ double cin[8][THREADS];
+    __shared__ int ncand;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float m32 = r32;
     for (int o = 16; o > 0; o >>= 1) m32 = fmaxf(m32, __shfl_xor_sync(0xffffffffu, m32, o));
     if (lane == 0) redf[wid] = m32;
+    if (threadIdx.x == 0) ncand = 0;
     __syncthreads();
     m32 = 0.0f;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m32 = fmaxf(m32, redf[q]);
+    const bool cand = active && (!(r32 < m32 * 0.9999f) || isinf(m32));  // an overflowed estimate: every cell
+    const unsigned cmask = __ballot_sync(0xffffffffu, cand);
+    bool lead = false;
+    if (cand) {
+      unsigned grp = __match_any_sync(cmask, __double_as_longlong(id));
+      grp &= __match_any_sync(cmask, __double_as_longlong(p));
+      grp &= __match_any_sync(cmask, __double_as_longlong(vx));
+      grp &= __match_any_sync(cmask, __double_as_longlong(vy));
+      grp &= __match_any_sync(cmask, __double_as_longlong(vz));
+      grp &= __match_any_sync(cmask, __double_as_longlong(bcx));
+      grp &= __match_any_sync(cmask, __double_as_longlong(bcy));
+      grp &= __match_any_sync(cmask, __double_as_longlong(bcz));
+      lead = (grp & ((1u << lane) - 1u)) == 0u;  // the lowest lane of its group
+    }
+    const unsigned lmask = __ballot_sync(0xffffffffu, lead);
+    int base = 0;
+    if (lane == 0 && lmask) base = atomicAdd(&ncand, __popc(lmask));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (lead) {
+      const int slot = base + __popc(lmask & ((1u << lane) - 1u));  // < blockDim.x: one slot per thread at most
+      cin[0][slot] = id;
+      cin[1][slot] = p;
+      cin[2][slot] = vx;
+      cin[3][slot] = vy;
+      cin[4][slot] = vz;
+      cin[5][slot] = bcx;
+      cin[6][slot] = bcy;
+      cin[7][slot] = bcz;
+    }
+    __syncthreads();
     unsigned long long rate_bits = 0ULL;
-    if (active && (!(r32 < m32 * 0.9999f) || isinf(m32))) {  // an overflowed estimate: evaluate every cell
-      const double bx2 = bcx * bcx, by2 = bcy * bcy, bz2 = bcz * bcz;
-      const double rx = (fabs(vx) + fast_speed_r(id, p, bx2, by2 + bz2, g.gamma)) * g.idx[0];
-      const double ry = (fabs(vy) + fast_speed_r(id, p, by2, bz2 + bx2, g.gamma)) * g.idx[1];
-      const double rz = (fabs(vz) + fast_speed_r(id, p, bz2, bx2 + by2, g.gamma)) * g.idx[2];
+    if ((int)threadIdx.x < ncand) {
+      const int q = threadIdx.x;
+      const double cid = cin[0][q], cp = cin[1][q];
+      const double bx2 = cin[5][q] * cin[5][q], by2 = cin[6][q] * cin[6][q], bz2 = cin[7][q] * cin[7][q];
+      const double rx = (fabs(cin[2][q]) + fast_speed_r(cid, cp, bx2, by2 + bz2, g.gamma)) * g.idx[0];
+      const double ry = (fabs(cin[3][q]) + fast_speed_r(cid, cp, by2, bz2 + bx2, g.gamma)) * g.idx[1];
+      const double rz = (fabs(cin[4][q]) + fast_speed_r(cid, cp, bz2, bx2 + by2, g.gamma)) * g.idx[2];
       const unsigned long long ax = __double_as_longlong(rx), ay = __double_as_longlong(ry),
                                az = __double_as_longlong(rz);
       rate_bits = ax > ay ? ax : ay;
