@@ -234,3 +234,25 @@ def test_floor_reported_and_matches_oracle(vl2, oracle):
     o.new_dt(0.3)
     assert g.floor_count() == o.floor_count() >= 1
     np.testing.assert_allclose(g.get_prims()[4], o.get_prims()[4], rtol=1e-14, atol=1e-14)
+
+
+def test_pinned_host_buffers_match_pageable(vl2):
+    """Page-locked host buffers (torch pinned tensors) in and out give bitwise the state of pageable numpy
+    buffers."""
+    import torch
+
+    prob = inputs.orszag_tang(n=(24, 20, 12), mb=(8, 10, 6), seed=9)
+    a = vl2.Mesh.from_problem(prob)
+    b = vl2.Mesh(prob.nx, prob.mb)
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    b.set_prims(*(pin(x) for x in (prob.w, prob.b1, prob.b2, prob.b3)))
+    for _ in range(2):
+        dt = a.new_dt()
+        assert b.new_dt() == dt
+        a.step(dt)
+        b.step(dt)
+    outs = (torch.zeros((5,) + b.shape, dtype=torch.float64).pin_memory(),
+            *[torch.zeros(s, dtype=torch.float64).pin_memory() for s in b.face_shapes()])
+    b.get_cons(outs)
+    for x, y in zip(a.get_cons(), outs):
+        np.testing.assert_array_equal(x, y.numpy())
