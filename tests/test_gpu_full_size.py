@@ -6,6 +6,9 @@
 - 512^3 decaying turbulence in 4096 MeshBlocks of 32^3, mixed precision: the oracle does not fit this
   size in a test, so what holds at any size is checked: conservation of the totals and div B at FP64
   round-off over two cycles.
+- The later rows at 256^3 in 512 MeshBlocks, one cycle against the oracle (<= 1e-12): VL2 + PPM on the
+  vortex (three ghost layers), the vortex carrying two passive scalars, and the hydrodynamic blast wave
+  (r0 = 0.01, 56 cells), whose uniform regions run the solvers' equal-state branch.
 """
 import numpy as np
 import pytest
@@ -61,3 +64,41 @@ def test_mixed_512cubed_conserves_and_keeps_divb(vl2):
     g.close()
     del g
     torch.cuda.empty_cache()
+
+
+def _one_cycle(vl2, oracle, prob, label, scalars=None, **kw):
+    g = vl2.Mesh.from_problem(prob, **kw)
+    o = oracle.Mesh.from_problem(prob, **kw)
+    if scalars is not None:
+        g.set_scalars(scalars)
+        o.set_scalars(scalars)
+    dt = o.new_dt(0.3)
+    assert g.new_dt() == pytest.approx(dt, rel=1e-13)
+    g.step(dt)
+    o.step(dt)
+    d = float(np.max(state_diff(g.get_cons(), o.get_cons())))
+    ds = 0.0
+    if scalars is not None:
+        os_ = o.get_scalars()
+        ds = float(np.max(np.abs(g.get_scalars() - os_))) / float(np.max(np.abs(os_)))
+    print("%s: max normalised difference %.2e (scalars %.2e)" % (label, d, ds))
+    assert d <= 1e-12 and ds <= 1e-12
+    assert g.floor_count() == 0 and g.divb_norm() <= 1e-13
+    g.close()
+
+
+def test_ppm_256cubed_one_cycle_matches_oracle(vl2, oracle):
+    prob = inputs.orszag_tang(n=256, mb=32, seed=2005)
+    _one_cycle(vl2, oracle, prob, "256^3 VL2 + PPM, one cycle", recon=vl2.PPM)
+
+
+def test_scalars_256cubed_one_cycle_match_oracle(vl2, oracle):
+    prob = inputs.orszag_tang(n=256, mb=32, seed=2005)
+    rng = np.random.default_rng(4004)
+    c = rng.uniform(0.0, 1.0, size=(2, 256, 256, 256))
+    _one_cycle(vl2, oracle, prob, "256^3 with 2 passive scalars, one cycle", scalars=c, nscalars=2)
+
+
+def test_hydro_blast_256cubed_one_cycle_matches_oracle(vl2, oracle):
+    prob = inputs.blast(n=256, mb=32, r0=0.01, magnetized=False)
+    _one_cycle(vl2, oracle, prob, "256^3 hydrodynamic blast, one cycle")
