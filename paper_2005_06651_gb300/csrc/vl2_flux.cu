@@ -63,9 +63,9 @@ __global__ void __launch_bounds__(256) k_flux(MeshView single, const MeshView* v
 // Corrector fluxes with each cell's reconstruction formed once (Sec. 3.2.1).  A CTA takes P lines of faces
 // along DIR: phase A reconstructs the mb+2 cells of each line (ng-1 .. ng+mb) into shared memory (the
 // cell's values at its lower and upper faces, 7 variables), phase B solves the mb+1 Riemann problems of each
-// line from shared memory.  PLM: q -+ delta/2; in FP64 the 7 limiter denominators of a cell share one
-// division (simultaneous inversion: the reciprocal of their product and of its prefix products), and a
-// product outside the normal range falls back to one division per variable.  PPM (ng = 3): phase A first
+// line from shared memory.  PLM: q -+ delta/2, each limiter denominator inverted by the Newton reciprocal
+// (sharing one reciprocal among the 7 variables of a cell through their products measured no faster and
+// needed a range fallback).  PPM (ng = 3): phase A first
 // forms the mb+3 limited face values of each line once (a face is shared by the cells on its two sides)
 // into shared memory behind the edge arrays, then limits each cell's parabola from its two faces.
 // ------------------------------------------------------------------------------------------------
@@ -75,11 +75,6 @@ struct LineMap {
   static constexpr int TA = (DIR == 0) ? 1 : 0;
   static constexpr int TB = (DIR == 2) ? 1 : 2;
 };
-
-__device__ __forceinline__ bool normal_pos(double x) {
-  const long long e = (__double_as_longlong(x) >> 52) & 0x7ff;
-  return e != 0 && e != 0x7ff;
-}
 
 template <int DIR, int RS, class T, int REC>
 __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const MeshView* views, const WorkItem* work,
@@ -176,27 +171,8 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
         den[n] = pos[n] ? dl[n] + dr[n] : T(1);
       }
       T rec[7];
-      if (sizeof(T) == 8) {
-        T pre[7];
-        pre[0] = den[0];
 #pragma unroll
-        for (int n = 1; n < 7; ++n) pre[n] = pre[n - 1] * den[n];
-        if (normal_pos((double)fabs(pre[6]))) {
-          T acc = inv(pre[6]);  // pre[6] is a positive normal number here
-#pragma unroll
-          for (int n = 6; n > 0; --n) {
-            rec[n] = acc * pre[n - 1];
-            acc = acc * den[n];
-          }
-          rec[0] = acc;
-        } else {
-#pragma unroll
-          for (int n = 0; n < 7; ++n) rec[n] = T(1) / den[n];
-        }
-      } else {  // FP32: divisions are cheap, and a 7-fold product could leave the float range
-#pragma unroll
-        for (int n = 0; n < 7; ++n) rec[n] = T(1) / den[n];
-      }
+      for (int n = 0; n < 7; ++n) rec[n] = sizeof(T) == 8 ? inv(den[n]) : T(1) / den[n];
 #pragma unroll
       for (int n = 0; n < 7; ++n) {
         // delta/2 = dl dr / (dl + dr): the factors 2 and 1/2 of the limited slope cancel exactly
