@@ -44,7 +44,8 @@ typedef enum vl2_status {
   VL2_E_ARG = 1,      /* invalid argument (null pointer, bad size, inconsistent parameters) */
   VL2_E_CUDA = 2,     /* a CUDA runtime call or kernel launch failed */
   VL2_E_NONPHYS = 3,  /* a density or pressure floor fired (value floored and counted), or dt not finite */
-  VL2_E_TIMEOUT = 4,  /* a bounded device-side wait expired */
+  VL2_E_TIMEOUT = 4,  /* reserved for a bounded device-side wait that expired; no kernel of this library
+                         waits on another (no spin-waits, no inter-CTA barriers), so no call returns it */
   VL2_E_STATE = 5,    /* call not valid in the mesh's current state */
   VL2_E_NOMEM = 6     /* workspace smaller than vl2_workspace_bytes() */
 } vl2_status;
