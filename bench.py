@@ -53,7 +53,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of
 # the k_flux_plm x sweep on the 128^3 vortex, 2,441,472 faces), scaled to a launch by its faces; valid only
 # for the kernel source it was taken on (hash of the flux and physics sources), else reported as null.
-NCU_TRAFFIC = {"hash": "2a0075ea623102f8", "bytes_per_face": 134.5}
+NCU_TRAFFIC = {"hash": "2b9fad020b33f73b", "bytes_per_face": 134.4}
 
 
 def flux_source_hash():
@@ -462,9 +462,9 @@ def adjoint_form(args, dev, stream, vl2, inputs):
 def integrators_form(args, dev, stream, vl2, inputs):
     """The other 2S integrators of Sec. 3.2.3 and PPM (Sec. 3.2.1) on the plain workload (256^3 vortex, 512
     MeshBlocks of 32^3, FP64, HLLD): RK2 (SSPRK(2,2)) and RK3 (SSPRK(3,3)) with PLM in every stage, and VL2
-    and RK3 with PPM (three ghost layers), and VL2 + PLM carrying four passive scalars (eq. passive_scalars),
-    zone-cycles/s next to VL2 + PLM (the bench line).  A cycle has 2 or 3 PLM / PPM stages against VL2's
-    donor-cell + PLM / PPM."""
+    and RK3 with PPM (three ghost layers), VL2 + PLM carrying four passive scalars (eq. passive_scalars), and
+    VL2 + PLM with the smoothed CT upwind weight (delta 1e-4, where most faces saturate, and delta 1, where
+    none does), zone-cycles/s next to VL2 + PLM (the bench line).  A cycle has 2 or 3 PLM / PPM stages against VL2's donor-cell + PLM / PPM."""
     import torch
 
     prob = inputs.orszag_tang(n=args.n, mb=args.mb, seed=2005)
@@ -472,10 +472,14 @@ def integrators_form(args, dev, stream, vl2, inputs):
         args.n, (args.n // args.mb) ** 3, args.mb), "steps": args.rk_steps, "dtype": "f64"}}
     import numpy as np
 
-    for name, integ, recon, nsc in (("rk2", vl2.RK2, vl2.PLM, 0), ("rk3", vl2.RK3, vl2.PLM, 0),
-                                    ("vl2_ppm", vl2.VL2, vl2.PPM, 0), ("rk3_ppm", vl2.RK3, vl2.PPM, 0),
-                                    ("vl2_4_scalars", vl2.VL2, vl2.PLM, 4)):
-        m = vl2.Mesh.from_problem(prob, device=dev, stream=stream, integrator=integ, recon=recon, nscalars=nsc)
+    for name, integ, recon, nsc, delta in (("rk2", vl2.RK2, vl2.PLM, 0, 0.0), ("rk3", vl2.RK3, vl2.PLM, 0, 0.0),
+                                           ("vl2_ppm", vl2.VL2, vl2.PPM, 0, 0.0),
+                                           ("rk3_ppm", vl2.RK3, vl2.PPM, 0, 0.0),
+                                           ("vl2_4_scalars", vl2.VL2, vl2.PLM, 4, 0.0),
+                                           ("vl2_ct_smooth", vl2.VL2, vl2.PLM, 0, 1e-4),
+                                           ("vl2_ct_smooth_wide", vl2.VL2, vl2.PLM, 0, 1.0)):
+        m = vl2.Mesh.from_problem(prob, device=dev, stream=stream, integrator=integ, recon=recon, nscalars=nsc,
+                                  ct_delta=delta)
         if nsc:
             rng = np.random.default_rng(4004)
             m.set_scalars(rng.uniform(0.0, 1.0, size=(nsc,) + prob.w.shape[1:]))

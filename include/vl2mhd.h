@@ -83,6 +83,12 @@ typedef struct vl2_params {
                          RK1 always use donor cell (Sec. 3.2.3). */
   int nscalars;       /* passive scalars rho C_i, d(rho C_i)/dt + div(rho v C_i) = 0 (eq. passive_scalars):
                          0 .. VL2_MAX_SCALARS; 0 with adjoint; not in a batch */
+  double ct_delta;    /* 0 (the default): the upwind CT corner picks the cell by the sign of the face mass flux,
+                         the mean at zero (Sec. 3.1, gs05).  > 0: an option beside the paper's method, the
+                         weight (1 + tanh(m / ct_delta)) / 2 on the upwind-side gradient, in mass-flux units;
+                         it equals the sign switch where tanh saturates and at m = 0, and makes the corner a
+                         smooth function of m (with adjoint, vl2_step_vjp then carries dw/dm).  Finite;
+                         not in a batch. */
 } vl2_params;
 
 #define VL2_MAX_SCALARS 16
@@ -204,7 +210,8 @@ vl2_status vl2_debug_emfs(vl2_mesh* mesh, int recon, double* e1, double* e2, dou
  * adjoint lam_out of the cycle's output (u [5][NZ][NY][NX] and face fields b1..b3, global layout, device),
  * writes lam_in = J(x)^T lam_out (same layout, device) where J is the Jacobian of the cycle.  The
  * cycle's forward intermediates are recomputed from x, which is left unchanged.  Reverse order: update,
- * upwind-CT EMFs (upwind choices frozen at x), Riemann fluxes (reverse-mode derivative replaying the
+ * upwind-CT EMFs (upwind choices frozen at x; with params.ct_delta > 0 the smoothed weights and their
+ * derivative in the face mass fluxes), Riemann fluxes (reverse-mode derivative replaying the
  * forward flux's arithmetic and branches), PLM (limiter switch frozen), cons->prim, ghost exchange;
  * corrector first, then the predictor.  Face entries follow the global layout: the adjoint of face N of a
  * periodic direction is kept apart from face 0 (they are separate array entries).  Needs a mesh created

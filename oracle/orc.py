@@ -45,7 +45,8 @@ def lib():
         ip = ctypes.POINTER(ctypes.c_int)
         L.orc_mesh_new.restype = ctypes.c_void_p
         L.orc_mesh_new.argtypes = [ip, ip, dp, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.c_double,
-                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_double]
         L.orc_set_scalars.argtypes = [ctypes.c_void_p, dp]
         L.orc_get_scalars.argtypes = [ctypes.c_void_p, dp]
         L.orc_mesh_free.argtypes = [ctypes.c_void_p]
@@ -79,8 +80,10 @@ def lib():
         L.orc_count_face_ops.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
                                          ctypes.POINTER(ctypes.c_longlong)]
         L.orc_ct_corner.argtypes = [dp, dp, dp, dp, dp]
-        L.orc_tl_step.argtypes = [ip, ip, dp, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.c_double] + [dp] * 16
-        L.orc_step_cons.argtypes = [ip, ip, dp, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.c_double] + [dp] * 8
+        L.orc_tl_step.argtypes = [ip, ip, dp, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.c_double,
+                                  ctypes.c_double] + [dp] * 16
+        L.orc_step_cons.argtypes = [ip, ip, dp, dp, ctypes.c_double, ctypes.c_int, ip, ctypes.c_double,
+                                    ctypes.c_double] + [dp] * 8
         L.orc_ct_corner.restype = ctypes.c_double
         _lib = L
     return _lib
@@ -163,26 +166,28 @@ def _geom_args(nx, mb, xmin, xmax, bc):
             (ctypes.c_double * 3)(*xmax), (ctypes.c_int * 6)(*bc))
 
 
-def tl_step(prob_geom, dt, state, tangent, gamma=5.0 / 3.0, riemann=HLLD):
+def tl_step(prob_geom, dt, state, tangent, gamma=5.0 / 3.0, riemann=HLLD, ct_delta=0.0):
     """Tangent-linear of one VL2 cycle (dual numbers): state/tangent = (u, b1, b2, b3) global arrays.
-    prob_geom = (nx, mb, xmin, xmax, bc).  Returns (new state, J @ tangent)."""
+    prob_geom = (nx, mb, xmin, xmax, bc); ct_delta > 0 takes the smoothed CT upwind weight, whose
+    derivative in the mass flux the tangent carries.  Returns (new state, J @ tangent)."""
     nx, mb, xmin, xmax, bc = prob_geom
     ins = [_c64(a) for a in state] + [_c64(a) for a in tangent]
     outs = [np.zeros_like(a) for a in ins]
     g = _geom_args(nx, mb, xmin, xmax, bc)
-    lib().orc_tl_step(g[0], g[1], g[2], g[3], float(gamma), riemann, g[4], float(dt),
+    lib().orc_tl_step(g[0], g[1], g[2], g[3], float(gamma), riemann, g[4], float(dt), float(ct_delta),
                       *[_dp(a) for a in ins[:4]], *[_dp(a) for a in ins[4:]], *[_dp(a) for a in outs[:4]],
                       *[_dp(a) for a in outs[4:]])
     return tuple(outs[:4]), tuple(outs[4:])
 
 
-def step_cons(prob_geom, dt, state, gamma=5.0 / 3.0, riemann=HLLD):
+def step_cons(prob_geom, dt, state, gamma=5.0 / 3.0, riemann=HLLD, ct_delta=0.0):
     """One VL2 cycle from a conserved state (global arrays); returns the new state."""
     nx, mb, xmin, xmax, bc = prob_geom
     ins = [_c64(a) for a in state]
     outs = [np.zeros_like(a) for a in ins]
     g = _geom_args(nx, mb, xmin, xmax, bc)
-    lib().orc_step_cons(g[0], g[1], g[2], g[3], float(gamma), riemann, g[4], float(dt), *[_dp(a) for a in ins],
+    lib().orc_step_cons(g[0], g[1], g[2], g[3], float(gamma), riemann, g[4], float(dt), float(ct_delta),
+                        *[_dp(a) for a in ins],
                         *[_dp(a) for a in outs])
     return tuple(outs)
 
@@ -194,11 +199,11 @@ def step_cons(prob_geom, dt, state, gamma=5.0 / 3.0, riemann=HLLD):
 class Mesh:
     """Oracle mesh of equal-size MeshBlocks holding one VL2 state.  recon is the reconstruction of the
     higher-order stages (PLM or PPM); ng the ghost layers (default 2, or 3 with PPM); nscalars the passive
-    scalars (eq. passive_scalars)."""
+    scalars (eq. passive_scalars); ct_delta > 0 smooths the CT upwind switch (an option, not the paper's)."""
 
     def __init__(self, nx, mb, xmin=(0.0, 0.0, 0.0), xmax=(1.0, 1.0, 1.0), gamma=5.0 / 3.0,
                  riemann=HLLD, bc=(0,) * 6, dfloor=1e-12, pfloor=1e-12, integrator=VL2, recon=PLM, ng=None,
-                 nscalars=0):
+                 nscalars=0, ct_delta=0.0):
         self.nx = tuple(int(v) for v in nx)
         self.mb = tuple(int(v) for v in mb)
         self.xmin, self.xmax = tuple(xmin), tuple(xmax)
@@ -212,7 +217,7 @@ class Mesh:
         self.ng = (3 if recon == PPM else 2) if ng is None else int(ng)
         self.nscalars = int(nscalars)
         self._h = L.orc_mesh_new(ia, ib, da, db, gamma, riemann, bcs, dfloor, pfloor, integrator, recon, self.ng,
-                                 self.nscalars)
+                                 self.nscalars, float(ct_delta))
         if not self._h:
             raise ValueError("invalid oracle mesh parameters")
 

@@ -137,6 +137,11 @@ static inline Dual sqrt(Dual a) {
   const double r = std::sqrt(a.v);
   return Dual(r, a.d / (2.0 * r));
 }
+static inline double tanh(double a) { return std::tanh(a); }
+static inline Dual tanh(Dual a) {  // d tanh(x) / dx = 1 - tanh(x)^2
+  const double t = std::tanh(a.v);
+  return Dual(t, a.d * (1.0 - t * t));
+}
 template <class T> static inline T make_scalar(double v, double t);
 template <> inline double make_scalar<double>(double v, double) { return v; }
 template <> inline Dual make_scalar<Dual>(double v, double t) { return Dual(v, t); }
@@ -431,9 +436,29 @@ static void ppm_edges(const T q[5], T& ql, T& qr) {
  *   eb[0], eb[1]: b-face EMFs at a-index i-1, i         (y-faces (i-1, j-1/2), (i, j-1/2))
  *   ec[0..3]: cell-centre EMFs at (i-1,j-1), (i,j-1), (i-1,j), (i,j)
  *   ma[0], ma[1]: a-face mass fluxes at j-1, j;  mb[0], mb[1]: b-face mass fluxes at i-1, i. */
+/* [option, not the paper's method] Smoothed upwind weight for the corner corrections: the gradient of
+ * the cell on the side the mass flux m comes from gets the weight w = (1 + tanh(m / delta)) / 2, the
+ * other cell's 1 - w.  w is 1/2 at m = 0 (the mean above) and tends to the upwind choice for
+ * |m| >> delta; written w lo + (1 - w) hi, it equals the sharp choice bitwise where tanh saturates and
+ * at m = 0.  delta = 0 is the sign switch itself.  For dual numbers the weight carries the tangent of m
+ * (dw/dm = (1 - tanh^2) / (2 delta)): the smoothed corner is differentiable in the mass flux, the switch
+ * is not. */
 template <class T>
-static T ct_corner(const T ea[2], const T eb[2], const T ec[4], const T ma[2], const T mb[2]) {
+static T ct_smooth_pick(const T& m, double delta, const T& lo, const T& hi) {
+  const T w = 0.5 * (1.0 + tanh(m / delta));
+  return w * lo + (1.0 - w) * hi;
+}
+
+template <class T>
+static T ct_corner(const T ea[2], const T eb[2], const T ec[4], const T ma[2], const T mb[2], double delta = 0.0) {
   const T sum4 = (ea[0] + ea[1]) + (eb[0] + eb[1]);
+  if (delta > 0.0) {
+    const T tlo = ct_smooth_pick(ma[0], delta, eb[0] - ec[0], eb[1] - ec[1]);
+    const T thi = ct_smooth_pick(ma[1], delta, ec[2] - eb[0], ec[3] - eb[1]);
+    const T slo = ct_smooth_pick(mb[0], delta, ea[0] - ec[0], ea[1] - ec[2]);
+    const T shi = ct_smooth_pick(mb[1], delta, ec[1] - ea[0], ec[3] - ea[1]);
+    return (0.25 * sum4 + 0.25 * (tlo - thi)) + 0.25 * (slo - shi);
+  }
   /* gradient along b between the corner and the a-face below it, in the cell chosen by ma[0] */
   const T dlo_m = eb[0] - ec[0];  // cell i-1
   const T dlo_p = eb[1] - ec[1];  // cell i
@@ -491,6 +516,7 @@ struct Params {
   int recon;  // reconstruction of the PLM stages: REC_PLM or REC_PPM (VL2 corrector, RK2/RK3 stages)
   int ng;     // ghost layers: 2 (DC, PLM) or 3 (PPM)
   int nscal;  // passive scalars (eq. passive_scalars)
+  double ct_delta;  // smoothed CT upwind weight width (0: the paper's sign switch)
 };
 
 /* dense 3D array (k, j, i), i fastest */
@@ -845,7 +871,7 @@ template <class T> struct Mesh {
             ec[1] = cell_emf(B, e, km_b, jm_b, im_b); // (a,   b-1)
             ec[2] = cell_emf(B, e, km_a, jm_a, im_a); // (a-1, b)
             ec[3] = cell_emf(B, e, k, j, i);          // (a,   b)
-            B.emf[e](k, j, i) = ct_corner(ea, eb, ec, ma, mb);
+            B.emf[e](k, j, i) = ct_corner(ea, eb, ec, ma, mb, P.ct_delta);
           }
     }
   }
@@ -1189,8 +1215,10 @@ extern "C" {
 
 void* orc_mesh_new(const int* nx, const int* mb, const double* xmin, const double* xmax, double gamma,
                    int riemann, const int* bc, double dfloor, double pfloor, int integrator, int recon, int ng,
-                   int nscal) {
+                   int nscal, double ct_delta) {
   orc::Params p;
+  if (!(ct_delta >= 0.0) || !std::isfinite(ct_delta)) return nullptr;
+  p.ct_delta = ct_delta;
   if (recon != orc::REC_PLM && recon != orc::REC_PPM) return nullptr;
   if (nscal < 0 || nscal > 16) return nullptr;
   p.nscal = nscal;
@@ -1393,7 +1421,8 @@ void orc_totals(void* m, double* out) {
 /* Tangent-linear of one VL2 cycle with a fixed dt, by dual numbers: from the conserved state (u, b1..3)
  * and a direction (du, db1..3), all in the global layout, return the new state and J*direction. */
 void orc_tl_step(const int* nx, const int* mb, const double* xmin, const double* xmax, double gamma, int riemann,
-                 const int* bc, double dt, const double* u, const double* b1, const double* b2, const double* b3,
+                 const int* bc, double dt, double ct_delta, const double* u, const double* b1, const double* b2,
+                 const double* b3,
                  const double* du, const double* db1, const double* db2, const double* db3, double* u_out,
                  double* b1_out, double* b2_out, double* b3_out, double* du_out, double* db1_out, double* db2_out,
                  double* db3_out) {
@@ -1413,6 +1442,7 @@ void orc_tl_step(const int* nx, const int* mb, const double* xmin, const double*
   p.recon = orc::REC_PLM;
   p.ng = 2;
   p.nscal = 0;
+  p.ct_delta = ct_delta;
   orc::Mesh<orc::Dual> M;
   M.init(p);
   orc::set_cons(M, u, du, b1, db1, b2, db2, b3, db3);
@@ -1423,7 +1453,8 @@ void orc_tl_step(const int* nx, const int* mb, const double* xmin, const double*
 
 /* Plain (value) cycle from a conserved state, same entry form as orc_tl_step (no tangent). */
 void orc_step_cons(const int* nx, const int* mb, const double* xmin, const double* xmax, double gamma, int riemann,
-                   const int* bc, double dt, const double* u, const double* b1, const double* b2, const double* b3,
+                   const int* bc, double dt, double ct_delta, const double* u, const double* b1, const double* b2,
+                 const double* b3,
                    double* u_out, double* b1_out, double* b2_out, double* b3_out) {
   orc::Params p;
   for (int d = 0; d < 3; ++d) {
@@ -1441,6 +1472,7 @@ void orc_step_cons(const int* nx, const int* mb, const double* xmin, const doubl
   p.recon = orc::REC_PLM;
   p.ng = 2;
   p.nscal = 0;
+  p.ct_delta = ct_delta;
   orc::Mesh<double> M;
   M.init(p);
   orc::set_cons(M, u, nullptr, b1, nullptr, b2, nullptr, b3, nullptr);

@@ -146,6 +146,29 @@ __device__ __forceinline__ void pick_w(double m, double& w0, double& w1) {
   }
 }
 
+// Smoothed upwind weight of the forward corner (w = (1 + tanh(m / delta)) / 2, flat at 0 or 1 where
+// |m| > 20 delta) and its derivative in the mass flux, dw/dm = (1 - tanh^2) / (2 delta).
+__device__ __forceinline__ void smooth_w(double m, double delta, double& w, double& dw) {
+  if (fabs(m) > 20.0 * delta) {
+    w = m > 0.0 ? 1.0 : 0.0;
+    dw = 0.0;
+    return;
+  }
+  const double t = m == 0.0 ? 0.0 : tanh(m / delta);
+  w = 0.5 * (1.0 + t);
+  dw = 0.5 * (1.0 - t * t) / delta;
+}
+
+__device__ __forceinline__ void pick_w(double m, double delta, double& w0, double& w1) {
+  if (delta > 0.0) {
+    double dw;
+    smooth_w(m, delta, w0, dw);
+    w1 = 1.0 - w0;
+  } else {
+    pick_w(m, w0, w1);
+  }
+}
+
 // Upwind weights and adjoint coefficients of one corner EMF (family e, node c): the corner EMF is
 //   E = cea0 ea(b-1) + cea1 ea(b) + ceb0 eb(a-1) + ceb1 eb(a) + cec0 ec(a-1,b-1) + cec1 ec(a,b-1)
 //     + cec2 ec(a-1,b) + cec3 ec(a,b)
@@ -154,12 +177,12 @@ struct EdgeCoef {
   double cea0, cea1, ceb0, ceb1, cec0, cec1, cec2, cec3;
 };
 __device__ __forceinline__ EdgeCoef edge_coef(const double* Ma, const double* Mb, long long c, long long sa,
-                                              long long sb) {
+                                              long long sb, double delta) {
   double w0, w1, u0, u1, s0, s1, r0, r1;
-  pick_w(Ma[c - sb], w0, w1);  // tlo: gradient along b below the corner, by the a-face mass flux at b-1
-  pick_w(Ma[c], u0, u1);       // thi
-  pick_w(Mb[c - sa], s0, s1);  // slo: gradient along a, by the b-face mass flux at a-1
-  pick_w(Mb[c], r0, r1);       // shi
+  pick_w(Ma[c - sb], delta, w0, w1);  // tlo: gradient along b below the corner, by the a-face mass flux at b-1
+  pick_w(Ma[c], delta, u0, u1);       // thi
+  pick_w(Mb[c - sa], delta, s0, s1);  // slo: gradient along a, by the b-face mass flux at a-1
+  pick_w(Mb[c], delta, r0, r1);       // shi
   EdgeCoef k;
   k.cea0 = 0.25 * (1.0 + s0 + r0);
   k.cea1 = 0.25 * (1.0 + s1 + r1);
@@ -180,14 +203,52 @@ __device__ __forceinline__ bool edge_valid(const Geom& g, int e, const int* n) {
   return ok;
 }
 
+// Of the corner EMF of family e at node n + da s_a + db s_b, lam_E times dE/dw of one of its weights (slot 0:
+// tlo by ma[0], 1: thi by ma[1], 2: slo by mb[0], 3: shi by mb[1]); each correction enters E as
+// +-(1/4)(w lo + (1 - w) hi), so dE/dw = +-(1/4)(lo - hi).  Zero outside the corners that exist.
+__device__ __forceinline__ double corner_dm(const Geom& g, const double* W, const double* const* M, long long e5off,
+                                           long long e6off, const double* const* LE, const long long* stride,
+                                           const int* li, int b, long long c, int e, int da, int db, int slot) {
+  const int a = (e + 1) % 3, bq = (e + 2) % 3;
+  int n[3] = {li[0], li[1], li[2]};
+  n[a] += da;
+  n[bq] += db;
+  if (!edge_valid(g, e, n)) return 0.0;
+  const long long sa = stride[a], sb = stride[bq];
+  const long long cn = c + da * sa + db * sb;
+  const double lam = LE[e][cn];
+  if (lam == 0.0) return 0.0;
+  const double* Wb = W + (long long)b * 8 * g.box;
+  auto cell_emf = [&](long long q) {  // -(v x b_c) component e of cell q
+    const double vx = Wb[g.box + q], vy = Wb[2 * g.box + q], vz = Wb[3 * g.box + q];
+    const double ux = Wb[5 * g.box + q], uy = Wb[6 * g.box + q], uz = Wb[7 * g.box + q];
+    return e == 0 ? vz * uy - vy * uz : (e == 1 ? vx * uz - vz * ux : vy * ux - vx * uy);
+  };
+  const double* Fa5 = M[a] + e5off;
+  const double* Fb6 = M[bq] + e6off;
+  double d;
+  switch (slot) {
+    case 0: d = (Fb6[cn - sa] - cell_emf(cn - sa - sb)) - (Fb6[cn] - cell_emf(cn - sb)); break;
+    case 1: d = -((cell_emf(cn - sa) - Fb6[cn - sa]) - (cell_emf(cn) - Fb6[cn])); break;
+    case 2: d = (-Fa5[cn - sb] - cell_emf(cn - sa - sb)) - (-Fa5[cn] - cell_emf(cn - sa)); break;
+    default: d = -((cell_emf(cn - sb) + Fa5[cn - sb]) - (cell_emf(cn) + Fa5[cn])); break;
+  }
+  return 0.25 * lam * d;
+}
+
 // Transpose of the upwind CT (linear for the upwind choices the forward step made), as a gather: the
 // thread of node n collects, in a fixed order, what the corner EMFs around it give to (i) the face-EMF
 // components of the fluxes at n (F_d[B_t1] from family d+2 at n and n + s_(d+1); F_d[B_t2] from family
 // d+1 at n and n + s_(d+2)) and (ii) the primitives of cell n through its three cell EMFs (each from the
-// four edges of its family around the cell).
+// four edges of its family around the cell).  With the smoothed weight (delta > 0) the corners are also
+// functions of the face mass fluxes: (iii) the mass-flux component of the fluxes at n collects
+// dE/dm = +-(1/4) dw/dm (lo - hi) of the four corners that weigh by it, from the forward face EMFs (at
+// e5off / e6off after each block's mass fluxes) and the cell EMFs -v x b of W.
+template <bool SMOOTH>
 __global__ void k_adj_ct(Geom g, const double* W, const double* m0, const double* m1, const double* m2, long long mstride,
-                         const double* le0, const double* le1, const double* le2, double* lf0, double* lf1,
-                         double* lf2, double* lw) {
+                         long long e5off, long long e6off, double delta_in, const double* le0, const double* le1,
+                         const double* le2, double* lf0, double* lf1, double* lf2, double* lw) {
+  const double delta = SMOOTH ? delta_in : 0.0;
   const int ex = g.mb[0] + 2, ey = g.mb[1] + 2, ez = g.mb[2] + 2;  // nodes NG-1 .. NG+mb
   const long long per = (long long)ex * ey * ez;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -210,7 +271,7 @@ __global__ void k_adj_ct(Geom g, const double* W, const double* m0, const double
     const long long cn = c + da * stride[a] + db * stride[bq];
     const double lam = LE[e][cn];
     if (lam == 0.0) return 0.0;
-    const EdgeCoef k = edge_coef(M[a], M[bq], cn, stride[a], stride[bq]);
+    const EdgeCoef k = edge_coef(M[a], M[bq], cn, stride[a], stride[bq], delta);
     switch (which) {
       case 0: return k.cea0 * lam;
       case 1: return k.cea1 * lam;
@@ -233,6 +294,19 @@ __global__ void k_adj_ct(Geom g, const double* W, const double* m0, const double
     const double g6 = edge_term(e6, 0, 0, 3) + edge_term(e6, 1, 0, 2);
     LF[d][5 * g.box + c] += g5;
     LF[d][6 * g.box + c] += g6;
+    if constexpr (SMOOTH) {
+      double w, dw;
+      smooth_w(M[d][c], delta, w, dw);
+      if (dw != 0.0) {
+        // slots of this face: ma[1] (thi) and ma[0] (tlo) of family e5 at n and n + s_(d+1); mb[1] (shi) and
+        // mb[0] (slo) of family e6 at n and n + s_(d+2)
+        const double gm = corner_dm(g, W, M, e5off, e6off, LE, stride, li, b, c, e5, 0, 0, 1) +
+                          corner_dm(g, W, M, e5off, e6off, LE, stride, li, b, c, e5, 0, 1, 0) +
+                          corner_dm(g, W, M, e5off, e6off, LE, stride, li, b, c, e6, 0, 0, 3) +
+                          corner_dm(g, W, M, e5off, e6off, LE, stride, li, b, c, e6, 1, 0, 2);
+        LF[d][c] += dw * gm;
+      }
+    }
   }
   // (ii) primitives of cell c through its cell EMFs (E = -v x b)
   const double* Wc = W + (long long)b * 8 * g.box + c;
@@ -744,9 +818,15 @@ cudaError_t adj_update(const Geom& g, const AdjArrays& j, int out_reg, int base_
 }
 
 cudaError_t adj_ct(const Geom& g, const AdjArrays& j, const double* W, const double* const* mflux, long long mstride,
-                   cudaStream_t st) {
-  k_adj_ct<<<grid_of(nodes_ext(g), AT), AT, 0, st>>>(g, W, mflux[0], mflux[1], mflux[2], mstride, j.le[0], j.le[1],
-                                                     j.le[2], j.lf[0], j.lf[1], j.lf[2], j.lw);
+                   long long e5off, long long e6off, cudaStream_t st) {
+  if (g.ct_delta > 0.0)
+    k_adj_ct<true><<<grid_of(nodes_ext(g), AT), AT, 0, st>>>(g, W, mflux[0], mflux[1], mflux[2], mstride, e5off,
+                                                             e6off, g.ct_delta, j.le[0], j.le[1], j.le[2], j.lf[0],
+                                                             j.lf[1], j.lf[2], j.lw);
+  else
+    k_adj_ct<false><<<grid_of(nodes_ext(g), AT), AT, 0, st>>>(g, W, mflux[0], mflux[1], mflux[2], mstride, e5off,
+                                                              e6off, 0.0, j.le[0], j.le[1], j.le[2], j.lf[0],
+                                                              j.lf[1], j.lf[2], j.lw);
   return cudaGetLastError();
 }
 

@@ -161,6 +161,10 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
     msg = "nscalars must be 0 .. VL2_MAX_SCALARS (and 0 with the adjoint)";
     return VL2_E_ARG;
   }
+  if (!(p->ct_delta >= 0.0) || !std::isfinite(p->ct_delta)) {
+    msg = "ct_delta must be finite and >= 0";
+    return VL2_E_ARG;
+  }
   for (int d = 0; d < 3; ++d) {
     const int lo = p->bc[2 * d], hi = p->bc[2 * d + 1];
     if ((lo != VL2_PERIODIC && lo != VL2_OUTFLOW) || (hi != VL2_PERIODIC && hi != VL2_OUTFLOW) ||
@@ -186,6 +190,7 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
   g.nblk = (int)nblk;
   g.ng = p->ng;
   g.ns = p->nscalars;
+  g.ct_delta = p->ct_delta;
   g.sx = ((p->mb[0] + 2 * g.ng + 1) + 3) & ~3;
   g.sy = p->mb[1] + 2 * g.ng + 1;
   g.sz = p->mb[2] + 2 * g.ng + 1;
@@ -207,9 +212,10 @@ struct Plan {
   size_t off_u[2], off_b[2][3], off_w, off_f[3], off_e[3], off_ec, off_stage, off_red, off_scal, total;
   size_t off_s[2], off_cs, off_fsc[3];  // passive scalars (empty when ns = 0)
   size_t stage_elems;
-  size_t off_adj;  // start of the adjoint arrays (59 FP64 arrays per block) when requested
+  size_t off_adj;  // start of the adjoint arrays (59 FP64 arrays per block, 65 with ct_delta) when requested
 };
 constexpr int ADJ_ARRAYS = 10 + 6 + 8 + 21 + 7 + 3 + 8 + 3;
+constexpr int ADJ_ARRAYS_SMOOTH_CT = 6;  // the predictor's face EMFs, kept for the smoothed weight's derivative
 
 Plan make_plan(const Geom& g, int precision, int adjoint) {
   Plan pl;
@@ -261,7 +267,7 @@ Plan make_plan(const Geom& g, int precision, int adjoint) {
   pl.off_scal = o;
   o = align256(o + vl2::SC_COUNT * sizeof(unsigned long long) + 16 * sizeof(double));
   pl.off_adj = o;
-  if (adjoint) o = align256(o + (size_t)ADJ_ARRAYS * per);
+  if (adjoint) o = align256(o + (size_t)(ADJ_ARRAYS + (g.ct_delta > 0.0 ? ADJ_ARRAYS_SMOOTH_CT : 0)) * per);
   pl.total = o;
   return pl;
 }
@@ -438,7 +444,7 @@ vl2_status vl2_mesh_create(const vl2_params* params, void* workspace, size_t byt
     m->adj.lr = take(7);
     for (int d = 0; d < 3; ++d) m->adj.le[d] = take(1);
     m->adj.w0 = take(8);
-    for (int d = 0; d < 3; ++d) m->adj.m1[d] = take(1);
+    for (int d = 0; d < 3; ++d) m->adj.m1[d] = take(g.ct_delta > 0.0 ? 3 : 1);
     m->has_adj = true;
   }
   m->a.stage = (double*)(base + pl.off_stage);
@@ -630,9 +636,17 @@ vl2_status vl2_step_vjp(vl2_mesh* m, double dt, const double* lam_u, const doubl
   VL2_CHECK(m, k_prim(m, 0, false));
   VL2_CHECK(m, cudaMemcpyAsync(j.w0, m->a.w, 8 * per, cudaMemcpyDeviceToDevice, st));
   VL2_CHECK(m, k_fluxes(m, 0, VL2_DC));
-  for (int d = 0; d < 3; ++d)
-    VL2_CHECK(m, cudaMemcpy2DAsync(j.m1[d], g.box * sizeof(double), m->a.f[d], 7 * g.box * sizeof(double),
+  // the predictor's mass fluxes (its upwind choices), and with the smoothed CT weight its face EMFs
+  const bool smooth_ct = g.ct_delta > 0.0;
+  const long long m1_stride = smooth_ct ? 3 * g.box : g.box;
+  for (int d = 0; d < 3; ++d) {
+    VL2_CHECK(m, cudaMemcpy2DAsync(j.m1[d], m1_stride * sizeof(double), m->a.f[d], 7 * g.box * sizeof(double),
                                    g.box * sizeof(double), g.nblk, cudaMemcpyDeviceToDevice, st));
+    if (smooth_ct)
+      VL2_CHECK(m, cudaMemcpy2DAsync(j.m1[d] + g.box, m1_stride * sizeof(double),
+                                     static_cast<const double*>(m->a.f[d]) + 5 * g.box, 7 * g.box * sizeof(double),
+                                     2 * g.box * sizeof(double), g.nblk, cudaMemcpyDeviceToDevice, st));
+  }
   VL2_CHECK(m, k_emfs(m));
   VL2_CHECK(m, k_update(m, 0, 1, 0.5 * dt));
   VL2_CHECK(m, k_ghosts(m, 1));
@@ -655,14 +669,14 @@ vl2_status vl2_step_vjp(vl2_mesh* m, double dt, const double* lam_u, const doubl
   const double* mf1[3] = {j.m1[0], j.m1[1], j.m1[2]};
   // corrector: U0 <- U0 + dt L_PLM(U1)
   VL2_CHECK(m, vl2::adj_update(g, j, 0, 0, dt, st));
-  VL2_CHECK(m, vl2::adj_ct(g, j, W1, mf2, 7 * g.box, st));
+  VL2_CHECK(m, vl2::adj_ct(g, j, W1, mf2, 7 * g.box, 5 * g.box, 6 * g.box, st));
   VL2_CHECK(m, vl2::adj_fluxes(g, j, vl2::REC_PLM, m->p.riemann, W1, bn1, 1, st));
   VL2_CHECK(m, vl2::adj_prim(g, j, W1, 1, st));
   VL2_CHECK(m, vl2::adj_ghosts(g, j, 1, st));
   // predictor: U1 = U0 + dt/2 L_DC(U0)
   VL2_CHECK(m, cudaMemsetAsync(j.lw, 0, 8 * per, st));
   VL2_CHECK(m, vl2::adj_update(g, j, 1, 0, 0.5 * dt, st));
-  VL2_CHECK(m, vl2::adj_ct(g, j, j.w0, mf1, g.box, st));
+  VL2_CHECK(m, vl2::adj_ct(g, j, j.w0, mf1, m1_stride, g.box, 2 * g.box, st));
   VL2_CHECK(m, vl2::adj_fluxes(g, j, vl2::REC_DC, m->p.riemann, j.w0, bn0, 0, st));
   VL2_CHECK(m, vl2::adj_prim(g, j, j.w0, 0, st));
   VL2_CHECK(m, vl2::adj_ghosts(g, j, 0, st));
@@ -1046,8 +1060,8 @@ vl2_status batch_check(vl2_mesh* const* meshes, int n, std::string& msg) {
       msg = "NULL mesh in the batch";
       return VL2_E_ARG;
     }
-    if (meshes[q]->p.integrator != VL2_INT_VL2 || meshes[q]->g.ns != 0) {
-      msg = "the batched form runs the VL2 integrator without passive scalars";
+    if (meshes[q]->p.integrator != VL2_INT_VL2 || meshes[q]->g.ns != 0 || meshes[q]->g.ct_delta > 0.0) {
+      msg = "the batched form runs the VL2 integrator without passive scalars or the smoothed CT weight";
       return VL2_E_ARG;
     }
     if (meshes[q]->p.riemann != meshes[0]->p.riemann || meshes[q]->p.precision != meshes[0]->p.precision ||

@@ -26,6 +26,7 @@ struct Geom {
   double dx[3];
   double gamma, gm1, igm1;
   double dfloor, pfloor;
+  double ct_delta;     // smoothed CT upwind weight width (0: the sign switch)
 };
 
 __host__ __device__ inline long long cell_off(const Geom& g, int k, int j, int i) {
@@ -150,14 +151,15 @@ struct AdjArrays {
   double* lr;        // right-state adjoints of the faces of the sweep being transposed: [nblk][7][box]
   double* le[3];     // adjoints of the corner EMFs
   double* w0;        // predictor primitives kept from the forward recompute: [nblk][8][box]
-  double* m1[3];     // predictor face mass fluxes (upwind choices of its CT): [nblk][box]
+  double* m1[3];     // predictor face mass fluxes (upwind choices of its CT): [nblk][box]; with the smoothed CT
+                     // weight also its face EMFs F[B_t1], F[B_t2]: [nblk][3][box]
 };
 
 cudaError_t adj_scatter_out(const Geom& g, const AdjArrays& j, const double* gu, const double* gb1, const double* gb2,
                             const double* gb3, cudaStream_t st);
 cudaError_t adj_update(const Geom& g, const AdjArrays& j, int out_reg, int base_reg, double h, cudaStream_t st);
 cudaError_t adj_ct(const Geom& g, const AdjArrays& j, const double* W, const double* const* mflux, long long mstride,
-                   cudaStream_t st);
+                   long long e5off, long long e6off, cudaStream_t st);
 cudaError_t adj_fluxes(const Geom& g, const AdjArrays& j, int recon, int riemann, const double* W,
                        const double* const* Bn, int lam_reg, cudaStream_t st);
 cudaError_t adj_prim(const Geom& g, const AdjArrays& j, const double* W, int lam_reg, cudaStream_t st);

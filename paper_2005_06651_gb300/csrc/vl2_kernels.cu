@@ -548,7 +548,7 @@ cudaError_t launch_gather_scalars(const Geom& g, const Arrays& a, double* out, c
 // transverse directions a = e+1, b = e+2.  Face EMFs of that component: -F_a[B_t1] on a-faces and
 // +F_b[B_t2] on b-faces (E = -v x B); cell EMFs as cons->prim wrote them.  One thread per corner node.
 // ------------------------------------------------------------------------------------------------
-template <class T>
+template <class T, bool SMOOTH>
 __global__ void __launch_bounds__(256) k_emf(MeshView single, const MeshView* views, const WorkItem* work) {
   __shared__ MeshView sv;
   int tile;
@@ -572,6 +572,13 @@ __global__ void __launch_bounds__(256) k_emf(MeshView single, const MeshView* vi
   const T* F[3] = {F0, F1, F2};
   T* E[3] = {E0, E1, E2};
   const T* Ecb = static_cast<const T*>(V.a.ec) + (long long)b * 3 * g.box;
+  // smoothed weights: the node's own three faces serve two edge families each, so 9 weights per node, not 12
+  [[maybe_unused]] const T delta = (T)g.ct_delta, band = T(20) * delta;
+  [[maybe_unused]] T wown[3];
+  if constexpr (SMOOTH) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) wown[d] = ct_weight(F[d][(long long)b * 7 * g.box + c], delta, band);
+  }
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     if (li[e] > g.ng + g.mb[e] - 1) continue;
@@ -584,16 +591,23 @@ __global__ void __launch_bounds__(256) k_emf(MeshView single, const MeshView* vi
     ea[1] = -Fa[5 * g.box + c];
     eb[0] = Fb[6 * g.box + c - sa];
     eb[1] = Fb[6 * g.box + c];
-    ma[0] = Fa[c - sb];
-    ma[1] = Fa[c];
-    mb[0] = Fb[c - sa];
-    mb[1] = Fb[c];
+    if constexpr (SMOOTH) {
+      ma[0] = ct_weight(Fa[c - sb], delta, band);
+      ma[1] = wown[a];
+      mb[0] = ct_weight(Fb[c - sa], delta, band);
+      mb[1] = wown[bq];
+    } else {
+      ma[0] = Fa[c - sb];
+      ma[1] = Fa[c];
+      mb[0] = Fb[c - sa];
+      mb[1] = Fb[c];
+    }
     const T* Ec = Ecb + (long long)e * g.box;
     ec[0] = Ec[c - sa - sb];
     ec[1] = Ec[c - sb];
     ec[2] = Ec[c - sa];
     ec[3] = Ec[c];
-    E[e][(long long)b * g.box + c] = ct_corner(ea, eb, ec, ma, mb);
+    E[e][(long long)b * g.box + c] = ct_corner<T, SMOOTH>(ea, eb, ec, ma, mb);
   }
 }
 
@@ -606,10 +620,18 @@ cudaError_t launch_emfs(const MeshView& v, const Dispatch* d, cudaStream_t st) {
   if (grid <= 0) return cudaSuccess;
   const MeshView* vs = d ? d->views : nullptr;
   const WorkItem* wk = d ? d->work : nullptr;
-  if (v.a.mixed)
-    k_emf<float><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk);
-  else
-    k_emf<double><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk);
+  const bool smooth = v.g.ct_delta > 0.0;
+  if (v.a.mixed) {
+    if (smooth)
+      k_emf<float, true><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk);
+    else
+      k_emf<float, false><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk);
+  } else {
+    if (smooth)
+      k_emf<double, true><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk);
+    else
+      k_emf<double, false><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk);
+  }
   return cudaGetLastError();
 }
 

@@ -427,9 +427,34 @@ __device__ __forceinline__ R ct_pick(R m, R lo, R hi) {
   return gt0(m) ? lo : (lt0(m) ? hi : R(0.5) * (lo + hi));
 }
 
+// [option, not the paper's method] smoothed upwind weight: w = (1 + tanh(m / delta)) / 2 on the gradient of the
+// cell the mass flux m comes from, 1 - w on the other.  Where |m| > 20 delta, 1 - |tanh(m / delta)| < 1e-17 is
+// below half an ulp of 1 (2^-54), so tanh rounds to +-1 and w to exactly 1 or 0: the sign switch's pick,
+// taken here without the tanh.  At m = 0, w = 1/2 is the switch's mean.
 template <class R>
+__device__ __forceinline__ R ct_weight(R m, R delta, R band) {
+  if (fabs(m) > band) return m > R(0) ? R(1) : R(0);
+  if (m == R(0)) return R(0.5);  // tanh(0) = 0; also where delta underflows to 0 in R
+  return R(0.5) * (R(1) + tanh(m / delta));
+}
+
+template <class R>
+__device__ __forceinline__ R ct_pick_w(R w, R lo, R hi) {
+  return w == R(1) ? lo : (w == R(0) ? hi : w * lo + (R(1) - w) * hi);
+}
+
+// The corner EMF with upwind picks by sign (SMOOTH false: ma, mb are the face mass fluxes) or by the weights
+// above (SMOOTH true: ma, mb are already the weights of those faces).
+template <class R, bool SMOOTH = false>
 __device__ __forceinline__ R ct_corner(const R* ea, const R* eb, const R* ec, const R* ma, const R* mb) {
   const R sum4 = (ea[0] + ea[1]) + (eb[0] + eb[1]);
+  if constexpr (SMOOTH) {
+    const R tlo = ct_pick_w(ma[0], eb[0] - ec[0], eb[1] - ec[1]);
+    const R thi = ct_pick_w(ma[1], ec[2] - eb[0], ec[3] - eb[1]);
+    const R slo = ct_pick_w(mb[0], ea[0] - ec[0], ea[1] - ec[2]);
+    const R shi = ct_pick_w(mb[1], ec[1] - ea[0], ec[3] - ea[1]);
+    return (R(0.25) * sum4 + R(0.25) * (tlo - thi)) + R(0.25) * (slo - shi);
+  }
   const R tlo = ct_pick(ma[0], eb[0] - ec[0], eb[1] - ec[1]);
   const R thi = ct_pick(ma[1], ec[2] - eb[0], ec[3] - eb[1]);
   const R slo = ct_pick(mb[0], ea[0] - ec[0], ea[1] - ec[2]);

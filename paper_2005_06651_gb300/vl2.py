@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("riemann", ctypes.c_int), ("precision", ctypes.c_int),
                 ("bc", ctypes.c_int * 6), ("dfloor", ctypes.c_double), ("pfloor", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("adjoint", ctypes.c_int), ("integrator", ctypes.c_int),
-                ("recon", ctypes.c_int), ("nscalars", ctypes.c_int)]
+                ("recon", ctypes.c_int), ("nscalars", ctypes.c_int), ("ct_delta", ctypes.c_double)]
 
 
 class Layout(ctypes.Structure):
@@ -153,7 +153,7 @@ class Mesh:
 
     def __init__(self, nx, mb, xmin=(0.0, 0.0, 0.0), xmax=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, cfl=0.3,
                  riemann=HLLD, bc=(PERIODIC,) * 6, dfloor=1e-12, pfloor=1e-12, precision=FP64, device=None,
-                 stream=None, adjoint=False, integrator=VL2, recon=PLM, ng=None, nscalars=0):
+                 stream=None, adjoint=False, integrator=VL2, recon=PLM, ng=None, nscalars=0, ct_delta=0.0):
         import torch
 
         L = load()
@@ -170,6 +170,7 @@ class Mesh:
         p.ng = (3 if recon == PPM else 2) if ng is None else int(ng)
         p.recon = int(recon)
         p.nscalars = int(nscalars)
+        p.ct_delta = float(ct_delta)
         self.nscalars = int(nscalars)
         p.xmin[:] = self.xmin
         p.xmax[:] = self.xmax

@@ -58,6 +58,7 @@ def _params(**kw):
     p.adjoint = kw.get("adjoint", 0)
     p.recon = kw.get("recon", 0)
     p.nscalars = kw.get("nscalars", 0)
+    p.ct_delta = kw.get("ct_delta", 0.0)
     return p
 
 
@@ -69,7 +70,8 @@ def test_workspace_bytes_and_argument_checks(lib):
     bad = [dict(nx=(30, 32, 32)), dict(ng=1), dict(ng=4), dict(gamma=1.0), dict(riemann=5), dict(precision=7),
            dict(bc=(0, 1, 0, 0, 0, 0)), dict(nx=(0, 32, 32)), dict(xmax=(0.0, 1.0, 1.0)), dict(recon=7),
            dict(recon=2, ng=2), dict(adjoint=1, ng=3), dict(adjoint=1, ng=3, recon=2), dict(nscalars=-1),
-           dict(nscalars=17), dict(adjoint=1, nscalars=1)]
+           dict(nscalars=17), dict(adjoint=1, nscalars=1), dict(ct_delta=-1.0),
+           dict(ct_delta=float("nan"))]
     for kw in bad:
         assert lib.vl2_workspace_bytes(ctypes.byref(_params(**kw)), ctypes.byref(n)) == 1, kw
         assert lib.vl2_last_error(None)
