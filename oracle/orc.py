@@ -17,7 +17,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liborc.so")
 
 HLLE, HLLD = 0, 1
-DC, PLM, PPM = 0, 1, 2
+DC, PLM, PPM, PLM_CHAR = 0, 1, 2, 3
 VL2, RK1, RK2, RK3 = 0, 1, 2, 3
 
 _lib = None
@@ -75,6 +75,8 @@ def lib():
         L.orc_vanleer_slope.argtypes = [ctypes.c_double] * 3
         L.orc_vanleer_slope.restype = ctypes.c_double
         L.orc_ppm_edges.argtypes = [dp, dp]
+        L.orc_mhd_eigensystem.argtypes = [dp, ctypes.c_double, ctypes.c_double, dp, dp, dp]
+        L.orc_char_slope.argtypes = [dp, ctypes.c_double, ctypes.c_double, dp]
         L.orc_ppm_face.argtypes = [dp]
         L.orc_ppm_face.restype = ctypes.c_double
         L.orc_count_face_ops.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
@@ -131,6 +133,23 @@ def fast_speed(d, p, bn, bt1, bt2, gamma):
 
 def vanleer_slope(qm, q0, qp):
     return lib().orc_vanleer_slope(qm, q0, qp)
+
+
+def mhd_eigensystem(w, bn, gamma):
+    """(R, L, lam) of the primitive MHD system at w = (rho, v_n, v_t1, v_t2, p, b_t1, b_t2) with normal field
+    bn: columns of R are the right eigenvectors, L = R^-1, lam the eigenvalues (ascending)."""
+    q = _c64(np.asarray(w, dtype=np.float64))
+    R, L, lam = np.zeros((7, 7)), np.zeros((7, 7)), np.zeros(7)
+    lib().orc_mhd_eigensystem(_dp(q), float(bn), float(gamma), _dp(R), _dp(L), _dp(lam))
+    return R, L, lam
+
+
+def char_slope(qm, q0, qp, bn, gamma):
+    """Limited slope of the characteristic reconstruction of the cell q0 between qm and qp (7 each)."""
+    q = _c64(np.concatenate([np.asarray(a, dtype=np.float64) for a in (qm, q0, qp)]))
+    out = np.zeros(7)
+    lib().orc_char_slope(_dp(q), float(bn), float(gamma), _dp(out))
+    return out
 
 
 def ppm_edges(q5):

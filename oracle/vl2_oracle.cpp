@@ -53,7 +53,7 @@ using std::sqrt;
 
 enum { RS_HLLE = 0, RS_HLLD = 1 };
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
-enum { REC_DC = 0, REC_PLM = 1, REC_PPM = 2 };
+enum { REC_DC = 0, REC_PLM = 1, REC_PPM = 2, REC_PLM_CHAR = 3 };
 enum { INT_VL2 = 0, INT_RK1 = 1, INT_RK2 = 2, INT_RK3 = 3 };
 
 /* Interface-state layout (normal n, transverse t1, t2 taken cyclically: x->(y,z), y->(z,x),
@@ -426,6 +426,154 @@ static void ppm_edges(const T q[5], T& ql, T& qr) {
   }
 }
 
+/* ---------------------------------------------------------------------------------------------
+ * Characteristic reconstruction (Sec. 3.2.1): the limiter acts on C = L W, the rows of L being the
+ * left eigenvectors of the primitive ideal-MHD system (the paper defers to Stone et al. 2008,
+ * Appendix A).  Along the sweep normal n, with W = (rho, v_n, v_t1, v_t2, p, b_t1, b_t2) and b_n held
+ * fixed, the primitive equations read W_t + A W_n = 0 with
+ *   A = [[v, rho,     0,     0,     0,       0,       0     ],
+ *        [0, v,       0,     0,     1/rho,   b_t1/rho, b_t2/rho],
+ *        [0, 0,       v,     0,     0,      -b_n/rho,  0     ],
+ *        [0, 0,       0,     v,     0,       0,      -b_n/rho],
+ *        [0, gamma p, 0,     0,     v,       0,       0     ],
+ *        [0, b_t1,   -b_n,   0,     0,       v,       0     ],
+ *        [0, b_t2,    0,    -b_n,   0,       0,       v     ]]   (v = v_n).
+ * Its eigenvalues are v -+ c_f, v -+ c_a, v -+ c_s and v, with a^2 = gamma p / rho, c_a^2 = b_n^2 / rho,
+ * c_t^2 = |b_t|^2 / rho, c_f^2 = (a^2 + c_a^2 + c_t^2 + sqrt((c_a^2 + c_t^2 - a^2)^2 + 4 a^2 c_t^2)) / 2
+ * and c_s^2 = a^2 c_a^2 / c_f^2.  The right eigenvectors (columns of R, in the order of the
+ * eigenvalues v - c_f, v - c_a, v - c_s, v, v + c_s, v + c_a, v + c_f) are written with the
+ * normalisation that stays finite where waves coincide:
+ *   beta = b_t / |b_t| (both components 1/sqrt(2) where b_t = 0), s = sign(b_n) (+1 at 0),
+ *   alpha_f^2 = (a^2 - c_s^2) / (c_f^2 - c_s^2), alpha_s^2 = (c_f^2 - a^2) / (c_f^2 - c_s^2) (both in
+ *   [0, 1], summing to 1), taken as (1, 0) where c_f = c_s,
+ *   C_f = c_f alpha_f, C_s = c_s alpha_s, Q_f = s C_f, Q_s = s C_s,
+ *   A_f = a alpha_f sqrt(rho), A_s = a alpha_s sqrt(rho):
+ *   fast  v -+ c_f: (rho alpha_f, -+C_f, +-Q_s beta, rho a^2 alpha_f,  A_s beta)
+ *   Alfven v -+ c_a: (0, 0, (-beta_2, beta_1), 0, -+s sqrt(rho) (beta_2, -beta_1))
+ *   slow  v -+ c_s: (rho alpha_s, -+C_s, -+Q_f beta, rho a^2 alpha_s, -A_f beta)
+ *   entropy v:      (1, 0, 0, 0, 0, 0, 0).
+ * (Derived from A: for a magnetosonic speed c, d rho = rho dv_n / c, dp = rho a^2 dv_n / c,
+ * db_t = b_t c dv_n / (c^2 - c_a^2), dv_t = -b_n db_t / (rho c); the normalisation follows from
+ * (c^2 - a^2)(c^2 - c_a^2) = c_t^2 c^2.)  L is R^-1, formed here by Gauss-Jordan elimination. */
+template <class T>
+static void mhd_eigensystem(const T w[NW7], T bn, double gamma, T R[NW7][NW7], T lam[NW7]) {
+  const T rho = w[IDN], v = w[IVN], p = w[IPR], bt1 = w[IBT1], bt2 = w[IBT2];
+  const T a2 = gamma * p / rho;
+  const T ca2 = bn * bn / rho;
+  const T bt2sum = bt1 * bt1 + bt2 * bt2;
+  const T ct2 = bt2sum / rho;
+  const T tdif = ca2 + ct2 - a2;
+  const T root = sqrt(tdif * tdif + 4.0 * a2 * ct2);  // c_f^2 - c_s^2
+  const T cf2 = 0.5 * ((a2 + ca2 + ct2) + root);
+  const T cs2 = a2 * ca2 / cf2;
+  /* c_f^2 - a^2 = (tdif + root)/2 and c_f^2 - c_a^2 = (X + root)/2 with X = a^2 - c_a^2 + c_t^2, each
+   * written without cancellation where its first term is negative ((root + x)(root - x) = 4 a^2 c_t^2,
+   * resp. 4 c_a^2 c_t^2); a^2 - c_s^2 = a^2 (c_f^2 - c_a^2) / c_f^2.  The normalisation is then exact
+   * where waves coincide (b_t = 0) and accurate near it. */
+  const T X = a2 - ca2 + ct2;
+  const T cf2_a2 = (tdif >= 0.0) ? 0.5 * (tdif + root) : 2.0 * a2 * ct2 / (root - tdif);
+  const T cf2_ca2 = (X >= 0.0) ? 0.5 * (X + root) : 2.0 * ca2 * ct2 / (root - X);
+  const T a2_cs2 = a2 * cf2_ca2 / cf2;
+  const T a = sqrt(a2), ca = sqrt(ca2), cf = sqrt(cf2), cs = sqrt(cs2);
+  T b1, b2;
+  if (bt2sum == 0.0) {
+    b1 = T(std::sqrt(0.5));
+    b2 = T(std::sqrt(0.5));
+  } else {
+    const T bt = sqrt(bt2sum);
+    b1 = bt1 / bt;
+    b2 = bt2 / bt;
+  }
+  T af, as;
+  if (root == 0.0) {  // c_f = c_s = a
+    af = T(1.0);
+    as = T(0.0);
+  } else {
+    af = sqrt(a2_cs2 / root);
+    as = sqrt(cf2_a2 / root);
+  }
+  const double sg = (bn >= 0.0) ? 1.0 : -1.0;
+  const T sr = sqrt(rho);
+  const T Cf = cf * af, Cs = cs * as, Qf = sg * Cf, Qs = sg * Cs, Af = a * af * sr, As = a * as * sr;
+  const T cols[NW7][NW7] = {
+      {rho * af, -Cf, Qs * b1, Qs * b2, rho * a2 * af, As * b1, As * b2},       // v - c_f
+      {T(0.0), T(0.0), -b2, b1, T(0.0), -sg * sr * b2, sg * sr * b1},           // v - c_a
+      {rho * as, -Cs, -Qf * b1, -Qf * b2, rho * a2 * as, -Af * b1, -Af * b2},   // v - c_s
+      {T(1.0), T(0.0), T(0.0), T(0.0), T(0.0), T(0.0), T(0.0)},                 // v
+      {rho * as, Cs, Qf * b1, Qf * b2, rho * a2 * as, -Af * b1, -Af * b2},      // v + c_s
+      {T(0.0), T(0.0), -b2, b1, T(0.0), sg * sr * b2, -sg * sr * b1},           // v + c_a
+      {rho * af, Cf, -Qs * b1, -Qs * b2, rho * a2 * af, As * b1, As * b2}};     // v + c_f
+  for (int k = 0; k < NW7; ++k)
+    for (int r = 0; r < NW7; ++r) R[r][k] = cols[k][r];
+  const T sp[NW7] = {-cf, -ca, -cs, T(0.0), cs, ca, cf};
+  for (int k = 0; k < NW7; ++k) lam[k] = v + sp[k];
+}
+
+/* Inverse of a 7 x 7 matrix by Gauss-Jordan elimination with partial pivoting. */
+template <class T>
+static void invert7(const T M[NW7][NW7], T Minv[NW7][NW7]) {
+  T A[NW7][2 * NW7];
+  for (int r = 0; r < NW7; ++r)
+    for (int c = 0; c < NW7; ++c) {
+      A[r][c] = M[r][c];
+      A[r][NW7 + c] = T(r == c ? 1.0 : 0.0);
+    }
+  for (int c = 0; c < NW7; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < NW7; ++r)
+      if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+    if (piv != c)
+      for (int q = 0; q < 2 * NW7; ++q) {
+        const T t = A[c][q];
+        A[c][q] = A[piv][q];
+        A[piv][q] = t;
+      }
+    const T d = A[c][c];
+    for (int q = 0; q < 2 * NW7; ++q) A[c][q] = A[c][q] / d;
+    for (int r = 0; r < NW7; ++r) {
+      if (r == c) continue;
+      const T f = A[r][c];
+      for (int q = 0; q < 2 * NW7; ++q) A[r][q] = A[r][q] - f * A[c][q];
+    }
+  }
+  for (int r = 0; r < NW7; ++r)
+    for (int c = 0; c < NW7; ++c) Minv[r][c] = A[r][NW7 + c];
+}
+
+/* Limited slope of the characteristic reconstruction for the cell with primitives q0 and normal field
+ * bn between neighbours qm, qp [reading: the paper names the projection but prints its steps only by
+ * reference]: C differences L (q0 - qm) and L (qp - q0) with L evaluated in the cell, the original van
+ * Leer limiter on each characteristic field, and the limited slope projected back with R. */
+template <class T>
+static void char_slope(const T qm[NW7], const T q0[NW7], const T qp[NW7], T bn, double gamma, T dw[NW7]) {
+  T R[NW7][NW7], L[NW7][NW7], lam[NW7];
+  mhd_eigensystem(q0, bn, gamma, R, lam);
+  invert7(R, L);
+  T cm[NW7];
+  for (int k = 0; k < NW7; ++k) {
+    T cl = T(0.0), cr = T(0.0);
+    for (int v = 0; v < NW7; ++v) {
+      cl = cl + L[k][v] * (q0[v] - qm[v]);
+      cr = cr + L[k][v] * (qp[v] - q0[v]);
+    }
+    cm[k] = vanleer_slope(-cl, T(0.0), cr);  // differences cl, cr
+  }
+  for (int v = 0; v < NW7; ++v) {
+    T acc = T(0.0);
+    for (int k = 0; k < NW7; ++k) acc = acc + R[v][k] * cm[k];
+    dw[v] = acc;
+  }
+}
+
+/* A primitive face value from the characteristic reconstruction, kept within the range of the two
+ * cells sharing the face [reading: projecting back can leave that range, and density and pressure
+ * must stay positive]. */
+template <class T>
+static T clamp_between(T x, T q1, T q2) {
+  const T lo = vmin(q1, q2), hi = vmax(q1, q2);
+  return vmin(vmax(x, lo), hi);
+}
+
 /* Upwind constrained-transport corner EMF (Gardiner & Stone 2005), for an edge whose two
  * transverse directions are "a" (first) and "b" (second), e.g. E_z at (i-1/2, j-1/2) with a = x,
  * b = y.  The corner value is the mean of the four face values plus one quarter of each of the two
@@ -513,7 +661,7 @@ struct Params {
   int bc[6];  // x-, x+, y-, y+, z-, z+
   double dfloor, pfloor;
   int integrator;
-  int recon;  // reconstruction of the PLM stages: REC_PLM or REC_PPM (VL2 corrector, RK2/RK3 stages)
+  int recon;  // reconstruction of the PLM stages: REC_PLM, REC_PPM or REC_PLM_CHAR (VL2 corrector, RK2/RK3 stages)
   int ng;     // ghost layers: 2 (DC, PLM) or 3 (PPM)
   int nscal;  // passive scalars (eq. passive_scalars)
   double ct_delta;  // smoothed CT upwind weight width (0: the paper's sign switch)
@@ -787,6 +935,16 @@ template <class T> struct Mesh {
                 wl[v] = qr;
                 ppm_edges(hi5, ql, qr);  // cell i
                 wr[v] = ql;
+              }
+            } else if (recon == REC_PLM_CHAR) {
+              cell_state(B, d, k - 2 * sh[2], j - 2 * sh[1], i - 2 * sh[0], qm2);
+              cell_state(B, d, k + sh[2], j + sh[1], i + sh[0], qp1);
+              T dlm[NW7], dl0[NW7];
+              char_slope(qm2, qm1, q0, B.w[5 + d](k - sh[2], j - sh[1], i - sh[0]), P.gamma, dlm);
+              char_slope(qm1, q0, qp1, B.w[5 + d](k, j, i), P.gamma, dl0);
+              for (int v = 0; v < NW7; ++v) {
+                wl[v] = clamp_between(qm1[v] + 0.5 * dlm[v], qm1[v], q0[v]);
+                wr[v] = clamp_between(q0[v] - 0.5 * dl0[v], qm1[v], q0[v]);
               }
             } else {
               cell_state(B, d, k - 2 * sh[2], j - 2 * sh[1], i - 2 * sh[0], qm2);
@@ -1219,7 +1377,7 @@ void* orc_mesh_new(const int* nx, const int* mb, const double* xmin, const doubl
   orc::Params p;
   if (!(ct_delta >= 0.0) || !std::isfinite(ct_delta)) return nullptr;
   p.ct_delta = ct_delta;
-  if (recon != orc::REC_PLM && recon != orc::REC_PPM) return nullptr;
+  if (recon != orc::REC_PLM && recon != orc::REC_PPM && recon != orc::REC_PLM_CHAR) return nullptr;
   if (nscal < 0 || nscal > 16) return nullptr;
   p.nscal = nscal;
   if (ng < 2 || (recon == orc::REC_PPM && ng < 3)) return nullptr;
@@ -1515,6 +1673,22 @@ double orc_vanleer_slope(double qm, double q0, double qp) { return orc::vanleer_
 
 /* PPM edges of one cell from q[0..4] = q_{i-2} .. q_{i+2}: out[0] = left edge, out[1] = right edge. */
 void orc_ppm_edges(const double* q, double* out) { orc::ppm_edges<double>(q, out[0], out[1]); }
+/* R (row-major 7 x 7, columns the right eigenvectors), its inverse L and the eigenvalues of the primitive
+ * MHD system at the state w = (rho, v_n, v_t1, v_t2, p, b_t1, b_t2) with normal field bn. */
+void orc_mhd_eigensystem(const double* w, double bn, double gamma, double* R, double* L, double* lam) {
+  double Rm[orc::NW7][orc::NW7], Lm[orc::NW7][orc::NW7];
+  orc::mhd_eigensystem<double>(w, bn, gamma, Rm, lam);
+  orc::invert7<double>(Rm, Lm);
+  for (int r = 0; r < orc::NW7; ++r)
+    for (int c = 0; c < orc::NW7; ++c) {
+      R[r * orc::NW7 + c] = Rm[r][c];
+      L[r * orc::NW7 + c] = Lm[r][c];
+    }
+}
+/* Limited slope of the characteristic reconstruction of the middle cell of q = (qm, q0, qp), 7 each. */
+void orc_char_slope(const double* q, double bn, double gamma, double* dw) {
+  orc::char_slope<double>(q, q + orc::NW7, q + 2 * orc::NW7, bn, gamma, dw);
+}
 
 /* PPM fourth-order face value between q[1] and q[2] from q[0..3], limited (step 2). */
 double orc_ppm_face(const double* q) { return orc::ppm_face<double>(q[0], q[1], q[2], q[3]); }
