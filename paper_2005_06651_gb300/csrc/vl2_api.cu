@@ -46,7 +46,7 @@ struct vl2_mesh {
   vl2::MeshView view() const { return vl2::MeshView{g, a}; }
   int max_mb() const { return std::max(g.mb[0], std::max(g.mb[1], g.mb[2])); }
   // reconstruction of the higher-order stages (params.recon, 0 meaning PLM)
-  int rec() const { return p.recon == VL2_PPM ? VL2_PPM : VL2_PLM; }
+  int rec() const { return (p.recon == VL2_PPM || p.recon == VL2_PLM_CHAR) ? p.recon : VL2_PLM; }
   ~vl2_mesh() {
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
   }
@@ -120,8 +120,8 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
     msg = "ng must be 2 or 3";
     return VL2_E_ARG;
   }
-  if (p->recon != 0 && p->recon != VL2_PLM && p->recon != VL2_PPM) {
-    msg = "recon must be VL2_PLM (or 0) or VL2_PPM";
+  if (p->recon != 0 && p->recon != VL2_PLM && p->recon != VL2_PPM && p->recon != VL2_PLM_CHAR) {
+    msg = "recon must be VL2_PLM (or 0), VL2_PPM or VL2_PLM_CHAR";
     return VL2_E_ARG;
   }
   if (p->recon == VL2_PPM && p->ng < 3) {
@@ -153,7 +153,7 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
     msg = "the adjoint (params.adjoint = 1) is written for the VL2 integrator";
     return VL2_E_ARG;
   }
-  if (p->adjoint && (p->ng != 2 || p->recon == VL2_PPM)) {
+  if (p->adjoint && (p->ng != 2 || (p->recon != 0 && p->recon != VL2_PLM))) {
     msg = "the adjoint (params.adjoint = 1) is written for PLM with ng = 2";
     return VL2_E_ARG;
   }
@@ -892,7 +892,7 @@ static vl2_status gather_out(vl2_mesh* m, int kind, int dir, double* out, long l
 
 vl2_status vl2_debug_fluxes(vl2_mesh* m, int recon, double* fx, double* fy, double* fz, int where) {
   if (!m || !fx || !fy || !fz) return fail(m, VL2_E_ARG, "NULL argument");
-  if (bad_where(where) || (recon != VL2_DC && recon != VL2_PLM && !(recon == VL2_PPM && m->g.ng >= 3)))
+  if (bad_where(where) || (recon != VL2_DC && recon != VL2_PLM && recon != VL2_PLM_CHAR && !(recon == VL2_PPM && m->g.ng >= 3)))
     return fail(m, VL2_E_ARG, "bad where or recon (PPM needs ng = 3)");
   if (!m->initialized) return fail(m, VL2_E_STATE, "vl2_set_prims has not been called");
   vl2_status s = ensure_prims(m);
@@ -910,7 +910,7 @@ vl2_status vl2_debug_fluxes(vl2_mesh* m, int recon, double* fx, double* fy, doub
 
 vl2_status vl2_debug_emfs(vl2_mesh* m, int recon, double* e1, double* e2, double* e3, int where) {
   if (!m || !e1 || !e2 || !e3) return fail(m, VL2_E_ARG, "NULL argument");
-  if (bad_where(where) || (recon != VL2_DC && recon != VL2_PLM && !(recon == VL2_PPM && m->g.ng >= 3)))
+  if (bad_where(where) || (recon != VL2_DC && recon != VL2_PLM && recon != VL2_PLM_CHAR && !(recon == VL2_PPM && m->g.ng >= 3)))
     return fail(m, VL2_E_ARG, "bad where or recon (PPM needs ng = 3)");
   if (!m->initialized) return fail(m, VL2_E_STATE, "vl2_set_prims has not been called");
   vl2_status s = ensure_prims(m);

@@ -51,6 +51,21 @@ template <class R> __device__ __forceinline__ R root(R x) { return sqrt(x); }
 template <> __device__ __forceinline__ double root<double>(double x) { return sqrt_nr(x); }
 template <class R> __device__ __forceinline__ R rroot(R x) { return rsqrt(x); }
 template <> __device__ __forceinline__ double rroot<double>(double x) { return rsqrt_nr(x); }
+// The same for inputs that may be zero or denormal (the Newton forms take normal numbers only): those
+// take the IEEE operation.
+constexpr double DBL_NORMAL_MIN = 2.2250738585072014e-308;
+template <class R> __device__ __forceinline__ R inv_any(R x) { return R(1) / x; }
+template <> __device__ __forceinline__ double inv_any<double>(double x) {
+  return fabs(x) >= DBL_NORMAL_MIN ? rcp_nr(x) : 1.0 / x;
+}
+template <class R> __device__ __forceinline__ R root_any(R x) { return sqrt(x); }
+template <> __device__ __forceinline__ double root_any<double>(double x) {
+  return x >= DBL_NORMAL_MIN ? sqrt_nr(x) : sqrt(x);
+}
+template <class R> __device__ __forceinline__ R rroot_any(R x) { return R(1) / sqrt(x); }
+template <> __device__ __forceinline__ double rroot_any<double>(double x) {
+  return x >= DBL_NORMAL_MIN ? rsqrt_nr(x) : 1.0 / sqrt(x);
+}
 
 // ---- float <-> double on the integer pipe ----------------------------------------------------------
 // On this part a hardware conversion between float and double occupies the FP64 pipe like an FP64
@@ -416,6 +431,102 @@ __device__ __forceinline__ void ppm_edges(R qm2, R qm1, R q0, R qp1, R qp2, R& q
   ql = ppm_face(qm2, qm1, q0, qp1);
   qr = ppm_face(qm1, q0, qp1, qp2);
   ppm_cell(qm2, qm1, q0, qp1, qp2, ql, qr);
+}
+
+// Characteristic PLM of one cell (Sec. 3.2.1: the limiter acts on C = L W).  q = (rho, v_n, v_t1, v_t2, p,
+// b_t1, b_t2) of the cell and its two neighbours along the sweep, bn the cell's normal field.  The
+// eigenvectors of the primitive system are those with the alpha/beta normalisation (finite where waves
+// coincide; alpha evaluated without cancellation, exact at b_t = 0).  With it alpha_f^2 c_f^2 +
+// alpha_s^2 c_s^2 = a^2, and the left eigenvectors take the closed form used below:
+//   fast -+ : (0, -+C_f, +-Q_s beta, 0) / (2 a^2) + (alpha_f, A_s beta) / (2 rho a^2) on (v_n, v_t, p, b_t),
+//   slow -+ : (0, -+C_s, -+Q_f beta, 0) / (2 a^2) + (alpha_s, -A_f beta) / (2 rho a^2),
+//   Alfven -+: (v_t . beta_perp) / 2 +- s (b_t . beta_perp) / (2 sqrt(rho)), beta_perp = (-beta_2, beta_1),
+//   entropy : d rho - dp / a^2.
+// Each characteristic difference pair gets the van Leer half-slope c_l c_r / (c_l + c_r), the half-slopes
+// are projected back with R, and each face value is kept within the range of the two cells sharing
+// the face.  lo / hi: the values at the cell's lower / upper face.
+template <class R>
+__device__ __forceinline__ void char_plm_cell(const R qm[7], const R q0[7], const R qp[7], R bn, R gamma, R lo[7],
+                                              R hi[7]) {
+  const R rho = q0[0];
+  const R irho = inv_any(rho);
+  const R a2 = gamma * q0[4] * irho;
+  const R ca2 = bn * bn * irho;
+  const R btsq = q0[5] * q0[5] + q0[6] * q0[6];
+  const R ct2 = btsq * irho;
+  const R tdif = ca2 + ct2 - a2;
+  const R root = root_any(tdif * tdif + R(4) * a2 * ct2);  // c_f^2 - c_s^2
+  const R cf2 = R(0.5) * ((a2 + ca2 + ct2) + root);
+  const R xs = a2 - ca2 + ct2;
+  const R cf2_a2 = tdif >= R(0) ? R(0.5) * (tdif + root) : R(2) * a2 * ct2 * inv_any(root - tdif);
+  const R cf2_ca2 = xs >= R(0) ? R(0.5) * (xs + root) : R(2) * ca2 * ct2 * inv_any(root - xs);
+  const R icf2 = inv_any(cf2);
+  R af = R(1), as = R(0);
+  if (root != R(0)) {
+    const R ir = inv_any(root);
+    af = root_any(a2 * cf2_ca2 * icf2 * ir);  // (a^2 - c_s^2) / (c_f^2 - c_s^2)
+    as = root_any(cf2_a2 * ir);
+  }
+  const R a = root_any(a2), cf = root_any(cf2), cs = root_any(a2 * ca2 * icf2);
+  R b1 = R(0.70710678118654752440), b2 = R(0.70710678118654752440);
+  if (btsq != R(0)) {
+    const R ibt = rroot_any(btsq);
+    b1 = q0[5] * ibt;
+    b2 = q0[6] * ibt;
+  }
+  const R sg = bn >= R(0) ? R(1) : R(-1);
+  const R sr = root_any(rho), isr = rroot_any(rho);
+  const R Cf = cf * af, Cs = cs * as, Qf = sg * Cf, Qs = sg * Cs, Af = a * af * sr, As = a * as * sr;
+  const R n2a = R(0.5) * inv_any(a2), n2ra = n2a * irho, hs = R(0.5) * sg * isr;
+  R dl[7], dr[7];
+#pragma unroll
+  for (int n = 0; n < 7; ++n) {
+    dl[n] = q0[n] - qm[n];
+    dr[n] = qp[n] - q0[n];
+  }
+  R m[7];
+  {
+    R cl[7], cr[7];
+    auto project = [&](const R* d, R* c) {
+      const R vp = b1 * d[2] + b2 * d[3], va = b1 * d[3] - b2 * d[2];
+      const R bp = b1 * d[5] + b2 * d[6], ba = b1 * d[6] - b2 * d[5];
+      const R pf = n2ra * (af * d[4] + As * bp), ps = n2ra * (as * d[4] - Af * bp);
+      const R uf = n2a * (Cf * d[1] - Qs * vp), us = n2a * (Cs * d[1] + Qf * vp);
+      c[0] = pf - uf;  // v - c_f
+      c[1] = R(0.5) * va + hs * ba;  // v - c_a
+      c[2] = ps - us;  // v - c_s
+      c[3] = d[0] - R(2) * n2a * d[4];  // v (entropy)
+      c[4] = ps + us;  // v + c_s
+      c[5] = R(0.5) * va - hs * ba;  // v + c_a
+      c[6] = pf + uf;  // v + c_f
+    };
+    project(dl, cl);
+    project(dr, cr);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      // where c_l c_r > 0 both are at least ~1e-162, so c_l + c_r is a normal number
+      const bool pos = gt0(cl[k] * cr[k]);
+      const R den = pos ? cl[k] + cr[k] : R(1);
+      m[k] = pos ? (cl[k] * cr[k]) * inv(den) : R(0);
+    }
+  }
+  // half of the limited slope, back in primitives
+  const R fsum = m[0] + m[6], ssum = m[2] + m[4];
+  R dh[7];
+  dh[0] = rho * (af * fsum + as * ssum) + m[3];
+  dh[1] = Cf * (m[6] - m[0]) + Cs * (m[4] - m[2]);
+  const R vp = Qs * (m[0] - m[6]) + Qf * (m[4] - m[2]), va = m[1] + m[5];
+  dh[2] = b1 * vp - b2 * va;
+  dh[3] = b2 * vp + b1 * va;
+  dh[4] = rho * a2 * (af * fsum + as * ssum);
+  const R bp = As * fsum - Af * ssum, ba = sg * sr * (m[1] - m[5]);
+  dh[5] = b1 * bp - b2 * ba;
+  dh[6] = b2 * bp + b1 * ba;
+#pragma unroll
+  for (int n = 0; n < 7; ++n) {
+    lo[n] = fmin(fmax(q0[n] - dh[n], fmin(qm[n], q0[n])), fmax(qm[n], q0[n]));
+    hi[n] = fmin(fmax(q0[n] + dh[n], fmin(q0[n], qp[n])), fmax(q0[n], qp[n]));
+  }
 }
 
 // Upwind CT corner EMF (Gardiner & Stone 2005) for an edge with transverse directions a, b:

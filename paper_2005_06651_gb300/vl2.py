@@ -23,7 +23,7 @@ PERIODIC, OUTFLOW = 0, 1
 VL2, RK1, RK2, RK3 = 0, 1, 2, 3  # time integrators (vl2_params.integrator)
 FP64, MIXED = 0, 1
 HOST, DEVICE = 0, 1
-DC, PLM, PPM = 0, 1, 2  # reconstructions (vl2_params.recon for the higher-order stages)
+DC, PLM, PPM, PLM_CHAR = 0, 1, 2, 3  # reconstructions (vl2_params.recon for the higher-order stages)
 
 STATUS_NAMES = {0: "VL2_OK", 1: "VL2_E_ARG", 2: "VL2_E_CUDA", 3: "VL2_E_NONPHYS", 4: "VL2_E_TIMEOUT",
                 5: "VL2_E_STATE", 6: "VL2_E_NOMEM"}
