@@ -16,7 +16,7 @@ SRC = os.path.join(HERE, "vl2_oracle.cpp")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liborc.so")
 
-HLLE, HLLD = 0, 1
+HLLE, HLLD, HLLE_ROE = 0, 1, 2
 DC, PLM, PPM, PLM_CHAR = 0, 1, 2, 3
 VL2, RK1, RK2, RK3 = 0, 1, 2, 3
 

@@ -51,7 +51,7 @@ namespace orc {
 using std::fabs;
 using std::sqrt;
 
-enum { RS_HLLE = 0, RS_HLLD = 1 };
+enum { RS_HLLE = 0, RS_HLLD = 1, RS_HLLE_ROE = 2 };
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
 enum { REC_DC = 0, REC_PLM = 1, REC_PPM = 2, REC_PLM_CHAR = 3 };
 enum { INT_VL2 = 0, INT_RK1 = 1, INT_RK2 = 2, INT_RK3 = 3 };
@@ -208,6 +208,55 @@ static void flux_hlle(const T wl[NW7], const T wr[NW7], T bn, double gamma, T f[
     f[n] = ((bp * fl[n] - bm * fr[n]) + (bp * bm) * (ur[n] - ul[n])) / (bp - bm);
 }
 
+/* HLLE flux with Einfeldt's outer speeds: S_L = min(u_L - c_L, u~ - c~_f), S_R = max(u_R + c_R, u~ + c~_f),
+ * where ~ is the Roe average of the two states (the paper names the solver and Roe's linearisation,
+ * Sec. 3.2.2, without formulas).  The averaged fast speed is that of the MHD Roe matrix of Cargo &
+ * Gallice 1997 (as used by Stone et al. 2008):
+ *   sqrt(rho) weights for velocity and total enthalpy H = (E + p_T) / rho, the cross weights for the
+ *   transverse field b~_t = (sqrt(rho_R) b_t,L + sqrt(rho_L) b_t,R) / (sqrt(rho_L) + sqrt(rho_R)),
+ *   rho~ = sqrt(rho_L rho_R), X = |b_t,L - b_t,R|^2 / (2 (sqrt(rho_L) + sqrt(rho_R))^2),
+ *   Y = (rho_L + rho_R) / (2 rho~),
+ *   a~^2 = (gamma - 1)(H~ - u~^2/2 - |b~|^2 / rho~) - (gamma - 2) X   [reading: floored at 0],
+ *   c~_t^2 = ((gamma - 1) - (gamma - 2) Y) |b~_t|^2 / rho~, c~_a^2 = b_n^2 / rho~,
+ *   c~_f^2 = (a~^2 + c~_a^2 + c~_t^2 + sqrt((c~_a^2 + c~_t^2 - a~^2)^2 + 4 a~^2 c~_t^2)) / 2.
+ * For equal states X = 0, Y = 1 and c~_f is the state's fast speed; without field a~ is the Roe sound
+ * speed of gas dynamics (both pinned).  X and Y themselves are pinned only through those limits
+ * ("parity partially pinned"). */
+template <class T>
+static void flux_hlle_roe(const T wl[NW7], const T wr[NW7], T bn, double gamma, T f[NW7]) {
+  T ul[NW7], ur[NW7], fl[NW7], fr[NW7];
+  physical_flux(wl, bn, gamma, ul, fl);
+  physical_flux(wr, bn, gamma, ur, fr);
+  const T cl = fast_speed(wl[IDN], wl[IPR], bn, wl[IBT1], wl[IBT2], gamma);
+  const T cr = fast_speed(wr[IDN], wr[IPR], bn, wr[IBT1], wr[IBT2], gamma);
+  const T sdl = sqrt(wl[IDN]), sdr = sqrt(wr[IDN]);
+  const T wsum = sdl + sdr;
+  const T rho = sdl * sdr;
+  T v[3], bt[2];
+  for (int k = 0; k < 3; ++k) v[k] = (sdl * wl[IVN + k] + sdr * wr[IVN + k]) / wsum;
+  for (int k = 0; k < 2; ++k) bt[k] = (sdr * wl[IBT1 + k] + sdl * wr[IBT1 + k]) / wsum;
+  const T ptl = wl[IPR] + 0.5 * ((bn * bn + wl[IBT1] * wl[IBT1]) + wl[IBT2] * wl[IBT2]);
+  const T ptr = wr[IPR] + 0.5 * ((bn * bn + wr[IBT1] * wr[IBT1]) + wr[IBT2] * wr[IBT2]);
+  const T h = ((ul[4] + ptl) / sdl + (ur[4] + ptr) / sdr) / wsum;
+  const T x = 0.5 * ((wl[IBT1] - wr[IBT1]) * (wl[IBT1] - wr[IBT1]) + (wl[IBT2] - wr[IBT2]) * (wl[IBT2] - wr[IBT2])) /
+              (wsum * wsum);
+  const T y = 0.5 * (wl[IDN] + wr[IDN]) / rho;
+  const T btsq = bt[0] * bt[0] + bt[1] * bt[1];
+  const T vsq = (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2];
+  const T ca2 = bn * bn / rho;
+  T a2 = (gamma - 1.0) * ((h - 0.5 * vsq) - (bn * bn + btsq) / rho) - (gamma - 2.0) * x;
+  if (a2 < 0.0) a2 = T(0.0);
+  const T ct2 = ((gamma - 1.0) - (gamma - 2.0) * y) * btsq / rho;
+  const T tdif = ca2 + ct2 - a2;
+  const T cf = sqrt(0.5 * ((a2 + ca2 + ct2) + sqrt(tdif * tdif + 4.0 * a2 * ct2)));
+  const T sl = vmin(wl[IVN] - cl, v[0] - cf);
+  const T sr = vmax(wr[IVN] + cr, v[0] + cf);
+  const T bm = vmin(sl, T(0.0));
+  const T bp = vmax(sr, T(0.0));
+  for (int n = 0; n < NW7; ++n)
+    f[n] = ((bp * fl[n] - bm * fr[n]) + (bp * bm) * (ur[n] - ul[n])) / (bp - bm);
+}
+
 /* HLLD flux (Miyoshi & Kusano 2005), written out in the order of that method:
  * outer speeds, contact speed S_M, total pressure p_T*, single-star states, Alfven speeds S*_L/R,
  * double-star states, flux selection.
@@ -340,6 +389,8 @@ template <class T>
 static void riemann(int solver, const T wl[NW7], const T wr[NW7], T bn, double gamma, T f[NW7]) {
   if (solver == RS_HLLE)
     flux_hlle(wl, wr, bn, gamma, f);
+  else if (solver == RS_HLLE_ROE)
+    flux_hlle_roe(wl, wr, bn, gamma, f);
   else
     flux_hlld(wl, wr, bn, gamma, f);
 }
@@ -1392,6 +1443,7 @@ void* orc_mesh_new(const int* nx, const int* mb, const double* xmin, const doubl
   }
   for (int f = 0; f < 6; ++f) p.bc[f] = bc[f];
   p.gamma = gamma;
+  if (riemann < orc::RS_HLLE || riemann > orc::RS_HLLE_ROE) return nullptr;
   p.riemann = riemann;
   p.dfloor = dfloor;
   p.pfloor = pfloor;

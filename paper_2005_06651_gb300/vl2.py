@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libvl2mhd.so")
 
 VL2_OK, VL2_E_ARG, VL2_E_CUDA, VL2_E_NONPHYS, VL2_E_TIMEOUT, VL2_E_STATE, VL2_E_NOMEM = range(7)
-HLLE, HLLD = 0, 1
+HLLE, HLLD, HLLE_ROE = 0, 1, 2
 PERIODIC, OUTFLOW = 0, 1
 VL2, RK1, RK2, RK3 = 0, 1, 2, 3  # time integrators (vl2_params.integrator)
 FP64, MIXED = 0, 1
