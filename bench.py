@@ -465,7 +465,8 @@ def integrators_form(args, dev, stream, vl2, inputs):
     and RK3 with PPM (three ghost layers), VL2 and RK3 with PLM on characteristic variables, VL2 + PLM
     carrying four passive scalars (eq. passive_scalars), and
     VL2 + PLM with the smoothed CT upwind weight (delta 1e-4, where most faces saturate, and delta 1, where
-    none does), zone-cycles/s next to VL2 + PLM (the bench line).  A cycle has 2 or 3 PLM / PPM stages against VL2's donor-cell + PLM / PPM."""
+    none does), and VL2 + PLM with HLLE (the states' own speeds, and Einfeldt's Roe-averaged ones),
+    zone-cycles/s next to VL2 + PLM + HLLD (the bench line).  A cycle has 2 or 3 PLM / PPM stages against VL2's donor-cell + PLM / PPM."""
     import torch
 
     prob = inputs.orszag_tang(n=args.n, mb=args.mb, seed=2005)
@@ -473,16 +474,19 @@ def integrators_form(args, dev, stream, vl2, inputs):
         args.n, (args.n // args.mb) ** 3, args.mb), "steps": args.rk_steps, "dtype": "f64"}}
     import numpy as np
 
-    for name, integ, recon, nsc, delta in (("rk2", vl2.RK2, vl2.PLM, 0, 0.0), ("rk3", vl2.RK3, vl2.PLM, 0, 0.0),
-                                           ("vl2_ppm", vl2.VL2, vl2.PPM, 0, 0.0),
-                                           ("rk3_ppm", vl2.RK3, vl2.PPM, 0, 0.0),
-                                           ("vl2_4_scalars", vl2.VL2, vl2.PLM, 4, 0.0),
-                                           ("vl2_plm_char", vl2.VL2, vl2.PLM_CHAR, 0, 0.0),
-                                           ("rk3_plm_char", vl2.RK3, vl2.PLM_CHAR, 0, 0.0),
-                                           ("vl2_ct_smooth", vl2.VL2, vl2.PLM, 0, 1e-4),
-                                           ("vl2_ct_smooth_wide", vl2.VL2, vl2.PLM, 0, 1.0)):
+    H = vl2.HLLD
+    for name, integ, recon, nsc, delta, rs in (("rk2", vl2.RK2, vl2.PLM, 0, 0.0, H), ("rk3", vl2.RK3, vl2.PLM, 0, 0.0, H),
+                                               ("vl2_ppm", vl2.VL2, vl2.PPM, 0, 0.0, H),
+                                               ("rk3_ppm", vl2.RK3, vl2.PPM, 0, 0.0, H),
+                                               ("vl2_4_scalars", vl2.VL2, vl2.PLM, 4, 0.0, H),
+                                               ("vl2_plm_char", vl2.VL2, vl2.PLM_CHAR, 0, 0.0, H),
+                                               ("rk3_plm_char", vl2.RK3, vl2.PLM_CHAR, 0, 0.0, H),
+                                               ("vl2_ct_smooth", vl2.VL2, vl2.PLM, 0, 1e-4, H),
+                                               ("vl2_ct_smooth_wide", vl2.VL2, vl2.PLM, 0, 1.0, H),
+                                               ("vl2_hlle", vl2.VL2, vl2.PLM, 0, 0.0, vl2.HLLE),
+                                               ("vl2_hlle_roe", vl2.VL2, vl2.PLM, 0, 0.0, vl2.HLLE_ROE)):
         m = vl2.Mesh.from_problem(prob, device=dev, stream=stream, integrator=integ, recon=recon, nscalars=nsc,
-                                  ct_delta=delta)
+                                  ct_delta=delta, riemann=rs)
         if nsc:
             rng = np.random.default_rng(4004)
             m.set_scalars(rng.uniform(0.0, 1.0, size=(nsc,) + prob.w.shape[1:]))

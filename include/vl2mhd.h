@@ -50,7 +50,9 @@ typedef enum vl2_status {
   VL2_E_NOMEM = 6     /* workspace smaller than vl2_workspace_bytes() */
 } vl2_status;
 
-enum { VL2_HLLE = 0, VL2_HLLD = 1 };       /* Riemann solver, Sec. 3.2.2 */
+/* Riemann solver, Sec. 3.2.2.  VL2_HLLE bounds the fan by the two states' fast speeds; VL2_HLLE_ROE takes
+ * Einfeldt's speeds min(u_L - c_L, u~ - c~_f), max(u_R + c_R, u~ + c~_f) with the MHD Roe average ~. */
+enum { VL2_HLLE = 0, VL2_HLLD = 1, VL2_HLLE_ROE = 2 };
 enum { VL2_PERIODIC = 0, VL2_OUTFLOW = 1 };/* per-face boundary condition */
 enum { VL2_FP64 = 0, VL2_MIXED = 1 };      /* arithmetic of reconstruction, fluxes and EMFs */
 enum { VL2_HOST = 0, VL2_DEVICE = 1 };     /* where a caller buffer lives */
@@ -70,7 +72,7 @@ typedef struct vl2_params {
   double xmin[3], xmax[3]; /* domain bounds; cells are uniform, dx_d = (xmax-xmin)/nx */
   double gamma;       /* adiabatic index of the ideal-gas EOS, P = (gamma-1) e (Sec. 3.1) */
   double cfl;         /* Courant number C0 of vl2_new_dt; <= 1/2 for VL2 in 3D (Sec. 3.2.3) */
-  int riemann;        /* VL2_HLLD or VL2_HLLE */
+  int riemann;        /* VL2_HLLD, VL2_HLLE or VL2_HLLE_ROE (not with adjoint) */
   int precision;      /* VL2_FP64: all arithmetic in FP64.  VL2_MIXED: reconstruction, Riemann fluxes and
                          CT EMFs in FP32 (FP32 scratch), while U and B stay FP64, cons->prim (pressure
                          recovery) is FP64, and the flux divergence / EMF curl are accumulated in FP64 */

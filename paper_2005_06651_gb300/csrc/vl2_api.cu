@@ -133,8 +133,8 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
     msg = "gamma > 1, cfl > 0 and floors that are positive normal numbers are required";
     return VL2_E_ARG;
   }
-  if (p->riemann != VL2_HLLD && p->riemann != VL2_HLLE) {
-    msg = "riemann must be VL2_HLLD or VL2_HLLE";
+  if (p->riemann != VL2_HLLD && p->riemann != VL2_HLLE && p->riemann != VL2_HLLE_ROE) {
+    msg = "riemann must be VL2_HLLD, VL2_HLLE or VL2_HLLE_ROE";
     return VL2_E_ARG;
   }
   if (p->precision != VL2_FP64 && p->precision != VL2_MIXED) {
@@ -151,6 +151,10 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
   }
   if (p->adjoint && p->integrator != VL2_INT_VL2) {
     msg = "the adjoint (params.adjoint = 1) is written for the VL2 integrator";
+    return VL2_E_ARG;
+  }
+  if (p->adjoint && p->riemann == VL2_HLLE_ROE) {
+    msg = "the adjoint (params.adjoint = 1) is written for VL2_HLLD and VL2_HLLE";
     return VL2_E_ARG;
   }
   if (p->adjoint && (p->ng != 2 || (p->recon != 0 && p->recon != VL2_PLM))) {
@@ -191,6 +195,7 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
   g.ng = p->ng;
   g.ns = p->nscalars;
   g.ct_delta = p->ct_delta;
+  g.hlle_roe = p->riemann == VL2_HLLE_ROE ? 1 : 0;
   g.sx = ((p->mb[0] + 2 * g.ng + 1) + 3) & ~3;
   g.sy = p->mb[1] + 2 * g.ng + 1;
   g.sz = p->mb[2] + 2 * g.ng + 1;

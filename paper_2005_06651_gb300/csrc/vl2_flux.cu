@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) k_flux(MeshView single, const MeshView* v
   if (RS == RS_HLLD)
     flux_hlld<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, f);
   else
-    flux_hlle<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, f);
+    flux_hlle<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, f, g.hlle_roe != 0);
   T* Fb = static_cast<T*>(V.a.f[DIR]) + (long long)b * 7 * g.box + c;
 #pragma unroll
   for (int n = 0; n < 7; ++n) Fb[(long long)n * g.box] = f[n];
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
     if (RS == RS_HLLD)
       flux_hlld<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, fl);
     else
-      flux_hlle<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, fl);
+      flux_hlle<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, fl, g.hlle_roe != 0);
     T* Fb = static_cast<T*>(V.a.f[DIR]) + (long long)b * 7 * g.box + o;
 #pragma unroll
     for (int n = 0; n < 7; ++n) Fb[(long long)n * g.box] = fl[n];

@@ -25,6 +25,7 @@ struct Geom {
   double idx[3];       // 1 / dx_d
   double dx[3];
   double gamma, gm1, igm1;
+  int hlle_roe;  // 1: the HLLE solver takes Einfeldt's Roe-averaged outer speeds
   double dfloor, pfloor;
   double ct_delta;     // smoothed CT upwind weight width (0: the sign switch)
 };

@@ -185,7 +185,7 @@ template <class R> __device__ __forceinline__ bool same_state(const R* a, const 
 // HLLE flux; outer speeds are the extreme fast-wave speeds of the two states (Sec. 3.2.2 names the
 // solver; the speed estimate is this library's reading).
 template <class R>
-__device__ __forceinline__ void flux_hlle(const R* wl, const R* wr, R bn, R gamma, R igm1, R* f) {
+__device__ __forceinline__ void flux_hlle(const R* wl, const R* wr, R bn, R gamma, R igm1, R* f, bool roe = false) {
   R ul[7], fl[7], ur[7], fr[7];
   phys_flux(wl, bn, igm1, ul, fl);
   if (same_state(wl, wr)) {
@@ -198,8 +198,36 @@ __device__ __forceinline__ void flux_hlle(const R* wl, const R* wr, R bn, R gamm
   const R ilr = inv(wl[0] * wr[0]);  // 1/rho_L and 1/rho_R from one reciprocal
   const R cl = fast_speed_r(wr[0] * ilr, wl[4], bn2, wl[5] * wl[5] + wl[6] * wl[6], gamma);
   const R cr = fast_speed_r(wl[0] * ilr, wr[4], bn2, wr[5] * wr[5] + wr[6] * wr[6], gamma);
-  const R sl = imin(wl[1] - cl, wr[1] - cr);
-  const R sr = imax(wl[1] + cl, wr[1] + cr);
+  R sl = imin(wl[1] - cl, wr[1] - cr);
+  R sr = imax(wl[1] + cl, wr[1] + cr);
+  if (roe) {
+    // Einfeldt's speeds: S_L = min(u_L - c_L, u~ - c~_f), S_R = max(u_R + c_R, u~ + c~_f), with c~_f the fast
+    // speed of the MHD Roe average (Cargo & Gallice): sqrt(rho) weights for u and H = (E + p_T) / rho,
+    // cross weights for b_t, X = |db_t|^2 / (2 (sqrt(rho_L) + sqrt(rho_R))^2), Y = (rho_L + rho_R) / (2 rho~)
+    const R sdl = root(wl[0]), sdr = root(wr[0]);
+    const R iws = inv(sdl + sdr);
+    const R irho = inv(sdl * sdr);
+    const R un = (sdl * wl[1] + sdr * wr[1]) * iws;
+    const R u1 = (sdl * wl[2] + sdr * wr[2]) * iws, u2 = (sdl * wl[3] + sdr * wr[3]) * iws;
+    const R b1 = (sdr * wl[5] + sdl * wr[5]) * iws, b2 = (sdr * wl[6] + sdl * wr[6]) * iws;
+    const R ptl = wl[4] + R(0.5) * ((bn2 + wl[5] * wl[5]) + wl[6] * wl[6]);
+    const R ptr = wr[4] + R(0.5) * ((bn2 + wr[5] * wr[5]) + wr[6] * wr[6]);
+    const R h = ((ul[4] + ptl) * inv(sdl) + (ur[4] + ptr) * inv(sdr)) * iws;
+    const R d1 = wl[5] - wr[5], d2 = wl[6] - wr[6];
+    const R x = R(0.5) * (d1 * d1 + d2 * d2) * (iws * iws);
+    const R y = R(0.5) * (wl[0] + wr[0]) * irho;
+    const R btsq = b1 * b1 + b2 * b2;
+    const R usq = (un * un + u1 * u1) + u2 * u2;
+    const R gm1 = gamma - R(1), gm2 = gamma - R(2);
+    const R ca2 = bn2 * irho;
+    R a2 = gm1 * ((h - R(0.5) * usq) - (bn2 + btsq) * irho) - gm2 * x;
+    a2 = a2 > R(0) ? a2 : R(0);
+    const R ct2 = (gm1 - gm2 * y) * btsq * irho;
+    const R tdif = ca2 + ct2 - a2;
+    const R cf = root_any(R(0.5) * ((a2 + ca2 + ct2) + root_any(tdif * tdif + R(4) * a2 * ct2)));
+    sl = imin(wl[1] - cl, un - cf);
+    sr = imax(wr[1] + cr, un + cf);
+  }
   const R bm = ge0(sl) ? R(0) : sl;
   const R bp = gt0(sr) ? sr : R(0);
   const R iden = inv(bp - bm);
