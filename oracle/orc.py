@@ -17,7 +17,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liborc.so")
 
 HLLE, HLLD, HLLE_ROE = 0, 1, 2
-DC, PLM, PPM, PLM_CHAR = 0, 1, 2, 3
+DC, PLM, PPM, PLM_CHAR, PPM_CHAR = 0, 1, 2, 3, 4
 VL2, RK1, RK2, RK3 = 0, 1, 2, 3
 
 _lib = None
@@ -77,6 +77,7 @@ def lib():
         L.orc_ppm_edges.argtypes = [dp, dp]
         L.orc_mhd_eigensystem.argtypes = [dp, ctypes.c_double, ctypes.c_double, dp, dp, dp]
         L.orc_char_slope.argtypes = [dp, ctypes.c_double, ctypes.c_double, dp]
+        L.orc_char_ppm_edges.argtypes = [dp, ctypes.c_double, ctypes.c_double, dp]
         L.orc_ppm_face.argtypes = [dp]
         L.orc_ppm_face.restype = ctypes.c_double
         L.orc_count_face_ops.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
@@ -150,6 +151,14 @@ def char_slope(qm, q0, qp, bn, gamma):
     out = np.zeros(7)
     lib().orc_char_slope(_dp(q), float(bn), float(gamma), _dp(out))
     return out
+
+
+def char_ppm_edges(q5, bn, gamma):
+    """Characteristic PPM (lower, upper) edge values of the middle of five states q5[5][7], as a (7, 2) array."""
+    q = _c64(np.asarray(q5, dtype=np.float64).reshape(35))
+    out = np.zeros(14)
+    lib().orc_char_ppm_edges(_dp(q), float(bn), float(gamma), _dp(out))
+    return out.reshape(7, 2)
 
 
 def ppm_edges(q5):
@@ -233,7 +242,7 @@ class Mesh:
         da = (ctypes.c_double * 3)(*self.xmin)
         db = (ctypes.c_double * 3)(*self.xmax)
         bcs = (ctypes.c_int * 6)(*bc)
-        self.ng = (3 if recon == PPM else 2) if ng is None else int(ng)
+        self.ng = (3 if recon in (PPM, PPM_CHAR) else 2) if ng is None else int(ng)
         self.nscalars = int(nscalars)
         self._h = L.orc_mesh_new(ia, ib, da, db, gamma, riemann, bcs, dfloor, pfloor, integrator, recon, self.ng,
                                  self.nscalars, float(ct_delta))

@@ -53,7 +53,7 @@ using std::sqrt;
 
 enum { RS_HLLE = 0, RS_HLLD = 1, RS_HLLE_ROE = 2 };
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
-enum { REC_DC = 0, REC_PLM = 1, REC_PPM = 2, REC_PLM_CHAR = 3 };
+enum { REC_DC = 0, REC_PLM = 1, REC_PPM = 2, REC_PLM_CHAR = 3, REC_PPM_CHAR = 4 };
 enum { INT_VL2 = 0, INT_RK1 = 1, INT_RK2 = 2, INT_RK3 = 3 };
 
 /* Interface-state layout (normal n, transverse t1, t2 taken cyclically: x->(y,z), y->(z,x),
@@ -616,6 +616,36 @@ static void char_slope(const T qm[NW7], const T q0[NW7], const T qp[NW7], T bn, 
   }
 }
 
+/* PPM edge values of the cell q[2] on characteristic variables [reading, as for char_slope]: the
+ * differences q[j] - q[2] of the five-cell stencil projected with L of the cell, the PPM edge steps
+ * (ppm_edges) on each characteristic field, and the two edges projected back with R.  ql / qr: the
+ * primitive values at the cell's lower / upper face (before the range clamp). */
+template <class T>
+static void char_ppm_edges(const T q[5][NW7], T bn, double gamma, T ql[NW7], T qr[NW7]) {
+  T R[NW7][NW7], L[NW7][NW7], lam[NW7];
+  mhd_eigensystem(q[2], bn, gamma, R, lam);
+  invert7(R, L);
+  T cl[NW7], cr[NW7];
+  for (int k = 0; k < NW7; ++k) {
+    T c[5];
+    for (int j = 0; j < 5; ++j) {
+      T acc = T(0.0);
+      for (int v = 0; v < NW7; ++v) acc = acc + L[k][v] * (q[j][v] - q[2][v]);
+      c[j] = (j == 2) ? T(0.0) : acc;
+    }
+    ppm_edges(c, cl[k], cr[k]);
+  }
+  for (int v = 0; v < NW7; ++v) {
+    T al = T(0.0), ar = T(0.0);
+    for (int k = 0; k < NW7; ++k) {
+      al = al + R[v][k] * cl[k];
+      ar = ar + R[v][k] * cr[k];
+    }
+    ql[v] = q[2][v] + al;
+    qr[v] = q[2][v] + ar;
+  }
+}
+
 /* A primitive face value from the characteristic reconstruction, kept within the range of the two
  * cells sharing the face [reading: projecting back can leave that range, and density and pressure
  * must stay positive]. */
@@ -712,7 +742,7 @@ struct Params {
   int bc[6];  // x-, x+, y-, y+, z-, z+
   double dfloor, pfloor;
   int integrator;
-  int recon;  // reconstruction of the PLM stages: REC_PLM, REC_PPM or REC_PLM_CHAR (VL2 corrector, RK2/RK3 stages)
+  int recon;  // reconstruction of the higher-order stages: REC_PLM, REC_PPM, REC_PLM_CHAR or REC_PPM_CHAR
   int ng;     // ghost layers: 2 (DC, PLM) or 3 (PPM)
   int nscal;  // passive scalars (eq. passive_scalars)
   double ct_delta;  // smoothed CT upwind weight width (0: the paper's sign switch)
@@ -987,6 +1017,15 @@ template <class T> struct Mesh {
                 ppm_edges(hi5, ql, qr);  // cell i
                 wr[v] = ql;
               }
+            } else if (recon == REC_PPM_CHAR) {
+              T qs[6][NW7];  // q_{i-3} .. q_{i+2} along d
+              for (int o = -3; o <= 2; ++o)
+                cell_state(B, d, k + o * sh[2], j + o * sh[1], i + o * sh[0], qs[o + 3]);
+              T a[NW7], b2[NW7];
+              char_ppm_edges(&qs[0], B.w[5 + d](k - sh[2], j - sh[1], i - sh[0]), P.gamma, a, b2);  // cell i-1
+              for (int v = 0; v < NW7; ++v) wl[v] = clamp_between(b2[v], qs[2][v], qs[3][v]);
+              char_ppm_edges(&qs[1], B.w[5 + d](k, j, i), P.gamma, a, b2);  // cell i
+              for (int v = 0; v < NW7; ++v) wr[v] = clamp_between(a[v], qs[2][v], qs[3][v]);
             } else if (recon == REC_PLM_CHAR) {
               cell_state(B, d, k - 2 * sh[2], j - 2 * sh[1], i - 2 * sh[0], qm2);
               cell_state(B, d, k + sh[2], j + sh[1], i + sh[0], qp1);
@@ -1019,7 +1058,7 @@ template <class T> struct Mesh {
               if (recon == REC_DC) {
                 cl = at(-1);
                 cr = at(0);
-              } else if (recon == REC_PPM) {
+              } else if (recon == REC_PPM || recon == REC_PPM_CHAR) {
                 const T lo5[5] = {at(-3), at(-2), at(-1), at(0), at(1)};
                 const T hi5[5] = {at(-2), at(-1), at(0), at(1), at(2)};
                 T a, b2;
@@ -1428,10 +1467,10 @@ void* orc_mesh_new(const int* nx, const int* mb, const double* xmin, const doubl
   orc::Params p;
   if (!(ct_delta >= 0.0) || !std::isfinite(ct_delta)) return nullptr;
   p.ct_delta = ct_delta;
-  if (recon != orc::REC_PLM && recon != orc::REC_PPM && recon != orc::REC_PLM_CHAR) return nullptr;
+  if (recon < orc::REC_PLM || recon > orc::REC_PPM_CHAR) return nullptr;
   if (nscal < 0 || nscal > 16) return nullptr;
   p.nscal = nscal;
-  if (ng < 2 || (recon == orc::REC_PPM && ng < 3)) return nullptr;
+  if (ng < 2 || ((recon == orc::REC_PPM || recon == orc::REC_PPM_CHAR) && ng < 3)) return nullptr;
   p.recon = recon;
   p.ng = ng;
   for (int d = 0; d < 3; ++d) {
@@ -1736,6 +1775,17 @@ void orc_mhd_eigensystem(const double* w, double bn, double gamma, double* R, do
       R[r * orc::NW7 + c] = Rm[r][c];
       L[r * orc::NW7 + c] = Lm[r][c];
     }
+}
+/* Characteristic PPM edges (lower, upper) of the middle cell of the five states q[5][7]. */
+void orc_char_ppm_edges(const double* q, double bn, double gamma, double* out) {
+  double qs[5][orc::NW7], ql[orc::NW7], qr[orc::NW7];
+  for (int j = 0; j < 5; ++j)
+    for (int v = 0; v < orc::NW7; ++v) qs[j][v] = q[j * orc::NW7 + v];
+  orc::char_ppm_edges<double>(qs, bn, gamma, ql, qr);
+  for (int v = 0; v < orc::NW7; ++v) {
+    out[2 * v] = ql[v];
+    out[2 * v + 1] = qr[v];
+  }
 }
 /* Limited slope of the characteristic reconstruction of the middle cell of q = (qm, q0, qp), 7 each. */
 void orc_char_slope(const double* q, double bn, double gamma, double* dw) {
