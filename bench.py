@@ -462,7 +462,7 @@ def adjoint_form(args, dev, stream, vl2, inputs):
 def integrators_form(args, dev, stream, vl2, inputs):
     """The other 2S integrators of Sec. 3.2.3 and PPM (Sec. 3.2.1) on the plain workload (256^3 vortex, 512
     MeshBlocks of 32^3, FP64, HLLD): RK2 (SSPRK(2,2)) and RK3 (SSPRK(3,3)) with PLM in every stage, and VL2
-    and RK3 with PPM (three ghost layers), VL2 and RK3 with PLM on characteristic variables, VL2 + PLM
+    and RK3 with PPM (three ghost layers), VL2 and RK3 with PLM and PPM on characteristic variables, VL2 + PLM
     carrying four passive scalars (eq. passive_scalars), and
     VL2 + PLM with the smoothed CT upwind weight (delta 1e-4, where most faces saturate, and delta 1, where
     none does), and VL2 + PLM with HLLE (the states' own speeds, and Einfeldt's Roe-averaged ones),
@@ -481,6 +481,8 @@ def integrators_form(args, dev, stream, vl2, inputs):
                                                ("vl2_4_scalars", vl2.VL2, vl2.PLM, 4, 0.0, H),
                                                ("vl2_plm_char", vl2.VL2, vl2.PLM_CHAR, 0, 0.0, H),
                                                ("rk3_plm_char", vl2.RK3, vl2.PLM_CHAR, 0, 0.0, H),
+                                               ("vl2_ppm_char", vl2.VL2, vl2.PPM_CHAR, 0, 0.0, H),
+                                               ("rk3_ppm_char", vl2.RK3, vl2.PPM_CHAR, 0, 0.0, H),
                                                ("vl2_ct_smooth", vl2.VL2, vl2.PLM, 0, 1e-4, H),
                                                ("vl2_ct_smooth_wide", vl2.VL2, vl2.PLM, 0, 1.0, H),
                                                ("vl2_hlle", vl2.VL2, vl2.PLM, 0, 0.0, vl2.HLLE),

@@ -56,9 +56,10 @@ enum { VL2_HLLE = 0, VL2_HLLD = 1, VL2_HLLE_ROE = 2 };
 enum { VL2_PERIODIC = 0, VL2_OUTFLOW = 1 };/* per-face boundary condition */
 enum { VL2_FP64 = 0, VL2_MIXED = 1 };      /* arithmetic of reconstruction, fluxes and EMFs */
 enum { VL2_HOST = 0, VL2_DEVICE = 1 };     /* where a caller buffer lives */
-/* reconstruction, Sec. 3.2.1 (PPM: eq. ppm-uniform-weights; PLM_CHAR: PLM on the characteristic variables
- * C = L W of the primitive MHD system, each face value then kept within its two cells' range) */
-enum { VL2_DC = 0, VL2_PLM = 1, VL2_PPM = 2, VL2_PLM_CHAR = 3 };
+/* reconstruction, Sec. 3.2.1 (PPM: eq. ppm-uniform-weights; PLM_CHAR / PPM_CHAR: PLM / PPM on the
+ * characteristic variables C = L W of the primitive MHD system, each face value then kept within its two
+ * cells' range) */
+enum { VL2_DC = 0, VL2_PLM = 1, VL2_PPM = 2, VL2_PLM_CHAR = 3, VL2_PPM_CHAR = 4 };
 /* time integrators of the 2S family (Sec. 3.2.3, eq. rk-2s and the coefficient list after it):
  * VL2 (default): donor-cell predictor with beta = 1/2, PLM corrector with beta = 1;
  * RK1: forward Euler with donor-cell fluxes; RK2 (SSPRK(2,2)) and RK3 (SSPRK(3,3)): PLM in every stage. */
@@ -83,8 +84,9 @@ typedef struct vl2_params {
   int adjoint;        /* 1: also reserve the arrays of vl2_step_vjp (VL2_FP64 only); 0: forward only */
   int integrator;     /* VL2_INT_VL2 (0, the default for a zero-initialised struct), VL2_INT_RK1, _RK2, _RK3 */
   int recon;          /* reconstruction of the higher-order stages (the VL2 corrector, every RK2 / RK3 stage):
-                         VL2_PLM (also 0), VL2_PPM (needs ng = 3) or VL2_PLM_CHAR; the adjoint takes
-                         VL2_PLM only.  The VL2 predictor and RK1 always use donor cell (Sec. 3.2.3). */
+                         VL2_PLM (also 0), VL2_PPM (needs ng = 3), VL2_PLM_CHAR or VL2_PPM_CHAR (needs
+                         ng = 3); the adjoint takes VL2_PLM only.  The VL2 predictor and RK1 always use
+                         donor cell (Sec. 3.2.3). */
   int nscalars;       /* passive scalars rho C_i, d(rho C_i)/dt + div(rho v C_i) = 0 (eq. passive_scalars):
                          0 .. VL2_MAX_SCALARS; 0 with adjoint; not in a batch */
   double ct_delta;    /* 0 (the default): the upwind CT corner picks the cell by the sign of the face mass flux,

@@ -46,7 +46,7 @@ struct vl2_mesh {
   vl2::MeshView view() const { return vl2::MeshView{g, a}; }
   int max_mb() const { return std::max(g.mb[0], std::max(g.mb[1], g.mb[2])); }
   // reconstruction of the higher-order stages (params.recon, 0 meaning PLM)
-  int rec() const { return (p.recon == VL2_PPM || p.recon == VL2_PLM_CHAR) ? p.recon : VL2_PLM; }
+  int rec() const { return (p.recon >= VL2_PPM && p.recon <= VL2_PPM_CHAR) ? p.recon : VL2_PLM; }
   ~vl2_mesh() {
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
   }
@@ -120,11 +120,11 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
     msg = "ng must be 2 or 3";
     return VL2_E_ARG;
   }
-  if (p->recon != 0 && p->recon != VL2_PLM && p->recon != VL2_PPM && p->recon != VL2_PLM_CHAR) {
-    msg = "recon must be VL2_PLM (or 0), VL2_PPM or VL2_PLM_CHAR";
+  if (p->recon < 0 || p->recon > VL2_PPM_CHAR) {
+    msg = "recon must be VL2_PLM (or 0), VL2_PPM, VL2_PLM_CHAR or VL2_PPM_CHAR";
     return VL2_E_ARG;
   }
-  if (p->recon == VL2_PPM && p->ng < 3) {
+  if ((p->recon == VL2_PPM || p->recon == VL2_PPM_CHAR) && p->ng < 3) {
     msg = "PPM needs ng = 3 (a face reads three cells on each side)";
     return VL2_E_ARG;
   }
@@ -345,7 +345,8 @@ cudaError_t k_ghosts(vl2_mesh* m, int reg) {
 }
 cudaError_t k_fluxes(vl2_mesh* m, int reg, int recon) {
   for (int d = 0; d < 3; ++d) {
-    const int kind = recon == VL2_DC ? VL2_K_FLUX_DC : (recon == VL2_PPM ? VL2_K_FLUX_PPM : VL2_K_FLUX_PLM);
+    const int kind = recon == VL2_DC ? VL2_K_FLUX_DC
+                                     : ((recon == VL2_PPM || recon == VL2_PPM_CHAR) ? VL2_K_FLUX_PPM : VL2_K_FLUX_PLM);
     cudaError_t e = timed(m, kind, flux_faces(m->g, d), [&] {
       return vl2::launch_flux(m->view(), nullptr, reg, recon, m->p.riemann, d, m->fs, m->max_mb(), m->st);
     });
@@ -897,7 +898,8 @@ static vl2_status gather_out(vl2_mesh* m, int kind, int dir, double* out, long l
 
 vl2_status vl2_debug_fluxes(vl2_mesh* m, int recon, double* fx, double* fy, double* fz, int where) {
   if (!m || !fx || !fy || !fz) return fail(m, VL2_E_ARG, "NULL argument");
-  if (bad_where(where) || (recon != VL2_DC && recon != VL2_PLM && recon != VL2_PLM_CHAR && !(recon == VL2_PPM && m->g.ng >= 3)))
+  if (bad_where(where) || (recon != VL2_DC && recon != VL2_PLM && recon != VL2_PLM_CHAR &&
+                              !((recon == VL2_PPM || recon == VL2_PPM_CHAR) && m->g.ng >= 3)))
     return fail(m, VL2_E_ARG, "bad where or recon (PPM needs ng = 3)");
   if (!m->initialized) return fail(m, VL2_E_STATE, "vl2_set_prims has not been called");
   vl2_status s = ensure_prims(m);
@@ -915,7 +917,8 @@ vl2_status vl2_debug_fluxes(vl2_mesh* m, int recon, double* fx, double* fy, doub
 
 vl2_status vl2_debug_emfs(vl2_mesh* m, int recon, double* e1, double* e2, double* e3, int where) {
   if (!m || !e1 || !e2 || !e3) return fail(m, VL2_E_ARG, "NULL argument");
-  if (bad_where(where) || (recon != VL2_DC && recon != VL2_PLM && recon != VL2_PLM_CHAR && !(recon == VL2_PPM && m->g.ng >= 3)))
+  if (bad_where(where) || (recon != VL2_DC && recon != VL2_PLM && recon != VL2_PLM_CHAR &&
+                              !((recon == VL2_PPM || recon == VL2_PPM_CHAR) && m->g.ng >= 3)))
     return fail(m, VL2_E_ARG, "bad where or recon (PPM needs ng = 3)");
   if (!m->initialized) return fail(m, VL2_E_STATE, "vl2_set_prims has not been called");
   vl2_status s = ensure_prims(m);

@@ -146,6 +146,31 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
       }
     }
   }
+  // phase A'': characteristic PPM of each cell from its five-cell stencil
+  for (int t = threadIdx.x; REC == REC_PPM_CHAR && t < P * L; t += blockDim.x) {
+    const int p = (DIR == 0) ? t / L : t % P;
+    const int c = (DIR == 0) ? t % L : t / P;
+    const int line = tile * P + p;
+    if (line >= nlines) continue;
+    int li[3];
+    li[DIR] = g.ng - 1 + c;
+    li[TA] = g.ng - 1 + line % na;
+    li[TB] = g.ng - 1 + line / na;
+    const long long o = cell_off(g, li[2], li[1], li[0]);
+    T qs[5][7], lo[7], hi[7];
+#pragma unroll
+    for (int n = 0; n < 7; ++n) {
+      const T* q = Wb + (long long)var[n] * g.box + o;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) qs[j][n] = q[(j - 2) * sd];
+    }
+    char_ppm_cell<T>(qs, Wb[(long long)(5 + DIR) * g.box + o], (T)g.gamma, lo, hi);
+#pragma unroll
+    for (int n = 0; n < 7; ++n) {
+      smem[sidx(n, 0, p, c)] = lo[n];
+      smem[sidx(n, 1, p, c)] = hi[n];
+    }
+  }
   // phase A': reconstruct cells on characteristic variables (its face values, clamped to the neighbours)
   for (int t = threadIdx.x; REC == REC_PLM_CHAR && t < P * L; t += blockDim.x) {
     const int p = (DIR == 0) ? t / L : t % P;
@@ -284,7 +309,7 @@ template <int DIR, int RS, class T>
 static cudaError_t launch_typed(const MeshView& v, const Dispatch* d, int reg, int recon, const FluxShape& fs,
                                 int max_mb, cudaStream_t st) {
   const Geom& g = v.g;
-  if (recon == REC_PLM || recon == REC_PPM || recon == REC_PLM_CHAR) {
+  if (recon == REC_PLM || recon == REC_PPM || recon == REC_PLM_CHAR || recon == REC_PPM_CHAR) {
     FluxShape f2 = fs;
     f2.plm_lines = plm_lines_for(g, DIR, fs, max_mb, recon);
     const size_t shmem = (size_t)f2.plm_lines * line_bytes(max_mb, recon, sizeof(T));
@@ -295,6 +320,9 @@ static cudaError_t launch_typed(const MeshView& v, const Dispatch* d, int reg, i
                                                                          d ? d->work : nullptr, reg, f2.plm_lines);
     else if (recon == REC_PLM_CHAR)
       k_flux_plm<DIR, RS, T, REC_PLM_CHAR><<<(unsigned)grid, 256, shmem, st>>>(
+          v, d ? d->views : nullptr, d ? d->work : nullptr, reg, f2.plm_lines);
+    else if (recon == REC_PPM_CHAR)
+      k_flux_plm<DIR, RS, T, REC_PPM_CHAR><<<(unsigned)grid, 256, shmem, st>>>(
           v, d ? d->views : nullptr, d ? d->work : nullptr, reg, f2.plm_lines);
     else
       k_flux_plm<DIR, RS, T, REC_PLM><<<(unsigned)grid, 256, shmem, st>>>(v, d ? d->views : nullptr,
@@ -332,6 +360,7 @@ cudaError_t prepare_kernel_attributes() {
 #define VL2_ATTR(DIR, RS, T)                                                      \
   if (e == cudaSuccess) e = set_smem_attr(k_flux_plm<DIR, RS, T, REC_PLM>);     \
   if (e == cudaSuccess) e = set_smem_attr(k_flux_plm<DIR, RS, T, REC_PLM_CHAR>); \
+  if (e == cudaSuccess) e = set_smem_attr(k_flux_plm<DIR, RS, T, REC_PPM_CHAR>); \
   if (e == cudaSuccess) e = set_smem_attr(k_flux_plm<DIR, RS, T, REC_PPM>);
   VL2_ATTR(0, RS_HLLD, double) VL2_ATTR(1, RS_HLLD, double) VL2_ATTR(2, RS_HLLD, double)
   VL2_ATTR(0, RS_HLLE, double) VL2_ATTR(1, RS_HLLE, double) VL2_ATTR(2, RS_HLLE, double)

@@ -8,7 +8,7 @@ namespace vl2 {
 
 
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
-enum { REC_DC = 0, REC_PLM = 1, REC_PPM = 2, REC_PLM_CHAR = 3 };
+enum { REC_DC = 0, REC_PLM = 1, REC_PPM = 2, REC_PLM_CHAR = 3, REC_PPM_CHAR = 4 };
 enum { RS_HLLE = 0, RS_HLLD = 1 };
 
 // Mesh geometry passed by value to every kernel.

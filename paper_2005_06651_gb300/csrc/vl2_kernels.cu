@@ -442,7 +442,7 @@ static cudaError_t launch_scalar_dir(const MeshView& v, int recon, cudaStream_t 
   if (n <= 0) return cudaSuccess;
   if (recon == REC_DC)
     k_scalar_flux<DIR, REC_DC, TF><<<grid, THREADS, 0, st>>>(v);
-  else if (recon == REC_PPM)
+  else if (recon == REC_PPM || recon == REC_PPM_CHAR)
     k_scalar_flux<DIR, REC_PPM, TF><<<grid, THREADS, 0, st>>>(v);
   else
     k_scalar_flux<DIR, REC_PLM, TF><<<grid, THREADS, 0, st>>>(v);

@@ -474,62 +474,100 @@ __device__ __forceinline__ void ppm_edges(R qm2, R qm1, R q0, R qp1, R qp2, R& q
 // are projected back with R, and each face value is kept within the range of the two cells sharing
 // the face.  lo / hi: the values at the cell's lower / upper face.
 template <class R>
+struct CharSys {
+  R rho, a2, af, as, b1, b2, sg, sr, Cf, Cs, Qf, Qs, Af, As, n2a, n2ra, hs;
+
+  __device__ __forceinline__ void init(const R q0[7], R bn, R gamma) {
+    rho = q0[0];
+    const R irho = inv_any(rho);
+    a2 = gamma * q0[4] * irho;
+    const R ca2 = bn * bn * irho;
+    const R btsq = q0[5] * q0[5] + q0[6] * q0[6];
+    const R ct2 = btsq * irho;
+    const R tdif = ca2 + ct2 - a2;
+    const R root = root_any(tdif * tdif + R(4) * a2 * ct2);  // c_f^2 - c_s^2
+    const R cf2 = R(0.5) * ((a2 + ca2 + ct2) + root);
+    const R xs = a2 - ca2 + ct2;
+    const R cf2_a2 = tdif >= R(0) ? R(0.5) * (tdif + root) : R(2) * a2 * ct2 * inv_any(root - tdif);
+    const R cf2_ca2 = xs >= R(0) ? R(0.5) * (xs + root) : R(2) * ca2 * ct2 * inv_any(root - xs);
+    const R icf2 = inv_any(cf2);
+    af = R(1);
+    as = R(0);
+    if (root != R(0)) {
+      const R ir = inv_any(root);
+      af = root_any(a2 * cf2_ca2 * icf2 * ir);  // (a^2 - c_s^2) / (c_f^2 - c_s^2)
+      as = root_any(cf2_a2 * ir);
+    }
+    const R a = root_any(a2), cf = root_any(cf2), cs = root_any(a2 * ca2 * icf2);
+    b1 = R(0.70710678118654752440);
+    b2 = R(0.70710678118654752440);
+    if (btsq != R(0)) {
+      const R ibt = rroot_any(btsq);
+      b1 = q0[5] * ibt;
+      b2 = q0[6] * ibt;
+    }
+    sg = bn >= R(0) ? R(1) : R(-1);
+    sr = root_any(rho);
+    const R isr = rroot_any(rho);
+    Cf = cf * af;
+    Cs = cs * as;
+    Qf = sg * Cf;
+    Qs = sg * Cs;
+    Af = a * af * sr;
+    As = a * as * sr;
+    n2a = R(0.5) * inv_any(a2);
+    n2ra = n2a * irho;
+    hs = R(0.5) * sg * isr;
+  }
+  // c = L d, in the order of the eigenvalues v - c_f, v - c_a, v - c_s, v, v + c_s, v + c_a, v + c_f
+  __device__ __forceinline__ void project(const R* d, R* c) const {
+    const R vp = b1 * d[2] + b2 * d[3], va = b1 * d[3] - b2 * d[2];
+    const R bp = b1 * d[5] + b2 * d[6], ba = b1 * d[6] - b2 * d[5];
+    const R pf = n2ra * (af * d[4] + As * bp), ps = n2ra * (as * d[4] - Af * bp);
+    const R uf = n2a * (Cf * d[1] - Qs * vp), us = n2a * (Cs * d[1] + Qf * vp);
+    c[0] = pf - uf;
+    c[1] = R(0.5) * va + hs * ba;
+    c[2] = ps - us;
+    c[3] = d[0] - R(2) * n2a * d[4];
+    c[4] = ps + us;
+    c[5] = R(0.5) * va - hs * ba;
+    c[6] = pf + uf;
+  }
+  // d = R m
+  __device__ __forceinline__ void back(const R* m, R* d) const {
+    const R fsum = m[0] + m[6], ssum = m[2] + m[4];
+    d[0] = rho * (af * fsum + as * ssum) + m[3];
+    d[1] = Cf * (m[6] - m[0]) + Cs * (m[4] - m[2]);
+    const R vp = Qs * (m[0] - m[6]) + Qf * (m[4] - m[2]), va = m[1] + m[5];
+    d[2] = b1 * vp - b2 * va;
+    d[3] = b2 * vp + b1 * va;
+    d[4] = rho * a2 * (af * fsum + as * ssum);
+    const R bp = As * fsum - Af * ssum, ba = sg * sr * (m[1] - m[5]);
+    d[5] = b1 * bp - b2 * ba;
+    d[6] = b2 * bp + b1 * ba;
+  }
+};
+
+template <class R>
+__device__ __forceinline__ R clamp_between(R x, R q1, R q2) {
+  return fmin(fmax(x, fmin(q1, q2)), fmax(q1, q2));
+}
+
+template <class R>
 __device__ __forceinline__ void char_plm_cell(const R qm[7], const R q0[7], const R qp[7], R bn, R gamma, R lo[7],
                                               R hi[7]) {
-  const R rho = q0[0];
-  const R irho = inv_any(rho);
-  const R a2 = gamma * q0[4] * irho;
-  const R ca2 = bn * bn * irho;
-  const R btsq = q0[5] * q0[5] + q0[6] * q0[6];
-  const R ct2 = btsq * irho;
-  const R tdif = ca2 + ct2 - a2;
-  const R root = root_any(tdif * tdif + R(4) * a2 * ct2);  // c_f^2 - c_s^2
-  const R cf2 = R(0.5) * ((a2 + ca2 + ct2) + root);
-  const R xs = a2 - ca2 + ct2;
-  const R cf2_a2 = tdif >= R(0) ? R(0.5) * (tdif + root) : R(2) * a2 * ct2 * inv_any(root - tdif);
-  const R cf2_ca2 = xs >= R(0) ? R(0.5) * (xs + root) : R(2) * ca2 * ct2 * inv_any(root - xs);
-  const R icf2 = inv_any(cf2);
-  R af = R(1), as = R(0);
-  if (root != R(0)) {
-    const R ir = inv_any(root);
-    af = root_any(a2 * cf2_ca2 * icf2 * ir);  // (a^2 - c_s^2) / (c_f^2 - c_s^2)
-    as = root_any(cf2_a2 * ir);
-  }
-  const R a = root_any(a2), cf = root_any(cf2), cs = root_any(a2 * ca2 * icf2);
-  R b1 = R(0.70710678118654752440), b2 = R(0.70710678118654752440);
-  if (btsq != R(0)) {
-    const R ibt = rroot_any(btsq);
-    b1 = q0[5] * ibt;
-    b2 = q0[6] * ibt;
-  }
-  const R sg = bn >= R(0) ? R(1) : R(-1);
-  const R sr = root_any(rho), isr = rroot_any(rho);
-  const R Cf = cf * af, Cs = cs * as, Qf = sg * Cf, Qs = sg * Cs, Af = a * af * sr, As = a * as * sr;
-  const R n2a = R(0.5) * inv_any(a2), n2ra = n2a * irho, hs = R(0.5) * sg * isr;
-  R dl[7], dr[7];
-#pragma unroll
-  for (int n = 0; n < 7; ++n) {
-    dl[n] = q0[n] - qm[n];
-    dr[n] = qp[n] - q0[n];
-  }
+  CharSys<R> cs;
+  cs.init(q0, bn, gamma);
   R m[7];
   {
-    R cl[7], cr[7];
-    auto project = [&](const R* d, R* c) {
-      const R vp = b1 * d[2] + b2 * d[3], va = b1 * d[3] - b2 * d[2];
-      const R bp = b1 * d[5] + b2 * d[6], ba = b1 * d[6] - b2 * d[5];
-      const R pf = n2ra * (af * d[4] + As * bp), ps = n2ra * (as * d[4] - Af * bp);
-      const R uf = n2a * (Cf * d[1] - Qs * vp), us = n2a * (Cs * d[1] + Qf * vp);
-      c[0] = pf - uf;  // v - c_f
-      c[1] = R(0.5) * va + hs * ba;  // v - c_a
-      c[2] = ps - us;  // v - c_s
-      c[3] = d[0] - R(2) * n2a * d[4];  // v (entropy)
-      c[4] = ps + us;  // v + c_s
-      c[5] = R(0.5) * va - hs * ba;  // v + c_a
-      c[6] = pf + uf;  // v + c_f
-    };
-    project(dl, cl);
-    project(dr, cr);
+    R dl[7], dr[7], cl[7], cr[7];
+#pragma unroll
+    for (int n = 0; n < 7; ++n) {
+      dl[n] = q0[n] - qm[n];
+      dr[n] = qp[n] - q0[n];
+    }
+    cs.project(dl, cl);
+    cs.project(dr, cr);
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
       // where c_l c_r > 0 both are at least ~1e-162, so c_l + c_r is a normal number
@@ -538,22 +576,41 @@ __device__ __forceinline__ void char_plm_cell(const R qm[7], const R q0[7], cons
       m[k] = pos ? (cl[k] * cr[k]) * inv(den) : R(0);
     }
   }
-  // half of the limited slope, back in primitives
-  const R fsum = m[0] + m[6], ssum = m[2] + m[4];
-  R dh[7];
-  dh[0] = rho * (af * fsum + as * ssum) + m[3];
-  dh[1] = Cf * (m[6] - m[0]) + Cs * (m[4] - m[2]);
-  const R vp = Qs * (m[0] - m[6]) + Qf * (m[4] - m[2]), va = m[1] + m[5];
-  dh[2] = b1 * vp - b2 * va;
-  dh[3] = b2 * vp + b1 * va;
-  dh[4] = rho * a2 * (af * fsum + as * ssum);
-  const R bp = As * fsum - Af * ssum, ba = sg * sr * (m[1] - m[5]);
-  dh[5] = b1 * bp - b2 * ba;
-  dh[6] = b2 * bp + b1 * ba;
+  R dh[7];  // half of the limited slope, back in primitives
+  cs.back(m, dh);
 #pragma unroll
   for (int n = 0; n < 7; ++n) {
-    lo[n] = fmin(fmax(q0[n] - dh[n], fmin(qm[n], q0[n])), fmax(qm[n], q0[n]));
-    hi[n] = fmin(fmax(q0[n] + dh[n], fmin(q0[n], qp[n])), fmax(q0[n], qp[n]));
+    lo[n] = clamp_between(q0[n] - dh[n], qm[n], q0[n]);
+    hi[n] = clamp_between(q0[n] + dh[n], q0[n], qp[n]);
+  }
+}
+
+// Characteristic PPM of one cell: the stencil differences q_j - q_0 (j = -2, -1, 1, 2) projected with the
+// cell's L, the PPM edge steps on each characteristic field, both edges projected back with R, and each
+// face value kept within the range of the two cells sharing the face.  qs[j][n] = stencil value j - 2.
+template <class R>
+__device__ __forceinline__ void char_ppm_cell(const R qs[5][7], R bn, R gamma, R lo[7], R hi[7]) {
+  CharSys<R> cs;
+  cs.init(qs[2], bn, gamma);
+  R c[4][7];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    R d[7];
+    const int s = j < 2 ? j : j + 1;
+#pragma unroll
+    for (int n = 0; n < 7; ++n) d[n] = qs[s][n] - qs[2][n];
+    cs.project(d, c[j]);
+  }
+  R el[7], er[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) ppm_edges(c[0][k], c[1][k], R(0), c[2][k], c[3][k], el[k], er[k]);
+  R dl[7], dr[7];
+  cs.back(el, dl);
+  cs.back(er, dr);
+#pragma unroll
+  for (int n = 0; n < 7; ++n) {
+    lo[n] = clamp_between(qs[2][n] + dl[n], qs[1][n], qs[2][n]);
+    hi[n] = clamp_between(qs[2][n] + dr[n], qs[2][n], qs[3][n]);
   }
 }
 

@@ -23,7 +23,7 @@ PERIODIC, OUTFLOW = 0, 1
 VL2, RK1, RK2, RK3 = 0, 1, 2, 3  # time integrators (vl2_params.integrator)
 FP64, MIXED = 0, 1
 HOST, DEVICE = 0, 1
-DC, PLM, PPM, PLM_CHAR = 0, 1, 2, 3  # reconstructions (vl2_params.recon for the higher-order stages)
+DC, PLM, PPM, PLM_CHAR, PPM_CHAR = 0, 1, 2, 3, 4  # reconstructions (vl2_params.recon for the higher-order stages)
 
 STATUS_NAMES = {0: "VL2_OK", 1: "VL2_E_ARG", 2: "VL2_E_CUDA", 3: "VL2_E_NONPHYS", 4: "VL2_E_TIMEOUT",
                 5: "VL2_E_STATE", 6: "VL2_E_NOMEM"}
@@ -167,7 +167,7 @@ class Mesh:
         p = Params()
         p.nx[:] = self.nx
         p.mb[:] = self.mb
-        p.ng = (3 if recon == PPM else 2) if ng is None else int(ng)
+        p.ng = (3 if recon in (PPM, PPM_CHAR) else 2) if ng is None else int(ng)
         p.recon = int(recon)
         p.nscalars = int(nscalars)
         p.ct_delta = float(ct_delta)

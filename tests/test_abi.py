@@ -71,7 +71,7 @@ def test_workspace_bytes_and_argument_checks(lib):
            dict(bc=(0, 1, 0, 0, 0, 0)), dict(nx=(0, 32, 32)), dict(xmax=(0.0, 1.0, 1.0)), dict(recon=7),
            dict(recon=2, ng=2), dict(adjoint=1, ng=3), dict(adjoint=1, ng=3, recon=2), dict(nscalars=-1),
            dict(nscalars=17), dict(adjoint=1, nscalars=1), dict(ct_delta=-1.0),
-           dict(ct_delta=float("nan")), dict(adjoint=1, recon=3), dict(recon=4),
+           dict(ct_delta=float("nan")), dict(adjoint=1, recon=3), dict(recon=5), dict(recon=4, ng=2),
            dict(riemann=3), dict(adjoint=1, riemann=2)]
     for kw in bad:
         assert lib.vl2_workspace_bytes(ctypes.byref(_params(**kw)), ctypes.byref(n)) == 1, kw

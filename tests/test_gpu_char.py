@@ -1,5 +1,5 @@
-"""PLM on characteristic variables (Sec. 3.2.1: C = L W) on the GPU, through the C ABI, against the FP64
-oracle.
+"""PLM and PPM on characteristic variables (Sec. 3.2.1: C = L W) on the GPU, through the C ABI, against the
+FP64 oracle.
 
 - stage fluxes and corner EMFs equal the oracle's to rounding (the GPU takes the left eigenvectors in
   closed form, the oracle as R^-1 by elimination)
@@ -44,13 +44,17 @@ def vl2():
     return mod
 
 
+RECONS = ["PLM_CHAR", "PPM_CHAR"]
+
+
+@pytest.mark.parametrize("recon", RECONS)
 @pytest.mark.parametrize("riemann", [1, 0])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_char_stage_fluxes_and_emfs(vl2, oracle, case, riemann):
+def test_char_stage_fluxes_and_emfs(vl2, oracle, case, riemann, recon):
     prob = CASES[case]()
-    g = vl2.Mesh.from_problem(prob, riemann=riemann, recon=vl2.PLM_CHAR)
-    o = oracle.Mesh.from_problem(prob, riemann=riemann, recon=oracle.PLM_CHAR)
-    gf, of = g.debug_fluxes(vl2.PLM_CHAR), o.debug_fluxes(oracle.PLM_CHAR)
+    g = vl2.Mesh.from_problem(prob, riemann=riemann, recon=getattr(vl2, recon))
+    o = oracle.Mesh.from_problem(prob, riemann=riemann, recon=getattr(oracle, recon))
+    gf, of = g.debug_fluxes(getattr(vl2, recon)), o.debug_fluxes(getattr(oracle, recon))
     worst = 0.0
     for d in range(3):
         scale = float(np.max(np.abs(of[d])))
@@ -58,83 +62,89 @@ def test_char_stage_fluxes_and_emfs(vl2, oracle, case, riemann):
             err = float(np.max(np.abs(gf[d][c] - of[d][c]))) / scale
             worst = max(worst, err)
             assert err <= 1e-12, (d, c, err)
-    ge, oe = g.debug_emfs(vl2.PLM_CHAR), o.debug_emfs(oracle.PLM_CHAR)
+    ge, oe = g.debug_emfs(getattr(vl2, recon)), o.debug_emfs(getattr(oracle, recon))
     for e in range(3):
         scale = float(np.max(np.abs(oe[e]))) + 1e-12
         err = float(np.max(np.abs(ge[e] - oe[e]))) / scale
         worst = max(worst, err)
         assert err <= 1e-12, (e, err)
-    print("characteristic PLM stage terms, %s, riemann %d: max normalised difference %.2e" % (case, riemann, worst))
-    # the characteristic limiter gives other fluxes than primitive PLM where several waves overlap (on a
-    # single eigenmode the two limit the same amplitudes and agree)
+    print("%s stage terms, %s, riemann %d: max normalised difference %.2e" % (recon, case, riemann, worst))
+    # the characteristic limiter gives other fluxes than the primitive one where several waves overlap (on
+    # a single eigenmode the two limit the same amplitudes and agree)
     if case.startswith("ot"):
-        assert np.max(np.abs(g.debug_fluxes(vl2.PLM)[0] - gf[0])) > 1e-10
+        prim = vl2.PLM if recon == "PLM_CHAR" else vl2.PPM
+        assert np.max(np.abs(g.debug_fluxes(prim)[0] - gf[0])) > 1e-10
 
 
+@pytest.mark.parametrize("recon", RECONS)
 @pytest.mark.parametrize("integrator", ["VL2", "RK3"])
 @pytest.mark.parametrize("riemann", [1, 0])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_char_one_cycle(vl2, oracle, case, riemann, integrator):
+def test_char_one_cycle(vl2, oracle, case, riemann, integrator, recon):
     prob = CASES[case]()
     kw = dict(riemann=riemann, integrator=getattr(vl2, integrator))
-    g = vl2.Mesh.from_problem(prob, recon=vl2.PLM_CHAR, **kw)
+    g = vl2.Mesh.from_problem(prob, recon=getattr(vl2, recon), **kw)
     okw = dict(riemann=riemann, integrator=getattr(oracle, integrator))
-    o = oracle.Mesh.from_problem(prob, recon=oracle.PLM_CHAR, **okw)
+    o = oracle.Mesh.from_problem(prob, recon=getattr(oracle, recon), **okw)
     dt = o.new_dt(0.3)
     assert g.new_dt() == pytest.approx(dt, rel=1e-13)
     g.step(dt)
     o.step(dt)
     d = float(np.max(state_diff(g.get_cons(), o.get_cons())))
-    spread = oracle_spread(oracle, prob, recon=oracle.PLM_CHAR, **okw)
-    print("characteristic PLM, one %s cycle, %s, riemann %d: GPU vs oracle %.2e, oracle spread %.2e"
-          % (integrator, case, riemann, d, spread))
+    spread = oracle_spread(oracle, prob, recon=getattr(oracle, recon), **okw)
+    print("%s, one %s cycle, %s, riemann %d: GPU vs oracle %.2e, oracle spread %.2e"
+          % (recon, integrator, case, riemann, d, spread))
     assert d <= max(1e-12, 4.0 * spread)
     assert g.divb_norm() <= 1e-13
 
 
+@pytest.mark.parametrize("recon", RECONS)
 @pytest.mark.parametrize("riemann", [1, 0])
-def test_char_brio_wu_ten_cycles(vl2, oracle, riemann):
+def test_char_brio_wu_ten_cycles(vl2, oracle, riemann, recon):
     prob = brio_wu()
-    g = vl2.Mesh.from_problem(prob, riemann=riemann, recon=vl2.PLM_CHAR, mb=(16, 1, 1))
-    o = oracle.Mesh.from_problem(prob, riemann=riemann, recon=oracle.PLM_CHAR, mb=(16, 1, 1))
+    g = vl2.Mesh.from_problem(prob, riemann=riemann, recon=getattr(vl2, recon), mb=(16, 1, 1))
+    o = oracle.Mesh.from_problem(prob, riemann=riemann, recon=getattr(oracle, recon), mb=(16, 1, 1))
     for _ in range(10):
         dt = o.new_dt(0.4)
         g.step(dt)
         o.step(dt)
     d = float(np.max(state_diff(g.get_cons(), o.get_cons())))
-    print("characteristic PLM, Brio-Wu tube, riemann %d, 10 cycles: %.2e" % (riemann, d))
+    print("%s, Brio-Wu tube, riemann %d, 10 cycles: %.2e" % (recon, riemann, d))
     assert d <= 1e-12
 
 
-def test_char_hundred_smooth_cycles(vl2, oracle):
+@pytest.mark.parametrize("recon", RECONS)
+def test_char_hundred_smooth_cycles(vl2, oracle, recon):
     prob = inputs.linear_wave(16, mb=8, kind="fast", amp=1e-2, v0=(0.3, -0.2, 0.1), phase=0.37)
-    g = vl2.Mesh.from_problem(prob, recon=vl2.PLM_CHAR)
-    o = oracle.Mesh.from_problem(prob, recon=oracle.PLM_CHAR)
+    g = vl2.Mesh.from_problem(prob, recon=getattr(vl2, recon))
+    o = oracle.Mesh.from_problem(prob, recon=getattr(oracle, recon))
     for _ in range(100):
         dt = o.new_dt(0.3)
         g.step(dt)
         o.step(dt)
     d = state_diff(g.get_cons(), o.get_cons())
-    print("characteristic PLM, 100 smooth cycles: %.2e" % np.max(d))
+    print("%s, 100 smooth cycles: %.2e" % (recon, np.max(d)))
     assert np.max(d) <= 1e-9
 
 
-def test_char_batch_bitwise_mixed_and_refusals(vl2):
+@pytest.mark.parametrize("recon", RECONS)
+def test_char_batch_bitwise_mixed_and_refusals(vl2, recon):
+    rc = getattr(vl2, recon)
     probs = [inputs.orszag_tang(n=n, mb=n, seed=60 + n) for n in (16, 24, 32)]
-    solo = [vl2.Mesh.from_problem(p, recon=vl2.PLM_CHAR) for p in probs]
+    solo = [vl2.Mesh.from_problem(p, recon=rc) for p in probs]
     dts = [m.new_dt() for m in solo]
     for m, dt in zip(solo, dts):
         m.step(dt)
-    meshes = [vl2.Mesh.from_problem(p, recon=vl2.PLM_CHAR) for p in probs]
+    meshes = [vl2.Mesh.from_problem(p, recon=rc) for p in probs]
     vl2.Batch(meshes).step(dts)
     for a, b in zip(solo, meshes):
         for x, y in zip(a.get_cons(), b.get_cons()):
             np.testing.assert_array_equal(x, y)
-    m = vl2.Mesh.from_problem(inputs.orszag_tang(n=32, mb=16, seed=2005), recon=vl2.PLM_CHAR, precision=vl2.MIXED)
+    m = vl2.Mesh.from_problem(inputs.orszag_tang(n=32, mb=16, seed=2005), recon=rc, precision=vl2.MIXED)
     t0 = m.totals()
     for _ in range(10):
         m.step(m.new_dt())
     assert abs(m.totals()[0] - t0[0]) <= 1e-13 * abs(t0[0])
     assert m.divb_norm() <= 1e-13
     with pytest.raises(vl2.VL2Error):
-        vl2.Mesh.from_problem(probs[0], recon=vl2.PLM_CHAR, adjoint=True)
+        vl2.Mesh.from_problem(probs[0], recon=rc, adjoint=True)
