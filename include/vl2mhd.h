@@ -94,7 +94,7 @@ typedef struct vl2_params {
                          weight (1 + tanh(m / ct_delta)) / 2 on the upwind-side gradient, in mass-flux units;
                          it equals the sign switch where tanh saturates and at m = 0, and makes the corner a
                          smooth function of m (with adjoint, vl2_step_vjp then carries dw/dm).  Finite;
-                         not in a batch. */
+                         the meshes of a batch share one value. */
 } vl2_params;
 
 #define VL2_MAX_SCALARS 16

@@ -1068,13 +1068,16 @@ vl2_status batch_check(vl2_mesh* const* meshes, int n, std::string& msg) {
       msg = "NULL mesh in the batch";
       return VL2_E_ARG;
     }
-    if (meshes[q]->p.integrator != VL2_INT_VL2 || meshes[q]->g.ns != 0 || meshes[q]->g.ct_delta > 0.0) {
-      msg = "the batched form runs the VL2 integrator without passive scalars or the smoothed CT weight";
+    if (meshes[q]->p.integrator != VL2_INT_VL2 || meshes[q]->g.ns != 0) {
+      msg = "the batched form runs the VL2 integrator without passive scalars";
       return VL2_E_ARG;
     }
+    // one launch serves every mesh: the kernel variants (solver, precision, reconstruction, smoothed CT
+    // or not) are chosen once, so the meshes must agree on them; the smoothed weight's delta is read per
+    // mesh, but is required equal too so that a batch is one configuration
     if (meshes[q]->p.riemann != meshes[0]->p.riemann || meshes[q]->p.precision != meshes[0]->p.precision ||
-        meshes[q]->rec() != meshes[0]->rec()) {
-      msg = "all meshes of a batch need the same Riemann solver, precision and reconstruction";
+        meshes[q]->rec() != meshes[0]->rec() || meshes[q]->g.ct_delta != meshes[0]->g.ct_delta) {
+      msg = "all meshes of a batch need the same Riemann solver, precision, reconstruction and ct_delta";
       return VL2_E_ARG;
     }
   }

@@ -85,8 +85,19 @@ def test_smooth_weight_refusals_and_mixed(vl2):
     for kw in (dict(ct_delta=-1.0), dict(ct_delta=float("inf")), dict(ct_delta=float("nan"))):
         with pytest.raises(vl2.VL2Error):
             vl2.Mesh.from_problem(prob, **kw)
+    # a batch whose meshes share delta is bitwise the per-mesh path; mixing deltas is refused
+    probs = [inputs.orszag_tang(n=n, mb=n, seed=80 + n) for n in (16, 24, 32)]
+    solo = [vl2.Mesh.from_problem(p, ct_delta=0.05) for p in probs]
+    dts = [m.new_dt() for m in solo]
+    for m, dt in zip(solo, dts):
+        m.step(dt)
+    meshes = [vl2.Mesh.from_problem(p, ct_delta=0.05) for p in probs]
+    vl2.Batch(meshes).step(dts)
+    for a, b in zip(solo, meshes):
+        for x, y in zip(a.get_cons(), b.get_cons()):
+            np.testing.assert_array_equal(x, y)
     with pytest.raises(vl2.VL2Error):
-        vl2.Batch([vl2.Mesh.from_problem(prob, ct_delta=1e-3)])
+        vl2.Batch([vl2.Mesh.from_problem(probs[0], ct_delta=1e-3), vl2.Mesh.from_problem(probs[1])])
     m = vl2.Mesh.from_problem(prob, precision=vl2.MIXED, ct_delta=0.1)
     t0 = m.totals()
     for _ in range(5):
