@@ -271,14 +271,15 @@ vl2_status vl2_launch_count(const vl2_mesh* mesh, long long* n);
  * (box, tile) work list that covers every box; each box keeps its own CFL time step (Sec. 2.1.7) on the
  * device; vl2_batch_run captures K cycles in one CUDA graph and launches it once.
  * The batch refers to the meshes' own device arrays (no copy): results are read back with the mesh calls
- * (vl2_get_cons, vl2_new_dt, ...).  All meshes need the same Riemann solver and precision and must not
- * be stepped through their own calls while a batch call runs; the batch uses the first mesh's stream.
+ * (vl2_get_cons, vl2_new_dt, ...).  All meshes need the VL2 integrator, no passive scalars, and the same
+ * Riemann solver, precision, reconstruction and ct_delta; they must not be stepped through their own
+ * calls while a batch call runs; the batch uses the first mesh's stream.
  * The caller owns the batch workspace (vl2_batch_workspace_bytes, 256-byte aligned) and the meshes; the
  * batch must be destroyed before its meshes. */
 typedef struct vl2_batch vl2_batch;
 
 /* Bytes of device workspace for a batch of these meshes (mesh views, per-box dt, work lists).
- * Errors: VL2_E_ARG (NULL, n <= 0, mixed solvers or precisions). */
+ * Errors: VL2_E_ARG (NULL, n <= 0, meshes that do not share the options above). */
 vl2_status vl2_batch_workspace_bytes(vl2_mesh* const* meshes, int n, size_t* bytes);
 
 /* Create the batch (builds and uploads its work lists).  Errors: VL2_E_ARG, VL2_E_NOMEM, VL2_E_CUDA. */
