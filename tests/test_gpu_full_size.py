@@ -8,7 +8,8 @@
   round-off over two cycles.
 - The later rows at 256^3 in 512 MeshBlocks, one cycle against the oracle (<= 1e-12): VL2 + PPM on the
   vortex (three ghost layers), the vortex carrying two passive scalars, and the hydrodynamic blast wave
-  (r0 = 0.01, 56 cells), whose uniform regions run the solvers' equal-state branch.
+  (r0 = 0.01, 56 cells), whose uniform regions run the solvers' equal-state branch; and the options on
+  the vortex: PLM on characteristic variables, HLLE with Einfeldt's speeds, the smoothed CT weight.
 """
 import numpy as np
 import pytest
@@ -102,3 +103,11 @@ def test_scalars_256cubed_one_cycle_match_oracle(vl2, oracle):
 def test_hydro_blast_256cubed_one_cycle_matches_oracle(vl2, oracle):
     prob = inputs.blast(n=256, mb=32, r0=0.01, magnetized=False)
     _one_cycle(vl2, oracle, prob, "256^3 hydrodynamic blast, one cycle")
+
+
+@pytest.mark.parametrize("option", ["plm_char", "hlle_roe", "ct_smooth"])
+def test_options_256cubed_one_cycle_match_oracle(vl2, oracle, option):
+    prob = inputs.orszag_tang(n=256, mb=32, seed=2005)
+    kw = {"plm_char": dict(recon=vl2.PLM_CHAR), "hlle_roe": dict(riemann=vl2.HLLE_ROE),
+          "ct_smooth": dict(ct_delta=1e-4)}[option]
+    _one_cycle(vl2, oracle, prob, "256^3 VL2, %s, one cycle" % option, **kw)
