@@ -2,9 +2,10 @@
 // of its input state, with dt held fixed.  Written kernel by kernel in reverse order of the cycle
 // (Sec. 3.2.3): update -> CT corner EMFs -> fluxes (PLM / donor cell + Riemann solver) -> cons->prim ->
 // ghost exchange, for the corrector and then the predictor.  The linear steps (update, CT for the frozen
-// upwind choices, ghost exchange, PLM limiter away from its switch) have hand-derived transposes; the
-// Riemann solvers have hand-written reverse-mode derivatives (vl2_riemann_vjp.cuh) that replay the
-// forward flux's arithmetic and branch decisions.
+// upwind choices, ghost exchange, PLM limiter away from its switch) have hand-derived transposes; with the
+// smoothed CT weight the corner is also differentiated in the face mass fluxes; the Riemann solvers have
+// hand-written reverse-mode derivatives (vl2_riemann_vjp.cuh) that replay the forward flux's arithmetic
+// and branch decisions.
 #include "vl2_internal.h"
 #include "vl2_physics.cuh"
 #include "vl2_riemann_vjp.cuh"
