@@ -627,11 +627,13 @@ __device__ __forceinline__ R ct_pick(R m, R lo, R hi) {
 // cell the mass flux m comes from, 1 - w on the other.  Where |m| > 20 delta, 1 - |tanh(m / delta)| < 1e-17 is
 // below half an ulp of 1 (2^-54), so tanh rounds to +-1 and w to exactly 1 or 0: the sign switch's pick,
 // taken here without the tanh.  At m = 0, w = 1/2 is the switch's mean.
+// Inside the band the weight is evaluated as (1 + tanh x) / 2 = 1 / (1 + exp(-2x)), x = m / delta: one
+// exponential and a reciprocal (|x| <= 20 keeps exp(-2x) within [4e-18, 3e17]).
 template <class R>
 __device__ __forceinline__ R ct_weight(R m, R delta, R band) {
   if (fabs(m) > band) return m > R(0) ? R(1) : R(0);
   if (m == R(0)) return R(0.5);  // tanh(0) = 0; also where delta underflows to 0 in R
-  return R(0.5) * (R(1) + tanh(m / delta));
+  return inv(R(1) + exp(R(-2) * (m / delta)));
 }
 
 template <class R>
