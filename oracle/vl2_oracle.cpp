@@ -24,6 +24,10 @@
  *   - one global time step from |v| + C_f                                      (Sec. 2.1.7, 3.2.3)
  *   - passive scalars rho C_i, d(rho C_i)/dt + div(rho v C_i) = 0 (eq. passive_scalars), C_i reconstructed
  *     like the other primitives and carried by the Riemann mass flux from the upwind side   (Sec. 3.1)
+ *   - options beside the paper's defaults: PLM and PPM on characteristic variables C = L W (Sec. 3.2.1;
+ *     eigensystem derived from the primitive equations, L = R^-1 by elimination), HLLE with Einfeldt's
+ *     Roe-averaged speeds (Sec. 3.2.2), and a smoothed upwind weight in the CT corner (tanh of the mass
+ *     flux; the tangent-linear carries its derivative)
  *
  * The paper names HLLE / HLLD / upwind CT / VL2 but prints no formulas for them; the formulas here
  * are written from the published methods (HLLD: Miyoshi & Kusano 2005; upwind CT: Gardiner &
@@ -38,7 +42,11 @@
  * Parity pins: every function here is pinned by a CPU test (consistency, exact contact / rotational
  * discontinuity, exact Sod solution, linear-wave convergence slope, CT identities, conservation,
  * mirror / axis symmetry).  The choice of the upwind cell in the CT corner EMF (gs05) is pinned only
- * through the convergence slope and the symmetry tests ("parity partially pinned").
+ * through the convergence slope and the symmetry tests ("parity partially pinned").  Of the options,
+ * the Roe-averaging factors X and Y of Einfeldt's HLLE speeds are pinned only through their limits
+ * (equal states, gas dynamics, equal densities and transverse fields: "parity partially pinned"); the
+ * characteristic eigensystem is pinned by A R = R lam and L R = I, the smoothed weight by its limits,
+ * its conditioning and its tangent against finite differences.
  */
 #include <cmath>
 #include <cstdint>
