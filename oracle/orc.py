@@ -72,6 +72,7 @@ def lib():
         L.orc_physical_flux.argtypes = [dp, ctypes.c_double, ctypes.c_double, dp, dp]
         L.orc_fast_speed.argtypes = [ctypes.c_double] * 6
         L.orc_fast_speed.restype = ctypes.c_double
+        L.orc_roe_fast_speed.argtypes = [dp, dp, ctypes.c_double, ctypes.c_double, dp]
         L.orc_vanleer_slope.argtypes = [ctypes.c_double] * 3
         L.orc_vanleer_slope.restype = ctypes.c_double
         L.orc_ppm_edges.argtypes = [dp, dp]
@@ -130,6 +131,14 @@ def physical_flux(w, bn, gamma):
 
 def fast_speed(d, p, bn, bt1, bt2, gamma):
     return lib().orc_fast_speed(d, p, bn, bt1, bt2, gamma)
+
+
+def roe_fast_speed(wl, wr, bn, gamma):
+    """(u~, c~_f): Roe-averaged normal velocity and the fast speed of the MHD Roe matrix (Einfeldt's HLLE)."""
+    out = np.zeros(2)
+    wl, wr = _c64(wl), _c64(wr)
+    lib().orc_roe_fast_speed(_dp(wl), _dp(wr), float(bn), float(gamma), _dp(out))
+    return float(out[0]), float(out[1])
 
 
 def vanleer_slope(qm, q0, qp):

@@ -43,8 +43,8 @@
  * discontinuity, exact Sod solution, linear-wave convergence slope, CT identities, conservation,
  * mirror / axis symmetry).  The choice of the upwind cell in the CT corner EMF (gs05) is pinned only
  * through the convergence slope and the symmetry tests ("parity partially pinned").  Of the options,
- * the Roe-averaging factors X and Y of Einfeldt's HLLE speeds are pinned only through their limits
- * (equal states, gas dynamics, equal densities and transverse fields: "parity partially pinned"); the
+ * Einfeldt's HLLE speed is pinned by a Roe matrix built independently from exact difference identities
+ * (Roe's property, its extreme eigenvalues) and by exact fast shocks, whose speed it must reproduce; the
  * characteristic eigensystem is pinned by A R = R lam and L R = I, the smoothed weight by its limits,
  * its conditioning and its tangent against finite differences.
  */
@@ -216,27 +216,27 @@ static void flux_hlle(const T wl[NW7], const T wr[NW7], T bn, double gamma, T f[
     f[n] = ((bp * fl[n] - bm * fr[n]) + (bp * bm) * (ur[n] - ul[n])) / (bp - bm);
 }
 
-/* HLLE flux with Einfeldt's outer speeds: S_L = min(u_L - c_L, u~ - c~_f), S_R = max(u_R + c_R, u~ + c~_f),
- * where ~ is the Roe average of the two states (the paper names the solver and Roe's linearisation,
- * Sec. 3.2.2, without formulas).  The averaged fast speed is that of the MHD Roe matrix of Cargo &
- * Gallice 1997 (as used by Stone et al. 2008):
- *   sqrt(rho) weights for velocity and total enthalpy H = (E + p_T) / rho, the cross weights for the
- *   transverse field b~_t = (sqrt(rho_R) b_t,L + sqrt(rho_L) b_t,R) / (sqrt(rho_L) + sqrt(rho_R)),
- *   rho~ = sqrt(rho_L rho_R), X = |b_t,L - b_t,R|^2 / (2 (sqrt(rho_L) + sqrt(rho_R))^2),
- *   Y = (rho_L + rho_R) / (2 rho~),
- *   a~^2 = (gamma - 1)(H~ - u~^2/2 - |b~|^2 / rho~) - (gamma - 2) X   [reading: floored at 0],
- *   c~_t^2 = ((gamma - 1) - (gamma - 2) Y) |b~_t|^2 / rho~, c~_a^2 = b_n^2 / rho~,
+/* Fast speed of a Roe matrix of the 1D ideal-MHD flux, about the Roe-averaged normal velocity (the paper
+ * names HLLE and Roe's linearisation, Sec. 3.2.2, without formulas) [reading].  The matrix is the one whose
+ * rows are exact difference identities of the flux in the averages
+ *   rho~ = sqrt(rho_L rho_R), u~ and H~ = (E + p_T) / rho weighted by sqrt(rho),
+ *   b~_t = (sqrt(rho_R) b_t,L + sqrt(rho_L) b_t,R) / (sqrt(rho_L) + sqrt(rho_R))   (cross weights),
+ * e.g. d(rho u v) = u~ d(rho v) + v~ d(rho u) - u~ v~ d(rho), d(b_t v_n) = v~_n db_t + b~_t dv_n,
+ * dv_n = (d(rho v_n) - v~_n d(rho)) / rho~; the magnetic pressure differs as
+ *   d(|b_t|^2 / 2) = b~_t . db_t + X d(rho),   X = |b_t,L - b_t,R|^2 / (2 (sqrt(rho_L) + sqrt(rho_R))^2).
+ * Its fast eigenvalues are u~ -+ c~_f with
+ *   a~^2 = (gamma - 1)(H~ - |u~|^2 / 2 - |b~|^2 / rho~) - (gamma - 2) X   (|b~|^2 = b_n^2 + |b~_t|^2),
+ *   c~_a^2 = b_n^2 / rho~, c~_t^2 = |b~_t|^2 / rho~,
  *   c~_f^2 = (a~^2 + c~_a^2 + c~_t^2 + sqrt((c~_a^2 + c~_t^2 - a~^2)^2 + 4 a~^2 c~_t^2)) / 2.
- * For equal states X = 0, Y = 1 and c~_f is the state's fast speed; without field a~ is the Roe sound
- * speed of gas dynamics (both pinned).  X and Y themselves are pinned only through those limits
- * ("parity partially pinned"). */
+ * a~^2 >= 0 holds in exact arithmetic (the sqrt(rho) average of |u|^2 is >= |u~|^2 and the field part of
+ * H~ exceeds |b~|^2 / rho~ by 2 X); it is floored at 0 against rounding.  Pins: the matrix satisfies
+ * Roe's property and has these eigenvalues (checked against an independently built matrix), and for two
+ * states joined by one exact fast shock u~ -+ c~_f is the shock speed, as Roe's property requires. */
 template <class T>
-static void flux_hlle_roe(const T wl[NW7], const T wr[NW7], T bn, double gamma, T f[NW7]) {
+static void roe_fast_speed(const T wl[NW7], const T wr[NW7], T bn, double gamma, T* un_out, T* cf_out) {
   T ul[NW7], ur[NW7], fl[NW7], fr[NW7];
   physical_flux(wl, bn, gamma, ul, fl);
   physical_flux(wr, bn, gamma, ur, fr);
-  const T cl = fast_speed(wl[IDN], wl[IPR], bn, wl[IBT1], wl[IBT2], gamma);
-  const T cr = fast_speed(wr[IDN], wr[IPR], bn, wr[IBT1], wr[IBT2], gamma);
   const T sdl = sqrt(wl[IDN]), sdr = sqrt(wr[IDN]);
   const T wsum = sdl + sdr;
   const T rho = sdl * sdr;
@@ -248,17 +248,30 @@ static void flux_hlle_roe(const T wl[NW7], const T wr[NW7], T bn, double gamma, 
   const T h = ((ul[4] + ptl) / sdl + (ur[4] + ptr) / sdr) / wsum;
   const T x = 0.5 * ((wl[IBT1] - wr[IBT1]) * (wl[IBT1] - wr[IBT1]) + (wl[IBT2] - wr[IBT2]) * (wl[IBT2] - wr[IBT2])) /
               (wsum * wsum);
-  const T y = 0.5 * (wl[IDN] + wr[IDN]) / rho;
   const T btsq = bt[0] * bt[0] + bt[1] * bt[1];
   const T vsq = (v[0] * v[0] + v[1] * v[1]) + v[2] * v[2];
   const T ca2 = bn * bn / rho;
   T a2 = (gamma - 1.0) * ((h - 0.5 * vsq) - (bn * bn + btsq) / rho) - (gamma - 2.0) * x;
   if (a2 < 0.0) a2 = T(0.0);
-  const T ct2 = ((gamma - 1.0) - (gamma - 2.0) * y) * btsq / rho;
+  const T ct2 = btsq / rho;
   const T tdif = ca2 + ct2 - a2;
-  const T cf = sqrt(0.5 * ((a2 + ca2 + ct2) + sqrt(tdif * tdif + 4.0 * a2 * ct2)));
-  const T sl = vmin(wl[IVN] - cl, v[0] - cf);
-  const T sr = vmax(wr[IVN] + cr, v[0] + cf);
+  *un_out = v[0];
+  *cf_out = sqrt(0.5 * ((a2 + ca2 + ct2) + sqrt(tdif * tdif + 4.0 * a2 * ct2)));
+}
+
+/* HLLE flux with Einfeldt's outer speeds: S_L = min(u_L - c_L, u~ - c~_f), S_R = max(u_R + c_R, u~ + c~_f),
+ * with u~ and c~_f from roe_fast_speed. */
+template <class T>
+static void flux_hlle_roe(const T wl[NW7], const T wr[NW7], T bn, double gamma, T f[NW7]) {
+  T ul[NW7], ur[NW7], fl[NW7], fr[NW7];
+  physical_flux(wl, bn, gamma, ul, fl);
+  physical_flux(wr, bn, gamma, ur, fr);
+  const T cl = fast_speed(wl[IDN], wl[IPR], bn, wl[IBT1], wl[IBT2], gamma);
+  const T cr = fast_speed(wr[IDN], wr[IPR], bn, wr[IBT1], wr[IBT2], gamma);
+  T un, cf;
+  roe_fast_speed(wl, wr, bn, gamma, &un, &cf);
+  const T sl = vmin(wl[IVN] - cl, un - cf);
+  const T sr = vmax(wr[IVN] + cr, un + cf);
   const T bm = vmin(sl, T(0.0));
   const T bp = vmax(sr, T(0.0));
   for (int n = 0; n < NW7; ++n)
@@ -1766,6 +1779,10 @@ void orc_physical_flux(const double* w, double bn, double gamma, double* u, doub
 
 double orc_fast_speed(double d, double p, double bn, double bt1, double bt2, double gamma) {
   return orc::fast_speed<double>(d, p, bn, bt1, bt2, gamma);
+}
+
+void orc_roe_fast_speed(const double* wl, const double* wr, double bn, double gamma, double* out) {
+  orc::roe_fast_speed<double>(wl, wr, bn, gamma, &out[0], &out[1]);
 }
 
 double orc_vanleer_slope(double qm, double q0, double qp) { return orc::vanleer_slope<double>(qm, q0, qp); }

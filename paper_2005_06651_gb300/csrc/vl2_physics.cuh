@@ -202,8 +202,10 @@ __device__ __forceinline__ void flux_hlle(const R* wl, const R* wr, R bn, R gamm
   R sr = imax(wl[1] + cl, wr[1] + cr);
   if (roe) {
     // Einfeldt's speeds: S_L = min(u_L - c_L, u~ - c~_f), S_R = max(u_R + c_R, u~ + c~_f), with c~_f the fast
-    // speed of the MHD Roe average (Cargo & Gallice): sqrt(rho) weights for u and H = (E + p_T) / rho,
-    // cross weights for b_t, X = |db_t|^2 / (2 (sqrt(rho_L) + sqrt(rho_R))^2), Y = (rho_L + rho_R) / (2 rho~)
+    // eigenvalue (about u~) of the Roe matrix of the 1D MHD flux built from sqrt(rho) weights for u and
+    // H = (E + p_T) / rho, cross weights for b_t and rho~ = sqrt(rho_L rho_R); its magnetic-pressure difference
+    // adds X = |db_t|^2 / (2 (sqrt(rho_L) + sqrt(rho_R))^2) to the sound speed term:
+    //   a~^2 = (gamma-1)(H~ - |u~|^2/2 - |b~|^2/rho~) - (gamma-2) X,  c~_t^2 = |b~_t|^2 / rho~
     const R sdl = root(wl[0]), sdr = root(wr[0]);
     const R iws = inv(sdl + sdr);
     const R irho = inv(sdl * sdr);
@@ -215,14 +217,13 @@ __device__ __forceinline__ void flux_hlle(const R* wl, const R* wr, R bn, R gamm
     const R h = ((ul[4] + ptl) * inv(sdl) + (ur[4] + ptr) * inv(sdr)) * iws;
     const R d1 = wl[5] - wr[5], d2 = wl[6] - wr[6];
     const R x = R(0.5) * (d1 * d1 + d2 * d2) * (iws * iws);
-    const R y = R(0.5) * (wl[0] + wr[0]) * irho;
     const R btsq = b1 * b1 + b2 * b2;
     const R usq = (un * un + u1 * u1) + u2 * u2;
     const R gm1 = gamma - R(1), gm2 = gamma - R(2);
     const R ca2 = bn2 * irho;
     R a2 = gm1 * ((h - R(0.5) * usq) - (bn2 + btsq) * irho) - gm2 * x;
     a2 = a2 > R(0) ? a2 : R(0);
-    const R ct2 = (gm1 - gm2 * y) * btsq * irho;
+    const R ct2 = btsq * irho;
     const R tdif = ca2 + ct2 - a2;
     const R cf = root_any(R(0.5) * ((a2 + ca2 + ct2) + root_any(tdif * tdif + R(4) * a2 * ct2)));
     sl = imin(wl[1] - cl, un - cf);

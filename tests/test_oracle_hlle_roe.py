@@ -5,11 +5,16 @@ solver and Roe's linearisation) against what the mathematics fixes, without a GP
 - gas dynamics (no field): the test's Roe averages u~, H~ satisfy Roe's property A(u~, H~) dU = dF for the
   Euler Jacobian (textbook), and the oracle's flux is the HLL flux with S_L = min(u_L - a_L, u~ - a~),
   S_R = max(u_R + a_R, u~ + a~)
-- with a field but equal densities and transverse fields (X = 0, Y = 1 in the MHD Roe average) the flux
-  is the HLL flux with the fast speed of the averaged state, a~^2 = (gamma-1)(H~ - u~^2/2 - B^2/rho)
+- MHD, unequal densities and transverse fields: a Roe matrix of the 1D ideal-MHD flux is built here, row by
+  row, from exact difference identities (no X, no closed-form speed in it); it satisfies Roe's property
+  A dU = dF to round-off, and its extreme eigenvalues are the oracle's u~ -+ c~_f
+- MHD, two states joined by one exact fast shock (Rankine-Hugoniot conditions solved here): Roe's property
+  makes the shock speed an eigenvalue of every Roe matrix, so u~ -+ c~_f is the shock speed and Einfeldt's
+  HLLE returns the exact upwind flux; X > 0 and rho_L != rho_R there
+- with a field but equal densities and transverse fields the flux is the HLL flux with the fast speed of
+  the averaged state, a~^2 = (gamma-1)(H~ - u~^2/2 - B^2/rho)
 - the scheme: mirror symmetry and MeshBlock independence bitwise; density and pressure stay positive
   through the strong double rarefaction where a linearised solver loses positivity
-X and Y themselves are pinned only through those limits (parity partially pinned).
 """
 import numpy as np
 import pytest
@@ -80,6 +85,170 @@ def test_gas_dynamics_einfeldt_speeds(oracle):
         sr = max(wr[1] + np.sqrt(g * wr[4] / wr[0]), ut[0] + at)
         np.testing.assert_allclose(oracle.riemann(2, wl, wr, 0.0, g), hll(oracle, wl, wr, 0.0, g, sl, sr),
                                    rtol=1e-12, atol=1e-12)
+
+
+def mhd_flux(w, bn, g):
+    """Physical x-flux of 1D ideal MHD for the primitive state w = (rho, u, v, w, p, b_y, b_z)."""
+    rho, u, v, wz, p, b1, b2 = w
+    e = cons(w, bn, g)[4]
+    pt = p + 0.5 * (bn * bn + b1 * b1 + b2 * b2)
+    vb = u * bn + v * b1 + wz * b2
+    return np.array([rho * u, rho * u * u + pt - bn * bn, rho * u * v - bn * b1, rho * u * wz - bn * b2,
+                     (e + pt) * u - bn * vb, b1 * u - bn * v, b2 * u - bn * wz])
+
+
+def roe_matrix(wl, wr, bn, g):
+    """A Roe matrix of the 1D ideal-MHD flux in the conserved variables (rho, M, E, b_y, b_z), written row by
+    row from exact identities for the difference of each flux term between the two states.  With s = sqrt(rho),
+    rho~ = s_L s_R and sqrt(rho)-weighted averages v~ and H~ = (E + p_T)/rho:
+      d(M_a M_b / rho) = v~_a dM_b + v~_b dM_a - v~_a v~_b d(rho)
+      d(v_a)           = (dM_a - v~_a d(rho)) / rho~
+      d(rho H v_n)     = H~ dM_n + v~_n d(rho H) - v~_n H~ d(rho),   d(rho H) = dE + d(p_T)
+      d(b v_a)         = v~_a db + b* d(v_a)   with the cross-weighted b* = (s_R b_L + s_L b_R)/(s_L + s_R)
+      d(|b_t|^2 / 2)   = b* . db_t + X d(rho),  X = |b_t,R - b_t,L|^2 / (2 (s_L + s_R)^2)
+                         (the arithmetic mean of b_t minus b* is (s_R - s_L) db_t / (2 (s_L + s_R)), and
+                         d(rho) = (s_R - s_L)(s_L + s_R))
+      d(p_T)           = (gamma-1)(dE - v~ . dM + |v~|^2/2 d(rho)) - (gamma-2)(b* . db_t + X d(rho))
+    Each identity is exact for any two states, so A dU = dF holds to round-off.  Writing the magnetic
+    pressure through b* keeps one averaged transverse field in every row; X then sits in the density
+    column.  (Through the arithmetic mean instead, A would be another Roe matrix with other eigenvalues
+    away from shocks; every Roe matrix has the speed of a single shock joining the two states as an
+    eigenvalue.)"""
+    sl, sr = np.sqrt(wl[0]), np.sqrt(wr[0])
+    rt = sl * sr
+    v = (sl * wl[1:4] + sr * wr[1:4]) / (sl + sr)
+    h = [(cons(w, bn, g)[4] + w[4] + 0.5 * (bn * bn + w[5] ** 2 + w[6] ** 2)) / w[0] for w in (wl, wr)]
+    ht = (sl * h[0] + sr * h[1]) / (sl + sr)
+    bstar = (sr * wl[5:7] + sl * wr[5:7]) / (sl + sr)
+    db = wr[5:7] - wl[5:7]
+    x = db @ db / (2 * (sl + sr) ** 2)
+    dpt = np.zeros(7)
+    dpt[0] = (g - 1) * 0.5 * v @ v - (g - 2) * x
+    dpt[1:4] = -(g - 1) * v
+    dpt[4] = g - 1
+    dpt[5:7] = -(g - 2) * bstar
+    dv = np.zeros((3, 7))
+    for a in range(3):
+        dv[a, 1 + a] = 1.0 / rt
+        dv[a, 0] = -v[a] / rt
+    A = np.zeros((7, 7))
+    A[0, 1] = 1.0
+    A[1] = dpt
+    A[1, 1] += 2 * v[0]
+    A[1, 0] -= v[0] * v[0]
+    for c in range(2):
+        A[2 + c, 2 + c] += v[0]
+        A[2 + c, 1] += v[1 + c]
+        A[2 + c, 0] -= v[0] * v[1 + c]
+        A[2 + c, 5 + c] -= bn
+    drh = dpt.copy()
+    drh[4] += 1.0
+    A[4] = v[0] * drh
+    A[4, 1] += ht
+    A[4, 0] -= v[0] * ht
+    A[4] -= bn * bn * dv[0]
+    for c in range(2):
+        A[4] -= bn * bstar[c] * dv[1 + c]
+        A[4, 5 + c] -= bn * v[1 + c]
+        A[5 + c] = bstar[c] * dv[0] - bn * dv[1 + c]
+        A[5 + c, 5 + c] += v[0]
+    return A
+
+
+def random_pair(rng):
+    def one():
+        return np.array([rng.uniform(0.2, 3), *rng.uniform(-2, 2, 3), rng.uniform(0.05, 3), *rng.uniform(-2, 2, 2)])
+    return one(), one(), rng.uniform(-2, 2)
+
+
+def test_mhd_roe_matrix_property_and_fast_eigenvalues(oracle):
+    rng = np.random.default_rng(11)
+    worst = 0.0
+    for _ in range(1000):
+        wl, wr, bn = random_pair(rng)
+        A = roe_matrix(wl, wr, bn, G)
+        du = cons(wr, bn, G) - cons(wl, bn, G)
+        df = mhd_flux(wr, bn, G) - mhd_flux(wl, bn, G)
+        np.testing.assert_allclose(A @ du, df, rtol=0, atol=1e-12 * (1 + np.abs(df).max()))
+        lam = np.linalg.eigvals(A)
+        assert np.abs(lam.imag).max() <= 1e-6 * np.abs(lam.real).max()
+        lam = np.sort(lam.real)
+        un, cf = oracle.roe_fast_speed(wl, wr, bn, G)
+        err = max(abs(lam[-1] - (un + cf)), abs(lam[0] - (un - cf))) / cf
+        worst = max(worst, err)
+    print("Roe matrix: max relative gap of the extreme eigenvalues to u~ -+ c~_f: %.2e" % worst)
+    assert worst <= 1e-10
+
+
+def fast_shock(rho1, p1, bn, bt1, r, g):
+    """Upstream (left, flowing in at u1 > 0) and downstream states of a fast shock at rest, compression r,
+    from the Rankine-Hugoniot conditions: mass, transverse momentum, induction and normal momentum fix the
+    downstream state for a given u1; the energy condition fixes u1 (root between the upstream fast speed and
+    20 times it)."""
+    from scipy.optimize import brentq
+
+    def down(u1):
+        m = rho1 * u1
+        b2 = bt1 * r * (rho1 * u1 * u1 - bn * bn) / (rho1 * u1 * u1 - r * bn * bn)
+        v2 = bn * (b2 - bt1) / m
+        p2 = p1 + m * (u1 - u1 / r) + 0.5 * (bt1 * bt1 - b2 * b2)
+        return (np.array([rho1, u1, 0.0, 0.0, p1, bt1, 0.0]), np.array([rho1 * r, u1 / r, v2, 0.0, p2, b2, 0.0]))
+
+    def energy_jump(u1):
+        wa, wb = down(u1)
+        return mhd_flux(wb, bn, g)[4] - mhd_flux(wa, bn, g)[4]
+
+    c1 = np.sqrt(fast(np.array([rho1, 0, 0, 0, p1, bt1, 0.0]), bn, g) ** 2)
+    us = np.linspace(c1 * 1.0001, 20 * c1, 2000)
+    f = [energy_jump(u) for u in us]
+    for a in range(len(us) - 1):
+        if f[a] * f[a + 1] < 0:
+            u1 = brentq(energy_jump, us[a], us[a + 1], xtol=1e-15, rtol=1e-15)
+            return down(u1)
+    return None
+
+
+def boost(w, bn, vx, vt, theta):
+    """The state in a frame moving with (-vx, -vt): velocities shifted, the transverse plane rotated by theta."""
+    c, s = np.cos(theta), np.sin(theta)
+    rho, u, v, wz, p, b1, b2 = w
+    vy, vz = c * v - s * wz + vt[0], s * v + c * wz + vt[1]
+    by, bz = c * b1 - s * b2, s * b1 + c * b2
+    return np.array([rho, u + vx, vy, vz, p, by, bz])
+
+
+def test_exact_fast_shocks_move_at_the_roe_fast_speed(oracle):
+    rng = np.random.default_rng(12)
+    checked = 0
+    for _ in range(60):
+        rho1, p1 = rng.uniform(0.3, 2), rng.uniform(0.1, 2)
+        bn, bt1 = rng.uniform(0.1, 1.5) * rng.choice([-1, 1]), rng.uniform(0.1, 1.5)
+        r = rng.uniform(1.1, 3.6)
+        pair = fast_shock(rho1, p1, bn, bt1, r, G)
+        if pair is None:
+            continue
+        wa, wb = pair
+        s = -rng.uniform(0.01, 0.4) * wb[1]    # the shock moves left, slower than the downstream flow
+        vt, theta = rng.uniform(-1, 1, 2), rng.uniform(0, 2 * np.pi)
+        wl, wr = boost(wa, bn, s, vt, theta), boost(wb, bn, s, vt, theta)
+        du = cons(wr, bn, G) - cons(wl, bn, G)
+        df = mhd_flux(wr, bn, G) - mhd_flux(wl, bn, G)
+        scale = np.abs(mhd_flux(wr, bn, G)).max()
+        assert np.abs(df - s * du).max() <= 1e-12 * scale        # Rankine-Hugoniot
+        un, cf = oracle.roe_fast_speed(wl, wr, bn, G)
+        assert abs((un - cf) - s) <= 1e-12 * cf
+        # S_L = s exactly, so Einfeldt's HLLE returns the flux of the right (downstream) state
+        np.testing.assert_allclose(oracle.riemann(2, wl, wr, bn, G), mhd_flux(wr, bn, G), rtol=0,
+                                   atol=1e-12 * scale)
+        # the mirror image: a right-facing shock moving right, upwind flux of the left state
+        mir = np.array([1, -1, 1, 1, 1, 1, 1.0])
+        ml, mr = wr * mir, wl * mir
+        un, cf = oracle.roe_fast_speed(ml, mr, -bn, G)
+        assert abs((un + cf) + s) <= 1e-12 * cf
+        np.testing.assert_allclose(oracle.riemann(2, ml, mr, -bn, G), mhd_flux(ml, -bn, G), rtol=0,
+                                   atol=1e-12 * scale)
+        checked += 1
+    assert checked >= 40
 
 
 def test_mhd_equal_density_and_field(oracle):
