@@ -325,7 +325,9 @@ const char* vl2_batch_last_error(const vl2_batch* batch);
  * Memory: the partial sums go to a file-scope device array that this library reserves on every GPU that
  * loads it, until the process exits; nothing is allocated or freed.  The first call on a device looks up
  * that array's device address with the device current, so make that first call before any stream
- * capture begins.  All calls share the array: calls whose work overlaps on the GPU (other streams, other
+ * capture begins.  The address is kept for the life of the process: a device reset (cudaDeviceReset, or
+ * any teardown of the device's primary context) leaves it stale, so do not call this entry point on a
+ * device after resetting it.  All calls share the array: calls whose work overlaps on the GPU (other streams, other
  * host threads) race and must be serialised by the caller.  Every slot a call reads it first writes, so
  * no clearing is needed between calls.
  * Errors: VL2_E_ARG (NULL pointer, non-positive size, nz > VL2_NOALLOC_MAX_NZ), VL2_E_CUDA; the message

@@ -147,17 +147,13 @@ __device__ __forceinline__ void pick_w(double m, double& w0, double& w1) {
   }
 }
 
-// Smoothed upwind weight of the forward corner (w = (1 + tanh(m / delta)) / 2, flat at 0 or 1 where
-// |m| > 20 delta) and its derivative in the mass flux, dw/dm = (1 - tanh^2) / (2 delta).
+// Smoothed upwind weight of the forward corner, evaluated by the forward step's own ct_weight (so the adjoint
+// linearises about the very weight the forward cycle used), and its derivative in the mass flux:
+// w = 1 / (1 + exp(-2 m / delta)) gives dw/dm = 2 w (1 - w) / delta, which is 0 where the weight is flat at
+// 0 or 1 (|m| > 20 delta).
 __device__ __forceinline__ void smooth_w(double m, double delta, double& w, double& dw) {
-  if (fabs(m) > 20.0 * delta) {
-    w = m > 0.0 ? 1.0 : 0.0;
-    dw = 0.0;
-    return;
-  }
-  const double t = m == 0.0 ? 0.0 : tanh(m / delta);
-  w = 0.5 * (1.0 + t);
-  dw = 0.5 * (1.0 - t * t) / delta;
+  w = ct_weight<double>(m, delta, 20.0 * delta);
+  dw = 2.0 * w * (1.0 - w) / delta;
 }
 
 __device__ __forceinline__ void pick_w(double m, double delta, double& w0, double& w1) {

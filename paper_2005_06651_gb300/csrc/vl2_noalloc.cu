@@ -21,7 +21,8 @@ constexpr int kThreads = 256;
 // reads is written earlier in the same call, so nothing has to be cleared between calls.
 static __device__ __align__(256) double g_plane_sums[kMaxPlanes * 8];
 
-// Device address of g_plane_sums per device, looked up once with that device current.
+// Device address of g_plane_sums per device, looked up once with that device current and kept for the life of
+// the process (a reset of the device's context makes it stale; the header says so).
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 double* g_scratch[kMaxDevices] = {nullptr};

@@ -367,20 +367,45 @@ class Mesh:
         return n
 
 
-def totals_noalloc(u, b1, b2, b3, dx, out, stream=None):
-    """vl2_totals_noalloc on device tensors u [5][NZ][NY][NX], b1, b2, b3 (global layout) into the device
-    tensor out (8 doubles), enqueued on `stream` (default: the current torch stream).  Allocates nothing."""
+def _noalloc_args(u, b1, b2, b3, out):
+    """Validate the tensors of totals_noalloc before anything reaches the device: shapes first (u [5][NZ][NY][NX],
+    b1 (NZ, NY, NX+1), b2 (NZ, NY+1, NX), b3 (NZ+1, NY, NX), out at least 8 elements), then contiguous
+    float64 CUDA tensors on one device.  Returns (NX, NY, NZ)."""
     import torch
 
-    for t in (u, b1, b2, b3, out):
-        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
-            raise ValueError("totals_noalloc takes contiguous float64 CUDA tensors")
-    nz, ny, nx = u.shape[1:]
+    for name, t in (("u", u), ("b1", b1), ("b2", b2), ("b3", b3), ("out", out)):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError("totals_noalloc: %s must be a torch tensor" % name)
+    if u.dim() != 4 or u.shape[0] != 5:
+        raise ValueError("totals_noalloc: u must have shape (5, NZ, NY, NX), got %s" % (tuple(u.shape),))
+    nz, ny, nx = (int(v) for v in u.shape[1:])
+    want = {"b1": (nz, ny, nx + 1), "b2": (nz, ny + 1, nx), "b3": (nz + 1, ny, nx)}
+    for name, t in (("b1", b1), ("b2", b2), ("b3", b3)):
+        if tuple(t.shape) != want[name]:
+            raise ValueError("totals_noalloc: %s must have shape %s, got %s" % (name, want[name], tuple(t.shape)))
+    if out.numel() < 8:
+        raise ValueError("totals_noalloc: out must hold at least 8 doubles")
+    for name, t in (("u", u), ("b1", b1), ("b2", b2), ("b3", b3), ("out", out)):
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+            raise ValueError("totals_noalloc: %s must be a contiguous float64 CUDA tensor" % name)
+    if len({t.device for t in (u, b1, b2, b3, out)}) != 1:
+        raise ValueError("totals_noalloc: all tensors must be on one device")
+    return nx, ny, nz
+
+
+def totals_noalloc(u, b1, b2, b3, dx, out, stream=None):
+    """vl2_totals_noalloc on device tensors u [5][NZ][NY][NX], b1, b2, b3 (global layout) into the device
+    tensor out (8 doubles), enqueued on `stream` (default: the current torch stream of u's device), with u's
+    device current.  Allocates nothing."""
+    import torch
+
+    nx, ny, nz = _noalloc_args(u, b1, b2, b3, out)
     dims = (ctypes.c_int * 3)(nx, ny, nz)
     h = (ctypes.c_double * 3)(*dx)
-    st = (stream or torch.cuda.current_stream(u.device)).cuda_stream
-    _check(load().vl2_totals_noalloc(*[ctypes.c_void_p(t.data_ptr()) for t in (u, b1, b2, b3)], dims, h,
-                                     ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st)))
+    with torch.cuda.device(u.device):
+        st = (stream or torch.cuda.current_stream(u.device)).cuda_stream
+        _check(load().vl2_totals_noalloc(*[ctypes.c_void_p(t.data_ptr()) for t in (u, b1, b2, b3)], dims, h,
+                                         ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st)))
     return out
 
 

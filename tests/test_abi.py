@@ -96,3 +96,27 @@ def test_full_size_workspace_fits_one_gb300(lib):
     assert n.value < 20e9
     assert lib.vl2_workspace_bytes(ctypes.byref(_params(nx=(512,) * 3, mb=(32,) * 3)), ctypes.byref(n)) == 0
     assert n.value < 200e9
+
+
+def test_totals_noalloc_binding_rejects_mis_shaped_tensors():
+    """The binding checks every shape before anything reaches the device (a wrong shape would make the kernel
+    read past a buffer); CPU tensors of the right shapes stop at the CUDA check."""
+    import torch
+
+    from paper_2005_06651_gb300 import vl2
+
+    nz, ny, nx = 4, 3, 5
+    f64 = torch.float64
+    u = torch.zeros((5, nz, ny, nx), dtype=f64)
+    b1, b2, b3 = (torch.zeros(s, dtype=f64) for s in ((nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)))
+    out = torch.zeros(8, dtype=f64)
+    with pytest.raises(ValueError, match="b1 must have shape"):
+        vl2.totals_noalloc(u, torch.zeros((nz, ny, nx), dtype=f64), b2, b3, (1.0, 1.0, 1.0), out)
+    with pytest.raises(ValueError, match="b3 must have shape"):
+        vl2.totals_noalloc(u, b1, b2, torch.zeros((nz, ny, nx), dtype=f64), (1.0, 1.0, 1.0), out)
+    with pytest.raises(ValueError, match="u must have shape"):
+        vl2.totals_noalloc(u[:4], b1, b2, b3, (1.0, 1.0, 1.0), out)
+    with pytest.raises(ValueError, match="at least 8"):
+        vl2.totals_noalloc(u, b1, b2, b3, (1.0, 1.0, 1.0), torch.zeros(7, dtype=f64))
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        vl2.totals_noalloc(u, b1, b2, b3, (1.0, 1.0, 1.0), out)

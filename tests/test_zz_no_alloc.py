@@ -49,8 +49,15 @@ def test_totals_noalloc_matches_totals_on_two_calls(vl2):
         ref = mesh.totals()
         u, b1, b2, b3 = device_state(mesh)
         out = torch.full((8,), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        before = (torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0])
         vl2.totals_noalloc(u, b1, b2, b3, dx, out)
         torch.cuda.synchronize()
+        after = (torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0])
+        if call == 1:
+            # the first call loaded the module and looked up the scratch; the second must leave both the torch
+            # allocator and the device's free memory exactly as they were
+            assert after == before, (before, after)
         got = out.cpu().numpy()
         if scale is None:
             scale = np.array([abs(ref[0])] + [abs(ref[4])] * 4 + [1.0] * 3)
