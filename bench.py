@@ -14,8 +14,10 @@ Printed JSON line (rank 0):
               (set_prims) and reads the new state back to pinned host memory (get_cons)
   roofline    the dominant kernel (largest device time in the timed region): achieved FP64 FLOP/s =
               algorithmic FP64 operations per face (counted with the oracle's operation-counting scalar:
-              add/sub, mul, div, sqrt each one) x faces per launch / event-timed launch duration, against
-              the FP64 peak derived from 152 SMs x 2 FP64 FMA per clock x 2 FLOP x 2.07 GHz
+              add/sub, mul, div, sqrt each one) x the method's faces per launch ((mb+1) mb^2 per MeshBlock)
+              / event-timed launch duration, against the FP64 FMA throughput measured on the same GPU by
+              vl2_debug_fp64_peak (the figure derived from 152 SMs x 2 FP64 FMA per clock x 2 FLOP x
+              2.07 GHz is printed beside it)
   hbm         320 algorithmic bytes per zone-cycle (8 doubles read+written in the predictor, a stencil
               read, a base read and a write of 8 doubles in the corrector) x value / measured HBM copy
               bandwidth
@@ -720,20 +722,29 @@ def main():
     ms_step = ms_total / args.steps
     value = whole_job_rate(prob.ncells, args.steps, ms_total / 1e3, world)
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel, against the FP64 peak measured on this GPU right after the timed region
     kinds = {k: v for k, v in prof.items() if v[1] > 0}
     tot = sum(v[0] for v in kinds.values())
     dom = max(kinds, key=lambda k: kinds[k][0])
     dms, dn, dunits = kinds[dom]
     rec = {"flux_plm": "plm", "flux_dc": "dc"}.get(dom)
-    roofline = {"kernel": dom, "bound": "alu", "unit": "TFLOP/s", "peak": round(FP64_PEAK_TFLOPS, 4),
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2.07 GHz",
-                "launches": dn, "ms_per_launch": dms / dn, "units_per_launch": dunits / dn}
+    sampler2 = ClockSampler(gpu_id)
+    sampler2.start()
+    time.sleep(0.3)
+    pk = vl2.fp64_peak(dev)
+    pk_clocks = sampler2.stop()
+    roofline = {"kernel": dom, "bound": "alu", "unit": "TFLOP/s", "peak": pk["tflops"],
+                "peak_source": "measured: vl2_debug_fp64_peak, %d CTAs x %d threads x 16 independent FMA chains, "
+                               "best of 5 event-timed launches of %.0f ms" % (pk["ctas"], pk["threads"], pk["ms"]),
+                "peak_clocks": pk_clocks, "peak_derived": round(FP64_PEAK_TFLOPS, 4),
+                "launches": dn, "ms_per_launch": dms / dn, "kernel_units_per_launch": dunits / dn}
     if rec:
         fpu = FLOPS_PER_FACE[(rec, "hlld")]
-        achieved = fpu * (dunits / dn) / (dms / dn / 1e3) / 1e12
-        roofline.update({"achieved": achieved, "frac": achieved / FP64_PEAK_TFLOPS,
-                         "flops_per_unit": fpu, "unit_kind": "face"})
+        # the method's faces: (mb + 1) mb^2 per MeshBlock and sweep direction (both block-surface faces counted)
+        faces = (prob.ncells // args.mb ** 3) * (args.mb + 1) * args.mb ** 2
+        achieved = fpu * faces / (dms / dn / 1e3) / 1e12
+        roofline.update({"achieved": achieved, "frac": achieved / pk["tflops"], "flops_per_unit": fpu,
+                         "unit_kind": "face", "units_per_launch": faces})
         if NCU_TRAFFIC["hash"] == flux_source_hash() and NCU_TRAFFIC["bytes_per_face"]:
             roofline["traffic"] = NCU_TRAFFIC["bytes_per_face"] * dunits / dn
         else:

@@ -241,6 +241,33 @@ vl2_status vl2_debug_riemann_vjp(int riemann, long long n, const double* wl, con
  * lam_w = [5][N] (device).  Errors: VL2_E_ARG, VL2_E_CUDA. */
 vl2_status vl2_prims_vjp(vl2_mesh* mesh, const double* w, const double* lam_u, double* lam_w);
 
+/* Measurement aid (the paper has no counterpart): enqueue on `stream` one launch of `ctas` CTAs of
+ * `threads` threads (32..256, a multiple of 32), each thread running 16 independent chains of `iters`
+ * FP64 fused multiply-adds: 2 * 16 * iters * ctas * threads FP64 operations, with no memory traffic.
+ * The caller times it (CUDA events on the same stream) to measure the FP64 peak that the roofline of the
+ * FP64-bound kernels is stated against.  out: one device double, written only if the chains reach a
+ * value they never reach (it keeps the arithmetic live).  Errors: VL2_E_ARG, VL2_E_CUDA. */
+vl2_status vl2_debug_fp64_peak(long long iters, int ctas, int threads, double* out, void* stream);
+
+/* Functions of vl2_debug_arith: this library's FP64 forms (Newton-refined reciprocal, reciprocal square
+ * root and square root, and the variants that take any non-negative or non-zero input), its integer-pipe
+ * conversions (double -> float rounded to nearest even, float -> double), and CUDA's own operations for
+ * comparison (IEEE 1/x and sqrt, CUDA rsqrt, __double2float_rn). */
+enum {
+  VL2_AR_RCP_NR = 0, VL2_AR_RSQRT_NR = 1, VL2_AR_SQRT_NR = 2, VL2_AR_INV_ANY = 3, VL2_AR_ROOT_ANY = 4,
+  VL2_AR_RROOT_ANY = 5, VL2_AR_TO_F32 = 6, VL2_AR_TO_F64 = 7, VL2_AR_IEEE_RCP = 8, VL2_AR_IEEE_SQRT = 9,
+  VL2_AR_CUDA_RSQRT = 10, VL2_AR_CUDA_D2F = 11, VL2_AR_COUNT = 12
+};
+
+/* Test aid (the paper has no counterpart): out[i] = fn(x[i]) for i < n on the device, x and out device arrays
+ * of n doubles owned by the caller; float results are returned widened exactly to double, and
+ * VL2_AR_TO_F64 takes inputs that are floats (it converts (float)x[i]).  Domains of the Newton forms:
+ * VL2_AR_RCP_NR needs 2^-1022 <= |x| < 2^1021 (near 2^1022 and above, the hardware seed flushes and
+ * the result is 0); VL2_AR_RSQRT_NR and VL2_AR_SQRT_NR need normal x > 0 (SQRT_NR also takes +0); the _ANY variants
+ * take every finite input of their domain.  Enqueued on `stream`; the call does not wait.
+ * Errors: VL2_E_ARG (fn out of range, n < 0, NULL array), VL2_E_CUDA. */
+vl2_status vl2_debug_arith(int fn, long long n, const double* x, double* out, void* stream);
+
 /* Kernel kinds of vl2_profile_read. */
 enum {
   VL2_K_PRIM = 0,     /* cons -> prim on every cell (with the fused CFL reduction after a cycle) */

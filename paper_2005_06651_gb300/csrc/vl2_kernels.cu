@@ -89,8 +89,12 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
       double* Cb = V.a.cs + (long long)b * g.ns * g.box + c;
       for (int q = 0; q < g.ns; ++q) {
         const double sq = Sb[(long long)q * g.box];
+#ifndef VL2_VALUE_SAFE
         const double c0 = sq * id;
         Cb[(long long)q * g.box] = fma(fma(-d, c0, sq), id, c0);
+#else
+        Cb[(long long)q * g.box] = sq / d;
+#endif
       }
     }
     TW* Wb = static_cast<TW*>(V.a.w) + (long long)b * 8 * g.box + c;

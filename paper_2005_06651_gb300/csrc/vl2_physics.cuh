@@ -14,10 +14,13 @@ namespace vl2 {
 // are refined by one cubically convergent Newton step (Newton's method on 1/r - b and on 1/y^2 - x, in the
 // series form given by Markstein and in Muller et al., Handbook of Floating-Point Arithmetic):
 //   r ~ 1/b,       e = 1 - b r:        1/b      = r (1 + e + e^2 + ...)
-//   y ~ x^(-1/2),  h = 1 - x y^2:      x^(-1/2) = y (1 + h/2 + 3 h^2/8 + ...)
-// The remaining relative error is O(1e-18) plus the rounding of the last steps: within about one ulp of
-// the correctly rounded result, not always equal to it.  Inputs are finite normal numbers (no denormals);
-// sqrt_nr also takes +0 and returns +0.  Other scalar types (float, dual numbers) use their own / and sqrt.
+//   y ~ x^(-1/2),  h = 1 - x y^2:      x^(-1/2) = y (1 + h/2 + 3 h^2/8 + ...),  x^(1/2) = x y (1 + h/2 + ...)
+// The remaining relative error is O(1e-18) plus the rounding of the last steps: within one ulp of the
+// correctly rounded result, not always equal to it (bounded by a test against IEEE results).  Inputs are
+// finite normal numbers (no denormals), and rcp_nr needs |b| < 2^1021 (its seed flushes to 0 where 1/b is
+// near or below the smallest normal, and the result is then 0); sqrt_nr also takes +0 and returns +0.
+// Other scalar types (float, dual numbers) use their own / and sqrt.
+#ifndef VL2_VALUE_SAFE
 __device__ __forceinline__ double rcp_nr(double b) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
@@ -30,13 +33,25 @@ __device__ __forceinline__ double rsqrt_nr(double x) {  // x a positive normal n
   const double h = fma(-(x * y), y, 1.0);
   return fma(y * h, fma(0.375, h, 0.5), y);
 }
+// sqrt(x) = s (1 - h)^(-1/2) with s = x y rounded and h = 1 - s y: the series is applied to s itself, so the
+// rounding of s enters only through h (half of it survives) and the result is within one ulp.
 __device__ __forceinline__ double sqrt_nr(double x) {
   double y;
   asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  const double h = fma(-(x * y), y, 1.0);
-  const double s = x * fma(y * h, fma(0.375, h, 0.5), y);
-  return (__double_as_longlong(x) << 1) == 0 ? x : s;
+  const double s = x * y;
+  const double h = fma(-s, y, 1.0);
+  const double r = fma(s * h, fma(0.375, h, 0.5), s);
+  return (__double_as_longlong(x) << 1) == 0 ? x : r;
 }
+#else
+// Value-safe build (VL2_VALUE_SAFE, compiled with -fmad=false): the IEEE division and square root, each
+// correctly rounded, and no contraction anywhere, so that every expression written symmetrically in its
+// left and right operands gives bitwise mirror-symmetric results (Sec. 3.3.5 asks for value-safe arithmetic
+// where symmetric solutions must stay symmetric).
+__device__ __forceinline__ double rcp_nr(double b) { return 1.0 / b; }
+__device__ __forceinline__ double rsqrt_nr(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ double sqrt_nr(double x) { return sqrt(x); }
+#endif
 // Products rounded on their own (never contracted into an FMA with a following add).  Used where two
 // products cancel exactly for mirror-image states, so that the difference is exactly zero there (an FMA
 // would leave the rounding error of one product): the contact speed S_M and the mass flux of a
@@ -51,12 +66,15 @@ template <class R> __device__ __forceinline__ R root(R x) { return sqrt(x); }
 template <> __device__ __forceinline__ double root<double>(double x) { return sqrt_nr(x); }
 template <class R> __device__ __forceinline__ R rroot(R x) { return rsqrt(x); }
 template <> __device__ __forceinline__ double rroot<double>(double x) { return rsqrt_nr(x); }
-// The same for inputs that may be zero or denormal (the Newton forms take normal numbers only): those
-// take the IEEE operation.
+// The same for any input of the operation's domain: the Newton forms take normal numbers only, and the
+// reciprocal seed (.ftz) flushes to 0 where it would be subnormal, which |x| close to or above 2^1022 can
+// give; inputs outside [2^-1022, 2^1021) take the IEEE operation.
 constexpr double DBL_NORMAL_MIN = 2.2250738585072014e-308;
+constexpr double RCP_NR_MAX = 0x1p1021;  // rcp_nr is used on 2^-1022 <= |x| < 2^1021
 template <class R> __device__ __forceinline__ R inv_any(R x) { return R(1) / x; }
 template <> __device__ __forceinline__ double inv_any<double>(double x) {
-  return fabs(x) >= DBL_NORMAL_MIN ? rcp_nr(x) : 1.0 / x;
+  const double a = fabs(x);
+  return (a >= DBL_NORMAL_MIN && a < RCP_NR_MAX) ? rcp_nr(x) : 1.0 / x;
 }
 template <class R> __device__ __forceinline__ R root_any(R x) { return sqrt(x); }
 template <> __device__ __forceinline__ double root_any<double>(double x) {

@@ -16,6 +16,8 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libvl2mhd.so")
+# the value-safe parity build of the same sources (IEEE division and square root, no FMA contraction)
+LIB_PATH_VALUE_SAFE = os.path.join(HERE, "_build", "libvl2mhd_vs.so")
 
 VL2_OK, VL2_E_ARG, VL2_E_CUDA, VL2_E_NONPHYS, VL2_E_TIMEOUT, VL2_E_STATE, VL2_E_NOMEM = range(7)
 HLLE, HLLD, HLLE_ROE = 0, 1, 2
@@ -51,14 +53,15 @@ class Layout(ctypes.Structure):
                 ("neighbor", ctypes.POINTER(ctypes.c_int)), ("u", ctypes.c_void_p), ("b", ctypes.c_void_p * 3)]
 
 
-_lib = None
+_libs = {}
 EXPORTS = ["vl2_workspace_bytes", "vl2_mesh_create", "vl2_mesh_destroy", "vl2_block_layout", "vl2_set_prims",
            "vl2_fill_ghosts", "vl2_step", "vl2_new_dt", "vl2_get_cons", "vl2_get_prims", "vl2_divb_norm",
            "vl2_totals", "vl2_floor_count", "vl2_debug_fluxes", "vl2_debug_emfs", "vl2_profile",
            "vl2_profile_read", "vl2_launch_count", "vl2_totals_noalloc", "vl2_batch_workspace_bytes",
            "vl2_batch_create", "vl2_batch_destroy", "vl2_batch_autotune", "vl2_batch_step", "vl2_batch_run",
            "vl2_batch_launch_count", "vl2_batch_last_error", "vl2_set_cons", "vl2_step_vjp", "vl2_prims_vjp",
-           "vl2_debug_riemann_vjp", "vl2_last_error", "vl2_set_scalars", "vl2_get_scalars"]
+           "vl2_debug_riemann_vjp", "vl2_last_error", "vl2_set_scalars", "vl2_get_scalars", "vl2_debug_fp64_peak",
+           "vl2_debug_arith"]
 NOALLOC_MAX_NZ = 4096
 K_PRIM, K_GHOSTS, K_FLUX_DC, K_FLUX_PLM, K_EMF, K_UPDATE, K_FLUX_PPM, K_SCALARS = range(8)
 KERNEL_KINDS = {K_PRIM: "prim", K_GHOSTS: "ghosts", K_FLUX_DC: "flux_dc", K_FLUX_PLM: "flux_plm", K_EMF: "emf",
@@ -66,12 +69,13 @@ KERNEL_KINDS = {K_PRIM: "prim", K_GHOSTS: "ghosts", K_FLUX_DC: "flux_dc", K_FLUX
 
 
 def load(path: str = LIB_PATH):
-    """Load libvl2mhd.so (raises if it has not been built: there is no fallback path)."""
-    global _lib
-    if _lib is not None:
-        return _lib
+    """Load libvl2mhd.so, or another build of it such as the value-safe one (raises if it has not been built:
+    there is no fallback path).  Each build is opened once, in its own symbol namespace."""
+    path = os.path.abspath(path)
+    if path in _libs:
+        return _libs[path]
     if not os.path.exists(path):
-        raise RuntimeError("libvl2mhd.so not found at %s; build it with paper_2005_06651_gb300.build.build()" % path)
+        raise RuntimeError("%s not found; build it with paper_2005_06651_gb300.build.build()" % path)
     L = ctypes.CDLL(path)
     vp, dp, sz = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t
     L.vl2_workspace_bytes.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]
@@ -99,6 +103,8 @@ def load(path: str = LIB_PATH):
     L.vl2_step_vjp.argtypes = [vp, ctypes.c_double] + [dp] * 8
     L.vl2_prims_vjp.argtypes = [vp, dp, dp, dp]
     L.vl2_debug_riemann_vjp.argtypes = [ctypes.c_int, ctypes.c_longlong, dp, dp, dp, dp, ctypes.c_double, dp, vp]
+    L.vl2_debug_fp64_peak.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, dp, vp]
+    L.vl2_debug_arith.argtypes = [ctypes.c_int, ctypes.c_longlong, dp, dp, vp]
     L.vl2_batch_workspace_bytes.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.vl2_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, vp, sz, ctypes.POINTER(ctypes.c_void_p)]
     L.vl2_batch_destroy.argtypes = [vp]
@@ -113,13 +119,13 @@ def load(path: str = LIB_PATH):
     for name in EXPORTS:
         if name not in ("vl2_last_error", "vl2_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
-    _lib = L
+    _libs[path] = L
     return L
 
 
-def _check(status, mesh_handle=None, allow=()):
+def _check(status, mesh_handle=None, allow=(), lib=None):
     if status != VL2_OK and status not in allow:
-        msg = load().vl2_last_error(mesh_handle)
+        msg = (lib or load()).vl2_last_error(mesh_handle)
         raise VL2Error(status, msg.decode() if msg else "")
     return status
 
@@ -153,10 +159,13 @@ class Mesh:
 
     def __init__(self, nx, mb, xmin=(0.0, 0.0, 0.0), xmax=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, cfl=0.3,
                  riemann=HLLD, bc=(PERIODIC,) * 6, dfloor=1e-12, pfloor=1e-12, precision=FP64, device=None,
-                 stream=None, adjoint=False, integrator=VL2, recon=PLM, ng=None, nscalars=0, ct_delta=0.0):
+                 stream=None, adjoint=False, integrator=VL2, recon=PLM, ng=None, nscalars=0, ct_delta=0.0,
+                 value_safe=False):
         import torch
 
-        L = load()
+        L = load(LIB_PATH_VALUE_SAFE if value_safe else LIB_PATH)
+        self._L = L
+        self.value_safe = bool(value_safe)
         self.nx, self.mb = tuple(int(v) for v in nx), tuple(int(v) for v in mb)
         self.xmin, self.xmax = tuple(float(v) for v in xmin), tuple(float(v) for v in xmax)
         self.gamma, self.cfl = float(gamma), float(cfl)
@@ -183,14 +192,14 @@ class Mesh:
         p.integrator = int(integrator)
         self._params = p
         nbytes = ctypes.c_size_t()
-        _check(L.vl2_workspace_bytes(ctypes.byref(p), ctypes.byref(nbytes)))
+        _check(L.vl2_workspace_bytes(ctypes.byref(p), ctypes.byref(nbytes)), lib=L)
         self.workspace_bytes = int(nbytes.value)
         self._ws = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
         base = self._ws.data_ptr()
         aligned = (base + 255) & ~255
         h = ctypes.c_void_p()
         _check(L.vl2_mesh_create(ctypes.byref(p), ctypes.c_void_p(aligned), ctypes.c_size_t(self.workspace_bytes),
-                                 ctypes.byref(h)))
+                                 ctypes.byref(h)), lib=L)
         self._h = h
 
     @classmethod
@@ -202,7 +211,7 @@ class Mesh:
     def close(self):
         h = getattr(self, "_h", None)
         if h is not None and h.value:
-            load().vl2_mesh_destroy(h)
+            self._L.vl2_mesh_destroy(h)
             self._h = None
 
     def __del__(self):
@@ -229,25 +238,25 @@ class Mesh:
         keep = [np.ascontiguousarray(x, dtype=np.float64) if isinstance(x, np.ndarray) else x for x in (w, b1, b2, b3)]
         ptrs = [_ptr(x) for x in keep]
         where = _where_of(ptrs)
-        _check(load().vl2_set_prims(self._h, *[ctypes.c_void_p(p) for p, _ in ptrs], where), self._h)
+        _check(self._L.vl2_set_prims(self._h, *[ctypes.c_void_p(p) for p, _ in ptrs], where), self._h, lib=self._L)
 
     def set_scalars(self, c):
         """Concentrations c (nscalars, NZ, NY, NX), host array or CUDA tensor; set the state first."""
         keep = np.ascontiguousarray(c, dtype=np.float64) if isinstance(c, np.ndarray) else c
         ptr, where = _ptr(keep)
-        _check(load().vl2_set_scalars(self._h, ctypes.c_void_p(ptr), where), self._h)
+        _check(self._L.vl2_set_scalars(self._h, ctypes.c_void_p(ptr), where), self._h, lib=self._L)
 
     def get_scalars(self):
         """Scalar masses rho C, (nscalars, NZ, NY, NX)."""
         out = np.empty((self.nscalars,) + self.shape)
-        _check(load().vl2_get_scalars(self._h, ctypes.c_void_p(out.ctypes.data), HOST), self._h)
+        _check(self._L.vl2_get_scalars(self._h, ctypes.c_void_p(out.ctypes.data), HOST), self._h, lib=self._L)
         return out
 
     def set_cons(self, u, b1, b2, b3):
         keep = [np.ascontiguousarray(x, dtype=np.float64) if isinstance(x, np.ndarray) else x for x in (u, b1, b2, b3)]
         ptrs = [_ptr(x) for x in keep]
         where = _where_of(ptrs)
-        _check(load().vl2_set_cons(self._h, *[ctypes.c_void_p(p) for p, _ in ptrs], where), self._h)
+        _check(self._L.vl2_set_cons(self._h, *[ctypes.c_void_p(p) for p, _ in ptrs], where), self._h, lib=self._L)
 
     def step_vjp(self, dt, lam, out=None):
         """J^T lam for one cycle of step dt at the current state; lam/out = (u, b1, b2, b3) CUDA tensors."""
@@ -258,8 +267,8 @@ class Mesh:
         for t in tuple(lam) + tuple(out):
             if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
                 raise ValueError("step_vjp takes contiguous float64 CUDA tensors")
-        _check(load().vl2_step_vjp(self._h, float(dt), *[ctypes.c_void_p(t.data_ptr()) for t in lam],
-                                   *[ctypes.c_void_p(t.data_ptr()) for t in out]), self._h)
+        _check(self._L.vl2_step_vjp(self._h, float(dt), *[ctypes.c_void_p(t.data_ptr()) for t in lam],
+                                   *[ctypes.c_void_p(t.data_ptr()) for t in out]), self._h, lib=self._L)
         return out
 
     def prims_vjp(self, w, lam_u, out=None):
@@ -267,19 +276,20 @@ class Mesh:
 
         if out is None:
             out = torch.empty_like(lam_u)
-        _check(load().vl2_prims_vjp(self._h, ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(lam_u.data_ptr()),
-                                    ctypes.c_void_p(out.data_ptr())), self._h)
+        _check(self._L.vl2_prims_vjp(self._h, ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(lam_u.data_ptr()),
+                                    ctypes.c_void_p(out.data_ptr())), self._h, lib=self._L)
         return out
 
     def fill_ghosts(self):
-        _check(load().vl2_fill_ghosts(self._h), self._h)
+        _check(self._L.vl2_fill_ghosts(self._h), self._h, lib=self._L)
 
     def step(self, dt):
-        _check(load().vl2_step(self._h, float(dt)), self._h)
+        _check(self._L.vl2_step(self._h, float(dt)), self._h, lib=self._L)
 
     def new_dt(self, allow_nonphys=False):
         out = ctypes.c_double()
-        _check(load().vl2_new_dt(self._h, ctypes.byref(out)), self._h, allow=(VL2_E_NONPHYS,) if allow_nonphys else ())
+        _check(self._L.vl2_new_dt(self._h, ctypes.byref(out)), self._h, allow=(VL2_E_NONPHYS,) if allow_nonphys else (),
+               lib=self._L)
         return out.value
 
     def get_cons(self, out=None):
@@ -288,34 +298,34 @@ class Mesh:
             out = (np.empty((5,) + self.shape), *[np.empty(s) for s in self.face_shapes()])
         ptrs = [_ptr(x) for x in out]
         where = _where_of(ptrs)
-        _check(load().vl2_get_cons(self._h, *[ctypes.c_void_p(p) if p else None for p, _ in ptrs], where), self._h)
+        _check(self._L.vl2_get_cons(self._h, *[ctypes.c_void_p(p) if p else None for p, _ in ptrs], where), self._h, lib=self._L)
         return out
 
     def get_prims(self, out=None):
         if out is None:
             out = np.empty((8,) + self.shape)
         p, where = _ptr(out)
-        _check(load().vl2_get_prims(self._h, ctypes.c_void_p(p), where), self._h)
+        _check(self._L.vl2_get_prims(self._h, ctypes.c_void_p(p), where), self._h, lib=self._L)
         return out
 
     def divb_norm(self):
         out = ctypes.c_double()
-        _check(load().vl2_divb_norm(self._h, ctypes.byref(out)), self._h)
+        _check(self._L.vl2_divb_norm(self._h, ctypes.byref(out)), self._h, lib=self._L)
         return out.value
 
     def totals(self):
         out = (ctypes.c_double * 8)()
-        _check(load().vl2_totals(self._h, out), self._h)
+        _check(self._L.vl2_totals(self._h, out), self._h, lib=self._L)
         return np.array(out[:])
 
     def floor_count(self):
         out = ctypes.c_longlong()
-        _check(load().vl2_floor_count(self._h, ctypes.byref(out)), self._h)
+        _check(self._L.vl2_floor_count(self._h, ctypes.byref(out)), self._h, lib=self._L)
         return out.value
 
     def block_layout(self):
         lay = Layout()
-        _check(load().vl2_block_layout(self._h, ctypes.byref(lay)), self._h)
+        _check(self._L.vl2_block_layout(self._h, ctypes.byref(lay)), self._h, lib=self._L)
         n = lay.nblocks
         return {"nblocks": n, "nb": tuple(lay.nb), "mb": tuple(lay.mb), "ng": lay.ng,
                 "strides": (lay.sx, lay.sy, lay.sz), "block_stride_vars": lay.block_stride_vars,
@@ -324,34 +334,34 @@ class Mesh:
                 "u": lay.u, "b": tuple(lay.b)}
 
     def profile(self, enable=True):
-        _check(load().vl2_profile(self._h, int(bool(enable))), self._h)
+        _check(self._L.vl2_profile(self._h, int(bool(enable))), self._h, lib=self._L)
 
     def profile_read(self):
         """{kind: (ms, launches, units)} accumulated since the last read (resets)."""
         out = {}
         for k, name in KERNEL_KINDS.items():
             ms, n, u = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
-            _check(load().vl2_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(u)), self._h)
+            _check(self._L.vl2_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(u)), self._h, lib=self._L)
             out[name] = (ms.value, n.value, u.value)
         return out
 
     def launch_count(self):
         n = ctypes.c_longlong()
-        _check(load().vl2_launch_count(self._h, ctypes.byref(n)), self._h)
+        _check(self._L.vl2_launch_count(self._h, ctypes.byref(n)), self._h, lib=self._L)
         return n.value
 
     def debug_fluxes(self, recon):
         NX, NY, NZ = self.nx
         fx, fy, fz = np.empty((7, NZ, NY, NX + 1)), np.empty((7, NZ, NY + 1, NX)), np.empty((7, NZ + 1, NY, NX))
-        _check(load().vl2_debug_fluxes(self._h, int(recon), *[ctypes.c_void_p(a.ctypes.data) for a in (fx, fy, fz)],
-                                       HOST), self._h)
+        _check(self._L.vl2_debug_fluxes(self._h, int(recon), *[ctypes.c_void_p(a.ctypes.data) for a in (fx, fy, fz)],
+                                       HOST), self._h, lib=self._L)
         return fx, fy, fz
 
     def debug_emfs(self, recon):
         NX, NY, NZ = self.nx
         e1, e2, e3 = np.empty((NZ + 1, NY + 1, NX)), np.empty((NZ + 1, NY, NX + 1)), np.empty((NZ, NY + 1, NX + 1))
-        _check(load().vl2_debug_emfs(self._h, int(recon), *[ctypes.c_void_p(a.ctypes.data) for a in (e1, e2, e3)],
-                                     HOST), self._h)
+        _check(self._L.vl2_debug_emfs(self._h, int(recon), *[ctypes.c_void_p(a.ctypes.data) for a in (e1, e2, e3)],
+                                     HOST), self._h, lib=self._L)
         return e1, e2, e3
 
     def run(self, t_end, max_steps=1_000_000):
@@ -425,9 +435,55 @@ def debug_riemann_vjp(riemann, wl, wr, bn, lf, gamma, stream=None):
     return out
 
 
-def _bcheck(status, handle=None):
+AR_RCP_NR, AR_RSQRT_NR, AR_SQRT_NR, AR_INV_ANY, AR_ROOT_ANY, AR_RROOT_ANY, AR_TO_F32, AR_TO_F64, AR_IEEE_RCP, \
+    AR_IEEE_SQRT, AR_CUDA_RSQRT, AR_CUDA_D2F = range(12)
+
+
+def debug_arith(fn, x, stream=None):
+    """vl2_debug_arith on a contiguous float64 CUDA tensor x: returns fn(x) as a new float64 tensor."""
+    import torch
+
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise ValueError("debug_arith takes a contiguous float64 CUDA tensor")
+    out = torch.empty_like(x)
+    with torch.cuda.device(x.device):
+        st = (stream or torch.cuda.current_stream(x.device)).cuda_stream
+        _check(load().vl2_debug_arith(int(fn), x.numel(), ctypes.c_void_p(x.data_ptr()),
+                                      ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st)))
+    return out
+
+
+def fp64_peak(device=None, iters=1 << 16, ctas=None, threads=256, repeats=5):
+    """Measured FP64 peak (TFLOP/s): the best of `repeats` event-timed launches of vl2_debug_fp64_peak, each
+    2 * 16 * iters * ctas * threads FP64 operations (fused multiply-adds count 2).  ctas defaults to 8 per SM."""
+    import torch
+
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    with torch.cuda.device(dev):
+        props = torch.cuda.get_device_properties(dev)
+        ctas = ctas or 8 * props.multi_processor_count
+        out = torch.zeros(1, dtype=torch.float64, device=dev)
+        st = torch.cuda.current_stream(dev)
+        L = load()
+        _check(L.vl2_debug_fp64_peak(int(iters) // 16, int(ctas), int(threads), ctypes.c_void_p(out.data_ptr()),
+                                     ctypes.c_void_p(st.cuda_stream)))  # warm-up
+        best = None
+        for _ in range(repeats):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _check(L.vl2_debug_fp64_peak(int(iters), int(ctas), int(threads), ctypes.c_void_p(out.data_ptr()),
+                                         ctypes.c_void_p(st.cuda_stream)))
+            e1.record(st)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+    flops = 2.0 * 16 * iters * ctas * threads
+    return {"tflops": flops / (best / 1e3) / 1e12, "ms": best, "flops": flops, "ctas": ctas, "threads": threads}
+
+
+def _bcheck(status, handle=None, lib=None):
     if status != VL2_OK:
-        msg = load().vl2_batch_last_error(handle)
+        msg = (lib or load()).vl2_batch_last_error(handle)
         raise VL2Error(status, msg.decode() if msg else "")
     return status
 
@@ -438,23 +494,25 @@ class Batch:
     def __init__(self, meshes):
         import torch
 
-        L = load()
         self.meshes = list(meshes)
+        if len({m._L._name for m in self.meshes}) > 1:
+            raise ValueError("the meshes of a batch must come from one build of the library")
+        L = self._L = self.meshes[0]._L
         arr = (ctypes.c_void_p * len(self.meshes))(*[m._h.value for m in self.meshes])
         self._arr = arr
         nbytes = ctypes.c_size_t()
-        _bcheck(L.vl2_batch_workspace_bytes(arr, len(self.meshes), ctypes.byref(nbytes)))
+        _bcheck(L.vl2_batch_workspace_bytes(arr, len(self.meshes), ctypes.byref(nbytes)), lib=L)
         dev = self.meshes[0].device
         self._ws = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=dev)
         aligned = (self._ws.data_ptr() + 255) & ~255
         h = ctypes.c_void_p()
-        _bcheck(L.vl2_batch_create(arr, len(self.meshes), ctypes.c_void_p(aligned), nbytes, ctypes.byref(h)))
+        _bcheck(L.vl2_batch_create(arr, len(self.meshes), ctypes.c_void_p(aligned), nbytes, ctypes.byref(h)), lib=L)
         self._h = h
 
     def close(self):
         h = getattr(self, "_h", None)
         if h is not None and h.value:
-            load().vl2_batch_destroy(h)
+            self._L.vl2_batch_destroy(h)
             self._h = None
 
     def __del__(self):
@@ -469,28 +527,28 @@ class Batch:
 
     def autotune(self):
         dc, pl = ctypes.c_int(), ctypes.c_int()
-        _bcheck(load().vl2_batch_autotune(self._h, ctypes.byref(dc), ctypes.byref(pl)), self._h)
+        _bcheck(self._L.vl2_batch_autotune(self._h, ctypes.byref(dc), ctypes.byref(pl)), self._h, lib=self._L)
         return dc.value, pl.value
 
     def step(self, dt):
         """One cycle with per-box steps dt (sequence of floats, or a CUDA float64 tensor)."""
         if isinstance(dt, np.ndarray) or isinstance(dt, (list, tuple)):
             a = np.ascontiguousarray(dt, dtype=np.float64)
-            _bcheck(load().vl2_batch_step(self._h, ctypes.c_void_p(a.ctypes.data), HOST), self._h)
+            _bcheck(self._L.vl2_batch_step(self._h, ctypes.c_void_p(a.ctypes.data), HOST), self._h, lib=self._L)
         else:
             p, where = _ptr(dt)
-            _bcheck(load().vl2_batch_step(self._h, ctypes.c_void_p(p), where), self._h)
+            _bcheck(self._L.vl2_batch_step(self._h, ctypes.c_void_p(p), where), self._h, lib=self._L)
 
     def run(self, nsteps, want_dt=True):
         """nsteps cycles with per-box CFL steps formed on the device, as one graph launch."""
         out = np.empty(len(self.meshes)) if want_dt else None
-        _bcheck(load().vl2_batch_run(self._h, int(nsteps), ctypes.c_void_p(out.ctypes.data) if want_dt else None),
-                self._h)
+        _bcheck(self._L.vl2_batch_run(self._h, int(nsteps), ctypes.c_void_p(out.ctypes.data) if want_dt else None),
+                self._h, lib=self._L)
         return out
 
     def launch_count(self):
         n = ctypes.c_longlong()
-        _bcheck(load().vl2_batch_launch_count(self._h, ctypes.byref(n)), self._h)
+        _bcheck(self._L.vl2_batch_launch_count(self._h, ctypes.byref(n)), self._h, lib=self._L)
         return n.value
 
 
