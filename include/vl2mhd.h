@@ -278,7 +278,10 @@ enum {
   VL2_K_UPDATE = 5,   /* register update of U and the face field (units: nodes) */
   VL2_K_FLUX_PPM = 6, /* PPM + Riemann fluxes of one sweep direction (units: faces) */
   VL2_K_SCALARS = 7,  /* passive-scalar fluxes and updates */
-  VL2_K_COUNT = 8
+  VL2_K_FLUX_HALO = 8, /* copy of the faces just outside each block's transverse range (mass flux and transverse
+                          induction fluxes, for the CT corners) from the neighbouring block that computed them,
+                          on fully periodic meshes (units: faces) */
+  VL2_K_COUNT = 9
 };
 
 /* Per-kernel timing, the measuring side of the paper's zone-cycles-per-second benchmarks (Sec. 3.4.1).

@@ -205,6 +205,8 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
     return VL2_E_ARG;
   }
   for (int f = 0; f < 6; ++f) g.bc[f] = p->bc[f];
+  g.flux_halo = 0;
+  for (int f = 0; f < 6; ++f) g.flux_halo |= p->bc[f] != VL2_PERIODIC;
   g.gamma = p->gamma;
   g.gm1 = p->gamma - 1.0;
   g.igm1 = 1.0 / (p->gamma - 1.0);
@@ -332,8 +334,14 @@ long long ghost_elems(const Geom& g) {
 }
 long long flux_faces(const Geom& g, int d) {
   long long n = g.nblk;
-  for (int q = 0; q < 3; ++q) n *= g.mb[q] + (q == d ? 1 : 2);
+  for (int q = 0; q < 3; ++q) n *= g.mb[q] + (q == d ? 1 : 2 * g.flux_halo);
   return n;
+}
+long long halo_faces(const Geom& g) {
+  if (g.flux_halo) return 0;
+  long long n = 0;
+  for (int d = 0; d < 3; ++d) n += 2LL * (g.mb[d] + 1) * (g.mb[(d + 1) % 3] + g.mb[(d + 2) % 3]);
+  return n * g.nblk;
 }
 
 cudaError_t k_prim(vl2_mesh* m, int reg, bool dt) {
@@ -352,7 +360,8 @@ cudaError_t k_fluxes(vl2_mesh* m, int reg, int recon) {
     });
     if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  if (m->g.flux_halo) return cudaSuccess;
+  return timed(m, VL2_K_FLUX_HALO, halo_faces(m->g), [&] { return vl2::launch_flux_halo(m->view(), nullptr, m->st); });
 }
 cudaError_t k_scalar_fluxes(vl2_mesh* m, int recon) {
   if (!m->g.ns) return cudaSuccess;
@@ -978,7 +987,7 @@ const char* vl2_last_error(const vl2_mesh* mesh) { return mesh ? mesh->err.c_str
  * work list; per-box CFL time steps stay on the device; K cycles are captured in one CUDA graph.
  * =========================================================================================== */
 struct vl2_batch {
-  enum { W_PRIM, W_GHOSTS, W_NODES, W_DC, W_PLM = W_DC + 3, W_COUNT = W_PLM + 3 };
+  enum { W_PRIM, W_GHOSTS, W_NODES, W_DC, W_PLM = W_DC + 3, W_HALO = W_PLM + 3, W_COUNT = W_HALO + 1 };
   std::vector<vl2_mesh*> meshes;
   int n = 0;
   cudaStream_t st = nullptr;
@@ -1036,6 +1045,7 @@ long long batch_tiles(const vl2_mesh* m, int w, const vl2::FluxShape& fs, int ma
   if (w == vl2_batch::W_PRIM) return vl2::tiles_prim(g);
   if (w == vl2_batch::W_GHOSTS) return vl2::tiles_ghosts(g);
   if (w == vl2_batch::W_NODES) return vl2::tiles_nodes(g);
+  if (w == vl2_batch::W_HALO) return vl2::tiles_flux_halo(g);
   if (w < vl2_batch::W_PLM) return vl2::tiles_flux_dc(g, w - vl2_batch::W_DC, fs);
   const int d = w - vl2_batch::W_PLM;
   vl2::FluxShape f2 = fs;
@@ -1141,7 +1151,10 @@ cudaError_t batch_fluxes(vl2_batch* B, int reg, int recon) {
     ++B->launches;
     if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  const vl2::Dispatch dh = disp(B, vl2_batch::W_HALO);
+  if (dh.nwork == 0) return cudaSuccess;
+  ++B->launches;
+  return vl2::launch_flux_halo(v0, &dh, B->cur);
 }
 
 // one VL2 cycle of every box; h = beta * dt[box] with dt in device memory.  With device_dt the cycle
@@ -1162,7 +1175,7 @@ cudaError_t batch_cycle(vl2_batch* B, bool device_dt) {
   if ((e = vl2::launch_update(v0, &dn, 0, 0, 0.0, B->ddt, 1.0, B->cur)) != cudaSuccess) return e;
   if ((e = vl2::launch_ghosts(v0, &dg, 0, B->cur)) != cudaSuccess) return e;
   if ((e = vl2::launch_prim(v0, &dp, 0, true, true, B->cur)) != cudaSuccess) return e;
-  B->launches += 11;  // plus the 6 flux launches counted in batch_fluxes
+  B->launches += 11;  // plus the 6 flux launches (and 2 halo copies) counted in batch_fluxes
   return cudaSuccess;
 }
 

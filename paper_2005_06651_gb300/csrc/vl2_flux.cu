@@ -9,8 +9,9 @@ namespace vl2 {
 
 // ------------------------------------------------------------------------------------------------
 // Predictor fluxes, one thread per face.  Faces of direction DIR cover the block's active faces along
-// DIR (ng .. ng+mb) and the active cells plus one ghost layer transversally (ng-1 .. ng+mb), which feed
-// the corner EMFs on the block surface.
+// DIR (ng .. ng+mb) and its active cells transversally (ng .. ng+mb-1); with g.flux_halo also one ghost
+// layer transversally (ng-1 .. ng+mb), whose faces feed the corner EMFs on the block surface (otherwise
+// k_flux_halo copies those from the neighbouring blocks).
 // ------------------------------------------------------------------------------------------------
 template <int DIR, int REC, int RS, class T>
 __global__ void __launch_bounds__(256) k_flux(MeshView single, const MeshView* views, const WorkItem* work, int reg) {
@@ -19,18 +20,19 @@ __global__ void __launch_bounds__(256) k_flux(MeshView single, const MeshView* v
   const MeshView& V = stage_view(sv, single, views, work, tile);
   const Geom& g = V.g;
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
-  const int rx = g.mb[0] + (DIR == 0 ? 1 : 2);
-  const int ry = g.mb[1] + (DIR == 1 ? 1 : 2);
-  const int rz = g.mb[2] + (DIR == 2 ? 1 : 2);
+  const int h = g.flux_halo;
+  const int rx = g.mb[0] + (DIR == 0 ? 1 : 2 * h);
+  const int ry = g.mb[1] + (DIR == 1 ? 1 : 2 * h);
+  const int rz = g.mb[2] + (DIR == 2 ? 1 : 2 * h);
   const long long per = (long long)rx * ry * rz;
   const long long t = (long long)tile * blockDim.x + threadIdx.x;
   if (t >= per * g.nblk) return;
   const int b = (int)(t / per);
   int rem = (int)(t - (long long)b * per);
-  const int i = rem % rx + (DIR == 0 ? g.ng : g.ng - 1);
+  const int i = rem % rx + (DIR == 0 ? g.ng : g.ng - h);
   rem /= rx;
-  const int j = rem % ry + (DIR == 1 ? g.ng : g.ng - 1);
-  const int k = rem / ry + (DIR == 2 ? g.ng : g.ng - 1);
+  const int j = rem % ry + (DIR == 1 ? g.ng : g.ng - h);
+  const int k = rem / ry + (DIR == 2 ? g.ng : g.ng - h);
   const long long c = cell_off(g, k, j, i);
   const long long sd = (DIR == 0) ? 1LL : ((DIR == 1) ? (long long)g.sx : (long long)g.sx * g.sy);
   const T* Wb = static_cast<const T*>(V.a.w) + (long long)b * 8 * g.box;
@@ -89,7 +91,8 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
   constexpr int TA = LineMap<DIR>::TA, TB = LineMap<DIR>::TB;
   const int L = g.mb[DIR] + 2;   // reconstructed cells per line
   const int NF = g.mb[DIR] + 1;  // faces per line
-  const int na = g.mb[TA] + 2, nb = g.mb[TB] + 2;
+  const int h = g.flux_halo;     // lines of the transverse halo too (see k_flux)
+  const int na = g.mb[TA] + 2 * h, nb = g.mb[TB] + 2 * h;
   const int nlines = na * nb;
   const int tiles = (nlines + P - 1) / P;
   const int b = tile_all / tiles;
@@ -115,8 +118,8 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
       if (line >= nlines) continue;
       int li[3];
       li[DIR] = g.ng - 1 + f;
-      li[TA] = g.ng - 1 + line % na;
-      li[TB] = g.ng - 1 + line / na;
+      li[TA] = g.ng - h + line % na;
+      li[TB] = g.ng - h + line / na;
       const long long o = cell_off(g, li[2], li[1], li[0]);
 #pragma unroll
       for (int n = 0; n < 7; ++n) {
@@ -133,8 +136,8 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
       if (line >= nlines) continue;
       int li[3];
       li[DIR] = g.ng - 1 + c;
-      li[TA] = g.ng - 1 + line % na;
-      li[TB] = g.ng - 1 + line / na;
+      li[TA] = g.ng - h + line % na;
+      li[TB] = g.ng - h + line / na;
       const long long o = cell_off(g, li[2], li[1], li[0]);
 #pragma unroll
       for (int n = 0; n < 7; ++n) {
@@ -154,8 +157,8 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
     if (line >= nlines) continue;
     int li[3];
     li[DIR] = g.ng - 1 + c;
-    li[TA] = g.ng - 1 + line % na;
-    li[TB] = g.ng - 1 + line / na;
+    li[TA] = g.ng - h + line % na;
+    li[TB] = g.ng - h + line / na;
     const long long o = cell_off(g, li[2], li[1], li[0]);
     T qs[5][7], lo[7], hi[7];
 #pragma unroll
@@ -179,8 +182,8 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
     if (line >= nlines) continue;
     int li[3];
     li[DIR] = g.ng - 1 + c;
-    li[TA] = g.ng - 1 + line % na;
-    li[TB] = g.ng - 1 + line / na;
+    li[TA] = g.ng - h + line % na;
+    li[TB] = g.ng - h + line / na;
     const long long o = cell_off(g, li[2], li[1], li[0]);
     T qm[7], q0[7], qp[7], lo[7], hi[7];
 #pragma unroll
@@ -205,8 +208,8 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
     if (line >= nlines) continue;
     int li[3];
     li[DIR] = g.ng - 1 + c;
-    li[TA] = g.ng - 1 + line % na;
-    li[TB] = g.ng - 1 + line / na;
+    li[TA] = g.ng - h + line % na;
+    li[TB] = g.ng - h + line / na;
     const long long o = cell_off(g, li[2], li[1], li[0]);
     {
       T q0[7], dl[7], dr[7], den[7];
@@ -243,8 +246,8 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
     if (line >= nlines) continue;
     int li[3];
     li[DIR] = g.ng + f;
-    li[TA] = g.ng - 1 + line % na;
-    li[TB] = g.ng - 1 + line / na;
+    li[TA] = g.ng - h + line % na;
+    li[TB] = g.ng - h + line / na;
     const long long o = cell_off(g, li[2], li[1], li[0]);
     T wl[7], wr[7];
 #pragma unroll
@@ -265,12 +268,103 @@ __global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const Mesh
 }
 
 // ------------------------------------------------------------------------------------------------
+// Halo faces for the CT corners on a block's surface (meshes with flux_halo = 0).  The corners of edge
+// family e read the a-faces one cell outside the block along b and the b-faces one cell outside along a
+// (a, b the directions transverse to e): the mass flux (upwind choice) and the transverse induction fluxes
+// (face EMFs).  Those faces lie in the neighbouring block's own transverse range, where the same arithmetic
+// on the same cells computed them, so they are copied: components 0, 5 and 6 of the d-faces at normal
+// index ng .. ng+mb_d on the four sides t = ng-1 / ng+mb of each transverse direction t (the other transverse
+// index over the active range; the corner lines outside both are not read).  One thread per face, with the
+// lower of the two free dimensions (memory order) fastest.
+// ------------------------------------------------------------------------------------------------
+__host__ __device__ inline long long halo_side_faces(const Geom& g, int d, int t) {
+  const int o = 3 - d - t;  // the other transverse direction
+  return (long long)(g.mb[d] + 1) * g.mb[o];
+}
+__host__ __device__ inline long long halo_faces_per_block(const Geom& g) {
+  long long n = 0;
+  for (int d = 0; d < 3; ++d) n += 2 * (halo_side_faces(g, d, (d + 1) % 3) + halo_side_faces(g, d, (d + 2) % 3));
+  return n;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_flux_halo(MeshView single, const MeshView* views, const WorkItem* work) {
+  __shared__ MeshView sv;
+  int tile;
+  const MeshView& V = stage_view(sv, single, views, work, tile);
+  const Geom& g = V.g;
+  if (g.flux_halo) return;
+  const long long per = halo_faces_per_block(g);
+  const long long t = (long long)tile * blockDim.x + threadIdx.x;
+  if (t >= per * g.nblk) return;
+  const int b = (int)(t / per);
+  long long r = t - (long long)b * per;
+  // which direction d, transverse side direction s, and lower / upper side
+  int d = 0, s = 0, hi = 0;
+  for (d = 0; d < 3; ++d) {
+    const int s1 = (d + 1) % 3, s2 = (d + 2) % 3;
+    const long long n1 = halo_side_faces(g, d, s1), n2 = halo_side_faces(g, d, s2);
+    if (r < 2 * n1) {
+      s = s1;
+      hi = (int)(r / n1);
+      r -= hi * n1;
+      break;
+    }
+    r -= 2 * n1;
+    if (r < 2 * n2) {
+      s = s2;
+      hi = (int)(r / n2);
+      r -= hi * n2;
+      break;
+    }
+    r -= 2 * n2;
+  }
+  const int o = 3 - d - s;
+  const int f0 = d < o ? d : o, f1 = d < o ? o : d;  // free dimensions, the lower one fastest
+  const int e0 = g.mb[f0] + (f0 == d ? 1 : 0);
+  int li[3], si[3];
+  li[f0] = g.ng + (int)(r % e0);
+  li[f1] = g.ng + (int)(r / e0);
+  li[s] = hi ? g.ng + g.mb[s] : g.ng - 1;
+  si[f0] = li[f0];
+  si[f1] = li[f1];
+  si[s] = hi ? g.ng : g.ng + g.mb[s] - 1;  // the same face in the neighbouring block's own range
+  // neighbouring block along s (periodic wrap; every neighbour exists on a fully periodic mesh)
+  int loc[3] = {b % g.nb[0], (b / g.nb[0]) % g.nb[1], b / (g.nb[0] * g.nb[1])};
+  loc[s] = (loc[s] + (hi ? 1 : g.nb[s] - 1)) % g.nb[s];
+  const int bs = (loc[2] * g.nb[1] + loc[1]) * g.nb[0] + loc[0];
+  T* F = static_cast<T*>(V.a.f[d]);
+  const long long dst = (long long)b * 7 * g.box + cell_off(g, li[2], li[1], li[0]);
+  const long long src = (long long)bs * 7 * g.box + cell_off(g, si[2], si[1], si[0]);
+  F[dst] = F[src];
+  F[dst + 5 * g.box] = F[src + 5 * g.box];
+  F[dst + 6 * g.box] = F[src + 6 * g.box];
+}
+
+long long tiles_flux_halo(const Geom& g) {
+  if (g.flux_halo) return 0;
+  return (halo_faces_per_block(g) * g.nblk + 255) / 256;
+}
+
+cudaError_t launch_flux_halo(const MeshView& v, const Dispatch* d, cudaStream_t st) {
+  const long long grid = d ? d->nwork : tiles_flux_halo(v.g);
+  if (grid <= 0) return cudaSuccess;
+  const MeshView* vs = d ? d->views : nullptr;
+  const WorkItem* wk = d ? d->work : nullptr;
+  if (v.a.mixed)
+    k_flux_halo<float><<<(unsigned)grid, 256, 0, st>>>(v, vs, wk);
+  else
+    k_flux_halo<double><<<(unsigned)grid, 256, 0, st>>>(v, vs, wk);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
 // launch shapes and launchers
 // ------------------------------------------------------------------------------------------------
 constexpr size_t PLM_SMEM_MAX = 112 * 1024;  // shared bytes one CTA may take (two fit in an SM)
 
-static int lines_ta(const Geom& g, int dir) { return g.mb[dir == 0 ? 1 : 0] + 2; }
-static int lines_tb(const Geom& g, int dir) { return g.mb[dir == 2 ? 1 : 2] + 2; }
+static int lines_ta(const Geom& g, int dir) { return g.mb[dir == 0 ? 1 : 0] + 2 * g.flux_halo; }
+static int lines_tb(const Geom& g, int dir) { return g.mb[dir == 2 ? 1 : 2] + 2 * g.flux_halo; }
 
 // Lines per CTA: the requested count, reduced until a CTA's shared memory fits (max_mb = the longest
 // line of any mesh sharing the launch).
@@ -290,7 +384,7 @@ int plm_lines_for(const Geom& g, int dir, const FluxShape& fs, int max_mb, int r
 
 long long tiles_flux_dc(const Geom& g, int dir, const FluxShape& fs) {
   long long n = g.nblk;
-  for (int q = 0; q < 3; ++q) n *= g.mb[q] + (q == dir ? 1 : 2);
+  for (int q = 0; q < 3; ++q) n *= g.mb[q] + (q == dir ? 1 : 2 * g.flux_halo);
   return (n + fs.dc_threads - 1) / fs.dc_threads;
 }
 

@@ -28,6 +28,12 @@ struct Geom {
   int hlle_roe;  // 1: the HLLE solver takes Einfeldt's Roe-averaged outer speeds
   double dfloor, pfloor;
   double ct_delta;     // smoothed CT upwind weight width (0: the sign switch)
+  // Faces one cell outside a block's transverse range feed the CT corners on the block surface.  1: the flux
+  // kernels compute them from the block's ghost cells (a mesh with an outflow boundary, where such a face
+  // can lie outside the mesh); 0: every block computes only its own transverse range, and k_flux_halo copies
+  // those faces' mass flux and transverse induction fluxes from the neighbouring block that owns them
+  // (periodic meshes), so each face flux is computed once per block surface.
+  int flux_halo;
 };
 
 __host__ __device__ inline long long cell_off(const Geom& g, int k, int j, int i) {
@@ -110,6 +116,7 @@ long long tiles_ghosts(const Geom& g);
 long long tiles_nodes(const Geom& g);  // EMF and update
 long long tiles_flux_dc(const Geom& g, int dir, const FluxShape& fs);
 long long tiles_flux_plm(const Geom& g, int dir, const FluxShape& fs);
+long long tiles_flux_halo(const Geom& g);  // 0 when g.flux_halo
 int plm_lines_for(const Geom& g, int dir, const FluxShape& fs, int max_mb, int recon);
 
 // ---- launchers (vl2_kernels.cu / vl2_flux.cu); all enqueue on `st`.  d == nullptr: the single mesh v.
@@ -118,6 +125,9 @@ cudaError_t launch_prim(const MeshView& v, const Dispatch* d, int reg, bool all_
 cudaError_t launch_ghosts(const MeshView& v, const Dispatch* d, int reg, cudaStream_t st);
 cudaError_t launch_flux(const MeshView& v, const Dispatch* d, int reg, int recon, int riemann, int dir,
                         const FluxShape& fs, int max_mb, cudaStream_t st);
+// copy the halo faces' mass flux and transverse induction fluxes from their owning blocks (meshes with
+// flux_halo = 0; a no-op launch-free call when no mesh of the launch needs it)
+cudaError_t launch_flux_halo(const MeshView& v, const Dispatch* d, cudaStream_t st);
 cudaError_t launch_emfs(const MeshView& v, const Dispatch* d, cudaStream_t st);
 cudaError_t launch_update(const MeshView& v, const Dispatch* d, int base_reg, int out_reg, double h,
                           const double* dtbox, double beta, cudaStream_t st, double g_base = 1.0, double g_other = 0.0);

@@ -63,9 +63,9 @@ EXPORTS = ["vl2_workspace_bytes", "vl2_mesh_create", "vl2_mesh_destroy", "vl2_bl
            "vl2_debug_riemann_vjp", "vl2_last_error", "vl2_set_scalars", "vl2_get_scalars", "vl2_debug_fp64_peak",
            "vl2_debug_arith"]
 NOALLOC_MAX_NZ = 4096
-K_PRIM, K_GHOSTS, K_FLUX_DC, K_FLUX_PLM, K_EMF, K_UPDATE, K_FLUX_PPM, K_SCALARS = range(8)
+K_PRIM, K_GHOSTS, K_FLUX_DC, K_FLUX_PLM, K_EMF, K_UPDATE, K_FLUX_PPM, K_SCALARS, K_FLUX_HALO = range(9)
 KERNEL_KINDS = {K_PRIM: "prim", K_GHOSTS: "ghosts", K_FLUX_DC: "flux_dc", K_FLUX_PLM: "flux_plm", K_EMF: "emf",
-                K_UPDATE: "update", K_FLUX_PPM: "flux_ppm", K_SCALARS: "scalars"}
+                K_UPDATE: "update", K_FLUX_PPM: "flux_ppm", K_SCALARS: "scalars", K_FLUX_HALO: "flux_halo"}
 
 
 def load(path: str = LIB_PATH):
