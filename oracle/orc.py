@@ -48,6 +48,7 @@ def lib():
                                    ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_double]
         L.orc_set_scalars.argtypes = [ctypes.c_void_p, dp]
+        L.orc_set_forcing.argtypes = [ctypes.c_void_p, dp]
         L.orc_get_scalars.argtypes = [ctypes.c_void_p, dp]
         L.orc_mesh_free.argtypes = [ctypes.c_void_p]
         L.orc_set_prims.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
@@ -300,6 +301,14 @@ class Mesh:
         """Concentrations c (nscalars, NZ, NY, NX); the state must be set first (rho C = rho c)."""
         c = _c64(np.asarray(c, dtype=np.float64).reshape((self.nscalars,) + self.shape))
         lib().orc_set_scalars(self._h, _dp(c))
+
+    def set_forcing(self, a):
+        """Forcing acceleration a (3, NZ, NY, NX) at the cell centres, or None to remove it."""
+        if a is None:
+            lib().orc_set_forcing(self._h, None)
+            return
+        self._acc = _c64(np.asarray(a, dtype=np.float64).reshape((3,) + self.shape))
+        lib().orc_set_forcing(self._h, _dp(self._acc))
 
     def get_scalars(self):
         """Scalar masses rho C, (nscalars, NZ, NY, NX)."""

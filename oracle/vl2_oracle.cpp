@@ -794,6 +794,7 @@ template <class T> struct Block {
   std::vector<Arr3<T>> s[2];   // two registers of the passive-scalar masses rho C_i
   std::vector<Arr3<T>> cs;     // concentrations C_i (primitive)
   std::vector<Arr3<T>> fs[3];  // scalar fluxes on faces of direction d
+  Arr3<T> acc[3];              // forcing acceleration a at the active cells (allocated when forcing is set)
 };
 
 template <class T> struct Mesh {
@@ -806,6 +807,7 @@ template <class T> struct Mesh {
   std::vector<Block<T>> blk;
   long floor_events = 0;
   long emf_mismatch = 0;
+  bool forced = false;  // a forcing acceleration field is set (source terms in every stage)
 
   int bid(int bx, int by, int bz) const { return (bz * nb[1] + by) * nb[0] + bx; }
 
@@ -1196,7 +1198,11 @@ template <class T> struct Mesh {
 
   /* 2S register update of one stage (eq. rk-2s):
    *   u1 <- u1 + delta_s u0 ;  u0 <- g0 u0 + g1 u1 + beta dt L(u0)
-   * with L = -div F for the cell-centred variables and L = -curl E for the face field. */
+   * with L = -div F for the cell-centred variables and L = -curl E for the face field.
+   * [reading: forcing] With a forcing acceleration a(x) set, L of the cell-centred variables also holds the
+   * source terms of a body force on the stage state u0: rho a in the momentum and M . a in the energy
+   * (the work of the force), L = -div F + S(u0).  The paper defines no forcing; this is the body-force form
+   * of the momentum and energy equations, added in every stage like the flux divergence. */
   void register_update(double delta, double g0, double g1, double beta, double dt) {
 #pragma omp parallel for schedule(static)
     for (size_t ib = 0; ib < blk.size(); ++ib) {
@@ -1233,7 +1239,17 @@ template <class T> struct Mesh {
       /* cell-centred: conserved variable v <- flux component (rho, M_n..., E) */
       for (int k = NG; k < n[2] + NG; ++k)
         for (int j = NG; j < n[1] + NG; ++j)
-          for (int i = NG; i < n[0] + NG; ++i)
+          for (int i = NG; i < n[0] + NG; ++i) {
+            /* body-force source of the stage state (before u0 is overwritten below) */
+            T src[5] = {T(0.0), T(0.0), T(0.0), T(0.0), T(0.0)};
+            if (forced) {
+              const T rho = B.u[0][0](k, j, i);
+              const T ax = B.acc[0](k, j, i), ay = B.acc[1](k, j, i), az = B.acc[2](k, j, i);
+              src[1] = rho * ax;
+              src[2] = rho * ay;
+              src[3] = rho * az;
+              src[4] = (B.u[0][1](k, j, i) * ax + B.u[0][2](k, j, i) * ay) + B.u[0][3](k, j, i) * az;
+            }
             for (int v = 0; v < 5; ++v) {
               T dfl[3];
               for (int d = 0; d < 3; ++d) {
@@ -1255,9 +1271,10 @@ template <class T> struct Mesh {
                 const int ip = i + (d == 0), jp = j + (d == 1), kp = k + (d == 2);
                 dfl[d] = (B.flx[d][comp](kp, jp, ip) - B.flx[d][comp](k, j, i)) / dx[d];
               }
-              const T L = -((dfl[0] + dfl[1]) + dfl[2]);
+              const T L = forced ? -((dfl[0] + dfl[1]) + dfl[2]) + src[v] : -((dfl[0] + dfl[1]) + dfl[2]);
               B.u[0][v](k, j, i) = (g0 * B.u[0][v](k, j, i) + g1 * B.u[1][v](k, j, i)) + h * L;
             }
+          }
       /* face field: B1 on x-faces uses E3 (along y) and E2 (along z), cyclically */
       for (int fd = 0; fd < 3; ++fd) {
         const int a = (fd + 1) % 3, b = (fd + 2) % 3;  // B_fd: -[(dE_b/d a) - (dE_a/d b)]
@@ -1545,6 +1562,26 @@ void orc_set_scalars(void* m, const double* c) {
             B.s[0][q](K, J, I) = B.u[0][0](K, J, I) * c[q * ncell + g];
           }
   M.fill_ghosts(0);
+}
+
+/* Forcing acceleration a[3][NZ][NY][NX] at the cell centres ([reading: forcing], see register_update);
+ * NULL removes it. */
+void orc_set_forcing(void* m, const double* a) {
+  Mesh<double>& M = *static_cast<Mesh<double>*>(m);
+  M.forced = a != nullptr;
+  if (!a) return;
+  const int NX = M.P.nx[0], NY = M.P.nx[1], NZ = M.P.nx[2];
+  const size_t ncell = (size_t)NX * NY * NZ;
+  for (auto& B : M.blk)
+    for (int d = 0; d < 3; ++d) {
+      B.acc[d].init(M.c[0], M.c[1], M.c[2]);
+      for (int k = 0; k < M.n[2]; ++k)
+        for (int j = 0; j < M.n[1]; ++j)
+          for (int i = 0; i < M.n[0]; ++i) {
+            const size_t g = ((size_t)(B.loc[2] * M.n[2] + k) * NY + (B.loc[1] * M.n[1] + j)) * NX + (B.loc[0] * M.n[0] + i);
+            B.acc[d](k + M.NG, j + M.NG, i + M.NG) = a[d * ncell + g];
+          }
+    }
 }
 
 /* Scalar masses rho C_q of the active cells, out[q][NZ][NY][NX]. */

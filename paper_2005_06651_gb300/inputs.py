@@ -301,6 +301,35 @@ def turbulence(n=64, mb=None, seed=3003, mach=1.0, beta=1.0, gamma=5.0 / 3.0):
                    b1, b2, b3, meta={"seed": seed, "mach": mach, "beta": beta})
 
 
+def forcing_field(n=64, seed=4004, amp=1.0, kmax=2.0):
+    """Fixed solenoidal acceleration field a(x) on the unit periodic cube, for driven turbulence (a forcing
+    the paper does not define; see the forcing reading): complex-Gaussian Fourier modes on the shell
+    1 <= |k|/(2 pi) <= kmax, each projected onto the plane normal to its wave vector (div a = 0 mode by mode),
+    mean removed, scaled to rms |a| = amp.  Returns a (3, NZ, NY, NX) at the cell centres."""
+    nx = (n, n, n) if np.isscalar(n) else tuple(n)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    NX, NY, NZ = nx
+    kx = np.fft.fftfreq(NX, 1.0 / NX)
+    ky = np.fft.fftfreq(NY, 1.0 / NY)
+    kz = np.fft.rfftfreq(NZ, 1.0 / NZ)
+    K = np.meshgrid(kx, ky, kz, indexing="ij")
+    kk2 = K[0] ** 2 + K[1] ** 2 + K[2] ** 2
+    mask = (kk2 >= 1.0) & (kk2 <= kmax * kmax)
+    modes = [np.where(mask, rng.standard_normal(kk2.shape) + 1j * rng.standard_normal(kk2.shape), 0.0)
+             for _ in range(3)]
+    kdot = sum(K[d] * modes[d] for d in range(3))
+    inv = np.where(kk2 > 0, 1.0 / np.where(kk2 > 0, kk2, 1.0), 0.0)
+    modes = [modes[d] - K[d] * kdot * inv for d in range(3)]
+    acc = []
+    for d in range(3):
+        field = _irfftn(modes[d], (NX, NY, NZ))
+        field -= field.mean()
+        acc.append(np.transpose(field, (2, 1, 0)))
+    arms = math.sqrt(sum(float(np.mean(a ** 2)) for a in acc))
+    scale = amp / arms if arms > 0 else 0.0
+    return np.ascontiguousarray(np.stack(acc) * scale)
+
+
 # ------------------------------------------------------------------------------------------------
 # Blast wave (Sec. 3.4, 3D blast wave tests; the paper's performance problem)
 # ------------------------------------------------------------------------------------------------
