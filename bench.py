@@ -23,9 +23,10 @@ Printed JSON line (rank 0):
               bandwidth
   cpu_baseline the CPU oracle timed on this host's cores on a bounded sample (N = 1, rank 0)
   forms       the other forms and workloads, each with its own config: mixed precision (512^3 decaying
-              turbulence), batched (1024 uneven boxes), adjoint (checkpointed rollout), integrators
-              (RK2, RK3, VL2 / RK3 with PPM, four passive scalars), blast (the paper's blast wave at 256^3)
-              and meshblocks (single 64^3 MeshBlock rates, MeshBlock-size sweep at 128^3)
+              turbulence), batched (1024 uneven boxes, 200 cycles in one graph launch), adjoint (checkpointed
+              rollout), integrators (RK2, RK3, VL2 / RK3 with PPM, four passive scalars), blast (the paper's
+              blast wave at 256^3), meshblocks (single 64^3 MeshBlock rates, MeshBlock-size sweep at 128^3)
+              and linear_waves (the Alfven, slow and fast waves at 16^3, 32^3, 64^3: GPU and oracle L1 error)
 
 --impl reference times the CPU oracle itself on the same workload (the full 256^3 vortex in 512 MeshBlocks
 of 32^3): every step is one oracle VL2 cycle of the whole mesh on the host's cores.
@@ -53,9 +54,9 @@ HBM_BYTES_PER_ZONE_CYCLE = 320.0
 FLOPS_PER_FACE = {("plm", "hlld"): 484.9, ("dc", "hlld"): 394.1, ("plm", "hlle"): 299.8, ("dc", "hlle"): 209.0}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of
-# the k_flux_plm x sweep on the 128^3 vortex, 2,441,472 faces), scaled to a launch by its faces; valid only
+# the k_flux_plm x sweep on the 128^3 vortex, 2,162,688 faces), scaled to a launch by its faces; valid only
 # for the kernel source it was taken on (hash of the flux and physics sources), else reported as null.
-NCU_TRAFFIC = {"hash": "0f7a0658ba709b90", "bytes_per_face": 134.4}
+NCU_TRAFFIC = {"hash": "81e066f4b586258d", "bytes_per_face": 132.43}
 
 
 def flux_source_hash():
@@ -307,73 +308,86 @@ def mixed_form(args, dev, stream, vl2, inputs):
 
 def batched_form(args, dev, stream, vl2, inputs):
     """Batched form: boxes of sizes drawn from {16, 32, 48, 64}^3 (seed 3003), one MeshBlock each, periodic
-    turbulence (Mach 1, beta 1), FP64.  The same meshes are timed through the per-box launch path (new_dt +
-    step per box) and through the batch (autotuned flux shapes, K cycles as one CUDA-graph launch with
-    per-box CFL steps on the device); both start from the same state and must end bitwise equal."""
+    turbulence (Mach 1, beta 1), FP64.  The per-box launch path (new_dt + step per box) is timed over
+    --per-box-steps cycles; the batch (autotuned flux shapes, per-box CFL steps on the device) then runs the
+    same cycles as one CUDA-graph launch and must end bitwise equal to the per-box path on the checked boxes.
+    Finally the batch runs --batch-steps cycles (200: the configuration's run) from the initial state as one
+    graph launch, timed with events; the state after it is summarised per box."""
     import numpy as np
     import torch
 
-    nbox, K = args.batch_boxes, args.batch_steps
+    nbox, K, Kp = args.batch_boxes, args.batch_steps, min(args.per_box_steps, args.batch_steps)
     rng = np.random.Generator(np.random.PCG64(3003))
     sizes = rng.choice([16, 32, 48, 64], size=nbox)
     probs = [inputs.turbulence(n=int(n), mb=int(n), seed=3003 + q, mach=1.0, beta=1.0) for q, n in enumerate(sizes)]
     meshes = [vl2.Mesh(p.nx, p.mb, p.xmin, p.xmax, p.gamma, device=dev, stream=stream) for p in probs]
     ncell = sum(p.ncells for p in probs)
-    for m, p in zip(meshes, probs):
-        m.set_prims(p.w, p.b1, p.b2, p.b3)
+
+    def reset():
+        for m, p in zip(meshes, probs):
+            m.set_prims(p.w, p.b1, p.b2, p.b3)
+
+    reset()
+    tot0 = np.array([m.totals() for m in meshes])
     for m in meshes:  # warm-up
         m.step(m.new_dt(allow_nonphys=True))
-    for m, p in zip(meshes, probs):
-        m.set_prims(p.w, p.b1, p.b2, p.b3)
+    reset()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = sum(m.launch_count() for m in meshes)
     t0 = time.perf_counter()
-    e0.record(stream)
-    floors0 = [m.floor_count() for m in meshes]
-    for _ in range(K):
+    for _ in range(Kp):
         for m in meshes:
             m.step(m.new_dt(allow_nonphys=True))  # a floor is part of the method: counted, not fatal
-    e1.record(stream)
     torch.cuda.synchronize(dev)
     per_box_s = time.perf_counter() - t0
     per_box_launches = sum(m.launch_count() for m in meshes) - launches0
     check = [q for q in range(0, nbox, max(1, nbox // 8))]
     ref = {q: meshes[q].get_cons() for q in check}
-    for m, p in zip(meshes, probs):
-        m.set_prims(p.w, p.b1, p.b2, p.b3)
+    reset()
     batch = vl2.Batch(meshes)
     dc, pl = batch.autotune()
-    batch.run(1, want_dt=False)  # capture-free warm-up of a one-cycle graph
-    for m, p in zip(meshes, probs):
-        m.set_prims(p.w, p.b1, p.b2, p.b3)
-    batch.run(K, want_dt=False)  # capture the K-cycle graph (untimed), then reset and time it
-    for m, p in zip(meshes, probs):
-        m.set_prims(p.w, p.b1, p.b2, p.b3)
+    reset()
+    batch.run(Kp, want_dt=False)
+    same = all(all(np.array_equal(a, b) for a, b in zip(meshes[q].get_cons(), ref[q])) for q in check)
+    reset()
+    floors0 = [m.floor_count() for m in meshes]
     torch.cuda.synchronize(dev)
     l0 = batch.launch_count()
     t0 = time.perf_counter()
     e0.record(stream)
-    batch.run(K, want_dt=False)
+    batch.run(K, want_dt=False)  # captures the K-cycle graph, then launches it once
     e1.record(stream)
     torch.cuda.synchronize(dev)
     batched_s = time.perf_counter() - t0
     batched_ms = e0.elapsed_time(e1)
     batched_launches = batch.launch_count() - l0
-    same = all(all(np.array_equal(a, b) for a, b in zip(meshes[q].get_cons(), ref[q])) for q in check)
-    floor_boxes = [q for q, m in enumerate(meshes) if m.floor_count() > floors0[q]]
+    floor_events = [m.floor_count() - floors0[q] for q, m in enumerate(meshes)]
+    floor_boxes = [q for q, f in enumerate(floor_events) if f > 0]
+    tot = np.array([m.totals() for m in meshes])
+    divb = max(m.divb_norm() for m in meshes)
+    dt_next = np.array([m.new_dt(allow_nonphys=True) for m in meshes])
+    mass_drift = float(np.max(np.abs(tot[:, 0] - tot0[:, 0]) / tot0[:, 0]))
     del batch
     counts = {int(v): int((sizes == v).sum()) for v in (16, 32, 48, 64)}
     return {"config": {"workload": "%d_turbulence_boxes_sizes_16_32_48_64_cubed_one_block_each" % nbox,
                        "box_counts": counts, "cells": ncell, "steps": K, "seed": 3003, "mach": 1.0, "beta": 1.0,
                        "dtype": "f64"},
-            "value": ncell * K / batched_s, "unit": UNIT, "ms_per_step": 1e3 * batched_s / K,
-            "device_ms_per_step": batched_ms / K, "gpu_launches_per_step": batched_launches / K,
-            "per_box_value": ncell * K / per_box_s, "per_box_ms_per_step": 1e3 * per_box_s / K,
-            "per_box_launches_per_step": per_box_launches / K, "speedup_vs_per_box": per_box_s / batched_s,
+            "value": ncell * K / (batched_ms / 1e3), "unit": UNIT, "ms_per_step": batched_ms / K,
+            "wall_ms_per_step": 1e3 * batched_s / K, "gpu_launches_per_step": batched_launches / K,
+            "timing": "one graph launch of %d cycles, CUDA events on the mesh stream; the wall time also holds "
+                      "the graph's capture and instantiation" % K,
+            "per_box_value": ncell * Kp / per_box_s, "per_box_ms_per_step": 1e3 * per_box_s / Kp,
+            "per_box_steps": Kp, "per_box_launches_per_step": per_box_launches / Kp,
+            "speedup_vs_per_box": (1e3 * per_box_s / Kp) / (batched_ms / K),
             "autotuned": {"dc_threads": dc, "plm_lines": pl},
-            "bitwise_equal_to_per_box_path": bool(same), "checked_boxes": len(check),
-            "boxes_with_floor_events": floor_boxes}
+            "bitwise_equal_to_per_box_path": bool(same), "checked_boxes": len(check), "checked_steps": Kp,
+            "after_steps": {"steps": K, "boxes_with_floor_events": len(floor_boxes),
+                            "floor_events": int(sum(floor_events)),
+                            "most_floored_boxes": sorted(floor_boxes, key=lambda q: -floor_events[q])[:8],
+                            "max_divb_norm": divb, "max_relative_mass_drift": mass_drift,
+                            "next_dt_min": float(np.min(dt_next)), "next_dt_median": float(np.median(dt_next)),
+                            "boxes_next_dt_below_1e-6": [int(q) for q in np.nonzero(dt_next < 1e-6)[0]][:16]}}
 
 
 def adjoint_form(args, dev, stream, vl2, inputs):
@@ -611,18 +625,62 @@ def meshblocks_form(args, dev, stream, vl2, inputs):
                        "timing": "K cycles with device-side dt as one CUDA graph (vl2_batch_run)"}}
 
 
+def linear_waves_form(args, dev, stream, vl2, inputs):
+    """Config 1 (Sec. 3.3.1, eq. RMS-error): the Alfven, slow and fast waves of amplitude 1e-6 along the unit
+    cube's diagonal (|B| = 1, CFL 0.3), one MeshBlock, VL2 + PLM + HLLD + CT, one wave period with the last
+    step clipped, at N = 16, 32, 64 (32^3 is the configuration).  The GPU's L1 error next to the oracle's
+    (16^3 MeshBlocks on the host's cores, its own CFL steps), and the GPU's slopes between the sizes."""
+    import math
+
+    out = {"config": {"workload": "linear_waves_unit_cube_diagonal_amp1e-6_one_block_cfl0.3_one_period",
+                      "sizes": list(args.wave_sizes), "dtype": "f64"}}
+    from oracle import orc
+
+    for kind in ("alfven", "slow", "fast"):
+        rec = {}
+        for n in args.wave_sizes:
+            prob = inputs.linear_wave(n, kind=kind, amp=1e-6)
+            m = vl2.Mesh.from_problem(prob, device=dev, stream=stream)
+            ref = m.get_cons()
+            steps = m.run(prob.meta["period"])
+            gl1 = rms_l1(m.get_cons(), ref)
+            del m
+            o = orc.Mesh.from_problem(prob, mb=(min(16, n),) * 3)
+            oref = o.get_cons()
+            o.run(prob.meta["period"], cfl=0.3)
+            ol1 = rms_l1(o.get_cons(), oref)
+            del o
+            rec[str(n)] = {"gpu_l1": gl1, "oracle_l1": ol1, "steps": steps,
+                           "relative_difference": abs(gl1 - ol1) / ol1}
+        ns = [str(n) for n in args.wave_sizes]
+        rec["gpu_slopes"] = {"%s->%s" % (a, b): math.log2(rec[a]["gpu_l1"] / rec[b]["gpu_l1"]) for a, b in zip(ns, ns[1:])}
+        out[kind] = rec
+    return out
+
+
 def run_forms(args, dev, stream, vl2, inputs):
     import torch
 
     fns = {"mixed": mixed_form, "batched": batched_form, "adjoint": adjoint_form, "integrators": integrators_form,
-           "blast": blast_form, "meshblocks": meshblocks_form}
+           "blast": blast_form, "meshblocks": meshblocks_form, "linear_waves": linear_waves_form}
     forms = {}
     for name in [f for f in args.forms.split(",") if f]:
         if name not in fns:
             raise SystemExit("unknown form %r (choose from %s)" % (name, ", ".join(fns)))
-        forms[name] = fns[name](args, dev, stream, vl2, inputs)
+        forms[name] = compact(fns[name](args, dev, stream, vl2, inputs))
         torch.cuda.empty_cache()
     return forms
+
+
+def compact(x, digits=6):
+    """Floats rounded to `digits` significant digits, recursively (keeps the one JSON line short)."""
+    if isinstance(x, float):
+        return float("%.*g" % (digits, x))
+    if isinstance(x, dict):
+        return {k: compact(v, digits) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [compact(v, digits) for v in x]
+    return x
 
 
 def rms_l1(state, ref):
@@ -651,10 +709,13 @@ def main():
     ap.add_argument("--forms-n", type=int, default=512, help="grid of the mixed-precision form")
     ap.add_argument("--forms-steps", type=int, default=50)
     ap.add_argument("--batch-boxes", type=int, default=1024)
-    ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--batch-steps", type=int, default=200, help="cycles of the batched form's graph launch")
+    ap.add_argument("--per-box-steps", type=int, default=20, help="cycles of the per-box path it is compared with")
     ap.add_argument("--adj-n", type=int, default=64, help="grid of the differentiation form")
     ap.add_argument("--adj-steps", type=int, default=100)
-    ap.add_argument("--forms", default="mixed,batched,adjoint,integrators,blast,meshblocks",
+    ap.add_argument("--wave-sizes", type=lambda t: [int(v) for v in t.split(",")], default=[16, 32, 64],
+                    help="grids of the linear-wave form")
+    ap.add_argument("--forms", default="mixed,adjoint,integrators,blast,meshblocks,batched,linear_waves",
                     help="comma list of the forms to run")
     ap.add_argument("--mb-sweep-steps", type=int, default=20, help="timed cycles per MeshBlock size")
     ap.add_argument("--blast-steps", type=int, default=20, help="timed cycles of the blast-wave form")

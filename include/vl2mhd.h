@@ -95,6 +95,8 @@ typedef struct vl2_params {
                          it equals the sign switch where tanh saturates and at m = 0, and makes the corner a
                          smooth function of m (with adjoint, vl2_step_vjp then carries dw/dm).  Finite;
                          the meshes of a batch share one value. */
+  int forcing;        /* 1: reserve the acceleration array of vl2_set_forcing (a body force; not with adjoint);
+                         0 (the default): no forcing */
 } vl2_params;
 
 #define VL2_MAX_SCALARS 16
@@ -200,6 +202,14 @@ vl2_status vl2_floor_count(vl2_mesh* mesh, long long* out);
  * VL2_E_STATE (state not set), VL2_E_CUDA. */
 vl2_status vl2_set_scalars(vl2_mesh* mesh, const double* c, int where);
 vl2_status vl2_get_scalars(vl2_mesh* mesh, double* out, int where);
+
+/* Forcing (the paper defines none; this library's reading): a fixed body acceleration a(x) at the cell
+ * centres, a = [3][NZ][NY][NX] (global cell layout).  Every stage of every integrator then adds the source
+ * terms of the stage's state to L: rho a to the momentum and M . a (the force's work) to the energy, in the
+ * same update as the flux divergence.  NULL removes the forcing.  Needs a mesh created with
+ * params.forcing = 1; a batch reads each mesh's forcing as it was when the batch was created.
+ * Errors: VL2_E_ARG (bad where), VL2_E_STATE (params.forcing was 0), VL2_E_CUDA. */
+vl2_status vl2_set_forcing(vl2_mesh* mesh, const double* a, int where);
 
 /* Inspection of one stage's terms for the current state (Sec. 3.2.1-3.2.2, 3.1), without updating
  * it: face fluxes of the given reconstruction (VL2_DC, VL2_PLM, or VL2_PPM on a mesh with ng = 3) on the

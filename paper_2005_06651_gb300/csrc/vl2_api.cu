@@ -43,6 +43,7 @@ struct vl2_mesh {
   vl2::FluxShape fs;
   vl2::AdjArrays adj{};
   bool has_adj = false;
+  double* acc_store = nullptr;  // reserved forcing array (params.forcing); a.acc points here once set
   vl2::MeshView view() const { return vl2::MeshView{g, a}; }
   int max_mb() const { return std::max(g.mb[0], std::max(g.mb[1], g.mb[2])); }
   // reconstruction of the higher-order stages (params.recon, 0 meaning PLM)
@@ -165,6 +166,10 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
     msg = "nscalars must be 0 .. VL2_MAX_SCALARS (and 0 with the adjoint)";
     return VL2_E_ARG;
   }
+  if ((p->forcing != 0 && p->forcing != 1) || (p->forcing && p->adjoint)) {
+    msg = "forcing must be 0 or 1 (and 0 with the adjoint)";
+    return VL2_E_ARG;
+  }
   if (!(p->ct_delta >= 0.0) || !std::isfinite(p->ct_delta)) {
     msg = "ct_delta must be finite and >= 0";
     return VL2_E_ARG;
@@ -218,13 +223,14 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
 struct Plan {
   size_t off_u[2], off_b[2][3], off_w, off_f[3], off_e[3], off_ec, off_stage, off_red, off_scal, total;
   size_t off_s[2], off_cs, off_fsc[3];  // passive scalars (empty when ns = 0)
+  size_t off_acc;                       // forcing acceleration (empty without params.forcing)
   size_t stage_elems;
   size_t off_adj;  // start of the adjoint arrays (59 FP64 arrays per block, 65 with ct_delta) when requested
 };
 constexpr int ADJ_ARRAYS = 10 + 6 + 8 + 21 + 7 + 3 + 8 + 3;
 constexpr int ADJ_ARRAYS_SMOOTH_CT = 6;  // the predictor's face EMFs, kept for the smoothed weight's derivative
 
-Plan make_plan(const Geom& g, int precision, int adjoint) {
+Plan make_plan(const Geom& g, int precision, int adjoint, int forcing) {
   Plan pl;
   size_t o = 0;
   const size_t per = (size_t)g.nblk * g.box * sizeof(double);
@@ -260,6 +266,8 @@ Plan make_plan(const Geom& g, int precision, int adjoint) {
     pl.off_fsc[d] = o;
     o = align256(o + sc);
   }
+  pl.off_acc = o;
+  if (forcing) o = align256(o + 3 * per);
   const long long nc = ncells(g);
   long long st = 5 * nc + nfaces_total(g);
   st = std::max(st, (long long)g.ns * nc);
@@ -380,9 +388,10 @@ cudaError_t k_scalar_update(vl2_mesh* m, int base, int out, double h, double g_b
 cudaError_t k_emfs(vl2_mesh* m) {
   return timed(m, VL2_K_EMF, nodes(m->g), [&] { return vl2::launch_emfs(m->view(), nullptr, m->st); });
 }
-cudaError_t k_update(vl2_mesh* m, int base, int out, double h, double g_base = 1.0, double g_other = 0.0) {
+cudaError_t k_update(vl2_mesh* m, int base, int out, double h, double g_base = 1.0, double g_other = 0.0,
+                     int stage = -1) {
   return timed(m, VL2_K_UPDATE, nodes(m->g), [&] {
-    return vl2::launch_update(m->view(), nullptr, base, out, h, nullptr, 0.0, m->st, g_base, g_other);
+    return vl2::launch_update(m->view(), nullptr, base, out, h, nullptr, 0.0, m->st, g_base, g_other, stage);
   });
 }
 
@@ -408,7 +417,7 @@ vl2_status vl2_workspace_bytes(const vl2_params* params, size_t* bytes) {
   vl2_status s = make_geom(params, g, msg);
   if (s != VL2_OK) return fail(nullptr, s, msg);
   if (!bytes) return fail(nullptr, VL2_E_ARG, "bytes is NULL");
-  *bytes = make_plan(g, params->precision, params->adjoint).total;
+  *bytes = make_plan(g, params->precision, params->adjoint, params->forcing).total;
   return VL2_OK;
 }
 
@@ -420,7 +429,7 @@ vl2_status vl2_mesh_create(const vl2_params* params, void* workspace, size_t byt
   vl2_status s = make_geom(params, g, msg);
   if (s != VL2_OK) return fail(nullptr, s, msg);
   if (!workspace || ((uintptr_t)workspace & 255u)) return fail(nullptr, VL2_E_ARG, "workspace must be 256-byte aligned");
-  const Plan pl = make_plan(g, params->precision, params->adjoint);
+  const Plan pl = make_plan(g, params->precision, params->adjoint, params->forcing);
   if (bytes < pl.total) return fail(nullptr, VL2_E_NOMEM, "workspace smaller than vl2_workspace_bytes()");
   vl2_mesh* m = new (std::nothrow) vl2_mesh();
   if (!m) return fail(nullptr, VL2_E_ARG, "host allocation failed");
@@ -441,6 +450,8 @@ vl2_status vl2_mesh_create(const vl2_params* params, void* workspace, size_t byt
   m->a.mixed = params->precision == VL2_MIXED ? 1 : 0;
   for (int r = 0; r < 2; ++r) m->a.s[r] = g.ns ? (double*)(base + pl.off_s[r]) : nullptr;
   m->a.cs = g.ns ? (double*)(base + pl.off_cs) : nullptr;
+  m->acc_store = params->forcing ? (double*)(base + pl.off_acc) : nullptr;
+  m->a.acc = nullptr;
   for (int d = 0; d < 3; ++d) m->a.fsc[d] = g.ns ? (double*)(base + pl.off_fsc[d]) : nullptr;
   if (params->adjoint) {
     const size_t per = (size_t)g.nblk * g.box;
@@ -584,6 +595,26 @@ vl2_status vl2_set_scalars(vl2_mesh* m, const double* c, int where) {
   VL2_CHECK(m, k_ghosts(m, 0));
   m->w_valid = false;
   m->dt_pending = false;
+  return sync(m);
+}
+
+vl2_status vl2_set_forcing(vl2_mesh* m, const double* a, int where) {
+  if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
+  if (bad_where(where)) return fail(m, VL2_E_ARG, "bad where");
+  if (!m->acc_store) return fail(m, VL2_E_STATE, "the mesh was created without params.forcing");
+  if (!a) {
+    m->a.acc = nullptr;
+    return VL2_OK;
+  }
+  const double* da = a;
+  if (where == VL2_HOST) {
+    vl2_status st;
+    if ((st = copy_in(m, m->a.stage, a, 3 * (size_t)ncells(m->g), where)) != VL2_OK) return st;
+    da = m->a.stage;
+  }
+  VL2_CHECK(m, vl2::launch_scatter_forcing(m->g, m->acc_store, da, m->st));
+  ++m->launches;
+  m->a.acc = m->acc_store;
   return sync(m);
 }
 
@@ -786,7 +817,7 @@ vl2_status vl2_step(vl2_mesh* m, double dt) {
   VL2_CHECK(m, k_fluxes(m, 1, m->rec()));
   VL2_CHECK(m, k_scalar_fluxes(m, m->rec()));
   VL2_CHECK(m, k_emfs(m));
-  VL2_CHECK(m, k_update(m, 0, 0, dt));
+  VL2_CHECK(m, k_update(m, 0, 0, dt, 1.0, 0.0, 1));  // the fluxes (and forcing sources) come from register 1
   VL2_CHECK(m, k_scalar_update(m, 0, 0, dt));
   VL2_CHECK(m, k_ghosts(m, 0));
   // primitives of U^{n+1} for the next cycle, with the CFL reduction fused in
@@ -1172,7 +1203,7 @@ cudaError_t batch_cycle(vl2_batch* B, bool device_dt) {
   if ((e = vl2::launch_prim(v0, &dp, 1, true, false, B->cur)) != cudaSuccess) return e;
   if ((e = batch_fluxes(B, 1, B->recon)) != cudaSuccess) return e;
   if ((e = vl2::launch_emfs(v0, &dn, B->cur)) != cudaSuccess) return e;
-  if ((e = vl2::launch_update(v0, &dn, 0, 0, 0.0, B->ddt, 1.0, B->cur)) != cudaSuccess) return e;
+  if ((e = vl2::launch_update(v0, &dn, 0, 0, 0.0, B->ddt, 1.0, B->cur, 1.0, 0.0, 1)) != cudaSuccess) return e;
   if ((e = vl2::launch_ghosts(v0, &dg, 0, B->cur)) != cudaSuccess) return e;
   if ((e = vl2::launch_prim(v0, &dp, 0, true, true, B->cur)) != cudaSuccess) return e;
   B->launches += 11;  // plus the 6 flux launches (and 2 halo copies) counted in batch_fluxes

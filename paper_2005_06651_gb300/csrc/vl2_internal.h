@@ -59,6 +59,8 @@ struct Arrays {
   double* s[2];      // registers of the scalar masses rho C: [nblk][ns][box]
   double* cs;        // concentrations C, written by cons->prim: [nblk][ns][box]
   double* fsc[3];    // scalar fluxes per sweep direction: [nblk][ns][box]
+  // forcing acceleration at the cell centres, FP64: [nblk][3][box] (active cells); null when no forcing is set
+  double* acc;
 };
 
 enum { SC_MAXRATE = 0, SC_FLOORS = 1, SC_MISMATCH = 2, SC_COUNT = 8 };
@@ -129,8 +131,12 @@ cudaError_t launch_flux(const MeshView& v, const Dispatch* d, int reg, int recon
 // flux_halo = 0; a no-op launch-free call when no mesh of the launch needs it)
 cudaError_t launch_flux_halo(const MeshView& v, const Dispatch* d, cudaStream_t st);
 cudaError_t launch_emfs(const MeshView& v, const Dispatch* d, cudaStream_t st);
+// stage_reg: the register the stage's fluxes were formed from (its state carries the forcing source terms;
+// -1: base_reg)
 cudaError_t launch_update(const MeshView& v, const Dispatch* d, int base_reg, int out_reg, double h,
-                          const double* dtbox, double beta, cudaStream_t st, double g_base = 1.0, double g_other = 0.0);
+                          const double* dtbox, double beta, cudaStream_t st, double g_base = 1.0, double g_other = 0.0,
+                          int stage_reg = -1);
+cudaError_t launch_scatter_forcing(const Geom& g, double* acc, const double* a, cudaStream_t st);
 // per-box dt from the CFL rates the last prim reduced: dt[box] = cfl / rate, rate reset to 0
 cudaError_t launch_batch_dt(const MeshView* views, int nbox, const double* cfl, double* dt, cudaStream_t st);
 cudaError_t prepare_kernel_attributes();

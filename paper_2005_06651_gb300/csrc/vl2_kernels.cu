@@ -535,6 +535,32 @@ __global__ void k_scalars_io(Geom g, Arrays a, const double* c, double* out) {
   }
 }
 
+// forcing acceleration a[3][NZ][NY][NX] (global cell layout) into acc[nblk][3][box] at the active cells
+__global__ void __launch_bounds__(256) k_scatter_forcing(Geom g, double* acc, const double* __restrict__ a) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)g.mb[0] * g.mb[1] * g.mb[2];
+  if (t >= per * g.nblk) return;
+  const int b = (int)(t / per);
+  int rem = (int)(t - (long long)b * per);
+  const int i = rem % g.mb[0];
+  rem /= g.mb[0];
+  const int j = rem % g.mb[1];
+  const int k = rem / g.mb[1];
+  int loc[3];
+  block_loc(g, b, loc);
+  const long long gi = ((long long)(loc[2] * g.mb[2] + k) * g.N[1] + (loc[1] * g.mb[1] + j)) * g.N[0] +
+                       (loc[0] * g.mb[0] + i);
+  const long long nc = (long long)g.N[0] * g.N[1] * g.N[2];
+  const long long cc = cell_off(g, k + g.ng, j + g.ng, i + g.ng);
+  for (int d = 0; d < 3; ++d) acc[((long long)b * 3 + d) * g.box + cc] = a[d * nc + gi];
+}
+
+cudaError_t launch_scatter_forcing(const Geom& g, double* acc, const double* a, cudaStream_t st) {
+  const long long n = (long long)g.nblk * g.mb[0] * g.mb[1] * g.mb[2];
+  k_scatter_forcing<<<(unsigned)((n + THREADS - 1) / THREADS), THREADS, 0, st>>>(g, acc, a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scatter_scalars(const Geom& g, const Arrays& a, const double* c, cudaStream_t st) {
   const long long n = (long long)g.nblk * g.mb[0] * g.mb[1] * g.mb[2];
   k_scalars_io<<<(unsigned)((n + THREADS - 1) / THREADS), THREADS, 0, st>>>(g, a, c, nullptr);
@@ -645,12 +671,15 @@ cudaError_t launch_emfs(const MeshView& v, const Dispatch* d, cudaStream_t st) {
 //   B_out = (g_base B_base + g_other B_other) - h curl_h E   (B1 uses E3 along y and E2 along z, cyclically)
 // with U_other the register that is not U_base.  g_base = 1, g_other = 0 is the plain U_base + h L (VL2's
 // stages, gamma_s = {0, 1}, written with the base register named directly).
+// With a forcing acceleration a set, L of the cell-centred variables also holds the body-force source terms of
+// the stage state (register stage_reg, the one the fluxes were formed from): rho a for the momentum and
+// M . a for the energy, L = -div F + S, in FP64 in every precision.
 // U_base / U_out may alias (stages update a register in place), so no __restrict__ here.
 // ------------------------------------------------------------------------------------------------
 template <class T, bool PLAIN>
 __global__ void __launch_bounds__(256) k_update(MeshView single, const MeshView* views, const WorkItem* work,
                                                 int base_reg, int out_reg, double h, const double* dtbox, double beta,
-                                                double g_base, double g_other) {
+                                                double g_base, double g_other, int stage_reg) {
   __shared__ MeshView sv;
   int tile, box;
   const MeshView& V = stage_view(sv, single, views, work, tile, &box);
@@ -685,6 +714,17 @@ __global__ void __launch_bounds__(256) k_update(MeshView single, const MeshView*
     const T* F[3] = {F0 + (long long)b * 7 * g.box + c, F1 + (long long)b * 7 * g.box + c,
                      F2 + (long long)b * 7 * g.box + c};
     const long long ub = (long long)b * 5 * g.box + c;
+    double src[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const bool forced = V.a.acc != nullptr;
+    if (forced) {  // from the stage state, before an in-place update overwrites it
+      const double* Us = V.a.u[stage_reg] + ub;
+      const double* Ab = V.a.acc + (long long)b * 3 * g.box + c;
+      const double rho = Us[0], ax = Ab[0], ay = Ab[g.box], az = Ab[2 * g.box];
+      src[1] = rho * ax;
+      src[2] = rho * ay;
+      src[3] = rho * az;
+      src[4] = (Us[g.box] * ax + Us[2 * g.box] * ay) + Us[3 * g.box] * az;
+    }
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       double dfl[3];
@@ -702,7 +742,7 @@ __global__ void __launch_bounds__(256) k_update(MeshView single, const MeshView*
         const T* fp = F[d] + (long long)comp * g.box;
         dfl[d] = (to_f64(fp[stride[d]]) - to_f64(fp[0])) * g.idx[d];  // FP64 accumulation
       }
-      const double L = -((dfl[0] + dfl[1]) + dfl[2]);
+      const double L = forced ? -((dfl[0] + dfl[1]) + dfl[2]) + src[v] : -((dfl[0] + dfl[1]) + dfl[2]);
       const long long o = ub + (long long)v * g.box;
       Uout[o] = (PLAIN ? Ubase[o] : g_base * Ubase[o] + g_other * Uoth[o]) + h * L;
     }
@@ -723,7 +763,9 @@ __global__ void __launch_bounds__(256) k_update(MeshView single, const MeshView*
 }
 
 cudaError_t launch_update(const MeshView& v, const Dispatch* d, int base_reg, int out_reg, double h,
-                          const double* dtbox, double beta, cudaStream_t st, double g_base, double g_other) {
+                          const double* dtbox, double beta, cudaStream_t st, double g_base, double g_other,
+                          int stage_reg) {
+  if (stage_reg < 0) stage_reg = base_reg;
   const long long grid = d ? d->nwork : tiles_nodes(v.g);
   if (grid <= 0) return cudaSuccess;
   const MeshView* vs = d ? d->views : nullptr;
@@ -732,17 +774,17 @@ cudaError_t launch_update(const MeshView& v, const Dispatch* d, int base_reg, in
   if (v.a.mixed) {
     if (plain)
       k_update<float, true><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk, base_reg, out_reg, h, dtbox, beta, g_base,
-                                                                g_other);
+                                                                g_other, stage_reg);
     else
       k_update<float, false><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk, base_reg, out_reg, h, dtbox, beta,
-                                                                 g_base, g_other);
+                                                                 g_base, g_other, stage_reg);
   } else {
     if (plain)
       k_update<double, true><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk, base_reg, out_reg, h, dtbox, beta,
-                                                                 g_base, g_other);
+                                                                 g_base, g_other, stage_reg);
     else
       k_update<double, false><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk, base_reg, out_reg, h, dtbox, beta,
-                                                                  g_base, g_other);
+                                                                  g_base, g_other, stage_reg);
   }
   return cudaGetLastError();
 }

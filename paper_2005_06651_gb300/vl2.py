@@ -43,7 +43,8 @@ class Params(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("riemann", ctypes.c_int), ("precision", ctypes.c_int),
                 ("bc", ctypes.c_int * 6), ("dfloor", ctypes.c_double), ("pfloor", ctypes.c_double),
                 ("stream", ctypes.c_void_p), ("adjoint", ctypes.c_int), ("integrator", ctypes.c_int),
-                ("recon", ctypes.c_int), ("nscalars", ctypes.c_int), ("ct_delta", ctypes.c_double)]
+                ("recon", ctypes.c_int), ("nscalars", ctypes.c_int), ("ct_delta", ctypes.c_double),
+                ("forcing", ctypes.c_int)]
 
 
 class Layout(ctypes.Structure):
@@ -61,7 +62,7 @@ EXPORTS = ["vl2_workspace_bytes", "vl2_mesh_create", "vl2_mesh_destroy", "vl2_bl
            "vl2_batch_create", "vl2_batch_destroy", "vl2_batch_autotune", "vl2_batch_step", "vl2_batch_run",
            "vl2_batch_launch_count", "vl2_batch_last_error", "vl2_set_cons", "vl2_step_vjp", "vl2_prims_vjp",
            "vl2_debug_riemann_vjp", "vl2_last_error", "vl2_set_scalars", "vl2_get_scalars", "vl2_debug_fp64_peak",
-           "vl2_debug_arith"]
+           "vl2_debug_arith", "vl2_set_forcing"]
 NOALLOC_MAX_NZ = 4096
 K_PRIM, K_GHOSTS, K_FLUX_DC, K_FLUX_PLM, K_EMF, K_UPDATE, K_FLUX_PPM, K_SCALARS, K_FLUX_HALO = range(9)
 KERNEL_KINDS = {K_PRIM: "prim", K_GHOSTS: "ghosts", K_FLUX_DC: "flux_dc", K_FLUX_PLM: "flux_plm", K_EMF: "emf",
@@ -105,6 +106,7 @@ def load(path: str = LIB_PATH):
     L.vl2_debug_riemann_vjp.argtypes = [ctypes.c_int, ctypes.c_longlong, dp, dp, dp, dp, ctypes.c_double, dp, vp]
     L.vl2_debug_fp64_peak.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, dp, vp]
     L.vl2_debug_arith.argtypes = [ctypes.c_int, ctypes.c_longlong, dp, dp, vp]
+    L.vl2_set_forcing.argtypes = [vp, dp, ctypes.c_int]
     L.vl2_batch_workspace_bytes.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.vl2_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, vp, sz, ctypes.POINTER(ctypes.c_void_p)]
     L.vl2_batch_destroy.argtypes = [vp]
@@ -160,7 +162,7 @@ class Mesh:
     def __init__(self, nx, mb, xmin=(0.0, 0.0, 0.0), xmax=(1.0, 1.0, 1.0), gamma=5.0 / 3.0, cfl=0.3,
                  riemann=HLLD, bc=(PERIODIC,) * 6, dfloor=1e-12, pfloor=1e-12, precision=FP64, device=None,
                  stream=None, adjoint=False, integrator=VL2, recon=PLM, ng=None, nscalars=0, ct_delta=0.0,
-                 value_safe=False):
+                 value_safe=False, forcing=False):
         import torch
 
         L = load(LIB_PATH_VALUE_SAFE if value_safe else LIB_PATH)
@@ -189,6 +191,7 @@ class Mesh:
         p.dfloor, p.pfloor = float(dfloor), float(pfloor)
         p.stream = ctypes.c_void_p(stream.cuda_stream)
         p.adjoint = 1 if adjoint else 0
+        p.forcing = 1 if forcing else 0
         p.integrator = int(integrator)
         self._params = p
         nbytes = ctypes.c_size_t()
@@ -251,6 +254,16 @@ class Mesh:
         out = np.empty((self.nscalars,) + self.shape)
         _check(self._L.vl2_get_scalars(self._h, ctypes.c_void_p(out.ctypes.data), HOST), self._h, lib=self._L)
         return out
+
+    def set_forcing(self, a):
+        """Forcing acceleration a (3, NZ, NY, NX) at the cell centres (host array or CUDA tensor), or None to
+        remove it; the mesh needs forcing=True."""
+        if a is None:
+            _check(self._L.vl2_set_forcing(self._h, None, HOST), self._h, lib=self._L)
+            return
+        keep = np.ascontiguousarray(a, dtype=np.float64) if isinstance(a, np.ndarray) else a
+        ptr, where = _ptr(keep)
+        _check(self._L.vl2_set_forcing(self._h, ctypes.c_void_p(ptr), where), self._h, lib=self._L)
 
     def set_cons(self, u, b1, b2, b3):
         keep = [np.ascontiguousarray(x, dtype=np.float64) if isinstance(x, np.ndarray) else x for x in (u, b1, b2, b3)]
