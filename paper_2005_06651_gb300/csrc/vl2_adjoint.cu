@@ -640,8 +640,8 @@ __global__ void k_adj_ghost_gather(Geom g, int pass, double* lu, double* lb0, do
       if (dup) continue;
       seen[nseen++] = bq;
       const int hi = hi_index(g, kind, q), ha = hi_active(g, kind, q);
-      for (int gl = 0; gl <= hi; ++gl) {
-        if (gl >= NG && gl <= ha) continue;  // not a ghost along q
+      // the ghosts along q only: indices 0 .. NG-1, then ha+1 .. hi (in that order)
+      for (int gl = 0; gl <= hi; gl = (gl == NG - 1) ? ha + 1 : gl + 1) {
         int sblk, sloc;
         source_of_adj(g, q, bq * g.mb[q] + gl - NG, face, sblk, sloc);
         if (sblk != loc[q] || sloc != li[q]) continue;
