@@ -236,6 +236,27 @@ vl2_status vl2_debug_emfs(vl2_mesh* mesh, int recon, double* e1, double* e2, dou
 vl2_status vl2_step_vjp(vl2_mesh* mesh, double dt, const double* lam_u, const double* lam_b1, const double* lam_b2,
                         const double* lam_b3, double* out_u, double* out_b1, double* out_b2, double* out_b3);
 
+/* Bytes of device memory that one cycle recorded by vl2_step_record keeps (a "tape"): the predictor's and
+ * corrector's primitives on every cell, their face mass fluxes (with params.ct_delta > 0 also the two face
+ * EMFs of each face), and the face fields of both stages.  Needs a mesh created with params.adjoint = 1.
+ * Errors: VL2_E_ARG, VL2_E_STATE. */
+vl2_status vl2_tape_bytes(const vl2_mesh* mesh, size_t* bytes);
+
+/* One VL2 cycle (Sec. 3.2.3), exactly as vl2_step, that also writes into `tape` (caller-owned device memory
+ * of vl2_tape_bytes, 256-byte aligned) everything the cycle's adjoint reads.  A checkpointed rollout
+ * replays a segment with it and then runs vl2_step_vjp_recorded backwards over the tapes, instead of
+ * letting vl2_step_vjp recompute every cycle a second time.  Work is only enqueued.  Errors: VL2_E_ARG
+ * (dt, tape), VL2_E_STATE (no adjoint arrays, no state), VL2_E_CUDA. */
+vl2_status vl2_step_record(vl2_mesh* mesh, double dt, void* tape);
+
+/* The adjoint of a cycle recorded by vl2_step_record with the same dt, read from its tape alone: the
+ * same lam_in = J(x)^T lam_out as vl2_step_vjp at that cycle's starting state x (bitwise), without
+ * recomputing the cycle.  The mesh's state is neither read nor changed.  Arguments and layouts as
+ * vl2_step_vjp.  Errors: VL2_E_ARG, VL2_E_STATE, VL2_E_CUDA. */
+vl2_status vl2_step_vjp_recorded(vl2_mesh* mesh, double dt, const void* tape, const double* lam_u,
+                                 const double* lam_b1, const double* lam_b2, const double* lam_b3, double* out_u,
+                                 double* out_b1, double* out_b2, double* out_b3);
+
 /* Pointwise reverse-mode derivative of the Riemann flux (Sec. 3.2.2) used by vl2_step_vjp, for checking it
  * against an independent Jacobian: for n interfaces q with sweep-frame states wl[q][7], wr[q][7]
  * (rho, v_n, v_t1, v_t2, p, b_t1, b_t2), normal field bn[q] and flux adjoint lf[q][7] (mass, M_n, M_t1,

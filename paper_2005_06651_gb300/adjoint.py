@@ -2,10 +2,12 @@
 
 The forward pass advances the mesh through the C ABI and keeps the conserved state every k cycles
 (k ~ sqrt(N) by default) plus the time steps it used.  The backward pass walks the segments in reverse:
-it restores a segment's checkpoint (vl2_set_cons), recomputes the segment's cycles to recover the state
-before each cycle, and applies the hand-written adjoint of one cycle (vl2_step_vjp) from the last cycle
-back to the first; the adjoint of the initial conserved state is then taken back to the initial
-velocity (vl2_prims_vjp).  Time steps are those of the forward pass, held fixed (no derivative through the
+it restores a segment's checkpoint (vl2_set_cons) and replays the segment's cycles with vl2_step_record,
+which keeps in one tape per cycle what that cycle's adjoint reads; vl2_step_vjp_recorded then applies the
+hand-written adjoint of each cycle from its tape, last cycle first.  Each cycle is thus computed once more
+in the backward pass, not twice.  (With record=False the replay keeps only the states, and vl2_step_vjp
+recomputes each cycle's intermediates from its state.)  The adjoint of the initial conserved state is
+then taken back to the initial velocity (vl2_prims_vjp).  Time steps are those of the forward pass, held fixed (no derivative through the
 CFL condition).  All arithmetic runs in the CUDA library; this module only moves tensors between calls.
 """
 from __future__ import annotations
@@ -21,7 +23,7 @@ class Rollout:
     """N cycles of one mesh from an initial velocity field, with the density, pressure and face field of
     `prob` held fixed; differentiable in the velocity."""
 
-    def __init__(self, prob, nsteps, checkpoint_every=None, device=None, riemann=_vl2.HLLD):
+    def __init__(self, prob, nsteps, checkpoint_every=None, device=None, riemann=_vl2.HLLD, record=True):
         self.prob = prob
         self.nsteps = int(nsteps)
         self.k = int(checkpoint_every or max(1, int(round(math.sqrt(self.nsteps)))))
@@ -36,6 +38,8 @@ class Rollout:
         self.checkpoints = {}
         self.w0 = None
         self.timing = {}
+        self.record = bool(record)
+        self.tapes = [self.mesh.new_tape() for _ in range(self.k)] if self.record else []
 
     def _state(self):
         m = self.mesh
@@ -66,6 +70,13 @@ class Rollout:
         for s0 in reversed(starts):
             s1 = min(s0 + self.k, self.nsteps)
             m.set_cons(*self.checkpoints[s0])
+            if self.record:
+                for s in range(s0, s1):
+                    m.step_record(self.dts[s], self.tapes[s - s0])
+                for s in reversed(range(s0, s1)):
+                    m.step_vjp_recorded(self.dts[s], self.tapes[s - s0], lam, out)
+                    lam, out = out, lam
+                continue
             states = []
             for s in range(s0, s1):  # recompute the states before each cycle of the segment
                 states.append(self.checkpoints[s0] if s == s0 else self._state())

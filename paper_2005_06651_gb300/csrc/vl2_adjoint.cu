@@ -409,6 +409,51 @@ __global__ void __launch_bounds__(128) k_adj_flux(Geom g, const double* __restri
   }
 }
 
+// The van Leer slopes' share of the face-state adjoints of one PLM sweep, formed once per slope: for the slope
+// delta_j of cell j (on q_{j-1}, q_j, q_{j+1}), lam delta_j = a(j+1)/2 - r(j)/2 times its three partial
+// derivatives, stored as the contributions PM (to q_{j-1}), P0 (to q_j) and PP (to q_{j+1}) that
+// k_adj_flux_cells then gathers.  Only the slopes of cells next to a face of the flux region are formed.
+template <int DIR>
+__global__ void __launch_bounds__(128) k_adj_slopes(Geom g, const double* __restrict__ W,
+                                                    const double* __restrict__ LA, const double* __restrict__ LR,
+                                                    double* PM, double* P0, double* PP) {
+  constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
+  const int nx = g.mb[0] + 2, ny = g.mb[1] + 2, nz = g.mb[2] + 2;  // cells NG-1 .. NG+mb in every direction
+  const long long per = (long long)nx * ny * nz;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per * g.nblk) return;
+  const int b = (int)(t / per);
+  int rem = (int)(t - (long long)b * per);
+  const int li[3] = {rem % nx + NG - 1, (rem / nx) % ny + NG - 1, rem / (nx * ny) + NG - 1};
+  const long long c = cell_off(g, li[2], li[1], li[0]);
+  const long long sd = (DIR == 0) ? 1LL : ((DIR == 1) ? (long long)g.sx : (long long)g.sx * g.sy);
+  const int id = li[DIR];
+  auto face_ok = [&](int f) { return f >= NG && f <= NG + g.mb[DIR]; };
+  const bool lo = face_ok(id), hi = face_ok(id + 1);
+  const long long fb = (long long)b * 7 * g.box + c;
+  const int var[7] = {0, 1 + DIR, 1 + T1, 1 + T2, 4, 5 + T1, 5 + T2};
+  const double* Wb = W + (long long)b * 8 * g.box + c;
+#pragma unroll
+  for (int n = 0; n < 7; ++n) {
+    const long long o = fb + (long long)n * g.box;
+    double pm = 0.0, p0 = 0.0, pp = 0.0;
+    if (lo || hi) {
+      const double a1 = hi ? LA[o + sd] : 0.0;  // a(j+1)
+      const double r0 = lo ? LR[o] : 0.0;       // r(j)
+      const double ld = 0.5 * a1 - 0.5 * r0;
+      const double* q = Wb + (long long)var[n] * g.box;
+      double dm, d0, dp;
+      vl_slope_grad(q[-sd], q[0], q[sd], dm, d0, dp);
+      pm = ld * dm;
+      p0 = ld * d0;
+      pp = ld * dp;
+    }
+    PM[o] = pm;
+    P0[o] = p0;
+    PP[o] = pp;
+  }
+}
+
 // The cells' share of the face-state adjoints of one sweep, gathered per cell in a fixed order.  With
 // a(f), r(f) the adjoints of the left and right states of face f (between cells f-1 and f):
 //   donor cell:  lam q_i += a(i+1) + r(i)
@@ -419,7 +464,8 @@ __global__ void __launch_bounds__(128) k_adj_flux(Geom g, const double* __restri
 template <int DIR, int REC>
 __global__ void __launch_bounds__(128) k_adj_flux_cells(Geom g, const double* __restrict__ W,
                                                         const double* __restrict__ LA, const double* __restrict__ LR,
-                                                        double* lw) {
+                                                        const double* __restrict__ PM, const double* __restrict__ P0,
+                                                        const double* __restrict__ PP, double* lw) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   constexpr int H = (REC == REC_DC) ? 1 : 2;  // cells NG-H .. NG+mb-1+H along the sweep
   const int nx = g.mb[0] + (DIR == 0 ? 2 * H : 2), ny = g.mb[1] + (DIR == 1 ? 2 * H : 2),
@@ -446,26 +492,10 @@ __global__ void __launch_bounds__(128) k_adj_flux_cells(Geom g, const double* __
     const double r0 = face_ok(id) ? LR[o] : 0.0;           // r(i)
     double lam = a1 + r0;
     if (REC == REC_PLM) {
-      const double a0 = face_ok(id) ? LA[o] : 0.0;                // a(i)
-      const double a2 = face_ok(id + 2) ? LA[o + 2 * sd] : 0.0;   // a(i+2)
-      const double rm = face_ok(id - 1) ? LR[o - sd] : 0.0;       // r(i-1)
-      const double r1 = face_ok(id + 1) ? LR[o + sd] : 0.0;       // r(i+1)
-      const double* q = Wb + (long long)var[n] * g.box;
-      double dm, d0, dp;
-      // A slope is evaluated only when one of its faces is in the flux region; its stencil then lies in
-      // cells NG-2 .. NG+mb+1 of the box.
-      if (face_ok(id) || face_ok(id - 1)) {  // slope of cell i-1 (q_{i-2}, q_{i-1}, q_i): d/dq_i = dp
-        vl_slope_grad(q[-2 * sd], q[-sd], q[0], dm, d0, dp);
-        lam += (0.5 * a0 - 0.5 * rm) * dp;
-      }
-      if (face_ok(id + 1) || face_ok(id)) {  // slope of cell i: d/dq_i = d0
-        vl_slope_grad(q[-sd], q[0], q[sd], dm, d0, dp);
-        lam += (0.5 * a1 - 0.5 * r0) * d0;
-      }
-      if (face_ok(id + 2) || face_ok(id + 1)) {  // slope of cell i+1 (q_i, q_{i+1}, q_{i+2}): d/dq_i = dm
-        vl_slope_grad(q[0], q[sd], q[2 * sd], dm, d0, dp);
-        lam += (0.5 * a2 - 0.5 * r1) * dm;
-      }
+      // the slopes of cells i-1, i, i+1 (each formed once, by k_adj_slopes), where next to the flux region
+      if (face_ok(id) || face_ok(id - 1)) lam += PP[o - sd];   // slope of cell i-1: d/dq_i
+      if (face_ok(id + 1) || face_ok(id)) lam += P0[o];        // slope of cell i
+      if (face_ok(id + 2) || face_ok(id + 1)) lam += PM[o + sd];  // slope of cell i+1
     }
     LWb[(long long)var[n] * g.box] += lam;
   }
@@ -835,10 +865,17 @@ static cudaError_t adj_flux_one(const Geom& g, const AdjArrays& j, const double*
   k_adj_flux<DIR, REC, RS><<<grid_of(n, 128), 128, 0, st>>>(g, W, Bn, j.lf[DIR], j.lr, lbn);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (REC == REC_PLM) {
+    const long long ns = (long long)g.nblk * (g.mb[0] + 2) * (g.mb[1] + 2) * (g.mb[2] + 2);
+    k_adj_slopes<DIR><<<grid_of(ns, 128), 128, 0, st>>>(g, W, j.lf[DIR], j.lr, j.ps[0], j.ps[1], j.ps[2]);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   constexpr int H = (REC == REC_DC) ? 1 : 2;
   long long nc = g.nblk;
   for (int q = 0; q < 3; ++q) nc *= g.mb[q] + (q == DIR ? 2 * H : 2);
-  k_adj_flux_cells<DIR, REC><<<grid_of(nc, 128), 128, 0, st>>>(g, W, j.lf[DIR], j.lr, j.lw);
+  k_adj_flux_cells<DIR, REC><<<grid_of(nc, 128), 128, 0, st>>>(g, W, j.lf[DIR], j.lr, j.ps[0], j.ps[1], j.ps[2],
+                                                              j.lw);
   return cudaGetLastError();
 }
 

@@ -471,6 +471,7 @@ vl2_status vl2_mesh_create(const vl2_params* params, void* workspace, size_t byt
     for (int d = 0; d < 3; ++d) m->adj.le[d] = take(1);
     m->adj.w0 = take(8);
     for (int d = 0; d < 3; ++d) m->adj.m1[d] = take(g.ct_delta > 0.0 ? 3 : 1);
+    for (int d = 0; d < 3; ++d) m->adj.ps[d] = static_cast<double*>(m->a.f[d]);  // FP64: the adjoint needs VL2_FP64
     m->has_adj = true;
   }
   m->a.stage = (double*)(base + pl.off_stage);
@@ -666,14 +667,116 @@ vl2_status vl2_set_cons(vl2_mesh* m, const double* u, const double* b1, const do
   return VL2_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// What the reverse sweep of one VL2 cycle reads: both stages' primitives (all cells), face mass fluxes (with
+// the smoothed CT weight also their face EMFs F[B_t1], F[B_t2]; `mstride` between blocks, the EMF components
+// at +box and +2 box) and the face fields of both stages.
+struct CycleInputs {
+  const double* w0;      // predictor primitives W(U^n): [nblk][8][box]
+  const double* w1;      // corrector primitives W(U^{n+1/2})
+  const double* m1[3];   // predictor face mass fluxes (per sweep direction)
+  const double* m2[3];   // corrector face mass fluxes
+  long long m1_stride, m2_stride, m2_e5, m2_e6;
+  const double* b0[3];   // face fields of U^n
+  const double* b1[3];   // face fields of U^{n+1/2}
+};
+
+// Reverse sweep of one VL2 cycle from its recorded inputs: the transposes of the corrector, then of the
+// predictor, each as update, upwind-CT EMFs, Riemann fluxes (with PLM), cons->prim, ghost exchange.
+vl2_status vjp_reverse(vl2_mesh* m, double dt, const CycleInputs& in, const double* lam_u, const double* lam_b1,
+                       const double* lam_b2, const double* lam_b3, double* out_u, double* out_b1, double* out_b2,
+                       double* out_b3) {
+  const Geom& g = m->g;
+  const vl2::AdjArrays& j = m->adj;
+  cudaStream_t st = m->st;
+  const size_t per = (size_t)g.nblk * g.box * sizeof(double);
+  for (int r = 0; r < 2; ++r) {
+    VL2_CHECK(m, cudaMemsetAsync(j.lu[r], 0, 5 * per, st));
+    for (int d = 0; d < 3; ++d) VL2_CHECK(m, cudaMemsetAsync(j.lb[r][d], 0, per, st));
+  }
+  VL2_CHECK(m, cudaMemsetAsync(j.lw, 0, 8 * per, st));
+  VL2_CHECK(m, vl2::adj_scatter_out(g, j, lam_u, lam_b1, lam_b2, lam_b3, st));
+  // corrector: U0 <- U0 + dt L_PLM(U1)
+  VL2_CHECK(m, vl2::adj_update(g, j, 0, 0, dt, st));
+  VL2_CHECK(m, vl2::adj_ct(g, j, in.w1, in.m2, in.m2_stride, in.m2_e5, in.m2_e6, st));
+  VL2_CHECK(m, vl2::adj_fluxes(g, j, vl2::REC_PLM, m->p.riemann, in.w1, in.b1, 1, st));
+  VL2_CHECK(m, vl2::adj_prim(g, j, in.w1, 1, st));
+  VL2_CHECK(m, vl2::adj_ghosts(g, j, 1, st));
+  // predictor: U1 = U0 + dt/2 L_DC(U0)
+  VL2_CHECK(m, cudaMemsetAsync(j.lw, 0, 8 * per, st));
+  VL2_CHECK(m, vl2::adj_update(g, j, 1, 0, 0.5 * dt, st));
+  VL2_CHECK(m, vl2::adj_ct(g, j, in.w0, in.m1, in.m1_stride, g.box, 2 * g.box, st));
+  VL2_CHECK(m, vl2::adj_fluxes(g, j, vl2::REC_DC, m->p.riemann, in.w0, in.b0, 0, st));
+  VL2_CHECK(m, vl2::adj_prim(g, j, in.w0, 0, st));
+  VL2_CHECK(m, vl2::adj_ghosts(g, j, 0, st));
+  VL2_CHECK(m, vl2::adj_gather_in(g, j, out_u, out_b1, out_b2, out_b3, st));
+  m->launches += 32;  // scatter, 2 x (update, CT, 3 x 2 flux, prim, 3 x 2 ghost passes), gather
+  return VL2_OK;
+}
+
+vl2_status vjp_args(vl2_mesh* m, double dt, const void* a, const void* b, const void* c, const void* d,
+                    const void* e, const void* f, const void* g, const void* h) {
+  if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
+  if (!a || !b || !c || !d || !e || !f || !g || !h) return fail(m, VL2_E_ARG, "NULL argument");
+  if (!m->has_adj) return fail(m, VL2_E_STATE, "mesh was created without params.adjoint");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(m, VL2_E_ARG, "dt must be finite and positive");
+  return VL2_OK;
+}
+
+// Tape of one recorded cycle, carved from the caller's buffer (doubles, each part 256-byte aligned).
+struct Tape {
+  double *w0, *w1, *b0[3], *b1[3], *m1[3], *m2[3];
+  long long mk;  // components kept per face: 1 (mass flux), 3 with the smoothed CT weight (+ two face EMFs)
+  size_t bytes;
+};
+Tape carve_tape(const vl2_mesh* m, void* base) {
+  const Geom& g = m->g;
+  Tape t;
+  t.mk = g.ct_delta > 0.0 ? 3 : 1;
+  const size_t per = (size_t)g.nblk * g.box * sizeof(double);
+  size_t o = 0;
+  char* p = static_cast<char*>(base);
+  auto take = [&](size_t nvar) {
+    double* r = p ? reinterpret_cast<double*>(p + o) : nullptr;
+    o = align256(o + nvar * per);
+    return r;
+  };
+  t.w0 = take(8);
+  t.w1 = take(8);
+  for (int d = 0; d < 3; ++d) t.b0[d] = take(1);
+  for (int d = 0; d < 3; ++d) t.b1[d] = take(1);
+  for (int d = 0; d < 3; ++d) t.m1[d] = take(t.mk);
+  for (int d = 0; d < 3; ++d) t.m2[d] = take(t.mk);
+  t.bytes = o;
+  return t;
+}
+
+// the face mass fluxes (and with the smoothed CT weight the two face EMFs) of the current flux arrays
+vl2_status keep_mass_fluxes(vl2_mesh* m, double* const* dst, long long mk) {
+  const Geom& g = m->g;
+  for (int d = 0; d < 3; ++d) {
+    VL2_CHECK(m, cudaMemcpy2DAsync(dst[d], mk * g.box * sizeof(double), m->a.f[d], 7 * g.box * sizeof(double),
+                                   g.box * sizeof(double), g.nblk, cudaMemcpyDeviceToDevice, m->st));
+    if (mk == 3)
+      VL2_CHECK(m, cudaMemcpy2DAsync(dst[d] + g.box, mk * g.box * sizeof(double),
+                                     static_cast<const double*>(m->a.f[d]) + 5 * g.box, 7 * g.box * sizeof(double),
+                                     2 * g.box * sizeof(double), g.nblk, cudaMemcpyDeviceToDevice, m->st));
+  }
+  return VL2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 vl2_status vl2_step_vjp(vl2_mesh* m, double dt, const double* lam_u, const double* lam_b1, const double* lam_b2,
                         const double* lam_b3, double* out_u, double* out_b1, double* out_b2, double* out_b3) {
-  if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
-  if (!lam_u || !lam_b1 || !lam_b2 || !lam_b3 || !out_u || !out_b1 || !out_b2 || !out_b3)
-    return fail(m, VL2_E_ARG, "NULL argument");
-  if (!m->has_adj) return fail(m, VL2_E_STATE, "mesh was created without params.adjoint");
+  vl2_status s = vjp_args(m, dt, lam_u, lam_b1, lam_b2, lam_b3, out_u, out_b1, out_b2, out_b3);
+  if (s != VL2_OK) return s;
   if (!m->initialized) return fail(m, VL2_E_STATE, "vl2_set_prims/vl2_set_cons has not been called");
-  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(m, VL2_E_ARG, "dt must be finite and positive");
   const Geom& g = m->g;
   const vl2::AdjArrays& j = m->adj;
   cudaStream_t st = m->st;
@@ -683,16 +786,9 @@ vl2_status vl2_step_vjp(vl2_mesh* m, double dt, const double* lam_u, const doubl
   VL2_CHECK(m, cudaMemcpyAsync(j.w0, m->a.w, 8 * per, cudaMemcpyDeviceToDevice, st));
   VL2_CHECK(m, k_fluxes(m, 0, VL2_DC));
   // the predictor's mass fluxes (its upwind choices), and with the smoothed CT weight its face EMFs
-  const bool smooth_ct = g.ct_delta > 0.0;
-  const long long m1_stride = smooth_ct ? 3 * g.box : g.box;
-  for (int d = 0; d < 3; ++d) {
-    VL2_CHECK(m, cudaMemcpy2DAsync(j.m1[d], m1_stride * sizeof(double), m->a.f[d], 7 * g.box * sizeof(double),
-                                   g.box * sizeof(double), g.nblk, cudaMemcpyDeviceToDevice, st));
-    if (smooth_ct)
-      VL2_CHECK(m, cudaMemcpy2DAsync(j.m1[d] + g.box, m1_stride * sizeof(double),
-                                     static_cast<const double*>(m->a.f[d]) + 5 * g.box, 7 * g.box * sizeof(double),
-                                     2 * g.box * sizeof(double), g.nblk, cudaMemcpyDeviceToDevice, st));
-  }
+  const long long mk = g.ct_delta > 0.0 ? 3 : 1;
+  s = keep_mass_fluxes(m, j.m1, mk);
+  if (s != VL2_OK) return s;
   VL2_CHECK(m, k_emfs(m));
   VL2_CHECK(m, k_update(m, 0, 1, 0.5 * dt));
   VL2_CHECK(m, k_ghosts(m, 1));
@@ -700,35 +796,85 @@ vl2_status vl2_step_vjp(vl2_mesh* m, double dt, const double* lam_u, const doubl
   VL2_CHECK(m, k_fluxes(m, 1, VL2_PLM));
   m->w_valid = false;
   m->dt_pending = false;
-  // reverse sweep
-  for (int r = 0; r < 2; ++r) {
-    VL2_CHECK(m, cudaMemsetAsync(j.lu[r], 0, 5 * per, st));
-    for (int d = 0; d < 3; ++d) VL2_CHECK(m, cudaMemsetAsync(j.lb[r][d], 0, per, st));
+  CycleInputs in;
+  in.w0 = j.w0;
+  in.w1 = static_cast<const double*>(m->a.w);
+  for (int d = 0; d < 3; ++d) {
+    in.m1[d] = j.m1[d];
+    in.m2[d] = static_cast<const double*>(m->a.f[d]);
+    in.b0[d] = m->a.b[0][d];
+    in.b1[d] = m->a.b[1][d];
   }
-  VL2_CHECK(m, cudaMemsetAsync(j.lw, 0, 8 * per, st));
-  VL2_CHECK(m, vl2::adj_scatter_out(g, j, lam_u, lam_b1, lam_b2, lam_b3, st));
-  const double* W1 = static_cast<const double*>(m->a.w);
-  const double* mf2[3] = {static_cast<const double*>(m->a.f[0]), static_cast<const double*>(m->a.f[1]),
-                          static_cast<const double*>(m->a.f[2])};
-  const double* bn1[3] = {m->a.b[1][0], m->a.b[1][1], m->a.b[1][2]};
-  const double* bn0[3] = {m->a.b[0][0], m->a.b[0][1], m->a.b[0][2]};
-  const double* mf1[3] = {j.m1[0], j.m1[1], j.m1[2]};
-  // corrector: U0 <- U0 + dt L_PLM(U1)
-  VL2_CHECK(m, vl2::adj_update(g, j, 0, 0, dt, st));
-  VL2_CHECK(m, vl2::adj_ct(g, j, W1, mf2, 7 * g.box, 5 * g.box, 6 * g.box, st));
-  VL2_CHECK(m, vl2::adj_fluxes(g, j, vl2::REC_PLM, m->p.riemann, W1, bn1, 1, st));
-  VL2_CHECK(m, vl2::adj_prim(g, j, W1, 1, st));
-  VL2_CHECK(m, vl2::adj_ghosts(g, j, 1, st));
-  // predictor: U1 = U0 + dt/2 L_DC(U0)
-  VL2_CHECK(m, cudaMemsetAsync(j.lw, 0, 8 * per, st));
-  VL2_CHECK(m, vl2::adj_update(g, j, 1, 0, 0.5 * dt, st));
-  VL2_CHECK(m, vl2::adj_ct(g, j, j.w0, mf1, m1_stride, g.box, 2 * g.box, st));
-  VL2_CHECK(m, vl2::adj_fluxes(g, j, vl2::REC_DC, m->p.riemann, j.w0, bn0, 0, st));
-  VL2_CHECK(m, vl2::adj_prim(g, j, j.w0, 0, st));
-  VL2_CHECK(m, vl2::adj_ghosts(g, j, 0, st));
-  VL2_CHECK(m, vl2::adj_gather_in(g, j, out_u, out_b1, out_b2, out_b3, st));
-  m->launches += 32;  // scatter, 2 x (update, CT, 3 x 2 flux, prim, 3 x 2 ghost passes), gather
+  in.m1_stride = mk * g.box;
+  in.m2_stride = 7 * g.box;
+  in.m2_e5 = 5 * g.box;
+  in.m2_e6 = 6 * g.box;
+  return vjp_reverse(m, dt, in, lam_u, lam_b1, lam_b2, lam_b3, out_u, out_b1, out_b2, out_b3);
+}
+
+vl2_status vl2_tape_bytes(const vl2_mesh* m, size_t* bytes) {
+  if (!m || !bytes) return fail(nullptr, VL2_E_ARG, "NULL argument");
+  if (!m->has_adj) return fail(nullptr, VL2_E_STATE, "mesh was created without params.adjoint");
+  *bytes = carve_tape(m, nullptr).bytes;
   return VL2_OK;
+}
+
+vl2_status vl2_step_record(vl2_mesh* m, double dt, void* tape) {
+  if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
+  if (!tape || ((uintptr_t)tape & 255u)) return fail(m, VL2_E_ARG, "tape must be non-NULL and 256-byte aligned");
+  if (!m->has_adj) return fail(m, VL2_E_STATE, "mesh was created without params.adjoint");
+  if (!m->initialized) return fail(m, VL2_E_STATE, "vl2_set_prims/vl2_set_cons has not been called");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(m, VL2_E_ARG, "dt must be finite and positive");
+  const Geom& g = m->g;
+  const Tape t = carve_tape(m, tape);
+  cudaStream_t st = m->st;
+  const size_t per = (size_t)g.nblk * g.box * sizeof(double);
+  vl2_status s = ensure_prims(m);
+  if (s != VL2_OK) return s;
+  // the VL2 cycle of vl2_step, keeping what its adjoint reads
+  VL2_CHECK(m, cudaMemcpyAsync(t.w0, m->a.w, 8 * per, cudaMemcpyDeviceToDevice, st));
+  for (int d = 0; d < 3; ++d) VL2_CHECK(m, cudaMemcpyAsync(t.b0[d], m->a.b[0][d], per, cudaMemcpyDeviceToDevice, st));
+  VL2_CHECK(m, k_fluxes(m, 0, VL2_DC));
+  if ((s = keep_mass_fluxes(m, t.m1, t.mk)) != VL2_OK) return s;
+  VL2_CHECK(m, k_emfs(m));
+  VL2_CHECK(m, k_update(m, 0, 1, 0.5 * dt));
+  VL2_CHECK(m, k_ghosts(m, 1));
+  VL2_CHECK(m, k_prim(m, 1, false));
+  VL2_CHECK(m, cudaMemcpyAsync(t.w1, m->a.w, 8 * per, cudaMemcpyDeviceToDevice, st));
+  for (int d = 0; d < 3; ++d) VL2_CHECK(m, cudaMemcpyAsync(t.b1[d], m->a.b[1][d], per, cudaMemcpyDeviceToDevice, st));
+  VL2_CHECK(m, k_fluxes(m, 1, VL2_PLM));
+  if ((s = keep_mass_fluxes(m, t.m2, t.mk)) != VL2_OK) return s;
+  VL2_CHECK(m, k_emfs(m));
+  VL2_CHECK(m, k_update(m, 0, 0, dt, 1.0, 0.0, 1));
+  VL2_CHECK(m, k_ghosts(m, 0));
+  VL2_CHECK(m, cudaMemsetAsync(m->a.scal + vl2::SC_MAXRATE, 0, sizeof(unsigned long long), st));
+  VL2_CHECK(m, k_prim(m, 0, true));
+  m->w_valid = true;
+  m->dt_pending = true;
+  return VL2_OK;
+}
+
+vl2_status vl2_step_vjp_recorded(vl2_mesh* m, double dt, const void* tape, const double* lam_u, const double* lam_b1,
+                                 const double* lam_b2, const double* lam_b3, double* out_u, double* out_b1,
+                                 double* out_b2, double* out_b3) {
+  vl2_status s = vjp_args(m, dt, lam_u, lam_b1, lam_b2, lam_b3, out_u, out_b1, out_b2, out_b3);
+  if (s != VL2_OK) return s;
+  if (!tape || ((uintptr_t)tape & 255u)) return fail(m, VL2_E_ARG, "tape must be non-NULL and 256-byte aligned");
+  const Geom& g = m->g;
+  const Tape t = carve_tape(m, const_cast<void*>(tape));
+  CycleInputs in;
+  in.w0 = t.w0;
+  in.w1 = t.w1;
+  for (int d = 0; d < 3; ++d) {
+    in.m1[d] = t.m1[d];
+    in.m2[d] = t.m2[d];
+    in.b0[d] = t.b0[d];
+    in.b1[d] = t.b1[d];
+  }
+  in.m1_stride = in.m2_stride = t.mk * g.box;
+  in.m2_e5 = g.box;
+  in.m2_e6 = 2 * g.box;
+  return vjp_reverse(m, dt, in, lam_u, lam_b1, lam_b2, lam_b3, out_u, out_b1, out_b2, out_b3);
 }
 
 vl2_status vl2_debug_riemann_vjp(int riemann, long long n, const double* wl, const double* wr, const double* bn,

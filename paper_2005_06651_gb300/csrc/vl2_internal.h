@@ -170,6 +170,10 @@ struct AdjArrays {
   double* w0;        // predictor primitives kept from the forward recompute: [nblk][8][box]
   double* m1[3];     // predictor face mass fluxes (upwind choices of its CT): [nblk][box]; with the smoothed CT
                      // weight also its face EMFs F[B_t1], F[B_t2]: [nblk][3][box]
+  // the PLM slopes' contributions of one sweep [nblk][7][box] x 3 (to the cells below, at and above the
+  // slope's cell).  They live in the forward flux arrays, free while the reverse sweep transposes fluxes
+  // (its CT transpose, the last reader of a corrector mass flux, has run by then).
+  double* ps[3];
 };
 
 cudaError_t adj_scatter_out(const Geom& g, const AdjArrays& j, const double* gu, const double* gb1, const double* gb2,

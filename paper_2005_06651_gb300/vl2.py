@@ -62,7 +62,7 @@ EXPORTS = ["vl2_workspace_bytes", "vl2_mesh_create", "vl2_mesh_destroy", "vl2_bl
            "vl2_batch_create", "vl2_batch_destroy", "vl2_batch_autotune", "vl2_batch_step", "vl2_batch_run",
            "vl2_batch_launch_count", "vl2_batch_last_error", "vl2_set_cons", "vl2_step_vjp", "vl2_prims_vjp",
            "vl2_debug_riemann_vjp", "vl2_last_error", "vl2_set_scalars", "vl2_get_scalars", "vl2_debug_fp64_peak",
-           "vl2_debug_arith", "vl2_set_forcing"]
+           "vl2_debug_arith", "vl2_set_forcing", "vl2_tape_bytes", "vl2_step_record", "vl2_step_vjp_recorded"]
 NOALLOC_MAX_NZ = 4096
 K_PRIM, K_GHOSTS, K_FLUX_DC, K_FLUX_PLM, K_EMF, K_UPDATE, K_FLUX_PPM, K_SCALARS, K_FLUX_HALO = range(9)
 KERNEL_KINDS = {K_PRIM: "prim", K_GHOSTS: "ghosts", K_FLUX_DC: "flux_dc", K_FLUX_PLM: "flux_plm", K_EMF: "emf",
@@ -107,6 +107,9 @@ def load(path: str = LIB_PATH):
     L.vl2_debug_fp64_peak.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, dp, vp]
     L.vl2_debug_arith.argtypes = [ctypes.c_int, ctypes.c_longlong, dp, dp, vp]
     L.vl2_set_forcing.argtypes = [vp, dp, ctypes.c_int]
+    L.vl2_tape_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.vl2_step_record.argtypes = [vp, ctypes.c_double, vp]
+    L.vl2_step_vjp_recorded.argtypes = [vp, ctypes.c_double, vp] + [dp] * 8
     L.vl2_batch_workspace_bytes.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
     L.vl2_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, vp, sz, ctypes.POINTER(ctypes.c_void_p)]
     L.vl2_batch_destroy.argtypes = [vp]
@@ -282,6 +285,38 @@ class Mesh:
                 raise ValueError("step_vjp takes contiguous float64 CUDA tensors")
         _check(self._L.vl2_step_vjp(self._h, float(dt), *[ctypes.c_void_p(t.data_ptr()) for t in lam],
                                    *[ctypes.c_void_p(t.data_ptr()) for t in out]), self._h, lib=self._L)
+        return out
+
+    def tape_bytes(self):
+        n = ctypes.c_size_t()
+        _check(self._L.vl2_tape_bytes(self._h, ctypes.byref(n)), self._h, lib=self._L)
+        return int(n.value)
+
+    def new_tape(self):
+        """A device buffer (uint8 tensor view, 256-byte aligned) that holds one recorded cycle."""
+        import torch
+
+        nbytes = self.tape_bytes()
+        raw = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-raw.data_ptr()) % 256
+        return raw[off:off + nbytes]
+
+    def step_record(self, dt, tape):
+        """One cycle like step(dt), keeping in `tape` (from new_tape) what its adjoint reads."""
+        _check(self._L.vl2_step_record(self._h, float(dt), ctypes.c_void_p(tape.data_ptr())), self._h, lib=self._L)
+
+    def step_vjp_recorded(self, dt, tape, lam, out=None):
+        """J^T lam of the cycle recorded in `tape` (same dt); lam/out = (u, b1, b2, b3) CUDA tensors."""
+        import torch
+
+        if out is None:
+            out = tuple(torch.empty_like(t) for t in lam)
+        for t in tuple(lam) + tuple(out):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+                raise ValueError("step_vjp_recorded takes contiguous float64 CUDA tensors")
+        _check(self._L.vl2_step_vjp_recorded(self._h, float(dt), ctypes.c_void_p(tape.data_ptr()),
+                                             *[ctypes.c_void_p(t.data_ptr()) for t in lam],
+                                             *[ctypes.c_void_p(t.data_ptr()) for t in out]), self._h, lib=self._L)
         return out
 
     def prims_vjp(self, w, lam_u, out=None):

@@ -198,6 +198,53 @@ def test_step_vjp_is_deterministic(vl2):
         np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("ct_delta", [0.0, 1e-2])
+def test_recorded_vjp_equals_step_vjp_bitwise(vl2, ct_delta):
+    """vl2_step_record keeps what the cycle's adjoint reads; vl2_step_vjp_recorded from that tape gives the same
+    bits as vl2_step_vjp at the cycle's starting state, the recorded cycle's state is vl2_step's, and the
+    recorded adjoint leaves the mesh's state alone."""
+    import torch
+
+    prob = inputs.turbulence(n=16, mb=8, seed=21, mach=1.0, beta=10.0)
+    g = vl2.Mesh.from_problem(prob, adjoint=True, ct_delta=ct_delta)
+    dt = g.new_dt()
+    x0 = g.get_cons()
+    rng = np.random.default_rng(4)
+    y = to_dev(tuple(rng.standard_normal(a.shape) for a in x0))
+    ref = [t.cpu().numpy() for t in g.step_vjp(dt, y)]
+    plain = vl2.Mesh.from_problem(prob, ct_delta=ct_delta)
+    plain.step(dt)
+    g.set_cons(*x0)
+    tape = g.new_tape()
+    g.step_record(dt, tape)
+    for a, b in zip(g.get_cons(), plain.get_cons()):
+        np.testing.assert_array_equal(a, b)
+    after = g.get_cons()
+    got = [t.cpu().numpy() for t in g.step_vjp_recorded(dt, tape, y)]
+    for a, b in zip(got, ref):
+        np.testing.assert_array_equal(a, b)
+    for a, b in zip(g.get_cons(), after):
+        np.testing.assert_array_equal(a, b)
+    torch.cuda.synchronize()
+
+
+def test_rollout_gradient_with_and_without_tapes_bitwise(vl2):
+    import torch
+
+    from paper_2005_06651_gb300 import adjoint
+
+    prob = inputs.turbulence(n=16, mb=8, seed=22, mach=1.0, beta=10.0)
+    grads = []
+    for record in (True, False):
+        runner = adjoint.Rollout(prob, nsteps=9, checkpoint_every=3, record=record)
+        v0 = torch.from_numpy(np.ascontiguousarray(prob.w[1:4])).cuda().requires_grad_(True)
+        u = adjoint.rollout(v0, runner)
+        (u[0] ** 2).sum().backward()
+        grads.append(v0.grad.detach().cpu().numpy())
+        runner.mesh.close()
+    np.testing.assert_array_equal(grads[0], grads[1])
+
+
 def test_rollout_gradient_independent_of_checkpoint_interval(vl2):
     """Recomputation from checkpoints replays the forward bit for bit and the adjoint is deterministic, so
     the gradient does not depend on the checkpoint interval, bit for bit."""
