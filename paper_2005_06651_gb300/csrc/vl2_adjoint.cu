@@ -349,18 +349,19 @@ template <int DIR, int REC, int RS>
 __global__ void __launch_bounds__(128) k_adj_flux(Geom g, const double* __restrict__ W, const double* __restrict__ Bn,
                                                   double* LF, double* LR, double* lbn) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
-  const int rx = g.mb[0] + (DIR == 0 ? 1 : 2);
-  const int ry = g.mb[1] + (DIR == 1 ? 1 : 2);
-  const int rz = g.mb[2] + (DIR == 2 ? 1 : 2);
+  const int h = g.flux_halo;  // the faces of the forward flux kernels (transverse halo only with flux_halo)
+  const int rx = g.mb[0] + (DIR == 0 ? 1 : 2 * h);
+  const int ry = g.mb[1] + (DIR == 1 ? 1 : 2 * h);
+  const int rz = g.mb[2] + (DIR == 2 ? 1 : 2 * h);
   const long long per = (long long)rx * ry * rz;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= per * g.nblk) return;
   const int b = (int)(t / per);
   int rem = (int)(t - (long long)b * per);
-  const int i = rem % rx + (DIR == 0 ? NG : NG - 1);
+  const int i = rem % rx + (DIR == 0 ? NG : NG - h);
   rem /= rx;
-  const int j = rem % ry + (DIR == 1 ? NG : NG - 1);
-  const int k = rem / ry + (DIR == 2 ? NG : NG - 1);
+  const int j = rem % ry + (DIR == 1 ? NG : NG - h);
+  const int k = rem / ry + (DIR == 2 ? NG : NG - h);
   const long long c = cell_off(g, k, j, i);
   const long long sd = (DIR == 0) ? 1LL : ((DIR == 1) ? (long long)g.sx : (long long)g.sx * g.sy);
   double* Fl = LF + (long long)b * 7 * g.box + c;
@@ -409,6 +410,56 @@ __global__ void __launch_bounds__(128) k_adj_flux(Geom g, const double* __restri
   }
 }
 
+// Transpose of the forward halo copy (k_flux_halo, meshes with flux_halo = 0): the faces just outside a
+// block's transverse range are copies of its neighbours' faces, so the adjoints the CT transpose left on
+// those copies (mass flux and the two transverse induction fluxes) belong to the owners.  As a gather: each
+// owned d-face on a boundary row of a transverse direction t adds, in a fixed order (t = d+1 then d+2; the
+// copy in the block below, then the one above), the adjoint of its copy in the neighbouring block along t.
+// One thread per owned face; threads off every boundary row return at once.
+__global__ void __launch_bounds__(256) k_adj_flux_halo(Geom g, double* lf0, double* lf1, double* lf2) {
+  if (g.flux_halo) return;
+  long long per[3], tot = 0;
+  for (int d = 0; d < 3; ++d) {
+    per[d] = (long long)(g.mb[0] + (d == 0)) * (g.mb[1] + (d == 1)) * (g.mb[2] + (d == 2));
+    tot += per[d];
+  }
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tot * g.nblk) return;
+  const int b = (int)(t / tot);
+  long long r = t - (long long)b * tot;
+  int d = 0;
+  while (r >= per[d]) r -= per[d++];
+  const int ex = g.mb[0] + (d == 0), ey = g.mb[1] + (d == 1);
+  int li[3] = {(int)(r % ex) + NG, (int)((r / ex) % ey) + NG, (int)(r / ((long long)ex * ey)) + NG};
+  double* LF = d == 0 ? lf0 : (d == 1 ? lf1 : lf2);
+  const int loc[3] = {b % g.nb[0], (b / g.nb[0]) % g.nb[1], b / (g.nb[0] * g.nb[1])};
+  const long long own = (long long)b * 7 * g.box + cell_off(g, li[2], li[1], li[0]);
+  double acc[3] = {0.0, 0.0, 0.0};
+  bool any = false;
+  for (int k = 1; k <= 2; ++k) {
+    const int tq = (d + k) % 3;
+    for (int side = 0; side < 2; ++side) {
+      // side 0: our lower row is copied into the upper halo of the block below; side 1: our upper row into
+      // the lower halo of the block above
+      if (li[tq] != (side ? NG + g.mb[tq] - 1 : NG)) continue;
+      int nl[3] = {loc[0], loc[1], loc[2]};
+      nl[tq] = (nl[tq] + (side ? 1 : g.nb[tq] - 1)) % g.nb[tq];
+      const int bs = (nl[2] * g.nb[1] + nl[1]) * g.nb[0] + nl[0];
+      int hi_[3] = {li[0], li[1], li[2]};
+      hi_[tq] = side ? NG - 1 : NG + g.mb[tq];
+      const long long o = (long long)bs * 7 * g.box + cell_off(g, hi_[2], hi_[1], hi_[0]);
+      acc[0] += LF[o];
+      acc[1] += LF[o + 5 * g.box];
+      acc[2] += LF[o + 6 * g.box];
+      any = true;
+    }
+  }
+  if (!any) return;
+  LF[own] += acc[0];
+  LF[own + 5 * g.box] += acc[1];
+  LF[own + 6 * g.box] += acc[2];
+}
+
 // The van Leer slopes' share of the face-state adjoints of one PLM sweep, formed once per slope: for the slope
 // delta_j of cell j (on q_{j-1}, q_j, q_{j+1}), lam delta_j = a(j+1)/2 - r(j)/2 times its three partial
 // derivatives, stored as the contributions PM (to q_{j-1}), P0 (to q_j) and PP (to q_{j+1}) that
@@ -418,13 +469,17 @@ __global__ void __launch_bounds__(128) k_adj_slopes(Geom g, const double* __rest
                                                     const double* __restrict__ LA, const double* __restrict__ LR,
                                                     double* PM, double* P0, double* PP) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
-  const int nx = g.mb[0] + 2, ny = g.mb[1] + 2, nz = g.mb[2] + 2;  // cells NG-1 .. NG+mb in every direction
+  // cells NG-1 .. NG+mb along the sweep; transversally the rows of the flux kernels' faces
+  const int h = g.flux_halo;
+  const int nx = g.mb[0] + (DIR == 0 ? 2 : 2 * h), ny = g.mb[1] + (DIR == 1 ? 2 : 2 * h),
+            nz = g.mb[2] + (DIR == 2 ? 2 : 2 * h);
   const long long per = (long long)nx * ny * nz;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= per * g.nblk) return;
   const int b = (int)(t / per);
   int rem = (int)(t - (long long)b * per);
-  const int li[3] = {rem % nx + NG - 1, (rem / nx) % ny + NG - 1, rem / (nx * ny) + NG - 1};
+  const int li[3] = {rem % nx + (DIR == 0 ? NG - 1 : NG - h), (rem / nx) % ny + (DIR == 1 ? NG - 1 : NG - h),
+                     rem / (nx * ny) + (DIR == 2 ? NG - 1 : NG - h)};
   const long long c = cell_off(g, li[2], li[1], li[0]);
   const long long sd = (DIR == 0) ? 1LL : ((DIR == 1) ? (long long)g.sx : (long long)g.sx * g.sy);
   const int id = li[DIR];
@@ -468,15 +523,16 @@ __global__ void __launch_bounds__(128) k_adj_flux_cells(Geom g, const double* __
                                                         const double* __restrict__ PP, double* lw) {
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   constexpr int H = (REC == REC_DC) ? 1 : 2;  // cells NG-H .. NG+mb-1+H along the sweep
-  const int nx = g.mb[0] + (DIR == 0 ? 2 * H : 2), ny = g.mb[1] + (DIR == 1 ? 2 * H : 2),
-            nz = g.mb[2] + (DIR == 2 ? 2 * H : 2);
+  const int h = g.flux_halo;                  // transversally the rows of the flux kernels' faces
+  const int nx = g.mb[0] + (DIR == 0 ? 2 * H : 2 * h), ny = g.mb[1] + (DIR == 1 ? 2 * H : 2 * h),
+            nz = g.mb[2] + (DIR == 2 ? 2 * H : 2 * h);
   const long long per = (long long)nx * ny * nz;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= per * g.nblk) return;
   const int b = (int)(t / per);
   int rem = (int)(t - (long long)b * per);
-  const int li[3] = {rem % nx + (DIR == 0 ? NG - H : NG - 1), (rem / nx) % ny + (DIR == 1 ? NG - H : NG - 1),
-                     rem / (nx * ny) + (DIR == 2 ? NG - H : NG - 1)};
+  const int li[3] = {rem % nx + (DIR == 0 ? NG - H : NG - h), (rem / nx) % ny + (DIR == 1 ? NG - H : NG - h),
+                     rem / (nx * ny) + (DIR == 2 ? NG - H : NG - h)};
   const long long c = cell_off(g, li[2], li[1], li[0]);
   const long long sd = (DIR == 0) ? 1LL : ((DIR == 1) ? (long long)g.sx : (long long)g.sx * g.sy);
   const int id = li[DIR];
@@ -857,23 +913,33 @@ cudaError_t adj_ct(const Geom& g, const AdjArrays& j, const double* W, const dou
   return cudaGetLastError();
 }
 
+cudaError_t adj_flux_halo(const Geom& g, const AdjArrays& j, cudaStream_t st) {
+  if (g.flux_halo) return cudaSuccess;
+  long long n = 0;
+  for (int d = 0; d < 3; ++d) n += (long long)(g.mb[0] + (d == 0)) * (g.mb[1] + (d == 1)) * (g.mb[2] + (d == 2));
+  n *= g.nblk;
+  k_adj_flux_halo<<<grid_of(n, 256), 256, 0, st>>>(g, j.lf[0], j.lf[1], j.lf[2]);
+  return cudaGetLastError();
+}
+
 template <int DIR, int REC, int RS>
 static cudaError_t adj_flux_one(const Geom& g, const AdjArrays& j, const double* W, const double* Bn, double* lbn,
                                 cudaStream_t st) {
   long long n = g.nblk;
-  for (int q = 0; q < 3; ++q) n *= g.mb[q] + (q == DIR ? 1 : 2);
+  for (int q = 0; q < 3; ++q) n *= g.mb[q] + (q == DIR ? 1 : 2 * g.flux_halo);
   k_adj_flux<DIR, REC, RS><<<grid_of(n, 128), 128, 0, st>>>(g, W, Bn, j.lf[DIR], j.lr, lbn);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (REC == REC_PLM) {
-    const long long ns = (long long)g.nblk * (g.mb[0] + 2) * (g.mb[1] + 2) * (g.mb[2] + 2);
+    long long ns = g.nblk;
+    for (int q = 0; q < 3; ++q) ns *= g.mb[q] + (q == DIR ? 2 : 2 * g.flux_halo);
     k_adj_slopes<DIR><<<grid_of(ns, 128), 128, 0, st>>>(g, W, j.lf[DIR], j.lr, j.ps[0], j.ps[1], j.ps[2]);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   constexpr int H = (REC == REC_DC) ? 1 : 2;
   long long nc = g.nblk;
-  for (int q = 0; q < 3; ++q) nc *= g.mb[q] + (q == DIR ? 2 * H : 2);
+  for (int q = 0; q < 3; ++q) nc *= g.mb[q] + (q == DIR ? 2 * H : 2 * g.flux_halo);
   k_adj_flux_cells<DIR, REC><<<grid_of(nc, 128), 128, 0, st>>>(g, W, j.lf[DIR], j.lr, j.ps[0], j.ps[1], j.ps[2],
                                                               j.lw);
   return cudaGetLastError();

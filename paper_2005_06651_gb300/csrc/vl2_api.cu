@@ -702,6 +702,7 @@ vl2_status vjp_reverse(vl2_mesh* m, double dt, const CycleInputs& in, const doub
   // corrector: U0 <- U0 + dt L_PLM(U1)
   VL2_CHECK(m, vl2::adj_update(g, j, 0, 0, dt, st));
   VL2_CHECK(m, vl2::adj_ct(g, j, in.w1, in.m2, in.m2_stride, in.m2_e5, in.m2_e6, st));
+  VL2_CHECK(m, vl2::adj_flux_halo(g, j, st));
   VL2_CHECK(m, vl2::adj_fluxes(g, j, vl2::REC_PLM, m->p.riemann, in.w1, in.b1, 1, st));
   VL2_CHECK(m, vl2::adj_prim(g, j, in.w1, 1, st));
   VL2_CHECK(m, vl2::adj_ghosts(g, j, 1, st));
@@ -709,11 +710,14 @@ vl2_status vjp_reverse(vl2_mesh* m, double dt, const CycleInputs& in, const doub
   VL2_CHECK(m, cudaMemsetAsync(j.lw, 0, 8 * per, st));
   VL2_CHECK(m, vl2::adj_update(g, j, 1, 0, 0.5 * dt, st));
   VL2_CHECK(m, vl2::adj_ct(g, j, in.w0, in.m1, in.m1_stride, g.box, 2 * g.box, st));
+  VL2_CHECK(m, vl2::adj_flux_halo(g, j, st));
   VL2_CHECK(m, vl2::adj_fluxes(g, j, vl2::REC_DC, m->p.riemann, in.w0, in.b0, 0, st));
   VL2_CHECK(m, vl2::adj_prim(g, j, in.w0, 0, st));
   VL2_CHECK(m, vl2::adj_ghosts(g, j, 0, st));
   VL2_CHECK(m, vl2::adj_gather_in(g, j, out_u, out_b1, out_b2, out_b3, st));
-  m->launches += 32;  // scatter, 2 x (update, CT, 3 x 2 flux, prim, 3 x 2 ghost passes), gather
+  // scatter, 2 x (update, CT, halo transpose, 3 x 2 flux (+3 slope passes for PLM), prim, 3 x 2 ghost passes),
+  // gather
+  m->launches += 32 + 3 + (g.flux_halo ? 0 : 2);
   return VL2_OK;
 }
 

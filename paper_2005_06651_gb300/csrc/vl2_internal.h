@@ -181,6 +181,8 @@ cudaError_t adj_scatter_out(const Geom& g, const AdjArrays& j, const double* gu,
 cudaError_t adj_update(const Geom& g, const AdjArrays& j, int out_reg, int base_reg, double h, cudaStream_t st);
 cudaError_t adj_ct(const Geom& g, const AdjArrays& j, const double* W, const double* const* mflux, long long mstride,
                    long long e5off, long long e6off, cudaStream_t st);
+// transpose of the forward halo copy (no-op when g.flux_halo): owner faces collect their copies' adjoints
+cudaError_t adj_flux_halo(const Geom& g, const AdjArrays& j, cudaStream_t st);
 cudaError_t adj_fluxes(const Geom& g, const AdjArrays& j, int recon, int riemann, const double* W,
                        const double* const* Bn, int lam_reg, cudaStream_t st);
 cudaError_t adj_prim(const Geom& g, const AdjArrays& j, const double* W, int lam_reg, cudaStream_t st);
