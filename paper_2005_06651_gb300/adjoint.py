@@ -4,7 +4,8 @@ The forward pass advances the mesh through the C ABI and keeps the conserved sta
 (k ~ sqrt(N) by default) plus the time steps it used.  The backward pass walks the segments in reverse:
 it restores a segment's checkpoint (vl2_set_cons) and replays the segment's cycles with vl2_step_record,
 which keeps in one tape per cycle what that cycle's adjoint reads; vl2_step_vjp_recorded then applies the
-hand-written adjoint of each cycle from its tape, last cycle first.  Each cycle is thus computed once more
+hand-written adjoint of each cycle from its tape, last cycle first.  The forward pass records the last
+segment itself, so the backward pass starts without a replay.  Each cycle is thus computed once more
 in the backward pass, not twice.  (With record=False the replay keeps only the states, and vl2_step_vjp
 recomputes each cycle's intermediates from its state.)  The adjoint of the initial conserved state is
 then taken back to the initial velocity (vl2_prims_vjp).  Time steps are those of the forward pass, held fixed (no derivative through the
@@ -39,6 +40,7 @@ class Rollout:
         self.w0 = None
         self.timing = {}
         self.record = bool(record)
+        self.tail_recorded = False
         self.tapes = [self.mesh.new_tape() for _ in range(self.k)] if self.record else []
 
     def _state(self):
@@ -54,12 +56,18 @@ class Rollout:
         self.w0 = w
         m.set_prims(w, *self.b)
         self.dts, self.checkpoints = [], {}
+        # the last segment is recorded on the way (its tapes are the first the backward pass needs)
+        last = ((self.nsteps - 1) // self.k) * self.k
         for s in range(self.nsteps):
             if s % self.k == 0:
                 self.checkpoints[s] = self._state()
             dt = self.fixed_dts[s] if self.fixed_dts is not None else m.new_dt()
             self.dts.append(dt)
-            m.step(dt)
+            if self.record and s >= last:
+                m.step_record(dt, self.tapes[s - last])
+            else:
+                m.step(dt)
+        self.tail_recorded = self.record
         return self._state()[0]
 
     def run_backward(self, grad_u):
@@ -69,14 +77,18 @@ class Rollout:
         starts = sorted(self.checkpoints)
         for s0 in reversed(starts):
             s1 = min(s0 + self.k, self.nsteps)
-            m.set_cons(*self.checkpoints[s0])
             if self.record:
-                for s in range(s0, s1):
-                    m.step_record(self.dts[s], self.tapes[s - s0])
+                if s1 == self.nsteps and self.tail_recorded:
+                    self.tail_recorded = False  # the forward pass recorded this segment
+                else:
+                    m.set_cons(*self.checkpoints[s0])
+                    for s in range(s0, s1):
+                        m.step_record(self.dts[s], self.tapes[s - s0])
                 for s in reversed(range(s0, s1)):
                     m.step_vjp_recorded(self.dts[s], self.tapes[s - s0], lam, out)
                     lam, out = out, lam
                 continue
+            m.set_cons(*self.checkpoints[s0])
             states = []
             for s in range(s0, s1):  # recompute the states before each cycle of the segment
                 states.append(self.checkpoints[s0] if s == s0 else self._state())

@@ -672,7 +672,11 @@ __device__ __forceinline__ bool moved_along(const Geom& g, int kind, const int* 
   return kind == 1 + q && li[q] == NG + g.mb[q] && locq < g.nb[q] - 1 && ghost_elsewhere(g, kind, li, q);
 }
 
-__global__ void k_adj_ghost_gather(Geom g, int pass, double* lu, double* lb0, double* lb1, double* lb2) {
+// PASS (the direction of the one-dimensional pass for the cells; the face kinds rotate) is a template
+// parameter, so every direction index below is a compile-time constant and the small index arrays stay in
+// registers.
+template <int PASS>
+__global__ void __launch_bounds__(256) k_adj_ghost_gather(Geom g, double* lu, double* lb0, double* lb1, double* lb2) {
   const int ex = g.mb[0] + 2 * NG + 1, ey = g.mb[1] + 2 * NG + 1, ez = g.mb[2] + 2 * NG + 1;
   const long long per = (long long)ex * ey * ez;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -685,9 +689,11 @@ __global__ void k_adj_ghost_gather(Geom g, int pass, double* lu, double* lb0, do
   const long long stride[3] = {1LL, (long long)g.sx, (long long)g.sx * g.sy};
   const long long bstride[3] = {1LL, (long long)g.nb[0], (long long)g.nb[0] * g.nb[1]};
   const long long c = cell_off(g, li[2], li[1], li[0]);
+#pragma unroll
   for (int kind = 0; kind < 4; ++kind) {
-    const int q = kind == 0 ? pass : (kind - 1 + pass) % 3;
+    const int q = kind == 0 ? PASS : (kind - 1 + PASS) % 3;
     bool ok = true;
+#pragma unroll
     for (int r = 0; r < 3; ++r) ok = ok && li[r] <= hi_index(g, kind, r);
     if (!ok || moved_along(g, kind, li, q, loc[q])) continue;  // targets only
     const bool face = (kind == 1 + q);
@@ -700,6 +706,7 @@ __global__ void k_adj_ghost_gather(Geom g, int pass, double* lu, double* lb0, do
     auto take = [&](long long blk2, long long c2) {
       if (kind == 0) {
         const double* U2 = lu + blk2 * 5 * g.box + c2;
+#pragma unroll
         for (int v = 0; v < 5; ++v) acc[v] += U2[(long long)v * g.box];
       } else {
         acc[0] += (kind == 1 ? lb0 : (kind == 2 ? lb1 : lb2))[blk2 * g.box + c2];
@@ -713,18 +720,20 @@ __global__ void k_adj_ghost_gather(Geom g, int pass, double* lu, double* lb0, do
     // here: a ghost of block bq has global index up to bq mb + mb + NG, at most R = 1 + (NG + mb) / mb
     // blocks away (R <= 4 for mb >= 1)
     const int R = 1 + (NG + g.mb[q]) / g.mb[q];
-    int seen[9];
-    int nseen = 0;
-    for (int dl = -R; dl <= R; ++dl) {
+    auto block_at = [&](int dl) -> int {  // block along q at offset dl (wrapped), or -1 beyond an outflow edge
       int bq = loc[q] + dl;
       if (bq < 0 || bq >= g.nb[q]) {
-        if (g.bc[dl < 0 ? 2 * q : 2 * q + 1] != BC_PERIODIC) continue;
+        if (g.bc[dl < 0 ? 2 * q : 2 * q + 1] != BC_PERIODIC) return -1;
         bq = ((bq % g.nb[q]) + g.nb[q]) % g.nb[q];
       }
-      bool dup = false;
-      for (int k = 0; k < nseen; ++k) dup = dup || seen[k] == bq;
+      return bq;
+    };
+    for (int dl = -R; dl <= R; ++dl) {
+      const int bq = block_at(dl);
+      if (bq < 0) continue;
+      bool dup = false;  // an earlier offset that wraps onto the same block
+      for (int d2 = -R; d2 < dl; ++d2) dup = dup || block_at(d2) == bq;
       if (dup) continue;
-      seen[nseen++] = bq;
       const int hi = hi_index(g, kind, q), ha = hi_active(g, kind, q);
       // the ghosts along q only: indices 0 .. NG-1, then ha+1 .. hi (in that order)
       for (int gl = 0; gl <= hi; gl = (gl == NG - 1) ? ha + 1 : gl + 1) {
@@ -737,6 +746,7 @@ __global__ void k_adj_ghost_gather(Geom g, int pass, double* lu, double* lb0, do
     if (!got) continue;
     if (kind == 0) {
       double* U = lu + (long long)b * 5 * g.box + c;
+#pragma unroll
       for (int v = 0; v < 5; ++v) U[(long long)v * g.box] += acc[v];
     } else {
       (kind == 1 ? lb0 : (kind == 2 ? lb1 : lb2))[(long long)b * g.box + c] += acc[0];
@@ -975,8 +985,15 @@ cudaError_t adj_prim(const Geom& g, const AdjArrays& j, const double* W, int lam
 cudaError_t adj_ghosts(const Geom& g, const AdjArrays& j, int lam_reg, cudaStream_t st) {
   const long long n = (long long)(g.mb[0] + 2 * NG + 1) * (g.mb[1] + 2 * NG + 1) * (g.mb[2] + 2 * NG + 1) * g.nblk;
   for (int pass = 0; pass < 3; ++pass) {
-    k_adj_ghost_gather<<<grid_of(n, AT), AT, 0, st>>>(g, pass, j.lu[lam_reg], j.lb[lam_reg][0], j.lb[lam_reg][1],
-                                                      j.lb[lam_reg][2]);
+    if (pass == 0)
+      k_adj_ghost_gather<0><<<grid_of(n, AT), AT, 0, st>>>(g, j.lu[lam_reg], j.lb[lam_reg][0], j.lb[lam_reg][1],
+                                                           j.lb[lam_reg][2]);
+    else if (pass == 1)
+      k_adj_ghost_gather<1><<<grid_of(n, AT), AT, 0, st>>>(g, j.lu[lam_reg], j.lb[lam_reg][0], j.lb[lam_reg][1],
+                                                           j.lb[lam_reg][2]);
+    else
+      k_adj_ghost_gather<2><<<grid_of(n, AT), AT, 0, st>>>(g, j.lu[lam_reg], j.lb[lam_reg][0], j.lb[lam_reg][1],
+                                                           j.lb[lam_reg][2]);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_adj_ghost_clear<<<grid_of(n, AT), AT, 0, st>>>(g, pass, j.lu[lam_reg], j.lb[lam_reg][0], j.lb[lam_reg][1],
