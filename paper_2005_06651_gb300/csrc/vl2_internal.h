@@ -87,19 +87,28 @@ struct Dispatch {
 
 #ifdef __CUDACC__
 // Resolve the mesh and tile of this CTA (single mesh: the launch argument and blockIdx.x; batch: the
-// CTA's work item) and stage the mesh view in shared memory.  Every thread of the CTA must call it.
+// CTA's work item) and stage the mesh view in shared memory.  Every thread of the CTA must call it.  The
+// view is copied as 8-byte words, one per thread of the first 64 (every launch that calls this has at least
+// 64 threads per CTA), so that the barrier behind it waits for one round of loads rather than for one
+// thread's serial copy of the whole view.
+static_assert(sizeof(MeshView) % 8 == 0, "the mesh view is staged in 8-byte words");
+static_assert(sizeof(MeshView) <= 64 * 8, "the mesh view is staged by the first 64 threads (every CTA has >= 64)");
 __device__ __forceinline__ const MeshView& stage_view(MeshView& sv, const MeshView& single, const MeshView* views,
                                                       const WorkItem* work, int& tile, int* box = nullptr) {
+  const MeshView* src = &single;
   if (work) {
     const WorkItem w = work[blockIdx.x];
     tile = w.tile;
     if (box) *box = w.box;
-    if (threadIdx.x == 0) sv = views[w.box];
+    src = views + w.box;
   } else {
     tile = blockIdx.x;
     if (box) *box = 0;
-    if (threadIdx.x == 0) sv = single;
   }
+  constexpr unsigned NW = (unsigned)(sizeof(MeshView) / 8);
+  if (threadIdx.x < NW)
+    reinterpret_cast<unsigned long long*>(&sv)[threadIdx.x] =
+        reinterpret_cast<const unsigned long long*>(src)[threadIdx.x];
   __syncthreads();
   return sv;
 }
