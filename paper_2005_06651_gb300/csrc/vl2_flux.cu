@@ -14,7 +14,7 @@ namespace vl2 {
 // k_flux_halo copies those from the neighbouring blocks).
 // ------------------------------------------------------------------------------------------------
 template <int DIR, int REC, int RS, class T>
-__global__ void __launch_bounds__(256) k_flux(MeshView single, const MeshView* views, const WorkItem* work, int reg) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_flux(MeshView single, const MeshView* views, const WorkItem* work, int reg) {
   __shared__ MeshView sv;
   int tile;
   const MeshView& V = stage_view(sv, single, views, work, tile);
@@ -79,7 +79,7 @@ struct LineMap {
 };
 
 template <int DIR, int RS, class T, int REC>
-__global__ void __launch_bounds__(256, 2) k_flux_plm(MeshView single, const MeshView* views, const WorkItem* work,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_flux_plm(MeshView single, const MeshView* views, const WorkItem* work,
                                                      int reg, int P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
