@@ -44,8 +44,9 @@ typedef enum vl2_status {
   VL2_E_ARG = 1,      /* invalid argument (null pointer, bad size, inconsistent parameters) */
   VL2_E_CUDA = 2,     /* a CUDA runtime call or kernel launch failed */
   VL2_E_NONPHYS = 3,  /* a density or pressure floor fired (value floored and counted), or dt not finite */
-  VL2_E_TIMEOUT = 4,  /* reserved for a bounded device-side wait that expired; no kernel of this library
-                         waits on another (no spin-waits, no inter-CTA barriers), so no call returns it */
+  VL2_E_TIMEOUT = 4,  /* a bounded device-side wait expired: the TMA-staged PLM sweeps wait (with a limit of
+                         about a quarter second) for each tile's bulk copy; if one never lands the CTA skips
+                         its tiles, the step's fluxes are incomplete, and the next vl2_new_dt returns this */
   VL2_E_STATE = 5,    /* call not valid in the mesh's current state */
   VL2_E_NOMEM = 6     /* workspace smaller than vl2_workspace_bytes() */
 } vl2_status;
@@ -299,6 +300,13 @@ enum {
  * Errors: VL2_E_ARG (fn out of range, n < 0, NULL array), VL2_E_CUDA. */
 vl2_status vl2_debug_arith(int fn, long long n, const double* x, double* out, void* stream);
 
+/* Test aid for the bounded waits (the paper has no counterpart): one thread waits, with the wait the
+ * TMA-staged kernels use, at most `polls` times (each a try-wait and a 256 ns sleep) on an mbarrier phase
+ * that nothing completes, then writes out[0] = 1 (device int owned by the caller) when it gave up, which is
+ * the expected outcome; the kernel then returns and the context stays usable.  Enqueued on `stream`.
+ * Errors: VL2_E_ARG (out NULL, polls outside 1 .. 2^20), VL2_E_CUDA. */
+vl2_status vl2_debug_wait_timeout(int polls, int* out, void* stream);
+
 /* Kernel kinds of vl2_profile_read. */
 enum {
   VL2_K_PRIM = 0,     /* cons -> prim on every cell (with the fused CFL reduction after a cycle) */
@@ -326,6 +334,22 @@ vl2_status vl2_profile_read(vl2_mesh* mesh, int kind, double* ms, long long* lau
 /* Number of CUDA kernels this mesh has launched since creation (every launch, profiled or not). */
 vl2_status vl2_launch_count(const vl2_mesh* mesh, long long* n);
 
+/* Launch shapes of this mesh's face-flux kernels (Sec. 3.2.1-3.2.2 sweeps); they change no result bit.
+ * dc_threads: CTA size of the donor-cell predictor sweeps, 64, 128 or 256.  plm_lines: lines of faces per
+ * tile of the PLM corrector sweeps, 4, 8 or 16.  tma: 0 takes the line-tile PLM kernel (one CTA per tile,
+ * primitives loaded by each thread); 1 takes the persistent PLM kernel, whose CTAs (as many as fit on the
+ * GPU) walk the tiles and stage each tile's primitives (the mb+4 cells along the sweep, the tile's lines,
+ * all 8 variables) in shared memory with one TMA bulk tensor copy, the next tile's copy in flight while the
+ * current one is solved.  tma = 1 needs the tensor maps vl2_mesh_create encodes for meshes with two ghost
+ * layers, and a tile that fits in shared memory; elsewhere, and for other reconstructions, the line-tile
+ * kernel runs.  A new mesh starts with (128, 16, 1) in the mixed precision and (128, 16, 0) in FP64, the
+ * faster of the two PLM kernels on GB300 for each.  Errors: VL2_E_ARG (NULL mesh, values outside the sets). */
+vl2_status vl2_set_flux_shape(vl2_mesh* mesh, int dc_threads, int plm_lines, int tma);
+
+/* The launch shapes set above; tma_active (may be NULL) receives 1 when the PLM sweeps actually take the
+ * TMA-staged kernel with these shapes.  Outputs may be NULL.  Errors: VL2_E_ARG. */
+vl2_status vl2_get_flux_shape(const vl2_mesh* mesh, int* dc_threads, int* plm_lines, int* tma, int* tma_active);
+
 /* ---- Batched form ----------------------------------------------------------------------------
  * Many independent meshes ("boxes", any sizes; the paper advances each MeshBlock independently between
  * exchanges, Sec. 2.1, 2.6) advanced together: each kernel of the VL2 cycle is one launch over a
@@ -343,15 +367,26 @@ typedef struct vl2_batch vl2_batch;
  * Errors: VL2_E_ARG (NULL, n <= 0, meshes that do not share the options above). */
 vl2_status vl2_batch_workspace_bytes(vl2_mesh* const* meshes, int n, size_t* bytes);
 
-/* Create the batch (builds and uploads its work lists).  Errors: VL2_E_ARG, VL2_E_NOMEM, VL2_E_CUDA. */
+/* Create the batch (builds and uploads its work lists).  It starts with the first mesh's flux launch shapes
+ * (vl2_set_flux_shape), the TMA-staged PLM kernel only where it serves every mesh, so that by default each
+ * box advances with the kernels it takes alone.  Errors: VL2_E_ARG, VL2_E_NOMEM, VL2_E_CUDA. */
 vl2_status vl2_batch_create(vl2_mesh* const* meshes, int n, void* workspace, size_t bytes, vl2_batch** out);
 
 vl2_status vl2_batch_destroy(vl2_batch* batch);
 
 /* Pick the launch shapes of the flux kernels by timing them on the batch's current state (donor-cell CTA
- * size in {64, 128, 256}, PLM lines per CTA in {4, 8, 16}); the state is not changed.  Outputs may be
- * NULL.  Blocks.  Errors: VL2_E_STATE, VL2_E_CUDA. */
+ * size in {64, 128, 256}, PLM lines per CTA in {4, 8, 16}, and the PLM kernel: line tiles or persistent
+ * TMA-staged tiles, see vl2_set_flux_shape); the state is not changed.  Outputs may be NULL.  Blocks.
+ * Errors: VL2_E_STATE, VL2_E_CUDA. */
 vl2_status vl2_batch_autotune(vl2_batch* batch, int* dc_threads, int* plm_lines);
+
+/* The batch's current flux launch shapes (as vl2_get_flux_shape).  Outputs may be NULL.  Errors: VL2_E_ARG. */
+vl2_status vl2_batch_flux_shape(const vl2_batch* batch, int* dc_threads, int* plm_lines, int* tma);
+
+/* Set the batch's flux launch shapes (values as vl2_set_flux_shape) and rebuild its work lists; a captured
+ * graph is dropped.  Errors: VL2_E_ARG (values outside the sets, or tma = 1 where the TMA-staged kernel does
+ * not serve every mesh of the batch), VL2_E_CUDA. */
+vl2_status vl2_batch_set_flux_shape(vl2_batch* batch, int dc_threads, int plm_lines, int tma);
 
 /* One VL2 cycle of every box with the given per-box steps dt[n] (host or device, see `where`); the same
  * arithmetic as vl2_step on each mesh.  Errors: VL2_E_ARG (dt not finite and positive), VL2_E_STATE,

@@ -224,6 +224,7 @@ struct Plan {
   size_t off_u[2], off_b[2][3], off_w, off_f[3], off_e[3], off_ec, off_stage, off_red, off_scal, total;
   size_t off_s[2], off_cs, off_fsc[3];  // passive scalars (empty when ns = 0)
   size_t off_acc;                       // forcing acceleration (empty without params.forcing)
+  size_t off_tmw;                       // tensor maps of w for the TMA-staged PLM sweeps (vl2::TMA_MAPS x 128 B)
   size_t stage_elems;
   size_t off_adj;  // start of the adjoint arrays (59 FP64 arrays per block, 65 with ct_delta) when requested
 };
@@ -268,6 +269,8 @@ Plan make_plan(const Geom& g, int precision, int adjoint, int forcing) {
   }
   pl.off_acc = o;
   if (forcing) o = align256(o + 3 * per);
+  pl.off_tmw = o;
+  o = align256(o + (size_t)vl2::TMA_MAPS * 128);
   const long long nc = ncells(g);
   long long st = 5 * nc + nfaces_total(g);
   st = std::max(st, (long long)g.ns * nc);
@@ -505,13 +508,22 @@ vl2_status vl2_mesh_create(const vl2_params* params, void* workspace, size_t byt
               ok ? (q[2] * g.nb[1] + q[1]) * g.nb[0] + q[0] : -1;
         }
   }
+  // tensor maps of the primitives for the TMA-staged PLM sweeps (host-encoded once: w never moves)
+  alignas(128) unsigned char maps[vl2::TMA_MAPS * 128];
+  const char* why = nullptr;
+  const bool have_maps = vl2::encode_w_maps(g, m->a.w, m->a.mixed ? 4 : 8, maps, &why);
+  m->a.tmw = have_maps ? base + pl.off_tmw : nullptr;
+  m->fs.plm_tma = have_maps && m->a.mixed ? 1 : 0;
   cudaError_t e = vl2::prepare_kernel_attributes();
   if (e == cudaSuccess) e = cudaMemsetAsync(workspace, 0, pl.total, m->st);
+  if (e == cudaSuccess && have_maps) e = cudaMemcpyAsync(base + pl.off_tmw, maps, sizeof(maps), cudaMemcpyHostToDevice, m->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->st);
   if (e != cudaSuccess) {
     delete m;
     return fail(nullptr, VL2_E_CUDA, std::string("workspace clear: ") + cudaGetErrorString(e));
   }
+  vl2::prime_flux_tma(m->view(), m->rec(), m->p.riemann == VL2_HLLD ? vl2::RS_HLLD : vl2::RS_HLLE, m->fs, m->max_mb(),
+                      m->st);
   *out = m;
   return VL2_OK;
 }
@@ -987,10 +999,14 @@ vl2_status vl2_new_dt(vl2_mesh* m, double* dt_out) {
     m->w_valid = true;
     m->dt_pending = true;
   }
-  unsigned long long sc[2];
+  unsigned long long sc[4];
   VL2_CHECK(m, cudaMemcpyAsync(sc, m->a.scal, sizeof(sc), cudaMemcpyDeviceToHost, m->st));
   vl2_status s = sync(m);
   if (s != VL2_OK) return s;
+  if (sc[vl2::SC_TIMEOUT]) {
+    VL2_CHECK(m, cudaMemsetAsync(m->a.scal + vl2::SC_TIMEOUT, 0, sizeof(unsigned long long), m->st));
+    return fail(m, VL2_E_TIMEOUT, "a TMA tile copy did not land within its bounded wait; the step is incomplete");
+  }
   double rate;
   std::memcpy(&rate, &sc[vl2::SC_MAXRATE], sizeof(rate));
   const double dt = m->p.cfl / rate;
@@ -1159,6 +1175,27 @@ vl2_status vl2_launch_count(const vl2_mesh* m, long long* n) {
   return VL2_OK;
 }
 
+vl2_status vl2_set_flux_shape(vl2_mesh* m, int dc_threads, int plm_lines, int tma) {
+  if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
+  if ((dc_threads != 64 && dc_threads != 128 && dc_threads != 256) ||
+      (plm_lines != 4 && plm_lines != 8 && plm_lines != 16) || (tma != 0 && tma != 1))
+    return fail(m, VL2_E_ARG, "dc_threads must be 64, 128 or 256, plm_lines 4, 8 or 16, tma 0 or 1");
+  m->fs.dc_threads = dc_threads;
+  m->fs.plm_lines = plm_lines;
+  m->fs.plm_tma = tma;
+  vl2::prime_flux_tma(m->view(), m->rec(), m->p.riemann == VL2_HLLD ? vl2::RS_HLLD : vl2::RS_HLLE, m->fs, m->max_mb(), m->st);
+  return VL2_OK;
+}
+
+vl2_status vl2_get_flux_shape(const vl2_mesh* m, int* dc_threads, int* plm_lines, int* tma, int* tma_active) {
+  if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
+  if (dc_threads) *dc_threads = m->fs.dc_threads;
+  if (plm_lines) *plm_lines = m->fs.plm_lines;
+  if (tma) *tma = m->fs.plm_tma;
+  if (tma_active) *tma_active = vl2::flux_tma_applies(m->view(), vl2::REC_PLM, m->fs, m->max_mb()) && m->rec() == VL2_PLM;
+  return VL2_OK;
+}
+
 const char* vl2_last_error(const vl2_mesh* mesh) { return mesh ? mesh->err.c_str() : g_err.c_str(); }
 
 }  // extern "C"
@@ -1229,6 +1266,7 @@ long long batch_tiles(const vl2_mesh* m, int w, const vl2::FluxShape& fs, int ma
   if (w == vl2_batch::W_HALO) return vl2::tiles_flux_halo(g);
   if (w < vl2_batch::W_PLM) return vl2::tiles_flux_dc(g, w - vl2_batch::W_DC, fs);
   const int d = w - vl2_batch::W_PLM;
+  if (fs.plm_tma) return vl2::tiles_flux_tma(g, d, fs.plm_lines);  // set only where every mesh qualifies
   vl2::FluxShape f2 = fs;
   f2.plm_lines = vl2::plm_lines_for(g, d, fs, max_mb, m->rec());
   return vl2::tiles_flux_plm(g, d, f2);
@@ -1238,15 +1276,24 @@ long long batch_tiles(const vl2_mesh* m, int w, const vl2::FluxShape& fs, int ma
 size_t batch_capacity(const std::vector<vl2_mesh*>& ms, int w, int max_mb) {
   size_t best = 0;
   for (int dc : kDcCandidates)
-    for (int pl : kPlmCandidates) {
-      vl2::FluxShape fs;
-      fs.dc_threads = dc;
-      fs.plm_lines = pl;
-      size_t tot = 0;
-      for (const vl2_mesh* m : ms) tot += (size_t)batch_tiles(m, w, fs, max_mb);
-      best = std::max(best, tot);
-    }
+    for (int pl : kPlmCandidates)
+      for (int tma = 0; tma < 2; ++tma) {
+        vl2::FluxShape fs;
+        fs.dc_threads = dc;
+        fs.plm_lines = pl;
+        fs.plm_tma = tma;
+        size_t tot = 0;
+        for (const vl2_mesh* m : ms) tot += (size_t)batch_tiles(m, w, fs, max_mb);
+        best = std::max(best, tot);
+      }
   return best;
+}
+
+// the TMA-staged PLM sweeps serve a batch only when every mesh of it qualifies under fs
+bool batch_tma_ok(const vl2_batch* B, const vl2::FluxShape& fs) {
+  for (const vl2_mesh* m : B->meshes)
+    if (!vl2::flux_tma_applies(m->view(), B->recon, fs, B->max_mb)) return false;
+  return true;
 }
 
 vl2_status batch_check(vl2_mesh* const* meshes, int n, std::string& msg) {
@@ -1420,6 +1467,11 @@ vl2_status vl2_batch_create(vl2_mesh* const* meshes, int n, void* workspace, siz
   B->riemann = meshes[0]->p.riemann;
   B->recon = meshes[0]->rec();
   for (vl2_mesh* m : B->meshes) B->max_mb = std::max(B->max_mb, m->max_mb());
+  // launch shapes of the first mesh (the PLM kernel its meshes take alone), where they serve every mesh
+  B->fs = meshes[0]->fs;
+  if (B->fs.plm_tma && !batch_tma_ok(B, B->fs)) B->fs.plm_tma = 0;
+  vl2::prime_flux_tma(meshes[0]->view(), B->recon, B->riemann == VL2_HLLD ? vl2::RS_HLLD : vl2::RS_HLLE, B->fs,
+                      B->max_mb, B->st);
   const BatchPlan pl = batch_plan(B->meshes, B->max_mb);
   if (bytes < pl.total) {
     delete B;
@@ -1471,27 +1523,35 @@ vl2_status vl2_batch_autotune(vl2_batch* B, int* dc_threads, int* plm_lines) {
   VL2_BCHECK(B, cudaEventCreate(&e1));
   float best = 1e30f;
   vl2::FluxShape best_fs = B->fs;
+  std::vector<vl2::FluxShape> cands;
   for (int dc : kDcCandidates)
-    for (int pl : kPlmCandidates) {
-      B->fs.dc_threads = dc;
-      B->fs.plm_lines = pl;
-      if ((s = batch_lists(B)) != VL2_OK) break;
-      float tmin = 1e30f;
-      for (int rep = 0; rep < 3; ++rep) {  // the flux launches only write flux scratch: the state is untouched
-        VL2_BCHECK(B, cudaEventRecord(e0, B->st));
-        VL2_BCHECK(B, batch_fluxes(B, 0, VL2_DC));
-        VL2_BCHECK(B, batch_fluxes(B, 0, B->recon));
-        VL2_BCHECK(B, cudaEventRecord(e1, B->st));
-        VL2_BCHECK(B, cudaEventSynchronize(e1));
-        float ms = 0.f;
-        VL2_BCHECK(B, cudaEventElapsedTime(&ms, e0, e1));
-        tmin = std::min(tmin, ms);
+    for (int pl : kPlmCandidates)
+      for (int tma = 0; tma < 2; ++tma) {
+        vl2::FluxShape fs;
+        fs.dc_threads = dc;
+        fs.plm_lines = pl;
+        fs.plm_tma = tma;
+        if (!tma || batch_tma_ok(B, fs)) cands.push_back(fs);
       }
-      if (tmin < best) {
-        best = tmin;
-        best_fs = B->fs;
-      }
+  for (const vl2::FluxShape& fs : cands) {
+    B->fs = fs;
+    if ((s = batch_lists(B)) != VL2_OK) break;
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {  // the flux launches only write flux scratch: the state is untouched
+      VL2_BCHECK(B, cudaEventRecord(e0, B->st));
+      VL2_BCHECK(B, batch_fluxes(B, 0, VL2_DC));
+      VL2_BCHECK(B, batch_fluxes(B, 0, B->recon));
+      VL2_BCHECK(B, cudaEventRecord(e1, B->st));
+      VL2_BCHECK(B, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      VL2_BCHECK(B, cudaEventElapsedTime(&ms, e0, e1));
+      tmin = std::min(tmin, ms);
     }
+    if (tmin < best) {
+      best = tmin;
+      best_fs = B->fs;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s != VL2_OK) return s;
@@ -1564,6 +1624,39 @@ vl2_status vl2_batch_run(vl2_batch* B, int nsteps, double* dt_last) {
   if (dt_last) {
     VL2_BCHECK(B, cudaMemcpyAsync(dt_last, B->ddt, B->n * sizeof(double), cudaMemcpyDeviceToHost, B->st));
     VL2_BCHECK(B, cudaStreamSynchronize(B->st));
+  }
+  return VL2_OK;
+}
+
+vl2_status vl2_batch_flux_shape(const vl2_batch* B, int* dc_threads, int* plm_lines, int* tma) {
+  if (!B) return bfail(nullptr, VL2_E_ARG, "batch is NULL");
+  if (dc_threads) *dc_threads = B->fs.dc_threads;
+  if (plm_lines) *plm_lines = B->fs.plm_lines;
+  if (tma) *tma = B->fs.plm_tma;
+  return VL2_OK;
+}
+
+vl2_status vl2_batch_set_flux_shape(vl2_batch* B, int dc_threads, int plm_lines, int tma) {
+  if (!B) return bfail(nullptr, VL2_E_ARG, "batch is NULL");
+  if ((dc_threads != 64 && dc_threads != 128 && dc_threads != 256) ||
+      (plm_lines != 4 && plm_lines != 8 && plm_lines != 16) || (tma != 0 && tma != 1))
+    return bfail(B, VL2_E_ARG, "dc_threads must be 64, 128 or 256, plm_lines 4, 8 or 16, tma 0 or 1");
+  vl2::FluxShape fs;
+  fs.dc_threads = dc_threads;
+  fs.plm_lines = plm_lines;
+  fs.plm_tma = tma;
+  if (tma && !batch_tma_ok(B, fs)) return bfail(B, VL2_E_ARG, "the TMA-staged PLM kernel does not serve every mesh");
+  B->fs = fs;
+  vl2::prime_flux_tma(B->meshes[0]->view(), B->recon, B->riemann == VL2_HLLD ? vl2::RS_HLLD : vl2::RS_HLLE, fs,
+                      B->max_mb, B->st);
+  vl2_status s = batch_lists(B);
+  if (s != VL2_OK) return s;
+  if (B->exec) {  // the captured graph used the old launch shapes
+    cudaGraphExecDestroy(B->exec);
+    cudaGraphDestroy(B->graph);
+    B->exec = nullptr;
+    B->graph = nullptr;
+    B->graph_steps = 0;
   }
   return VL2_OK;
 }

@@ -4,6 +4,13 @@
 // work list; the mesh view is staged in shared memory once per CTA.
 #include "vl2_internal.h"
 #include "vl2_physics.cuh"
+#include "vl2_tma.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <atomic>
 
 namespace vl2 {
 
@@ -211,29 +218,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_flux_plm(MeshVi
     li[TA] = g.ng - h + line % na;
     li[TB] = g.ng - h + line / na;
     const long long o = cell_off(g, li[2], li[1], li[0]);
-    {
-      T q0[7], dl[7], dr[7], den[7];
-      bool pos[7];
+    T qm[7], qc[7], qp[7], lo[7], hi[7];
 #pragma unroll
-      for (int n = 0; n < 7; ++n) {
-        const T* q = Wb + (long long)var[n] * g.box + o;
-        const T qm = q[-sd], qc = q[0], qp = q[sd];
-        q0[n] = qc;
-        dl[n] = qc - qm;
-        dr[n] = qp - qc;
-        pos[n] = gt0(dl[n] * dr[n]);
-        den[n] = pos[n] ? dl[n] + dr[n] : T(1);
-      }
-      T rec[7];
+    for (int n = 0; n < 7; ++n) {
+      const T* q = Wb + (long long)var[n] * g.box + o;
+      qm[n] = q[-sd];
+      qc[n] = q[0];
+      qp[n] = q[sd];
+    }
+    plm_cell_faces<T>(qm, qc, qp, lo, hi);
 #pragma unroll
-      for (int n = 0; n < 7; ++n) rec[n] = sizeof(T) == 8 ? inv(den[n]) : T(1) / den[n];
-#pragma unroll
-      for (int n = 0; n < 7; ++n) {
-        // delta/2 = dl dr / (dl + dr): the factors 2 and 1/2 of the limited slope cancel exactly
-        const T half = pos[n] ? (dl[n] * dr[n]) * rec[n] : T(0);
-        smem[sidx(n, 0, p, c)] = q0[n] - half;  // value at the cell's lower face
-        smem[sidx(n, 1, p, c)] = q0[n] + half;  // value at the cell's upper face
-      }
+    for (int n = 0; n < 7; ++n) {
+      smem[sidx(n, 0, p, c)] = lo[n];  // value at the cell's lower face
+      smem[sidx(n, 1, p, c)] = hi[n];  // value at the cell's upper face
     }
   }
   __syncthreads();
@@ -264,6 +261,156 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_flux_plm(MeshVi
     T* Fb = static_cast<T*>(V.a.f[DIR]) + (long long)b * 7 * g.box + o;
 #pragma unroll
     for (int n = 0; n < 7; ++n) Fb[(long long)n * g.box] = fl[n];
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Corrector fluxes (PLM, Sec. 3.2.1, and the Riemann fluxes of Sec. 3.2.2) by persistent CTAs whose
+// primitive tiles are staged in shared memory by TMA.  A tile is P lines of faces along DIR, adjacent along
+// the faster transverse direction TA, in one TB row of one block; its primitives are one 4D box of w (see
+// tma_w_box), loaded by a single bulk tensor copy that completes on an mbarrier.  Each CTA walks the work
+// items blockIdx.x, blockIdx.x + gridDim.x, ... and copies the next item's box into the second of two buffers
+// while it reconstructs and solves the current one, so the loads of w overlap the arithmetic.  Per tile the
+// arithmetic is that of k_flux_plm (REC_PLM): phase A limits each cell's slope once into shared memory,
+// phase B solves the faces, with the same operations in the same order, so both kernels give the same bits.
+// A bounded wait that expires sets scal[SC_TIMEOUT] and the CTA returns after its copies have landed.
+// ------------------------------------------------------------------------------------------------
+constexpr int TMA_WAIT_POLLS = 1 << 20;  // polls of an mbarrier (each with a 256 ns sleep) before giving up
+
+template <int DIR, int RS, class T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+    k_flux_tma(MeshView single, const MeshView* views, const WorkItem* work, int nitems, int reg, int P, int wcap) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ MeshView sv;
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int landed;
+  constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
+  constexpr int TA = LineMap<DIR>::TA, TB = LineMap<DIR>::TB;
+  T* rec = reinterpret_cast<T*>(smem_raw + 2 * (size_t)wcap);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  // thread 0: start the copy of item i's box into buffer k
+  auto issue = [&](int i, int k) {
+    const MeshView* mv = &single;
+    int tile = i;
+    if (work) {
+      const WorkItem w = work[i];
+      mv = views + w.box;
+      tile = w.tile;
+    }
+    const Geom& g = mv->g;
+    const int h = g.flux_halo;
+    const int na = g.mb[TA] + 2 * h, nbl = g.mb[TB] + 2 * h;
+    const int tpr = (na + P - 1) / P;
+    const int b = tile / (nbl * tpr);
+    const int r = tile - b * (nbl * tpr);
+    const int tb = r / tpr, ta0 = (r - tb * tpr) * P;
+    int box[4], xoff;
+    tma_w_box(g, DIR, P, (int)sizeof(T), box, &xoff);
+    int c[4];
+    c[DIR] = g.ng - 2;
+    c[TA] = g.ng - h + ta0 - xoff;
+    c[TB] = g.ng - h + tb;
+    c[3] = 8 * b;
+    const uint32_t bytes = (uint32_t)(box[0] * box[1] * box[2] * box[3]) * (uint32_t)sizeof(T);
+    fence_proxy_async_smem();  // the CTA's reads of this buffer (previous item) come before the copy's writes
+    mbar_arrive_expect_tx(&bar[k], bytes);
+    tma_load_4d(smem_raw + (size_t)k * wcap, static_cast<const unsigned char*>(mv->a.tmw) + 128 * tma_map_index(DIR, P),
+                c[0], c[1], c[2], c[3], &bar[k]);
+  };
+  if (threadIdx.x == 0 && (int)blockIdx.x < nitems) issue((int)blockIdx.x, 0);
+  int k = 0;
+  for (int item = (int)blockIdx.x; item < nitems; item += (int)gridDim.x, ++k) {
+    const int buf = k & 1;
+    const uint32_t parity = (uint32_t)((k >> 1) & 1);
+    const bool more = item + (int)gridDim.x < nitems;
+    if (threadIdx.x == 0 && more) issue(item + (int)gridDim.x, buf ^ 1);
+    int tile;
+    const MeshView& V = stage_view_item(sv, single, views, work, item, tile);
+    const Geom& g = V.g;
+    if (threadIdx.x == 0) landed = mbar_wait_bounded(&bar[buf], parity, TMA_WAIT_POLLS) ? 1 : 0;
+    __syncthreads();
+    if (!landed) {
+      if (threadIdx.x == 0) {
+        atomicOr(V.a.scal + SC_TIMEOUT, 1ULL);
+        mbar_wait_bounded(&bar[buf], parity, TMA_WAIT_POLLS);  // let this CTA's copies land before it exits
+        if (more) mbar_wait_bounded(&bar[buf ^ 1], (uint32_t)(((k + 1) >> 1) & 1), TMA_WAIT_POLLS);
+      }
+      return;
+    }
+    mbar_wait_bounded(&bar[buf], parity, TMA_WAIT_POLLS);  // completed: each thread observes the copied bytes
+    const int h = g.flux_halo;
+    const int na = g.mb[TA] + 2 * h, nbl = g.mb[TB] + 2 * h;
+    const int tpr = (na + P - 1) / P;
+    const int b = tile / (nbl * tpr);
+    const int r = tile - b * (nbl * tpr);
+    const int tb = r / tpr, ta0 = (r - tb * tpr) * P;
+    const int L = g.mb[DIR] + 2;   // reconstructed cells per line
+    const int NF = g.mb[DIR] + 1;  // faces per line
+    const int L4 = g.mb[DIR] + 4;  // cells of the box along DIR
+    int box[4], xoff;
+    tma_w_box(g, DIR, P, (int)sizeof(T), box, &xoff);
+    const T* Ws = reinterpret_cast<const T*>(smem_raw + (size_t)buf * wcap);
+    // box element of variable v, DIR index a (0 = cell ng-2), line p
+    auto widx = [&](int v, int a, int p) -> int {
+      return (DIR == 0) ? (v * P + p) * box[0] + a : (v * L4 + a) * box[0] + xoff + p;
+    };
+    auto sidx = [&](int v, int side, int p, int c) -> int {
+      return (DIR == 0) ? (((v * 2 + side) * P + p) * L + c) : (((v * 2 + side) * L + c) * P + p);
+    };
+    const int var[7] = {0, 1 + DIR, 1 + T1, 1 + T2, 4, 5 + T1, 5 + T2};
+    // phase A: the lower- and upper-face values of the cells ng-1 .. ng+mb of every line
+    for (int t = threadIdx.x; t < P * L; t += blockDim.x) {
+      const int p = (DIR == 0) ? t / L : t % P;
+      const int c = (DIR == 0) ? t % L : t / P;
+      if (ta0 + p >= na) continue;
+      T qm[7], qc[7], qp[7], lo[7], hi[7];
+#pragma unroll
+      for (int n = 0; n < 7; ++n) {
+        qm[n] = Ws[widx(var[n], c, p)];
+        qc[n] = Ws[widx(var[n], c + 1, p)];
+        qp[n] = Ws[widx(var[n], c + 2, p)];
+      }
+      plm_cell_faces<T>(qm, qc, qp, lo, hi);
+#pragma unroll
+      for (int n = 0; n < 7; ++n) {
+        rec[sidx(n, 0, p, c)] = lo[n];
+        rec[sidx(n, 1, p, c)] = hi[n];
+      }
+    }
+    __syncthreads();
+    // phase B: Riemann problems of the faces ng .. ng+mb of every line
+    const double* Bn = V.a.b[reg][DIR];
+    for (int t = threadIdx.x; t < P * NF; t += blockDim.x) {
+      const int p = (DIR == 0) ? t / NF : t % P;
+      const int f = (DIR == 0) ? t % NF : t / P;
+      if (ta0 + p >= na) continue;
+      int li[3];
+      li[DIR] = g.ng + f;
+      li[TA] = g.ng - h + ta0 + p;
+      li[TB] = g.ng - h + tb;
+      const long long o = cell_off(g, li[2], li[1], li[0]);
+      T wl[7], wr[7];
+#pragma unroll
+      for (int n = 0; n < 7; ++n) {
+        wl[n] = rec[sidx(n, 1, p, f)];
+        wr[n] = rec[sidx(n, 0, p, f + 1)];
+      }
+      const T bn = (T)Bn[(long long)b * g.box + o];
+      T fl[7];
+      if (RS == RS_HLLD)
+        flux_hlld<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, fl);
+      else
+        flux_hlle<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, fl, g.hlle_roe != 0);
+      T* Fb = static_cast<T*>(V.a.f[DIR]) + (long long)b * 7 * g.box + o;
+#pragma unroll
+      for (int n = 0; n < 7; ++n) Fb[(long long)n * g.box] = fl[n];
+    }
+    __syncthreads();  // the view, the reconstruction and this buffer are rewritten by the next item
   }
 }
 
@@ -394,6 +541,128 @@ long long tiles_flux_plm(const Geom& g, int dir, const FluxShape& fs) {
   return (long long)g.nblk * ((nlines + P - 1) / P);
 }
 
+// ---- the TMA-staged PLM path ----
+static int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+
+// bytes of one primitive buffer of k_flux_tma (largest box of any mesh of the launch), a multiple of 128
+static size_t tma_buf_bytes(int dir, int lines, int max_mb, int esize) {
+  const int q = 16 / esize;
+  const size_t elems = dir == 0 ? (size_t)((max_mb + 4 + q - 1) / q * q) * lines : (size_t)(lines + q) * (max_mb + 4);
+  return (elems * 8 * esize + 127) / 128 * 128;
+}
+static size_t tma_smem(int dir, int lines, int max_mb, int esize) {
+  return 2 * tma_buf_bytes(dir, lines, max_mb, esize) + (size_t)14 * lines * (max_mb + 2) * esize;
+}
+
+bool flux_tma_applies(const MeshView& v, int recon, const FluxShape& fs, int max_mb) {
+  const Geom& g = v.g;
+  if (!fs.plm_tma || recon != REC_PLM || !v.a.tmw || g.ng != 2) return false;
+  if (fs.plm_lines != 4 && fs.plm_lines != 8 && fs.plm_lines != 16) return false;
+  if (max_mb + 4 > 256) return false;
+  const int es = v.a.mixed ? 4 : 8;
+  for (int d = 0; d < 3; ++d)
+    if (tma_smem(d, fs.plm_lines, max_mb, es) > PLM_SMEM_MAX) return false;
+  return true;
+}
+
+long long tiles_flux_tma(const Geom& g, int dir, int lines) {
+  const int ta = dir == 0 ? 1 : 0, tb = dir == 2 ? 1 : 2;
+  const long long na = g.mb[ta] + 2 * g.flux_halo, nbl = g.mb[tb] + 2 * g.flux_halo;
+  return (long long)g.nblk * nbl * ((na + lines - 1) / lines);
+}
+
+bool encode_w_maps(const Geom& g, const void* w, int esize, void* maps, const char** why) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode) {
+    *why = "the driver offers no cuTensorMapEncodeTiled";
+    return false;
+  }
+  if (g.ng != 2 || (esize != 4 && esize != 8) || ((uintptr_t)w & 255u) || (g.sx * esize) % 16) {
+    *why = "w does not meet the TMA layout rules (two ghost layers, 16-byte rows)";
+    return false;
+  }
+  const cuuint64_t dims[4] = {(cuuint64_t)g.sx, (cuuint64_t)g.sy, (cuuint64_t)g.sz, (cuuint64_t)g.nblk * 8};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.sx * esize, (cuuint64_t)g.sx * g.sy * esize, (cuuint64_t)g.box * esize};
+  const cuuint32_t unit[4] = {1, 1, 1, 1};
+  if (dims[3] > 0xffffffffull) {
+    *why = "too many MeshBlocks for a TMA tensor";
+    return false;
+  }
+  CUtensorMap* out = static_cast<CUtensorMap*>(maps);
+  const int heights[3] = {4, 8, 16};
+  for (int dir = 0; dir < 3; ++dir)
+    for (int lines : heights) {
+      int box[4], xoff;
+      tma_w_box(g, dir, lines, esize, box, &xoff);
+      cuuint32_t bd[4];
+      for (int q = 0; q < 4; ++q) {
+        if (box[q] < 1 || box[q] > 256) {
+          *why = "a MeshBlock edge is too long for a TMA box";
+          return false;
+        }
+        bd[q] = (cuuint32_t)box[q];
+      }
+      const CUresult r = encode(&out[tma_map_index(dir, lines)],
+                                esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+                                const_cast<void*>(w), dims, strides, bd, unit, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) {
+        *why = "cuTensorMapEncodeTiled rejected the primitive tensor";
+        return false;
+      }
+    }
+  return true;
+}
+
+// Resident CTAs per SM of k_flux_tma with this shared memory, cached per instantiation.  The occupancy query
+// is not made while `st` is being captured into a graph (a capture records stream work only); an uncached
+// shape there takes one CTA per SM, which changes no result.
+template <int DIR, int RS, class T>
+static int tma_ctas_per_sm(size_t shmem, cudaStream_t st) {
+  static std::atomic<long long> cache{-1};  // (shmem << 8) | CTAs per SM
+  const long long c = cache.load();
+  if (c >= 0 && (size_t)(c >> 8) == shmem) return (int)(c & 255);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 1;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_flux_tma<DIR, RS, T>, 256, shmem) != cudaSuccess ||
+      per_sm < 1) {
+    (void)cudaGetLastError();
+    return 1;
+  }
+  per_sm = std::min(per_sm, 255);
+  cache.store(((long long)shmem << 8) | per_sm);
+  return per_sm;
+}
+
+template <int DIR, int RS, class T>
+static cudaError_t launch_tma(const MeshView& v, const Dispatch* d, int reg, const FluxShape& fs, int max_mb,
+                              cudaStream_t st) {
+  const int P = fs.plm_lines;
+  const size_t wcap = tma_buf_bytes(DIR, P, max_mb, (int)sizeof(T));
+  const size_t shmem = tma_smem(DIR, P, max_mb, (int)sizeof(T));
+  const long long items = d ? d->nwork : tiles_flux_tma(v.g, DIR, P);
+  if (items <= 0) return cudaSuccess;
+  if (items > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const long long grid = std::min<long long>(items, (long long)tma_ctas_per_sm<DIR, RS, T>(shmem, st) * sm_count());
+  k_flux_tma<DIR, RS, T><<<(unsigned)grid, 256, shmem, st>>>(v, d ? d->views : nullptr, d ? d->work : nullptr,
+                                                             (int)items, reg, P, (int)wcap);
+  return cudaGetLastError();
+}
+
 template <class K>
 static cudaError_t set_smem_attr(K kern) {
   return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PLM_SMEM_MAX);
@@ -403,6 +672,7 @@ template <int DIR, int RS, class T>
 static cudaError_t launch_typed(const MeshView& v, const Dispatch* d, int reg, int recon, const FluxShape& fs,
                                 int max_mb, cudaStream_t st) {
   const Geom& g = v.g;
+  if (flux_tma_applies(v, recon, fs, max_mb)) return launch_tma<DIR, RS, T>(v, d, reg, fs, max_mb, st);
   if (recon == REC_PLM || recon == REC_PPM || recon == REC_PLM_CHAR || recon == REC_PPM_CHAR) {
     FluxShape f2 = fs;
     f2.plm_lines = plm_lines_for(g, DIR, fs, max_mb, recon);
@@ -440,6 +710,30 @@ static cudaError_t launch_dir(const MeshView& v, const Dispatch* d, int reg, int
                             : launch_typed<DIR, RS_HLLE, double>(v, d, reg, recon, fs, max_mb, st);
 }
 
+template <class T>
+static void prime_typed(int riemann, size_t shmem0, size_t shmem1, size_t shmem2, cudaStream_t st) {
+  if (riemann == RS_HLLD) {
+    tma_ctas_per_sm<0, RS_HLLD, T>(shmem0, st);
+    tma_ctas_per_sm<1, RS_HLLD, T>(shmem1, st);
+    tma_ctas_per_sm<2, RS_HLLD, T>(shmem2, st);
+  } else {
+    tma_ctas_per_sm<0, RS_HLLE, T>(shmem0, st);
+    tma_ctas_per_sm<1, RS_HLLE, T>(shmem1, st);
+    tma_ctas_per_sm<2, RS_HLLE, T>(shmem2, st);
+  }
+}
+
+void prime_flux_tma(const MeshView& v, int recon, int riemann, const FluxShape& fs, int max_mb, cudaStream_t st) {
+  if (!flux_tma_applies(v, recon, fs, max_mb)) return;
+  const int es = v.a.mixed ? 4 : 8;
+  const size_t s0 = tma_smem(0, fs.plm_lines, max_mb, es), s1 = tma_smem(1, fs.plm_lines, max_mb, es),
+               s2 = tma_smem(2, fs.plm_lines, max_mb, es);
+  if (v.a.mixed)
+    prime_typed<float>(riemann, s0, s1, s2, st);
+  else
+    prime_typed<double>(riemann, s0, s1, s2, st);
+}
+
 cudaError_t launch_flux(const MeshView& v, const Dispatch* d, int reg, int recon, int riemann, int dir,
                         const FluxShape& fs, int max_mb, cudaStream_t st) {
   if (dir == 0) return launch_dir<0>(v, d, reg, recon, riemann, fs, max_mb, st);
@@ -452,6 +746,7 @@ cudaError_t launch_flux(const MeshView& v, const Dispatch* d, int reg, int recon
 cudaError_t prepare_kernel_attributes() {
   cudaError_t e = cudaSuccess;
 #define VL2_ATTR(DIR, RS, T)                                                      \
+  if (e == cudaSuccess) e = set_smem_attr(k_flux_tma<DIR, RS, T>);              \
   if (e == cudaSuccess) e = set_smem_attr(k_flux_plm<DIR, RS, T, REC_PLM>);     \
   if (e == cudaSuccess) e = set_smem_attr(k_flux_plm<DIR, RS, T, REC_PLM_CHAR>); \
   if (e == cudaSuccess) e = set_smem_attr(k_flux_plm<DIR, RS, T, REC_PPM_CHAR>); \

@@ -61,9 +61,14 @@ struct Arrays {
   double* fsc[3];    // scalar fluxes per sweep direction: [nblk][ns][box]
   // forcing acceleration at the cell centres, FP64: [nblk][3][box] (active cells); null when no forcing is set
   double* acc;
+  // TMA_MAPS tensor maps (CUtensorMap, 128 bytes each) describing w for the TMA-staged PLM sweeps, one per
+  // sweep direction and tile height (tma_map_index); null when that path is not available for this mesh
+  const void* tmw;
 };
 
-enum { SC_MAXRATE = 0, SC_FLOORS = 1, SC_MISMATCH = 2, SC_COUNT = 8 };
+// Device scalars: CFL rate bits, floor count, periodic-check mismatches, and a flag set by a kernel whose
+// bounded wait for a TMA tile expired (it skips its work and returns).
+enum { SC_MAXRATE = 0, SC_FLOORS = 1, SC_MISMATCH = 2, SC_TIMEOUT = 3, SC_COUNT = 8 };
 
 // A mesh as the kernels see it (copied to device memory for batched launches).
 struct MeshView {
@@ -86,23 +91,24 @@ struct Dispatch {
 };
 
 #ifdef __CUDACC__
-// Resolve the mesh and tile of this CTA (single mesh: the launch argument and blockIdx.x; batch: the
-// CTA's work item) and stage the mesh view in shared memory.  Every thread of the CTA must call it.  The
-// view is copied as 8-byte words, one per thread of the first 64 (every launch that calls this has at least
-// 64 threads per CTA), so that the barrier behind it waits for one round of loads rather than for one
-// thread's serial copy of the whole view.
+// Resolve the mesh and tile of work item `item` (single mesh: the launch argument, tile = item; batch: the
+// item's entry of the work list) and stage the mesh view in shared memory.  Every thread of the CTA must
+// call it.  The view is copied as 8-byte words, one per thread of the first 64 (every launch that calls
+// this has at least 64 threads per CTA), so that the barrier behind it waits for one round of loads rather
+// than for one thread's serial copy of the whole view.
 static_assert(sizeof(MeshView) % 8 == 0, "the mesh view is staged in 8-byte words");
 static_assert(sizeof(MeshView) <= 64 * 8, "the mesh view is staged by the first 64 threads (every CTA has >= 64)");
-__device__ __forceinline__ const MeshView& stage_view(MeshView& sv, const MeshView& single, const MeshView* views,
-                                                      const WorkItem* work, int& tile, int* box = nullptr) {
+__device__ __forceinline__ const MeshView& stage_view_item(MeshView& sv, const MeshView& single,
+                                                           const MeshView* views, const WorkItem* work, int item,
+                                                           int& tile, int* box = nullptr) {
   const MeshView* src = &single;
   if (work) {
-    const WorkItem w = work[blockIdx.x];
+    const WorkItem w = work[item];
     tile = w.tile;
     if (box) *box = w.box;
     src = views + w.box;
   } else {
-    tile = blockIdx.x;
+    tile = item;
     if (box) *box = 0;
   }
   constexpr unsigned NW = (unsigned)(sizeof(MeshView) / 8);
@@ -112,6 +118,11 @@ __device__ __forceinline__ const MeshView& stage_view(MeshView& sv, const MeshVi
   __syncthreads();
   return sv;
 }
+// The same for the CTA's own item, blockIdx.x (one work item per CTA).
+__device__ __forceinline__ const MeshView& stage_view(MeshView& sv, const MeshView& single, const MeshView* views,
+                                                      const WorkItem* work, int& tile, int* box = nullptr) {
+  return stage_view_item(sv, single, views, work, (int)blockIdx.x, tile, box);
+}
 #endif
 
 // Threads per CTA of the per-element kernels, and the tunable flux launch shapes.
@@ -119,7 +130,26 @@ constexpr int THREADS = 256;
 struct FluxShape {
   int dc_threads = 128;  // CTA size of the donor-cell flux kernel
   int plm_lines = 16;    // lines of faces per CTA of the PLM flux kernel (0: largest that fits)
+  int plm_tma = 0;       // 1: PLM sweeps take the persistent TMA-staged kernel (tile height plm_lines: 4, 8, 16)
 };
+
+// ---- TMA-staged PLM sweeps (k_flux_tma).  A tile is plm_lines lines of faces along the sweep direction,
+// adjacent along the faster transverse direction; its primitives arrive as one 4D box (x, y, z, variable)
+// of w: the mb+4 cells ng-2 .. ng+mb+1 along the sweep, the tile's lines across it, all 8 variables. ----
+constexpr int TMA_MAPS = 9;  // 3 sweep directions x tile heights 4, 8, 16
+__host__ __device__ inline int tma_map_index(int dir, int lines) { return 3 * dir + (lines == 4 ? 0 : (lines == 8 ? 1 : 2)); }
+// Box extents (x, y, z, variable) of a tile's primitives and the x offset of its first line inside the box.
+// The box's first x coordinate is a multiple of 16 bytes (TMA): the sweep along x starts at cell ng-2 = 0,
+// the others at the tile's first line rounded down, which needs xoff extra columns.
+__host__ __device__ inline void tma_w_box(const Geom& g, int dir, int lines, int esize, int box[4], int* xoff) {
+  const int q = 16 / esize;
+  const int o = (g.ng - g.flux_halo) % q;
+  *xoff = dir == 0 ? 0 : o;
+  box[0] = dir == 0 ? (g.mb[0] + 4 + q - 1) / q * q : (o + lines + q - 1) / q * q;
+  box[1] = dir == 1 ? g.mb[1] + 4 : (dir == 0 ? lines : 1);
+  box[2] = dir == 2 ? g.mb[2] + 4 : 1;
+  box[3] = 8;
+}
 
 // Work units of each kernel for one mesh (used to size single launches and to build work lists).
 long long tiles_prim(const Geom& g);
@@ -129,6 +159,16 @@ long long tiles_flux_dc(const Geom& g, int dir, const FluxShape& fs);
 long long tiles_flux_plm(const Geom& g, int dir, const FluxShape& fs);
 long long tiles_flux_halo(const Geom& g);  // 0 when g.flux_halo
 int plm_lines_for(const Geom& g, int dir, const FluxShape& fs, int max_mb, int recon);
+// true when the PLM sweeps of this mesh (or batch: v is its first mesh, and every mesh qualifies) run as
+// k_flux_tma under fs; tiles of one direction for that kernel
+bool flux_tma_applies(const MeshView& v, int recon, const FluxShape& fs, int max_mb);
+long long tiles_flux_tma(const Geom& g, int dir, int lines);
+// Look up (outside any graph capture) the occupancy the TMA-staged launches of this shape will use.
+void prime_flux_tma(const MeshView& v, int recon, int riemann, const FluxShape& fs, int max_mb, cudaStream_t st);
+// Encode the TMA_MAPS tensor maps of the primitives w (device, 256-byte aligned; float or double elements)
+// into maps (host memory, 128-byte aligned, TMA_MAPS * 128 bytes).  Returns false, with a message, when
+// the driver cannot encode them (the mesh then keeps the line-tile kernel).
+bool encode_w_maps(const Geom& g, const void* w, int esize, void* maps, const char** why);
 
 // ---- launchers (vl2_kernels.cu / vl2_flux.cu); all enqueue on `st`.  d == nullptr: the single mesh v.
 // For batched launches v only selects the precision; dtbox (per-box dt, device) and beta give h. ----

@@ -7,6 +7,7 @@
 
 #include "vl2_internal.h"
 #include "vl2_physics.cuh"
+#include "vl2_tma.cuh"
 #include "vl2mhd.h"
 
 namespace vl2 {
@@ -54,10 +55,34 @@ __global__ void k_arith(int fn, long long n, const double* __restrict__ x, doubl
   out[t] = r;
 }
 
+// One thread waits, with the same bounded wait as the TMA-staged kernels, on an mbarrier phase that
+// nothing completes (no arrival, no copy); out[0] = 1 when the wait gave up, 0 if it (wrongly) completed.
+__global__ void k_mbar_timeout(int polls, int* out) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  mbar_init_fence();
+  out[0] = mbar_wait_bounded(&bar, 0u, polls) ? 0 : 1;
+}
+
 }  // namespace
 }  // namespace vl2
 
 extern "C" {
+
+vl2_status vl2_debug_wait_timeout(int polls, int* out, void* stream) {
+  if (!out || polls <= 0 || polls > (1 << 20)) {
+    vl2::record_error("vl2_debug_wait_timeout: out must be non-NULL and polls in 1 .. 2^20");
+    return VL2_E_ARG;
+  }
+  vl2::k_mbar_timeout<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(polls, out);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    vl2::record_error(cudaGetErrorString(e));
+    return VL2_E_CUDA;
+  }
+  return VL2_OK;
+}
 
 vl2_status vl2_debug_fp64_peak(long long iters, int ctas, int threads, double* out, void* stream) {
   if (!out || iters <= 0 || ctas <= 0 || threads <= 0 || threads > 256 || threads % 32 != 0) {

@@ -62,7 +62,9 @@ EXPORTS = ["vl2_workspace_bytes", "vl2_mesh_create", "vl2_mesh_destroy", "vl2_bl
            "vl2_batch_create", "vl2_batch_destroy", "vl2_batch_autotune", "vl2_batch_step", "vl2_batch_run",
            "vl2_batch_launch_count", "vl2_batch_last_error", "vl2_set_cons", "vl2_step_vjp", "vl2_prims_vjp",
            "vl2_debug_riemann_vjp", "vl2_last_error", "vl2_set_scalars", "vl2_get_scalars", "vl2_debug_fp64_peak",
-           "vl2_debug_arith", "vl2_set_forcing", "vl2_tape_bytes", "vl2_step_record", "vl2_step_vjp_recorded"]
+           "vl2_debug_arith", "vl2_set_forcing", "vl2_tape_bytes", "vl2_step_record", "vl2_step_vjp_recorded",
+           "vl2_set_flux_shape", "vl2_get_flux_shape", "vl2_batch_flux_shape", "vl2_batch_set_flux_shape",
+           "vl2_debug_wait_timeout"]
 NOALLOC_MAX_NZ = 4096
 K_PRIM, K_GHOSTS, K_FLUX_DC, K_FLUX_PLM, K_EMF, K_UPDATE, K_FLUX_PPM, K_SCALARS, K_FLUX_HALO = range(9)
 KERNEL_KINDS = {K_PRIM: "prim", K_GHOSTS: "ghosts", K_FLUX_DC: "flux_dc", K_FLUX_PLM: "flux_plm", K_EMF: "emf",
@@ -117,6 +119,12 @@ def load(path: str = LIB_PATH):
     L.vl2_batch_step.argtypes = [vp, vp, ctypes.c_int]
     L.vl2_batch_run.argtypes = [vp, ctypes.c_int, vp]
     L.vl2_batch_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.vl2_set_flux_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.vl2_get_flux_shape.argtypes = [vp, ip, ip, ip, ip]
+    L.vl2_batch_flux_shape.argtypes = [vp, ip, ip, ip]
+    L.vl2_batch_set_flux_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.vl2_debug_wait_timeout.argtypes = [ctypes.c_int, dp, vp]
     L.vl2_batch_last_error.argtypes = [vp]
     L.vl2_batch_last_error.restype = ctypes.c_char_p
     L.vl2_last_error.argtypes = [vp]
@@ -398,6 +406,16 @@ class Mesh:
         _check(self._L.vl2_launch_count(self._h, ctypes.byref(n)), self._h, lib=self._L)
         return n.value
 
+    def set_flux_shape(self, dc_threads=128, plm_lines=16, tma=0):
+        """Launch shapes of the flux sweeps (vl2_set_flux_shape); no result bit depends on them."""
+        _check(self._L.vl2_set_flux_shape(self._h, int(dc_threads), int(plm_lines), int(tma)), self._h, lib=self._L)
+
+    def flux_shape(self):
+        """(dc_threads, plm_lines, tma, tma_active) of this mesh (vl2_get_flux_shape)."""
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(self._L.vl2_get_flux_shape(self._h, *[ctypes.byref(x) for x in v]), self._h, lib=self._L)
+        return tuple(x.value for x in v)
+
     def debug_fluxes(self, recon):
         NX, NY, NZ = self.nx
         fx, fy, fz = np.empty((7, NZ, NY, NX + 1)), np.empty((7, NZ, NY + 1, NX)), np.empty((7, NZ + 1, NY, NX))
@@ -501,6 +519,18 @@ def debug_arith(fn, x, stream=None):
     return out
 
 
+def debug_wait_timeout(polls=1000, device=None):
+    """vl2_debug_wait_timeout: 1 when the bounded wait on a phase that nothing completes gave up (expected)."""
+    import torch
+
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    with torch.cuda.device(dev):
+        out = torch.full((1,), -1, dtype=torch.int32, device=dev)
+        st = torch.cuda.current_stream(dev)
+        _check(load().vl2_debug_wait_timeout(int(polls), ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(st.cuda_stream)))
+        return int(out.item())
+
+
 def fp64_peak(device=None, iters=1 << 16, ctas=None, threads=256, repeats=5):
     """Measured FP64 peak (TFLOP/s): the best of `repeats` event-timed launches of vl2_debug_fp64_peak, each
     2 * 16 * iters * ctas * threads FP64 operations (fused multiply-adds count 2).  ctas defaults to 8 per SM."""
@@ -598,6 +628,17 @@ class Batch:
         n = ctypes.c_longlong()
         _bcheck(self._L.vl2_batch_launch_count(self._h, ctypes.byref(n)), self._h, lib=self._L)
         return n.value
+
+    def set_flux_shape(self, dc_threads=128, plm_lines=16, tma=0):
+        """Launch shapes of the batch's flux sweeps (vl2_batch_set_flux_shape)."""
+        _bcheck(self._L.vl2_batch_set_flux_shape(self._h, int(dc_threads), int(plm_lines), int(tma)), self._h,
+                lib=self._L)
+
+    def flux_shape(self):
+        """(dc_threads, plm_lines, tma) the batch's flux launches use (vl2_batch_flux_shape)."""
+        v = [ctypes.c_int() for _ in range(3)]
+        _bcheck(self._L.vl2_batch_flux_shape(self._h, *[ctypes.byref(x) for x in v]), self._h, lib=self._L)
+        return tuple(x.value for x in v)
 
 
 # ---- ABI-named module functions ----
