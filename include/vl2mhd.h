@@ -342,8 +342,8 @@ vl2_status vl2_launch_count(const vl2_mesh* mesh, long long* n);
  * all 8 variables) in shared memory with one TMA bulk tensor copy, the next tile's copy in flight while the
  * current one is solved.  tma = 1 needs the tensor maps vl2_mesh_create encodes for meshes with two ghost
  * layers, and a tile that fits in shared memory; elsewhere, and for other reconstructions, the line-tile
- * kernel runs.  A new mesh starts with (128, 16, 1) in the mixed precision and (128, 16, 0) in FP64, the
- * faster of the two PLM kernels on GB300 for each.  Errors: VL2_E_ARG (NULL mesh, values outside the sets). */
+ * kernel runs.  A new mesh starts with (128, 16, 0): on GB300 the line-tile kernel measured faster in both
+ * precisions.  Errors: VL2_E_ARG (NULL mesh, values outside the sets). */
 vl2_status vl2_set_flux_shape(vl2_mesh* mesh, int dc_threads, int plm_lines, int tma);
 
 /* The launch shapes set above; tma_active (may be NULL) receives 1 when the PLM sweeps actually take the

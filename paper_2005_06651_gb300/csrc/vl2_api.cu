@@ -513,7 +513,7 @@ vl2_status vl2_mesh_create(const vl2_params* params, void* workspace, size_t byt
   const char* why = nullptr;
   const bool have_maps = vl2::encode_w_maps(g, m->a.w, m->a.mixed ? 4 : 8, maps, &why);
   m->a.tmw = have_maps ? base + pl.off_tmw : nullptr;
-  m->fs.plm_tma = have_maps && m->a.mixed ? 1 : 0;
+  m->fs.plm_tma = 0;  // the line-tile PLM kernel measured faster on GB300 in both precisions
   cudaError_t e = vl2::prepare_kernel_attributes();
   if (e == cudaSuccess) e = cudaMemsetAsync(workspace, 0, pl.total, m->st);
   if (e == cudaSuccess && have_maps) e = cudaMemcpyAsync(base + pl.off_tmw, maps, sizeof(maps), cudaMemcpyHostToDevice, m->st);
