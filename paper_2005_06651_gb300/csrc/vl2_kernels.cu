@@ -464,7 +464,7 @@ cudaError_t launch_scalar_fluxes(const MeshView& v, int recon, int dir, cudaStre
   return launch_scalar_dir<2, double>(v, recon, st);
 }
 
-// Register update of the scalar masses, written as the conserved variables' update in k_update (same
+// Register update of the scalar masses, written as the FP64 conserved variables' update in k_update (same
 // association, same weights), so that a unit scalar stays bitwise equal to the density.
 template <bool PLAIN>
 __global__ void __launch_bounds__(256) k_scalar_update(MeshView V, int base_reg, int out_reg, double h, double g_base,
@@ -486,10 +486,11 @@ __global__ void __launch_bounds__(256) k_scalar_update(MeshView V, int base_reg,
   double* Sout = V.a.s[out_reg];
   for (int q = 0; q < g.ns; ++q) {
     const long long o = ((long long)b * g.ns + q) * g.box + c;
-    double dfl[3];
+    double df[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) dfl[d] = (V.a.fsc[d][o + stride[d]] - V.a.fsc[d][o]) * g.idx[d];
-    const double L = -((dfl[0] + dfl[1]) + dfl[2]);
+    for (int d = 0; d < 3; ++d) df[d] = V.a.fsc[d][o + stride[d]] - V.a.fsc[d][o];
+    const double dv = (df[0] * g.idx[0] + df[1] * g.idx[1]) + df[2] * g.idx[2];
+    const double L = -dv;
     Sout[o] = (PLAIN ? Sbase[o] : g_base * Sbase[o] + g_other * Soth[o]) + h * L;
   }
 }
@@ -675,6 +676,10 @@ cudaError_t launch_emfs(const MeshView& v, const Dispatch* d, cudaStream_t st) {
 // the stage state (register stage_reg, the one the fluxes were formed from): rho a for the momentum and
 // M . a for the energy, L = -div F + S, in FP64 in every precision.
 // U_base / U_out may alias (stages update a register in place), so no __restrict__ here.
+// In the mixed precision the plain form is accumulated as U_base - sum_d (h/dx_d) dF_d (+ h S) with fused
+// multiply-adds, and B_base - (h/dx_a) dE_b + (h/dx_b) dE_a: a third fewer FP64 operations than forming L
+// first (measured 8% faster there; in FP64, where the loads dominate, the chain of dependent FMAs measured 4%
+// slower, so FP64 and the value-safe build keep the L form, which the oracle uses).
 // ------------------------------------------------------------------------------------------------
 template <class T, bool PLAIN>
 __global__ void __launch_bounds__(256, 3) k_update(MeshView single, const MeshView* views, const WorkItem* work,
@@ -727,7 +732,7 @@ __global__ void __launch_bounds__(256, 3) k_update(MeshView single, const MeshVi
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      double dfl[3];
+      double df[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         int comp;
@@ -740,10 +745,20 @@ __global__ void __launch_bounds__(256, 3) k_update(MeshView single, const MeshVi
           comp = (m == d) ? 1 : ((m == (d + 1) % 3) ? 2 : 3);
         }
         const T* fp = F[d] + (long long)comp * g.box;
-        dfl[d] = (to_f64(fp[stride[d]]) - to_f64(fp[0])) * g.idx[d];  // FP64 accumulation
+        df[d] = to_f64(fp[stride[d]]) - to_f64(fp[0]);  // FP64 accumulation
       }
-      const double L = forced ? -((dfl[0] + dfl[1]) + dfl[2]) + src[v] : -((dfl[0] + dfl[1]) + dfl[2]);
       const long long o = ub + (long long)v * g.box;
+#ifndef VL2_VALUE_SAFE
+      if (PLAIN && sizeof(T) == 4) {
+        double acc = Ubase[o];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) acc = fma(-(h * g.idx[d]), df[d], acc);
+        Uout[o] = forced ? fma(h, src[v], acc) : acc;
+        continue;
+      }
+#endif
+      const double dv = (df[0] * g.idx[0] + df[1] * g.idx[1]) + df[2] * g.idx[2];
+      const double L = forced ? -dv + src[v] : -dv;
       Uout[o] = (PLAIN ? Ubase[o] : g_base * Ubase[o] + g_other * Uoth[o]) + h * L;
     }
   }
@@ -755,9 +770,16 @@ __global__ void __launch_bounds__(256, 3) k_update(MeshView single, const MeshVi
   for (int fd = 0; fd < 3; ++fd) {
     const int a = (fd + 1) % 3, bq = (fd + 2) % 3;
     if (!inside[a] || !inside[bq]) continue;
-    const double curl = (to_f64(E[bq][stride[a]]) - to_f64(E[bq][0])) * g.idx[a] -
-                        (to_f64(E[a][stride[bq]]) - to_f64(E[a][0])) * g.idx[bq];
+    const double deb = to_f64(E[bq][stride[a]]) - to_f64(E[bq][0]);
+    const double dea = to_f64(E[a][stride[bq]]) - to_f64(E[a][0]);
     const long long o = (long long)b * g.box + c;
+#ifndef VL2_VALUE_SAFE
+    if (PLAIN && sizeof(T) == 4) {
+      Bo[fd][o] = fma(h * g.idx[bq], dea, fma(-(h * g.idx[a]), deb, Bb[fd][o]));
+      continue;
+    }
+#endif
+    const double curl = deb * g.idx[a] - dea * g.idx[bq];
     Bo[fd][o] = (PLAIN ? Bb[fd][o] : g_base * Bb[fd][o] + g_other * Bx[fd][o]) + h * (-curl);
   }
 }
