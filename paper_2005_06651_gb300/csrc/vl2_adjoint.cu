@@ -387,9 +387,10 @@ __global__ void __launch_bounds__(128) k_adj_flux(Geom g, const double* __restri
     if (REC == REC_DC) {
       wl[n] = p[-sd];
       wr[n] = p[0];
-    } else {
-      wl[n] = p[-sd] + 0.5 * vl_slope(p[-2 * sd], p[-sd], p[0]);
-      wr[n] = p[0] - 0.5 * vl_slope(p[-sd], p[0], p[sd]);
+    } else {  // the forward sweep's face values: the upper face of cell i-1, the lower face of cell i
+      double unused;
+      plm_var_faces<double>(p[-2 * sd], p[-sd], p[0], unused, wl[n]);
+      plm_var_faces<double>(p[-sd], p[0], p[sd], wr[n], unused);
     }
   }
   const double bn = Bn[(long long)b * g.box + c];

@@ -682,7 +682,7 @@ cudaError_t launch_emfs(const MeshView& v, const Dispatch* d, cudaStream_t st) {
 // slower, so FP64 and the value-safe build keep the L form, which the oracle uses).
 // ------------------------------------------------------------------------------------------------
 template <class T, bool PLAIN>
-__global__ void __launch_bounds__(256, 3) k_update(MeshView single, const MeshView* views, const WorkItem* work,
+__global__ void __launch_bounds__(256, 4) k_update(MeshView single, const MeshView* views, const WorkItem* work,
                                                 int base_reg, int out_reg, double h, const double* dtbox, double beta,
                                                 double g_base, double g_other, int stage_reg) {
   __shared__ MeshView sv;

@@ -417,38 +417,35 @@ __device__ __forceinline__ R vl_slope(R qm, R q0, R qp) {
   return gt0(pr) ? (R(2) * pr) / (dl + dr) : R(0);
 }
 
-// PLM values of the 7 sweep variables of one cell at its lower and upper faces from the cell (qc) and its two
+// PLM values of one variable of a cell at its lower and upper faces from the cell (qc) and its two
 // neighbours along the sweep (qm, qp), Sec. 3.2.1: q -+ delta/2 with the van Leer slope's half
 // delta/2 = dl dr / (dl + dr) where dl dr > 0, else 0 (the slope's factor 2 and the 1/2 cancel exactly).
-// Each limiter denominator is inverted once (the Newton reciprocal in FP64).  The fast build writes both
-// face values as explicit fused multiply-adds, so that every kernel calling this rounds them alike whatever
-// code surrounds it; the value-safe build (no contraction anywhere) multiplies and then adds.
+// The limiter denominator is inverted by the Newton reciprocal in FP64.  The fast build writes both face
+// values as explicit fused multiply-adds, so that every kernel calling this (the forward sweeps and the
+// adjoint's replay of them) rounds them alike whatever code surrounds it; the value-safe build (no
+// contraction anywhere) multiplies and then adds.
+template <class T>
+__device__ __forceinline__ void plm_var_faces(T qm, T qc, T qp, T& lo, T& hi) {
+  const T dl = qc - qm, dr = qp - qc;
+  const bool pos = gt0(dl * dr);
+  const T den = pos ? dl + dr : T(1);
+  const T rc = sizeof(T) == 8 ? inv(den) : T(1) / den;
+#ifdef VL2_VALUE_SAFE
+  const T half = pos ? (dl * dr) * rc : T(0);
+  lo = qc - half;
+  hi = qc + half;
+#else
+  const T pr = pos ? dl * dr : T(0);
+  lo = fma(-pr, rc, qc);
+  hi = fma(pr, rc, qc);
+#endif
+}
+
+// The same for the 7 sweep variables of one cell.
 template <class T>
 __device__ __forceinline__ void plm_cell_faces(const T* qm, const T* qc, const T* qp, T* lo, T* hi) {
-  T dl[7], dr[7], den[7];
-  bool pos[7];
 #pragma unroll
-  for (int n = 0; n < 7; ++n) {
-    dl[n] = qc[n] - qm[n];
-    dr[n] = qp[n] - qc[n];
-    pos[n] = gt0(dl[n] * dr[n]);
-    den[n] = pos[n] ? dl[n] + dr[n] : T(1);
-  }
-  T rc[7];
-#pragma unroll
-  for (int n = 0; n < 7; ++n) rc[n] = sizeof(T) == 8 ? inv(den[n]) : T(1) / den[n];
-#pragma unroll
-  for (int n = 0; n < 7; ++n) {
-#ifdef VL2_VALUE_SAFE
-    const T half = pos[n] ? (dl[n] * dr[n]) * rc[n] : T(0);
-    lo[n] = qc[n] - half;
-    hi[n] = qc[n] + half;
-#else
-    const T pr = pos[n] ? dl[n] * dr[n] : T(0);
-    lo[n] = fma(-pr, rc[n], qc[n]);
-    hi[n] = fma(pr, rc[n], qc[n]);
-#endif
-  }
+  for (int n = 0; n < 7; ++n) plm_var_faces<T>(qm[n], qc[n], qp[n], lo[n], hi[n]);
 }
 
 // PPM (Sec. 3.2.1).  Face value: eq. ppm-uniform-weights, q_{i-1/2} = 7/12 (q_{i-1} + q_i) - 1/12 (q_{i-2} + q_{i+1});
