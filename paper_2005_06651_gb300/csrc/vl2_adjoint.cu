@@ -673,110 +673,163 @@ __device__ __forceinline__ bool moved_along(const Geom& g, int kind, const int* 
   return kind == 1 + q && li[q] == NG + g.mb[q] && locq < g.nb[q] - 1 && ghost_elsewhere(g, kind, li, q);
 }
 
-// PASS (the direction of the one-dimensional pass for the cells; the face kinds rotate) is a template
-// parameter, so every direction index below is a compile-time constant and the small index arrays stay in
-// registers.
+// Pass direction of element kind `kind` in pass PASS: cells and x-faces take PASS, y-faces PASS+1, z-faces
+// PASS+2 (mod 3).
 template <int PASS>
-__global__ void __launch_bounds__(256) k_adj_ghost_gather(Geom g, double* lu, double* lb0, double* lb1, double* lb2) {
-  const int ex = g.mb[0] + 2 * NG + 1, ey = g.mb[1] + 2 * NG + 1, ez = g.mb[2] + 2 * NG + 1;
-  const long long per = (long long)ex * ey * ez;
+__device__ __forceinline__ int pass_dir(int kind) {
+  return kind == 0 ? PASS : (kind - 1 + PASS) % 3;
+}
+
+// Compact thread spaces of one pass.  For each kind the pass touches only a few indices along its pass
+// direction q (the gather: the NG+2 active indices nearest each end, the only ones a ghost copies from; the
+// clear: the ghost indices and the upper surface), each over the full extents of the other two directions.
+// A flat index within one block is split as kind, then slot s (the index along q), then the two other
+// directions, the lower one fastest.  `slots` is the number of slots per kind.
+struct PassElem {
+  int kind, q, li[3];
+};
+template <int PASS>
+__device__ __forceinline__ bool pass_elem(const Geom& g, long long r, int slots, PassElem& e) {
+  const int ext[3] = {g.mb[0] + 2 * NG + 1, g.mb[1] + 2 * NG + 1, g.mb[2] + 2 * NG + 1};
+  for (int kind = 0; kind < 4; ++kind) {
+    const int q = pass_dir<PASS>(kind), r1 = q == 0 ? 1 : 0, r2 = q == 2 ? 1 : 2;
+    const long long n = (long long)slots * ext[r1] * ext[r2];
+    if (r >= n) {
+      r -= n;
+      continue;
+    }
+    e.kind = kind;
+    e.q = q;
+    e.li[r1] = (int)(r % ext[r1]);
+    e.li[r2] = (int)((r / ext[r1]) % ext[r2]);
+    e.li[q] = (int)(r / ((long long)ext[r1] * ext[r2]));  // the slot, mapped to an index by the caller
+    return true;
+  }
+  return false;
+}
+// Threads per block of one pass: each direction's slots times its other two extents, for the four kinds
+// (cells and x-faces both take direction `pass`).
+inline long long pass_elems(const Geom& g, int slots, int pass) {
+  const long long e0 = g.mb[0] + 2 * NG + 1, e1 = g.mb[1] + 2 * NG + 1, e2 = g.mb[2] + 2 * NG + 1;
+  const long long a[3] = {e1 * e2, e0 * e2, e0 * e1};
+  return (long long)slots * (a[0] + a[1] + a[2] + a[pass]);
+}
+
+// Gather of pass PASS: each target element (an active index along its pass direction q within NG + 1 of a
+// block end: a neighbour's ghost layer, a periodic wrap or an outflow clamp reaches no further, and small
+// blocks are near an end everywhere) collects, in a fixed order, the adjoints of the elements that copy from
+// it.  PASS is a template parameter, so every direction index below is a compile-time constant and the small
+// index arrays stay in registers.
+template <int PASS>
+__global__ void __launch_bounds__(256) k_adj_ghost_gather(Geom g, long long per, double* lu, double* lb0, double* lb1,
+                                                          double* lb2) {
+  constexpr int S = NG + 2;  // targets nearest each end
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= per * g.nblk) return;
   const int b = (int)(t / per);
-  int rem = (int)(t - (long long)b * per);
-  const int li[3] = {rem % ex, (rem / ex) % ey, rem / (ex * ey)};
+  PassElem e;
+  if (!pass_elem<PASS>(g, t - (long long)b * per, 2 * S, e)) return;
+  const int kind = e.kind, q = e.q;
+  int li[3] = {e.li[0], e.li[1], e.li[2]};
+  const int ha = hi_active(g, kind, q);
+  const int slot = li[q];
+  if (slot < S) {
+    li[q] = NG + slot;
+    if (li[q] > ha) return;
+  } else {
+    li[q] = ha - (slot - S);
+    if (li[q] < NG + S) return;  // already a lower target (short blocks)
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    if (li[r] > hi_index(g, kind, r)) return;
   int loc[3];
   loc_of(g, b, loc);
+  if (moved_along(g, kind, li, q, loc[q])) return;  // targets only
   const long long stride[3] = {1LL, (long long)g.sx, (long long)g.sx * g.sy};
   const long long bstride[3] = {1LL, (long long)g.nb[0], (long long)g.nb[0] * g.nb[1]};
   const long long c = cell_off(g, li[2], li[1], li[0]);
-#pragma unroll
-  for (int kind = 0; kind < 4; ++kind) {
-    const int q = kind == 0 ? PASS : (kind - 1 + PASS) % 3;
-    bool ok = true;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) ok = ok && li[r] <= hi_index(g, kind, r);
-    if (!ok || moved_along(g, kind, li, q, loc[q])) continue;  // targets only
-    const bool face = (kind == 1 + q);
-    // only elements within NG + 1 of a block edge along q are the source of a ghost (a neighbour's ghost
-    // layer, a periodic wrap or an outflow clamp reaches no further; small blocks are near an edge
-    // everywhere)
-    if (li[q] - NG > NG + 1 && hi_active(g, kind, q) - li[q] > NG + 1) continue;
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    bool got = false;
-    auto take = [&](long long blk2, long long c2) {
-      if (kind == 0) {
-        const double* U2 = lu + blk2 * 5 * g.box + c2;
-#pragma unroll
-        for (int v = 0; v < 5; ++v) acc[v] += U2[(long long)v * g.box];
-      } else {
-        acc[0] += (kind == 1 ? lb0 : (kind == 2 ? lb1 : lb2))[blk2 * g.box + c2];
-      }
-      got = true;
-    };
-    // an upper-surface face of the block below that is moved onto this lower face
-    if (face && li[q] == NG && loc[q] >= 1 && ghost_elsewhere(g, kind, li, q))
-      take((long long)b - bstride[q], c + (long long)g.mb[q] * stride[q]);
-    // ghosts along q in this block and the blocks within reach along q (distinct, existing) that copy from
-    // here: a ghost of block bq has global index up to bq mb + mb + NG, at most R = 1 + (NG + mb) / mb
-    // blocks away (R <= 4 for mb >= 1)
-    const int R = 1 + (NG + g.mb[q]) / g.mb[q];
-    auto block_at = [&](int dl) -> int {  // block along q at offset dl (wrapped), or -1 beyond an outflow edge
-      int bq = loc[q] + dl;
-      if (bq < 0 || bq >= g.nb[q]) {
-        if (g.bc[dl < 0 ? 2 * q : 2 * q + 1] != BC_PERIODIC) return -1;
-        bq = ((bq % g.nb[q]) + g.nb[q]) % g.nb[q];
-      }
-      return bq;
-    };
-    for (int dl = -R; dl <= R; ++dl) {
-      const int bq = block_at(dl);
-      if (bq < 0) continue;
-      bool dup = false;  // an earlier offset that wraps onto the same block
-      for (int d2 = -R; d2 < dl; ++d2) dup = dup || block_at(d2) == bq;
-      if (dup) continue;
-      const int hi = hi_index(g, kind, q), ha = hi_active(g, kind, q);
-      // the ghosts along q only: indices 0 .. NG-1, then ha+1 .. hi (in that order)
-      for (int gl = 0; gl <= hi; gl = (gl == NG - 1) ? ha + 1 : gl + 1) {
-        int sblk, sloc;
-        source_of_adj(g, q, bq * g.mb[q] + gl - NG, face, sblk, sloc);
-        if (sblk != loc[q] || sloc != li[q]) continue;
-        take((long long)b + (long long)(bq - loc[q]) * bstride[q], c + (long long)(gl - li[q]) * stride[q]);
-      }
-    }
-    if (!got) continue;
+  const bool face = (kind == 1 + q);
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  bool got = false;
+  auto take = [&](long long blk2, long long c2) {
     if (kind == 0) {
-      double* U = lu + (long long)b * 5 * g.box + c;
+      const double* U2 = lu + blk2 * 5 * g.box + c2;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) U[(long long)v * g.box] += acc[v];
+      for (int v = 0; v < 5; ++v) acc[v] += U2[(long long)v * g.box];
     } else {
-      (kind == 1 ? lb0 : (kind == 2 ? lb1 : lb2))[(long long)b * g.box + c] += acc[0];
+      acc[0] += (kind == 1 ? lb0 : (kind == 2 ? lb1 : lb2))[blk2 * g.box + c2];
     }
+    got = true;
+  };
+  // an upper-surface face of the block below that is moved onto this lower face
+  if (face && li[q] == NG && loc[q] >= 1 && ghost_elsewhere(g, kind, li, q))
+    take((long long)b - bstride[q], c + (long long)g.mb[q] * stride[q]);
+  // ghosts along q in this block and the blocks within reach along q (distinct, existing) that copy from
+  // here: a ghost of block bq has global index up to bq mb + mb + NG, at most R = 1 + (NG + mb) / mb
+  // blocks away (R <= 4 for mb >= 1)
+  const int R = 1 + (NG + g.mb[q]) / g.mb[q];
+  auto block_at = [&](int dl) -> int {  // block along q at offset dl (wrapped), or -1 beyond an outflow edge
+    int bq = loc[q] + dl;
+    if (bq < 0 || bq >= g.nb[q]) {
+      if (g.bc[dl < 0 ? 2 * q : 2 * q + 1] != BC_PERIODIC) return -1;
+      bq = ((bq % g.nb[q]) + g.nb[q]) % g.nb[q];
+    }
+    return bq;
+  };
+  for (int dl = -R; dl <= R; ++dl) {
+    const int bq = block_at(dl);
+    if (bq < 0) continue;
+    bool dup = false;  // an earlier offset that wraps onto the same block
+    for (int d2 = -R; d2 < dl; ++d2) dup = dup || block_at(d2) == bq;
+    if (dup) continue;
+    const int hi = hi_index(g, kind, q);
+    // the ghosts along q only: indices 0 .. NG-1, then ha+1 .. hi (in that order)
+    for (int gl = 0; gl <= hi; gl = (gl == NG - 1) ? ha + 1 : gl + 1) {
+      int sblk, sloc;
+      source_of_adj(g, q, bq * g.mb[q] + gl - NG, face, sblk, sloc);
+      if (sblk != loc[q] || sloc != li[q]) continue;
+      take((long long)b + (long long)(bq - loc[q]) * bstride[q], c + (long long)(gl - li[q]) * stride[q]);
+    }
+  }
+  if (!got) return;
+  if (kind == 0) {
+    double* U = lu + (long long)b * 5 * g.box + c;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) U[(long long)v * g.box] += acc[v];
+  } else {
+    (kind == 1 ? lb0 : (kind == 2 ? lb1 : lb2))[(long long)b * g.box + c] += acc[0];
   }
 }
 
-__global__ void k_adj_ghost_clear(Geom g, int pass, double* lu, double* lb0, double* lb1, double* lb2) {
-  const int ex = g.mb[0] + 2 * NG + 1, ey = g.mb[1] + 2 * NG + 1, ez = g.mb[2] + 2 * NG + 1;
-  const long long per = (long long)ex * ey * ez;
+// Clear of pass PASS: the elements moved along their pass direction (its ghost indices 0 .. NG-1 and
+// ha+1 .. hi, and the upper-surface faces the rule above moves, index ha) drop the adjoints just gathered.
+template <int PASS>
+__global__ void __launch_bounds__(256) k_adj_ghost_clear(Geom g, long long per, double* lu, double* lb0, double* lb1,
+                                                         double* lb2) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= per * g.nblk) return;
   const int b = (int)(t / per);
-  int rem = (int)(t - (long long)b * per);
-  const int li[3] = {rem % ex, (rem / ex) % ey, rem / (ex * ey)};
+  PassElem e;
+  if (!pass_elem<PASS>(g, t - (long long)b * per, 2 * NG + 1, e)) return;
+  const int kind = e.kind, q = e.q;
+  int li[3] = {e.li[0], e.li[1], e.li[2]};
+  const int ha = hi_active(g, kind, q), hi = hi_index(g, kind, q);
+  const int slot = li[q];
+  li[q] = slot < NG ? slot : ha + (slot - NG);  // 0 .. NG-1, then ha .. ha+NG
+  if (slot >= NG && li[q] > hi) return;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+    if (li[r] > hi_index(g, kind, r)) return;
   int loc[3];
   loc_of(g, b, loc);
+  if (!moved_along(g, kind, li, q, loc[q])) return;
   const long long c = cell_off(g, li[2], li[1], li[0]);
-  for (int kind = 0; kind < 4; ++kind) {
-    const int q = kind == 0 ? pass : (kind - 1 + pass) % 3;
-    bool ok = true;
-    for (int r = 0; r < 3; ++r) ok = ok && li[r] <= hi_index(g, kind, r);
-    if (!ok || !moved_along(g, kind, li, q, loc[q])) continue;
-    if (kind == 0) {
-      double* U = lu + (long long)b * 5 * g.box + c;
-      for (int v = 0; v < 5; ++v) U[(long long)v * g.box] = 0.0;
-    } else {
-      (kind == 1 ? lb0 : (kind == 2 ? lb1 : lb2))[(long long)b * g.box + c] = 0.0;
-    }
+  if (kind == 0) {
+    double* U = lu + (long long)b * 5 * g.box + c;
+    for (int v = 0; v < 5; ++v) U[(long long)v * g.box] = 0.0;
+  } else {
+    (kind == 1 ? lb0 : (kind == 2 ? lb1 : lb2))[(long long)b * g.box + c] = 0.0;
   }
 }
 
@@ -984,22 +1037,21 @@ cudaError_t adj_prim(const Geom& g, const AdjArrays& j, const double* W, int lam
 }
 
 cudaError_t adj_ghosts(const Geom& g, const AdjArrays& j, int lam_reg, cudaStream_t st) {
-  const long long n = (long long)(g.mb[0] + 2 * NG + 1) * (g.mb[1] + 2 * NG + 1) * (g.mb[2] + 2 * NG + 1) * g.nblk;
+  double* U = j.lu[lam_reg];
+  double* const* Bl = j.lb[lam_reg];
   for (int pass = 0; pass < 3; ++pass) {
-    if (pass == 0)
-      k_adj_ghost_gather<0><<<grid_of(n, AT), AT, 0, st>>>(g, j.lu[lam_reg], j.lb[lam_reg][0], j.lb[lam_reg][1],
-                                                           j.lb[lam_reg][2]);
-    else if (pass == 1)
-      k_adj_ghost_gather<1><<<grid_of(n, AT), AT, 0, st>>>(g, j.lu[lam_reg], j.lb[lam_reg][0], j.lb[lam_reg][1],
-                                                           j.lb[lam_reg][2]);
-    else
-      k_adj_ghost_gather<2><<<grid_of(n, AT), AT, 0, st>>>(g, j.lu[lam_reg], j.lb[lam_reg][0], j.lb[lam_reg][1],
-                                                           j.lb[lam_reg][2]);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_adj_ghost_clear<<<grid_of(n, AT), AT, 0, st>>>(g, pass, j.lu[lam_reg], j.lb[lam_reg][0], j.lb[lam_reg][1],
-                                                     j.lb[lam_reg][2]);
-    e = cudaGetLastError();
+    const long long pg = pass_elems(g, 2 * (NG + 2), pass), pc = pass_elems(g, 2 * NG + 1, pass);  // per block
+    if (pass == 0) {
+      k_adj_ghost_gather<0><<<grid_of(pg * g.nblk, AT), AT, 0, st>>>(g, pg, U, Bl[0], Bl[1], Bl[2]);
+      k_adj_ghost_clear<0><<<grid_of(pc * g.nblk, AT), AT, 0, st>>>(g, pc, U, Bl[0], Bl[1], Bl[2]);
+    } else if (pass == 1) {
+      k_adj_ghost_gather<1><<<grid_of(pg * g.nblk, AT), AT, 0, st>>>(g, pg, U, Bl[0], Bl[1], Bl[2]);
+      k_adj_ghost_clear<1><<<grid_of(pc * g.nblk, AT), AT, 0, st>>>(g, pc, U, Bl[0], Bl[1], Bl[2]);
+    } else {
+      k_adj_ghost_gather<2><<<grid_of(pg * g.nblk, AT), AT, 0, st>>>(g, pg, U, Bl[0], Bl[1], Bl[2]);
+      k_adj_ghost_clear<2><<<grid_of(pc * g.nblk, AT), AT, 0, st>>>(g, pc, U, Bl[0], Bl[1], Bl[2]);
+    }
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -847,21 +847,38 @@ vl2_status vl2_step_record(vl2_mesh* m, double dt, void* tape) {
   const size_t per = (size_t)g.nblk * g.box * sizeof(double);
   vl2_status s = ensure_prims(m);
   if (s != VL2_OK) return s;
-  // the VL2 cycle of vl2_step, keeping what its adjoint reads
+  // The VL2 cycle of vl2_step, keeping what its adjoint reads.  The predictor writes its face field, and
+  // cons->prim the corrector's primitives, straight into the tape: the mesh's own register-1 field and
+  // primitive arrays are next needed by the following cycle, so for this one the mesh points at the tape
+  // (restored on every exit).  The TMA-staged sweeps' tensor maps describe the mesh's own primitive array,
+  // so with them the primitives are copied instead.
+  struct Redirect {
+    vl2_mesh* m;
+    void* w;
+    double* b1[3];
+    void restore() {
+      m->a.w = w;
+      for (int d = 0; d < 3; ++d) m->a.b[1][d] = b1[d];
+    }
+    ~Redirect() { restore(); }
+  } keep{m, m->a.w, {m->a.b[1][0], m->a.b[1][1], m->a.b[1][2]}};
+  const bool w_direct = !vl2::flux_tma_applies(m->view(), vl2::REC_PLM, m->fs, m->max_mb());
   VL2_CHECK(m, cudaMemcpyAsync(t.w0, m->a.w, 8 * per, cudaMemcpyDeviceToDevice, st));
   for (int d = 0; d < 3; ++d) VL2_CHECK(m, cudaMemcpyAsync(t.b0[d], m->a.b[0][d], per, cudaMemcpyDeviceToDevice, st));
   VL2_CHECK(m, k_fluxes(m, 0, VL2_DC));
   if ((s = keep_mass_fluxes(m, t.m1, t.mk)) != VL2_OK) return s;
   VL2_CHECK(m, k_emfs(m));
+  for (int d = 0; d < 3; ++d) m->a.b[1][d] = t.b1[d];
   VL2_CHECK(m, k_update(m, 0, 1, 0.5 * dt));
   VL2_CHECK(m, k_ghosts(m, 1));
+  if (w_direct) m->a.w = t.w1;
   VL2_CHECK(m, k_prim(m, 1, false));
-  VL2_CHECK(m, cudaMemcpyAsync(t.w1, m->a.w, 8 * per, cudaMemcpyDeviceToDevice, st));
-  for (int d = 0; d < 3; ++d) VL2_CHECK(m, cudaMemcpyAsync(t.b1[d], m->a.b[1][d], per, cudaMemcpyDeviceToDevice, st));
+  if (!w_direct) VL2_CHECK(m, cudaMemcpyAsync(t.w1, m->a.w, 8 * per, cudaMemcpyDeviceToDevice, st));
   VL2_CHECK(m, k_fluxes(m, 1, VL2_PLM));
   if ((s = keep_mass_fluxes(m, t.m2, t.mk)) != VL2_OK) return s;
   VL2_CHECK(m, k_emfs(m));
   VL2_CHECK(m, k_update(m, 0, 0, dt, 1.0, 0.0, 1));
+  keep.restore();  // the mesh's own arrays again
   VL2_CHECK(m, k_ghosts(m, 0));
   VL2_CHECK(m, cudaMemsetAsync(m->a.scal + vl2::SC_MAXRATE, 0, sizeof(unsigned long long), st));
   VL2_CHECK(m, k_prim(m, 0, true));
