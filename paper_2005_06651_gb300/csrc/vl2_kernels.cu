@@ -37,8 +37,14 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
   const long long per = (long long)ex * ey * ez;
   const long long t = (long long)tile * blockDim.x + threadIdx.x;
   // kept for the CFL rate: the cell's FP64 primitives and a single-precision estimate of its rate
+#ifndef VL2_VALUE_SAFE
+  constexpr bool LEAN = sizeof(TW) == 4;
+#else
+  constexpr bool LEAN = false;
+#endif
   bool active = false;
   double id = 0.0, p = 0.0, vx = 0.0, vy = 0.0, vz = 0.0, bcx = 0.0, bcy = 0.0, bcz = 0.0;
+  [[maybe_unused]] float s32v[6];
   float r32 = 0.0f;
   if (t < per * g.nblk) {
     const int b = (int)(t / per);
@@ -52,9 +58,12 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
     const double* B0 = V.a.b[reg][0];
     const double* B1 = V.a.b[reg][1];
     const double* B2 = V.a.b[reg][2];
-    bcx = 0.5 * (B0[fb] + B0[fb + 1]);
-    bcy = 0.5 * (B1[fb] + B1[fb + g.sx]);
-    bcz = 0.5 * (B2[fb] + B2[fb + (long long)g.sx * g.sy]);
+    // LEAN (FP32 primitives): bc* hold the sums of the two face values (2 b_c) and v* the momenta; the
+    // halvings and the FP64 products M / rho are taken only where an FP64 result needs them (the CFL
+    // candidates), the stored FP32 velocity being the FP32 product of M and 1/rho
+    bcx = LEAN ? B0[fb] + B0[fb + 1] : 0.5 * (B0[fb] + B0[fb + 1]);
+    bcy = LEAN ? B1[fb] + B1[fb + g.sx] : 0.5 * (B1[fb] + B1[fb + g.sx]);
+    bcz = LEAN ? B2[fb] + B2[fb + (long long)g.sx * g.sy] : 0.5 * (B2[fb] + B2[fb + (long long)g.sx * g.sy]);
     double* Ub = V.a.u[reg] + (long long)b * 5 * g.box + c;
     double d = Ub[0];
     const double m1 = Ub[g.box], m2 = Ub[2 * g.box], m3 = Ub[3 * g.box];
@@ -66,11 +75,12 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
       fired = true;
     }
     id = rcp_nr(d);  // d >= dfloor, a positive normal number
-    vx = m1 * id;
-    vy = m2 * id;
-    vz = m3 * id;
+    vx = LEAN ? m1 : m1 * id;
+    vy = LEAN ? m2 : m2 * id;
+    vz = LEAN ? m3 : m3 * id;
     const double ke = 0.5 * ((m1 * m1 + m2 * m2) + m3 * m3) * id;
-    const double me = 0.5 * ((bcx * bcx + bcy * bcy) + bcz * bcz);
+    // (2 b)^2 / 8 is b^2 / 2 exactly (powers of two), so both forms give the same bits
+    const double me = (LEAN ? 0.125 : 0.5) * ((bcx * bcx + bcy * bcy) + bcz * bcz);
     p = g.gm1 * (e - ke - me);
     if (p < g.pfloor) {
       p = g.pfloor;
@@ -98,8 +108,27 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
       }
     }
     TW* Wb = static_cast<TW*>(V.a.w) + (long long)b * 8 * g.box + c;
-    const TW wx = to_wtype<TW>(vx), wy = to_wtype<TW>(vy), wz = to_wtype<TW>(vz);
-    const TW ux = to_wtype<TW>(bcx), uy = to_wtype<TW>(bcy), uz = to_wtype<TW>(bcz);
+    TW wx, wy, wz, ux, uy, uz;
+    if constexpr (LEAN) {
+      const float fid = to_f32(id);
+      wx = to_f32(vx) * fid;
+      wy = to_f32(vy) * fid;
+      wz = to_f32(vz) * fid;
+      ux = 0.5f * to_f32(bcx);
+      uy = 0.5f * to_f32(bcy);
+      uz = 0.5f * to_f32(bcz);
+    } else {
+      wx = to_wtype<TW>(vx), wy = to_wtype<TW>(vy), wz = to_wtype<TW>(vz);
+      ux = to_wtype<TW>(bcx), uy = to_wtype<TW>(bcy), uz = to_wtype<TW>(bcz);
+    }
+    if constexpr (LEAN) {  // the FP32 screen below reads the FP32 primitives
+      s32v[0] = (float)wx;
+      s32v[1] = (float)wy;
+      s32v[2] = (float)wz;
+      s32v[3] = (float)ux;
+      s32v[4] = (float)uy;
+      s32v[5] = (float)uz;
+    }
     Wb[0] = to_wtype<TW>(d);
     Wb[g.box] = wx;
     Wb[2 * g.box] = wy;
@@ -117,11 +146,12 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
     if (DT && active) {
       // single-precision estimate of the rate (relative error well below 1e-5)
       const float fid = to_f32(id), fp = to_f32(p), fg = (float)g.gamma;
-      const float fx = to_f32(bcx), fy = to_f32(bcy), fz = to_f32(bcz);
+      const float fx = LEAN ? s32v[3] : to_f32(bcx), fy = LEAN ? s32v[4] : to_f32(bcy), fz = LEAN ? s32v[5] : to_f32(bcz);
+      const float ax = LEAN ? s32v[0] : to_f32(vx), ay = LEAN ? s32v[1] : to_f32(vy), az = LEAN ? s32v[2] : to_f32(vz);
       const float x2 = fx * fx, y2 = fy * fy, z2 = fz * fz;
-      const float sx = (fabsf(to_f32(vx)) + fast_speed_r(fid, fp, x2, y2 + z2, fg)) * (float)g.idx[0];
-      const float sy = (fabsf(to_f32(vy)) + fast_speed_r(fid, fp, y2, z2 + x2, fg)) * (float)g.idx[1];
-      const float sz = (fabsf(to_f32(vz)) + fast_speed_r(fid, fp, z2, x2 + y2, fg)) * (float)g.idx[2];
+      const float sx = (fabsf(ax) + fast_speed_r(fid, fp, x2, y2 + z2, fg)) * (float)g.idx[0];
+      const float sy = (fabsf(ay) + fast_speed_r(fid, fp, y2, z2 + x2, fg)) * (float)g.idx[1];
+      const float sz = (fabsf(az) + fast_speed_r(fid, fp, z2, x2 + y2, fg)) * (float)g.idx[2];
       r32 = fmaxf(fmaxf(sx, sy), sz);
       if (sx != sx || sy != sy || sz != sz) r32 = __int_as_float(0x7fc00000);  // keep a NaN visible
     }
@@ -168,12 +198,12 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
       const int slot = base + __popc(lmask & ((1u << lane) - 1u));  // < blockDim.x: one slot per thread at most
       cin[0][slot] = id;
       cin[1][slot] = p;
-      cin[2][slot] = vx;
-      cin[3][slot] = vy;
-      cin[4][slot] = vz;
-      cin[5][slot] = bcx;
-      cin[6][slot] = bcy;
-      cin[7][slot] = bcz;
+      cin[2][slot] = LEAN ? vx * id : vx;  // the FP64 velocity and cell field, as in the FP64 form
+      cin[3][slot] = LEAN ? vy * id : vy;
+      cin[4][slot] = LEAN ? vz * id : vz;
+      cin[5][slot] = LEAN ? 0.5 * bcx : bcx;
+      cin[6][slot] = LEAN ? 0.5 * bcy : bcy;
+      cin[7][slot] = LEAN ? 0.5 * bcz : bcz;
     }
     __syncthreads();
     unsigned long long rate_bits = 0ULL;
