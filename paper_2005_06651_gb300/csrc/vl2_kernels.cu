@@ -758,7 +758,7 @@ __global__ void __launch_bounds__(256, 4) k_update(MeshView single, const MeshVi
       src[1] = rho * ax;
       src[2] = rho * ay;
       src[3] = rho * az;
-      src[4] = (Us[g.box] * ax + Us[2 * g.box] * ay) + Us[3 * g.box] * az;
+      src[4] = fma(Us[3 * g.box], az, fma(Us[2 * g.box], ay, Us[g.box] * ax));
     }
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -814,6 +814,175 @@ __global__ void __launch_bounds__(256, 4) k_update(MeshView single, const MeshVi
   }
 }
 
+// The plain (VL2-stage) update of the mixed precision for two adjacent nodes along x per thread, with paired
+// loads and stores (float2 for the FP32 fluxes and EMFs, double2 for the FP64 registers; the first node's x
+// index ng + 2p is even, and rows and arrays start on 16-byte boundaries).  Per node it performs the
+// operations of k_update<float, true> in the same order, so it gives the same bits; a face shared by the
+// two cells is read once.  Meshes with an even ghost width only; the second node of the last pair of a row
+// lies past the block when mb_x is even and is skipped.
+template <class T>
+__device__ __forceinline__ void ld_pair(const T* p, T& a, T& b);
+template <>
+__device__ __forceinline__ void ld_pair<float>(const float* p, float& a, float& b) {
+  const float2 v = *reinterpret_cast<const float2*>(p);
+  a = v.x;
+  b = v.y;
+}
+template <>
+__device__ __forceinline__ void ld_pair<double>(const double* p, double& a, double& b) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void st_pair(double* p, double a, double b) { *reinterpret_cast<double2*>(p) = make_double2(a, b); }
+
+__global__ void __launch_bounds__(256, 4) k_update_pair(MeshView single, int base_reg, int out_reg, double h,
+                                                        int stage_reg) {
+  __shared__ MeshView sv;
+  int tile;
+  const MeshView& V = stage_view(sv, single, nullptr, nullptr, tile);
+  const Geom& g = V.g;
+  const int ex = g.mb[0] + 1, ey = g.mb[1] + 1, ez = g.mb[2] + 1;
+  const int px = (ex + 1) / 2;
+  const long long per = (long long)px * ey * ez;
+  const long long t = (long long)tile * blockDim.x + threadIdx.x;
+  if (t >= per * g.nblk) return;
+  const int b = (int)(t / per);
+  int rem = (int)(t - (long long)b * per);
+  const int i0 = 2 * (rem % px) + g.ng;
+  const int j = (rem / px) % ey + g.ng, k = rem / (px * ey) + g.ng;
+  const bool node1 = i0 + 1 <= g.ng + g.mb[0];  // the second node exists
+  const bool in0 = i0 < g.ng + g.mb[0], in1 = i0 + 1 < g.ng + g.mb[0];  // cells along x
+  const bool iny = j < g.ng + g.mb[1], inz = k < g.ng + g.mb[2];
+  const long long c = cell_off(g, k, j, i0);
+  const long long sy = g.sx, sz = (long long)g.sx * g.sy;
+  const double* Ubase = V.a.u[base_reg];
+  double* Uout = V.a.u[out_reg];
+  const float* F[3] = {static_cast<const float*>(V.a.f[0]) + (long long)b * 7 * g.box + c,
+                       static_cast<const float*>(V.a.f[1]) + (long long)b * 7 * g.box + c,
+                       static_cast<const float*>(V.a.f[2]) + (long long)b * 7 * g.box + c};
+  if (in0 && iny && inz) {
+    const long long ub = (long long)b * 5 * g.box + c;
+    double src0[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, src1[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const bool forced = V.a.acc != nullptr;
+    if (forced) {  // from the stage state, before an in-place update overwrites it
+      const double* Us = V.a.u[stage_reg] + ub;
+      const double* Ab = V.a.acc + (long long)b * 3 * g.box + c;
+      double r0, r1, ax0, ax1, ay0, ay1, az0, az1, m10, m11, m20, m21, m30, m31;
+      ld_pair(Us, r0, r1);
+      ld_pair(Ab, ax0, ax1);
+      ld_pair(Ab + g.box, ay0, ay1);
+      ld_pair(Ab + 2 * g.box, az0, az1);
+      ld_pair(Us + g.box, m10, m11);
+      ld_pair(Us + 2 * g.box, m20, m21);
+      ld_pair(Us + 3 * g.box, m30, m31);
+      src0[1] = r0 * ax0;
+      src0[2] = r0 * ay0;
+      src0[3] = r0 * az0;
+      src0[4] = fma(m30, az0, fma(m20, ay0, m10 * ax0));
+      src1[1] = r1 * ax1;
+      src1[2] = r1 * ay1;
+      src1[3] = r1 * az1;
+      src1[4] = fma(m31, az1, fma(m21, ay1, m11 * ax1));
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      double d0[3], d1[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        int comp;
+        if (v == 0)
+          comp = 0;
+        else if (v == 4)
+          comp = 4;
+        else {
+          const int m = v - 1;
+          comp = (m == d) ? 1 : ((m == (d + 1) % 3) ? 2 : 3);
+        }
+        const float* fp = F[d] + (long long)comp * g.box;
+        float a0, a1, b0, b1;
+        ld_pair(fp, a0, a1);
+        if (d == 0) {
+          b0 = a1;
+          b1 = in1 ? fp[2] : 0.0f;
+        } else {
+          ld_pair(fp + (d == 1 ? sy : sz), b0, b1);
+        }
+        d0[d] = to_f64(b0) - to_f64(a0);
+        d1[d] = to_f64(b1) - to_f64(a1);
+      }
+      const long long o = ub + (long long)v * g.box;
+      double acc0, acc1;
+      ld_pair(Ubase + o, acc0, acc1);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        acc0 = fma(-(h * g.idx[d]), d0[d], acc0);
+        acc1 = fma(-(h * g.idx[d]), d1[d], acc1);
+      }
+      if (forced) {
+        acc0 = fma(h, src0[v], acc0);
+        acc1 = fma(h, src1[v], acc1);
+      }
+      if (in1)
+        st_pair(Uout + o, acc0, acc1);
+      else
+        Uout[o] = acc0;
+    }
+  }
+  const float* E[3] = {static_cast<const float*>(V.a.e[0]) + (long long)b * g.box + c,
+                       static_cast<const float*>(V.a.e[1]) + (long long)b * g.box + c,
+                       static_cast<const float*>(V.a.e[2]) + (long long)b * g.box + c};
+  const long long o = (long long)b * g.box + c;
+  // face field fd = 0: B1 -= (h/dy) dE3/dy, += (h/dz) dE2/dz at both nodes (transversally inside)
+  if (iny && inz) {
+    float p0, p1, q0, q1, r0, r1, s0, s1;
+    ld_pair(E[2], p0, p1);
+    ld_pair(E[2] + sy, q0, q1);
+    ld_pair(E[1], r0, r1);
+    ld_pair(E[1] + sz, s0, s1);
+    double b0, b1;
+    ld_pair(V.a.b[base_reg][0] + o, b0, b1);
+    const double n0 = fma(h * g.idx[2], to_f64(s0) - to_f64(r0), fma(-(h * g.idx[1]), to_f64(q0) - to_f64(p0), b0));
+    const double n1 = fma(h * g.idx[2], to_f64(s1) - to_f64(r1), fma(-(h * g.idx[1]), to_f64(q1) - to_f64(p1), b1));
+    if (node1)
+      st_pair(V.a.b[out_reg][0] + o, n0, n1);
+    else
+      V.a.b[out_reg][0][o] = n0;
+  }
+  // fd = 1: B2 -= (h/dz) dE1/dz, += (h/dx) dE3/dx (inside along z and x)
+  if (inz && in0) {
+    float p0, p1, q0, q1, r0, r1;
+    ld_pair(E[0], p0, p1);
+    ld_pair(E[0] + sz, q0, q1);
+    ld_pair(E[2], r0, r1);
+    const float r2 = in1 ? E[2][2] : 0.0f;
+    double b0, b1;
+    ld_pair(V.a.b[base_reg][1] + o, b0, b1);
+    const double n0 = fma(h * g.idx[0], to_f64(r1) - to_f64(r0), fma(-(h * g.idx[2]), to_f64(q0) - to_f64(p0), b0));
+    const double n1 = fma(h * g.idx[0], to_f64(r2) - to_f64(r1), fma(-(h * g.idx[2]), to_f64(q1) - to_f64(p1), b1));
+    if (in1)
+      st_pair(V.a.b[out_reg][1] + o, n0, n1);
+    else
+      V.a.b[out_reg][1][o] = n0;
+  }
+  // fd = 2: B3 -= (h/dx) dE2/dx, += (h/dy) dE1/dy (inside along x and y)
+  if (in0 && iny) {
+    float p0, p1, q0, q1, r0, r1;
+    ld_pair(E[1], p0, p1);
+    const float p2 = in1 ? E[1][2] : 0.0f;
+    ld_pair(E[0], q0, q1);
+    ld_pair(E[0] + sy, r0, r1);
+    double b0, b1;
+    ld_pair(V.a.b[base_reg][2] + o, b0, b1);
+    const double n0 = fma(h * g.idx[1], to_f64(r0) - to_f64(q0), fma(-(h * g.idx[0]), to_f64(p1) - to_f64(p0), b0));
+    const double n1 = fma(h * g.idx[1], to_f64(r1) - to_f64(q1), fma(-(h * g.idx[0]), to_f64(p2) - to_f64(p1), b1));
+    if (in1)
+      st_pair(V.a.b[out_reg][2] + o, n0, n1);
+    else
+      V.a.b[out_reg][2][o] = n0;
+  }
+}
+
 cudaError_t launch_update(const MeshView& v, const Dispatch* d, int base_reg, int out_reg, double h,
                           const double* dtbox, double beta, cudaStream_t st, double g_base, double g_other,
                           int stage_reg) {
@@ -823,6 +992,14 @@ cudaError_t launch_update(const MeshView& v, const Dispatch* d, int base_reg, in
   const MeshView* vs = d ? d->views : nullptr;
   const WorkItem* wk = d ? d->work : nullptr;
   const bool plain = g_other == 0.0 && g_base == 1.0;  // U_base + h L: the VL2 stages
+#ifndef VL2_VALUE_SAFE
+  if (v.a.mixed && plain && !d && v.g.ng % 2 == 0) {  // two nodes per thread (one mesh, even ghost width)
+    const Geom& g = v.g;
+    const long long pairs = (long long)((g.mb[0] + 2) / 2) * (g.mb[1] + 1) * (g.mb[2] + 1) * g.nblk;
+    k_update_pair<<<(unsigned)((pairs + THREADS - 1) / THREADS), THREADS, 0, st>>>(v, base_reg, out_reg, h, stage_reg);
+    return cudaGetLastError();
+  }
+#endif
   if (v.a.mixed) {
     if (plain)
       k_update<float, true><<<(unsigned)grid, THREADS, 0, st>>>(v, vs, wk, base_reg, out_reg, h, dtbox, beta, g_base,
