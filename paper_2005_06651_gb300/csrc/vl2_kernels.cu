@@ -494,6 +494,40 @@ cudaError_t launch_scalar_fluxes(const MeshView& v, int recon, int dir, cudaStre
   return launch_scalar_dir<2, double>(v, recon, st);
 }
 
+// The L form of the register update with its roundings written out (fused multiply-adds in the fast build,
+// separate products and sums in the value-safe build, which contracts nothing), so that every kernel that
+// applies it (the one-node and two-node updates, the scalar update) gives the same bits:
+//   div = ((dF_x/dx + dF_y/dy) + dF_z/dz),  out = base + h L,  base = g_base U_base + g_other U_other.
+__device__ __forceinline__ double div3(const double* df, const double* idx) {
+#ifndef VL2_VALUE_SAFE
+  return fma(df[2], idx[2], fma(df[1], idx[1], df[0] * idx[0]));
+#else
+  return (df[0] * idx[0] + df[1] * idx[1]) + df[2] * idx[2];
+#endif
+}
+__device__ __forceinline__ double stage_base(bool plain, double ub, double uo, double g_base, double g_other) {
+#ifndef VL2_VALUE_SAFE
+  return plain ? ub : fma(g_other, uo, g_base * ub);
+#else
+  return plain ? ub : g_base * ub + g_other * uo;
+#endif
+}
+__device__ __forceinline__ double plus_hl(double base, double h, double L) {
+#ifndef VL2_VALUE_SAFE
+  return fma(h, L, base);
+#else
+  return base + h * L;
+#endif
+}
+// (dE_b / dx_a - dE_a / dx_b) of a face field's CT curl
+__device__ __forceinline__ double curl2(double deb, double ia, double dea, double ib) {
+#ifndef VL2_VALUE_SAFE
+  return fma(deb, ia, -(dea * ib));
+#else
+  return deb * ia - dea * ib;
+#endif
+}
+
 // Register update of the scalar masses, written as the FP64 conserved variables' update in k_update (same
 // association, same weights), so that a unit scalar stays bitwise equal to the density.
 template <bool PLAIN>
@@ -519,9 +553,8 @@ __global__ void __launch_bounds__(256) k_scalar_update(MeshView V, int base_reg,
     double df[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) df[d] = V.a.fsc[d][o + stride[d]] - V.a.fsc[d][o];
-    const double dv = (df[0] * g.idx[0] + df[1] * g.idx[1]) + df[2] * g.idx[2];
-    const double L = -dv;
-    Sout[o] = (PLAIN ? Sbase[o] : g_base * Sbase[o] + g_other * Soth[o]) + h * L;
+    const double L = -div3(df, g.idx);
+    Sout[o] = plus_hl(stage_base(PLAIN, Sbase[o], PLAIN ? 0.0 : Soth[o], g_base, g_other), h, L);
   }
 }
 
@@ -787,9 +820,9 @@ __global__ void __launch_bounds__(256, 4) k_update(MeshView single, const MeshVi
         continue;
       }
 #endif
-      const double dv = (df[0] * g.idx[0] + df[1] * g.idx[1]) + df[2] * g.idx[2];
-      const double L = forced ? -dv + src[v] : -dv;
-      Uout[o] = (PLAIN ? Ubase[o] : g_base * Ubase[o] + g_other * Uoth[o]) + h * L;
+      const double dv = div3(df, g.idx);
+      const double L = forced ? src[v] - dv : -dv;
+      Uout[o] = plus_hl(stage_base(PLAIN, Ubase[o], PLAIN ? 0.0 : Uoth[o], g_base, g_other), h, L);
     }
   }
   const double* Bb[3] = {Bb0, Bb1, Bb2};
@@ -809,17 +842,17 @@ __global__ void __launch_bounds__(256, 4) k_update(MeshView single, const MeshVi
       continue;
     }
 #endif
-    const double curl = deb * g.idx[a] - dea * g.idx[bq];
-    Bo[fd][o] = (PLAIN ? Bb[fd][o] : g_base * Bb[fd][o] + g_other * Bx[fd][o]) + h * (-curl);
+    const double curl = curl2(deb, g.idx[a], dea, g.idx[bq]);
+    Bo[fd][o] = plus_hl(stage_base(PLAIN, Bb[fd][o], PLAIN ? 0.0 : Bx[fd][o], g_base, g_other), h, -curl);
   }
 }
 
-// The plain (VL2-stage) update of the mixed precision for two adjacent nodes along x per thread, with paired
-// loads and stores (float2 for the FP32 fluxes and EMFs, double2 for the FP64 registers; the first node's x
-// index ng + 2p is even, and rows and arrays start on 16-byte boundaries).  Per node it performs the
-// operations of k_update<float, true> in the same order, so it gives the same bits; a face shared by the
-// two cells is read once.  Meshes with an even ghost width only; the second node of the last pair of a row
-// lies past the block when mb_x is even and is skipped.
+// The plain (VL2-stage) update for two adjacent nodes along x per thread, with paired loads and stores
+// (float2 / double2 for the fluxes and EMFs, double2 for the FP64 registers; the first node's x index
+// ng + 2p is even, and rows and arrays start on 16-byte boundaries).  Per node it performs the operations of
+// k_update<T, true> in the same order (the accumulated form with FP32 fluxes, the L form in FP64), so it
+// gives the same bits; a face shared by the two cells is read once.  Meshes with an even ghost width only;
+// the second node of the last pair of a row lies past the block when mb_x is even and is skipped.
 template <class T>
 __device__ __forceinline__ void ld_pair(const T* p, T& a, T& b);
 template <>
@@ -836,8 +869,10 @@ __device__ __forceinline__ void ld_pair<double>(const double* p, double& a, doub
 }
 __device__ __forceinline__ void st_pair(double* p, double a, double b) { *reinterpret_cast<double2*>(p) = make_double2(a, b); }
 
+template <class T>
 __global__ void __launch_bounds__(256, 4) k_update_pair(MeshView single, int base_reg, int out_reg, double h,
                                                         int stage_reg) {
+  constexpr bool ACC = sizeof(T) == 4;  // the accumulated form (FP32 fluxes); else the L form
   __shared__ MeshView sv;
   int tile;
   const MeshView& V = stage_view(sv, single, nullptr, nullptr, tile);
@@ -858,9 +893,9 @@ __global__ void __launch_bounds__(256, 4) k_update_pair(MeshView single, int bas
   const long long sy = g.sx, sz = (long long)g.sx * g.sy;
   const double* Ubase = V.a.u[base_reg];
   double* Uout = V.a.u[out_reg];
-  const float* F[3] = {static_cast<const float*>(V.a.f[0]) + (long long)b * 7 * g.box + c,
-                       static_cast<const float*>(V.a.f[1]) + (long long)b * 7 * g.box + c,
-                       static_cast<const float*>(V.a.f[2]) + (long long)b * 7 * g.box + c};
+  const T* F[3] = {static_cast<const T*>(V.a.f[0]) + (long long)b * 7 * g.box + c,
+                   static_cast<const T*>(V.a.f[1]) + (long long)b * 7 * g.box + c,
+                   static_cast<const T*>(V.a.f[2]) + (long long)b * 7 * g.box + c};
   if (in0 && iny && inz) {
     const long long ub = (long long)b * 5 * g.box + c;
     double src0[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, src1[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -899,12 +934,12 @@ __global__ void __launch_bounds__(256, 4) k_update_pair(MeshView single, int bas
           const int m = v - 1;
           comp = (m == d) ? 1 : ((m == (d + 1) % 3) ? 2 : 3);
         }
-        const float* fp = F[d] + (long long)comp * g.box;
-        float a0, a1, b0, b1;
+        const T* fp = F[d] + (long long)comp * g.box;
+        T a0, a1, b0, b1;
         ld_pair(fp, a0, a1);
         if (d == 0) {
           b0 = a1;
-          b1 = in1 ? fp[2] : 0.0f;
+          b1 = in1 ? fp[2] : T(0);
         } else {
           ld_pair(fp + (d == 1 ? sy : sz), b0, b1);
         }
@@ -914,14 +949,20 @@ __global__ void __launch_bounds__(256, 4) k_update_pair(MeshView single, int bas
       const long long o = ub + (long long)v * g.box;
       double acc0, acc1;
       ld_pair(Ubase + o, acc0, acc1);
+      if constexpr (ACC) {
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        acc0 = fma(-(h * g.idx[d]), d0[d], acc0);
-        acc1 = fma(-(h * g.idx[d]), d1[d], acc1);
-      }
-      if (forced) {
-        acc0 = fma(h, src0[v], acc0);
-        acc1 = fma(h, src1[v], acc1);
+        for (int d = 0; d < 3; ++d) {
+          acc0 = fma(-(h * g.idx[d]), d0[d], acc0);
+          acc1 = fma(-(h * g.idx[d]), d1[d], acc1);
+        }
+        if (forced) {
+          acc0 = fma(h, src0[v], acc0);
+          acc1 = fma(h, src1[v], acc1);
+        }
+      } else {
+        const double dv0 = div3(d0, g.idx), dv1 = div3(d1, g.idx);
+        acc0 = plus_hl(acc0, h, forced ? src0[v] - dv0 : -dv0);
+        acc1 = plus_hl(acc1, h, forced ? src1[v] - dv1 : -dv1);
       }
       if (in1)
         st_pair(Uout + o, acc0, acc1);
@@ -929,21 +970,28 @@ __global__ void __launch_bounds__(256, 4) k_update_pair(MeshView single, int bas
         Uout[o] = acc0;
     }
   }
-  const float* E[3] = {static_cast<const float*>(V.a.e[0]) + (long long)b * g.box + c,
-                       static_cast<const float*>(V.a.e[1]) + (long long)b * g.box + c,
-                       static_cast<const float*>(V.a.e[2]) + (long long)b * g.box + c};
+  const T* E[3] = {static_cast<const T*>(V.a.e[0]) + (long long)b * g.box + c,
+                   static_cast<const T*>(V.a.e[1]) + (long long)b * g.box + c,
+                   static_cast<const T*>(V.a.e[2]) + (long long)b * g.box + c};
+  // B_out of one node from dE_b (along a) and dE_a (along b): the accumulated form or the L form
+  auto bnew = [&](double base, double deb, double ia, double dea, double ib) -> double {
+    if constexpr (ACC)
+      return fma(h * ib, dea, fma(-(h * ia), deb, base));
+    else
+      return plus_hl(base, h, -curl2(deb, ia, dea, ib));
+  };
   const long long o = (long long)b * g.box + c;
   // face field fd = 0: B1 -= (h/dy) dE3/dy, += (h/dz) dE2/dz at both nodes (transversally inside)
   if (iny && inz) {
-    float p0, p1, q0, q1, r0, r1, s0, s1;
+    T p0, p1, q0, q1, r0, r1, s0, s1;
     ld_pair(E[2], p0, p1);
     ld_pair(E[2] + sy, q0, q1);
     ld_pair(E[1], r0, r1);
     ld_pair(E[1] + sz, s0, s1);
     double b0, b1;
     ld_pair(V.a.b[base_reg][0] + o, b0, b1);
-    const double n0 = fma(h * g.idx[2], to_f64(s0) - to_f64(r0), fma(-(h * g.idx[1]), to_f64(q0) - to_f64(p0), b0));
-    const double n1 = fma(h * g.idx[2], to_f64(s1) - to_f64(r1), fma(-(h * g.idx[1]), to_f64(q1) - to_f64(p1), b1));
+    const double n0 = bnew(b0, to_f64(q0) - to_f64(p0), g.idx[1], to_f64(s0) - to_f64(r0), g.idx[2]);
+    const double n1 = bnew(b1, to_f64(q1) - to_f64(p1), g.idx[1], to_f64(s1) - to_f64(r1), g.idx[2]);
     if (node1)
       st_pair(V.a.b[out_reg][0] + o, n0, n1);
     else
@@ -951,15 +999,15 @@ __global__ void __launch_bounds__(256, 4) k_update_pair(MeshView single, int bas
   }
   // fd = 1: B2 -= (h/dz) dE1/dz, += (h/dx) dE3/dx (inside along z and x)
   if (inz && in0) {
-    float p0, p1, q0, q1, r0, r1;
+    T p0, p1, q0, q1, r0, r1;
     ld_pair(E[0], p0, p1);
     ld_pair(E[0] + sz, q0, q1);
     ld_pair(E[2], r0, r1);
-    const float r2 = in1 ? E[2][2] : 0.0f;
+    const T r2 = in1 ? E[2][2] : T(0);
     double b0, b1;
     ld_pair(V.a.b[base_reg][1] + o, b0, b1);
-    const double n0 = fma(h * g.idx[0], to_f64(r1) - to_f64(r0), fma(-(h * g.idx[2]), to_f64(q0) - to_f64(p0), b0));
-    const double n1 = fma(h * g.idx[0], to_f64(r2) - to_f64(r1), fma(-(h * g.idx[2]), to_f64(q1) - to_f64(p1), b1));
+    const double n0 = bnew(b0, to_f64(q0) - to_f64(p0), g.idx[2], to_f64(r1) - to_f64(r0), g.idx[0]);
+    const double n1 = bnew(b1, to_f64(q1) - to_f64(p1), g.idx[2], to_f64(r2) - to_f64(r1), g.idx[0]);
     if (in1)
       st_pair(V.a.b[out_reg][1] + o, n0, n1);
     else
@@ -967,15 +1015,15 @@ __global__ void __launch_bounds__(256, 4) k_update_pair(MeshView single, int bas
   }
   // fd = 2: B3 -= (h/dx) dE2/dx, += (h/dy) dE1/dy (inside along x and y)
   if (in0 && iny) {
-    float p0, p1, q0, q1, r0, r1;
+    T p0, p1, q0, q1, r0, r1;
     ld_pair(E[1], p0, p1);
-    const float p2 = in1 ? E[1][2] : 0.0f;
+    const T p2 = in1 ? E[1][2] : T(0);
     ld_pair(E[0], q0, q1);
     ld_pair(E[0] + sy, r0, r1);
     double b0, b1;
     ld_pair(V.a.b[base_reg][2] + o, b0, b1);
-    const double n0 = fma(h * g.idx[1], to_f64(r0) - to_f64(q0), fma(-(h * g.idx[0]), to_f64(p1) - to_f64(p0), b0));
-    const double n1 = fma(h * g.idx[1], to_f64(r1) - to_f64(q1), fma(-(h * g.idx[0]), to_f64(p2) - to_f64(p1), b1));
+    const double n0 = bnew(b0, to_f64(p1) - to_f64(p0), g.idx[0], to_f64(r0) - to_f64(q0), g.idx[1]);
+    const double n1 = bnew(b1, to_f64(p2) - to_f64(p1), g.idx[0], to_f64(r1) - to_f64(q1), g.idx[1]);
     if (in1)
       st_pair(V.a.b[out_reg][2] + o, n0, n1);
     else
@@ -993,10 +1041,13 @@ cudaError_t launch_update(const MeshView& v, const Dispatch* d, int base_reg, in
   const WorkItem* wk = d ? d->work : nullptr;
   const bool plain = g_other == 0.0 && g_base == 1.0;  // U_base + h L: the VL2 stages
 #ifndef VL2_VALUE_SAFE
-  if (v.a.mixed && plain && !d && v.g.ng % 2 == 0) {  // two nodes per thread (one mesh, even ghost width)
+  // two nodes per thread (one mesh, even ghost width) in the mixed precision; in FP64 the paired kernel
+  // measured no faster (3.39 against 3.35 ms per 256^3 cycle), so FP64 keeps one node per thread
+  if (v.a.mixed && plain && !d && v.g.ng % 2 == 0) {
     const Geom& g = v.g;
     const long long pairs = (long long)((g.mb[0] + 2) / 2) * (g.mb[1] + 1) * (g.mb[2] + 1) * g.nblk;
-    k_update_pair<<<(unsigned)((pairs + THREADS - 1) / THREADS), THREADS, 0, st>>>(v, base_reg, out_reg, h, stage_reg);
+    k_update_pair<float><<<(unsigned)((pairs + THREADS - 1) / THREADS), THREADS, 0, st>>>(v, base_reg, out_reg, h,
+                                                                                          stage_reg);
     return cudaGetLastError();
   }
 #endif
