@@ -56,7 +56,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of
 # the k_flux_plm x sweep on the 128^3 vortex, 2,162,688 faces), scaled to a launch by its faces; valid only
 # for the kernel source it was taken on (hash of the flux and physics sources), else reported as null.
-NCU_TRAFFIC = {"hash": "81e066f4b586258d", "bytes_per_face": 132.43}
+NCU_TRAFFIC = {"hash": "060654fe30c8f87e", "bytes_per_face": 132.15}
 
 
 def flux_source_hash():
@@ -236,7 +236,8 @@ def workload_config(args):
         args.n, (args.n // args.mb) ** 3, args.mb), "grid": [args.n] * 3, "meshblock": [args.mb] * 3,
         "meshblocks": (args.n // args.mb) ** 3, "ghosts": 2, "gamma": 5.0 / 3.0, "cfl": 0.3,
         "integrator": "vl2", "reconstruction": "plm (donor cell predictor)", "riemann": "hlld", "seed": 2005,
-        "l2": "state (1.07 GB per register at 256^3) exceeds the 129 MB L2; no flush", "parallelism": "replicas"}
+        "l2": "state (1.07 GB per register at 256^3) exceeds the 129 MB L2; no flush", "parallelism": "replicas",
+        **({"flux_shape": list(args.flux_shape)} if getattr(args, "flux_shape", None) else {})}
 
 
 def timed_steps(mesh, steps, stream, dts=None):
@@ -268,6 +269,8 @@ def mixed_form(args, dev, stream, vl2, inputs):
     dts = None
     for name, prec in (("fp64", vl2.FP64), ("mixed", vl2.MIXED)):
         m = vl2.Mesh.from_problem(prob, device=dev, stream=stream, precision=prec)
+        if args.flux_shape:
+            m.set_flux_shape(*args.flux_shape)
         for _ in range(3):
             m.step(m.new_dt())
         m.set_prims(prob.w, prob.b1, prob.b2, prob.b3)
@@ -731,6 +734,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", "--grid", dest="n", type=int, default=256, help="cells per direction of the vortex")
     ap.add_argument("--mb", type=int, default=32)
+    ap.add_argument("--flux-shape", type=lambda t: tuple(int(v) for v in t.split(",")), default=None,
+                    help="DC_THREADS,PLM_LINES,TMA for the headline and mixed-form meshes (default: the library's)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the mixed-precision, batched and differentiation forms")
@@ -779,6 +784,8 @@ def main():
     prob = inputs.orszag_tang(n=args.n, mb=args.mb, seed=2005)
     stream = torch.cuda.current_stream(dev)
     mesh = vl2.Mesh.from_problem(prob, device=dev, stream=stream)
+    if args.flux_shape:
+        mesh.set_flux_shape(*args.flux_shape)
     for _ in range(args.warmup):
         mesh.step(mesh.new_dt())
     torch.cuda.synchronize(dev)
