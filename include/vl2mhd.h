@@ -171,9 +171,25 @@ vl2_status vl2_step(vl2_mesh* mesh, double dt);
 /* CFL time step of the current state (Sec. 2.1.7, 3.2.3): dt = cfl * min over active cells and
  * directions d of dx_d / (|v_d| + C_f,d), C_f,d the fast speed with b_c,d as normal field.  Blocks on
  * the device; also reports floor events seen since the previous call: returns VL2_E_NONPHYS (with
- * *dt_out still set) when a density/pressure floor fired or dt is not finite.  Errors: VL2_E_ARG,
- * VL2_E_CUDA, VL2_E_NONPHYS. */
+ * *dt_out still set) when a density/pressure floor fired or dt is not finite, and VL2_E_ARG when a
+ * vl2_set_prims_async since the previous report met periodic face duplicates that differ.  Errors:
+ * VL2_E_ARG, VL2_E_CUDA, VL2_E_NONPHYS, VL2_E_TIMEOUT. */
 vl2_status vl2_new_dt(vl2_mesh* mesh, double* dt_out);
+
+/* Stream-ordered stepping, for callers that overlap host<->device copies with the cycles (no call below
+ * waits for the device):
+ * vl2_set_prims_async: vl2_set_prims without its two waits.  Host inputs must be page-locked for the copy to
+ * be asynchronous; the staging area they pass through is shared with the host forms of the get calls.  The
+ * periodic-face check raises a device flag that the next vl2_new_dt or vl2_last_dt reports (VL2_E_ARG).
+ * vl2_step_cfl: one VL2 cycle whose step dt = cfl * min dx_d / (|v_d| + C_f,d) (as vl2_new_dt) is formed and
+ * read on the device; the same arithmetic as vl2_new_dt followed by vl2_step, so the same bits.  VL2
+ * integrator without passive scalars.  Errors: VL2_E_ARG, VL2_E_STATE, VL2_E_CUDA.
+ * vl2_last_dt: waits, returns the step the last vl2_step_cfl used, and reports as vl2_new_dt does (floors,
+ * a non-finite step, the asynchronous periodic check, an expired TMA wait). */
+vl2_status vl2_set_prims_async(vl2_mesh* mesh, const double* w, const double* b1, const double* b2,
+                               const double* b3, int where);
+vl2_status vl2_step_cfl(vl2_mesh* mesh);
+vl2_status vl2_last_dt(vl2_mesh* mesh, double* dt_out);
 
 /* Copy out the conserved state: u = [5][NZ][NY][NX] (rho, M1, M2, M3, E) and the face fields (any of
  * the four pointers may be NULL to skip it).  Errors: VL2_E_ARG, VL2_E_CUDA. */

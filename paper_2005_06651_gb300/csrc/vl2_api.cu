@@ -26,6 +26,7 @@ struct vl2_mesh {
   bool dt_pending = false;  // scal[SC_MAXRATE] holds the CFL rate of register 0
   unsigned long long floors_seen = 0;
   double* dres = nullptr;   // device result slots of the reductions
+  double* ddt = nullptr;    // device slot of the step vl2_step_cfl formed (dres[15])
   std::string err;
   // kernel timing (vl2_profile) and launch counting
   bool prof = false;
@@ -397,6 +398,12 @@ cudaError_t k_update(vl2_mesh* m, int base, int out, double h, double g_base = 1
     return vl2::launch_update(m->view(), nullptr, base, out, h, nullptr, 0.0, m->st, g_base, g_other, stage);
   });
 }
+// the plain update with h = beta * dt[0] read on the device (vl2_step_cfl)
+cudaError_t k_update_ddt(vl2_mesh* m, int base, int out, double beta, int stage = -1) {
+  return timed(m, VL2_K_UPDATE, nodes(m->g), [&] {
+    return vl2::launch_update(m->view(), nullptr, base, out, 0.0, m->ddt, beta, m->st, 1.0, 0.0, stage);
+  });
+}
 
 vl2_status ensure_prims(vl2_mesh* m) {
   if (!m->w_valid) {
@@ -483,6 +490,7 @@ vl2_status vl2_mesh_create(const vl2_params* params, void* workspace, size_t byt
   m->a.red_ctas = RED_CTAS;
   m->a.scal = (unsigned long long*)(base + pl.off_scal);
   m->dres = (double*)(m->a.scal + vl2::SC_COUNT);
+  m->ddt = m->dres + 15;
   // block table and 26-neighbour table (x fastest block order)
   m->loc.resize((size_t)g.nblk * 3);
   m->nbr.resize((size_t)g.nblk * 27);
@@ -589,6 +597,40 @@ vl2_status vl2_set_prims(vl2_mesh* m, const double* w, const double* b1, const d
   m->w_valid = false;
   m->dt_pending = false;
   return sync(m);
+}
+
+vl2_status vl2_set_prims_async(vl2_mesh* m, const double* w, const double* b1, const double* b2, const double* b3,
+                               int where) {
+  if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
+  if (!w || !b1 || !b2 || !b3 || bad_where(where)) return fail(m, VL2_E_ARG, "NULL input or bad where");
+  const Geom& g = m->g;
+  const long long nc = ncells(g);
+  const long long n1 = (long long)(g.N[0] + 1) * g.N[1] * g.N[2];
+  const long long n2 = (long long)g.N[0] * (g.N[1] + 1) * g.N[2];
+  const long long n3 = (long long)g.N[0] * g.N[1] * (g.N[2] + 1);
+  const double *dw = w, *d1 = b1, *d2 = b2, *d3 = b3;
+  if (where == VL2_HOST) {
+    double* s = m->a.stage;
+    vl2_status st;
+    if ((st = copy_in(m, s, w, 5 * nc, where)) != VL2_OK) return st;
+    if ((st = copy_in(m, s + 5 * nc, b1, n1, where)) != VL2_OK) return st;
+    if ((st = copy_in(m, s + 5 * nc + n1, b2, n2, where)) != VL2_OK) return st;
+    if ((st = copy_in(m, s + 5 * nc + n1 + n2, b3, n3, where)) != VL2_OK) return st;
+    dw = s;
+    d1 = s + 5 * nc;
+    d2 = d1 + n1;
+    d3 = d2 + n2;
+  }
+  // the periodic-face check raises a sticky device flag, reported by the next vl2_new_dt or vl2_last_dt
+  VL2_CHECK(m, vl2::launch_check_periodic(g, d1, d2, d3, m->a.scal + vl2::SC_MISMATCH_ASYNC, m->st));
+  ++m->launches;
+  VL2_CHECK(m, vl2::launch_scatter_prims(g, m->a, dw, d1, d2, d3, m->st));
+  ++m->launches;
+  VL2_CHECK(m, k_ghosts(m, 0));
+  m->initialized = true;
+  m->w_valid = false;
+  m->dt_pending = false;
+  return VL2_OK;
 }
 
 vl2_status vl2_set_scalars(vl2_mesh* m, const double* c, int where) {
@@ -1007,6 +1049,60 @@ vl2_status vl2_step(vl2_mesh* m, double dt) {
   return VL2_OK;
 }
 
+vl2_status vl2_step_cfl(vl2_mesh* m) {
+  if (!m) return fail(nullptr, VL2_E_ARG, "mesh is NULL");
+  if (!m->initialized) return fail(m, VL2_E_STATE, "vl2_set_prims has not been called");
+  if (m->p.integrator != VL2_INT_VL2 || m->g.ns)
+    return fail(m, VL2_E_STATE, "vl2_step_cfl runs the VL2 integrator without passive scalars");
+  if (!m->dt_pending) {  // the CFL rate of the current state (vl2_step leaves it behind)
+    VL2_CHECK(m, cudaMemsetAsync(m->a.scal + vl2::SC_MAXRATE, 0, sizeof(unsigned long long), m->st));
+    VL2_CHECK(m, k_prim(m, 0, true));
+    m->w_valid = true;
+  }
+  VL2_CHECK(m, vl2::launch_mesh_dt(m->a.scal, m->p.cfl, m->ddt, m->st));
+  ++m->launches;
+  // the cycle of vl2_step with h = beta dt read on the device
+  VL2_CHECK(m, k_fluxes(m, 0, VL2_DC));
+  VL2_CHECK(m, k_emfs(m));
+  VL2_CHECK(m, k_update_ddt(m, 0, 1, 0.5));
+  VL2_CHECK(m, k_ghosts(m, 1));
+  VL2_CHECK(m, k_prim(m, 1, false));
+  VL2_CHECK(m, k_fluxes(m, 1, m->rec()));
+  VL2_CHECK(m, k_emfs(m));
+  VL2_CHECK(m, k_update_ddt(m, 0, 0, 1.0, 1));
+  VL2_CHECK(m, k_ghosts(m, 0));
+  VL2_CHECK(m, cudaMemsetAsync(m->a.scal + vl2::SC_MAXRATE, 0, sizeof(unsigned long long), m->st));
+  VL2_CHECK(m, k_prim(m, 0, true));
+  m->w_valid = true;
+  m->dt_pending = true;
+  return VL2_OK;
+}
+
+vl2_status vl2_last_dt(vl2_mesh* m, double* dt_out) {
+  if (!m || !dt_out) return fail(m, VL2_E_ARG, "NULL argument");
+  double dt = 0.0;
+  unsigned long long sc[5];
+  VL2_CHECK(m, cudaMemcpyAsync(&dt, m->ddt, sizeof(dt), cudaMemcpyDeviceToHost, m->st));
+  VL2_CHECK(m, cudaMemcpyAsync(sc, m->a.scal, sizeof(sc), cudaMemcpyDeviceToHost, m->st));
+  vl2_status s = sync(m);
+  if (s != VL2_OK) return s;
+  *dt_out = dt;
+  if (sc[vl2::SC_MISMATCH_ASYNC]) {
+    VL2_CHECK(m, cudaMemsetAsync(m->a.scal + vl2::SC_MISMATCH_ASYNC, 0, sizeof(unsigned long long), m->st));
+    return fail(m, VL2_E_ARG, "periodic duplicate faces (face N and face 0) differed in vl2_set_prims_async");
+  }
+  if (sc[vl2::SC_TIMEOUT]) {
+    VL2_CHECK(m, cudaMemsetAsync(m->a.scal + vl2::SC_TIMEOUT, 0, sizeof(unsigned long long), m->st));
+    return fail(m, VL2_E_TIMEOUT, "a TMA tile copy did not land within its bounded wait; the step is incomplete");
+  }
+  const unsigned long long floors = sc[vl2::SC_FLOORS];
+  const bool fired = floors > m->floors_seen;
+  m->floors_seen = floors;
+  if (!std::isfinite(dt) || !(dt > 0.0)) return fail(m, VL2_E_NONPHYS, "time step is not finite and positive");
+  if (fired) return fail(m, VL2_E_NONPHYS, "a density or pressure floor fired");
+  return VL2_OK;
+}
+
 vl2_status vl2_new_dt(vl2_mesh* m, double* dt_out) {
   if (!m || !dt_out) return fail(m, VL2_E_ARG, "NULL argument");
   if (!m->initialized) return fail(m, VL2_E_STATE, "vl2_set_prims has not been called");
@@ -1016,10 +1112,14 @@ vl2_status vl2_new_dt(vl2_mesh* m, double* dt_out) {
     m->w_valid = true;
     m->dt_pending = true;
   }
-  unsigned long long sc[4];
+  unsigned long long sc[5];
   VL2_CHECK(m, cudaMemcpyAsync(sc, m->a.scal, sizeof(sc), cudaMemcpyDeviceToHost, m->st));
   vl2_status s = sync(m);
   if (s != VL2_OK) return s;
+  if (sc[vl2::SC_MISMATCH_ASYNC]) {
+    VL2_CHECK(m, cudaMemsetAsync(m->a.scal + vl2::SC_MISMATCH_ASYNC, 0, sizeof(unsigned long long), m->st));
+    return fail(m, VL2_E_ARG, "periodic duplicate faces (face N and face 0) differed in vl2_set_prims_async");
+  }
   if (sc[vl2::SC_TIMEOUT]) {
     VL2_CHECK(m, cudaMemsetAsync(m->a.scal + vl2::SC_TIMEOUT, 0, sizeof(unsigned long long), m->st));
     return fail(m, VL2_E_TIMEOUT, "a TMA tile copy did not land within its bounded wait; the step is incomplete");

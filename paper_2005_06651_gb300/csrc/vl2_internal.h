@@ -68,7 +68,9 @@ struct Arrays {
 
 // Device scalars: CFL rate bits, floor count, periodic-check mismatches, and a flag set by a kernel whose
 // bounded wait for a TMA tile expired (it skips its work and returns).
-enum { SC_MAXRATE = 0, SC_FLOORS = 1, SC_MISMATCH = 2, SC_TIMEOUT = 3, SC_COUNT = 8 };
+// SC_MISMATCH_ASYNC: the periodic-face check of a stream-ordered vl2_set_prims_async, sticky until a
+// synchronising call reports it.
+enum { SC_MAXRATE = 0, SC_FLOORS = 1, SC_MISMATCH = 2, SC_TIMEOUT = 3, SC_MISMATCH_ASYNC = 4, SC_COUNT = 8 };
 
 // A mesh as the kernels see it (copied to device memory for batched launches).
 struct MeshView {
@@ -174,6 +176,7 @@ bool encode_w_maps(const Geom& g, const void* w, int esize, void* maps, const ch
 // For batched launches v only selects the precision; dtbox (per-box dt, device) and beta give h. ----
 cudaError_t launch_prim(const MeshView& v, const Dispatch* d, int reg, bool all_cells, bool want_dt, cudaStream_t st);
 cudaError_t launch_ghosts(const MeshView& v, const Dispatch* d, int reg, cudaStream_t st);
+cudaError_t launch_mesh_dt(const unsigned long long* scal, double cfl, double* dt, cudaStream_t st);
 cudaError_t launch_flux(const MeshView& v, const Dispatch* d, int reg, int recon, int riemann, int dir,
                         const FluxShape& fs, int max_mb, cudaStream_t st);
 // copy the halo faces' mass flux and transverse induction fluxes from their owning blocks (meshes with

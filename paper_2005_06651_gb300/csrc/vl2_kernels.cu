@@ -276,6 +276,16 @@ __global__ void k_batch_dt(const MeshView* views, int nbox, const double* cfl, d
   *rp = 0ULL;
 }
 
+// dt = cfl / (the mesh's reduced CFL rate), on the device (one mesh; the rate slot is left for the caller)
+__global__ void k_mesh_dt(const unsigned long long* scal, double cfl, double* dt) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *dt = cfl / __longlong_as_double((long long)scal[SC_MAXRATE]);
+}
+
+cudaError_t launch_mesh_dt(const unsigned long long* scal, double cfl, double* dt, cudaStream_t st) {
+  k_mesh_dt<<<1, 32, 0, st>>>(scal, cfl, dt);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_batch_dt(const MeshView* views, int nbox, const double* cfl, double* dt, cudaStream_t st) {
   k_batch_dt<<<(nbox + 127) / 128, 128, 0, st>>>(views, nbox, cfl, dt);
   return cudaGetLastError();
@@ -871,12 +881,13 @@ __device__ __forceinline__ void st_pair(double* p, double a, double b) { *reinte
 
 template <class T>
 __global__ void __launch_bounds__(256, 4) k_update_pair(MeshView single, int base_reg, int out_reg, double h,
-                                                        int stage_reg) {
+                                                        const double* dtbox, double beta, int stage_reg) {
   constexpr bool ACC = sizeof(T) == 4;  // the accumulated form (FP32 fluxes); else the L form
   __shared__ MeshView sv;
   int tile;
   const MeshView& V = stage_view(sv, single, nullptr, nullptr, tile);
   const Geom& g = V.g;
+  if (dtbox) h = beta * dtbox[0];  // the step formed on the device
   const int ex = g.mb[0] + 1, ey = g.mb[1] + 1, ez = g.mb[2] + 1;
   const int px = (ex + 1) / 2;
   const long long per = (long long)px * ey * ez;
@@ -1047,7 +1058,7 @@ cudaError_t launch_update(const MeshView& v, const Dispatch* d, int base_reg, in
     const Geom& g = v.g;
     const long long pairs = (long long)((g.mb[0] + 2) / 2) * (g.mb[1] + 1) * (g.mb[2] + 1) * g.nblk;
     k_update_pair<float><<<(unsigned)((pairs + THREADS - 1) / THREADS), THREADS, 0, st>>>(v, base_reg, out_reg, h,
-                                                                                          stage_reg);
+                                                                                          dtbox, beta, stage_reg);
     return cudaGetLastError();
   }
 #endif

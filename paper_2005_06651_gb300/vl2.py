@@ -64,7 +64,7 @@ EXPORTS = ["vl2_workspace_bytes", "vl2_mesh_create", "vl2_mesh_destroy", "vl2_bl
            "vl2_debug_riemann_vjp", "vl2_last_error", "vl2_set_scalars", "vl2_get_scalars", "vl2_debug_fp64_peak",
            "vl2_debug_arith", "vl2_set_forcing", "vl2_tape_bytes", "vl2_step_record", "vl2_step_vjp_recorded",
            "vl2_set_flux_shape", "vl2_get_flux_shape", "vl2_batch_flux_shape", "vl2_batch_set_flux_shape",
-           "vl2_debug_wait_timeout"]
+           "vl2_debug_wait_timeout", "vl2_set_prims_async", "vl2_step_cfl", "vl2_last_dt"]
 NOALLOC_MAX_NZ = 4096
 K_PRIM, K_GHOSTS, K_FLUX_DC, K_FLUX_PLM, K_EMF, K_UPDATE, K_FLUX_PPM, K_SCALARS, K_FLUX_HALO = range(9)
 KERNEL_KINDS = {K_PRIM: "prim", K_GHOSTS: "ghosts", K_FLUX_DC: "flux_dc", K_FLUX_PLM: "flux_plm", K_EMF: "emf",
@@ -125,6 +125,9 @@ def load(path: str = LIB_PATH):
     L.vl2_batch_flux_shape.argtypes = [vp, ip, ip, ip]
     L.vl2_batch_set_flux_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.vl2_debug_wait_timeout.argtypes = [ctypes.c_int, dp, vp]
+    L.vl2_set_prims_async.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int]
+    L.vl2_step_cfl.argtypes = [vp]
+    L.vl2_last_dt.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.vl2_batch_last_error.argtypes = [vp]
     L.vl2_batch_last_error.restype = ctypes.c_char_p
     L.vl2_last_error.argtypes = [vp]
@@ -253,6 +256,66 @@ class Mesh:
         ptrs = [_ptr(x) for x in keep]
         where = _where_of(ptrs)
         _check(self._L.vl2_set_prims(self._h, *[ctypes.c_void_p(p) for p, _ in ptrs], where), self._h, lib=self._L)
+
+    def set_prims_async(self, w, b1, b2, b3):
+        """vl2_set_prims_async: enqueue the state from primitives without waiting (CUDA tensors, or page-locked
+        host tensors).  The inputs must stay untouched until the mesh's stream has consumed them."""
+        ptrs = [_ptr(x) for x in (w, b1, b2, b3)]
+        where = _where_of(ptrs)
+        _check(self._L.vl2_set_prims_async(self._h, *[ctypes.c_void_p(p) for p, _ in ptrs], where), self._h,
+               lib=self._L)
+
+    def step_cfl(self):
+        """vl2_step_cfl: one VL2 cycle with its CFL step formed and read on the device (no wait)."""
+        _check(self._L.vl2_step_cfl(self._h), self._h, lib=self._L)
+
+    def last_dt(self, allow_nonphys=False):
+        """The step of the last step_cfl (waits; reports as new_dt does)."""
+        out = ctypes.c_double()
+        _check(self._L.vl2_last_dt(self._h, ctypes.byref(out)), self._h,
+               allow=(VL2_E_NONPHYS,) if allow_nonphys else (), lib=self._L)
+        return out.value
+
+    def streamed_steps(self, host_in, host_out, nsteps):
+        """nsteps repetitions of: host_in (page-locked w, b1, b2, b3) to the device, vl2_set_prims_async,
+        vl2_step_cfl, vl2_get_cons into device buffers, and those to host_out (page-locked u, b1, b2, b3).  Two
+        copy streams and double-buffered device staging let each step's copies run beside the neighbouring
+        steps' cycles; events order every buffer's reuse.  Waits for the last step; returns its dt."""
+        import torch
+
+        dev = self.device
+        main = self.stream
+        cin, cout = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        din = [tuple(torch.empty(x.shape, dtype=torch.float64, device=dev) for x in host_in) for _ in range(2)]
+        dout = [tuple(torch.empty(x.shape, dtype=torch.float64, device=dev) for x in host_out) for _ in range(2)]
+        in_ready, in_free, out_ready, out_free = ([torch.cuda.Event() for _ in range(2)] for _ in range(4))
+
+        def upload(i):
+            cin.wait_event(in_free[i])  # the cycle that read this buffer has consumed it
+            with torch.cuda.stream(cin):
+                for d, h in zip(din[i], host_in):
+                    d.copy_(h, non_blocking=True)
+            in_ready[i].record(cin)
+
+        upload(0)
+        for k in range(nsteps):
+            i = k % 2
+            if k + 1 < nsteps:
+                upload(1 - i)
+            main.wait_event(in_ready[i])
+            self.set_prims_async(*din[i])
+            in_free[i].record(main)
+            self.step_cfl()
+            main.wait_event(out_free[i])  # the copy out of this buffer two steps ago has finished
+            self.get_cons(dout[i])
+            out_ready[i].record(main)
+            cout.wait_event(out_ready[i])
+            with torch.cuda.stream(cout):
+                for h, d in zip(host_out, dout[i]):
+                    h.copy_(d, non_blocking=True)
+            out_free[i].record(cout)
+        cout.synchronize()
+        return self.last_dt(allow_nonphys=True)
 
     def set_scalars(self, c):
         """Concentrations c (nscalars, NZ, NY, NX), host array or CUDA tensor; set the state first."""
