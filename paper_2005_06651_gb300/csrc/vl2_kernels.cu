@@ -206,8 +206,10 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
       cin[7][slot] = LEAN ? 0.5 * bcz : bcz;
     }
     __syncthreads();
+    const int nc = ncand;  // CTA-uniform
+    if (nc <= 32 && wid > 0) return;  // the first warp evaluates every candidate and reduces alone
     unsigned long long rate_bits = 0ULL;
-    if ((int)threadIdx.x < ncand) {
+    if ((int)threadIdx.x < nc) {
       const int q = threadIdx.x;
       const double cid = cin[0][q], cp = cin[1][q];
       const double bx2 = cin[5][q] * cin[5][q], by2 = cin[6][q] * cin[6][q], bz2 = cin[7][q] * cin[7][q];
@@ -222,6 +224,10 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned long long v = __shfl_xor_sync(0xffffffffu, rate_bits, o);
       rate_bits = v > rate_bits ? v : rate_bits;
+    }
+    if (nc <= 32) {
+      if (lane == 0 && rate_bits) atomicMax(V.a.scal + SC_MAXRATE, rate_bits);
+      return;
     }
     if (lane == 0) red[wid] = rate_bits;
     __syncthreads();
@@ -371,11 +377,19 @@ __global__ void __launch_bounds__(256) k_ghosts(MeshView single, const MeshView*
   double* B1 = V.a.b[reg][1];
   double* B2 = V.a.b[reg][2];
   const long long per = shell_size(g);
-  const long long t = (long long)tile * blockDim.x + threadIdx.x;
-  if (t >= per * g.nblk) return;
-  const int b = (int)(t / per);
+  int b, e;
+  if (work || gridDim.y == 1) {  // a flat index over (block, shell element)
+    const long long t = (long long)tile * blockDim.x + threadIdx.x;
+    if (t >= per * g.nblk) return;
+    b = (int)(t / per);
+    e = (int)(t - (long long)b * per);
+  } else {  // one grid row per block: no 64-bit division
+    b = (int)blockIdx.y;
+    e = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (e >= per) return;
+  }
   int li[3];
-  shell_index(g, (int)(t - (long long)b * per), li);
+  shell_index(g, e, li);
   int loc[3];
   block_loc(g, b, loc);
   const long long c = cell_off(g, li[2], li[1], li[0]);
@@ -428,7 +442,15 @@ long long tiles_ghosts(const Geom& g) {
 }
 
 cudaError_t launch_ghosts(const MeshView& v, const Dispatch* d, int reg, cudaStream_t st) {
-  const long long grid = d ? d->nwork : tiles_ghosts(v.g);
+  const Geom& g = v.g;
+  if (!d && g.nblk > 1 && g.nblk <= 65535) {  // one grid row per MeshBlock
+    const long long per = (long long)(g.mb[0] + 2 * g.ng + 1) * (g.mb[1] + 2 * g.ng + 1) * (g.mb[2] + 2 * g.ng + 1) -
+                          (long long)g.mb[0] * g.mb[1] * g.mb[2];
+    const dim3 grid((unsigned)((per + THREADS - 1) / THREADS), (unsigned)g.nblk);
+    k_ghosts<<<grid, THREADS, 0, st>>>(v, nullptr, nullptr, reg);
+    return cudaGetLastError();
+  }
+  const long long grid = d ? d->nwork : tiles_ghosts(g);
   if (grid <= 0) return cudaSuccess;
   k_ghosts<<<(unsigned)grid, THREADS, 0, st>>>(v, d ? d->views : nullptr, d ? d->work : nullptr, reg);
   return cudaGetLastError();
