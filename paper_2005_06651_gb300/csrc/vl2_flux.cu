@@ -469,23 +469,27 @@ __global__ void __launch_bounds__(256) k_flux_halo(MeshView single, const MeshVi
   const int o = 3 - d - s;
   const int f0 = d < o ? d : o, f1 = d < o ? o : d;  // free dimensions, the lower one fastest
   const int e0 = g.mb[f0] + (f0 == d ? 1 : 0);
-  int li[3], si[3];
-  li[f0] = g.ng + (int)(r % e0);
-  li[f1] = g.ng + (int)(r / e0);
-  li[s] = hi ? g.ng + g.mb[s] : g.ng - 1;
-  si[f0] = li[f0];
-  si[f1] = li[f1];
-  si[s] = hi ? g.ng : g.ng + g.mb[s] - 1;  // the same face in the neighbouring block's own range
+  const int a0 = g.ng + (int)(r % e0), a1 = g.ng + (int)(r / e0);  // along f0 and f1
+  const int ls = hi ? g.ng + g.mb[s] : g.ng - 1;
+  const int ss = hi ? g.ng : g.ng + g.mb[s] - 1;  // the same face in the neighbouring block's own range
+  // per-coordinate selects instead of arrays indexed by d, s (which would live in local memory)
+  auto pick = [&](int q, int side) { return q == s ? side : (q == f0 ? a0 : a1); };
   // neighbouring block along s (periodic wrap; every neighbour exists on a fully periodic mesh)
-  int loc[3] = {b % g.nb[0], (b / g.nb[0]) % g.nb[1], b / (g.nb[0] * g.nb[1])};
-  loc[s] = (loc[s] + (hi ? 1 : g.nb[s] - 1)) % g.nb[s];
-  const int bs = (loc[2] * g.nb[1] + loc[1]) * g.nb[0] + loc[0];
+  int l0 = b % g.nb[0], l1 = (b / g.nb[0]) % g.nb[1], l2 = b / (g.nb[0] * g.nb[1]);
+  const int step = hi ? 1 : g.nb[s] - 1;
+  if (s == 0) l0 = (l0 + step) % g.nb[0];
+  if (s == 1) l1 = (l1 + step) % g.nb[1];
+  if (s == 2) l2 = (l2 + step) % g.nb[2];
+  const int bs = (l2 * g.nb[1] + l1) * g.nb[0] + l0;
   T* F = static_cast<T*>(V.a.f[d]);
-  const long long dst = (long long)b * 7 * g.box + cell_off(g, li[2], li[1], li[0]);
-  const long long src = (long long)bs * 7 * g.box + cell_off(g, si[2], si[1], si[0]);
-  F[dst] = F[src];
-  F[dst + 5 * g.box] = F[src + 5 * g.box];
-  F[dst + 6 * g.box] = F[src + 6 * g.box];
+  const long long dst = (long long)b * 7 * g.box + cell_off(g, pick(2, ls), pick(1, ls), pick(0, ls));
+  const long long src = (long long)bs * 7 * g.box + cell_off(g, pick(2, ss), pick(1, ss), pick(0, ss));
+  // the sources are faces of the neighbour's own range, which this launch does not write: three loads, then
+  // three stores
+  const T m = F[src], e1 = F[src + 5 * g.box], e2 = F[src + 6 * g.box];
+  F[dst] = m;
+  F[dst + 5 * g.box] = e1;
+  F[dst + 6 * g.box] = e2;
 }
 
 long long tiles_flux_halo(const Geom& g) {

@@ -398,26 +398,22 @@ __global__ void __launch_bounds__(256) k_ghosts(MeshView single, const MeshView*
   int sb[3], sl[3];
 #pragma unroll
   for (int q = 0; q < 3; ++q) source_of(g, q, loc[q] * g.mb[q] + li[q] - g.ng, false, sb[q], sl[q]);
-  // cell-centred conserved variables
+  // Every source is an active cell or face of its block, which no thread of this launch writes, so all of a
+  // thread's loads are issued before its stores (one memory round trip instead of one per copied value).
+  bool cell = false;
+  int ublk = 0;
+  long long ucell = 0, usrc = 0;
   if (li[0] < cmax[0] && li[1] < cmax[1] && li[2] < cmax[2]) {
-    bool ghost = false;
-    for (int q = 0; q < 3; ++q) ghost |= (li[q] < g.ng || li[q] >= g.ng + g.mb[q]);
-    if (ghost) {
-      const int src = (sb[2] * g.nb[1] + sb[1]) * g.nb[0] + sb[0];
-      const long long sc = cell_off(g, sl[2], sl[1], sl[0]);
-      const double* Us = U + (long long)src * 5 * g.box + sc;
-      double* Ud = U + (long long)b * 5 * g.box + c;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) Ud[(long long)v * g.box] = Us[(long long)v * g.box];
-      if (g.ns) {  // passive scalars ride with the conserved variables
-        const double* Ss = V.a.s[reg] + (long long)src * g.ns * g.box + sc;
-        double* Sd = V.a.s[reg] + (long long)b * g.ns * g.box + c;
-        for (int q = 0; q < g.ns; ++q) Sd[(long long)q * g.box] = Ss[(long long)q * g.box];
-      }
+    for (int q = 0; q < 3; ++q) cell |= (li[q] < g.ng || li[q] >= g.ng + g.mb[q]);
+    if (cell) {
+      ublk = (sb[2] * g.nb[1] + sb[1]) * g.nb[0] + sb[0];
+      ucell = cell_off(g, sl[2], sl[1], sl[0]);
+      usrc = (long long)ublk * 5 * g.box + ucell;
     }
   }
-  // face-centred field
   double* Bf[3] = {B0, B1, B2};
+  bool face[3];
+  long long fsrc[3];
 #pragma unroll
   for (int fd = 0; fd < 3; ++fd) {
     bool valid = true, ghost = false;
@@ -427,12 +423,37 @@ __global__ void __launch_bounds__(256) k_ghosts(MeshView single, const MeshView*
       valid &= li[q] <= hi_valid;
       ghost |= (li[q] < g.ng || li[q] > hi_active);
     }
-    if (!valid || !ghost) continue;
-    int fb[3] = {sb[0], sb[1], sb[2]}, fl[3] = {sl[0], sl[1], sl[2]};
-    source_of(g, fd, loc[fd] * g.mb[fd] + li[fd] - g.ng, true, fb[fd], fl[fd]);
-    const int src = (fb[2] * g.nb[1] + fb[1]) * g.nb[0] + fb[0];
-    Bf[fd][(long long)b * g.box + c] = Bf[fd][(long long)src * g.box + cell_off(g, fl[2], fl[1], fl[0])];
+    face[fd] = valid && ghost;
+    fsrc[fd] = 0;
+    if (face[fd]) {
+      int fb[3] = {sb[0], sb[1], sb[2]}, fl[3] = {sl[0], sl[1], sl[2]};
+      source_of(g, fd, loc[fd] * g.mb[fd] + li[fd] - g.ng, true, fb[fd], fl[fd]);
+      fsrc[fd] = (long long)((fb[2] * g.nb[1] + fb[1]) * g.nb[0] + fb[0]) * g.box + cell_off(g, fl[2], fl[1], fl[0]);
+    }
   }
+  double uv[5], fv[3];
+  if (cell) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) uv[v] = U[usrc + (long long)v * g.box];
+  }
+#pragma unroll
+  for (int fd = 0; fd < 3; ++fd)
+    if (face[fd]) fv[fd] = Bf[fd][fsrc[fd]];
+  // cell-centred conserved variables
+  if (cell) {
+    double* Ud = U + (long long)b * 5 * g.box + c;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Ud[(long long)v * g.box] = uv[v];
+    if (g.ns) {  // passive scalars ride with the conserved variables
+      const double* Ss = V.a.s[reg] + (long long)ublk * g.ns * g.box + ucell;
+      double* Sd = V.a.s[reg] + (long long)b * g.ns * g.box + c;
+      for (int q = 0; q < g.ns; ++q) Sd[(long long)q * g.box] = Ss[(long long)q * g.box];
+    }
+  }
+  // face-centred field
+#pragma unroll
+  for (int fd = 0; fd < 3; ++fd)
+    if (face[fd]) Bf[fd][(long long)b * g.box + c] = fv[fd];
 }
 
 long long tiles_ghosts(const Geom& g) {
