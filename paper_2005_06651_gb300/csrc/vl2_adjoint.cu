@@ -540,7 +540,6 @@ __global__ void __launch_bounds__(128) k_adj_flux_cells(Geom g, const double* __
   auto face_ok = [&](int f) { return f >= NG && f <= NG + g.mb[DIR]; };
   const long long fb = (long long)b * 7 * g.box + c;
   const int var[7] = {0, 1 + DIR, 1 + T1, 1 + T2, 4, 5 + T1, 5 + T2};
-  const double* Wb = W + (long long)b * 8 * g.box + c;
   double* LWb = lw + (long long)b * 8 * g.box + c;
 #pragma unroll
   for (int n = 0; n < 7; ++n) {

@@ -280,13 +280,13 @@ constexpr int TMA_WAIT_POLLS = 1 << 20;  // polls of an mbarrier (each with a 25
 template <int DIR, int RS, class T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
     k_flux_tma(MeshView single, const MeshView* views, const WorkItem* work, int nitems, int reg, int P, int wcap) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char tile_smem[];  // its own name: the line kernel's is 16-aligned
   __shared__ MeshView sv;
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int landed;
   constexpr int T1 = (DIR + 1) % 3, T2 = (DIR + 2) % 3;
   constexpr int TA = LineMap<DIR>::TA, TB = LineMap<DIR>::TB;
-  T* rec = reinterpret_cast<T*>(smem_raw + 2 * (size_t)wcap);
+  T* rec = reinterpret_cast<T*>(tile_smem + 2 * (size_t)wcap);
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
     const uint32_t bytes = (uint32_t)(box[0] * box[1] * box[2] * box[3]) * (uint32_t)sizeof(T);
     fence_proxy_async_smem();  // the CTA's reads of this buffer (previous item) come before the copy's writes
     mbar_arrive_expect_tx(&bar[k], bytes);
-    tma_load_4d(smem_raw + (size_t)k * wcap, static_cast<const unsigned char*>(mv->a.tmw) + 128 * tma_map_index(DIR, P),
+    tma_load_4d(tile_smem + (size_t)k * wcap, static_cast<const unsigned char*>(mv->a.tmw) + 128 * tma_map_index(DIR, P),
                 c[0], c[1], c[2], c[3], &bar[k]);
   };
   if (threadIdx.x == 0 && (int)blockIdx.x < nitems) issue((int)blockIdx.x, 0);
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
     const int L4 = g.mb[DIR] + 4;  // cells of the box along DIR
     int box[4], xoff;
     tma_w_box(g, DIR, P, (int)sizeof(T), box, &xoff);
-    const T* Ws = reinterpret_cast<const T*>(smem_raw + (size_t)buf * wcap);
+    const T* Ws = reinterpret_cast<const T*>(tile_smem + (size_t)buf * wcap);
     // box element of variable v, DIR index a (0 = cell ng-2), line p
     auto widx = [&](int v, int a, int p) -> int {
       return (DIR == 0) ? (v * P + p) * box[0] + a : (v * L4 + a) * box[0] + xoff + p;
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(256) k_flux_halo(MeshView single, const MeshVi
     r -= 2 * n2;
   }
   const int o = 3 - d - s;
-  const int f0 = d < o ? d : o, f1 = d < o ? o : d;  // free dimensions, the lower one fastest
+  const int f0 = d < o ? d : o;  // the lower free dimension, fastest (the other one is f1 = d + o - f0)
   const int e0 = g.mb[f0] + (f0 == d ? 1 : 0);
   const int a0 = g.ng + (int)(r % e0), a1 = g.ng + (int)(r / e0);  // along f0 and f1
   const int ls = hi ? g.ng + g.mb[s] : g.ng - 1;

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
 #endif
   bool active = false;
   double id = 0.0, p = 0.0, vx = 0.0, vy = 0.0, vz = 0.0, bcx = 0.0, bcy = 0.0, bcz = 0.0;
-  [[maybe_unused]] float s32v[6];
+  [[maybe_unused]] float s32v[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   float r32 = 0.0f;
   if (t < per * g.nblk) {
     const int b = (int)(t / per);
