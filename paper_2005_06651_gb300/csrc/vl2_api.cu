@@ -216,6 +216,9 @@ vl2_status make_geom(const vl2_params* p, Geom& g, std::string& msg) {
   g.gamma = p->gamma;
   g.gm1 = p->gamma - 1.0;
   g.igm1 = 1.0 / (p->gamma - 1.0);
+  g.gamma_f = (float)g.gamma;
+  g.igm1_f = (float)g.igm1;
+  for (int d = 0; d < 3; ++d) g.idx_f[d] = (float)g.idx[d];
   g.dfloor = p->dfloor;
   g.pfloor = p->pfloor;
   return VL2_OK;

@@ -14,6 +14,16 @@
 
 namespace vl2 {
 
+// Per-mesh constants in the stage's precision: the FP32 forms take the mesh's precomputed FP32 copies instead of
+// converting per thread.  (The FP64 face field keeps the hardware conversion: narrowing it on the integer pipe
+// measured slower in the FP32 sweeps, whose busiest pipe is the integer one.)
+template <class T> __device__ __forceinline__ T stage_gamma(const Geom& g);
+template <> __device__ __forceinline__ double stage_gamma<double>(const Geom& g) { return g.gamma; }
+template <> __device__ __forceinline__ float stage_gamma<float>(const Geom& g) { return g.gamma_f; }
+template <class T> __device__ __forceinline__ T stage_igm1(const Geom& g);
+template <> __device__ __forceinline__ double stage_igm1<double>(const Geom& g) { return g.igm1; }
+template <> __device__ __forceinline__ float stage_igm1<float>(const Geom& g) { return g.igm1_f; }
+
 // ------------------------------------------------------------------------------------------------
 // Predictor fluxes, one thread per face.  Faces of direction DIR cover the block's active faces along
 // DIR (ng .. ng+mb) and its active cells transversally (ng .. ng+mb-1); with g.flux_halo also one ghost
@@ -60,9 +70,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_flux(MeshView s
   const T bn = (T)V.a.b[reg][DIR][(long long)b * g.box + c];
   T f[7];
   if (RS == RS_HLLD)
-    flux_hlld<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, f);
+    flux_hlld<T>(wl, wr, bn, stage_gamma<T>(g), stage_igm1<T>(g), f);
   else
-    flux_hlle<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, f, g.hlle_roe != 0);
+    flux_hlle<T>(wl, wr, bn, stage_gamma<T>(g), stage_igm1<T>(g), f, g.hlle_roe != 0);
   T* Fb = static_cast<T*>(V.a.f[DIR]) + (long long)b * 7 * g.box + c;
 #pragma unroll
   for (int n = 0; n < 7; ++n) Fb[(long long)n * g.box] = f[n];
@@ -174,7 +184,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_flux_plm(MeshVi
 #pragma unroll
       for (int j = 0; j < 5; ++j) qs[j][n] = q[(j - 2) * sd];
     }
-    char_ppm_cell<T>(qs, Wb[(long long)(5 + DIR) * g.box + o], (T)g.gamma, lo, hi);
+    char_ppm_cell<T>(qs, Wb[(long long)(5 + DIR) * g.box + o], stage_gamma<T>(g), lo, hi);
 #pragma unroll
     for (int n = 0; n < 7; ++n) {
       smem[sidx(n, 0, p, c)] = lo[n];
@@ -200,7 +210,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_flux_plm(MeshVi
       q0[n] = q[0];
       qp[n] = q[sd];
     }
-    char_plm_cell<T>(qm, q0, qp, Wb[(long long)(5 + DIR) * g.box + o], (T)g.gamma, lo, hi);
+    char_plm_cell<T>(qm, q0, qp, Wb[(long long)(5 + DIR) * g.box + o], stage_gamma<T>(g), lo, hi);
 #pragma unroll
     for (int n = 0; n < 7; ++n) {
       smem[sidx(n, 0, p, c)] = lo[n];
@@ -255,9 +265,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_flux_plm(MeshVi
     const T bn = (T)Bn[(long long)b * g.box + o];
     T fl[7];
     if (RS == RS_HLLD)
-      flux_hlld<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, fl);
+      flux_hlld<T>(wl, wr, bn, stage_gamma<T>(g), stage_igm1<T>(g), fl);
     else
-      flux_hlle<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, fl, g.hlle_roe != 0);
+      flux_hlle<T>(wl, wr, bn, stage_gamma<T>(g), stage_igm1<T>(g), fl, g.hlle_roe != 0);
     T* Fb = static_cast<T*>(V.a.f[DIR]) + (long long)b * 7 * g.box + o;
 #pragma unroll
     for (int n = 0; n < 7; ++n) Fb[(long long)n * g.box] = fl[n];
@@ -403,9 +413,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
       const T bn = (T)Bn[(long long)b * g.box + o];
       T fl[7];
       if (RS == RS_HLLD)
-        flux_hlld<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, fl);
+        flux_hlld<T>(wl, wr, bn, stage_gamma<T>(g), stage_igm1<T>(g), fl);
       else
-        flux_hlle<T>(wl, wr, bn, (T)g.gamma, (T)g.igm1, fl, g.hlle_roe != 0);
+        flux_hlle<T>(wl, wr, bn, stage_gamma<T>(g), stage_igm1<T>(g), fl, g.hlle_roe != 0);
       T* Fb = static_cast<T*>(V.a.f[DIR]) + (long long)b * 7 * g.box + o;
 #pragma unroll
       for (int n = 0; n < 7; ++n) Fb[(long long)n * g.box] = fl[n];

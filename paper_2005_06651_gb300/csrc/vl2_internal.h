@@ -25,6 +25,9 @@ struct Geom {
   double idx[3];       // 1 / dx_d
   double dx[3];
   double gamma, gm1, igm1;
+  // the same in FP32 (rounded to nearest on the host), for FP32 stage arithmetic: a conversion in a kernel
+  // would occupy the FP64 pipe once per thread
+  float gamma_f, igm1_f, idx_f[3];
   int hlle_roe;  // 1: the HLLE solver takes Einfeldt's Roe-averaged outer speeds
   double dfloor, pfloor;
   double ct_delta;     // smoothed CT upwind weight width (0: the sign switch)

@@ -145,13 +145,13 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
     Eb[2 * g.box] = wy * ux - wx * uy;
     if (DT && active) {
       // single-precision estimate of the rate (relative error well below 1e-5)
-      const float fid = to_f32(id), fp = to_f32(p), fg = (float)g.gamma;
+      const float fid = to_f32(id), fp = to_f32(p), fg = g.gamma_f;
       const float fx = LEAN ? s32v[3] : to_f32(bcx), fy = LEAN ? s32v[4] : to_f32(bcy), fz = LEAN ? s32v[5] : to_f32(bcz);
       const float ax = LEAN ? s32v[0] : to_f32(vx), ay = LEAN ? s32v[1] : to_f32(vy), az = LEAN ? s32v[2] : to_f32(vz);
       const float x2 = fx * fx, y2 = fy * fy, z2 = fz * fz;
-      const float sx = (fabsf(ax) + fast_speed_r(fid, fp, x2, y2 + z2, fg)) * (float)g.idx[0];
-      const float sy = (fabsf(ay) + fast_speed_r(fid, fp, y2, z2 + x2, fg)) * (float)g.idx[1];
-      const float sz = (fabsf(az) + fast_speed_r(fid, fp, z2, x2 + y2, fg)) * (float)g.idx[2];
+      const float sx = (fabsf(ax) + fast_speed_r(fid, fp, x2, y2 + z2, fg)) * g.idx_f[0];
+      const float sy = (fabsf(ay) + fast_speed_r(fid, fp, y2, z2 + x2, fg)) * g.idx_f[1];
+      const float sz = (fabsf(az) + fast_speed_r(fid, fp, z2, x2 + y2, fg)) * g.idx_f[2];
       r32 = fmaxf(fmaxf(sx, sy), sz);
       if (sx != sx || sy != sy || sz != sz) r32 = __int_as_float(0x7fc00000);  // keep a NaN visible
     }
