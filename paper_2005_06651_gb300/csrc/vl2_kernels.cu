@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
   double id = 0.0, p = 0.0, vx = 0.0, vy = 0.0, vz = 0.0, bcx = 0.0, bcy = 0.0, bcz = 0.0;
   [[maybe_unused]] float s32v[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
   float r32 = 0.0f;
+  float s32[3] = {0.0f, 0.0f, 0.0f};  // the single-precision rate of each direction
   if (t < per * g.nblk) {
     const int b = (int)(t / per);
     int rem = (int)(t - (long long)b * per);
@@ -152,14 +153,18 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
       const float sx = (fabsf(ax) + fast_speed_r(fid, fp, x2, y2 + z2, fg)) * g.idx_f[0];
       const float sy = (fabsf(ay) + fast_speed_r(fid, fp, y2, z2 + x2, fg)) * g.idx_f[1];
       const float sz = (fabsf(az) + fast_speed_r(fid, fp, z2, x2 + y2, fg)) * g.idx_f[2];
+      s32[0] = sx;
+      s32[1] = sy;
+      s32[2] = sz;
       r32 = fmaxf(fmaxf(sx, sy), sz);
       if (sx != sx || sy != sy || sz != sz) r32 = __int_as_float(0x7fc00000);  // keep a NaN visible
     }
   }
   if (DT) {
-    // The CFL rate max_d (|v_d| + C_f,d) / dx_d of the CTA's cells, in FP64.  Only cells whose
-    // single-precision rate is within 1e-4 of the CTA's single-precision maximum (or is not a number) can
-    // hold the FP64 maximum, so only they are candidates; the result equals the FP64 maximum over all cells.
+    // The CFL rate max_d (|v_d| + C_f,d) / dx_d of the CTA's cells, in FP64.  Only (cell, direction) pairs
+    // whose single-precision rate is within 1e-4 of the CTA's single-precision maximum can hold the FP64
+    // maximum, so only they are evaluated in FP64 (every direction of a cell whose estimate is not a number,
+    // and everything when the estimate overflowed); the result equals the FP64 maximum over all cells.
     // The rate is a function of (1/rho, p, v, b_c) alone: candidates of a warp whose eight inputs are
     // bitwise equal (a region at rest makes whole warps of them) keep one representative, and the
     // representatives of the CTA are gathered into shared memory and evaluated by its first threads, so
@@ -167,6 +172,7 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
     __shared__ float redf[8];
     __shared__ unsigned long long red[8];
     __shared__ double cin[8][THREADS];
+    __shared__ unsigned char cdir[THREADS];  // the candidate's directions to evaluate (bits 0, 1, 2)
     __shared__ int ncand;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     float m32 = r32;
@@ -176,7 +182,15 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
     __syncthreads();
     m32 = 0.0f;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m32 = fmaxf(m32, redf[q]);
-    const bool cand = active && (!(r32 < m32 * 0.9999f) || isinf(m32));  // an overflowed estimate: every cell
+    const float thr = m32 * 0.9999f;
+    int dirs = 0;
+    if (active) {
+      if (isnan(r32) || isinf(m32))  // an unreliable estimate (an overflowed one: every cell)
+        dirs = 7;
+      else
+        dirs = (!(s32[0] < thr) ? 1 : 0) | (!(s32[1] < thr) ? 2 : 0) | (!(s32[2] < thr) ? 4 : 0);
+    }
+    const bool cand = dirs != 0;  // the cell's rate max_d s_d reaches the threshold
     const unsigned cmask = __ballot_sync(0xffffffffu, cand);
     bool lead = false;
     if (cand) {
@@ -204,6 +218,7 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
       cin[5][slot] = LEAN ? 0.5 * bcx : bcx;
       cin[6][slot] = LEAN ? 0.5 * bcy : bcy;
       cin[7][slot] = LEAN ? 0.5 * bcz : bcz;
+      cdir[slot] = (unsigned char)dirs;  // equal inputs give equal estimates, so the group shares it
     }
     __syncthreads();
     const int nc = ncand;  // CTA-uniform
@@ -213,11 +228,14 @@ __global__ void __launch_bounds__(256) k_prim(MeshView single, const MeshView* v
       const int q = threadIdx.x;
       const double cid = cin[0][q], cp = cin[1][q];
       const double bx2 = cin[5][q] * cin[5][q], by2 = cin[6][q] * cin[6][q], bz2 = cin[7][q] * cin[7][q];
-      const double rx = (fabs(cin[2][q]) + fast_speed_r(cid, cp, bx2, by2 + bz2, g.gamma)) * g.idx[0];
-      const double ry = (fabs(cin[3][q]) + fast_speed_r(cid, cp, by2, bz2 + bx2, g.gamma)) * g.idx[1];
-      const double rz = (fabs(cin[4][q]) + fast_speed_r(cid, cp, bz2, bx2 + by2, g.gamma)) * g.idx[2];
-      const unsigned long long ax = __double_as_longlong(rx), ay = __double_as_longlong(ry),
-                               az = __double_as_longlong(rz);
+      const int dq = cdir[q];
+      unsigned long long ax = 0ULL, ay = 0ULL, az = 0ULL;  // a direction left out cannot hold the maximum
+      if (dq & 1)
+        ax = __double_as_longlong((fabs(cin[2][q]) + fast_speed_r(cid, cp, bx2, by2 + bz2, g.gamma)) * g.idx[0]);
+      if (dq & 2)
+        ay = __double_as_longlong((fabs(cin[3][q]) + fast_speed_r(cid, cp, by2, bz2 + bx2, g.gamma)) * g.idx[1]);
+      if (dq & 4)
+        az = __double_as_longlong((fabs(cin[4][q]) + fast_speed_r(cid, cp, bz2, bx2 + by2, g.gamma)) * g.idx[2]);
       rate_bits = ax > ay ? ax : ay;
       rate_bits = rate_bits > az ? rate_bits : az;
     }
