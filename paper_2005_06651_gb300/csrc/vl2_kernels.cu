@@ -824,6 +824,8 @@ __global__ void __launch_bounds__(256, 4) k_update(MeshView single, const MeshVi
   const MeshView& V = stage_view(sv, single, views, work, tile, &box);
   const Geom& g = V.g;
   if (dtbox) h = beta * dtbox[box];
+  // h / dx_d, formed once per thread (the accumulated form's coefficients in the mixed precision)
+  [[maybe_unused]] const double hidx[3] = {h * g.idx[0], h * g.idx[1], h * g.idx[2]};
   const double* Ubase = V.a.u[base_reg];
   const double* Uoth = V.a.u[1 - base_reg];
   double* Uout = V.a.u[out_reg];
@@ -886,7 +888,7 @@ __global__ void __launch_bounds__(256, 4) k_update(MeshView single, const MeshVi
       if (PLAIN && sizeof(T) == 4) {
         double acc = Ubase[o];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) acc = fma(-(h * g.idx[d]), df[d], acc);
+        for (int d = 0; d < 3; ++d) acc = fma(-hidx[d], df[d], acc);
         Uout[o] = forced ? fma(h, src[v], acc) : acc;
         continue;
       }
@@ -909,7 +911,7 @@ __global__ void __launch_bounds__(256, 4) k_update(MeshView single, const MeshVi
     const long long o = (long long)b * g.box + c;
 #ifndef VL2_VALUE_SAFE
     if (PLAIN && sizeof(T) == 4) {
-      Bo[fd][o] = fma(h * g.idx[bq], dea, fma(-(h * g.idx[a]), deb, Bb[fd][o]));
+      Bo[fd][o] = fma(hidx[bq], dea, fma(-hidx[a], deb, Bb[fd][o]));
       continue;
     }
 #endif
@@ -949,6 +951,8 @@ __global__ void __launch_bounds__(256, 4) k_update_pair(MeshView single, int bas
   const MeshView& V = stage_view(sv, single, nullptr, nullptr, tile);
   const Geom& g = V.g;
   if (dtbox) h = beta * dtbox[0];  // the step formed on the device
+  // h / dx_d, formed once per thread (the accumulated form's coefficients)
+  const double hidx[3] = {h * g.idx[0], h * g.idx[1], h * g.idx[2]};
   const int ex = g.mb[0] + 1, ey = g.mb[1] + 1, ez = g.mb[2] + 1;
   const int px = (ex + 1) / 2;
   const long long per = (long long)px * ey * ez;
@@ -1024,8 +1028,8 @@ __global__ void __launch_bounds__(256, 4) k_update_pair(MeshView single, int bas
       if constexpr (ACC) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          acc0 = fma(-(h * g.idx[d]), d0[d], acc0);
-          acc1 = fma(-(h * g.idx[d]), d1[d], acc1);
+          acc0 = fma(-hidx[d], d0[d], acc0);
+          acc1 = fma(-hidx[d], d1[d], acc1);
         }
         if (forced) {
           acc0 = fma(h, src0[v], acc0);
@@ -1046,11 +1050,11 @@ __global__ void __launch_bounds__(256, 4) k_update_pair(MeshView single, int bas
                    static_cast<const T*>(V.a.e[1]) + (long long)b * g.box + c,
                    static_cast<const T*>(V.a.e[2]) + (long long)b * g.box + c};
   // B_out of one node from dE_b (along a) and dE_a (along b): the accumulated form or the L form
-  auto bnew = [&](double base, double deb, double ia, double dea, double ib) -> double {
+  auto bnew = [&](double base, double deb, int a, double dea, int bq) -> double {
     if constexpr (ACC)
-      return fma(h * ib, dea, fma(-(h * ia), deb, base));
+      return fma(hidx[bq], dea, fma(-hidx[a], deb, base));
     else
-      return plus_hl(base, h, -curl2(deb, ia, dea, ib));
+      return plus_hl(base, h, -curl2(deb, g.idx[a], dea, g.idx[bq]));
   };
   const long long o = (long long)b * g.box + c;
   // face field fd = 0: B1 -= (h/dy) dE3/dy, += (h/dz) dE2/dz at both nodes (transversally inside)
@@ -1062,8 +1066,8 @@ __global__ void __launch_bounds__(256, 4) k_update_pair(MeshView single, int bas
     ld_pair(E[1] + sz, s0, s1);
     double b0, b1;
     ld_pair(V.a.b[base_reg][0] + o, b0, b1);
-    const double n0 = bnew(b0, to_f64(q0) - to_f64(p0), g.idx[1], to_f64(s0) - to_f64(r0), g.idx[2]);
-    const double n1 = bnew(b1, to_f64(q1) - to_f64(p1), g.idx[1], to_f64(s1) - to_f64(r1), g.idx[2]);
+    const double n0 = bnew(b0, to_f64(q0) - to_f64(p0), 1, to_f64(s0) - to_f64(r0), 2);
+    const double n1 = bnew(b1, to_f64(q1) - to_f64(p1), 1, to_f64(s1) - to_f64(r1), 2);
     if (node1)
       st_pair(V.a.b[out_reg][0] + o, n0, n1);
     else
@@ -1078,8 +1082,8 @@ __global__ void __launch_bounds__(256, 4) k_update_pair(MeshView single, int bas
     const T r2 = in1 ? E[2][2] : T(0);
     double b0, b1;
     ld_pair(V.a.b[base_reg][1] + o, b0, b1);
-    const double n0 = bnew(b0, to_f64(q0) - to_f64(p0), g.idx[2], to_f64(r1) - to_f64(r0), g.idx[0]);
-    const double n1 = bnew(b1, to_f64(q1) - to_f64(p1), g.idx[2], to_f64(r2) - to_f64(r1), g.idx[0]);
+    const double n0 = bnew(b0, to_f64(q0) - to_f64(p0), 2, to_f64(r1) - to_f64(r0), 0);
+    const double n1 = bnew(b1, to_f64(q1) - to_f64(p1), 2, to_f64(r2) - to_f64(r1), 0);
     if (in1)
       st_pair(V.a.b[out_reg][1] + o, n0, n1);
     else
@@ -1094,8 +1098,8 @@ __global__ void __launch_bounds__(256, 4) k_update_pair(MeshView single, int bas
     ld_pair(E[0] + sy, r0, r1);
     double b0, b1;
     ld_pair(V.a.b[base_reg][2] + o, b0, b1);
-    const double n0 = bnew(b0, to_f64(p1) - to_f64(p0), g.idx[0], to_f64(r0) - to_f64(q0), g.idx[1]);
-    const double n1 = bnew(b1, to_f64(p2) - to_f64(p1), g.idx[0], to_f64(r1) - to_f64(q1), g.idx[1]);
+    const double n0 = bnew(b0, to_f64(p1) - to_f64(p0), 0, to_f64(r0) - to_f64(q0), 1);
+    const double n1 = bnew(b1, to_f64(p2) - to_f64(p1), 0, to_f64(r1) - to_f64(q1), 1);
     if (in1)
       st_pair(V.a.b[out_reg][2] + o, n0, n1);
     else
